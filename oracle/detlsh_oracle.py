@@ -1,0 +1,401 @@
+"""CPU oracle for DET-LSH (Wei et al., PVLDB 17(9), 2024) -- TEST INFRASTRUCTURE.
+
+This module is a plain, slow, deliberately unoptimised restatement of what the
+paper's method computes. It exists only to check the CUDA library: it may be
+imported by ``tests/``, by ``__graft_entry__.smoke()`` and by the CPU-baseline
+leg of ``bench.py``, and by nothing else. It shares no code with the CUDA path.
+
+Precision: FP64 throughout, except where floating point decides an integer
+(a leaf's activation round): there the lower bound is evaluated in FP32 with a
+fixed operation order, the precision the GPU path decides in (see
+``leaf_lb2_fp32``).
+
+Readings of passages that are silent or ambiguous (numbered as in the design
+notes):
+ R1  breakpoints: interior edge z (1-based, z=1..N_r-1) is the element of
+     0-based rank floor(n_s/N_r)*z of the sorted sample (Sec. 4.1 formula for
+     B_ij, indices read 0-based, n replaced by the sample size n_s of Alg. 1).
+ R2  encoding: regions are half-open [e_z, e_{z+1}); a value equal to an edge
+     goes up; values outside the sample range clamp to region 0 / N_r-1.
+ R3  DE-Tree: bulk-loaded, insertion-order-free version of Alg. 3: a node
+     holding more than max_size points splits by one more bit of the dimension
+     whose next bit divides its points most evenly (ties to the lowest
+     dimension); bit-0 child first; empty children dropped; a node whose codes
+     are fully resolved stays an (oversized) leaf.
+ R4  leaf box in the lower bound uses -inf/+inf for the outermost edges.
+ R5  query (Alg. 7 + the optimised range query of Sec. 6.2.2): a leaf is taken
+     whole in the first round whose projected radius covers its lower bound;
+     within a round trees go in order 1..L and leaves by (lower bound, leaf
+     number); the |S| >= beta*n+k test runs after every leaf; the
+     ">= k within c*r" test after every round; the loop also ends once every
+     leaf is active (S cannot grow further, so the result is unchanged).
+ R6  thresholds: r_0 = r_min, r_{t+1} = r_t * c in FP64; the projected-radius
+     threshold (eps*r_t)^2 and the exact-distance threshold (c*r_t)^2 are
+     formed in FP64 and rounded once to FP32; from round ROUND_CAP-1 on both
+     are +inf.
+ R7  r_min <= 0 selects sqrt(min positive leaf lower bound^2)/eps (the paper's
+     "magic" r_min of Sec. 5.2 is defined only through the search itself);
+     with no positive lower bound r_min = 1.
+ R8  eps = sqrt(chi2 upper alpha1-quantile with K degrees of freedom),
+     alpha1 = exp(-1/L) (Lemma 3, Eq. 2).
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+ROUND_CAP = 256
+
+
+# ---------------------------------------------------------------- parameters
+def eps_from_lemma3(K: int, L: int) -> float:
+    """epsilon of Lemma 3 / Eq. 2: eps^2 = chi2_{alpha1}(K), alpha1 = exp(-1/L).
+
+    L = -1/ln(alpha1) in Lemma 3 is inverted for alpha1 (reading R8).
+    """
+    from scipy.stats import chi2
+    alpha1 = math.exp(-1.0 / L)
+    return math.sqrt(chi2.isf(alpha1, K))
+
+
+def beta_from_lemma3(K: int, L: int, c: float) -> float:
+    """Theoretical beta of Lemma 3: beta = 2 - 2 * alpha2^L with
+    chi2_{alpha2}(K) = eps^2 / c^2 (Eq. 2)."""
+    from scipy.stats import chi2
+    eps2 = eps_from_lemma3(K, L) ** 2
+    alpha2 = chi2.sf(eps2 / (c * c), K)
+    return 2.0 - 2.0 * alpha2 ** L
+
+
+# ---------------------------------------------------------------- encoding phase
+def project(A: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """Eq. 1, h(o) = a . o for all L*K hash vectors: P[o, r] = sum_t A[r,t] X[o,t].
+
+    A is [L*K, d] (row r = i*K + j), X is [n, d]; returns FP64 [n, L*K].
+    """
+    return np.asarray(X, dtype=np.float64) @ np.asarray(A, dtype=np.float64).T
+
+
+def select_breakpoints(Ps: np.ndarray, n_regions: int) -> np.ndarray:
+    """Alg. 1 / Sec. 4.1: N_r+1 breakpoints per projected dimension from the sample.
+
+    Ps is [n_s, L*K] (projections of the sampled points). For each column the
+    values are sorted ascending (the QuickSelect rounds of Alg. 1 find the
+    same order statistics); B(1) is the minimum, B(N_r+1) the maximum and the
+    interior breakpoint z (z=1..N_r-1) is the element of rank
+    floor(n_s/N_r)*z (reading R1). Returns FP64 [L*K, N_r+1].
+    """
+    n_s, LK = Ps.shape
+    m = n_s // n_regions
+    E = np.empty((LK, n_regions + 1), dtype=np.float64)
+    for r in range(LK):
+        srt = np.sort(np.asarray(Ps[:, r], dtype=np.float64))
+        E[r, 0] = srt[0]
+        for z in range(1, n_regions):
+            E[r, z] = srt[m * z]
+        E[r, n_regions] = srt[n_s - 1]
+    return E
+
+
+def encode(P: np.ndarray, E: np.ndarray) -> np.ndarray:
+    """Alg. 2: region symbol of every projected coordinate.
+
+    code = number of interior breakpoints e_z (z=1..N_r-1) with e_z <= p,
+    i.e. the b of B(b) <= h < B(b+1) with half-open regions (reading R2).
+    P is [n, L*K]; returns uint8 [n, L*K].
+    """
+    n, LK = P.shape
+    out = np.empty((n, LK), dtype=np.uint8)
+    for r in range(LK):
+        interior = E[r, 1:-1]
+        out[:, r] = np.searchsorted(interior, P[:, r], side="right")
+    return out
+
+
+# ---------------------------------------------------------------- indexing phase
+@dataclass
+class Tree:
+    """One DE-Tree as its leaves in depth-first order.
+
+    ids:      point ids in leaf order (leaf by leaf, ascending id within a leaf)
+    offset:   [n_leaves+1] start of each leaf in ``ids``
+    plen:     [n_leaves, K] prefix length (bits) of each dimension
+    prefix:   [n_leaves, K] prefix value of each dimension
+    """
+    ids: np.ndarray
+    offset: np.ndarray
+    plen: np.ndarray
+    prefix: np.ndarray
+
+    @property
+    def n_leaves(self) -> int:
+        return len(self.offset) - 1
+
+    def box(self, bits: int):
+        """Code range [lo, hi] of every leaf in every dimension."""
+        shift = bits - self.plen.astype(np.int64)
+        lo = self.prefix.astype(np.int64) << shift
+        hi = ((self.prefix.astype(np.int64) + 1) << shift) - 1
+        return lo, hi
+
+
+def build_tree(codes: np.ndarray, n_regions: int, max_size: int) -> Tree:
+    """Alg. 3 with the split rule of Sec. 4.2, bulk-loaded (reading R3).
+
+    codes is uint8 [n, K] (one projected space). The root has 2^K first-layer
+    nodes, one per vector of the K most significant code bits (dimension 0 is
+    the most significant bit of the node key). A node holding more than
+    max_size points is split on the dimension whose next bit divides it most
+    evenly, bit-0 child first.
+    """
+    codes = np.asarray(codes, dtype=np.int64)
+    n, K = codes.shape
+    bits = int(round(math.log2(n_regions)))
+    assert 1 << bits == n_regions
+    leaves_ids: List[np.ndarray] = []
+    leaves_plen: List[np.ndarray] = []
+    leaves_prefix: List[np.ndarray] = []
+
+    def split(members: np.ndarray, plen: np.ndarray, prefix: np.ndarray):
+        count = len(members)
+        splittable = np.nonzero(plen < bits)[0]
+        if count <= max_size or len(splittable) == 0:
+            leaves_ids.append(members)
+            leaves_plen.append(plen.copy())
+            leaves_prefix.append(prefix.copy())
+            return
+        best_j, best_gap, best_bit = -1, None, None
+        for j in splittable:
+            nb = (codes[members, j] >> (bits - 1 - plen[j])) & 1
+            ones = int(nb.sum())
+            gap = abs(2 * ones - count)
+            if best_gap is None or gap < best_gap:
+                best_j, best_gap, best_bit = j, gap, nb
+        for bit in (0, 1):
+            child = members[best_bit == bit]
+            if len(child) == 0:
+                continue
+            cplen = plen.copy()
+            cprefix = prefix.copy()
+            cplen[best_j] += 1
+            cprefix[best_j] = prefix[best_j] * 2 + bit
+            split(child, cplen, cprefix)
+
+    msb = (codes >> (bits - 1)) & 1
+    key = np.zeros(n, dtype=np.int64)
+    for j in range(K):
+        key = key * 2 + msb[:, j]
+    order = np.argsort(key, kind="stable")
+    skey = key[order]
+    starts = np.nonzero(np.r_[True, skey[1:] != skey[:-1]])[0]
+    ends = np.r_[starts[1:], n]
+    for s, e in zip(starts, ends):
+        members = order[s:e]
+        plen = np.ones(K, dtype=np.int64)
+        prefix = msb[members[0]].astype(np.int64)
+        split(members, plen, prefix)
+
+    offset = np.zeros(len(leaves_ids) + 1, dtype=np.int64)
+    offset[1:] = np.cumsum([len(x) for x in leaves_ids])
+    ids = np.concatenate(leaves_ids) if leaves_ids else np.zeros(0, np.int64)
+    return Tree(ids=ids.astype(np.int64), offset=offset,
+                plen=np.array(leaves_plen, dtype=np.int64).reshape(-1, K),
+                prefix=np.array(leaves_prefix, dtype=np.int64).reshape(-1, K))
+
+
+@dataclass
+class Index:
+    """Everything the query phase reads: data, hash vectors, breakpoints, L trees."""
+    X: np.ndarray
+    A: np.ndarray
+    E: np.ndarray          # FP64 [L*K, N_r+1]
+    trees: List[Tree]
+    K: int
+    L: int
+    n_regions: int
+    P: Optional[np.ndarray] = None       # FP64 projections [n, L*K] (kept for tests)
+    codes: Optional[np.ndarray] = None   # uint8 [n, L*K]
+
+    @property
+    def n(self) -> int:
+        return self.X.shape[0]
+
+
+def build_index(X, A, sample, K: int, L: int, n_regions: int, max_size: int) -> Index:
+    """Encoding phase (Alg. 1, Alg. 2) followed by the indexing phase (Alg. 3)."""
+    X = np.asarray(X)
+    A = np.asarray(A)
+    sample = np.asarray(sample, dtype=np.int64)
+    P = project(A, X)
+    E = select_breakpoints(P[sample], n_regions)
+    codes = encode(P, E)
+    trees = [build_tree(codes[:, i * K:(i + 1) * K], n_regions, max_size) for i in range(L)]
+    return Index(X=X, A=A, E=E, trees=trees, K=K, L=L, n_regions=n_regions, P=P, codes=codes)
+
+
+# ---------------------------------------------------------------- query phase
+def leaf_lb2_fp32(qp32: np.ndarray, E32: np.ndarray, lo: np.ndarray, hi: np.ndarray,
+                  n_regions: int) -> np.ndarray:
+    """Squared lower-bound distance between q' and each leaf box (Alg. 5, first step).
+
+    For one projected space: qp32 [K] fp32, E32 [K, N_r+1] fp32 breakpoints,
+    lo/hi [n_leaves, K] code ranges. A leaf covers [e_lo, e_{hi+1}) in every
+    dimension, with e_0 = -inf and e_{N_r} = +inf (reading R4). Per dimension
+    delta = max(e_lo - x, x - e_{hi+1}, 0) in FP32; the squares are added in
+    FP32 in dimension order 0..K-1 (the decision precision of the GPU path).
+    """
+    nl, K = lo.shape
+    acc = np.zeros(nl, dtype=np.float32)
+    inf = np.float32(np.inf)
+    for j in range(K):
+        x = np.float32(qp32[j])
+        el = np.where(lo[:, j] == 0, -inf, E32[j, lo[:, j]]).astype(np.float32)
+        eh = np.where(hi[:, j] == n_regions - 1, inf,
+                      E32[j, np.minimum(hi[:, j] + 1, n_regions)]).astype(np.float32)
+        a = (el - x).astype(np.float32)
+        b = (x - eh).astype(np.float32)
+        delta = np.maximum(np.maximum(a, b), np.float32(0.0))
+        sq = (delta * delta).astype(np.float32)
+        acc = (acc + sq).astype(np.float32)
+    return acc
+
+
+def round_thresholds(r_min: float, c: float, eps: float):
+    """Per-round thresholds of Alg. 7 (r <- c*r), reading R6.
+
+    Returns (thr_proj, thr_exact): FP32 arrays of length ROUND_CAP holding
+    (eps*r_t)^2 and (c*r_t)^2.
+    """
+    thr_p = np.empty(ROUND_CAP, dtype=np.float32)
+    thr_c = np.empty(ROUND_CAP, dtype=np.float32)
+    r = float(r_min)
+    c = float(np.float32(c))
+    with np.errstate(over="ignore"):
+        for t in range(ROUND_CAP):
+            if t == ROUND_CAP - 1:
+                thr_p[t] = np.inf
+                thr_c[t] = np.inf
+                break
+            er = eps * r
+            cr = c * r
+            thr_p[t] = np.float32(er * er)
+            thr_c[t] = np.float32(cr * cr)
+            r = r * c
+    return thr_p, thr_c
+
+
+@dataclass
+class QueryResult:
+    ids: np.ndarray          # int64 [k], -1 padded
+    dist: np.ndarray         # FP64 [k] Euclidean distance, +inf padded
+    n_cand: int              # |S| at termination
+    rounds: int              # rounds started (t* + 1)
+    stop: int                # 1: |S| >= beta n + k; 2: >= k within c r; 3: all leaves active
+    cand: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))  # sorted S
+
+
+def c2k_ann(index: Index, q: np.ndarray, k: int, c: float, r_min: float, eps: float,
+            beta: float, keep_candidates: bool = False) -> QueryResult:
+    """Alg. 7 (c^2-k-ANN) with the optimised range query of Sec. 6.2.2 (readings R5-R7)."""
+    X = index.X
+    n = X.shape[0]
+    K, L, Nr = index.K, index.L, index.n_regions
+    bits = int(round(math.log2(Nr)))
+    T = math.ceil(float(beta) * float(n) + float(k))
+
+    q64 = np.asarray(q, dtype=np.float64)
+    qp = project(index.A, q64[None, :])[0]               # Alg. 7: H_i(q), hoisted out of the loop
+    qp32 = qp.astype(np.float32)
+    E32 = index.E.astype(np.float32)
+
+    lb2 = []
+    for i, tree in enumerate(index.trees):
+        lo, hi = tree.box(bits)
+        lb2.append(leaf_lb2_fp32(qp32[i * K:(i + 1) * K], E32[i * K:(i + 1) * K], lo, hi, Nr))
+
+    if r_min <= 0:                                       # reading R7
+        pos = [x[x > 0] for x in lb2]
+        pos = np.concatenate(pos) if pos else np.zeros(0, np.float32)
+        r_min = math.sqrt(float(pos.min())) / eps if pos.size else 1.0
+    thr_p, thr_c = round_thresholds(r_min, c, eps)
+
+    # first round in which each leaf's lower bound is covered
+    first_round = [np.searchsorted(thr_p, x, side="left") for x in lb2]
+
+    in_S = np.zeros(n, dtype=bool)
+    S_order: List[np.ndarray] = []
+    dist2_of = {}
+    n_S = 0
+    stop = 0
+    t = 0
+    for t in range(ROUND_CAP):
+        for i, tree in enumerate(index.trees):
+            new_leaves = np.nonzero(first_round[i] == t)[0]
+            order = np.lexsort((new_leaves, lb2[i][new_leaves]))
+            for leaf in new_leaves[order]:
+                pts = tree.ids[tree.offset[leaf]:tree.offset[leaf + 1]]
+                fresh = pts[~in_S[pts]]
+                in_S[fresh] = True
+                if len(fresh):
+                    S_order.append(fresh)
+                    diff = X[fresh].astype(np.float64) - q64[None, :]
+                    d2 = np.einsum("ij,ij->i", diff, diff)
+                    for o, v in zip(fresh.tolist(), d2.tolist()):
+                        dist2_of[o] = v
+                n_S += len(fresh)
+                if n_S >= T:
+                    stop = 1
+                    break
+            if stop:
+                break
+        if stop:
+            break
+        within = sum(1 for v in dist2_of.values() if v <= float(thr_c[t]))
+        if within >= k:
+            stop = 2
+            break
+        if all((fr <= t).all() for fr in first_round):
+            stop = 3
+            break
+
+    cand = np.concatenate(S_order) if S_order else np.zeros(0, np.int64)
+    d2 = np.array([dist2_of[o] for o in cand.tolist()], dtype=np.float64)
+    order = np.lexsort((cand, d2))[:k]
+    ids = np.full(k, -1, dtype=np.int64)
+    dist = np.full(k, np.inf, dtype=np.float64)
+    ids[:len(order)] = cand[order]
+    dist[:len(order)] = np.sqrt(d2[order])
+    return QueryResult(ids=ids, dist=dist, n_cand=int(n_S), rounds=t + 1, stop=stop,
+                       cand=np.sort(cand) if keep_candidates else np.zeros(0, np.int64))
+
+
+# ---------------------------------------------------------------- evaluation measures
+def exact_knn(X: np.ndarray, q: np.ndarray, k: int):
+    """The exact k nearest points o*_1..o*_k of Def. 2 by a full scan (FP64), ties by id."""
+    diff = np.asarray(X, dtype=np.float64) - np.asarray(q, dtype=np.float64)[None, :]
+    d2 = np.einsum("ij,ij->i", diff, diff)
+    order = np.lexsort((np.arange(len(d2)), d2))[:k]
+    return order.astype(np.int64), np.sqrt(d2[order])
+
+
+def recall(result_ids: np.ndarray, exact_ids: np.ndarray) -> float:
+    """Sec. 6.1: |R intersect R*| / k."""
+    k = len(exact_ids)
+    return len(set(int(x) for x in result_ids if x >= 0) & set(int(x) for x in exact_ids)) / k
+
+
+def overall_ratio(result_dist: np.ndarray, exact_dist: np.ndarray) -> float:
+    """Sec. 6.1: (1/k) sum_i ||q,o_i|| / ||q,o*_i||, both lists ascending."""
+    rd = np.sort(np.asarray(result_dist, dtype=np.float64))
+    ed = np.sort(np.asarray(exact_dist, dtype=np.float64))
+    ratios = []
+    for a, b in zip(rd, ed):
+        if b == 0.0:
+            ratios.append(1.0 if a == 0.0 else np.inf)
+        else:
+            ratios.append(a / b)
+    return float(np.mean(ratios))

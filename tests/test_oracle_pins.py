@@ -1,0 +1,317 @@
+"""Pins for the CPU oracle: each test checks it against something the paper or
+the mathematics fixes independently of the oracle's own code (closed forms,
+hand-worked examples, order-statistic counts, brute force, distribution laws).
+"""
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import detlsh_oracle as O
+from workloads import gaussian_projection, make_workload, sample_ids
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+# ------------------------------------------------------------------ Lemma 3 / Eq. 2
+def _chi2_sf_even(x, K):
+    """Survival function of chi2 with even K in closed form (Poisson sum)."""
+    m = K // 2
+    h = x / 2.0
+    term, tot = 1.0, 1.0
+    for i in range(1, m):
+        term *= h / i
+        tot += term
+    return math.exp(-h) * tot
+
+
+def _bisect(f, lo, hi, it=200):
+    for _ in range(it):
+        mid = 0.5 * (lo + hi)
+        if f(mid) > 0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+@pytest.mark.parametrize("K,L", [(16, 4), (16, 1), (16, 8), (8, 4), (32, 2)])
+def test_eps_matches_closed_form(K, L):
+    alpha1 = math.exp(-1.0 / L)
+    eps2 = _bisect(lambda x: _chi2_sf_even(x, K) - alpha1, 0.0, 400.0)
+    assert abs(O.eps_from_lemma3(K, L) ** 2 - eps2) < 1e-9 * eps2
+
+
+@pytest.mark.parametrize("L,c,beta", [(4, 1.2, 0.3734), (4, 1.5, 0.0380), (4, 2.0, 0.0010),
+                                      (1, 1.5, 0.0843), (2, 1.5, 0.0553), (8, 1.5, 0.0275)])
+def test_beta_matches_closed_form(L, c, beta):
+    K = 16
+    alpha1 = math.exp(-1.0 / L)
+    eps2 = _bisect(lambda x: _chi2_sf_even(x, K) - alpha1, 0.0, 400.0)
+    alpha2 = _chi2_sf_even(eps2 / (c * c), K)
+    b = 2.0 - 2.0 * alpha2 ** L
+    assert abs(O.beta_from_lemma3(K, L, c) - b) < 1e-9
+    assert abs(b - beta) < 6e-5
+
+
+def test_eps_default_value():
+    # K=16, L=4 (the paper's defaults, Sec. 5.2): eps^2 = 11.4820...
+    assert abs(O.eps_from_lemma3(16, 4) - 3.388514699) < 1e-8
+
+
+# ------------------------------------------------------------------ Eq. 1 projection
+def test_project_permutation_special_case():
+    # L=1, K=d and A a scaled permutation: h_j(o) = 2 * o[perm[j]] exactly
+    rng = np.random.default_rng(0)
+    d = 12
+    perm = rng.permutation(d)
+    A = np.zeros((d, d))
+    A[np.arange(d), perm] = 2.0
+    X = rng.standard_normal((50, d))
+    P = O.project(A, X)
+    assert np.array_equal(P, 2.0 * X[:, perm])
+
+
+def test_project_lemma1_chi2_law():
+    """Lemma 1: s'^2 / s^2 ~ chi2(K) over the draws of the hash vectors."""
+    from scipy.stats import chi2, kstest
+    rng = np.random.default_rng(1)
+    d, K = 40, 16
+    o1 = rng.standard_normal(d)
+    o2 = rng.standard_normal(d) * 3.0
+    s2 = float(((o1 - o2) ** 2).sum())
+    ratios = []
+    for seed in range(300):
+        A = gaussian_projection(1, K, d, seed=seed + 100).numpy()
+        P = O.project(A, np.stack([o1, o2]))
+        ratios.append(float(((P[0] - P[1]) ** 2).sum()) / s2)
+    ratios = np.array(ratios)
+    assert kstest(ratios, chi2(K).cdf).pvalue > 0.01
+    assert abs(ratios.mean() - K) < 4 * math.sqrt(2 * K / len(ratios))
+
+
+# ------------------------------------------------------------------ Alg. 1 breakpoints
+@pytest.mark.parametrize("n_s,Nr", [(1000, 16), (10_000, 256), (257, 256), (64, 2)])
+def test_breakpoints_are_rank_m_z_order_statistics(n_s, Nr):
+    rng = np.random.default_rng(2)
+    Ps = rng.standard_normal((n_s, 3)) * np.array([1.0, 50.0, 1e-3])
+    E = O.select_breakpoints(Ps, Nr)
+    m = n_s // Nr
+    for r in range(3):
+        col = Ps[:, r]
+        assert E[r, 0] == col.min() and E[r, Nr] == col.max()
+        for z in range(1, Nr):
+            # exactly m*z sampled values lie strictly below interior edge z
+            assert int((col < E[r, z]).sum()) == m * z
+    # the sample's own codes fill regions 0..N_r-2 with m points each (Sec. 4.1)
+    codes = O.encode(Ps, E)
+    for r in range(3):
+        counts = np.bincount(codes[:, r], minlength=Nr)
+        assert (counts[:-1] == m).all()
+        assert counts[-1] == n_s - m * (Nr - 1)
+
+
+# ------------------------------------------------------------------ Alg. 2 encoding
+def test_encode_bruteforce_and_ties():
+    rng = np.random.default_rng(4)
+    Nr = 8
+    E = np.sort(rng.standard_normal((2, Nr + 1)), axis=1)
+    P = np.concatenate([rng.standard_normal((200, 2)) * 2,
+                        E[:, 1:-1].T,                  # exactly on interior edges
+                        np.array([[-1e9, 1e9]])])      # outside the sampled range
+    codes = O.encode(P, E)
+    for o in range(P.shape[0]):
+        for r in range(2):
+            # brute force: the region b with e_b <= p < e_{b+1}, e_0=-inf, e_Nr=+inf
+            b = 0
+            for z in range(1, Nr):
+                if P[o, r] >= E[r, z]:
+                    b = z
+            assert codes[o, r] == b
+    # on an edge the value goes up into the region that starts there
+    for z in range(1, Nr):
+        assert codes[200 + z - 1, 0] == z
+    assert codes[-1, 0] == 0 and codes[-1, 1] == Nr - 1
+
+
+def test_encode_monotone():
+    rng = np.random.default_rng(5)
+    Ps = rng.standard_normal((500, 1))
+    E = O.select_breakpoints(Ps, 32)
+    p = np.sort(rng.standard_normal(3000) * 2)[:, None]
+    c = O.encode(p, E)[:, 0]
+    assert (np.diff(c.astype(int)) >= 0).all()
+    assert c.min() == 0 and c.max() == 31
+
+
+# ------------------------------------------------------------------ Alg. 3 DE-Tree
+@pytest.mark.parametrize("fixture", ["split_example.json", "split_rule_hand.json"])
+def test_split_examples(fixture):
+    g = _load(fixture)
+    tree = O.build_tree(np.array(g["codes"], dtype=np.uint8), g["n_regions"], g["max_size"])
+    assert tree.n_leaves == len(g["expected_leaves"])
+    for leaf, exp in enumerate(g["expected_leaves"]):
+        ids = tree.ids[tree.offset[leaf]:tree.offset[leaf + 1]]
+        assert ids.tolist() == exp["ids"]
+        assert tree.plen[leaf].tolist() == exp["plen"]
+        assert tree.prefix[leaf].tolist() == exp["prefix"]
+
+
+def _check_tree(tree, codes, Nr, max_size):
+    n, K = codes.shape
+    bits = int(math.log2(Nr))
+    lo, hi = tree.box(bits)
+    # the leaves partition the points
+    assert sorted(tree.ids.tolist()) == list(range(n))
+    keys_prev = None
+    for leaf in range(tree.n_leaves):
+        ids = tree.ids[tree.offset[leaf]:tree.offset[leaf + 1]]
+        assert len(ids) > 0
+        assert (np.diff(ids) > 0).all()                         # ascending ids
+        cl = codes[ids].astype(np.int64)
+        assert ((cl >= lo[leaf]) & (cl <= hi[leaf])).all()      # points lie in the box
+        if len(ids) > max_size:                                 # oversized only if unsplittable
+            assert (tree.plen[leaf] == bits).all()
+        assert (tree.plen[leaf] >= 1).all()
+        # depth-first order: boxes visited in ascending code order, dim 0 most significant
+        key = tuple((lo[leaf] >> (bits - 1)).tolist())
+        if keys_prev is not None:
+            assert key >= keys_prev
+        keys_prev = key
+    # boxes are disjoint: every point's code vector falls in exactly one box
+    inside = ((codes[:, None, :].astype(np.int64) >= lo[None]) &
+              (codes[:, None, :].astype(np.int64) <= hi[None])).all(axis=2)
+    assert (inside.sum(axis=1) == 1).all()
+
+
+@pytest.mark.parametrize("Nr,max_size,K", [(16, 8, 4), (4, 3, 3), (256, 16, 2), (2, 1, 5)])
+def test_tree_invariants_random(Nr, max_size, K):
+    rng = np.random.default_rng(6)
+    n = 600
+    # skewed codes so that many splits happen, with duplicates
+    codes = np.minimum(rng.geometric(0.3, size=(n, K)) - 1, Nr - 1).astype(np.uint8)
+    tree = O.build_tree(codes, Nr, max_size)
+    _check_tree(tree, codes, Nr, max_size)
+    # the root has 2^K first-layer nodes: no leaf mixes two MSB vectors
+    bits = int(math.log2(Nr))
+    for leaf in range(tree.n_leaves):
+        ids = tree.ids[tree.offset[leaf]:tree.offset[leaf + 1]]
+        msb = codes[ids] >> (bits - 1)
+        assert (msb == msb[0]).all()
+
+
+def test_tree_no_split_equals_root_partition():
+    # with max_size >= n there are no splits: the leaves are the 2^K root children
+    rng = np.random.default_rng(7)
+    codes = rng.integers(0, 16, size=(300, 3)).astype(np.uint8)
+    tree = O.build_tree(codes, 16, 1000)
+    keys = (codes >> 3).astype(int) @ np.array([4, 2, 1])
+    assert tree.n_leaves == len(np.unique(keys))
+    for leaf in range(tree.n_leaves):
+        ids = tree.ids[tree.offset[leaf]:tree.offset[leaf + 1]]
+        assert len(set(keys[ids].tolist())) == 1
+        assert (tree.plen[leaf] == 1).all()
+
+
+# ------------------------------------------------------------------ Alg. 5 lower bound
+def test_lower_bound_vs_brute_force():
+    rng = np.random.default_rng(8)
+    K, Nr = 3, 8
+    E32 = np.sort(rng.standard_normal((K, Nr + 1)), axis=1).astype(np.float32)
+    lo = rng.integers(0, Nr, size=(200, K))
+    hi = np.minimum(lo + rng.integers(0, 4, size=(200, K)), Nr - 1)
+    for trial in range(20):
+        q = (rng.standard_normal(K) * 1.5).astype(np.float32)
+        lb2 = O.leaf_lb2_fp32(q, E32, lo, hi, Nr)
+        for leaf in range(0, 200, 7):
+            lower = np.where(lo[leaf] == 0, -np.inf, E32[np.arange(K), lo[leaf]]).astype(np.float64)
+            upper = np.where(hi[leaf] == Nr - 1, np.inf,
+                             E32[np.arange(K), np.minimum(hi[leaf] + 1, Nr)]).astype(np.float64)
+            # random points of the box never come closer than the bound
+            pts = rng.uniform(np.maximum(lower, -5), np.minimum(upper, 5), size=(64, K))
+            d2 = ((pts - q.astype(np.float64)) ** 2).sum(axis=1)
+            assert lb2[leaf] <= d2.min() * (1 + 1e-6) + 1e-12
+            # and the box point nearest to q attains it
+            nearest = np.clip(q.astype(np.float64), lower, upper)
+            d2n = ((nearest - q.astype(np.float64)) ** 2).sum()
+            assert abs(float(lb2[leaf]) - d2n) <= 1e-6 * max(d2n, 1e-30) + 1e-12
+
+
+def test_lower_bound_zero_inside():
+    E32 = np.array([[-3, -1, 0, 1, 3]], dtype=np.float32)
+    lo = np.array([[0], [1], [2], [3], [1]])
+    hi = np.array([[0], [1], [2], [3], [2]])
+    lb = O.leaf_lb2_fp32(np.array([0.5], np.float32), E32, lo, hi, 4)
+    assert lb.tolist() == [np.float32(1.5) ** 2, np.float32(0.5) ** 2, 0.0, np.float32(0.5) ** 2, 0.0]
+
+
+# ------------------------------------------------------------------ Alg. 7 query
+def _hand_index(g):
+    X = np.array(g["X"], dtype=np.float64)[:, None]
+    A = np.array([[1.0]])
+    E = np.array([g["edges"]], dtype=np.float64)
+    codes = O.encode(O.project(A, X), E)
+    tree = O.build_tree(codes, 4, g["max_size"])
+    return O.Index(X=X, A=A, E=E, trees=[tree], K=1, L=1, n_regions=4)
+
+
+def test_query_hand_worked():
+    g = _load("query_hand.json")
+    idx = _hand_index(g)
+    assert idx.trees[0].n_leaves == 4
+    for case in g["cases"]:
+        res = O.c2k_ann(idx, np.array([g["q"]]), case["k"], case["c"], case["r_min"],
+                        g["eps"], case["beta"])
+        exp_d = [np.inf if v == "inf" else v for v in case["dist"]]
+        assert res.ids.tolist() == case["ids"], case["why"]
+        assert res.dist.tolist() == exp_d, case["why"]
+        assert (res.n_cand, res.rounds, res.stop) == (case["n_cand"], case["rounds"], case["stop"]), case["why"]
+
+
+def test_query_all_leaves_is_exact_knn():
+    # beta*n + k >= n and a radius covering every leaf: S = D, so Alg. 7 returns the exact kNN
+    X, Q = make_workload("tiny", n=2000, nq=10)
+    X, Q = X.numpy(), Q.numpy()
+    A = gaussian_projection(2, 8, X.shape[1]).numpy()
+    idx = O.build_index(X, A, sample_ids(2000, 200).numpy(), 8, 2, 16, 32)
+    for q in Q:
+        res = O.c2k_ann(idx, q, 7, 1.5, 1e6, 3.0, 1.0, keep_candidates=True)
+        ids, dist = O.exact_knn(X, q, 7)
+        assert res.n_cand == 2000
+        assert res.ids.tolist() == ids.tolist()
+        assert np.allclose(res.dist, dist, rtol=0, atol=0)
+
+
+def test_tiny_config_quality():
+    """Theorem 2 (statistical): on the tiny workload the result is a c^2-k-ANN for
+    well over a (1/2 - 1/e) fraction of queries, and recall is high."""
+    X, Q = make_workload("tiny")
+    X, Q = X.numpy(), Q.numpy()
+    A = gaussian_projection(4, 16, 32).numpy()
+    idx = O.build_index(X, A, sample_ids(10_000, 1000).numpy(), 16, 4, 16, 256)
+    eps = O.eps_from_lemma3(16, 4)
+    recalls, ok = [], 0
+    for q in Q[:40]:
+        res = O.c2k_ann(idx, q, 10, 1.5, 0.0, eps, 0.1)
+        ids, dist = O.exact_knn(X, q, 10)
+        recalls.append(O.recall(res.ids, ids))
+        if (res.dist <= 1.5 ** 2 * dist * (1 + 1e-12)).all():
+            ok += 1
+    assert ok / 40 >= 0.5 - 1 / math.e
+    assert np.mean(recalls) >= 0.9
+
+
+# ------------------------------------------------------------------ Sec. 6.1 measures
+def test_recall_and_ratio_hand():
+    assert O.recall(np.array([1, 2, 3, -1]), np.array([3, 2, 9, 8])) == 0.5
+    assert O.overall_ratio(np.array([2.0, 1.0]), np.array([1.0, 2.0])) == 1.0
+    assert abs(O.overall_ratio(np.array([1.0, 3.0]), np.array([1.0, 2.0])) - 1.25) < 1e-15
