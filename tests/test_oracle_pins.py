@@ -154,7 +154,7 @@ def test_encode_monotone():
 
 
 # ------------------------------------------------------------------ Alg. 3 DE-Tree
-@pytest.mark.parametrize("fixture", ["split_example.json", "split_rule_hand.json"])
+@pytest.mark.parametrize("fixture", ["split_example.json", "split_rule_hand.json", "split_tie_hand.json"])
 def test_split_examples(fixture):
     g = _load(fixture)
     tree = O.build_tree(np.array(g["codes"], dtype=np.uint8), g["n_regions"], g["max_size"])
