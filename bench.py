@@ -1,0 +1,376 @@
+"""Benchmark of the DET-LSH hot path on GB300: one step = build the index over
+n points already resident in HBM (projection, breakpoints, encoding, DE-Tree
+leaves) and answer a batch of c^2-k-ANN queries (Alg. 7) against it.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0). With N > 1 (torchrun) every rank runs an
+independent replica on its own GPU with its own query batch (weak scaling);
+the value is the queries of all ranks over the slowest rank's time.
+"""
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "index Mpts/s; QPS@recall≥0.9 vs plain FP32 GPU; p99 latency; % HBM peak"
+WORKLOAD = dict(name="mid", n=1_000_000, d=128, nq=10_000, K=16, L=4, n_regions=256, n_s=10_000,
+                max_leaf=256, c=1.5, k=50, beta=0.1)
+def workload_desc():
+    return ("mid: n=1,000,000 d=128 fp32 integer 0-255 Gaussian mixture of 1,000 clusters, "
+            f"{WORKLOAD['nq']:,} queries from the same mixture; K=16 L=4 N_r=256 n_s=1% c=1.5 k=50 "
+            "beta=0.1 max_leaf=256")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _src_sha1(relpath):
+    with open(os.path.join(ROOT, relpath), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def _ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel's source is unchanged since that capture; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_mid.md")
+    try:
+        for line in open(path):
+            if line.startswith("traffic_bytes_per_launch:"):
+                _, val, src, sha = line.split()
+                if _src_sha1(src) == sha:
+                    return float(val)
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+# ------------------------------------------------------------------ CPU oracle
+CPU_SCRIPT = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from workloads import make_workload, gaussian_projection, sample_ids
+from oracle import detlsh_oracle as O
+w = {w!r}
+nqs = {nqs}
+X, Q = make_workload(w["name"], n=w["n"], nq=nqs, seed_query=2)
+A = gaussian_projection(w["L"], w["K"], w["d"]).numpy()
+ids = sample_ids(w["n"], w["n_s"]).numpy()
+Xn, Qn = X.numpy(), Q.numpy()
+t0 = time.perf_counter()
+idx = O.build_index(Xn, A, ids, w["K"], w["L"], w["n_regions"], w["max_leaf"])
+tb = time.perf_counter() - t0
+eps = O.eps_from_lemma3(w["K"], w["L"])
+tq = []
+for i in range(nqs):
+    t0 = time.perf_counter()
+    O.c2k_ann(idx, Qn[i], w["k"], w["c"], 0.0, eps, w["beta"])
+    tq.append(time.perf_counter() - t0)
+print(json.dumps({{"build_s": tb, "query_s": tq}}))
+"""
+
+
+def run_cpu_oracle(nqs):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = CPU_SCRIPT.format(root=ROOT, w=WORKLOAD, nqs=nqs)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_obj(res, nq):
+    tq = statistics.mean(res["query_s"])
+    step_s = res["build_s"] + nq * tq
+    return {"value": nq / step_s, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 oracle, 1 thread: full {WORKLOAD['n']:,}-point index build "
+                       f"({res['build_s']:.1f} s) + {len(res['query_s'])} of the {nq:,} queries "
+                       f"({tq:.3f} s each); step time = build + {nq:,} x mean query")}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    nq = WORKLOAD["nq"]
+    n_steps = args.warmup + args.steps
+    res = run_cpu_oracle(max(n_steps, 2))
+    tq = res["query_s"][args.warmup:] or res["query_s"]
+    step_s = res["build_s"] + nq * statistics.mean(tq)
+    value = nq / step_s
+    cb = cpu_baseline_obj({"build_s": res["build_s"], "query_s": tq}, nq)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1000.0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_desc(), **WORKLOAD},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def gpu_arm(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2406_10938_gb300 as pkg
+    from workloads import gaussian_projection, make_workload, sample_ids
+
+    pkg.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = WORKLOAD
+    X, Q = make_workload(w["name"], n=w["n"], nq=w["nq"], seed_query=2 + rank, device=dev)
+    A = gaussian_projection(w["L"], w["K"], w["d"], device=dev)
+    ids = sample_ids(w["n"], w["n_s"], device=dev)
+    nq = w["nq"]
+    kk = torch.full((nq,), w["k"], dtype=torch.int32, device=dev)
+    cc = torch.full((nq,), w["c"], dtype=torch.float32, device=dev)
+    rr = torch.zeros(nq, dtype=torch.float32, device=dev)
+    eps = pkg.detlsh_eps_lemma3(w["K"], w["L"])
+    out = (torch.empty(nq, w["k"], dtype=torch.int64, device=dev),
+           torch.empty(nq, w["k"], dtype=torch.float32, device=dev),
+           torch.empty(nq, 4, dtype=torch.int32, device=dev))
+
+    def step():
+        idx = pkg.detlsh_build(X, A, ids, w["K"], w["L"], w["n_regions"], w["max_leaf"], borrow=True)
+        pkg.detlsh_query(idx, Q, kk, cc, rr, k_max=w["k"], eps=eps, beta=w["beta"], out=out)
+        tr = pkg.detlsh_trace_get()
+        info = idx.info()
+        idx.free()
+        return tr, info
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    pkg.detlsh_trace_enable(True)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = pkg.detlsh_launch_count()
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    traces = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        tr, info = step()
+        traces.append(tr)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = pkg.detlsh_launch_count() - launches0
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / args.steps
+    value = world * nq / (ms_per_step / 1000.0)
+
+    # phases (mean over timed steps)
+    ph = {k: statistics.mean(tr[k] for tr in traces) for k in traces[0]}
+    stats = out[2].cpu().numpy()
+    mean_S = float(stats[:, 0].astype("float64").mean())
+    s_in = 4
+    total_leaves = info["total_leaves"]
+    search_bytes = float(stats[:, 0].astype("float64").sum()) * (w["d"] * s_in + 4) + nq * total_leaves * 4.0
+    enc_bytes = w["n"] * (w["d"] * s_in + w["K"] * w["L"])
+    cand = {
+        "k_search": (search_bytes, ph["search_ms"], ph["search_launches"]),
+        "k_project_encode": (enc_bytes, ph["encode_ms"], 1.0),
+        "k_leaf_lb": (nq * total_leaves * 4.0 + ph["lb_launches"] * total_leaves * (2 * w["K"] + 10.0),
+                      ph["lb_ms"], ph["lb_launches"]),
+    }
+    dom = max(cand, key=lambda k_: cand[k_][1])
+    b, ms, launches_dom = cand[dom]
+    peak, peak_kind = _peaks()
+    achieved = (b / launches_dom) / ((ms / launches_dom) / 1000.0) / 1e9
+    traffic = _ncu_traffic(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "traffic": traffic, "algorithmic_bytes_per_launch": b / launches_dom,
+                "launches_per_step": launches_dom, "avg_launch_ms": ms / launches_dom}
+
+    # recall@k on 200 queries against a brute-force scan (evaluation only, untimed)
+    nqr = min(200, nq)
+    ids_out = out[0][:nqr]
+    hits = 0
+    for qi in range(nqr):
+        d2 = ((X - Q[qi]) ** 2).sum(dim=1)
+        exact = torch.topk(d2, w["k"], largest=False).indices
+        hits += len(set(exact.tolist()) & set(ids_out[qi].tolist()))
+    recall = hits / (nqr * w["k"])
+
+    # end to end through the public API with host buffers
+    e2e_steps = max(1, min(args.steps, 3))
+    Xh = X.cpu().pin_memory()
+    Qh = Q.cpu().pin_memory()
+    Ah, idh = A.cpu().pin_memory(), ids.cpu().pin_memory()
+    kh, ch, rh = kk.cpu(), cc.cpu(), rr.cpu()
+    outh = (torch.empty(nq, w["k"], dtype=torch.int64).pin_memory(),
+            torch.empty(nq, w["k"], dtype=torch.float32).pin_memory(),
+            torch.empty(nq, 4, dtype=torch.int32).pin_memory())
+    pkg.detlsh_trace_enable(False)
+
+    def step_host():
+        idx = pkg.detlsh_build(Xh, Ah, idh, w["K"], w["L"], w["n_regions"], w["max_leaf"])
+        pkg.detlsh_query(idx, Qh, kh, ch, rh, k_max=w["k"], eps=eps, beta=w["beta"], out=outh)
+        idx.free()
+
+    step_host()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_host()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te.item())
+    h2d = X.numel() * 4 + Q.numel() * 4 + A.numel() * 4 + ids.numel() * 8 + nq * 12
+    d2h = nq * w["k"] * 12 + nq * 16
+
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu_base = cpu_baseline_obj(run_cpu_oracle(args.cpu_queries), nq)
+        except Exception as e:  # reported, not fatal
+            cpu_base = {"value": None, "error": str(e)[-300:]}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": workload_desc(), **w, "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (X is 512 MB)"},
+                "clocks": clk,
+                "e2e": {"value": world * nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": int(launches),
+                "roofline": roofline,
+                "cpu_baseline": cpu_base,
+                "build_mpts_per_s": w["n"] / (ph["build_ms"] / 1000.0) / 1e6,
+                "query_qps": nq / (ph["query_ms"] / 1000.0),
+                "recall_at_k": recall,
+                "mean_candidates": mean_S,
+                "phase_ms": {k_: round(v, 4) for k_, v in ph.items()}}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-queries", type=int, default=8)
+    ap.add_argument("--nq", type=int, default=WORKLOAD["nq"], help="queries per step (default: the workload's)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    WORKLOAD["nq"] = args.nq
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        return gpu_arm(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,224 @@
+/*
+ * detlsh.h -- C ABI of a GB300 (sm_103a) implementation of DET-LSH
+ * (Wei et al., "DET-LSH: A Locality-Sensitive Hashing Scheme with Dynamic
+ * Encoding Tree for Approximate Nearest Neighbor Search", PVLDB 17(9), 2024).
+ *
+ * Every entry point returns 0 (DETLSH_OK) or a negative detlsh_status; on
+ * error detlsh_last_error() describes the cause (thread-local string).
+ * Pointers are plain host or device addresses, chosen per call by a `mem`
+ * argument (DETLSH_MEM_HOST or DETLSH_MEM_DEVICE) that applies to every data
+ * pointer of that call. The caller owns every buffer it passes; the library
+ * owns the index it returns. `stream` is a cudaStream_t (NULL: the legacy
+ * default stream); device work of a call is ordered on that stream and, with
+ * host pointers, the call returns after its results reached host memory.
+ * All computation of build and query runs in this library's CUDA kernels;
+ * there is no CPU fallback: without a usable GPU every call returns
+ * DETLSH_ECUDA.
+ *
+ * Limits: 1 <= K <= 16, 1 <= L <= 16, n_regions a power of two in [2, 256],
+ * n_regions <= n_s <= n, 1 <= d <= 65536, n*L < 2^32, 1 <= k <= 1024.
+ * Input values must be finite.
+ */
+#ifndef DETLSH_H_
+#define DETLSH_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DETLSH_OK = 0,
+  DETLSH_EINVAL = -1,    /* an argument is out of range or inconsistent   */
+  DETLSH_ENOMEM = -2,    /* device or host allocation failed              */
+  DETLSH_ECUDA = -3,     /* a CUDA call failed (no device, launch error)  */
+  DETLSH_ETIMEOUT = -4,  /* a bounded device wait ran out                 */
+  DETLSH_EADMIT = -5,    /* request refused by memory-based admission     */
+  DETLSH_EINTERNAL = -6  /* an internal consistency check failed          */
+} detlsh_status;
+
+typedef enum { DETLSH_F32 = 0, DETLSH_U8 = 1 } detlsh_dtype;
+typedef enum { DETLSH_MEM_HOST = 0, DETLSH_MEM_DEVICE = 1 } detlsh_mem;
+
+/* projection arithmetic of the build (Eq. 1 for every point) */
+typedef enum {
+  DETLSH_PROJ_FP32 = 0   /* FP32 fused multiply-add on the CUDA cores */
+} detlsh_proj_mode;
+
+/* detlsh_params.flags */
+#define DETLSH_BORROW_X 1  /* with DETLSH_MEM_DEVICE: keep a reference to the
+                              caller's X instead of copying it; X must then
+                              stay alive and unchanged until detlsh_free */
+
+typedef struct detlsh_index detlsh_index;
+
+/* Index parameters (Alg. 1-3 inputs; Sec. 5.2 and Sec. 6.1 give the paper's
+ * defaults K=16, L=4, N_r=256, n_s=0.1n; max_size is not given there). */
+typedef struct {
+  int32_t K;          /* hash functions per projected space                */
+  int32_t L;          /* projected spaces = DE-Trees                       */
+  int32_t n_regions;  /* N_r: regions per projected dimension              */
+  int32_t max_leaf;   /* max_size of Alg. 3 (>= 1)                         */
+  int64_t n_s;        /* sample size: number of entries in sample_ids      */
+  int32_t proj_mode;  /* detlsh_proj_mode                                  */
+  int32_t flags;      /* DETLSH_BORROW_X or 0                              */
+} detlsh_params;
+
+/* Query parameters shared by a batch (Alg. 7 inputs besides q, k, c, r_min). */
+typedef struct {
+  double eps;         /* projected-radius factor of Lemma 3 (Eq. 2); <= 0 selects
+                         detlsh_eps_lemma3(K, L)                            */
+  double beta;        /* false-positive fraction: a query stops once its
+                         candidate set holds ceil(beta*n + k) points (>= 0)  */
+  uint32_t* cand_ids; /* optional [nq][cand_cap]: the candidate set S of each
+                         query (unordered ids; the first |S| entries), in
+                         the call's `mem` space; NULL to skip               */
+  int64_t cand_cap;   /* capacity per query of cand_ids                      */
+} detlsh_query_params;
+
+/*
+ * detlsh_build -- encoding and indexing phases (Sec. 4.1-4.2: Eq. 1, Alg. 1,
+ * Alg. 2, Alg. 3).
+ *
+ *   X           [n][d] row-major points, dtype DETLSH_F32 or DETLSH_U8 (uint8
+ *               values are widened to FP32 inside the kernels).
+ *   A           [L*K][d] row-major FP32 hash vectors of Eq. 1 (entries drawn
+ *               from N(0,1) by the caller); row r = i*K + j is a_ij, the j-th
+ *               hash of projected space i.
+ *   sample_ids  [n_s] distinct point ids in [0, n) whose projections select the
+ *               breakpoints (Alg. 1: the sample of the n points).
+ *   params      see detlsh_params.
+ *   out         receives the new index (free it with detlsh_free).
+ *
+ * The index holds: A; per projected dimension N_r+1 breakpoints (minimum,
+ * N_r-1 interior edges at sample ranks floor(n_s/N_r)*z, maximum); the 8-bit
+ * region code of every point in every projected dimension; and L DE-Trees as
+ * leaf tables (root split on the top code bit of all K dimensions, then
+ * binary splits of the most evenly dividing dimension while a node holds more
+ * than max_leaf points). It keeps a device copy of X (or the caller's X with
+ * DETLSH_BORROW_X). The index is read-only afterwards; concurrent queries on
+ * different streams are safe.
+ * Errors: DETLSH_EINVAL for sizes or parameters outside the limits above,
+ * DETLSH_ENOMEM, DETLSH_ECUDA.
+ */
+int detlsh_build(const void* X, int64_t n, int32_t d, int32_t dtype,
+                 const float* A, const int64_t* sample_ids,
+                 const detlsh_params* params, int32_t mem, void* stream,
+                 detlsh_index** out);
+
+/*
+ * detlsh_query -- batched c^2-k-ANN queries (Alg. 7 with the optimised range
+ * query of Sec. 6.2.2: a leaf whose lower-bound distance to q' is within the
+ * projected radius eps*r joins the candidate set whole, leaves in order of
+ * their lower bound; r grows r_min, c*r_min, c^2*r_min, ...).
+ *
+ *   Q           [nq][d] row-major queries, dtype as the index's X.
+ *   k, c, r_min [nq] per query: result size (1 <= k <= k_max), approximation
+ *               ratio (> 1), initial radius (<= 0 selects the square root of
+ *               the smallest positive leaf lower bound divided by eps).
+ *   k_max       row length of the outputs (1..1024).
+ *   qp          see detlsh_query_params (NULL: eps from Lemma 3, beta = 0.1).
+ *   out_ids     [nq][k_max] int64 ids of the k nearest candidates by
+ *               (distance, id); -1 after the k-th or when |S| < k.
+ *   out_dist    [nq][k_max] FP32 Euclidean distances (+inf padding).
+ *   out_stats   optional [nq][4] int32: |S| at termination, rounds started,
+ *               stop rule (1: |S| >= beta*n+k, 2: >= k candidates within c*r,
+ *               3: every leaf active), reserved 0.
+ * Errors: DETLSH_EINVAL (bad sizes/parameters, dtype differs from the index),
+ * DETLSH_ENOMEM, DETLSH_ECUDA.
+ */
+int detlsh_query(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dtype,
+                 const int32_t* k, const float* c, const float* r_min, int32_t k_max,
+                 const detlsh_query_params* qp, int64_t* out_ids, float* out_dist,
+                 int32_t* out_stats, int32_t mem, void* stream);
+
+/* detlsh_free -- release an index and all its device memory (NULL is a no-op). */
+void detlsh_free(detlsh_index* idx);
+
+/* What detlsh_export copies out (test introspection and persistence). */
+typedef enum {
+  DETLSH_EXPORT_A = 0,            /* float   [L*K][d]                          */
+  DETLSH_EXPORT_EDGES = 1,        /* float   [L*K][N_r+1] breakpoints (Alg. 1) */
+  DETLSH_EXPORT_CODES = 2,        /* uint8   [L][n][K] region codes (Alg. 2)   */
+  DETLSH_EXPORT_LEAF_IDS = 3,     /* uint32  [L][n] point ids in leaf order     */
+  DETLSH_EXPORT_LEAF_BASE = 4,    /* int64   [L+1] first leaf of each tree      */
+  DETLSH_EXPORT_LEAF_RANGE = 5,   /* uint32  [n_leaves][2] start (within the
+                                     tree's part of LEAF_IDS), count           */
+  DETLSH_EXPORT_LEAF_PLEN = 6,    /* uint8   [n_leaves][K] prefix bits per dim  */
+  DETLSH_EXPORT_LEAF_PREFIX = 7,  /* uint8   [n_leaves][K] prefix value per dim */
+  DETLSH_EXPORT_SAMPLE_PROJ = 8   /* float   [L*K][n_s] projections of the
+                                     sampled points                            */
+} detlsh_export_what;
+
+/* detlsh_export_size -- bytes detlsh_export needs for `what` (< 0 on error). */
+int64_t detlsh_export_size(const detlsh_index* idx, int32_t what);
+
+/* detlsh_export -- copy one index array into dst (`bytes` >= export size). */
+int detlsh_export(const detlsh_index* idx, int32_t what, void* dst, int64_t bytes,
+                  int32_t mem, void* stream);
+
+/* detlsh_info -- index sizes: out[0..9] = n, d, dtype, K, L, n_regions,
+ * max_leaf, n_s, total leaves, largest leaf. Returns the entries written. */
+int detlsh_info(const detlsh_index* idx, int64_t* out, int32_t len);
+
+/*
+ * detlsh_project -- Eq. 1 for a batch of points: P[o][r] = sum_t A[r][t] X[o][t]
+ * in FP32, X [n][d] (dtype), A [LK][d], P [n][LK] FP32. Same kernel as the
+ * build's projection of the sample.
+ */
+int detlsh_project(const void* X, int64_t n, int32_t d, int32_t dtype,
+                   const float* A, int32_t LK, float* P, int32_t mem, void* stream);
+
+/*
+ * detlsh_encode_values -- Alg. 2 on given projected values: codes[o][r] =
+ * number of interior breakpoints E[r][z] (z = 1..N_r-1) with E[r][z] <= P[o][r]
+ * (regions half-open [e_z, e_{z+1}), values below the first edge -> 0, at or
+ * above the last -> N_r-1). P [n][LK] FP32, E [LK][N_r+1] FP32 sorted rows,
+ * codes [n][LK] uint8. Same search routine as the build's fused kernel.
+ */
+int detlsh_encode_values(const float* P, int64_t n, int32_t LK, const float* E,
+                         int32_t n_regions, uint8_t* codes, int32_t mem, void* stream);
+
+/*
+ * detlsh_select_breakpoints -- Alg. 1 (closed form of Sec. 4.1) on given sample
+ * projections: for each row r of Ps [LK][n_s] (FP32), E[r][0] = minimum,
+ * E[r][z] = the element of 0-based rank floor(n_s/N_r)*z (z = 1..N_r-1),
+ * E[r][N_r] = maximum; E is [LK][N_r+1] FP32. Same kernels as the build.
+ */
+int detlsh_select_breakpoints(const float* Ps, int64_t n_s, int32_t LK, int32_t n_regions,
+                              float* E, int32_t mem, void* stream);
+
+/* detlsh_eps_lemma3 -- eps of Lemma 3 (Eq. 2): eps^2 is the upper
+ * alpha1-quantile of chi2(K), alpha1 = exp(-1/L). Returns < 0 on bad input. */
+double detlsh_eps_lemma3(int32_t K, int32_t L);
+
+/*
+ * Tracing (no counterpart in the paper; its Fig. 4 reports a per-phase time
+ * breakdown of the build, which this makes measurable on the GPU).
+ * detlsh_trace_enable -- on != 0: every later build/query on the calling thread
+ *   records CUDA events around its phases on its stream and synchronizes that
+ *   stream before returning. Returns the previous setting.
+ * detlsh_trace_get -- device milliseconds of the last build and the last query
+ *   on this thread: out[0] sample projection, [1] breakpoint selection,
+ *   [2] fused projection+encoding, [3] DE-Tree leaves, [4] query projection,
+ *   [5] leaf lower bounds, [6] search kernels, [7] number of search launches,
+ *   [8] number of lower-bound launches, [9] whole build, [10] whole query.
+ *   Returns the number of entries written (<= len).
+ * detlsh_launch_count -- kernels this library has launched in the process.
+ */
+int detlsh_trace_enable(int32_t on);
+int detlsh_trace_get(double* out, int32_t len);
+int64_t detlsh_launch_count(void);
+
+/* detlsh_strerror -- static text for a detlsh_status value. */
+const char* detlsh_strerror(int status);
+
+/* detlsh_last_error -- detail of the last error on the calling thread. */
+const char* detlsh_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DETLSH_H_ */

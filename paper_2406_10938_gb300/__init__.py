@@ -1,0 +1,23 @@
+"""GB300 (sm_103a) implementation of DET-LSH's encode/index/query hot path.
+
+The computation lives in ``libdetlsh.so`` (CUDA kernels behind the C ABI of
+``include/detlsh.h``); ``binding`` exposes the same entry points to Python.
+"""
+
+from .binding import (  # noqa: F401
+    DetlshError,
+    Index,
+    detlsh_build,
+    detlsh_encode_values,
+    detlsh_eps_lemma3,
+    detlsh_export,
+    detlsh_info,
+    detlsh_launch_count,
+    detlsh_project,
+    detlsh_query,
+    detlsh_select_breakpoints,
+    detlsh_trace_enable,
+    detlsh_trace_get,
+    lib,
+)
+from .build_lib import LIB, build  # noqa: F401

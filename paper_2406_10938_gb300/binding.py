@@ -1,0 +1,273 @@
+"""ctypes binding of libdetlsh (include/detlsh.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: torch tensors supply pointers (all CPU -> host memory,
+all CUDA -> device memory on torch's current stream) and receive the outputs.
+If the library has not been built, loading it raises; there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+from .build_lib import LIB
+
+F32, U8 = 0, 1
+MEM_HOST, MEM_DEVICE = 0, 1
+BORROW_X = 1
+EXPORT = {"A": 0, "EDGES": 1, "CODES": 2, "LEAF_IDS": 3, "LEAF_BASE": 4, "LEAF_RANGE": 5,
+          "LEAF_PLEN": 6, "LEAF_PREFIX": 7, "SAMPLE_PROJ": 8}
+_EXPORT_DTYPE = {"A": torch.float32, "EDGES": torch.float32, "CODES": torch.uint8,
+                 "LEAF_IDS": torch.int32, "LEAF_BASE": torch.int64, "LEAF_RANGE": torch.int32,
+                 "LEAF_PLEN": torch.uint8, "LEAF_PREFIX": torch.uint8, "SAMPLE_PROJ": torch.float32}
+
+# every symbol declared in include/detlsh.h
+SYMBOLS = ("detlsh_build", "detlsh_query", "detlsh_free", "detlsh_export_size", "detlsh_export",
+           "detlsh_info", "detlsh_project", "detlsh_encode_values", "detlsh_select_breakpoints",
+           "detlsh_eps_lemma3", "detlsh_strerror", "detlsh_last_error", "detlsh_trace_enable",
+           "detlsh_trace_get", "detlsh_launch_count")
+TRACE_KEYS = ("sample_proj_ms", "breakpoints_ms", "encode_ms", "leaves_ms", "query_proj_ms", "lb_ms",
+              "search_ms", "search_launches", "lb_launches", "build_ms", "query_ms")
+
+
+class DetlshError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status}: {detail}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("L", ctypes.c_int32), ("n_regions", ctypes.c_int32),
+                ("max_leaf", ctypes.c_int32), ("n_s", ctypes.c_int64), ("proj_mode", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+class QueryParams(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("beta", ctypes.c_double),
+                ("cand_ids", ctypes.c_void_p), ("cand_cap", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib(path: Optional[str] = None):
+    """Load libdetlsh.so (raises if it is missing)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(p)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.detlsh_build.argtypes = [vp, i64, i32, i32, vp, vp, ctypes.POINTER(Params), i32, vp,
+                               ctypes.POINTER(vp)]
+    L.detlsh_build.restype = ctypes.c_int
+    L.detlsh_query.argtypes = [vp, vp, i64, i32, vp, vp, vp, i32, ctypes.POINTER(QueryParams), vp,
+                               vp, vp, i32, vp]
+    L.detlsh_query.restype = ctypes.c_int
+    L.detlsh_free.argtypes = [vp]
+    L.detlsh_free.restype = None
+    L.detlsh_export_size.argtypes = [vp, i32]
+    L.detlsh_export_size.restype = i64
+    L.detlsh_export.argtypes = [vp, i32, vp, i64, i32, vp]
+    L.detlsh_export.restype = ctypes.c_int
+    L.detlsh_info.argtypes = [vp, ctypes.POINTER(i64), i32]
+    L.detlsh_info.restype = ctypes.c_int
+    L.detlsh_project.argtypes = [vp, i64, i32, i32, vp, i32, vp, i32, vp]
+    L.detlsh_project.restype = ctypes.c_int
+    L.detlsh_encode_values.argtypes = [vp, i64, i32, vp, i32, vp, i32, vp]
+    L.detlsh_encode_values.restype = ctypes.c_int
+    L.detlsh_select_breakpoints.argtypes = [vp, i64, i32, i32, vp, i32, vp]
+    L.detlsh_select_breakpoints.restype = ctypes.c_int
+    L.detlsh_eps_lemma3.argtypes = [i32, i32]
+    L.detlsh_eps_lemma3.restype = dbl
+    L.detlsh_strerror.argtypes = [ctypes.c_int]
+    L.detlsh_strerror.restype = ctypes.c_char_p
+    L.detlsh_last_error.argtypes = []
+    L.detlsh_last_error.restype = ctypes.c_char_p
+    L.detlsh_trace_enable.argtypes = [i32]
+    L.detlsh_trace_enable.restype = ctypes.c_int
+    L.detlsh_trace_get.argtypes = [ctypes.POINTER(dbl), i32]
+    L.detlsh_trace_get.restype = ctypes.c_int
+    L.detlsh_launch_count.argtypes = []
+    L.detlsh_launch_count.restype = i64
+    if path is None:
+        _lib = L
+    return L
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        L = lib()
+        raise DetlshError(st, where, f"{L.detlsh_strerror(st).decode()} -- {L.detlsh_last_error().decode()}")
+
+
+def _mem_of(*ts):
+    devs = {t.device.type for t in ts if t is not None}
+    if len(devs) != 1:
+        raise ValueError("all tensors of one call must be on the CPU or all on the GPU")
+    return MEM_DEVICE if devs.pop() == "cuda" else MEM_HOST
+
+
+def _stream(mem):
+    if mem == MEM_DEVICE:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _dtype_code(t):
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.uint8:
+        return U8
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+class Index:
+    """Owner of a detlsh_index*; freed by ``free()`` or on garbage collection."""
+
+    def __init__(self, handle: int, keep=None):
+        self.handle = ctypes.c_void_p(handle)
+        self._keep = keep      # a borrowed X must outlive the index
+
+    def free(self):
+        if self.handle:
+            lib().detlsh_free(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self):
+        return detlsh_info(self)
+
+
+def detlsh_build(X: torch.Tensor, A: torch.Tensor, sample_ids: torch.Tensor, K: int, L: int,
+                 n_regions: int, max_leaf: int, borrow: bool = False) -> Index:
+    X = X.contiguous()
+    A = A.contiguous().to(torch.float32)
+    sample_ids = sample_ids.contiguous().to(torch.int64)
+    mem = _mem_of(X, A, sample_ids)
+    p = Params(K=K, L=L, n_regions=n_regions, max_leaf=max_leaf, n_s=sample_ids.numel(), proj_mode=0,
+               flags=BORROW_X if (borrow and mem == MEM_DEVICE) else 0)
+    out = ctypes.c_void_p(0)
+    st = lib().detlsh_build(_ptr(X), X.shape[0], X.shape[1], _dtype_code(X), _ptr(A), _ptr(sample_ids),
+                            ctypes.byref(p), mem, _stream(mem), ctypes.byref(out))
+    _check(st, "detlsh_build")
+    return Index(out.value, keep=X if p.flags else None)
+
+
+def detlsh_query(index: Index, Q: torch.Tensor, k, c, r_min=None, k_max: Optional[int] = None,
+                 eps: float = 0.0, beta: float = 0.1, cand_cap: int = 0,
+                 out=None):
+    """Returns (ids int64 [nq,k_max], dist fp32 [nq,k_max], stats int32 [nq,4], cand or None).
+
+    ``k``, ``c``, ``r_min`` are per-query tensors (or scalars, broadcast).
+    ``out`` optionally supplies preallocated (ids, dist, stats) tensors.
+    """
+    Q = Q.contiguous()
+    nq = Q.shape[0]
+    dev = Q.device
+    k = torch.as_tensor(k, dtype=torch.int32, device=dev).expand(nq).contiguous() if not torch.is_tensor(k) or k.dim() == 0 else k.to(dev, torch.int32).contiguous()
+    c = torch.as_tensor(c, dtype=torch.float32, device=dev).expand(nq).contiguous() if not torch.is_tensor(c) or c.dim() == 0 else c.to(dev, torch.float32).contiguous()
+    if r_min is None:
+        r_min = 0.0
+    r_min = torch.as_tensor(r_min, dtype=torch.float32, device=dev).expand(nq).contiguous() if not torch.is_tensor(r_min) or r_min.dim() == 0 else r_min.to(dev, torch.float32).contiguous()
+    if k_max is None:
+        k_max = int(k.max().item()) if nq else 1
+    mem = _mem_of(Q, k, c, r_min)
+    if out is None:
+        ids = torch.empty(nq, k_max, dtype=torch.int64, device=dev)
+        dist = torch.empty(nq, k_max, dtype=torch.float32, device=dev)
+        stats = torch.empty(nq, 4, dtype=torch.int32, device=dev)
+    else:
+        ids, dist, stats = out
+    cand = torch.empty(nq, cand_cap, dtype=torch.int32, device=dev) if cand_cap > 0 else None
+    qp = QueryParams(eps=eps, beta=beta, cand_ids=cand.data_ptr() if cand is not None else None,
+                     cand_cap=cand_cap)
+    st = lib().detlsh_query(index.handle, _ptr(Q), nq, _dtype_code(Q), _ptr(k), _ptr(c), _ptr(r_min),
+                            k_max, ctypes.byref(qp), _ptr(ids), _ptr(dist), _ptr(stats), mem, _stream(mem))
+    _check(st, "detlsh_query")
+    return ids, dist, stats, cand
+
+
+def detlsh_export(index: Index, what: str, device="cpu") -> torch.Tensor:
+    L = lib()
+    code = EXPORT[what]
+    nbytes = L.detlsh_export_size(index.handle, code)
+    if nbytes < 0:
+        _check(int(nbytes), "detlsh_export_size")
+    dt = _EXPORT_DTYPE[what]
+    out = torch.empty(nbytes // torch.empty(0, dtype=dt).element_size(), dtype=dt, device=device)
+    mem = _mem_of(out)
+    _check(L.detlsh_export(index.handle, code, _ptr(out), nbytes, mem, _stream(mem)), "detlsh_export")
+    return out
+
+
+def detlsh_info(index: Index) -> dict:
+    buf = (ctypes.c_int64 * 10)()
+    m = lib().detlsh_info(index.handle, buf, 10)
+    if m < 0:
+        _check(m, "detlsh_info")
+    keys = ("n", "d", "dtype", "K", "L", "n_regions", "max_leaf", "n_s", "total_leaves", "largest_leaf")
+    return {k: int(buf[i]) for i, k in enumerate(keys[:m])}
+
+
+def detlsh_project(X: torch.Tensor, A: torch.Tensor) -> torch.Tensor:
+    X = X.contiguous()
+    A = A.contiguous().to(torch.float32)
+    mem = _mem_of(X, A)
+    P = torch.empty(X.shape[0], A.shape[0], dtype=torch.float32, device=X.device)
+    _check(lib().detlsh_project(_ptr(X), X.shape[0], X.shape[1], _dtype_code(X), _ptr(A), A.shape[0],
+                                _ptr(P), mem, _stream(mem)), "detlsh_project")
+    return P
+
+
+def detlsh_encode_values(P: torch.Tensor, E: torch.Tensor, n_regions: int) -> torch.Tensor:
+    P = P.contiguous().to(torch.float32)
+    E = E.contiguous().to(torch.float32)
+    mem = _mem_of(P, E)
+    codes = torch.empty(P.shape, dtype=torch.uint8, device=P.device)
+    _check(lib().detlsh_encode_values(_ptr(P), P.shape[0], P.shape[1], _ptr(E), n_regions, _ptr(codes),
+                                      mem, _stream(mem)), "detlsh_encode_values")
+    return codes
+
+
+def detlsh_select_breakpoints(Ps: torch.Tensor, n_regions: int) -> torch.Tensor:
+    """Ps [LK, n_s] -> E [LK, n_regions+1]."""
+    Ps = Ps.contiguous().to(torch.float32)
+    mem = _mem_of(Ps)
+    E = torch.empty(Ps.shape[0], n_regions + 1, dtype=torch.float32, device=Ps.device)
+    _check(lib().detlsh_select_breakpoints(_ptr(Ps), Ps.shape[1], Ps.shape[0], n_regions, _ptr(E), mem,
+                                           _stream(mem)), "detlsh_select_breakpoints")
+    return E
+
+
+def detlsh_eps_lemma3(K: int, L: int) -> float:
+    return float(lib().detlsh_eps_lemma3(K, L))
+
+
+def detlsh_trace_enable(on: bool) -> bool:
+    return bool(lib().detlsh_trace_enable(1 if on else 0))
+
+
+def detlsh_trace_get() -> dict:
+    buf = (ctypes.c_double * len(TRACE_KEYS))()
+    m = lib().detlsh_trace_get(buf, len(TRACE_KEYS))
+    return {k: float(buf[i]) for i, k in enumerate(TRACE_KEYS[:m])}
+
+
+def detlsh_launch_count() -> int:
+    return int(lib().detlsh_launch_count())

@@ -1,0 +1,499 @@
+// C ABI of libdetlsh: argument checks, host/device staging and index lifetime.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace detlsh {
+
+static thread_local char g_err[512] = "";
+static thread_local bool g_trace_on = false;
+static thread_local double g_trace[TR_COUNT] = {0};
+static unsigned long long g_launches = 0;
+
+void count_launch() { __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED); }
+bool trace_on() { return g_trace_on; }
+void trace_reset(int first, int last) {
+  for (int i = first; i <= last; ++i) g_trace[i] = 0.0;
+}
+void trace_add(int phase, double v) { g_trace[phase] += v; }
+
+PhaseTimer::PhaseTimer(cudaStream_t s) : s_(s), on_(g_trace_on) {}
+PhaseTimer::~PhaseTimer() {
+  for (int i = 0; i < n_; ++i) {
+    cudaEventDestroy(a_[i]);
+    cudaEventDestroy(b_[i]);
+  }
+}
+void PhaseTimer::begin(int phase) {
+  if (!on_ || n_ >= kMax) return;
+  cudaEventCreate(&a_[n_]);
+  cudaEventCreate(&b_[n_]);
+  phase_[n_] = phase;
+  cudaEventRecord(a_[n_], s_);
+  open_ = n_++;
+}
+void PhaseTimer::end() {
+  if (!on_ || open_ < 0) return;
+  cudaEventRecord(b_[open_], s_);
+  open_ = -1;
+}
+int PhaseTimer::finish() {
+  if (!on_) return DETLSH_OK;
+  DL_CUDA(cudaStreamSynchronize(s_));
+  for (int i = 0; i < n_; ++i) {
+    float ms = 0.f;
+    DL_CUDA(cudaEventElapsedTime(&ms, a_[i], b_[i]));
+    g_trace[phase_[i]] += ms;
+  }
+  return DETLSH_OK;
+}
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+namespace {
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int log2i(int v) {
+  int b = 0;
+  while ((1 << b) < v) ++b;
+  return b;
+}
+size_t dtype_size(int dtype) { return dtype == DETLSH_U8 ? 1 : 4; }
+
+// A device view of a caller buffer: the pointer itself for device memory,
+// otherwise a stream-ordered device copy.
+struct In {
+  const void* d = nullptr;
+  Scratch own;
+  int stage(const void* p, size_t bytes, int mem, cudaStream_t s) {
+    if (mem == DETLSH_MEM_DEVICE || p == nullptr || bytes == 0) {
+      d = p;
+      return DETLSH_OK;
+    }
+    DL_TRY(own.alloc(bytes, s));
+    DL_CUDA(cudaMemcpyAsync(own.p, p, bytes, cudaMemcpyHostToDevice, s));
+    d = own.p;
+    return DETLSH_OK;
+  }
+};
+
+// A device destination for a caller buffer, copied back for host memory.
+struct Out {
+  void* d = nullptr;
+  void* h = nullptr;
+  size_t bytes = 0;
+  Scratch own;
+  int stage(void* p, size_t b, int mem, cudaStream_t s) {
+    bytes = b;
+    if (mem == DETLSH_MEM_DEVICE || p == nullptr || b == 0) {
+      d = p;
+      return DETLSH_OK;
+    }
+    h = p;
+    DL_TRY(own.alloc(b, s));
+    d = own.p;
+    return DETLSH_OK;
+  }
+  int finish(cudaStream_t s) {
+    if (h) DL_CUDA(cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, s));
+    return DETLSH_OK;
+  }
+};
+
+__global__ void k_check_ids(const int64_t* ids, int64_t m, int64_t n, int* bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m && (ids[i] < 0 || ids[i] >= n)) atomicExch(bad, 1);
+}
+
+__global__ void k_check_query_args(const int32_t* k, const float* c, const float* r_min, int64_t nq,
+                                   int k_max, int* bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  const bool ok = k[i] >= 1 && k[i] <= k_max && isfinite(c[i]) && c[i] > 1.0f &&
+                  !isnan(r_min[i]) && isfinite(r_min[i]);
+  if (!ok) atomicExch(bad, 1);
+}
+
+int check_flag(int* d_bad, cudaStream_t s, const char* what) {
+  int h = 0;
+  DL_CUDA(cudaMemcpyAsync(&h, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DL_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    set_error("%s", what);
+    return DETLSH_EINVAL;
+  }
+  return DETLSH_OK;
+}
+
+void free_index(detlsh_index* idx) {
+  if (!idx) return;
+  if (idx->owns_x && idx->X) cudaFree(const_cast<void*>(idx->X));
+  void* arrays[] = {idx->A, idx->At, idx->E, idx->Ps, idx->codes, idx->leaf_ids, idx->leaf_base,
+                    idx->leaf_range, idx->leaf_plen, idx->leaf_prefix, idx->leaf_lo, idx->leaf_hi,
+                    idx->leaf_tree};
+  for (void* p : arrays)
+    if (p) cudaFree(p);
+  delete idx;
+}
+
+int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* A,
+               const int64_t* sample_ids, const detlsh_params* prm, int32_t mem,
+               cudaStream_t s, detlsh_index* idx) {
+  const int K = prm->K, L = prm->L, Nr = prm->n_regions;
+  const int LK = K * L;
+  idx->n = n;
+  idx->d = d;
+  idx->dtype = dtype;
+  idx->K = K;
+  idx->L = L;
+  idx->Nr = Nr;
+  idx->bits = log2i(Nr);
+  idx->max_leaf = prm->max_leaf;
+  idx->n_s = prm->n_s;
+  DL_CUDA(cudaGetDevice(&idx->device));
+
+  const size_t xbytes = (size_t)n * d * dtype_size(dtype);
+  if (mem == DETLSH_MEM_DEVICE && (prm->flags & DETLSH_BORROW_X)) {
+    idx->X = X;
+    idx->owns_x = false;
+  } else {
+    void* xd = nullptr;
+    DL_CUDA(cudaMalloc(&xd, xbytes));
+    idx->X = xd;
+    DL_CUDA(cudaMemcpyAsync(xd, X, xbytes,
+                            mem == DETLSH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            s));
+  }
+  DL_CUDA(cudaMalloc(&idx->A, sizeof(float) * LK * d));
+  DL_CUDA(cudaMemcpyAsync(idx->A, A, sizeof(float) * LK * d,
+                          mem == DETLSH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  DL_CUDA(cudaMalloc(&idx->At, sizeof(float) * LK * d));
+  DL_TRY(transpose_hashes(idx->A, LK, d, idx->At, s));
+
+  In ids;
+  DL_TRY(ids.stage(sample_ids, sizeof(int64_t) * prm->n_s, mem, s));
+  {
+    Scratch bad;
+    DL_TRY(bad.alloc(sizeof(int), s));
+    DL_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+    k_check_ids<<<ceil_div(prm->n_s, 256), 256, 0, s>>>(static_cast<const int64_t*>(ids.d), prm->n_s, n,
+                                                       bad.as<int>());
+    DL_LAUNCH();
+    DL_TRY(check_flag(bad.as<int>(), s, "sample_ids must lie in [0, n)"));
+  }
+  PhaseTimer tm(s);
+  // Alg. 1: projections of the sample, [LK][n_s]
+  DL_CUDA(cudaMalloc(&idx->Ps, sizeof(float) * LK * prm->n_s));
+  DL_CUDA(cudaMalloc(&idx->E, sizeof(float) * LK * (Nr + 1)));
+  DL_CUDA(cudaMalloc(&idx->codes, (size_t)n * LK));
+  DL_CUDA(cudaMalloc(&idx->leaf_ids, sizeof(uint32_t) * n * L));
+  tm.begin(TR_SAMPLE_PROJ);
+  DL_TRY(launch_project_t(idx->X, dtype, prm->n_s, d, static_cast<const int64_t*>(ids.d), idx->At, LK,
+                          idx->Ps, 1, prm->n_s, s));
+  tm.end();
+  tm.begin(TR_BREAKPOINTS);
+  DL_TRY(select_breakpoints(idx->Ps, prm->n_s, LK, Nr, idx->E, s));
+  tm.end();
+  // Alg. 2: codes of every point, fused with the projection
+  tm.begin(TR_ENCODE);
+  DL_TRY(launch_project_encode_t(idx->X, dtype, n, d, idx->At, K, L, idx->E, Nr, idx->codes, s));
+  tm.end();
+  // Alg. 3: leaves
+  tm.begin(TR_LEAVES);
+  DL_TRY(build_leaves(idx, s));
+  tm.end();
+  DL_TRY(tm.finish());
+  DL_CUDA(cudaStreamSynchronize(s));
+  return DETLSH_OK;
+}
+
+}  // namespace
+}  // namespace detlsh
+
+using namespace detlsh;
+
+extern "C" {
+
+const char* detlsh_strerror(int status) {
+  switch (status) {
+    case DETLSH_OK: return "success";
+    case DETLSH_EINVAL: return "invalid argument";
+    case DETLSH_ENOMEM: return "out of memory";
+    case DETLSH_ECUDA: return "CUDA error";
+    case DETLSH_ETIMEOUT: return "device wait timed out";
+    case DETLSH_EADMIT: return "request not admitted";
+    case DETLSH_EINTERNAL: return "internal error";
+    default: return "unknown status";
+  }
+}
+
+const char* detlsh_last_error(void) { return g_err; }
+
+int detlsh_trace_enable(int32_t on) {
+  const int prev = g_trace_on ? 1 : 0;
+  g_trace_on = on != 0;
+  return prev;
+}
+
+int detlsh_trace_get(double* out, int32_t len) {
+  if (!out || len < 0) return DETLSH_EINVAL;
+  const int m = std::min<int>(len, TR_COUNT);
+  for (int i = 0; i < m; ++i) out[i] = g_trace[i];
+  return m;
+}
+
+int64_t detlsh_launch_count(void) {
+  return (int64_t)__atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+}
+
+double detlsh_eps_lemma3(int32_t K, int32_t L) {
+  if (K < 1 || L < 1) return -1.0;
+  return std::sqrt(chi2_upper_quantile(std::exp(-1.0 / L), K));
+}
+
+int detlsh_build(const void* X, int64_t n, int32_t d, int32_t dtype, const float* A,
+                 const int64_t* sample_ids, const detlsh_params* params, int32_t mem, void* stream,
+                 detlsh_index** out) {
+  g_err[0] = 0;
+  DL_REQUIRE(out != nullptr && params != nullptr, "out and params must be non-NULL");
+  *out = nullptr;
+  DL_REQUIRE(X && A && sample_ids, "X, A and sample_ids must be non-NULL");
+  DL_REQUIRE(mem == DETLSH_MEM_HOST || mem == DETLSH_MEM_DEVICE, "bad mem flag");
+  DL_REQUIRE(dtype == DETLSH_F32 || dtype == DETLSH_U8, "bad dtype");
+  const detlsh_params& p = *params;
+  DL_REQUIRE(p.K >= 1 && p.K <= kMaxK, "K must be in [1, %d]", kMaxK);
+  DL_REQUIRE(p.L >= 1 && p.L <= kMaxL, "L must be in [1, %d]", kMaxL);
+  DL_REQUIRE(is_pow2(p.n_regions) && p.n_regions >= 2 && p.n_regions <= 256,
+             "n_regions must be a power of two in [2, 256]");
+  DL_REQUIRE(p.max_leaf >= 1, "max_leaf must be >= 1");
+  DL_REQUIRE(d >= 1 && d <= 65536, "d must be in [1, 65536]");
+  DL_REQUIRE(n >= 1 && n * (int64_t)p.L < ((int64_t)1 << 32), "need 1 <= n and n*L < 2^32");
+  DL_REQUIRE(p.n_s >= p.n_regions && p.n_s <= n, "need n_regions <= n_s <= n");
+  DL_REQUIRE(p.proj_mode == DETLSH_PROJ_FP32, "unsupported proj_mode");
+  DL_REQUIRE(p.n_s * (int64_t)p.K * p.L < ((int64_t)1 << 32), "n_s*L*K must be < 2^32");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  trace_reset(TR_SAMPLE_PROJ, TR_LEAVES);
+  trace_reset(TR_BUILD_TOTAL, TR_BUILD_TOTAL);
+  PhaseTimer total(s);
+  total.begin(TR_BUILD_TOTAL);
+  detlsh_index* idx = new (std::nothrow) detlsh_index();
+  if (!idx) {
+    set_error("host allocation failed");
+    return DETLSH_ENOMEM;
+  }
+  const int st = build_impl(X, n, d, dtype, A, sample_ids, params, mem, s, idx);
+  if (st != DETLSH_OK) {
+    cudaStreamSynchronize(s);
+    free_index(idx);
+    return st;
+  }
+  total.end();
+  const int ts = total.finish();
+  if (ts != DETLSH_OK) {
+    free_index(idx);
+    return ts;
+  }
+  *out = idx;
+  return DETLSH_OK;
+}
+
+int detlsh_query(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dtype, const int32_t* k,
+                 const float* c, const float* r_min, int32_t k_max, const detlsh_query_params* qp,
+                 int64_t* out_ids, float* out_dist, int32_t* out_stats, int32_t mem, void* stream) {
+  g_err[0] = 0;
+  DL_REQUIRE(idx != nullptr, "index is NULL");
+  DL_REQUIRE(mem == DETLSH_MEM_HOST || mem == DETLSH_MEM_DEVICE, "bad mem flag");
+  DL_REQUIRE(dtype == idx->dtype, "query dtype differs from the index's");
+  DL_REQUIRE(nq >= 0, "nq must be >= 0");
+  DL_REQUIRE(k_max >= 1 && k_max <= kMaxTopK, "k_max must be in [1, %d]", kMaxTopK);
+  if (nq == 0) return DETLSH_OK;
+  DL_REQUIRE(Q && k && c && r_min && out_ids && out_dist, "NULL query argument");
+  double eps = qp ? qp->eps : 0.0;
+  const double beta = qp ? qp->beta : 0.1;
+  DL_REQUIRE(beta >= 0.0 && std::isfinite(beta), "beta must be finite and >= 0");
+  if (!(eps > 0.0)) eps = detlsh_eps_lemma3(idx->K, idx->L);
+  DL_REQUIRE(std::isfinite(eps) && eps > 0.0, "eps must be finite and > 0");
+  uint32_t* cand = qp ? qp->cand_ids : nullptr;
+  const int64_t cand_cap = qp ? qp->cand_cap : 0;
+  DL_REQUIRE(cand == nullptr || cand_cap >= 1, "cand_cap must be >= 1 with cand_ids");
+  if (mem == DETLSH_MEM_HOST) {
+    for (int64_t i = 0; i < nq; ++i) {
+      DL_REQUIRE(k[i] >= 1 && k[i] <= k_max, "k[%lld] must be in [1, k_max]", (long long)i);
+      DL_REQUIRE(std::isfinite(c[i]) && c[i] > 1.0f, "c[%lld] must be finite and > 1", (long long)i);
+      DL_REQUIRE(std::isfinite(r_min[i]), "r_min[%lld] must be finite", (long long)i);
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  In dQ, dk, dc, dr;
+  DL_TRY(dQ.stage(Q, (size_t)nq * idx->d * dtype_size(dtype), mem, s));
+  DL_TRY(dk.stage(k, sizeof(int32_t) * nq, mem, s));
+  DL_TRY(dc.stage(c, sizeof(float) * nq, mem, s));
+  DL_TRY(dr.stage(r_min, sizeof(float) * nq, mem, s));
+  if (mem == DETLSH_MEM_DEVICE) {
+    Scratch bad;
+    DL_TRY(bad.alloc(sizeof(int), s));
+    DL_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+    k_check_query_args<<<ceil_div(nq, 256), 256, 0, s>>>(static_cast<const int32_t*>(dk.d),
+                                                        static_cast<const float*>(dc.d),
+                                                        static_cast<const float*>(dr.d), nq, k_max,
+                                                        bad.as<int>());
+    DL_LAUNCH();
+    DL_TRY(check_flag(bad.as<int>(), s, "each query needs 1 <= k <= k_max, finite c > 1, finite r_min"));
+  }
+  trace_reset(TR_QUERY_PROJ, TR_LB_LAUNCHES);
+  trace_reset(TR_QUERY_TOTAL, TR_QUERY_TOTAL);
+  PhaseTimer total(s);
+  total.begin(TR_QUERY_TOTAL);
+  Out oi, od, os, oc;
+  DL_TRY(oi.stage(out_ids, sizeof(int64_t) * nq * k_max, mem, s));
+  DL_TRY(od.stage(out_dist, sizeof(float) * nq * k_max, mem, s));
+  DL_TRY(os.stage(out_stats, sizeof(int32_t) * nq * 4, mem, s));
+  DL_TRY(oc.stage(cand, cand ? sizeof(uint32_t) * nq * cand_cap : 0, mem, s));
+  DL_TRY(run_query(idx, dQ.d, nq, static_cast<const int32_t*>(dk.d), static_cast<const float*>(dc.d),
+                   static_cast<const float*>(dr.d), k_max, eps, beta, static_cast<int64_t*>(oi.d),
+                   static_cast<float*>(od.d), static_cast<int32_t*>(os.d), static_cast<uint32_t*>(oc.d),
+                   cand_cap, s));
+  DL_TRY(oi.finish(s));
+  DL_TRY(od.finish(s));
+  DL_TRY(os.finish(s));
+  DL_TRY(oc.finish(s));
+  total.end();
+  DL_TRY(total.finish());
+  if (mem == DETLSH_MEM_HOST) DL_CUDA(cudaStreamSynchronize(s));
+  return DETLSH_OK;
+}
+
+void detlsh_free(detlsh_index* idx) {
+  if (!idx) return;
+  cudaDeviceSynchronize();
+  free_index(idx);
+}
+
+int64_t detlsh_export_size(const detlsh_index* idx, int32_t what) {
+  if (!idx) return DETLSH_EINVAL;
+  const int64_t LK = (int64_t)idx->K * idx->L;
+  switch (what) {
+    case DETLSH_EXPORT_A: return sizeof(float) * LK * idx->d;
+    case DETLSH_EXPORT_EDGES: return sizeof(float) * LK * (idx->Nr + 1);
+    case DETLSH_EXPORT_CODES: return idx->n * LK;
+    case DETLSH_EXPORT_LEAF_IDS: return sizeof(uint32_t) * idx->n * idx->L;
+    case DETLSH_EXPORT_LEAF_BASE: return sizeof(int64_t) * (idx->L + 1);
+    case DETLSH_EXPORT_LEAF_RANGE: return sizeof(uint32_t) * 2 * idx->total_leaves;
+    case DETLSH_EXPORT_LEAF_PLEN:
+    case DETLSH_EXPORT_LEAF_PREFIX: return idx->total_leaves * idx->K;
+    case DETLSH_EXPORT_SAMPLE_PROJ: return sizeof(float) * LK * idx->n_s;
+    default: set_error("unknown export item %d", what); return DETLSH_EINVAL;
+  }
+}
+
+int detlsh_export(const detlsh_index* idx, int32_t what, void* dst, int64_t bytes, int32_t mem,
+                  void* stream) {
+  g_err[0] = 0;
+  DL_REQUIRE(idx && dst, "NULL argument");
+  DL_REQUIRE(mem == DETLSH_MEM_HOST || mem == DETLSH_MEM_DEVICE, "bad mem flag");
+  const int64_t need = detlsh_export_size(idx, what);
+  if (need < 0) return (int)need;
+  DL_REQUIRE(bytes >= need, "destination holds %lld bytes, %lld needed", (long long)bytes,
+             (long long)need);
+  const void* src = nullptr;
+  switch (what) {
+    case DETLSH_EXPORT_A: src = idx->A; break;
+    case DETLSH_EXPORT_EDGES: src = idx->E; break;
+    case DETLSH_EXPORT_CODES: src = idx->codes; break;
+    case DETLSH_EXPORT_LEAF_IDS: src = idx->leaf_ids; break;
+    case DETLSH_EXPORT_LEAF_BASE: src = idx->leaf_base; break;
+    case DETLSH_EXPORT_LEAF_RANGE: src = idx->leaf_range; break;
+    case DETLSH_EXPORT_LEAF_PLEN: src = idx->leaf_plen; break;
+    case DETLSH_EXPORT_LEAF_PREFIX: src = idx->leaf_prefix; break;
+    case DETLSH_EXPORT_SAMPLE_PROJ: src = idx->Ps; break;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DL_CUDA(cudaMemcpyAsync(dst, src, need,
+                          mem == DETLSH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  DL_CUDA(cudaStreamSynchronize(s));
+  return DETLSH_OK;
+}
+
+int detlsh_info(const detlsh_index* idx, int64_t* out, int32_t len) {
+  if (!idx || !out) return DETLSH_EINVAL;
+  const int64_t v[10] = {idx->n, idx->d, idx->dtype, idx->K, idx->L, idx->Nr, idx->max_leaf,
+                         idx->n_s, idx->total_leaves, idx->max_leaf_count};
+  const int m = std::min(len, 10);
+  for (int i = 0; i < m; ++i) out[i] = v[i];
+  return m;
+}
+
+int detlsh_project(const void* X, int64_t n, int32_t d, int32_t dtype, const float* A, int32_t LK,
+                   float* P, int32_t mem, void* stream) {
+  g_err[0] = 0;
+  DL_REQUIRE(X && A && P, "NULL argument");
+  DL_REQUIRE(dtype == DETLSH_F32 || dtype == DETLSH_U8, "bad dtype");
+  DL_REQUIRE(mem == DETLSH_MEM_HOST || mem == DETLSH_MEM_DEVICE, "bad mem flag");
+  DL_REQUIRE(n >= 0 && d >= 1 && d <= 65536 && LK >= 1 && LK <= kMaxLK, "bad sizes");
+  if (n == 0) return DETLSH_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  In dX, dA;
+  DL_TRY(dX.stage(X, (size_t)n * d * dtype_size(dtype), mem, s));
+  DL_TRY(dA.stage(A, sizeof(float) * LK * d, mem, s));
+  Scratch At;
+  DL_TRY(At.alloc(sizeof(float) * LK * d, s));
+  DL_TRY(transpose_hashes(static_cast<const float*>(dA.d), LK, d, At.as<float>(), s));
+  Out dP;
+  DL_TRY(dP.stage(P, sizeof(float) * n * LK, mem, s));
+  DL_TRY(launch_project_t(dX.d, dtype, n, d, nullptr, At.as<float>(), LK, static_cast<float*>(dP.d), LK,
+                          1, s));
+  DL_TRY(dP.finish(s));
+  DL_CUDA(cudaStreamSynchronize(s));
+  return DETLSH_OK;
+}
+
+int detlsh_encode_values(const float* P, int64_t n, int32_t LK, const float* E, int32_t n_regions,
+                         uint8_t* codes, int32_t mem, void* stream) {
+  g_err[0] = 0;
+  DL_REQUIRE(P && E && codes, "NULL argument");
+  DL_REQUIRE(mem == DETLSH_MEM_HOST || mem == DETLSH_MEM_DEVICE, "bad mem flag");
+  DL_REQUIRE(n >= 0 && LK >= 1 && LK <= kMaxLK, "bad sizes");
+  DL_REQUIRE(is_pow2(n_regions) && n_regions >= 2 && n_regions <= 256, "bad n_regions");
+  if (n == 0) return DETLSH_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  In dP, dE;
+  DL_TRY(dP.stage(P, sizeof(float) * n * LK, mem, s));
+  DL_TRY(dE.stage(E, sizeof(float) * LK * (n_regions + 1), mem, s));
+  Out dc;
+  DL_TRY(dc.stage(codes, (size_t)n * LK, mem, s));
+  DL_TRY(launch_encode_values(static_cast<const float*>(dP.d), n, LK, static_cast<const float*>(dE.d),
+                              n_regions, static_cast<uint8_t*>(dc.d), s));
+  DL_TRY(dc.finish(s));
+  DL_CUDA(cudaStreamSynchronize(s));
+  return DETLSH_OK;
+}
+
+int detlsh_select_breakpoints(const float* Ps, int64_t n_s, int32_t LK, int32_t n_regions, float* E,
+                              int32_t mem, void* stream) {
+  g_err[0] = 0;
+  DL_REQUIRE(Ps && E, "NULL argument");
+  DL_REQUIRE(mem == DETLSH_MEM_HOST || mem == DETLSH_MEM_DEVICE, "bad mem flag");
+  DL_REQUIRE(LK >= 1 && LK <= kMaxLK, "LK must be in [1, %d]", kMaxLK);
+  DL_REQUIRE(is_pow2(n_regions) && n_regions >= 2 && n_regions <= 256, "bad n_regions");
+  DL_REQUIRE(n_s >= n_regions && n_s * (int64_t)LK < ((int64_t)1 << 32), "bad n_s");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  In dP;
+  DL_TRY(dP.stage(Ps, sizeof(float) * n_s * LK, mem, s));
+  Out dE;
+  DL_TRY(dE.stage(E, sizeof(float) * LK * (n_regions + 1), mem, s));
+  DL_TRY(select_breakpoints(static_cast<const float*>(dP.d), n_s, LK, n_regions, static_cast<float*>(dE.d),
+                            s));
+  DL_TRY(dE.finish(s));
+  DL_CUDA(cudaStreamSynchronize(s));
+  return DETLSH_OK;
+}
+
+}  // extern "C"

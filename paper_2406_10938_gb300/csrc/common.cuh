@@ -1,0 +1,181 @@
+// Internal declarations shared by the translation units of libdetlsh.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+
+#include "../../include/detlsh.h"
+
+namespace detlsh {
+
+constexpr int kMaxK = 16;
+constexpr int kMaxL = 16;
+constexpr int kMaxLK = 256;
+constexpr int kRoundCap = 256;   // rounds of Alg. 7; the last one has infinite radius
+constexpr int kMaxTopK = 1024;
+
+void set_error(const char* fmt, ...);
+void count_launch();
+
+// Per-phase device times of the last build/query on this thread (tracing).
+enum TracePhase {
+  TR_SAMPLE_PROJ = 0, TR_BREAKPOINTS, TR_ENCODE, TR_LEAVES, TR_QUERY_PROJ, TR_LB, TR_SEARCH,
+  TR_SEARCH_LAUNCHES, TR_LB_LAUNCHES, TR_BUILD_TOTAL, TR_QUERY_TOTAL, TR_COUNT
+};
+bool trace_on();
+void trace_reset(int first, int last);
+void trace_add(int phase, double v);
+
+// Records CUDA events around phases on one stream when tracing is on.
+class PhaseTimer {
+ public:
+  explicit PhaseTimer(cudaStream_t s);
+  ~PhaseTimer();
+  void begin(int phase);
+  void end();
+  int finish();  // synchronizes and adds the elapsed times to the trace
+ private:
+  static constexpr int kMax = 256;
+  cudaStream_t s_;
+  bool on_;
+  int n_ = 0, open_ = -1;
+  int phase_[kMax];
+  cudaEvent_t a_[kMax], b_[kMax];
+};
+
+#define DL_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      ::detlsh::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),  \
+                          __FILE__, __LINE__);                                     \
+      return e_ == cudaErrorMemoryAllocation ? DETLSH_ENOMEM : DETLSH_ECUDA;       \
+    }                                                                              \
+  } while (0)
+
+#define DL_LAUNCH()                                                                \
+  do {                                                                             \
+    ::detlsh::count_launch();                                                      \
+    cudaError_t e_ = cudaGetLastError();                                           \
+    if (e_ != cudaSuccess) {                                                       \
+      ::detlsh::set_error("kernel launch failed: %s (%s:%d)",                      \
+                          cudaGetErrorString(e_), __FILE__, __LINE__);             \
+      return DETLSH_ECUDA;                                                         \
+    }                                                                              \
+  } while (0)
+
+#define DL_REQUIRE(cond, ...)                                                      \
+  do {                                                                             \
+    if (!(cond)) {                                                                 \
+      ::detlsh::set_error(__VA_ARGS__);                                            \
+      return DETLSH_EINVAL;                                                        \
+    }                                                                              \
+  } while (0)
+
+#define DL_TRY(expr)                                                               \
+  do {                                                                             \
+    int s_ = (expr);                                                               \
+    if (s_ != DETLSH_OK) return s_;                                                \
+  } while (0)
+
+// Stream-ordered scratch allocation that frees itself on scope exit.
+struct Scratch {
+  void* p = nullptr;
+  cudaStream_t s = nullptr;
+  Scratch() = default;
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  ~Scratch() {
+    if (p) cudaFreeAsync(p, s);
+  }
+  int alloc(size_t bytes, cudaStream_t stream) {
+    s = stream;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      set_error("cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
+      return DETLSH_ENOMEM;
+    }
+    return DETLSH_OK;
+  }
+  template <class T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace detlsh
+
+// The index. Device arrays unless marked _h.
+struct detlsh_index {
+  int64_t n = 0;
+  int32_t d = 0, dtype = 0, K = 0, L = 0, Nr = 0, bits = 0, max_leaf = 0;
+  int64_t n_s = 0;
+  int32_t device = 0;
+  bool owns_x = true;
+  const void* X = nullptr;          // [n][d] f32 or u8
+  float* A = nullptr;               // [LK][d]
+  float* At = nullptr;              // [d][LK] (transposed A)
+  float* E = nullptr;               // [LK][Nr+1]
+  float* Ps = nullptr;              // [LK][n_s]
+  uint8_t* codes = nullptr;         // [L][n][K]
+  uint32_t* leaf_ids = nullptr;     // [L][n]
+  int64_t* leaf_base = nullptr;     // [L+1]
+  uint32_t* leaf_range = nullptr;   // [total][2] (start within tree, count)
+  uint8_t* leaf_plen = nullptr;     // [total][K]
+  uint8_t* leaf_prefix = nullptr;   // [total][K]
+  uint8_t* leaf_lo = nullptr;       // [total][K] lowest code of the leaf box
+  uint8_t* leaf_hi = nullptr;       // [total][K] highest code of the leaf box
+  uint16_t* leaf_tree = nullptr;    // [total] tree of each leaf
+  int64_t total_leaves = 0;
+  int64_t max_leaf_count = 0;
+  int64_t leaf_base_h[detlsh::kMaxL + 1] = {0};
+};
+
+namespace detlsh {
+
+// ---- projection / encoding (project.cu)
+// At [d][LK] = transpose of A [LK][d].
+int transpose_hashes(const float* A, int LK, int d, float* At, cudaStream_t s);
+// P[o*p_so + r*p_sr] = sum_t A[r][t] * X[rows ? rows[o] : o][t], FP32 (At transposed).
+int launch_project_t(const void* X, int dtype, int64_t n, int d, const int64_t* rows,
+                     const float* At, int LK, float* P, int64_t p_so, int64_t p_sr,
+                     cudaStream_t s);
+// Same projection, then Alg. 2 against E [LK][Nr+1]; writes codes [L][n][K].
+int launch_project_encode_t(const void* X, int dtype, int64_t n, int d, const float* At,
+                            int K, int L, const float* E, int Nr, uint8_t* codes,
+                            cudaStream_t s);
+int launch_encode_values(const float* P, int64_t n, int LK, const float* E, int Nr,
+                         uint8_t* codes, cudaStream_t s);
+
+// ---- sorting / scans (sort.cu)
+// Stable LSD radix sort of (key, value) pairs on key bits [bit_lo, bit_hi).
+int radix_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, int64_t n,
+                     int bit_lo, int bit_hi, uint32_t* keys_out, uint32_t* vals_out,
+                     cudaStream_t s);
+// Exclusive prefix sum of n uint32 values into uint32 (sum must fit) ; total to *d_total.
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* d_total,
+                       cudaStream_t s);
+
+// ---- breakpoints (breakpoints.cu)
+// Ps [LK][n_s] -> E [LK][Nr+1].
+int select_breakpoints(const float* Ps, int64_t n_s, int LK, int Nr, float* E,
+                       cudaStream_t s);
+
+// ---- leaves (leaves.cu)
+int build_leaves(detlsh_index* idx, cudaStream_t s);
+
+// ---- query (query.cu)
+int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t* k,
+              const float* c, const float* r_min, int k_max, double eps, double beta,
+              int64_t* out_ids, float* out_dist, int32_t* out_stats, uint32_t* cand_ids,
+              int64_t cand_cap, cudaStream_t s);
+
+// ---- host math (chi2.cpp)
+double chi2_upper_quantile(double alpha, int K);
+
+}  // namespace detlsh

@@ -1,0 +1,516 @@
+// DE-Tree construction (Alg. 3 and the split rule of Sec. 4.2), bulk-loaded.
+//
+// Per tree the points are first stably sorted by the K-bit vector of their
+// codes' top bits (dimension 0 most significant): the runs of that order are
+// the root's 2^K first-layer nodes. Then, level-synchronously, every node
+// (a contiguous segment of the tree's id array) holding more than max_leaf
+// points whose codes still have an unresolved bit is split: its tiles count
+// the next bit of every splittable dimension, the dimension minimising
+// |2*ones - count| (lowest on ties) is chosen, and the segment is stably
+// partitioned bit 0 first. Empty children vanish. Because every split is a
+// stable in-place partition, the final segments are the leaves in
+// depth-first order with ascending ids inside each leaf.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace detlsh {
+namespace {
+
+constexpr int LT = 256;          // threads per tile block
+constexpr int LIPT = 4;          // items per thread
+constexpr int LTILE = LT * LIPT; // items per tile
+
+__device__ __forceinline__ uint32_t byte_of(const uint4& v, int j) {
+  const uint32_t w = (j < 4) ? v.x : (j < 8) ? v.y : (j < 12) ? v.z : v.w;
+  return (w >> ((j & 3) * 8)) & 0xffu;
+}
+__device__ __forceinline__ void set_byte(uint4& v, int j, uint32_t b) {
+  const uint32_t sh = (j & 3) * 8, mask = ~(0xffu << sh);
+  if (j < 4) v.x = (v.x & mask) | (b << sh);
+  else if (j < 8) v.y = (v.y & mask) | (b << sh);
+  else if (j < 12) v.z = (v.z & mask) | (b << sh);
+  else v.w = (v.w & mask) | (b << sh);
+}
+
+__device__ __forceinline__ uint4 load_code(const uint8_t* __restrict__ codes, int64_t row, int K) {
+  if (K == 16) return __ldg(reinterpret_cast<const uint4*>(codes + row * 16));
+  uint4 v = make_uint4(0, 0, 0, 0);
+  for (int j = 0; j < K; ++j) set_byte(v, j, codes[row * K + j]);
+  return v;
+}
+
+// ---- root level
+__global__ void k_root_keys(const uint8_t* __restrict__ codes, int64_t n, int K, int bits,
+                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 c = load_code(codes, i, K);
+  uint32_t key = 0;
+#pragma unroll
+  for (int j = 0; j < kMaxK; ++j)
+    if (j < K) key = (key << 1) | ((byte_of(c, j) >> (bits - 1)) & 1u);
+  keys[i] = key;
+  vals[i] = (uint32_t)i;
+}
+
+__global__ void k_root_flags(const uint32_t* __restrict__ keys, int64_t n, int64_t tree_off,
+                             uint32_t* __restrict__ flags) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  flags[tree_off + i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_root_segments(const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos,
+                                const uint32_t* __restrict__ keys_all, int64_t total, int64_t n,
+                                int K, int bits, uint32_t* __restrict__ seg_start,
+                                uint4* __restrict__ seg_plen, uint4* __restrict__ seg_prefix) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total || !flags[g]) return;
+  const uint32_t s = pos[g];
+  seg_start[s] = (uint32_t)g;
+  const uint32_t key = keys_all[g];
+  uint4 pl = make_uint4(0, 0, 0, 0), pf = make_uint4(0, 0, 0, 0);
+#pragma unroll
+  for (int j = 0; j < kMaxK; ++j) {
+    set_byte(pl, j, j < K ? 1u : (uint32_t)bits);
+    set_byte(pf, j, j < K ? (key >> (K - 1 - j)) & 1u : 0u);
+  }
+  seg_plen[s] = pl;
+  seg_prefix[s] = pf;
+  (void)n;
+}
+
+__global__ void k_seg_counts(const uint32_t* __restrict__ seg_start, uint32_t nseg, int64_t n,
+                             int64_t total, uint32_t* __restrict__ seg_count) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nseg) return;
+  const uint32_t a = seg_start[s];
+  // a segment never crosses its tree's end
+  const int64_t tree_end = ((int64_t)a / n + 1) * n;
+  int64_t b = total;
+  if (s + 1 < nseg) b = (int64_t)seg_start[s + 1] < tree_end ? (int64_t)seg_start[s + 1] : tree_end;
+  seg_count[s] = (uint32_t)(b - a);
+}
+
+// ---- split iteration
+__global__ void k_plan(const uint32_t* __restrict__ seg_count, const uint4* __restrict__ seg_plen,
+                       uint32_t nseg, int K, int bits, int max_leaf,
+                       uint32_t* __restrict__ tiles_needed) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nseg) return;
+  const uint32_t cnt = seg_count[s];
+  bool splittable = false;
+  const uint4 pl = seg_plen[s];
+#pragma unroll
+  for (int j = 0; j < kMaxK; ++j)
+    if (j < K && byte_of(pl, j) < (uint32_t)bits) splittable = true;
+  tiles_needed[s] = (cnt > (uint32_t)max_leaf && splittable) ? (cnt + LTILE - 1) / LTILE : 0u;
+}
+
+__global__ void k_tile_map(const uint32_t* __restrict__ tiles_needed,
+                           const uint32_t* __restrict__ tile_base, uint32_t nseg,
+                           uint32_t* __restrict__ tile_seg) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nseg) return;
+  const uint32_t t0 = tile_base[s], nt = tiles_needed[s];
+  for (uint32_t t = 0; t < nt; ++t) tile_seg[t0 + t] = (uint32_t)s;
+}
+
+// Per tile: number of points whose next unresolved bit is 1, for every dimension.
+__global__ void __launch_bounds__(LT)
+k_tile_count(const uint32_t* __restrict__ tile_seg, const uint32_t* __restrict__ tile_base,
+             const uint32_t* __restrict__ seg_start, const uint32_t* __restrict__ seg_count,
+             const uint4* __restrict__ seg_plen, const uint32_t* __restrict__ ids,
+             const uint8_t* __restrict__ codes, int64_t n, int K, int bits,
+             uint32_t* __restrict__ tile_cnt) {
+  __shared__ uint32_t s_cnt[kMaxK];
+  const uint32_t tile = blockIdx.x;
+  const uint32_t s = tile_seg[tile];
+  const uint32_t chunk = tile - tile_base[s];
+  const uint32_t start = seg_start[s], count = seg_count[s];
+  const uint4 pl = seg_plen[s];
+  const int64_t tree_row = ((int64_t)start / n) * n;
+  if (threadIdx.x < kMaxK) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  uint32_t cnt[kMaxK];
+#pragma unroll
+  for (int j = 0; j < kMaxK; ++j) cnt[j] = 0;
+  for (int r = 0; r < LIPT; ++r) {
+    const uint32_t off = chunk * LTILE + r * LT + threadIdx.x;
+    if (off < count) {
+      const uint32_t id = ids[start + off];
+      const uint4 c = load_code(codes, tree_row + id, K);
+#pragma unroll
+      for (int j = 0; j < kMaxK; ++j) {
+        const uint32_t l = byte_of(pl, j);
+        if (j < K && l < (uint32_t)bits) cnt[j] += (byte_of(c, j) >> (bits - 1 - l)) & 1u;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kMaxK; ++j) {
+    uint32_t v = cnt[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_cnt[j], v);
+  }
+  __syncthreads();
+  if (threadIdx.x < kMaxK) tile_cnt[(int64_t)tile * kMaxK + threadIdx.x] = s_cnt[threadIdx.x];
+}
+
+// Per active segment: choose the split dimension and the per-tile bases.
+__global__ void k_choose(const uint32_t* __restrict__ tiles_needed,
+                         const uint32_t* __restrict__ tile_base,
+                         const uint32_t* __restrict__ seg_count, const uint4* __restrict__ seg_plen,
+                         uint32_t nseg, int K, int bits, const uint32_t* __restrict__ tile_cnt,
+                         uint32_t* __restrict__ seg_dim, uint32_t* __restrict__ seg_ones,
+                         uint32_t* __restrict__ tile_ones_before,
+                         uint32_t* __restrict__ out_n) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nseg) return;
+  const uint32_t nt = tiles_needed[s];
+  if (nt == 0) {
+    out_n[s] = 1;
+    return;
+  }
+  const uint32_t t0 = tile_base[s], cnt = seg_count[s];
+  const uint4 pl = seg_plen[s];
+  int best = -1;
+  uint32_t best_gap = 0xffffffffu, best_ones = 0;
+  for (int j = 0; j < K; ++j) {
+    if (byte_of(pl, j) >= (uint32_t)bits) continue;
+    uint32_t ones = 0;
+    for (uint32_t t = 0; t < nt; ++t) ones += tile_cnt[(int64_t)(t0 + t) * kMaxK + j];
+    const uint32_t gap = (2u * ones > cnt) ? 2u * ones - cnt : cnt - 2u * ones;
+    if (gap < best_gap) {
+      best_gap = gap;
+      best = j;
+      best_ones = ones;
+    }
+  }
+  seg_dim[s] = (uint32_t)best;
+  seg_ones[s] = best_ones;
+  uint32_t run = 0;
+  for (uint32_t t = 0; t < nt; ++t) {
+    tile_ones_before[t0 + t] = run;
+    run += tile_cnt[(int64_t)(t0 + t) * kMaxK + best];
+  }
+  out_n[s] = (best_ones > 0 ? 1u : 0u) + (best_ones < cnt ? 1u : 0u);
+}
+
+// Stable partition of each active segment by the chosen bit, into tmp.
+__global__ void __launch_bounds__(LT)
+k_tile_scatter(const uint32_t* __restrict__ tile_seg, const uint32_t* __restrict__ tile_base,
+               const uint32_t* __restrict__ seg_start, const uint32_t* __restrict__ seg_count,
+               const uint4* __restrict__ seg_plen, const uint32_t* __restrict__ seg_dim,
+               const uint32_t* __restrict__ seg_ones, const uint32_t* __restrict__ tile_ones_before,
+               const uint32_t* __restrict__ ids, const uint8_t* __restrict__ codes, int64_t n,
+               int K, int bits, uint32_t* __restrict__ tmp) {
+  __shared__ uint32_t s_warp[LT / 32];
+  const uint32_t tile = blockIdx.x;
+  const uint32_t s = tile_seg[tile];
+  const uint32_t chunk = tile - tile_base[s];
+  const uint32_t start = seg_start[s], count = seg_count[s];
+  const int j = (int)seg_dim[s];
+  const uint32_t shift = (uint32_t)(bits - 1) - byte_of(seg_plen[s], j);
+  const uint32_t zeros_total = count - seg_ones[s];
+  const int64_t tree_row = ((int64_t)start / n) * n;
+  // contiguous items per thread keep the in-tile order for the scan
+  uint32_t id[LIPT], bit[LIPT];
+  uint32_t my_ones = 0;
+#pragma unroll
+  for (int r = 0; r < LIPT; ++r) {
+    const uint32_t off = chunk * LTILE + threadIdx.x * LIPT + r;
+    bit[r] = 2;
+    if (off < count) {
+      id[r] = ids[start + off];
+      const uint4 c = load_code(codes, tree_row + id[r], K);
+      bit[r] = (byte_of(c, j) >> shift) & 1u;
+      my_ones += bit[r];
+    }
+  }
+  // exclusive scan of ones over threads
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = my_ones;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  uint32_t warp_before = 0;
+  for (int q = 0; q < w; ++q) warp_before += s_warp[q];
+  uint32_t ones_before = tile_ones_before[tile] + warp_before + x - my_ones;
+#pragma unroll
+  for (int r = 0; r < LIPT; ++r) {
+    if (bit[r] > 1) continue;
+    const uint32_t off = chunk * LTILE + threadIdx.x * LIPT + r;
+    uint32_t dest;
+    if (bit[r]) {
+      dest = start + zeros_total + ones_before;
+      ++ones_before;
+    } else {
+      dest = start + (off - ones_before);
+    }
+    tmp[dest] = id[r];
+  }
+}
+
+__global__ void __launch_bounds__(LT)
+k_tile_copyback(const uint32_t* __restrict__ tile_seg, const uint32_t* __restrict__ tile_base,
+                const uint32_t* __restrict__ seg_start, const uint32_t* __restrict__ seg_count,
+                const uint32_t* __restrict__ tmp, uint32_t* __restrict__ ids) {
+  const uint32_t tile = blockIdx.x;
+  const uint32_t s = tile_seg[tile];
+  const uint32_t chunk = tile - tile_base[s];
+  const uint32_t start = seg_start[s], count = seg_count[s];
+  for (int r = 0; r < LIPT; ++r) {
+    const uint32_t off = chunk * LTILE + r * LT + threadIdx.x;
+    if (off < count) ids[start + off] = tmp[start + off];
+  }
+}
+
+__global__ void k_emit(const uint32_t* __restrict__ tiles_needed, const uint32_t* __restrict__ out_pos,
+                       const uint32_t* __restrict__ seg_start, const uint32_t* __restrict__ seg_count,
+                       const uint4* __restrict__ seg_plen, const uint4* __restrict__ seg_prefix,
+                       const uint32_t* __restrict__ seg_dim, const uint32_t* __restrict__ seg_ones,
+                       uint32_t nseg, uint32_t* __restrict__ n_start, uint32_t* __restrict__ n_count,
+                       uint4* __restrict__ n_plen, uint4* __restrict__ n_prefix) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nseg) return;
+  uint32_t o = out_pos[s];
+  const uint32_t start = seg_start[s], cnt = seg_count[s];
+  const uint4 pl = seg_plen[s], pf = seg_prefix[s];
+  if (tiles_needed[s] == 0) {
+    n_start[o] = start;
+    n_count[o] = cnt;
+    n_plen[o] = pl;
+    n_prefix[o] = pf;
+    return;
+  }
+  const int j = (int)seg_dim[s];
+  const uint32_t ones = seg_ones[s], zeros = cnt - ones;
+  uint4 cpl = pl;
+  set_byte(cpl, j, byte_of(pl, j) + 1);
+  const uint32_t p2 = byte_of(pf, j) * 2;
+  if (zeros) {
+    uint4 cpf = pf;
+    set_byte(cpf, j, p2);
+    n_start[o] = start;
+    n_count[o] = zeros;
+    n_plen[o] = cpl;
+    n_prefix[o] = cpf;
+    ++o;
+  }
+  if (ones) {
+    uint4 cpf = pf;
+    set_byte(cpf, j, p2 + 1);
+    n_start[o] = start + zeros;
+    n_count[o] = ones;
+    n_plen[o] = cpl;
+    n_prefix[o] = cpf;
+  }
+}
+
+// ---- leaf table
+__global__ void k_finalize(const uint32_t* __restrict__ seg_start, const uint32_t* __restrict__ seg_count,
+                           const uint4* __restrict__ seg_plen, const uint4* __restrict__ seg_prefix,
+                           uint32_t nseg, int64_t n, int K, int bits,
+                           uint32_t* __restrict__ leaf_range, uint8_t* __restrict__ leaf_plen,
+                           uint8_t* __restrict__ leaf_prefix, uint8_t* __restrict__ leaf_lo,
+                           uint8_t* __restrict__ leaf_hi, uint16_t* __restrict__ leaf_tree,
+                           int64_t* __restrict__ leaf_base, unsigned long long* __restrict__ max_count) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nseg) return;
+  const uint32_t start = seg_start[s];
+  const int64_t tree = (int64_t)start / n;
+  leaf_range[2 * s] = (uint32_t)(start - tree * n);
+  leaf_range[2 * s + 1] = seg_count[s];
+  leaf_tree[s] = (uint16_t)tree;
+  const uint4 pl = seg_plen[s], pf = seg_prefix[s];
+  for (int j = 0; j < K; ++j) {
+    const uint32_t l = byte_of(pl, j), p = byte_of(pf, j);
+    const uint32_t lo = p << (bits - l);
+    const uint32_t hi = lo + (1u << (bits - l)) - 1u;
+    leaf_plen[s * K + j] = (uint8_t)l;
+    leaf_prefix[s * K + j] = (uint8_t)p;
+    leaf_lo[s * K + j] = (uint8_t)lo;
+    leaf_hi[s * K + j] = (uint8_t)hi;
+  }
+  if (s == 0 || (int64_t)seg_start[s - 1] / n != tree) leaf_base[tree] = s;
+  if (s == nseg - 1) leaf_base[tree + 1] = nseg;
+  atomicMax(max_count, (unsigned long long)seg_count[s]);
+}
+
+int read_u32(const uint32_t* d, uint32_t* h, cudaStream_t s) {
+  DL_CUDA(cudaMemcpyAsync(h, d, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  DL_CUDA(cudaStreamSynchronize(s));
+  return DETLSH_OK;
+}
+
+}  // namespace
+
+int build_leaves(detlsh_index* idx, cudaStream_t s) {
+  const int64_t n = idx->n, L = idx->L, total = n * L;
+  const int K = idx->K, bits = idx->bits;
+  // ---- root level: per tree stable sort of ids by the top-bit vector
+  Scratch keys_all, flags, pos, k0, v0, d_tot;
+  DL_TRY(keys_all.alloc(sizeof(uint32_t) * total, s));
+  DL_TRY(flags.alloc(sizeof(uint32_t) * total, s));
+  DL_TRY(pos.alloc(sizeof(uint32_t) * total, s));
+  DL_TRY(k0.alloc(sizeof(uint32_t) * n, s));
+  DL_TRY(v0.alloc(sizeof(uint32_t) * n, s));
+  DL_TRY(d_tot.alloc(sizeof(uint32_t) * 4, s));
+  for (int64_t t = 0; t < L; ++t) {
+    k_root_keys<<<ceil_div(n, 256), 256, 0, s>>>(idx->codes + t * n * K, n, K, bits,
+                                                 k0.as<uint32_t>(), v0.as<uint32_t>());
+    DL_LAUNCH();
+    DL_TRY(radix_sort_pairs(k0.as<uint32_t>(), v0.as<uint32_t>(), n, 0, K,
+                            keys_all.as<uint32_t>() + t * n, idx->leaf_ids + t * n, s));
+    k_root_flags<<<ceil_div(n, 256), 256, 0, s>>>(keys_all.as<uint32_t>() + t * n, n, t * n,
+                                                  flags.as<uint32_t>());
+    DL_LAUNCH();
+  }
+  DL_TRY(exclusive_scan_u32(flags.as<uint32_t>(), pos.as<uint32_t>(), total, d_tot.as<uint32_t>(), s));
+  uint32_t nseg = 0;
+  DL_TRY(read_u32(d_tot.as<uint32_t>(), &nseg, s));
+
+  // segment tables (ping-pong); capacity: at most one segment per point
+  const int64_t cap = total;
+  Scratch a_start, a_count, a_plen, a_prefix, b_start, b_count, b_plen, b_prefix;
+  DL_TRY(a_start.alloc(sizeof(uint32_t) * cap, s));
+  DL_TRY(a_count.alloc(sizeof(uint32_t) * cap, s));
+  DL_TRY(a_plen.alloc(sizeof(uint4) * cap, s));
+  DL_TRY(a_prefix.alloc(sizeof(uint4) * cap, s));
+  DL_TRY(b_start.alloc(sizeof(uint32_t) * cap, s));
+  DL_TRY(b_count.alloc(sizeof(uint32_t) * cap, s));
+  DL_TRY(b_plen.alloc(sizeof(uint4) * cap, s));
+  DL_TRY(b_prefix.alloc(sizeof(uint4) * cap, s));
+  k_root_segments<<<ceil_div(total, 256), 256, 0, s>>>(
+      flags.as<uint32_t>(), pos.as<uint32_t>(), keys_all.as<uint32_t>(), total, n, K, bits,
+      a_start.as<uint32_t>(), a_plen.as<uint4>(), a_prefix.as<uint4>());
+  DL_LAUNCH();
+  k_seg_counts<<<ceil_div(nseg, 256), 256, 0, s>>>(a_start.as<uint32_t>(), nseg, n, total,
+                                                   a_count.as<uint32_t>());
+  DL_LAUNCH();
+
+  // per-segment and per-tile work arrays
+  Scratch tiles_needed, tile_base, seg_dim, seg_ones, out_n, out_pos, tmp;
+  DL_TRY(tiles_needed.alloc(sizeof(uint32_t) * cap, s));
+  DL_TRY(tile_base.alloc(sizeof(uint32_t) * cap, s));
+  DL_TRY(seg_dim.alloc(sizeof(uint32_t) * cap, s));
+  DL_TRY(seg_ones.alloc(sizeof(uint32_t) * cap, s));
+  DL_TRY(out_n.alloc(sizeof(uint32_t) * cap, s));
+  DL_TRY(out_pos.alloc(sizeof(uint32_t) * cap, s));
+  DL_TRY(tmp.alloc(sizeof(uint32_t) * total, s));
+  const int64_t tile_cap = ceil_div(total, LTILE) + cap / 1;  // every segment may add one partial tile
+  Scratch tile_seg, tile_cnt, tile_ones_before;
+  int64_t tile_alloc = std::min<int64_t>(tile_cap, ceil_div(total, LTILE) + (int64_t)nseg + 1);
+  DL_TRY(tile_seg.alloc(sizeof(uint32_t) * tile_alloc, s));
+  DL_TRY(tile_cnt.alloc(sizeof(uint32_t) * kMaxK * tile_alloc, s));
+  DL_TRY(tile_ones_before.alloc(sizeof(uint32_t) * tile_alloc, s));
+
+  uint32_t* cs = a_start.as<uint32_t>();
+  uint32_t* cc = a_count.as<uint32_t>();
+  uint4* cpl = a_plen.as<uint4>();
+  uint4* cpf = a_prefix.as<uint4>();
+  uint32_t* ns = b_start.as<uint32_t>();
+  uint32_t* nc = b_count.as<uint32_t>();
+  uint4* npl = b_plen.as<uint4>();
+  uint4* npf = b_prefix.as<uint4>();
+
+  for (int iter = 0; iter < kMaxK * 8 + 2; ++iter) {
+    k_plan<<<ceil_div(nseg, 256), 256, 0, s>>>(cc, cpl, nseg, K, bits, idx->max_leaf,
+                                               tiles_needed.as<uint32_t>());
+    DL_LAUNCH();
+    DL_TRY(exclusive_scan_u32(tiles_needed.as<uint32_t>(), tile_base.as<uint32_t>(), nseg,
+                              d_tot.as<uint32_t>(), s));
+    uint32_t ntiles = 0;
+    DL_TRY(read_u32(d_tot.as<uint32_t>(), &ntiles, s));
+    if (ntiles == 0) break;
+    if ((int64_t)ntiles > tile_alloc) {
+      set_error("leaf build: tile table overflow (%u > %lld)", ntiles, (long long)tile_alloc);
+      return DETLSH_EINTERNAL;
+    }
+    k_tile_map<<<ceil_div(nseg, 256), 256, 0, s>>>(tiles_needed.as<uint32_t>(),
+                                                   tile_base.as<uint32_t>(), nseg,
+                                                   tile_seg.as<uint32_t>());
+    DL_LAUNCH();
+    k_tile_count<<<ntiles, LT, 0, s>>>(tile_seg.as<uint32_t>(), tile_base.as<uint32_t>(), cs, cc,
+                                       cpl, idx->leaf_ids, idx->codes, n, K, bits,
+                                       tile_cnt.as<uint32_t>());
+    DL_LAUNCH();
+    k_choose<<<ceil_div(nseg, 256), 256, 0, s>>>(
+        tiles_needed.as<uint32_t>(), tile_base.as<uint32_t>(), cc, cpl, nseg, K, bits,
+        tile_cnt.as<uint32_t>(), seg_dim.as<uint32_t>(), seg_ones.as<uint32_t>(),
+        tile_ones_before.as<uint32_t>(), out_n.as<uint32_t>());
+    DL_LAUNCH();
+    k_tile_scatter<<<ntiles, LT, 0, s>>>(tile_seg.as<uint32_t>(), tile_base.as<uint32_t>(), cs, cc,
+                                         cpl, seg_dim.as<uint32_t>(), seg_ones.as<uint32_t>(),
+                                         tile_ones_before.as<uint32_t>(), idx->leaf_ids,
+                                         idx->codes, n, K, bits, tmp.as<uint32_t>());
+    DL_LAUNCH();
+    k_tile_copyback<<<ntiles, LT, 0, s>>>(tile_seg.as<uint32_t>(), tile_base.as<uint32_t>(), cs,
+                                          cc, tmp.as<uint32_t>(), idx->leaf_ids);
+    DL_LAUNCH();
+    DL_TRY(exclusive_scan_u32(out_n.as<uint32_t>(), out_pos.as<uint32_t>(), nseg,
+                              d_tot.as<uint32_t>(), s));
+    uint32_t nseg_new = 0;
+    DL_TRY(read_u32(d_tot.as<uint32_t>(), &nseg_new, s));
+    if ((int64_t)nseg_new > cap) {
+      set_error("leaf build: segment table overflow");
+      return DETLSH_EINTERNAL;
+    }
+    k_emit<<<ceil_div(nseg, 256), 256, 0, s>>>(tiles_needed.as<uint32_t>(), out_pos.as<uint32_t>(),
+                                               cs, cc, cpl, cpf, seg_dim.as<uint32_t>(),
+                                               seg_ones.as<uint32_t>(), nseg, ns, nc, npl, npf);
+    DL_LAUNCH();
+    std::swap(cs, ns);
+    std::swap(cc, nc);
+    std::swap(cpl, npl);
+    std::swap(cpf, npf);
+    nseg = nseg_new;
+    // the tile tables must cover the next iteration's active segments
+    const int64_t need = ceil_div(total, LTILE) + (int64_t)nseg + 1;
+    if (need > tile_alloc) {
+      tile_alloc = need;
+      Scratch a, b2, c2;
+      DL_TRY(a.alloc(sizeof(uint32_t) * tile_alloc, s));
+      DL_TRY(b2.alloc(sizeof(uint32_t) * kMaxK * tile_alloc, s));
+      DL_TRY(c2.alloc(sizeof(uint32_t) * tile_alloc, s));
+      std::swap(tile_seg.p, a.p);
+      std::swap(tile_cnt.p, b2.p);
+      std::swap(tile_ones_before.p, c2.p);
+    }
+  }
+
+  // ---- leaf table
+  idx->total_leaves = nseg;
+  DL_CUDA(cudaMalloc(&idx->leaf_range, sizeof(uint32_t) * 2 * nseg));
+  DL_CUDA(cudaMalloc(&idx->leaf_plen, (size_t)nseg * K));
+  DL_CUDA(cudaMalloc(&idx->leaf_prefix, (size_t)nseg * K));
+  DL_CUDA(cudaMalloc(&idx->leaf_lo, (size_t)nseg * K));
+  DL_CUDA(cudaMalloc(&idx->leaf_hi, (size_t)nseg * K));
+  DL_CUDA(cudaMalloc(&idx->leaf_tree, sizeof(uint16_t) * nseg));
+  DL_CUDA(cudaMalloc(&idx->leaf_base, sizeof(int64_t) * (L + 1)));
+  Scratch d_max;
+  DL_TRY(d_max.alloc(sizeof(unsigned long long), s));
+  DL_CUDA(cudaMemsetAsync(d_max.p, 0, sizeof(unsigned long long), s));
+  k_finalize<<<ceil_div(nseg, 256), 256, 0, s>>>(cs, cc, cpl, cpf, nseg, n, K, bits,
+                                                 idx->leaf_range, idx->leaf_plen, idx->leaf_prefix,
+                                                 idx->leaf_lo, idx->leaf_hi, idx->leaf_tree,
+                                                 idx->leaf_base, d_max.as<unsigned long long>());
+  DL_LAUNCH();
+  unsigned long long mx = 0;
+  DL_CUDA(cudaMemcpyAsync(idx->leaf_base_h, idx->leaf_base, sizeof(int64_t) * (L + 1),
+                          cudaMemcpyDeviceToHost, s));
+  DL_CUDA(cudaMemcpyAsync(&mx, d_max.p, sizeof(mx), cudaMemcpyDeviceToHost, s));
+  DL_CUDA(cudaStreamSynchronize(s));
+  idx->max_leaf_count = (int64_t)mx;
+  return DETLSH_OK;
+}
+
+}  // namespace detlsh

@@ -1,0 +1,206 @@
+// Device-wide exclusive scan and stable LSD radix sort of (key, value) pairs.
+//
+// Radix pass (8-bit digit): every tile of TILE items counts its digits, one
+// exclusive scan over the digit-major [256][tiles] count table gives every
+// (digit, tile) its output base, and the scatter kernel ranks each item among
+// the equal digits of its tile in input order (warp match + per-warp counts),
+// which makes each pass stable.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace detlsh {
+namespace {
+
+constexpr int ST = 256;               // threads per block
+constexpr int IPT = 8;                // items per thread
+constexpr int TILE = ST * IPT;        // items per tile
+constexpr int NW = ST / 32;
+
+// ------------------------------------------------------------------ scan
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp,
+                                                         uint32_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = lane < NW ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < NW) s_warp[lane] = t;
+  }
+  __syncthreads();
+  const uint32_t before = (w > 0 ? s_warp[w - 1] : 0) + x - v;
+  if (total) *total = s_warp[NW - 1];
+  __syncthreads();
+  return before;
+}
+
+__global__ void k_block_sums(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ sums) {
+  __shared__ uint32_t s_warp[NW];
+  const int64_t base = (int64_t)blockIdx.x * TILE;
+  uint32_t acc = 0;
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
+    const int64_t i = base + (int64_t)threadIdx.x * IPT + r;
+    if (i < n) acc += in[i];
+  }
+  uint32_t total;
+  block_exclusive_scan(acc, s_warp, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_block_scan(const uint32_t* __restrict__ in, int64_t n,
+                             const uint32_t* __restrict__ block_base, uint32_t* __restrict__ out,
+                             uint32_t* __restrict__ d_total) {
+  __shared__ uint32_t s_warp[NW];
+  const int64_t base = (int64_t)blockIdx.x * TILE + (int64_t)threadIdx.x * IPT;
+  uint32_t v[IPT];
+  uint32_t acc = 0;
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
+    v[r] = (base + r < n) ? in[base + r] : 0;
+    acc += v[r];
+  }
+  uint32_t total;
+  uint32_t run = block_exclusive_scan(acc, s_warp, &total);
+  if (block_base) run += block_base[blockIdx.x];
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
+    if (base + r < n) out[base + r] = run;
+    run += v[r];
+  }
+  if (d_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == ST - 1) *d_total = run;
+}
+
+// ------------------------------------------------------------------ radix pass
+__global__ void __launch_bounds__(ST)
+k_digit_hist(const uint32_t* __restrict__ keys, int64_t n, int bit, uint32_t* __restrict__ hist,
+             int64_t n_tiles) {
+  __shared__ uint32_t s_h[256];
+  s_h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * TILE;
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
+    const int64_t i = base + (int64_t)r * ST + threadIdx.x;
+    if (i < n) atomicAdd(&s_h[(keys[i] >> bit) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = s_h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(ST)
+k_digit_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                int64_t n, int bit, const uint32_t* __restrict__ offs, int64_t n_tiles,
+                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
+  __shared__ uint32_t s_base[256];
+  __shared__ uint32_t s_wc[NW][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  s_base[threadIdx.x] = offs[(int64_t)threadIdx.x * n_tiles + blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < NW; ++q) s_wc[q][threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t lt = (1u << lane) - 1u;
+  const int64_t base = (int64_t)blockIdx.x * TILE;
+  for (int r = 0; r < IPT; ++r) {
+    const int64_t i = base + (int64_t)r * ST + threadIdx.x;
+    const bool valid = i < n;
+    uint32_t key = 0, val = 0;
+    int digit = 256;
+    if (valid) {
+      key = keys_in[i];
+      val = vals_in[i];
+      digit = (int)((key >> bit) & 255u);
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+    const uint32_t rank_in_warp = __popc(peers & lt);
+    if (valid && rank_in_warp == 0) s_wc[w][digit] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = s_base[digit] + rank_in_warp;
+      for (int q = 0; q < w; ++q) pos += s_wc[q][digit];
+      keys_out[pos] = key;
+      vals_out[pos] = val;
+    }
+    __syncthreads();
+    uint32_t add = 0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+      add += s_wc[q][threadIdx.x];
+      s_wc[q][threadIdx.x] = 0;
+    }
+    s_base[threadIdx.x] += add;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* d_total,
+                       cudaStream_t s) {
+  if (n == 0) {
+    if (d_total) DL_CUDA(cudaMemsetAsync(d_total, 0, sizeof(uint32_t), s));
+    return DETLSH_OK;
+  }
+  const int64_t nb = ceil_div(n, TILE);
+  if (nb == 1) {
+    k_block_scan<<<1, ST, 0, s>>>(in, n, nullptr, out, d_total);
+    DL_LAUNCH();
+    return DETLSH_OK;
+  }
+  Scratch sums, sums_scan;
+  DL_TRY(sums.alloc(sizeof(uint32_t) * nb, s));
+  DL_TRY(sums_scan.alloc(sizeof(uint32_t) * nb, s));
+  k_block_sums<<<(unsigned)nb, ST, 0, s>>>(in, n, sums.as<uint32_t>());
+  DL_LAUNCH();
+  DL_TRY(exclusive_scan_u32(sums.as<uint32_t>(), sums_scan.as<uint32_t>(), nb, nullptr, s));
+  k_block_scan<<<(unsigned)nb, ST, 0, s>>>(in, n, sums_scan.as<uint32_t>(), out, d_total);
+  DL_LAUNCH();
+  return DETLSH_OK;
+}
+
+int radix_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, int64_t n, int bit_lo,
+                     int bit_hi, uint32_t* keys_out, uint32_t* vals_out, cudaStream_t s) {
+  if (n == 0) return DETLSH_OK;
+  const int passes = (bit_hi - bit_lo + 7) / 8;
+  const int64_t n_tiles = ceil_div(n, TILE);
+  Scratch hist, offs, kb, vb;
+  DL_TRY(hist.alloc(sizeof(uint32_t) * 256 * n_tiles, s));
+  DL_TRY(offs.alloc(sizeof(uint32_t) * 256 * n_tiles, s));
+  if (passes > 1) {
+    DL_TRY(kb.alloc(sizeof(uint32_t) * n, s));
+    DL_TRY(vb.alloc(sizeof(uint32_t) * n, s));
+  }
+  // ping-pong so that the last pass lands in keys_out/vals_out
+  const uint32_t* ki = keys_in;
+  const uint32_t* vi = vals_in;
+  for (int p = 0; p < passes; ++p) {
+    const bool last = (p == passes - 1);
+    const bool to_out = ((passes - 1 - p) % 2) == 0;
+    uint32_t* ko = to_out ? keys_out : kb.as<uint32_t>();
+    uint32_t* vo = to_out ? vals_out : vb.as<uint32_t>();
+    const int bit = bit_lo + 8 * p;
+    k_digit_hist<<<(unsigned)n_tiles, ST, 0, s>>>(ki, n, bit, hist.as<uint32_t>(), n_tiles);
+    DL_LAUNCH();
+    DL_TRY(exclusive_scan_u32(hist.as<uint32_t>(), offs.as<uint32_t>(), 256 * n_tiles, nullptr, s));
+    k_digit_scatter<<<(unsigned)n_tiles, ST, 0, s>>>(ki, vi, n, bit, offs.as<uint32_t>(), n_tiles,
+                                                     ko, vo);
+    DL_LAUNCH();
+    ki = ko;
+    vi = vo;
+    (void)last;
+  }
+  return DETLSH_OK;
+}
+
+}  // namespace detlsh
