@@ -5,7 +5,9 @@
 //               (query, leaf) pair. One thread owns one leaf and keeps its box
 //               edges in registers while it loops over a chunk of queries whose
 //               projections sit in shared memory, so the leaf table and the
-//               breakpoints are read once per chunk of queries.
+//               breakpoints are read once per chunk of queries. It also folds
+//               each query's smallest positive and largest bound into two
+//               per-query words (for r_min and the round table).
 // k_search    -- one CTA per query (persistent over the batch). Every leaf is
 //               assigned the first round t whose projected threshold
 //               (eps*r_t)^2 covers its lower bound; leaves are bucketed by
@@ -15,9 +17,10 @@
 //               leaf, in (lower bound, leaf number) order, where |S| reaches
 //               the target -- found by a weighted radix select instead of a
 //               sort. New points are deduplicated in a bitmap, their exact
-//               distances computed warp-cooperatively from HBM, counted per
-//               round for the ">= k within c*r" test, and kept in a pruned
-//               top-k buffer in shared memory.
+//               distances computed warp-cooperatively from HBM (8 rows per warp
+//               in flight, one transposed reduction, the 8 rows' bookkeeping in
+//               8 lanes at once), counted per round for the ">= k within c*r"
+//               test, and kept in a pruned top-k buffer in shared memory.
 #include <algorithm>
 #include <cfloat>
 
@@ -34,8 +37,10 @@ constexpr int LB_QCH = 32;
 __global__ void __launch_bounds__(LB_THREADS)
 k_leaf_lb(const float* __restrict__ qp, int64_t nqb, int LK, const float* __restrict__ E, int Nr,
           int K, const uint8_t* __restrict__ leaf_lo, const uint8_t* __restrict__ leaf_hi,
-          const uint16_t* __restrict__ leaf_tree, int64_t total_leaves, float* __restrict__ lb2) {
+          const uint16_t* __restrict__ leaf_tree, int64_t total_leaves, float* __restrict__ lb2,
+          uint32_t* __restrict__ minpos, uint32_t* __restrict__ maxlb) {
   __shared__ float s_q[LB_QCH][kMaxLK + 1];
+  __shared__ uint32_t s_min[LB_QCH], s_max[LB_QCH];
   const int64_t leaf = (int64_t)blockIdx.x * LB_THREADS + threadIdx.x;
   const int64_t qb0 = (int64_t)blockIdx.y * LB_QCH;
   const int nqc = (int)((nqb - qb0) < LB_QCH ? (nqb - qb0) : LB_QCH);
@@ -43,15 +48,19 @@ k_leaf_lb(const float* __restrict__ qp, int64_t nqb, int LK, const float* __rest
     const int q = i / LK, r = i % LK;
     s_q[q][r] = qp[(qb0 + q) * LK + r];
   }
+  if (threadIdx.x < LB_QCH) {
+    s_min[threadIdx.x] = 0xffffffffu;
+    s_max[threadIdx.x] = 0u;
+  }
   __syncthreads();
-  if (leaf >= total_leaves) return;
-  const int tree = leaf_tree[leaf];
+  const bool valid = leaf < total_leaves;
+  const int tree = valid ? leaf_tree[leaf] : 0;
   float el[kMaxK], eh[kMaxK];
 #pragma unroll
   for (int j = 0; j < kMaxK; ++j) {
     el[j] = -INFINITY;
     eh[j] = INFINITY;
-    if (j < K) {
+    if (valid && j < K) {
       const int r = tree * K + j;
       const int lo = leaf_lo[leaf * K + j], hi = leaf_hi[leaf * K + j];
       if (lo > 0) el[j] = __ldg(E + (int64_t)r * (Nr + 1) + lo);
@@ -71,7 +80,21 @@ k_leaf_lb(const float* __restrict__ qp, int64_t nqb, int LK, const float* __rest
         acc = __fadd_rn(acc, __fmul_rn(dl, dl));
       }
     }
-    lb2[(qb0 + q) * total_leaves + leaf] = acc;
+    if (valid) lb2[(qb0 + q) * total_leaves + leaf] = acc;
+    // non-negative floats order like their bit patterns
+    uint32_t mn = (valid && acc > 0.f) ? __float_as_uint(acc) : 0xffffffffu;
+    uint32_t mx = valid ? __float_as_uint(acc) : 0u;
+    mn = __reduce_min_sync(0xffffffffu, mn);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&s_min[q], mn);
+      atomicMax(&s_max[q], mx);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nqc) {
+    atomicMin(&minpos[qb0 + threadIdx.x], s_min[threadIdx.x]);
+    atomicMax(&maxlb[qb0 + threadIdx.x], s_max[threadIdx.x]);
   }
 }
 
@@ -79,9 +102,10 @@ k_leaf_lb(const float* __restrict__ qp, int64_t nqb, int LK, const float* __rest
 constexpr int ST = 512;           // threads per search CTA
 constexpr int NW = ST / 32;
 constexpr int TK_CAP = 4096;      // top-k buffer entries
-constexpr int QCAP = 2048;        // new-point queue per batch (<= TK_CAP - kMaxTopK)
+constexpr int QCAP = 3072;        // new points per batch (<= TK_CAP - kMaxTopK)
 constexpr int BATCH_LEAVES = ST;  // leaves examined per batch step
-constexpr int ILP = 8;            // rows per warp in flight
+constexpr int ILP = 8;            // rows per warp in flight (the transposed reduction assumes 8)
+static_assert(QCAP + kMaxTopK <= TK_CAP, "top-k buffer too small for a batch");
 
 struct SearchArgs {
   const void* X;
@@ -96,6 +120,8 @@ struct SearchArgs {
   const void* Q;
   int64_t q0, nqb;
   const float* lb2;
+  const uint32_t* minpos;
+  const uint32_t* maxlb;
   const int32_t* k;
   const float* c;
   const float* r_min;
@@ -108,13 +134,15 @@ struct SearchArgs {
   int64_t cand_cap;
   uint32_t* ws_list;
   uint32_t* ws_newcnt;
+  uint8_t* ws_round;
   uint32_t* ws_bitmap;
   int64_t bitmap_words;
   int smem_bitmap;
 };
 
 struct SmemLayout {
-  size_t thrP, thrC, cnt, pts, boff, hist_u, tk, queue, bpref, bleaf, sel, misc, bitmap, total;
+  size_t thrP, thrC, cnt, pts, boff, hist_u, tk, queue, bpref, bleaf, bstart, fmap, sel, misc, bitmap,
+      total;
 };
 
 __host__ __device__ inline SmemLayout search_layout(int L, int64_t smem_bitmap_words) {
@@ -136,6 +164,8 @@ __host__ __device__ inline SmemLayout search_layout(int L, int64_t smem_bitmap_w
   o.queue = take(sizeof(uint32_t) * QCAP);
   o.bpref = take(sizeof(uint32_t) * (BATCH_LEAVES + 1));
   o.bleaf = take(sizeof(uint32_t) * BATCH_LEAVES);
+  o.bstart = take(sizeof(uint32_t) * BATCH_LEAVES);
+  o.fmap = take(sizeof(uint16_t) * QCAP);
   o.sel = take(sizeof(unsigned long long) * 256);
   o.misc = take(sizeof(unsigned long long) * 64);
   o.bitmap = take(sizeof(uint32_t) * (size_t)smem_bitmap_words);
@@ -145,15 +175,9 @@ __host__ __device__ inline SmemLayout search_layout(int L, int64_t smem_bitmap_w
 
 // misc slots (unsigned long long each)
 enum {
-  M_S = 0, M_T, M_TAU, M_TKN, M_QN, M_STOP, M_TLAST, M_TCAP, M_RU, M_MINPOS, M_MAXLB,
-  M_NEED, M_KSTAR, M_ACC, M_TOTNEW, M_BCOUNT, M_BPTS, M_LEAFA, M_OFFA, M_TMP
+  M_S = 0, M_T, M_TAU, M_TKN, M_QN, M_STOP, M_TLAST, M_TCAP, M_RU, M_NEED, M_KSTAR, M_ACC,
+  M_TOTNEW, M_LEAFA, M_OFFA
 };
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // index of the first element >= v in a non-decreasing array (n if none)
 __device__ __forceinline__ int lower_bound_f(const float* a, int n, float v) {
@@ -190,7 +214,7 @@ __device__ void sort_topk(unsigned long long* tk) {
 // once k keys are held.
 __device__ void prune_topk(unsigned long long* tk, unsigned long long* misc, int k) {
   __syncthreads();
-  const int cnt = (int)misc[M_TKN];
+  const int cnt = (int)min(misc[M_TKN], (unsigned long long)TK_CAP);
   for (int i = cnt + threadIdx.x; i < TK_CAP; i += ST) tk[i] = ~0ull;
   sort_topk(tk);
   if (threadIdx.x == 0) {
@@ -265,6 +289,32 @@ __device__ __forceinline__ void rows_dist2(const TX* __restrict__ X, int d,
   }
 }
 
+// Sum 8 per-lane partials over the warp so that lane l ends with the total of
+// row (l >> 2) & 7: three halving exchanges (16, 8, 4) each keep half of the
+// rows, then two plain butterfly steps.
+__device__ __forceinline__ float transpose_reduce8(const float* acc, int lane) {
+  float a4[4], a2[2];
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = b4 ? acc[i] : acc[i + 4];
+    const float keep = b4 ? acc[i + 4] : acc[i];
+    a4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = b3 ? a4[i] : a4[i + 2];
+    const float keep = b3 ? a4[i + 2] : a4[i];
+    a2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const float send = b2 ? a2[0] : a2[1];
+  const float keep = b2 ? a2[1] : a2[0];
+  float v = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
 // Add the points of bucket leaves list[0..nl) (only leaves whose select key is
 // <= kstar when filtered) to S. Runs in batches of at most QCAP points: the
 // batch's points are tested-and-set in the bitmap, the new ones queued, then
@@ -279,12 +329,14 @@ __device__ void add_leaves(const SearchArgs& a, const TX* __restrict__ X, const 
   unsigned long long* tk = reinterpret_cast<unsigned long long*>(sm + ly.tk);
   uint32_t* queue = reinterpret_cast<uint32_t*>(sm + ly.queue);
   uint32_t* bpref = reinterpret_cast<uint32_t*>(sm + ly.bpref);
-  uint32_t* bleaf = reinterpret_cast<uint32_t*>(sm + ly.bleaf);
+  uint32_t* bstart = reinterpret_cast<uint32_t*>(sm + ly.bstart);
+  uint16_t* fmap = reinterpret_cast<uint16_t*>(sm + ly.fmap);
   uint32_t* hist_u = reinterpret_cast<uint32_t*>(sm + ly.hist_u);
   const float* thrC = reinterpret_cast<const float*>(sm + ly.thrC);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   const uint32_t* tree_ids = a.leaf_ids + (int64_t)tree * a.n;
+  __shared__ uint32_t s_w[NW];
 
   if (threadIdx.x == 0) {
     misc[M_LEAFA] = 0;
@@ -297,9 +349,10 @@ __device__ void add_leaves(const SearchArgs& a, const TX* __restrict__ X, const 
     if (la >= nl) break;
     // --- batch: leaves [la, la+nb) with their (filtered) counts, the first one from offa
     const uint32_t nb = min((uint32_t)BATCH_LEAVES, nl - la);
-    uint32_t cnt = 0, leaf = 0;
+    uint32_t cnt = 0;
     if (threadIdx.x < nb) {
-      leaf = list[la + threadIdx.x];
+      const uint32_t leaf = list[la + threadIdx.x];
+      const uint32_t st = a.leaf_range[2 * (int64_t)leaf];
       cnt = a.leaf_range[2 * (int64_t)leaf + 1];
       if (filtered) {
         const unsigned long long key =
@@ -307,7 +360,7 @@ __device__ void add_leaves(const SearchArgs& a, const TX* __restrict__ X, const 
         if (key > kstar) cnt = 0;
       }
       if (threadIdx.x == 0) cnt = cnt >= offa ? cnt - offa : 0u;
-      bleaf[threadIdx.x] = leaf;
+      bstart[threadIdx.x] = st + (threadIdx.x == 0 ? offa : 0u);
     }
     // inclusive scan of cnt over the block (ST == BATCH_LEAVES)
     uint32_t x = cnt;
@@ -316,20 +369,17 @@ __device__ void add_leaves(const SearchArgs& a, const TX* __restrict__ X, const 
       const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
-    __shared__ uint32_t s_w[NW];
     if (lane == 31) s_w[w] = x;
     __syncthreads();
     uint32_t wb = 0;
     for (int qq = 0; qq < w; ++qq) wb += s_w[qq];
-    const uint32_t incl = wb + x;
-    bpref[threadIdx.x + 1] = incl;   // bpref[j] = points before leaf j of the batch
+    bpref[threadIdx.x + 1] = wb + x;   // bpref[j] = points before leaf j of the batch
     if (threadIdx.x == 0) bpref[0] = 0;
     __syncthreads();
     // batch extent: whole leaves while they fit in QCAP points, at least one (partially)
     uint32_t take_leaves, take_pts;
     {
-      // largest j with bpref[j] <= QCAP
-      int lo = 0, hi = (int)nb;
+      int lo = 0, hi = (int)nb;   // largest j with bpref[j] <= QCAP
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (bpref[mid] <= (uint32_t)QCAP) lo = mid;
@@ -338,6 +388,12 @@ __device__ void add_leaves(const SearchArgs& a, const TX* __restrict__ X, const 
       take_leaves = (uint32_t)lo;
       take_pts = bpref[lo];
       if (take_leaves == 0) take_pts = min(bpref[1], (uint32_t)QCAP);
+    }
+    // flat point -> batch leaf map (a warp per leaf)
+    const uint32_t map_leaves = take_leaves == 0 ? 1u : take_leaves;
+    for (uint32_t j = (uint32_t)w; j < map_leaves; j += NW) {
+      const uint32_t e = min(bpref[j + 1], take_pts);
+      for (uint32_t f = bpref[j] + lane; f < e; f += 32) fmap[f] = (uint16_t)j;
     }
     // make room in the top-k buffer for up to take_pts insertions
     if (misc[M_TKN] + take_pts > TK_CAP) prune_topk(tk, misc, kq);
@@ -349,16 +405,8 @@ __device__ void add_leaves(const SearchArgs& a, const TX* __restrict__ X, const 
       bool fresh = false;
       uint32_t id = 0;
       if (f < take_pts) {
-        // leaf j of the batch holding flat point f
-        int lo = 0, hi = (int)nb - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (bpref[mid] <= f) lo = mid;
-          else hi = mid - 1;
-        }
-        const uint32_t lf = bleaf[lo];
-        const uint32_t within = f - bpref[lo] + (lo == 0 ? offa : 0u);
-        id = tree_ids[a.leaf_range[2 * (int64_t)lf] + within];
+        const uint32_t j = fmap[f];
+        id = tree_ids[bstart[j] + (f - bpref[j])];
         const uint32_t bit = 1u << (id & 31);
         const uint32_t old = atomicOr(bitmap + (id >> 5), bit);
         fresh = !(old & bit);
@@ -372,7 +420,8 @@ __device__ void add_leaves(const SearchArgs& a, const TX* __restrict__ X, const 
     __syncthreads();
     const uint32_t qn = (uint32_t)misc[M_QN];
     const unsigned long long S_before = misc[M_S];
-    // --- phase B: exact distances of the queued points
+    const unsigned long long tau = misc[M_TAU];
+    // --- phase B: exact distances of the queued points, 8 rows per warp
     for (uint32_t e0 = (uint32_t)w * ILP; e0 < qn; e0 += NW * ILP) {
       float acc[ILP];
       uint32_t ids[ILP];
@@ -382,22 +431,20 @@ __device__ void add_leaves(const SearchArgs& a, const TX* __restrict__ X, const 
         acc[u] = 0.f;
       }
       rows_dist2<TX>(X, a.d, ids, q, vec4, lane, acc);
-#pragma unroll
-      for (int u = 0; u < ILP; ++u) {
-        const float d2 = warp_sum(acc[u]);
-        if (lane == u && ids[u] != 0xffffffffu) {
-          const int uu = lower_bound_f(thrC, Ru, d2);
-          atomicAdd(&hist_u[min(uu, kRoundCap)], 1u);
-          const unsigned long long key =
-              ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned long long)ids[u];
-          if (key < misc[M_TAU]) {
-            const unsigned long long slot = atomicAdd(&misc[M_TKN], 1ull);
-            if (slot < TK_CAP) tk[slot] = key;
-          }
-          if (a.cand_ids) {
-            const unsigned long long pos = S_before + e0 + u;
-            if ((int64_t)pos < a.cand_cap) a.cand_ids[qglob * a.cand_cap + (int64_t)pos] = ids[u];
-          }
+      const float d2 = transpose_reduce8(acc, lane);
+      const uint32_t r = (uint32_t)(lane >> 2) & 7u;
+      if ((lane & 3) == 0 && e0 + r < qn) {
+        const uint32_t id = queue[e0 + r];
+        const int uu = lower_bound_f(thrC, Ru, d2);
+        atomicAdd(&hist_u[min(uu, kRoundCap)], 1u);
+        const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | id;
+        if (key < tau) {
+          const unsigned long long slot = atomicAdd(&misc[M_TKN], 1ull);
+          if (slot < TK_CAP) tk[slot] = key;
+        }
+        if (a.cand_ids) {
+          const unsigned long long pos = S_before + e0 + r;
+          if ((int64_t)pos < a.cand_cap) a.cand_ids[qglob * a.cand_cap + (int64_t)pos] = id;
         }
       }
     }
@@ -441,15 +488,17 @@ __global__ void __launch_bounds__(ST, 1) k_search(SearchArgs a) {
                                    : a.ws_bitmap + (int64_t)blockIdx.x * a.bitmap_words;
   uint32_t* list = a.ws_list + (int64_t)blockIdx.x * a.total_leaves;
   uint32_t* newcnt = a.ws_newcnt + (int64_t)blockIdx.x * a.total_leaves;
+  uint8_t* lround = a.ws_round + (int64_t)blockIdx.x * a.total_leaves;
   const TX* X = static_cast<const TX*>(a.X);
   const int L = a.L;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __shared__ float s_red_f[NW];
-  __shared__ float s_red_f2[NW];
+  const uint32_t lt = (1u << lane) - 1u;
   __shared__ unsigned long long s_red_u[NW];
   const bool vec4 = (a.d % 4 == 0) &&
                     (reinterpret_cast<uintptr_t>(a.X) % (sizeof(TX) == 4 ? 16 : 4) == 0) &&
                     (reinterpret_cast<uintptr_t>(a.Q) % (sizeof(TX) == 4 ? 16 : 4) == 0);
+  // every lane of a warp runs the same number of leaf iterations (warp-aggregated atomics)
+  const int64_t leaf_iters = (a.total_leaves + ST - 1) / ST * ST;
 
   for (int64_t qb = blockIdx.x; qb < a.nqb; qb += gridDim.x) {
     const int64_t qg = a.q0 + qb;
@@ -469,33 +518,11 @@ __global__ void __launch_bounds__(ST, 1) k_search(SearchArgs a) {
       misc[M_TAU] = ~0ull;
       misc[M_STOP] = 0;
       misc[M_TLAST] = 0;
-    }
-    // ---- pass 1: smallest positive and largest lower bound
-    float mn = INFINITY, mx = 0.f;
-    for (int64_t l = threadIdx.x; l < a.total_leaves; l += ST) {
-      const float v = lbrow[l];
-      if (v > 0.f) mn = fminf(mn, v);
-      mx = fmaxf(mx, v);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
-    if (lane == 0) {
-      s_red_f[w] = mn;
-      s_red_f2[w] = mx;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float m1 = INFINITY, m2 = 0.f;
-      for (int i = 0; i < NW; ++i) {
-        m1 = fminf(m1, s_red_f[i]);
-        m2 = fmaxf(m2, s_red_f2[i]);
-      }
       // Alg. 7 thresholds: r_0 = r_min, r_{t+1} = c * r_t (FP64), rounded once to FP32
+      const uint32_t mnb = a.minpos[qb];
+      const float m2 = __uint_as_float(a.maxlb[qb]);
       double r = (double)a.r_min[qg];
-      if (!(r > 0.0)) r = (m1 < INFINITY) ? sqrt((double)m1) / a.eps : 1.0;
+      if (!(r > 0.0)) r = (mnb != 0xffffffffu) ? sqrt((double)__uint_as_float(mnb)) / a.eps : 1.0;
       const double cq = (double)a.c[qg];
       int Ru = kRoundCap;
       for (int t = 0; t < kRoundCap; ++t) {
@@ -519,17 +546,26 @@ __global__ void __launch_bounds__(ST, 1) k_search(SearchArgs a) {
     __syncthreads();
     const int Ru = (int)misc[M_RU];
     const unsigned long long T = misc[M_T];
-    // ---- pass 2: round of each leaf; histogram per (round, tree)
+    // ---- pass A: round of each leaf; histogram per (round, tree), warp-aggregated
     uint32_t tl = 0;
-    for (int64_t l = threadIdx.x; l < a.total_leaves; l += ST) {
-      const int t = lower_bound_f(thrP, Ru, lbrow[l]);
-      const int tree = a.leaf_tree[l];
-      atomicAdd(&s_cnt[t * L + tree], 1u);
-      atomicAdd(&s_pts[t * L + tree], a.leaf_range[2 * l + 1]);
-      tl = max(tl, (uint32_t)t);
+    for (int64_t l = threadIdx.x; l < leaf_iters; l += ST) {
+      const bool valid = l < a.total_leaves;
+      uint32_t key = 0xffffffffu, pts = 0;
+      if (valid) {
+        const int t = lower_bound_f(thrP, Ru, lbrow[l]);
+        lround[l] = (uint8_t)t;
+        key = (uint32_t)(t * L + a.leaf_tree[l]);
+        pts = a.leaf_range[2 * l + 1];
+        tl = max(tl, (uint32_t)t);
+      }
+      const uint32_t peers = __match_any_sync(0xffffffffu, key);
+      const uint32_t sum = __reduce_add_sync(peers, pts);
+      if (valid && (peers & lt) == 0) {
+        atomicAdd(&s_cnt[key], (uint32_t)__popc(peers));
+        atomicAdd(&s_pts[key], sum);
+      }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tl = max(tl, __shfl_xor_sync(0xffffffffu, tl, o));
+    tl = __reduce_max_sync(0xffffffffu, tl);
     if (lane == 0) atomicMax(&misc[M_TLAST], (unsigned long long)tl);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -555,19 +591,25 @@ __global__ void __launch_bounds__(ST, 1) k_search(SearchArgs a) {
     __syncthreads();
     const int tcap = (int)misc[M_TCAP];
     const int tlast = (int)misc[M_TLAST];
-    // ---- pass 3: bucket the leaves of rounds <= tcap (s_pts reused as cursors)
     // s_cnt now keeps each bucket's point total, s_pts becomes the insertion cursor
     for (int i = threadIdx.x; i < (tcap + 1) * L; i += ST) {
       s_cnt[i] = s_pts[i];
       s_pts[i] = s_boff[i];
     }
     __syncthreads();
-    for (int64_t l = threadIdx.x; l < a.total_leaves; l += ST) {
-      const int t = lower_bound_f(thrP, Ru, lbrow[l]);
-      if (t <= tcap) {
-        const uint32_t slot = atomicAdd(&s_pts[t * L + a.leaf_tree[l]], 1u);
-        list[slot] = (uint32_t)l;
+    // ---- pass B: bucket the leaves of rounds <= tcap
+    for (int64_t l = threadIdx.x; l < leaf_iters; l += ST) {
+      uint32_t key = 0xffffffffu;
+      if (l < a.total_leaves) {
+        const int t = lround[l];
+        if (t <= tcap) key = (uint32_t)(t * L + a.leaf_tree[l]);
       }
+      const uint32_t peers = __match_any_sync(0xffffffffu, key);
+      const int leader = __ffs(peers) - 1;
+      uint32_t base = 0;
+      if (key != 0xffffffffu && lane == leader) base = atomicAdd(&s_pts[key], (uint32_t)__popc(peers));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (key != 0xffffffffu) list[base + __popc(peers & lt)] = (uint32_t)l;
     }
     __syncthreads();
     // ---- walk the buckets in Alg. 7 order
@@ -594,8 +636,7 @@ __global__ void __launch_bounds__(ST, 1) k_search(SearchArgs a) {
               const uint32_t id = ids[e];
               nw += (bitmap[id >> 5] >> (id & 31)) & 1u ? 0u : 1u;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) nw += __shfl_xor_sync(0xffffffffu, nw, o);
+            nw = __reduce_add_sync(0xffffffffu, nw);
             if (lane == 0) newcnt[j] = nw;
             tot += nw;
           }
@@ -717,12 +758,12 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
                           s));
   tm.end();
 
-  // search configuration
+  // search configuration (static shared memory of the kernel: < 1 KiB)
   const int64_t words = (idx->n + 31) / 32;
   const SmemLayout base = search_layout(idx->L, 0);
-  const bool smem_bitmap = (int64_t)base.total + words * 4 + 64 <= (int64_t)smem_optin;
+  const bool smem_bitmap = (int64_t)base.total + words * 4 + 1024 <= (int64_t)smem_optin;
   const SmemLayout ly = search_layout(idx->L, smem_bitmap ? words : 0);
-  if ((int64_t)ly.total > smem_optin) {
+  if ((int64_t)ly.total + 1024 > smem_optin) {
     set_error("search kernel needs %zu bytes of shared memory", ly.total);
     return DETLSH_EINVAL;
   }
@@ -731,22 +772,28 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
   int64_t qb = std::max<int64_t>(1, std::min<int64_t>(nq, ((int64_t)2 << 30) / std::max<int64_t>(per_q, 1)));
   qb = std::min<int64_t>(qb, 8192);
   const int grid = (int)std::min<int64_t>(qb, nsm);
-  Scratch lb, ws_list, ws_new, ws_bm;
+  Scratch lb, mm, ws_list, ws_new, ws_round, ws_bm;
   DL_TRY(lb.alloc(sizeof(float) * qb * idx->total_leaves, s));
+  DL_TRY(mm.alloc(sizeof(uint32_t) * 2 * qb, s));
   DL_TRY(ws_list.alloc(sizeof(uint32_t) * grid * idx->total_leaves, s));
   DL_TRY(ws_new.alloc(sizeof(uint32_t) * grid * idx->total_leaves, s));
+  DL_TRY(ws_round.alloc((size_t)grid * idx->total_leaves, s));
   if (!smem_bitmap) DL_TRY(ws_bm.alloc(sizeof(uint32_t) * grid * words, s));
+  uint32_t* d_min = mm.as<uint32_t>();
+  uint32_t* d_max = d_min + qb;
 
   auto kern = idx->dtype == DETLSH_U8 ? k_search<uint8_t> : k_search<float>;
   DL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ly.total));
 
   for (int64_t q0 = 0; q0 < nq; q0 += qb) {
     const int64_t nqb = std::min<int64_t>(qb, nq - q0);
+    DL_CUDA(cudaMemsetAsync(d_min, 0xff, sizeof(uint32_t) * nqb, s));
+    DL_CUDA(cudaMemsetAsync(d_max, 0x00, sizeof(uint32_t) * nqb, s));
     dim3 g1(ceil_div(idx->total_leaves, LB_THREADS), ceil_div(nqb, LB_QCH));
     tm.begin(TR_LB);
     k_leaf_lb<<<g1, LB_THREADS, 0, s>>>(qp.as<float>() + q0 * LK, nqb, LK, idx->E, idx->Nr, idx->K,
                                         idx->leaf_lo, idx->leaf_hi, idx->leaf_tree,
-                                        idx->total_leaves, lb.as<float>());
+                                        idx->total_leaves, lb.as<float>(), d_min, d_max);
     DL_LAUNCH();
     tm.end();
     trace_add(TR_LB_LAUNCHES, 1.0);
@@ -766,6 +813,8 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
     sa.q0 = q0;
     sa.nqb = nqb;
     sa.lb2 = lb.as<float>();
+    sa.minpos = d_min;
+    sa.maxlb = d_max;
     sa.k = k;
     sa.c = c;
     sa.r_min = r_min;
@@ -779,6 +828,7 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
     sa.cand_cap = cand_cap;
     sa.ws_list = ws_list.as<uint32_t>();
     sa.ws_newcnt = ws_new.as<uint32_t>();
+    sa.ws_round = ws_round.as<uint8_t>();
     sa.ws_bitmap = smem_bitmap ? nullptr : ws_bm.as<uint32_t>();
     sa.bitmap_words = words;
     sa.smem_bitmap = smem_bitmap ? 1 : 0;
