@@ -255,10 +255,15 @@ def gpu_arm(args, rank, world, local_rank):
     mean_S = float(stats[:, 0].astype("float64").mean())
     s_in = 4
     total_leaves = info["total_leaves"]
-    search_bytes = float(stats[:, 0].astype("float64").sum()) * (w["d"] * s_in + 4) + nq * total_leaves * 4.0
     enc_bytes = w["n"] * (w["d"] * s_in + w["K"] * w["L"])
+    # algorithmic bytes per step of each query kernel: the candidate rows and
+    # ids (k_dist), the lower-bound rows plus leaf ids (k_walk), the candidate
+    # distances and ids (k_finalize), the leaf table and lower bounds (k_leaf_lb)
+    n_cand = float(stats[:, 0].astype("float64").sum())
     cand = {
-        "k_search": (search_bytes, ph["search_ms"], ph["search_launches"]),
+        "k_dist": (n_cand * (w["d"] * s_in + 4 + 4), ph["dist_ms"], ph["dist_launches"]),
+        "k_walk": (nq * total_leaves * 4.0 + n_cand * 8, ph["walk_ms"], ph["dist_launches"]),
+        "k_finalize": (n_cand * 8.0, ph["finalize_ms"], ph["dist_launches"]),
         "k_project_encode": (enc_bytes, ph["encode_ms"], 1.0),
         "k_leaf_lb": (nq * total_leaves * 4.0 + ph["lb_launches"] * total_leaves * (2 * w["K"] + 10.0),
                       ph["lb_ms"], ph["lb_launches"]),

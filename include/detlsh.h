@@ -124,7 +124,8 @@ int detlsh_build(const void* X, int64_t n, int32_t d, int32_t dtype,
  *   out_dist    [nq][k_max] FP32 Euclidean distances (+inf padding).
  *   out_stats   optional [nq][4] int32: |S| at termination, rounds started,
  *               stop rule (1: |S| >= beta*n+k, 2: >= k candidates within c*r,
- *               3: every leaf active), reserved 0.
+ *               3: every leaf active), and 0 (1 would flag an internal
+ *               candidate-list overflow, which the list's sizing excludes).
  * Errors: DETLSH_EINVAL (bad sizes/parameters, dtype differs from the index),
  * DETLSH_ENOMEM, DETLSH_ECUDA.
  */
@@ -202,8 +203,10 @@ double detlsh_eps_lemma3(int32_t K, int32_t L);
  * detlsh_trace_get -- device milliseconds of the last build and the last query
  *   on this thread: out[0] sample projection, [1] breakpoint selection,
  *   [2] fused projection+encoding, [3] DE-Tree leaves, [4] query projection,
- *   [5] leaf lower bounds, [6] search kernels, [7] number of search launches,
- *   [8] number of lower-bound launches, [9] whole build, [10] whole query.
+ *   [5] leaf lower bounds, [6] candidate distances, [7] number of distance
+ *   launches, [8] number of lower-bound launches, [9] whole build, [10] whole
+ *   query, [11] bucket walks, [12] stop test and top-k, [13] round table,
+ *   leaf rounds and bucket lists.
  *   Returns the number of entries written (<= len).
  * detlsh_launch_count -- kernels this library has launched in the process.
  */

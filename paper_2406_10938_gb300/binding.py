@@ -31,7 +31,8 @@ SYMBOLS = ("detlsh_build", "detlsh_query", "detlsh_free", "detlsh_export_size", 
            "detlsh_eps_lemma3", "detlsh_strerror", "detlsh_last_error", "detlsh_trace_enable",
            "detlsh_trace_get", "detlsh_launch_count")
 TRACE_KEYS = ("sample_proj_ms", "breakpoints_ms", "encode_ms", "leaves_ms", "query_proj_ms", "lb_ms",
-              "search_ms", "search_launches", "lb_launches", "build_ms", "query_ms")
+              "dist_ms", "dist_launches", "lb_launches", "build_ms", "query_ms", "walk_ms", "finalize_ms",
+              "bucket_ms")
 
 
 class DetlshError(RuntimeError):

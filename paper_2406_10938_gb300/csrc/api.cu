@@ -349,7 +349,7 @@ int detlsh_query(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dty
     DL_TRY(check_flag(bad.as<int>(), s, "each query needs 1 <= k <= k_max, finite c > 1, finite r_min"));
   }
   trace_reset(TR_QUERY_PROJ, TR_LB_LAUNCHES);
-  trace_reset(TR_QUERY_TOTAL, TR_QUERY_TOTAL);
+  trace_reset(TR_QUERY_TOTAL, TR_BUCKET);
   PhaseTimer total(s);
   total.begin(TR_QUERY_TOTAL);
   Out oi, od, os, oc;

@@ -22,8 +22,9 @@ void count_launch();
 
 // Per-phase device times of the last build/query on this thread (tracing).
 enum TracePhase {
-  TR_SAMPLE_PROJ = 0, TR_BREAKPOINTS, TR_ENCODE, TR_LEAVES, TR_QUERY_PROJ, TR_LB, TR_SEARCH,
-  TR_SEARCH_LAUNCHES, TR_LB_LAUNCHES, TR_BUILD_TOTAL, TR_QUERY_TOTAL, TR_COUNT
+  TR_SAMPLE_PROJ = 0, TR_BREAKPOINTS, TR_ENCODE, TR_LEAVES, TR_QUERY_PROJ, TR_LB, TR_DIST,
+  TR_DIST_LAUNCHES, TR_LB_LAUNCHES, TR_BUILD_TOTAL, TR_QUERY_TOTAL, TR_WALK, TR_FINALIZE, TR_BUCKET,
+  TR_COUNT
 };
 bool trace_on();
 void trace_reset(int first, int last);

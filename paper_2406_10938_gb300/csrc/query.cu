@@ -1,26 +1,33 @@
 // Query phase: Alg. 7 (c^2-k-ANN) with the optimised range query of
-// Sec. 6.2.2, for a batch of queries.
+// Sec. 6.2.2, for a batch of queries, in four kernels.
 //
-// k_leaf_lb   -- the squared lower-bound distance (Alg. 5, first step) of every
+// k_leaf_lb   -- squared lower-bound distance (Alg. 5, first step) of every
 //               (query, leaf) pair. One thread owns one leaf and keeps its box
 //               edges in registers while it loops over a chunk of queries whose
-//               projections sit in shared memory, so the leaf table and the
-//               breakpoints are read once per chunk of queries. It also folds
-//               each query's smallest positive and largest bound into two
-//               per-query words (for r_min and the round table).
-// k_search    -- one CTA per query (persistent over the batch). Every leaf is
-//               assigned the first round t whose projected threshold
-//               (eps*r_t)^2 covers its lower bound; leaves are bucketed by
-//               (round, tree). Buckets are visited in Alg. 7's order; a bucket
-//               that cannot reach |S| >= beta*n+k is added whole (order inside
-//               it does not change S), the one that can is cut at the first
-//               leaf, in (lower bound, leaf number) order, where |S| reaches
-//               the target -- found by a weighted radix select instead of a
-//               sort. New points are deduplicated in a bitmap, their exact
-//               distances computed warp-cooperatively from HBM (8 rows per warp
-//               in flight, one transposed reduction, the 8 rows' bookkeeping in
-//               8 lanes at once), counted per round for the ">= k within c*r"
-//               test, and kept in a pruned top-k buffer in shared memory.
+//               projections sit in shared memory; it also folds each query's
+//               smallest positive and largest bound into two per-query words.
+// k_walk      -- one CTA per query. Each leaf gets the first round t whose
+//               projected threshold (eps*r_t)^2 covers its lower bound; leaves
+//               are bucketed by (round, tree) and the buckets visited in
+//               Alg. 7's order. A bucket that cannot bring |S| to beta*n+k is
+//               taken whole (order inside it does not change S); the one that
+//               can is cut at the first leaf, in (lower bound, leaf number)
+//               order, where |S| reaches it, found by a weighted radix select.
+//               New points (deduplicated in a bitmap) are appended to the
+//               query's candidate list with the round boundaries. The walk
+//               needs no distances because it only applies the |S| >= beta*n+k
+//               rule and the every-leaf-active rule.
+// k_dist      -- the exact FP32 squared distance of every listed candidate: a
+//               pure row gather from HBM, 8 rows per warp in flight, many warps
+//               per SM.
+// k_finalize  -- one CTA per query. Replays the ">= k candidates within c*r"
+//               rule of Alg. 7 after each completed round from the distances
+//               and insertion rounds; where it fires first, S is the list's
+//               prefix up to that round. Then the k nearest of S by
+//               (distance, id) through a pruned top-k buffer.
+// The result equals the sequential walk: the rule that needs distances can
+// only end the walk at a round boundary, and S at a round boundary is a
+// prefix of the list.
 #include <algorithm>
 #include <cfloat>
 
@@ -98,87 +105,6 @@ k_leaf_lb(const float* __restrict__ qp, int64_t nqb, int LK, const float* __rest
   }
 }
 
-// ------------------------------------------------------------------ search
-constexpr int ST = 512;           // threads per search CTA
-constexpr int NW = ST / 32;
-constexpr int TK_CAP = 4096;      // top-k buffer entries
-constexpr int QCAP = 3072;        // new points per batch (<= TK_CAP - kMaxTopK)
-constexpr int BATCH_LEAVES = ST;  // leaves examined per batch step
-constexpr int ILP = 8;            // rows per warp in flight (the transposed reduction assumes 8)
-static_assert(QCAP + kMaxTopK <= TK_CAP, "top-k buffer too small for a batch");
-
-struct SearchArgs {
-  const void* X;
-  int dtype;
-  int64_t n;
-  int d;
-  int K, L, Nr;
-  const uint32_t* leaf_ids;
-  const uint32_t* leaf_range;
-  const uint16_t* leaf_tree;
-  int64_t total_leaves;
-  const void* Q;
-  int64_t q0, nqb;
-  const float* lb2;
-  const uint32_t* minpos;
-  const uint32_t* maxlb;
-  const int32_t* k;
-  const float* c;
-  const float* r_min;
-  double eps, beta;
-  int k_max;
-  int64_t* out_ids;
-  float* out_dist;
-  int32_t* out_stats;
-  uint32_t* cand_ids;
-  int64_t cand_cap;
-  uint32_t* ws_list;
-  uint32_t* ws_newcnt;
-  uint8_t* ws_round;
-  uint32_t* ws_bitmap;
-  int64_t bitmap_words;
-  int smem_bitmap;
-};
-
-struct SmemLayout {
-  size_t thrP, thrC, cnt, pts, boff, hist_u, tk, queue, bpref, bleaf, bstart, fmap, sel, misc, bitmap,
-      total;
-};
-
-__host__ __device__ inline SmemLayout search_layout(int L, int64_t smem_bitmap_words) {
-  SmemLayout o{};
-  size_t p = 0;
-  auto take = [&](size_t bytes) {
-    const size_t at = p;
-    p += (bytes + 15) & ~size_t(15);
-    return at;
-  };
-  const size_t RL = (size_t)kRoundCap * L;
-  o.thrP = take(sizeof(float) * kRoundCap);
-  o.thrC = take(sizeof(float) * kRoundCap);
-  o.cnt = take(sizeof(uint32_t) * RL);
-  o.pts = take(sizeof(uint32_t) * RL);
-  o.boff = take(sizeof(uint32_t) * (RL + 1));
-  o.hist_u = take(sizeof(uint32_t) * (kRoundCap + 1));
-  o.tk = take(sizeof(unsigned long long) * TK_CAP);
-  o.queue = take(sizeof(uint32_t) * QCAP);
-  o.bpref = take(sizeof(uint32_t) * (BATCH_LEAVES + 1));
-  o.bleaf = take(sizeof(uint32_t) * BATCH_LEAVES);
-  o.bstart = take(sizeof(uint32_t) * BATCH_LEAVES);
-  o.fmap = take(sizeof(uint16_t) * QCAP);
-  o.sel = take(sizeof(unsigned long long) * 256);
-  o.misc = take(sizeof(unsigned long long) * 64);
-  o.bitmap = take(sizeof(uint32_t) * (size_t)smem_bitmap_words);
-  o.total = p;
-  return o;
-}
-
-// misc slots (unsigned long long each)
-enum {
-  M_S = 0, M_T, M_TAU, M_TKN, M_QN, M_STOP, M_TLAST, M_TCAP, M_RU, M_NEED, M_KSTAR, M_ACC,
-  M_TOTNEW, M_LEAFA, M_OFFA
-};
-
 // index of the first element >= v in a non-decreasing array (n if none)
 __device__ __forceinline__ int lower_bound_f(const float* a, int n, float v) {
   int lo = 0, hi = n;
@@ -190,40 +116,521 @@ __device__ __forceinline__ int lower_bound_f(const float* a, int n, float v) {
   return lo;
 }
 
-// Bitonic sort of TK_CAP keys ascending (block-wide).
-__device__ void sort_topk(unsigned long long* tk) {
-  for (int size = 2; size <= TK_CAP; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      __syncthreads();
-      for (int i = threadIdx.x; i < TK_CAP / 2; i += ST) {
-        const int lo = 2 * i - (i & (stride - 1));
-        const int hi = lo + stride;
-        const bool up = ((lo & size) == 0);
-        const unsigned long long a = tk[lo], b = tk[hi];
-        if ((a > b) == up) {
-          tk[lo] = b;
-          tk[hi] = a;
+// index of the first element > v in a non-decreasing array (n if none)
+__device__ __forceinline__ int upper_bound_u(const uint32_t* a, int n, uint32_t v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] <= v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// per-query words of the pipeline (uint32)
+enum {
+  MQ_RU = 0,      // rounds in the threshold table
+  MQ_T_LO,        // T = ceil(beta*n + k), low and high words
+  MQ_T_HI,
+  MQ_TLAST,       // last round in which some leaf activates
+  MQ_TCAP,        // last round the walk can reach
+  MQ_NS,          // candidates listed by the walk
+  MQ_TEND,        // round in which the walk ended
+  MQ_STOP,        // 1: |S| >= T, 3: every leaf active
+  MQ_OVERFLOW,    // candidate list overflow (never expected)
+  MQ_WORDS = 16
+};
+
+// ------------------------------------------------------------------ round table
+// One thread per query: r_0 = r_min (or sqrt(smallest positive lower bound)/eps),
+// r_{t+1} = c * r_t in FP64; (eps*r_t)^2 and (c*r_t)^2 rounded once to FP32; the
+// table ends at the first round covering every leaf, or at the round cap with
+// infinite thresholds.
+__global__ void k_thresh(const uint32_t* __restrict__ minpos, const uint32_t* __restrict__ maxlb,
+                         int64_t q0, int64_t nqb, const int32_t* __restrict__ k,
+                         const float* __restrict__ c, const float* __restrict__ r_min, double eps,
+                         double beta, int64_t n, float* __restrict__ thrP, float* __restrict__ thrC,
+                         uint32_t* __restrict__ meta) {
+  const int64_t qb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (qb >= nqb) return;
+  const int64_t qg = q0 + qb;
+  float* tp = thrP + qb * kRoundCap;
+  float* tc = thrC + qb * kRoundCap;
+  const uint32_t mnb = minpos[qb];
+  const float m2 = __uint_as_float(maxlb[qb]);
+  double r = (double)r_min[qg];
+  if (!(r > 0.0)) r = (mnb != 0xffffffffu) ? sqrt((double)__uint_as_float(mnb)) / eps : 1.0;
+  const double cq = (double)c[qg];
+  int Ru = kRoundCap;
+  for (int t = 0; t < kRoundCap; ++t) {
+    if (t == kRoundCap - 1) {
+      tp[t] = INFINITY;
+      tc[t] = INFINITY;
+      break;
+    }
+    const double er = __dmul_rn(eps, r), cr = __dmul_rn(cq, r);
+    tp[t] = __double2float_rn(__dmul_rn(er, er));
+    tc[t] = __double2float_rn(__dmul_rn(cr, cr));
+    r = __dmul_rn(r, cq);
+    if (tp[t] >= m2) {
+      Ru = t + 1;
+      break;
+    }
+  }
+  const unsigned long long T =
+      (unsigned long long)ceil(__dadd_rn(__dmul_rn(beta, (double)n), (double)k[qg]));
+  uint32_t* m = meta + qb * MQ_WORDS;
+  m[MQ_RU] = (uint32_t)Ru;
+  m[MQ_T_LO] = (uint32_t)(T & 0xffffffffull);
+  m[MQ_T_HI] = (uint32_t)(T >> 32);
+  m[MQ_TLAST] = 0;
+}
+
+// ------------------------------------------------------------------ buckets
+// One CTA per query, many CTAs per SM: pass A gives every leaf its first round
+// t with (eps*r_t)^2 >= its lower bound and counts leaves and points per
+// (round, tree); the last reachable round is the first one in which some tree
+// alone holds T points; pass B scatters the leaves of rounds up to it into
+// their (round, tree) bucket lists (order inside a bucket is free).
+constexpr int BT = 256;
+
+__global__ void __launch_bounds__(BT)
+k_buckets(const float* __restrict__ lb2, int64_t total_leaves, const float* __restrict__ thrP,
+          const uint16_t* __restrict__ leaf_tree, const uint32_t* __restrict__ leaf_range, int L,
+          uint8_t* __restrict__ lround, uint32_t* __restrict__ boff, uint32_t* __restrict__ bpts,
+          uint32_t* __restrict__ list, uint32_t* __restrict__ meta) {
+  extern __shared__ __align__(16) unsigned char smb[];
+  const int RL = kRoundCap * L;
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smb);          // [RL]
+  uint32_t* s_pts = s_cnt + RL;                                  // [RL]
+  float* s_thr = reinterpret_cast<float*>(s_pts + RL);           // [kRoundCap]
+  __shared__ uint32_t s_tl;
+  __shared__ int s_tcap;
+  const int64_t qb = blockIdx.x;
+  uint32_t* m = meta + qb * MQ_WORDS;
+  const int Ru = (int)m[MQ_RU];
+  const float* lbrow = lb2 + qb * total_leaves;
+  uint8_t* lr = lround + qb * total_leaves;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  for (int i = threadIdx.x; i < RL; i += BT) {
+    s_cnt[i] = 0;
+    s_pts[i] = 0;
+  }
+  for (int i = threadIdx.x; i < Ru; i += BT) s_thr[i] = thrP[qb * kRoundCap + i];
+  if (threadIdx.x == 0) s_tl = 0;
+  __syncthreads();
+  const int64_t iters = (total_leaves + BT - 1) / BT * BT;
+  uint32_t tl = 0;
+  for (int64_t l = threadIdx.x; l < iters; l += BT) {
+    const bool valid = l < total_leaves;
+    uint32_t key = 0xffffffffu, pts = 0;
+    if (valid) {
+      const uint32_t t = (uint32_t)lower_bound_f(s_thr, Ru, lbrow[l]);
+      lr[l] = (uint8_t)t;
+      key = t * (uint32_t)L + leaf_tree[l];
+      pts = leaf_range[2 * l + 1];
+      tl = max(tl, t);
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, key);
+    const uint32_t sum = __reduce_add_sync(peers, pts);
+    if (valid && (peers & lt) == 0) {
+      atomicAdd(&s_cnt[key], (uint32_t)__popc(peers));
+      atomicAdd(&s_pts[key], sum);
+    }
+  }
+  tl = __reduce_max_sync(0xffffffffu, tl);
+  if (lane == 0) atomicMax(&s_tl, tl);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int tlast = (int)s_tl;
+    const unsigned long long T = ((unsigned long long)m[MQ_T_HI] << 32) | m[MQ_T_LO];
+    int tcap = tlast;
+    unsigned long long cum[kMaxL];
+    for (int i = 0; i < L; ++i) cum[i] = 0;
+    for (int t = 0; t <= tlast && tcap == tlast; ++t) {
+      for (int i = 0; i < L; ++i) {
+        cum[i] += s_pts[t * L + i];
+        if (cum[i] >= T) tcap = t;
+      }
+    }
+    m[MQ_TLAST] = (uint32_t)tlast;
+    m[MQ_TCAP] = (uint32_t)tcap;
+    s_tcap = tcap;
+    uint32_t* bo = boff + qb * (RL + 1);
+    uint32_t* bp = bpts + qb * RL;
+    uint32_t run = 0;
+    for (int b = 0; b < (tcap + 1) * L; ++b) {
+      bo[b] = run;
+      bp[b] = s_pts[b];
+      const uint32_t c = s_cnt[b];
+      s_cnt[b] = run;   // becomes the bucket cursor
+      run += c;
+    }
+    bo[(tcap + 1) * L] = run;
+  }
+  __syncthreads();
+  const uint32_t tcap = (uint32_t)s_tcap;
+  uint32_t* ql = list + qb * total_leaves;
+  for (int64_t l = threadIdx.x; l < iters; l += BT) {
+    uint32_t key = 0xffffffffu;
+    if (l < total_leaves) {
+      const uint32_t t = lr[l];
+      if (t <= tcap) key = t * (uint32_t)L + leaf_tree[l];
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (key != 0xffffffffu && lane == leader) base = atomicAdd(&s_cnt[key], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (key != 0xffffffffu) ql[base + __popc(peers & lt)] = (uint32_t)l;
+  }
+}
+
+// ------------------------------------------------------------------ walk
+constexpr int WT = 256;            // threads per walk CTA (several per SM)
+constexpr int WNW = WT / 32;
+constexpr int WBATCH = WT;         // leaves examined per batch step
+constexpr int WCAP = 4096;         // points examined per batch step
+constexpr int WILP = 4;            // points per thread in flight
+
+struct WalkArgs {
+  int64_t n;
+  int L;
+  const uint32_t* leaf_ids;
+  const uint32_t* leaf_range;
+  int64_t total_leaves;
+  int64_t nqb;
+  const float* lb2;
+  const uint32_t* list;       // [nqb][total_leaves] bucket lists
+  const uint32_t* boff;       // [nqb][kRoundCap*L+1]
+  const uint32_t* hist_pts;   // [nqb][kRoundCap*L]
+  uint32_t* meta;             // [nqb][MQ_WORDS]
+  uint32_t* cand;             // [nqb][cap]
+  int64_t cap;
+  uint32_t* round_end;        // [nqb][kRoundCap] |S| after each round
+  uint32_t* ws_newcnt;        // [grid][total_leaves]
+  uint32_t* ws_bitmap;        // [grid][bitmap_words] when not in shared memory
+  int64_t bitmap_words;
+  int smem_bitmap;
+};
+
+struct WalkLayout {
+  size_t boff, pts, bpref, bstart, fmap, sel, misc, bitmap, total;
+};
+
+__host__ __device__ inline WalkLayout walk_layout(int L, int64_t smem_bitmap_words) {
+  WalkLayout o{};
+  size_t p = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = p;
+    p += (bytes + 15) & ~size_t(15);
+    return at;
+  };
+  const size_t RL = (size_t)kRoundCap * L;
+  o.boff = take(sizeof(uint32_t) * (RL + 1));
+  o.pts = take(sizeof(uint32_t) * RL);
+  o.bpref = take(sizeof(uint32_t) * (WBATCH + 1));
+  o.bstart = take(sizeof(uint32_t) * WBATCH);
+  o.fmap = take(sizeof(uint16_t) * WCAP);
+  o.sel = take(sizeof(unsigned long long) * 256);
+  o.misc = take(sizeof(unsigned long long) * 32);
+  o.bitmap = take(sizeof(uint32_t) * (size_t)smem_bitmap_words);
+  o.total = p;
+  return o;
+}
+
+enum { W_S = 0, W_STOP, W_NEED, W_KSTAR, W_ACC, W_TOTNEW, W_QN, W_LEAFA, W_OFFA, W_OVF };
+
+// Append the new points of bucket leaves list[0..nl) (only leaves whose select
+// key is <= kstar when filtered) to the candidate list, in batches of at most
+// WCAP examined points: each point is tested-and-set in the bitmap and, if
+// new, written at the list's end.
+__device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, bool filtered,
+                         unsigned long long kstar, const float* lbrow, int tree, unsigned char* sm,
+                         const WalkLayout& ly, uint32_t* bitmap, uint32_t* cand) {
+  unsigned long long* misc = reinterpret_cast<unsigned long long*>(sm + ly.misc);
+  uint32_t* bpref = reinterpret_cast<uint32_t*>(sm + ly.bpref);
+  uint32_t* bstart = reinterpret_cast<uint32_t*>(sm + ly.bstart);
+  uint16_t* fmap = reinterpret_cast<uint16_t*>(sm + ly.fmap);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t* tree_ids = a.leaf_ids + (int64_t)tree * a.n;
+  __shared__ uint32_t s_w[WNW];
+
+  if (threadIdx.x == 0) {
+    misc[W_LEAFA] = 0;
+    misc[W_OFFA] = 0;
+  }
+  __syncthreads();
+  while (true) {
+    const uint32_t la = (uint32_t)misc[W_LEAFA];
+    const uint32_t offa = (uint32_t)misc[W_OFFA];
+    if (la >= nl) break;
+    // batch: leaves [la, la+nb) with their (filtered) counts, the first one from offa
+    const uint32_t nb = min((uint32_t)WBATCH, nl - la);
+    uint32_t cnt = 0;
+    if (threadIdx.x < nb) {
+      const uint32_t leaf = list[la + threadIdx.x];
+      const uint32_t st = a.leaf_range[2 * (int64_t)leaf];
+      cnt = a.leaf_range[2 * (int64_t)leaf + 1];
+      if (filtered) {
+        const unsigned long long key =
+            ((unsigned long long)__float_as_uint(lbrow[leaf]) << 32) | (unsigned long long)leaf;
+        if (key > kstar) cnt = 0;
+      }
+      if (threadIdx.x == 0) cnt = cnt >= offa ? cnt - offa : 0u;
+      bstart[threadIdx.x] = st + (threadIdx.x == 0 ? offa : 0u);
+    }
+    uint32_t x = cnt;   // inclusive scan over the block (WT == WBATCH)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    uint32_t wb = 0;
+    for (int qq = 0; qq < w; ++qq) wb += s_w[qq];
+    bpref[threadIdx.x + 1] = wb + x;   // bpref[j] = points before leaf j of the batch
+    if (threadIdx.x == 0) bpref[0] = 0;
+    __syncthreads();
+    uint32_t take_leaves, take_pts;
+    {
+      int lo = 0, hi = (int)nb;   // largest j with bpref[j] <= WCAP
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bpref[mid] <= (uint32_t)WCAP) lo = mid;
+        else hi = mid - 1;
+      }
+      take_leaves = (uint32_t)lo;
+      take_pts = bpref[lo];
+      if (take_leaves == 0) take_pts = min(bpref[1], (uint32_t)WCAP);
+    }
+    const uint32_t map_leaves = take_leaves == 0 ? 1u : take_leaves;
+    for (uint32_t j = (uint32_t)w; j < map_leaves; j += WNW) {
+      const uint32_t e = min(bpref[j + 1], take_pts);
+      for (uint32_t f = bpref[j] + lane; f < e; f += 32) fmap[f] = (uint16_t)j;
+    }
+    if (threadIdx.x == 0) misc[W_QN] = 0;
+    __syncthreads();
+    const unsigned long long S0 = misc[W_S];
+    for (uint32_t f0 = 0; f0 < take_pts; f0 += WT * WILP) {
+      uint32_t ids[WILP];
+#pragma unroll
+      for (int u = 0; u < WILP; ++u) {
+        const uint32_t f = f0 + u * WT + threadIdx.x;
+        ids[u] = 0xffffffffu;
+        if (f < take_pts) {
+          const uint32_t j = fmap[f];
+          ids[u] = __ldg(tree_ids + bstart[j] + (f - bpref[j]));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < WILP; ++u) {
+        bool fresh = false;
+        const uint32_t id = ids[u];
+        if (id != 0xffffffffu) {
+          const uint32_t bit = 1u << (id & 31);
+          const uint32_t old = atomicOr(bitmap + (id >> 5), bit);
+          fresh = !(old & bit);
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, fresh);
+        uint32_t base = 0;
+        if (lane == 0 && m) base = (uint32_t)atomicAdd(&misc[W_QN], (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (fresh) {
+          const unsigned long long pos = S0 + base + __popc(m & lt);
+          if ((int64_t)pos < a.cap) cand[pos] = id;
+          else misc[W_OVF] = 1;
         }
       }
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      misc[W_S] += misc[W_QN];
+      if (take_leaves == 0) {
+        const uint32_t first_total = bpref[1] + offa;  // points of leaf la (after filter)
+        const uint32_t newoff = offa + take_pts;
+        if (newoff >= first_total) {
+          misc[W_LEAFA] = la + 1;
+          misc[W_OFFA] = 0;
+        } else {
+          misc[W_OFFA] = newoff;
+        }
+      } else {
+        misc[W_LEAFA] = la + take_leaves;
+        misc[W_OFFA] = 0;
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
-// Keep the k smallest keys of the buffer; tau becomes the largest kept key
-// once k keys are held.
-__device__ void prune_topk(unsigned long long* tk, unsigned long long* misc, int k) {
-  __syncthreads();
-  const int cnt = (int)min(misc[M_TKN], (unsigned long long)TK_CAP);
-  for (int i = cnt + threadIdx.x; i < TK_CAP; i += ST) tk[i] = ~0ull;
-  sort_topk(tk);
-  if (threadIdx.x == 0) {
-    const int keep = min(cnt, k);
-    misc[M_TKN] = keep;
-    if (keep == k) misc[M_TAU] = tk[k - 1];
+// One CTA per query (persistent over the batch): the buckets in Alg. 7 order.
+__global__ void __launch_bounds__(WT, 4) k_walk(WalkArgs a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const WalkLayout ly = walk_layout(a.L, a.smem_bitmap ? a.bitmap_words : 0);
+  uint32_t* s_boff = reinterpret_cast<uint32_t*>(sm + ly.boff);
+  uint32_t* s_pts = reinterpret_cast<uint32_t*>(sm + ly.pts);
+  unsigned long long* sel = reinterpret_cast<unsigned long long*>(sm + ly.sel);
+  unsigned long long* misc = reinterpret_cast<unsigned long long*>(sm + ly.misc);
+  uint32_t* bitmap = a.smem_bitmap ? reinterpret_cast<uint32_t*>(sm + ly.bitmap)
+                                   : a.ws_bitmap + (int64_t)blockIdx.x * a.bitmap_words;
+  uint32_t* newcnt = a.ws_newcnt + (int64_t)blockIdx.x * a.total_leaves;
+  const int L = a.L;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ unsigned long long s_red_u[WNW];
+
+  for (int64_t qb = blockIdx.x; qb < a.nqb; qb += gridDim.x) {
+    const float* lbrow = a.lb2 + qb * a.total_leaves;
+    const uint32_t* list = a.list + qb * a.total_leaves;
+    uint32_t* cand = a.cand + qb * a.cap;
+    uint32_t* rend = a.round_end + qb * kRoundCap;
+    uint32_t* m = a.meta + qb * MQ_WORDS;
+    const unsigned long long T = ((unsigned long long)m[MQ_T_HI] << 32) | m[MQ_T_LO];
+    const int tcap = (int)m[MQ_TCAP];
+    const int tlast = (int)m[MQ_TLAST];
+    const int nbk = (tcap + 1) * L;
+    for (int64_t i = threadIdx.x; i < a.bitmap_words; i += WT) bitmap[i] = 0u;
+    for (int i = threadIdx.x; i <= nbk; i += WT) s_boff[i] = a.boff[qb * (kRoundCap * L + 1) + i];
+    for (int i = threadIdx.x; i < nbk; i += WT) s_pts[i] = a.hist_pts[qb * kRoundCap * L + i];
+    if (threadIdx.x == 0) {
+      misc[W_S] = 0;
+      misc[W_STOP] = 0;
+      misc[W_OVF] = 0;
+    }
+    __syncthreads();
+    int t_end = tcap;
+    for (int t = 0; t <= tcap; ++t) {
+      for (int i = 0; i < L; ++i) {
+        const int b = t * L + i;
+        const uint32_t nl = s_boff[b + 1] - s_boff[b];
+        if (nl == 0) continue;
+        const uint32_t* bl = list + s_boff[b];
+        const unsigned long long bpts = s_pts[b];   // all of the bucket's points
+        const unsigned long long S0 = misc[W_S];
+        bool cut = false;
+        if (S0 + bpts >= T) {
+          // new points of every leaf of the bucket (bitmap read only)
+          unsigned long long tot = 0;
+          for (uint32_t j = (uint32_t)w; j < nl; j += WNW) {
+            const uint32_t lf = bl[j];
+            const uint32_t st = a.leaf_range[2 * (int64_t)lf], ct = a.leaf_range[2 * (int64_t)lf + 1];
+            const uint32_t* ids = a.leaf_ids + (int64_t)i * a.n + st;
+            uint32_t nw = 0;
+            for (uint32_t e = lane; e < ct; e += 32) {
+              const uint32_t id = ids[e];
+              nw += (bitmap[id >> 5] >> (id & 31)) & 1u ? 0u : 1u;
+            }
+            nw = __reduce_add_sync(0xffffffffu, nw);
+            if (lane == 0) newcnt[j] = nw;
+            tot += nw;
+          }
+          if (lane == 0) s_red_u[w] = tot;
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            unsigned long long sum = 0;
+            for (int qq = 0; qq < WNW; ++qq) sum += s_red_u[qq];
+            misc[W_TOTNEW] = sum;
+          }
+          __syncthreads();
+          cut = (S0 + misc[W_TOTNEW] >= T);
+        }
+        unsigned long long kstar = ~0ull;
+        if (cut) {
+          // weighted radix select: the smallest key (lower bound, leaf) whose
+          // prefix of new points reaches T - |S|
+          if (threadIdx.x == 0) {
+            misc[W_NEED] = T - S0;
+            misc[W_KSTAR] = 0;
+            misc[W_ACC] = 0;
+          }
+          __syncthreads();
+          unsigned long long prefix = 0, pmask = 0;
+          for (int p = 7; p >= 0; --p) {
+            for (int i2 = threadIdx.x; i2 < 256; i2 += WT) sel[i2] = 0;
+            __syncthreads();
+            for (uint32_t j = threadIdx.x; j < nl; j += WT) {
+              const uint32_t lf = bl[j];
+              const unsigned long long key =
+                  ((unsigned long long)__float_as_uint(lbrow[lf]) << 32) | (unsigned long long)lf;
+              if ((key & pmask) == prefix && newcnt[j])
+                atomicAdd(&sel[(key >> (8 * p)) & 255ull], (unsigned long long)newcnt[j]);
+            }
+            __syncthreads();
+            if (threadIdx.x < 32) {
+              // the first digit whose cumulative weight reaches the need (a warp scan)
+              const unsigned long long need = misc[W_NEED];
+              unsigned long long acc0 = misc[W_ACC];
+              unsigned long long v[8], run = 0;
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                v[e] = sel[lane * 8 + e];
+                run += v[e];
+              }
+              unsigned long long incl = run;
+#pragma unroll
+              for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+              }
+              const unsigned long long before = incl - run;
+              const bool reaches = acc0 + incl >= need;
+              const uint32_t bal = __ballot_sync(0xffffffffu, reaches);
+              // a lane always reaches: the selected bin's weight covers the need
+              const int first = bal ? __ffs(bal) - 1 : 31;
+              if (lane == first) {
+                unsigned long long acc = acc0 + before;
+                int dg = lane * 8;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                  if (acc + v[e] >= need) break;
+                  acc += v[e];
+                  ++dg;
+                }
+                misc[W_ACC] = acc;
+                misc[W_KSTAR] = prefix | ((unsigned long long)min(dg, 255) << (8 * p));
+              }
+            }
+            __syncthreads();
+            prefix = misc[W_KSTAR];
+            pmask |= 255ull << (8 * p);
+          }
+          kstar = prefix;
+        }
+        walk_add(a, bl, nl, cut, kstar, lbrow, i, sm, ly, bitmap, cand);
+        if (cut) {
+          if (threadIdx.x == 0) misc[W_STOP] = 1;
+          break;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        rend[t] = (uint32_t)misc[W_S];
+        if (!misc[W_STOP] && t == tlast) misc[W_STOP] = 3;
+      }
+      __syncthreads();
+      if (misc[W_STOP]) {
+        t_end = t;
+        break;
+      }
+    }
+    if (threadIdx.x == 0) {
+      m[MQ_NS] = (uint32_t)misc[W_S];
+      m[MQ_TEND] = (uint32_t)t_end;
+      m[MQ_STOP] = misc[W_STOP] ? (uint32_t)misc[W_STOP] : 3u;
+      m[MQ_OVERFLOW] = (uint32_t)misc[W_OVF];
+    }
+    __syncthreads();
   }
-  __syncthreads();
 }
+
+// ------------------------------------------------------------------ distances
+constexpr int DT = 256;            // threads per distance CTA
+constexpr int DNW = DT / 32;
+constexpr int ILP = 8;             // rows per warp in flight (the transposed reduction assumes 8)
+constexpr int DROWS = DNW * ILP * 4;  // rows per CTA
 
 template <typename TX>
 struct Vec4Of;
@@ -315,410 +722,172 @@ __device__ __forceinline__ float transpose_reduce8(const float* acc, int lane) {
   return v;
 }
 
-// Add the points of bucket leaves list[0..nl) (only leaves whose select key is
-// <= kstar when filtered) to S. Runs in batches of at most QCAP points: the
-// batch's points are tested-and-set in the bitmap, the new ones queued, then
-// their distances computed by warps.
 template <typename TX>
-__device__ void add_leaves(const SearchArgs& a, const TX* __restrict__ X, const TX* __restrict__ q,
-                           bool vec4, const uint32_t* list, uint32_t nl, bool filtered,
-                           unsigned long long kstar, const float* lbrow, int tree, int kq,
-                           int Ru, unsigned char* sm, const SmemLayout& ly, uint32_t* bitmap,
-                           int64_t qglob) {
-  unsigned long long* misc = reinterpret_cast<unsigned long long*>(sm + ly.misc);
-  unsigned long long* tk = reinterpret_cast<unsigned long long*>(sm + ly.tk);
-  uint32_t* queue = reinterpret_cast<uint32_t*>(sm + ly.queue);
-  uint32_t* bpref = reinterpret_cast<uint32_t*>(sm + ly.bpref);
-  uint32_t* bstart = reinterpret_cast<uint32_t*>(sm + ly.bstart);
-  uint16_t* fmap = reinterpret_cast<uint16_t*>(sm + ly.fmap);
-  uint32_t* hist_u = reinterpret_cast<uint32_t*>(sm + ly.hist_u);
-  const float* thrC = reinterpret_cast<const float*>(sm + ly.thrC);
+__global__ void __launch_bounds__(DT, 3)
+k_dist(const TX* __restrict__ X, int d, const TX* __restrict__ Q, int64_t q0,
+       const uint32_t* __restrict__ cand, int64_t cap, const uint32_t* __restrict__ meta,
+       float* __restrict__ d2out, bool vec4) {
+  const int64_t qb = blockIdx.y;
+  const uint32_t nS = meta[qb * MQ_WORDS + MQ_NS];
+  const int64_t r0 = (int64_t)blockIdx.x * DROWS;
+  if (r0 >= nS) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint32_t lt = (1u << lane) - 1u;
-  const uint32_t* tree_ids = a.leaf_ids + (int64_t)tree * a.n;
-  __shared__ uint32_t s_w[NW];
-
-  if (threadIdx.x == 0) {
-    misc[M_LEAFA] = 0;
-    misc[M_OFFA] = 0;
-  }
-  __syncthreads();
-  while (true) {
-    const uint32_t la = (uint32_t)misc[M_LEAFA];
-    const uint32_t offa = (uint32_t)misc[M_OFFA];
-    if (la >= nl) break;
-    // --- batch: leaves [la, la+nb) with their (filtered) counts, the first one from offa
-    const uint32_t nb = min((uint32_t)BATCH_LEAVES, nl - la);
-    uint32_t cnt = 0;
-    if (threadIdx.x < nb) {
-      const uint32_t leaf = list[la + threadIdx.x];
-      const uint32_t st = a.leaf_range[2 * (int64_t)leaf];
-      cnt = a.leaf_range[2 * (int64_t)leaf + 1];
-      if (filtered) {
-        const unsigned long long key =
-            ((unsigned long long)__float_as_uint(lbrow[leaf]) << 32) | (unsigned long long)leaf;
-        if (key > kstar) cnt = 0;
-      }
-      if (threadIdx.x == 0) cnt = cnt >= offa ? cnt - offa : 0u;
-      bstart[threadIdx.x] = st + (threadIdx.x == 0 ? offa : 0u);
-    }
-    // inclusive scan of cnt over the block (ST == BATCH_LEAVES)
-    uint32_t x = cnt;
+  const TX* q = Q + (q0 + qb) * (int64_t)d;
+  const uint32_t* cl = cand + qb * cap;
+  float* out = d2out + qb * cap;
+  const int64_t r1 = min(r0 + (int64_t)DROWS, (int64_t)nS);
+  for (int64_t e0 = r0 + (int64_t)w * ILP; e0 < r1; e0 += DNW * ILP) {
+    uint32_t ids[ILP];
+    float acc[ILP];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+    for (int u = 0; u < ILP; ++u) {
+      ids[u] = (e0 + u < r1) ? __ldg(cl + e0 + u) : 0xffffffffu;
+      acc[u] = 0.f;
     }
-    if (lane == 31) s_w[w] = x;
-    __syncthreads();
-    uint32_t wb = 0;
-    for (int qq = 0; qq < w; ++qq) wb += s_w[qq];
-    bpref[threadIdx.x + 1] = wb + x;   // bpref[j] = points before leaf j of the batch
-    if (threadIdx.x == 0) bpref[0] = 0;
-    __syncthreads();
-    // batch extent: whole leaves while they fit in QCAP points, at least one (partially)
-    uint32_t take_leaves, take_pts;
-    {
-      int lo = 0, hi = (int)nb;   // largest j with bpref[j] <= QCAP
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (bpref[mid] <= (uint32_t)QCAP) lo = mid;
-        else hi = mid - 1;
-      }
-      take_leaves = (uint32_t)lo;
-      take_pts = bpref[lo];
-      if (take_leaves == 0) take_pts = min(bpref[1], (uint32_t)QCAP);
-    }
-    // flat point -> batch leaf map (a warp per leaf)
-    const uint32_t map_leaves = take_leaves == 0 ? 1u : take_leaves;
-    for (uint32_t j = (uint32_t)w; j < map_leaves; j += NW) {
-      const uint32_t e = min(bpref[j + 1], take_pts);
-      for (uint32_t f = bpref[j] + lane; f < e; f += 32) fmap[f] = (uint16_t)j;
-    }
-    // make room in the top-k buffer for up to take_pts insertions
-    if (misc[M_TKN] + take_pts > TK_CAP) prune_topk(tk, misc, kq);
-    if (threadIdx.x == 0) misc[M_QN] = 0;
-    __syncthreads();
-    // --- phase A: test-and-set, queue the new points
-    for (uint32_t f0 = 0; f0 < take_pts; f0 += ST) {
-      const uint32_t f = f0 + threadIdx.x;
-      bool fresh = false;
-      uint32_t id = 0;
-      if (f < take_pts) {
-        const uint32_t j = fmap[f];
-        id = tree_ids[bstart[j] + (f - bpref[j])];
-        const uint32_t bit = 1u << (id & 31);
-        const uint32_t old = atomicOr(bitmap + (id >> 5), bit);
-        fresh = !(old & bit);
-      }
-      const uint32_t m = __ballot_sync(0xffffffffu, fresh);
-      uint32_t base = 0;
-      if (lane == 0 && m) base = (uint32_t)atomicAdd(&misc[M_QN], (unsigned long long)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (fresh) queue[base + __popc(m & lt)] = id;
-    }
-    __syncthreads();
-    const uint32_t qn = (uint32_t)misc[M_QN];
-    const unsigned long long S_before = misc[M_S];
-    const unsigned long long tau = misc[M_TAU];
-    // --- phase B: exact distances of the queued points, 8 rows per warp
-    for (uint32_t e0 = (uint32_t)w * ILP; e0 < qn; e0 += NW * ILP) {
-      float acc[ILP];
-      uint32_t ids[ILP];
-#pragma unroll
-      for (int u = 0; u < ILP; ++u) {
-        ids[u] = (e0 + u < qn) ? queue[e0 + u] : 0xffffffffu;
-        acc[u] = 0.f;
-      }
-      rows_dist2<TX>(X, a.d, ids, q, vec4, lane, acc);
-      const float d2 = transpose_reduce8(acc, lane);
-      const uint32_t r = (uint32_t)(lane >> 2) & 7u;
-      if ((lane & 3) == 0 && e0 + r < qn) {
-        const uint32_t id = queue[e0 + r];
-        const int uu = lower_bound_f(thrC, Ru, d2);
-        atomicAdd(&hist_u[min(uu, kRoundCap)], 1u);
-        const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | id;
-        if (key < tau) {
-          const unsigned long long slot = atomicAdd(&misc[M_TKN], 1ull);
-          if (slot < TK_CAP) tk[slot] = key;
-        }
-        if (a.cand_ids) {
-          const unsigned long long pos = S_before + e0 + r;
-          if ((int64_t)pos < a.cand_cap) a.cand_ids[qglob * a.cand_cap + (int64_t)pos] = id;
-        }
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      misc[M_S] += qn;
-      // advance the batch cursor
-      if (take_leaves == 0) {
-        const uint32_t first_total = bpref[1] + offa;  // points of leaf la (after filter)
-        const uint32_t newoff = offa + take_pts;
-        if (newoff >= first_total) {
-          misc[M_LEAFA] = la + 1;
-          misc[M_OFFA] = 0;
-        } else {
-          misc[M_OFFA] = newoff;
-        }
-      } else {
-        misc[M_LEAFA] = la + take_leaves;
-        misc[M_OFFA] = 0;
-      }
-    }
-    __syncthreads();
+    rows_dist2<TX>(X, d, ids, q, vec4, lane, acc);
+    const float v = transpose_reduce8(acc, lane);
+    const int r = (lane >> 2) & 7;
+    if ((lane & 3) == 0 && e0 + r < r1) out[e0 + r] = v;
   }
 }
 
-template <typename TX>
-__global__ void __launch_bounds__(ST, 1) k_search(SearchArgs a) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  const int64_t smem_words = a.smem_bitmap ? a.bitmap_words : 0;
-  const SmemLayout ly = search_layout(a.L, smem_words);
-  float* thrP = reinterpret_cast<float*>(sm + ly.thrP);
-  float* thrC = reinterpret_cast<float*>(sm + ly.thrC);
-  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(sm + ly.cnt);
-  uint32_t* s_pts = reinterpret_cast<uint32_t*>(sm + ly.pts);
-  uint32_t* s_boff = reinterpret_cast<uint32_t*>(sm + ly.boff);
-  uint32_t* hist_u = reinterpret_cast<uint32_t*>(sm + ly.hist_u);
-  unsigned long long* tk = reinterpret_cast<unsigned long long*>(sm + ly.tk);
-  unsigned long long* sel = reinterpret_cast<unsigned long long*>(sm + ly.sel);
-  unsigned long long* misc = reinterpret_cast<unsigned long long*>(sm + ly.misc);
-  uint32_t* bitmap = a.smem_bitmap ? reinterpret_cast<uint32_t*>(sm + ly.bitmap)
-                                   : a.ws_bitmap + (int64_t)blockIdx.x * a.bitmap_words;
-  uint32_t* list = a.ws_list + (int64_t)blockIdx.x * a.total_leaves;
-  uint32_t* newcnt = a.ws_newcnt + (int64_t)blockIdx.x * a.total_leaves;
-  uint8_t* lround = a.ws_round + (int64_t)blockIdx.x * a.total_leaves;
-  const TX* X = static_cast<const TX*>(a.X);
-  const int L = a.L;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint32_t lt = (1u << lane) - 1u;
-  __shared__ unsigned long long s_red_u[NW];
-  const bool vec4 = (a.d % 4 == 0) &&
-                    (reinterpret_cast<uintptr_t>(a.X) % (sizeof(TX) == 4 ? 16 : 4) == 0) &&
-                    (reinterpret_cast<uintptr_t>(a.Q) % (sizeof(TX) == 4 ? 16 : 4) == 0);
-  // every lane of a warp runs the same number of leaf iterations (warp-aggregated atomics)
-  const int64_t leaf_iters = (a.total_leaves + ST - 1) / ST * ST;
+// ------------------------------------------------------------------ finalize
+constexpr int FT = 256;
+constexpr int TK_CAP = 4096;       // top-k buffer entries
+constexpr int TK_CHUNK = TK_CAP - kMaxTopK;
 
-  for (int64_t qb = blockIdx.x; qb < a.nqb; qb += gridDim.x) {
-    const int64_t qg = a.q0 + qb;
-    const float* lbrow = a.lb2 + qb * a.total_leaves;
-    const TX* q = static_cast<const TX*>(a.Q) + qg * a.d;
-    const int kq = a.k[qg];
-    // ---- reset per-query state
-    for (int64_t i = threadIdx.x; i < a.bitmap_words; i += ST) bitmap[i] = 0u;
-    for (int i = threadIdx.x; i < kRoundCap * L; i += ST) {
-      s_cnt[i] = 0;
-      s_pts[i] = 0;
-    }
-    for (int i = threadIdx.x; i <= kRoundCap; i += ST) hist_u[i] = 0;
-    if (threadIdx.x == 0) {
-      misc[M_S] = 0;
-      misc[M_TKN] = 0;
-      misc[M_TAU] = ~0ull;
-      misc[M_STOP] = 0;
-      misc[M_TLAST] = 0;
-      // Alg. 7 thresholds: r_0 = r_min, r_{t+1} = c * r_t (FP64), rounded once to FP32
-      const uint32_t mnb = a.minpos[qb];
-      const float m2 = __uint_as_float(a.maxlb[qb]);
-      double r = (double)a.r_min[qg];
-      if (!(r > 0.0)) r = (mnb != 0xffffffffu) ? sqrt((double)__uint_as_float(mnb)) / a.eps : 1.0;
-      const double cq = (double)a.c[qg];
-      int Ru = kRoundCap;
-      for (int t = 0; t < kRoundCap; ++t) {
-        if (t == kRoundCap - 1) {
-          thrP[t] = INFINITY;
-          thrC[t] = INFINITY;
-          break;
-        }
-        const double er = __dmul_rn(a.eps, r), cr = __dmul_rn(cq, r);
-        thrP[t] = __double2float_rn(__dmul_rn(er, er));
-        thrC[t] = __double2float_rn(__dmul_rn(cr, cr));
-        r = __dmul_rn(r, cq);
-        if (thrP[t] >= m2) {
-          Ru = t + 1;
-          break;
-        }
-      }
-      misc[M_RU] = (unsigned long long)Ru;
-      misc[M_T] = (unsigned long long)ceil(__dadd_rn(__dmul_rn(a.beta, (double)a.n), (double)kq));
-    }
-    __syncthreads();
-    const int Ru = (int)misc[M_RU];
-    const unsigned long long T = misc[M_T];
-    // ---- pass A: round of each leaf; histogram per (round, tree), warp-aggregated
-    uint32_t tl = 0;
-    for (int64_t l = threadIdx.x; l < leaf_iters; l += ST) {
-      const bool valid = l < a.total_leaves;
-      uint32_t key = 0xffffffffu, pts = 0;
-      if (valid) {
-        const int t = lower_bound_f(thrP, Ru, lbrow[l]);
-        lround[l] = (uint8_t)t;
-        key = (uint32_t)(t * L + a.leaf_tree[l]);
-        pts = a.leaf_range[2 * l + 1];
-        tl = max(tl, (uint32_t)t);
-      }
-      const uint32_t peers = __match_any_sync(0xffffffffu, key);
-      const uint32_t sum = __reduce_add_sync(peers, pts);
-      if (valid && (peers & lt) == 0) {
-        atomicAdd(&s_cnt[key], (uint32_t)__popc(peers));
-        atomicAdd(&s_pts[key], sum);
-      }
-    }
-    tl = __reduce_max_sync(0xffffffffu, tl);
-    if (lane == 0) atomicMax(&misc[M_TLAST], (unsigned long long)tl);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      // rounds past the first one where some tree alone holds T points are never reached
-      const int tlast = (int)misc[M_TLAST];
-      int tcap = tlast;
-      unsigned long long cum[kMaxL];
-      for (int i = 0; i < L; ++i) cum[i] = 0;
-      for (int t = 0; t <= tlast && tcap == tlast; ++t) {
-        for (int i = 0; i < L; ++i) {
-          cum[i] += s_pts[t * L + i];
-          if (cum[i] >= T) tcap = t;
-        }
-      }
-      misc[M_TCAP] = (unsigned long long)tcap;
-      uint32_t run = 0;
-      for (int b = 0; b < (tcap + 1) * L; ++b) {
-        s_boff[b] = run;
-        run += s_cnt[b];
-      }
-      s_boff[(tcap + 1) * L] = run;
-    }
-    __syncthreads();
-    const int tcap = (int)misc[M_TCAP];
-    const int tlast = (int)misc[M_TLAST];
-    // s_cnt now keeps each bucket's point total, s_pts becomes the insertion cursor
-    for (int i = threadIdx.x; i < (tcap + 1) * L; i += ST) {
-      s_cnt[i] = s_pts[i];
-      s_pts[i] = s_boff[i];
-    }
-    __syncthreads();
-    // ---- pass B: bucket the leaves of rounds <= tcap
-    for (int64_t l = threadIdx.x; l < leaf_iters; l += ST) {
-      uint32_t key = 0xffffffffu;
-      if (l < a.total_leaves) {
-        const int t = lround[l];
-        if (t <= tcap) key = (uint32_t)(t * L + a.leaf_tree[l]);
-      }
-      const uint32_t peers = __match_any_sync(0xffffffffu, key);
-      const int leader = __ffs(peers) - 1;
-      uint32_t base = 0;
-      if (key != 0xffffffffu && lane == leader) base = atomicAdd(&s_pts[key], (uint32_t)__popc(peers));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (key != 0xffffffffu) list[base + __popc(peers & lt)] = (uint32_t)l;
-    }
-    __syncthreads();
-    // ---- walk the buckets in Alg. 7 order
-    int t_stop = tcap;
-    for (int t = 0; t <= tcap; ++t) {
-      for (int i = 0; i < L; ++i) {
-        const int b = t * L + i;
-        const uint32_t nl = s_boff[b + 1] - s_boff[b];
-        if (nl == 0) continue;
-        const uint32_t* bl = list + s_boff[b];
-        // upper bound on the points this bucket can add: all of its points
-        const unsigned long long bpts = s_cnt[b];
-        const unsigned long long S0 = misc[M_S];
-        bool cut = false;
-        if (S0 + bpts >= T) {
-          // count the new points of every leaf of the bucket (no bitmap update)
-          unsigned long long tot = 0;
-          for (uint32_t j = (uint32_t)w; j < nl; j += NW) {
-            const uint32_t lf = bl[j];
-            const uint32_t st = a.leaf_range[2 * (int64_t)lf], ct = a.leaf_range[2 * (int64_t)lf + 1];
-            const uint32_t* ids = a.leaf_ids + (int64_t)i * a.n + st;
-            uint32_t nw = 0;
-            for (uint32_t e = lane; e < ct; e += 32) {
-              const uint32_t id = ids[e];
-              nw += (bitmap[id >> 5] >> (id & 31)) & 1u ? 0u : 1u;
-            }
-            nw = __reduce_add_sync(0xffffffffu, nw);
-            if (lane == 0) newcnt[j] = nw;
-            tot += nw;
-          }
-          if (lane == 0) s_red_u[w] = tot;
-          __syncthreads();
-          if (threadIdx.x == 0) {
-            unsigned long long sum = 0;
-            for (int qq = 0; qq < NW; ++qq) sum += s_red_u[qq];
-            misc[M_TOTNEW] = sum;
-          }
-          __syncthreads();
-          cut = (S0 + misc[M_TOTNEW] >= T);
-        }
-        unsigned long long kstar = ~0ull;
-        if (cut) {
-          // weighted radix select: the smallest key (lower bound, leaf) whose
-          // prefix of new points reaches T - |S|
-          if (threadIdx.x == 0) {
-            misc[M_NEED] = T - S0;
-            misc[M_KSTAR] = 0;
-            misc[M_ACC] = 0;
-          }
-          __syncthreads();
-          unsigned long long prefix = 0, pmask = 0;
-          for (int p = 7; p >= 0; --p) {
-            for (int i2 = threadIdx.x; i2 < 256; i2 += ST) sel[i2] = 0;
-            __syncthreads();
-            for (uint32_t j = threadIdx.x; j < nl; j += ST) {
-              const uint32_t lf = bl[j];
-              const unsigned long long key =
-                  ((unsigned long long)__float_as_uint(lbrow[lf]) << 32) | (unsigned long long)lf;
-              if ((key & pmask) == prefix && newcnt[j])
-                atomicAdd(&sel[(key >> (8 * p)) & 255ull], (unsigned long long)newcnt[j]);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-              unsigned long long acc = misc[M_ACC];
-              const unsigned long long need = misc[M_NEED];
-              int dg = 0;
-              for (; dg < 256; ++dg) {
-                if (acc + sel[dg] >= need) break;
-                acc += sel[dg];
-              }
-              misc[M_ACC] = acc;
-              misc[M_KSTAR] = prefix | ((unsigned long long)dg << (8 * p));
-            }
-            __syncthreads();
-            prefix = misc[M_KSTAR];
-            pmask |= 255ull << (8 * p);
-          }
-          kstar = prefix;
-        }
-        add_leaves<TX>(a, X, q, vec4, bl, nl, cut, kstar, lbrow, i, kq, Ru, sm, ly, bitmap, qg);
-        if (cut) {
-          if (threadIdx.x == 0) misc[M_STOP] = 1;
-          break;
-        }
-      }
+// Bitonic sort of TK_CAP keys ascending (block-wide).
+__device__ void sort_topk(unsigned long long* tk) {
+  for (int size = 2; size <= TK_CAP; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
       __syncthreads();
-      if (misc[M_STOP]) {
-        t_stop = t;
+      for (int i = threadIdx.x; i < TK_CAP / 2; i += FT) {
+        const int lo = 2 * i - (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = ((lo & size) == 0);
+        const unsigned long long a = tk[lo], b = tk[hi];
+        if ((a > b) == up) {
+          tk[lo] = b;
+          tk[hi] = a;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+struct FinalArgs {
+  const uint32_t* cand;
+  int64_t cap;
+  const float* d2;
+  const uint32_t* round_end;
+  const float* thrC;
+  const uint32_t* meta;
+  int64_t q0, nqb;
+  const int32_t* k;
+  int k_max;
+  int64_t* out_ids;
+  float* out_dist;
+  int32_t* out_stats;
+  uint32_t* cand_ids;
+  int64_t cand_cap;
+};
+
+__global__ void __launch_bounds__(FT) k_finalize(FinalArgs a) {
+  __shared__ unsigned long long tk[TK_CAP];
+  __shared__ uint32_t s_rend[kRoundCap];
+  __shared__ float s_thr[kRoundCap];
+  __shared__ uint32_t s_hist[kRoundCap + 1];
+  __shared__ unsigned long long s_tkn, s_tau;
+  __shared__ uint32_t s_nsf, s_stop, s_rounds;
+  const int64_t qb = blockIdx.x;
+  const int64_t qg = a.q0 + qb;
+  const uint32_t* m = a.meta + qb * MQ_WORDS;
+  const uint32_t nS = m[MQ_NS], t_end = m[MQ_TEND], stopT = m[MQ_STOP];
+  const int Ru = (int)m[MQ_RU];
+  const int kq = a.k[qg];
+  const uint32_t* cl = a.cand + qb * a.cap;
+  const float* dl = a.d2 + qb * a.cap;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const int nr = (int)t_end + 1;
+  for (int i = threadIdx.x; i < kRoundCap; i += FT) {
+    s_rend[i] = i < nr ? a.round_end[qb * kRoundCap + i] : 0u;
+    s_thr[i] = i < Ru ? a.thrC[qb * kRoundCap + i] : INFINITY;
+  }
+  for (int i = threadIdx.x; i <= kRoundCap; i += FT) s_hist[i] = 0;
+  __syncthreads();
+  // a candidate inserted in round r counts as within c*r_t for every t >= max(r, u),
+  // u = first round whose exact threshold (c*r_u)^2 covers its distance
+  const uint32_t iters = (nS + FT - 1) / FT * FT;
+  for (uint32_t p = threadIdx.x; p < iters; p += FT) {
+    uint32_t key = 0xffffffffu;
+    if (p < nS) {
+      const int r = upper_bound_u(s_rend, nr, p);
+      const int u = lower_bound_f(s_thr, Ru, dl[p]);
+      const int x = max(r, u);
+      if (x < nr) key = (uint32_t)x;
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, key);
+    if (key != 0xffffffffu && (peers & lt) == 0) atomicAdd(&s_hist[key], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // the ">= k within c*r" test runs after every completed round (not after a
+    // round the |S| rule ended early)
+    const int last_check = (stopT == 1) ? (int)t_end - 1 : (int)t_end;
+    uint32_t stop = stopT, nsf = nS, rounds = t_end + 1;
+    unsigned long long within = 0;
+    for (int t = 0; t <= last_check; ++t) {
+      within += s_hist[t];
+      if (within >= (unsigned long long)kq) {
+        stop = 2;
+        nsf = s_rend[t];
+        rounds = (uint32_t)t + 1;
         break;
       }
+    }
+    s_nsf = nsf;
+    s_stop = stop;
+    s_rounds = rounds;
+    s_tkn = 0;
+    s_tau = ~0ull;
+  }
+  __syncthreads();
+  const uint32_t nsf = s_nsf;
+  // k nearest of the first nsf candidates by (distance, id)
+  for (uint32_t c0 = 0; c0 < nsf; c0 += TK_CHUNK) {
+    if (s_tkn + TK_CHUNK > TK_CAP) {
+      const int cnt = (int)min(s_tkn, (unsigned long long)TK_CAP);
+      for (int i = cnt + threadIdx.x; i < TK_CAP; i += FT) tk[i] = ~0ull;
+      sort_topk(tk);
       if (threadIdx.x == 0) {
-        unsigned long long within = 0;
-        for (int u = 0; u <= t; ++u) within += hist_u[u];
-        if (within >= (unsigned long long)kq) misc[M_STOP] = 2;
-        else if (t == tlast) misc[M_STOP] = 3;
+        const int keep = min(cnt, kq);
+        s_tkn = keep;
+        if (keep == kq) s_tau = tk[kq - 1];
       }
       __syncthreads();
-      if (misc[M_STOP]) {
-        t_stop = t;
-        break;
+    }
+    const unsigned long long tau = s_tau;
+    const uint32_t c1 = min(nsf, c0 + (uint32_t)TK_CHUNK);
+    for (uint32_t p = c0 + threadIdx.x; p < c1; p += FT) {
+      const unsigned long long key = ((unsigned long long)__float_as_uint(dl[p]) << 32) | cl[p];
+      if (key < tau) {
+        const unsigned long long slot = atomicAdd(&s_tkn, 1ull);
+        if (slot < TK_CAP) tk[slot] = key;
       }
     }
-    // ---- top-k output
-    prune_topk(tk, misc, kq);
-    const int have = (int)misc[M_TKN];
-    for (int r = threadIdx.x; r < a.k_max; r += ST) {
+    __syncthreads();
+  }
+  {
+    const int cnt = (int)min(s_tkn, (unsigned long long)TK_CAP);
+    for (int i = cnt + threadIdx.x; i < TK_CAP; i += FT) tk[i] = ~0ull;
+    sort_topk(tk);
+    const int have = min(cnt, kq);
+    for (int r = threadIdx.x; r < a.k_max; r += FT) {
       int64_t id = -1;
       float dist = INFINITY;
-      if (r < have && r < kq) {
+      if (r < have) {
         const unsigned long long key = tk[r];
         id = (int64_t)(key & 0xffffffffull);
         dist = sqrtf(__uint_as_float((uint32_t)(key >> 32)));
@@ -726,13 +895,16 @@ __global__ void __launch_bounds__(ST, 1) k_search(SearchArgs a) {
       a.out_ids[qg * a.k_max + r] = id;
       a.out_dist[qg * a.k_max + r] = dist;
     }
-    if (threadIdx.x == 0 && a.out_stats) {
-      a.out_stats[qg * 4 + 0] = (int32_t)misc[M_S];
-      a.out_stats[qg * 4 + 1] = t_stop + 1;
-      a.out_stats[qg * 4 + 2] = (int32_t)misc[M_STOP];
-      a.out_stats[qg * 4 + 3] = 0;
-    }
-    __syncthreads();
+  }
+  if (a.cand_ids) {
+    for (uint32_t p = threadIdx.x; p < nsf && (int64_t)p < a.cand_cap; p += FT)
+      a.cand_ids[qg * a.cand_cap + p] = cl[p];
+  }
+  if (threadIdx.x == 0 && a.out_stats) {
+    a.out_stats[qg * 4 + 0] = (int32_t)nsf;
+    a.out_stats[qg * 4 + 1] = (int32_t)s_rounds;
+    a.out_stats[qg * 4 + 2] = (int32_t)s_stop;
+    a.out_stats[qg * 4 + 3] = (int32_t)m[MQ_OVERFLOW];
   }
 }
 
@@ -743,7 +915,8 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
               float* out_dist, int32_t* out_stats, uint32_t* cand_ids, int64_t cand_cap,
               cudaStream_t s) {
   if (nq == 0) return DETLSH_OK;
-  const int LK = idx->K * idx->L;
+  const int LK = idx->K * idx->L, L = idx->L;
+  const int64_t TL = idx->total_leaves;
   int dev = 0, nsm = 0, smem_optin = 0;
   DL_CUDA(cudaGetDevice(&dev));
   DL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -758,86 +931,140 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
                           s));
   tm.end();
 
-  // search configuration (static shared memory of the kernel: < 1 KiB)
+  // walk configuration: the dedup bitmap in shared memory when it fits
   const int64_t words = (idx->n + 31) / 32;
-  const SmemLayout base = search_layout(idx->L, 0);
-  const bool smem_bitmap = (int64_t)base.total + words * 4 + 1024 <= (int64_t)smem_optin;
-  const SmemLayout ly = search_layout(idx->L, smem_bitmap ? words : 0);
-  if ((int64_t)ly.total + 1024 > smem_optin) {
-    set_error("search kernel needs %zu bytes of shared memory", ly.total);
+  int smem_sm = 0;
+  DL_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  const WalkLayout with_bm = walk_layout(L, words);
+  const bool smem_bitmap = 4 * ((int64_t)with_bm.total + 2048) <= (int64_t)smem_sm;
+  const WalkLayout wl = walk_layout(L, smem_bitmap ? words : 0);
+  if ((int64_t)wl.total + 1024 > smem_optin) {
+    set_error("walk kernel needs %zu bytes of shared memory", wl.total);
     return DETLSH_EINVAL;
   }
-  // batch size bounded by the lower-bound buffer (<= ~2 GiB)
-  const int64_t per_q = idx->total_leaves * (int64_t)sizeof(float);
-  int64_t qb = std::max<int64_t>(1, std::min<int64_t>(nq, ((int64_t)2 << 30) / std::max<int64_t>(per_q, 1)));
+  DL_CUDA(cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wl.total));
+  int walk_per_sm = 0;
+  DL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&walk_per_sm, k_walk, WT, wl.total));
+  walk_per_sm = std::max(walk_per_sm, 1);
+
+  // candidate capacity per query: S stays below beta*n+k until its last leaf
+  const double tmax = std::ceil(beta * (double)idx->n + (double)k_max);
+  const int64_t cap = std::max<int64_t>(
+      1, std::min<int64_t>(idx->n, (int64_t)std::min(tmax, 9.0e18) - 1 + idx->max_leaf_count));
+  // batch size bounded by the per-query buffers (<= ~3 GiB)
+  const int64_t RL = (int64_t)kRoundCap * L;
+  const int64_t per_q = TL * 9 + cap * 8 + RL * 16 + kRoundCap * 12 + MQ_WORDS * 4 + 64;
+  int64_t qb = std::max<int64_t>(1, std::min<int64_t>(nq, ((int64_t)3 << 30) / per_q));
   qb = std::min<int64_t>(qb, 8192);
-  const int grid = (int)std::min<int64_t>(qb, nsm);
-  Scratch lb, mm, ws_list, ws_new, ws_round, ws_bm;
-  DL_TRY(lb.alloc(sizeof(float) * qb * idx->total_leaves, s));
+  const int wgrid = (int)std::min<int64_t>(qb, (int64_t)nsm * walk_per_sm);
+  Scratch lb, mm, lround, hist, boff, list, candb, d2b, rend, thr, meta, ws_new, ws_bm;
+  DL_TRY(lb.alloc(sizeof(float) * qb * TL, s));
   DL_TRY(mm.alloc(sizeof(uint32_t) * 2 * qb, s));
-  DL_TRY(ws_list.alloc(sizeof(uint32_t) * grid * idx->total_leaves, s));
-  DL_TRY(ws_new.alloc(sizeof(uint32_t) * grid * idx->total_leaves, s));
-  DL_TRY(ws_round.alloc((size_t)grid * idx->total_leaves, s));
-  if (!smem_bitmap) DL_TRY(ws_bm.alloc(sizeof(uint32_t) * grid * words, s));
+  DL_TRY(lround.alloc((size_t)qb * TL, s));
+  DL_TRY(hist.alloc(sizeof(uint32_t) * qb * RL, s));
+  DL_TRY(boff.alloc(sizeof(uint32_t) * qb * (RL + 1), s));
+  DL_TRY(list.alloc(sizeof(uint32_t) * qb * TL, s));
+  DL_TRY(candb.alloc(sizeof(uint32_t) * qb * cap, s));
+  DL_TRY(d2b.alloc(sizeof(float) * qb * cap, s));
+  DL_TRY(rend.alloc(sizeof(uint32_t) * qb * kRoundCap, s));
+  DL_TRY(thr.alloc(sizeof(float) * 2 * qb * kRoundCap, s));
+  DL_TRY(meta.alloc(sizeof(uint32_t) * qb * MQ_WORDS, s));
+  DL_TRY(ws_new.alloc(sizeof(uint32_t) * wgrid * TL, s));
+  if (!smem_bitmap) DL_TRY(ws_bm.alloc(sizeof(uint32_t) * wgrid * words, s));
   uint32_t* d_min = mm.as<uint32_t>();
   uint32_t* d_max = d_min + qb;
+  uint32_t* h_pts = hist.as<uint32_t>();
+  const size_t bk_smem = sizeof(uint32_t) * 2 * RL + sizeof(float) * kRoundCap;
+  if (bk_smem > 48 * 1024)
+    DL_CUDA(cudaFuncSetAttribute(k_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bk_smem));
+  float* thrP = thr.as<float>();
+  float* thrC = thrP + qb * kRoundCap;
 
-  auto kern = idx->dtype == DETLSH_U8 ? k_search<uint8_t> : k_search<float>;
-  DL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ly.total));
+  const bool vec4 = (idx->d % 4 == 0) &&
+                    (reinterpret_cast<uintptr_t>(idx->X) % (idx->dtype == DETLSH_U8 ? 4 : 16) == 0) &&
+                    (reinterpret_cast<uintptr_t>(Q) % (idx->dtype == DETLSH_U8 ? 4 : 16) == 0);
 
   for (int64_t q0 = 0; q0 < nq; q0 += qb) {
     const int64_t nqb = std::min<int64_t>(qb, nq - q0);
     DL_CUDA(cudaMemsetAsync(d_min, 0xff, sizeof(uint32_t) * nqb, s));
     DL_CUDA(cudaMemsetAsync(d_max, 0x00, sizeof(uint32_t) * nqb, s));
-    dim3 g1(ceil_div(idx->total_leaves, LB_THREADS), ceil_div(nqb, LB_QCH));
+    dim3 g1(ceil_div(TL, LB_THREADS), ceil_div(nqb, LB_QCH));
     tm.begin(TR_LB);
     k_leaf_lb<<<g1, LB_THREADS, 0, s>>>(qp.as<float>() + q0 * LK, nqb, LK, idx->E, idx->Nr, idx->K,
-                                        idx->leaf_lo, idx->leaf_hi, idx->leaf_tree,
-                                        idx->total_leaves, lb.as<float>(), d_min, d_max);
+                                        idx->leaf_lo, idx->leaf_hi, idx->leaf_tree, TL, lb.as<float>(),
+                                        d_min, d_max);
     DL_LAUNCH();
     tm.end();
     trace_add(TR_LB_LAUNCHES, 1.0);
-    SearchArgs sa{};
-    sa.X = idx->X;
-    sa.dtype = idx->dtype;
-    sa.n = idx->n;
-    sa.d = idx->d;
-    sa.K = idx->K;
-    sa.L = idx->L;
-    sa.Nr = idx->Nr;
-    sa.leaf_ids = idx->leaf_ids;
-    sa.leaf_range = idx->leaf_range;
-    sa.leaf_tree = idx->leaf_tree;
-    sa.total_leaves = idx->total_leaves;
-    sa.Q = Q;
-    sa.q0 = q0;
-    sa.nqb = nqb;
-    sa.lb2 = lb.as<float>();
-    sa.minpos = d_min;
-    sa.maxlb = d_max;
-    sa.k = k;
-    sa.c = c;
-    sa.r_min = r_min;
-    sa.eps = eps;
-    sa.beta = beta;
-    sa.k_max = k_max;
-    sa.out_ids = out_ids;
-    sa.out_dist = out_dist;
-    sa.out_stats = out_stats;
-    sa.cand_ids = cand_ids;
-    sa.cand_cap = cand_cap;
-    sa.ws_list = ws_list.as<uint32_t>();
-    sa.ws_newcnt = ws_new.as<uint32_t>();
-    sa.ws_round = ws_round.as<uint8_t>();
-    sa.ws_bitmap = smem_bitmap ? nullptr : ws_bm.as<uint32_t>();
-    sa.bitmap_words = words;
-    sa.smem_bitmap = smem_bitmap ? 1 : 0;
-    const int gq = (int)std::min<int64_t>(nqb, grid);
-    tm.begin(TR_SEARCH);
-    kern<<<gq, ST, ly.total, s>>>(sa);
+
+    tm.begin(TR_BUCKET);
+    k_thresh<<<ceil_div(nqb, 128), 128, 0, s>>>(d_min, d_max, q0, nqb, k, c, r_min, eps, beta, idx->n,
+                                                thrP, thrC, meta.as<uint32_t>());
+    DL_LAUNCH();
+    k_buckets<<<(unsigned)nqb, BT, bk_smem, s>>>(lb.as<float>(), TL, thrP, idx->leaf_tree,
+                                                 idx->leaf_range, L, lround.as<uint8_t>(),
+                                                 boff.as<uint32_t>(), h_pts, list.as<uint32_t>(),
+                                                 meta.as<uint32_t>());
     DL_LAUNCH();
     tm.end();
-    trace_add(TR_SEARCH_LAUNCHES, 1.0);
+    WalkArgs wa{};
+    wa.n = idx->n;
+    wa.L = L;
+    wa.leaf_ids = idx->leaf_ids;
+    wa.leaf_range = idx->leaf_range;
+    wa.total_leaves = TL;
+    wa.nqb = nqb;
+    wa.lb2 = lb.as<float>();
+    wa.list = list.as<uint32_t>();
+    wa.boff = boff.as<uint32_t>();
+    wa.hist_pts = h_pts;
+    wa.meta = meta.as<uint32_t>();
+    wa.cand = candb.as<uint32_t>();
+    wa.cap = cap;
+    wa.round_end = rend.as<uint32_t>();
+    wa.ws_newcnt = ws_new.as<uint32_t>();
+    wa.ws_bitmap = smem_bitmap ? nullptr : ws_bm.as<uint32_t>();
+    wa.bitmap_words = words;
+    wa.smem_bitmap = smem_bitmap ? 1 : 0;
+    tm.begin(TR_WALK);
+    k_walk<<<(unsigned)std::min<int64_t>(nqb, wgrid), WT, wl.total, s>>>(wa);
+    DL_LAUNCH();
+    tm.end();
+
+    dim3 g3(ceil_div(cap, DROWS), (unsigned)nqb);
+    tm.begin(TR_DIST);
+    if (idx->dtype == DETLSH_U8)
+      k_dist<uint8_t><<<g3, DT, 0, s>>>(static_cast<const uint8_t*>(idx->X), idx->d,
+                                        static_cast<const uint8_t*>(Q), q0, candb.as<uint32_t>(), cap,
+                                        meta.as<uint32_t>(), d2b.as<float>(), vec4);
+    else
+      k_dist<float><<<g3, DT, 0, s>>>(static_cast<const float*>(idx->X), idx->d,
+                                      static_cast<const float*>(Q), q0, candb.as<uint32_t>(), cap,
+                                      meta.as<uint32_t>(), d2b.as<float>(), vec4);
+    DL_LAUNCH();
+    tm.end();
+    trace_add(TR_DIST_LAUNCHES, 1.0);
+
+    FinalArgs fa{};
+    fa.cand = candb.as<uint32_t>();
+    fa.cap = cap;
+    fa.d2 = d2b.as<float>();
+    fa.round_end = rend.as<uint32_t>();
+    fa.thrC = thrC;
+    fa.meta = meta.as<uint32_t>();
+    fa.q0 = q0;
+    fa.nqb = nqb;
+    fa.k = k;
+    fa.k_max = k_max;
+    fa.out_ids = out_ids;
+    fa.out_dist = out_dist;
+    fa.out_stats = out_stats;
+    fa.cand_ids = cand_ids;
+    fa.cand_cap = cand_cap;
+    tm.begin(TR_FINALIZE);
+    k_finalize<<<(unsigned)nqb, FT, 0, s>>>(fa);
+    DL_LAUNCH();
+    tm.end();
   }
   DL_TRY(tm.finish());
   return DETLSH_OK;
