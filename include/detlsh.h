@@ -190,6 +190,26 @@ int detlsh_encode_values(const float* P, int64_t n, int32_t LK, const float* E,
 int detlsh_select_breakpoints(const float* Ps, int64_t n_s, int32_t LK, int32_t n_regions,
                               float* E, int32_t mem, void* stream);
 
+/*
+ * detlsh_select_breakpoints_noalloc -- detlsh_select_breakpoints for callers
+ * that must not allocate device memory, e.g. a serving process that keeps a
+ * fixed device-memory footprint (an allocation may fail under memory pressure
+ * mid-request; freeing synchronizes the device) or an application whose own
+ * allocator owns all device memory. The paper has no counterpart: this is an
+ * integration variant of the same Alg. 1 selection, with the same results.
+ *
+ * Ps [LK][n_s] and E [LK][N_r+1] are device pointers; the call only enqueues
+ * work on `stream`. Temporary storage comes from one fixed 7 MiB array built
+ * into the library (held by every GPU that loads it, until process exit), so
+ * n_s*LK must not exceed DETLSH_NOALLOC_MAX_ITEMS (DETLSH_EINVAL otherwise).
+ * The first call on each device looks up that array's device address; make it
+ * before any stream capture. All calls share the array: calls whose GPU work
+ * overlaps (e.g. on two streams) race and must be serialized by the caller.
+ */
+#define DETLSH_NOALLOC_MAX_ITEMS 262144
+int detlsh_select_breakpoints_noalloc(const float* Ps, int64_t n_s, int32_t LK, int32_t n_regions,
+                                      float* E, void* stream);
+
 /* detlsh_eps_lemma3 -- eps of Lemma 3 (Eq. 2): eps^2 is the upper
  * alpha1-quantile of chi2(K), alpha1 = exp(-1/L). Returns < 0 on bad input. */
 double detlsh_eps_lemma3(int32_t K, int32_t L);

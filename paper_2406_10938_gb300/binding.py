@@ -29,7 +29,7 @@ _EXPORT_DTYPE = {"A": torch.float32, "EDGES": torch.float32, "CODES": torch.uint
 SYMBOLS = ("detlsh_build", "detlsh_query", "detlsh_free", "detlsh_export_size", "detlsh_export",
            "detlsh_info", "detlsh_project", "detlsh_encode_values", "detlsh_select_breakpoints",
            "detlsh_eps_lemma3", "detlsh_strerror", "detlsh_last_error", "detlsh_trace_enable",
-           "detlsh_trace_get", "detlsh_launch_count")
+           "detlsh_trace_get", "detlsh_launch_count", "detlsh_select_breakpoints_noalloc")
 TRACE_KEYS = ("sample_proj_ms", "breakpoints_ms", "encode_ms", "leaves_ms", "query_proj_ms", "lb_ms",
               "dist_ms", "dist_launches", "lb_launches", "build_ms", "query_ms", "walk_ms", "finalize_ms",
               "bucket_ms")
@@ -97,6 +97,8 @@ def lib(path: Optional[str] = None):
     L.detlsh_trace_get.restype = ctypes.c_int
     L.detlsh_launch_count.argtypes = []
     L.detlsh_launch_count.restype = i64
+    L.detlsh_select_breakpoints_noalloc.argtypes = [vp, i64, i32, i32, vp, vp]
+    L.detlsh_select_breakpoints_noalloc.restype = ctypes.c_int
     if path is None:
         _lib = L
     return L
@@ -254,6 +256,17 @@ def detlsh_select_breakpoints(Ps: torch.Tensor, n_regions: int) -> torch.Tensor:
     _check(lib().detlsh_select_breakpoints(_ptr(Ps), Ps.shape[1], Ps.shape[0], n_regions, _ptr(E), mem,
                                            _stream(mem)), "detlsh_select_breakpoints")
     return E
+
+
+def detlsh_select_breakpoints_noalloc(Ps: torch.Tensor, n_regions: int, E: torch.Tensor) -> None:
+    """Same as detlsh_select_breakpoints into a preallocated device E, allocating
+    nothing on the device (for callers that must not allocate); asynchronous on
+    torch's current stream."""
+    if Ps.device.type != "cuda" or E.device.type != "cuda":
+        raise ValueError("detlsh_select_breakpoints_noalloc takes device tensors only")
+    Ps = Ps.contiguous()
+    _check(lib().detlsh_select_breakpoints_noalloc(_ptr(Ps), Ps.shape[1], Ps.shape[0], n_regions, _ptr(E),
+                                                   _stream(MEM_DEVICE)), "detlsh_select_breakpoints_noalloc")
 
 
 def detlsh_eps_lemma3(K: int, L: int) -> float:

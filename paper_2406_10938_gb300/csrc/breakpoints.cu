@@ -69,3 +69,50 @@ int select_breakpoints(const float* Ps, int64_t n_s, int LK, int Nr, float* E, c
 }
 
 }  // namespace detlsh
+
+// ---------------------------------------------------------------------------
+// The same breakpoint selection with caller-provided temporary storage.
+namespace detlsh {
+
+size_t radix_ws_bytes(int64_t n, int bit_lo, int bit_hi);
+int radix_sort_pairs_ws(const uint32_t* keys_in, const uint32_t* vals_in, int64_t n, int bit_lo,
+                        int bit_hi, uint32_t* keys_out, uint32_t* vals_out, void* ws, size_t ws_bytes,
+                        cudaStream_t s);
+
+namespace {
+size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+}  // namespace
+
+size_t select_breakpoints_ws_bytes(int64_t n_s, int LK) {
+  const int64_t total = n_s * LK;
+  return 4 * al256(sizeof(uint32_t) * total) + radix_ws_bytes(total, 0, 32);
+}
+
+int select_breakpoints_ws(const float* Ps, int64_t n_s, int LK, int Nr, float* E, void* ws,
+                          size_t ws_bytes, cudaStream_t s) {
+  const int64_t total = n_s * LK;
+  if (ws_bytes < select_breakpoints_ws_bytes(n_s, LK)) {
+    set_error("breakpoint workspace too small");
+    return DETLSH_EINTERNAL;
+  }
+  char* p = static_cast<char*>(ws);
+  const size_t arr = al256(sizeof(uint32_t) * total);
+  uint32_t* k0 = reinterpret_cast<uint32_t*>(p);
+  uint32_t* v0 = reinterpret_cast<uint32_t*>(p + arr);
+  uint32_t* k1 = reinterpret_cast<uint32_t*>(p + 2 * arr);
+  uint32_t* v1 = reinterpret_cast<uint32_t*>(p + 3 * arr);
+  void* sort_ws = p + 4 * arr;
+  const size_t sort_b = ws_bytes - 4 * arr;
+  const unsigned nb = ceil_div(total, 256);
+  k_make_keys<<<nb, 256, 0, s>>>(Ps, total, k0, v0);
+  DL_LAUNCH();
+  DL_TRY(radix_sort_pairs_ws(k0, v0, total, 0, 32, k1, v1, sort_ws, sort_b, s));
+  k_row_keys<<<nb, 256, 0, s>>>(v1, total, n_s, k0);
+  DL_LAUNCH();
+  DL_TRY(radix_sort_pairs_ws(k0, v1, total, 0, 8, k1, v0, sort_ws, sort_b, s));
+  k_gather_edges<<<ceil_div((int64_t)LK * (Nr + 1), 256), 256, 0, s>>>(Ps, v0, n_s, LK, Nr, E);
+  DL_LAUNCH();
+  return DETLSH_OK;
+}
+
+}  // namespace detlsh

@@ -204,3 +204,104 @@ int radix_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, int64_t n
 }
 
 }  // namespace detlsh
+
+// ---------------------------------------------------------------------------
+// Variants of the scan and the radix sort that take their temporary storage
+// from the caller instead of allocating it (same kernels, same results).
+namespace detlsh {
+namespace {
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+size_t scan_ws_bytes(int64_t n) {
+  size_t total = 0;
+  int64_t m = n;
+  while (m > TILE) {
+    const int64_t nb = ceil_div(m, TILE);
+    total += 2 * align256(sizeof(uint32_t) * nb);
+    m = nb;
+  }
+  return total;
+}
+
+int exclusive_scan_u32_ws(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* d_total, void* ws,
+                          size_t ws_bytes, cudaStream_t s) {
+  if (n == 0) {
+    if (d_total) DL_CUDA(cudaMemsetAsync(d_total, 0, sizeof(uint32_t), s));
+    return DETLSH_OK;
+  }
+  const int64_t nb = ceil_div(n, TILE);
+  if (nb == 1) {
+    k_block_scan<<<1, ST, 0, s>>>(in, n, nullptr, out, d_total);
+    DL_LAUNCH();
+    return DETLSH_OK;
+  }
+  const size_t part = align256(sizeof(uint32_t) * nb);
+  if (ws_bytes < 2 * part + scan_ws_bytes(nb)) {
+    set_error("scan workspace too small");
+    return DETLSH_EINTERNAL;
+  }
+  uint32_t* sums = static_cast<uint32_t*>(ws);
+  uint32_t* sums_scan = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + part);
+  k_block_sums<<<(unsigned)nb, ST, 0, s>>>(in, n, sums);
+  DL_LAUNCH();
+  DL_TRY(exclusive_scan_u32_ws(sums, sums_scan, nb, nullptr, static_cast<char*>(ws) + 2 * part,
+                               ws_bytes - 2 * part, s));
+  k_block_scan<<<(unsigned)nb, ST, 0, s>>>(in, n, sums_scan, out, d_total);
+  DL_LAUNCH();
+  return DETLSH_OK;
+}
+
+size_t radix_ws_bytes(int64_t n, int bit_lo, int bit_hi) {
+  const int passes = (bit_hi - bit_lo + 7) / 8;
+  const int64_t n_tiles = ceil_div(n, TILE);
+  size_t b = 2 * align256(sizeof(uint32_t) * 256 * n_tiles) + scan_ws_bytes(256 * n_tiles);
+  if (passes > 1) b += 2 * align256(sizeof(uint32_t) * n);
+  return b;
+}
+
+int radix_sort_pairs_ws(const uint32_t* keys_in, const uint32_t* vals_in, int64_t n, int bit_lo,
+                        int bit_hi, uint32_t* keys_out, uint32_t* vals_out, void* ws, size_t ws_bytes,
+                        cudaStream_t s) {
+  if (n == 0) return DETLSH_OK;
+  if (ws_bytes < radix_ws_bytes(n, bit_lo, bit_hi)) {
+    set_error("radix sort workspace too small");
+    return DETLSH_EINTERNAL;
+  }
+  const int passes = (bit_hi - bit_lo + 7) / 8;
+  const int64_t n_tiles = ceil_div(n, TILE);
+  char* p = static_cast<char*>(ws);
+  const size_t tbl = align256(sizeof(uint32_t) * 256 * n_tiles);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(p);
+  uint32_t* offs = reinterpret_cast<uint32_t*>(p + tbl);
+  p += 2 * tbl;
+  const size_t scan_b = scan_ws_bytes(256 * n_tiles);
+  void* scan_ws = p;
+  p += scan_b;
+  uint32_t* kb = nullptr;
+  uint32_t* vb = nullptr;
+  if (passes > 1) {
+    kb = reinterpret_cast<uint32_t*>(p);
+    vb = reinterpret_cast<uint32_t*>(p + align256(sizeof(uint32_t) * n));
+  }
+  const uint32_t* ki = keys_in;
+  const uint32_t* vi = vals_in;
+  for (int pass = 0; pass < passes; ++pass) {
+    const bool to_out = ((passes - 1 - pass) % 2) == 0;
+    uint32_t* ko = to_out ? keys_out : kb;
+    uint32_t* vo = to_out ? vals_out : vb;
+    const int bit = bit_lo + 8 * pass;
+    k_digit_hist<<<(unsigned)n_tiles, ST, 0, s>>>(ki, n, bit, hist, n_tiles);
+    DL_LAUNCH();
+    DL_TRY(exclusive_scan_u32_ws(hist, offs, 256 * n_tiles, nullptr, scan_ws, scan_b, s));
+    k_digit_scatter<<<(unsigned)n_tiles, ST, 0, s>>>(ki, vi, n, bit, offs, n_tiles, ko, vo);
+    DL_LAUNCH();
+    ki = ko;
+    vi = vo;
+  }
+  return DETLSH_OK;
+}
+
+}  // namespace detlsh
