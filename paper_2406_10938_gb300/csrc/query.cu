@@ -465,6 +465,8 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
     }
     __syncthreads();
   }
+  // every thread has read the exhausted cursor before the next call resets it
+  __syncthreads();
 }
 
 // One CTA per query (persistent over the batch): the buckets in Alg. 7 order.
