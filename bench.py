@@ -102,14 +102,14 @@ def _src_sha1(relpath):
         return hashlib.sha1(f.read()).hexdigest()
 
 
-def _ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
-    kernel's source is unchanged since that capture; else None."""
+def _ncu_traffic_per_unit(kernel):
+    """DRAM bytes per processed unit of `kernel` from its committed ncu summary,
+    if the kernel's source file is unchanged since that capture; else None."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_mid.md")
     try:
         for line in open(path):
-            if line.startswith("traffic_bytes_per_launch:"):
-                _, val, src, sha = line.split()
+            if line.startswith("traffic_bytes_per_unit:"):
+                _, val, _unit, src, sha = line.split()
                 if _src_sha1(src) == sha:
                     return float(val)
     except (OSError, ValueError):
@@ -272,7 +272,8 @@ def gpu_arm(args, rank, world, local_rank):
     b, ms, launches_dom = cand[dom]
     peak, peak_kind = _peaks()
     achieved = (b / launches_dom) / ((ms / launches_dom) / 1000.0) / 1e9
-    traffic = _ncu_traffic(dom)
+    per_unit = _ncu_traffic_per_unit(dom.split("<")[0])
+    traffic = per_unit * (n_cand / launches_dom) if (per_unit is not None and dom == "k_dist") else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
                 "traffic": traffic, "algorithmic_bytes_per_launch": b / launches_dom,
