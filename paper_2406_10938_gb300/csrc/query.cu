@@ -220,23 +220,39 @@ k_buckets(const float* __restrict__ lb2, int64_t total_leaves, const float* __re
   for (int i = threadIdx.x; i < Ru; i += BT) s_thr[i] = thrP[qb * kRoundCap + i];
   if (threadIdx.x == 0) s_tl = 0;
   __syncthreads();
-  const int64_t iters = (total_leaves + BT - 1) / BT * BT;
+  constexpr int BU = 4;   // leaves per thread in flight
+  const int64_t iters = (total_leaves + BT * BU - 1) / (BT * BU) * (BT * BU);
   uint32_t tl = 0;
-  for (int64_t l = threadIdx.x; l < iters; l += BT) {
-    const bool valid = l < total_leaves;
-    uint32_t key = 0xffffffffu, pts = 0;
-    if (valid) {
-      const uint32_t t = (uint32_t)lower_bound_f(s_thr, Ru, lbrow[l]);
-      lr[l] = (uint8_t)t;
-      key = t * (uint32_t)L + leaf_tree[l];
-      pts = leaf_range[2 * l + 1];
-      tl = max(tl, t);
+  for (int64_t l0 = threadIdx.x; l0 < iters; l0 += BT * BU) {
+    float lbv[BU];
+    uint32_t tr[BU], pc[BU];
+#pragma unroll
+    for (int u = 0; u < BU; ++u) {
+      const int64_t l = l0 + (int64_t)u * BT;
+      if (l < total_leaves) {
+        lbv[u] = lbrow[l];
+        tr[u] = leaf_tree[l];
+        pc[u] = leaf_range[2 * l + 1];
+      }
     }
-    const uint32_t peers = __match_any_sync(0xffffffffu, key);
-    const uint32_t sum = __reduce_add_sync(peers, pts);
-    if (valid && (peers & lt) == 0) {
-      atomicAdd(&s_cnt[key], (uint32_t)__popc(peers));
-      atomicAdd(&s_pts[key], sum);
+#pragma unroll
+    for (int u = 0; u < BU; ++u) {
+      const int64_t l = l0 + (int64_t)u * BT;
+      const bool valid = l < total_leaves;
+      uint32_t key = 0xffffffffu, pts = 0;
+      if (valid) {
+        const uint32_t t = (uint32_t)lower_bound_f(s_thr, Ru, lbv[u]);
+        lr[l] = (uint8_t)t;
+        key = t * (uint32_t)L + tr[u];
+        pts = pc[u];
+        tl = max(tl, t);
+      }
+      const uint32_t peers = __match_any_sync(0xffffffffu, key);
+      const uint32_t sum = __reduce_add_sync(peers, pts);
+      if (valid && (peers & lt) == 0) {
+        atomicAdd(&s_cnt[key], (uint32_t)__popc(peers));
+        atomicAdd(&s_pts[key], sum);
+      }
     }
   }
   tl = __reduce_max_sync(0xffffffffu, tl);
@@ -272,26 +288,36 @@ k_buckets(const float* __restrict__ lb2, int64_t total_leaves, const float* __re
   __syncthreads();
   const uint32_t tcap = (uint32_t)s_tcap;
   uint32_t* ql = list + qb * total_leaves;
-  for (int64_t l = threadIdx.x; l < iters; l += BT) {
-    uint32_t key = 0xffffffffu;
-    if (l < total_leaves) {
-      const uint32_t t = lr[l];
-      if (t <= tcap) key = t * (uint32_t)L + leaf_tree[l];
+  for (int64_t l0 = threadIdx.x; l0 < iters; l0 += BT * BU) {
+    uint32_t tv[BU], tr[BU];
+#pragma unroll
+    for (int u = 0; u < BU; ++u) {
+      const int64_t l = l0 + (int64_t)u * BT;
+      tv[u] = 0xffffffffu;
+      if (l < total_leaves) {
+        tv[u] = lr[l];
+        tr[u] = leaf_tree[l];
+      }
     }
-    const uint32_t peers = __match_any_sync(0xffffffffu, key);
-    const int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (key != 0xffffffffu && lane == leader) base = atomicAdd(&s_cnt[key], (uint32_t)__popc(peers));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (key != 0xffffffffu) ql[base + __popc(peers & lt)] = (uint32_t)l;
+#pragma unroll
+    for (int u = 0; u < BU; ++u) {
+      const int64_t l = l0 + (int64_t)u * BT;
+      const uint32_t key = (tv[u] <= tcap) ? tv[u] * (uint32_t)L + tr[u] : 0xffffffffu;
+      const uint32_t peers = __match_any_sync(0xffffffffu, key);
+      const int leader = __ffs(peers) - 1;
+      uint32_t base = 0;
+      if (key != 0xffffffffu && lane == leader) base = atomicAdd(&s_cnt[key], (uint32_t)__popc(peers));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (key != 0xffffffffu) ql[base + __popc(peers & lt)] = (uint32_t)l;
+    }
   }
 }
 
 // ------------------------------------------------------------------ walk
 constexpr int WT = 256;            // threads per walk CTA (several per SM)
 constexpr int WNW = WT / 32;
-constexpr int WBATCH = WT;         // leaves examined per batch step
-constexpr int WCAP = 4096;         // points examined per batch step
+constexpr int WBATCH = 2 * WT;     // leaves examined per batch step (two per thread)
+constexpr int WCAP = 8192;         // points examined per batch step
 constexpr int WILP = 4;            // points per thread in flight
 
 struct WalkArgs {
@@ -299,6 +325,7 @@ struct WalkArgs {
   int L;
   const uint32_t* leaf_ids;
   const uint32_t* leaf_range;
+  const uint16_t* leaf_tree;
   int64_t total_leaves;
   int64_t nqb;
   const float* lb2;
@@ -309,14 +336,15 @@ struct WalkArgs {
   uint32_t* cand;             // [nqb][cap]
   int64_t cap;
   uint32_t* round_end;        // [nqb][kRoundCap] |S| after each round
-  uint32_t* ws_newcnt;        // [grid][total_leaves]
+  uint32_t* ws_newcnt;        // [grid][2][max_bucket] new counts and lower-bound bits
+  int64_t max_bucket;         // most leaves a (round, tree) bucket can hold
   uint32_t* ws_bitmap;        // [grid][bitmap_words] when not in shared memory
   int64_t bitmap_words;
   int smem_bitmap;
 };
 
 struct WalkLayout {
-  size_t boff, pts, bpref, bstart, fmap, sel, misc, bitmap, total;
+  size_t boff, pts, bpref, bstart, newc, fmap, sel, misc, bitmap, total;
 };
 
 __host__ __device__ inline WalkLayout walk_layout(int L, int64_t smem_bitmap_words) {
@@ -332,6 +360,7 @@ __host__ __device__ inline WalkLayout walk_layout(int L, int64_t smem_bitmap_wor
   o.pts = take(sizeof(uint32_t) * RL);
   o.bpref = take(sizeof(uint32_t) * (WBATCH + 1));
   o.bstart = take(sizeof(uint32_t) * WBATCH);
+  o.newc = take(sizeof(uint32_t) * WBATCH);
   o.fmap = take(sizeof(uint16_t) * WCAP);
   o.sel = take(sizeof(unsigned long long) * 256);
   o.misc = take(sizeof(unsigned long long) * 32);
@@ -346,43 +375,63 @@ enum { W_S = 0, W_STOP, W_NEED, W_KSTAR, W_ACC, W_TOTNEW, W_QN, W_LEAFA, W_OFFA,
 // key is <= kstar when filtered) to the candidate list, in batches of at most
 // WCAP examined points: each point is tested-and-set in the bitmap and, if
 // new, written at the list's end.
+// With count_only the bitmap is only read: newcnt[j] receives the number of
+// points of leaf list[j] not yet in S, lbk[j] its lower-bound bits, and
+// misc[W_TOTNEW] their total.
 __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, bool filtered,
-                         unsigned long long kstar, const float* lbrow, int tree, unsigned char* sm,
-                         const WalkLayout& ly, uint32_t* bitmap, uint32_t* cand) {
+                         unsigned long long kstar, const float* lbrow, unsigned char* sm,
+                         const WalkLayout& ly, uint32_t* bitmap, uint32_t* cand,
+                         bool count_only = false, uint32_t* newcnt = nullptr,
+                         uint32_t* lbk = nullptr) {
   unsigned long long* misc = reinterpret_cast<unsigned long long*>(sm + ly.misc);
   uint32_t* bpref = reinterpret_cast<uint32_t*>(sm + ly.bpref);
   uint32_t* bstart = reinterpret_cast<uint32_t*>(sm + ly.bstart);
   uint16_t* fmap = reinterpret_cast<uint16_t*>(sm + ly.fmap);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
-  const uint32_t* tree_ids = a.leaf_ids + (int64_t)tree * a.n;
   __shared__ uint32_t s_w[WNW];
 
+  uint32_t* s_newc = reinterpret_cast<uint32_t*>(sm + ly.newc);
   if (threadIdx.x == 0) {
     misc[W_LEAFA] = 0;
     misc[W_OFFA] = 0;
+    misc[W_TOTNEW] = 0;
   }
+  if (count_only)
+    for (uint32_t j = threadIdx.x; j < nl; j += WT) newcnt[j] = 0;
   __syncthreads();
   while (true) {
     const uint32_t la = (uint32_t)misc[W_LEAFA];
     const uint32_t offa = (uint32_t)misc[W_OFFA];
     if (la >= nl) break;
-    // batch: leaves [la, la+nb) with their (filtered) counts, the first one from offa
+    // batch: leaves [la, la+nb) with their (filtered) counts, the first one from
+    // offa; thread t owns leaves 2t and 2t+1. bstart holds each leaf's first
+    // position in the concatenated per-tree id arrays.
     const uint32_t nb = min((uint32_t)WBATCH, nl - la);
-    uint32_t cnt = 0;
-    if (threadIdx.x < nb) {
-      const uint32_t leaf = list[la + threadIdx.x];
-      const uint32_t st = a.leaf_range[2 * (int64_t)leaf];
-      cnt = a.leaf_range[2 * (int64_t)leaf + 1];
-      if (filtered) {
-        const unsigned long long key =
-            ((unsigned long long)__float_as_uint(lbrow[leaf]) << 32) | (unsigned long long)leaf;
-        if (key > kstar) cnt = 0;
+    uint32_t c2[2] = {0u, 0u};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t j = 2 * threadIdx.x + h;
+      if (j < nb) {
+        const uint32_t leaf = list[la + j];
+        const uint32_t st = a.leaf_range[2 * (int64_t)leaf];
+        uint32_t cnt = a.leaf_range[2 * (int64_t)leaf + 1];
+        if (filtered) {
+          const unsigned long long key =
+              ((unsigned long long)__float_as_uint(lbrow[leaf]) << 32) | (unsigned long long)leaf;
+          if (key > kstar) cnt = 0;
+        }
+        if (j == 0) cnt = cnt >= offa ? cnt - offa : 0u;
+        c2[h] = cnt;
+        if (count_only) {
+          s_newc[j] = 0;
+          if (offa == 0 || j > 0) lbk[la + j] = __float_as_uint(lbrow[leaf]);
+        }
+        bstart[j] = (uint32_t)((int64_t)a.leaf_tree[leaf] * a.n) + st + (j == 0 ? offa : 0u);
       }
-      if (threadIdx.x == 0) cnt = cnt >= offa ? cnt - offa : 0u;
-      bstart[threadIdx.x] = st + (threadIdx.x == 0 ? offa : 0u);
     }
-    uint32_t x = cnt;   // inclusive scan over the block (WT == WBATCH)
+    const uint32_t cnt = c2[0] + c2[1];
+    uint32_t x = cnt;   // inclusive scan over the block of the per-thread pair sums
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -392,7 +441,9 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
     __syncthreads();
     uint32_t wb = 0;
     for (int qq = 0; qq < w; ++qq) wb += s_w[qq];
-    bpref[threadIdx.x + 1] = wb + x;   // bpref[j] = points before leaf j of the batch
+    const uint32_t before = wb + x - cnt;
+    bpref[2 * threadIdx.x + 1] = before + c2[0];   // bpref[j] = points before leaf j of the batch
+    bpref[2 * threadIdx.x + 2] = before + cnt;
     if (threadIdx.x == 0) bpref[0] = 0;
     __syncthreads();
     uint32_t take_leaves, take_pts;
@@ -423,8 +474,22 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
         ids[u] = 0xffffffffu;
         if (f < take_pts) {
           const uint32_t j = fmap[f];
-          ids[u] = __ldg(tree_ids + bstart[j] + (f - bpref[j]));
+          ids[u] = __ldg(a.leaf_ids + bstart[j] + (f - bpref[j]));
         }
+      }
+      if (count_only) {
+#pragma unroll
+        for (int u = 0; u < WILP; ++u) {
+          const uint32_t f = f0 + u * WT + threadIdx.x;
+          const uint32_t id = ids[u];
+          const bool fresh = id != 0xffffffffu && !((bitmap[id >> 5] >> (id & 31)) & 1u);
+          const uint32_t key = fresh ? (uint32_t)fmap[f] : 0xffffffffu;
+          const uint32_t peers = __match_any_sync(0xffffffffu, key);
+          if (fresh && (peers & lt) == 0) atomicAdd(&s_newc[key], (uint32_t)__popc(peers));
+          const uint32_t m = __ballot_sync(0xffffffffu, fresh);
+          if (lane == 0 && m) atomicAdd(&misc[W_TOTNEW], (unsigned long long)__popc(m));
+        }
+        continue;
       }
 #pragma unroll
       for (int u = 0; u < WILP; ++u) {
@@ -447,8 +512,12 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
       }
     }
     __syncthreads();
+    if (count_only) {
+      const uint32_t map_leaves2 = take_leaves == 0 ? 1u : take_leaves;
+      for (uint32_t j = threadIdx.x; j < map_leaves2; j += WT) newcnt[la + j] += s_newc[j];
+    }
     if (threadIdx.x == 0) {
-      misc[W_S] += misc[W_QN];
+      if (!count_only) misc[W_S] += misc[W_QN];
       if (take_leaves == 0) {
         const uint32_t first_total = bpref[1] + offa;  // points of leaf la (after filter)
         const uint32_t newoff = offa + take_pts;
@@ -470,7 +539,7 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
 }
 
 // One CTA per query (persistent over the batch): the buckets in Alg. 7 order.
-__global__ void __launch_bounds__(WT, 4) k_walk(WalkArgs a) {
+__global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
   const WalkLayout ly = walk_layout(a.L, a.smem_bitmap ? a.bitmap_words : 0);
   uint32_t* s_boff = reinterpret_cast<uint32_t*>(sm + ly.boff);
@@ -479,10 +548,11 @@ __global__ void __launch_bounds__(WT, 4) k_walk(WalkArgs a) {
   unsigned long long* misc = reinterpret_cast<unsigned long long*>(sm + ly.misc);
   uint32_t* bitmap = a.smem_bitmap ? reinterpret_cast<uint32_t*>(sm + ly.bitmap)
                                    : a.ws_bitmap + (int64_t)blockIdx.x * a.bitmap_words;
-  uint32_t* newcnt = a.ws_newcnt + (int64_t)blockIdx.x * a.total_leaves;
+  uint32_t* newcnt = a.ws_newcnt + (int64_t)blockIdx.x * 2 * a.max_bucket;
+  uint32_t* lbk = newcnt + a.max_bucket;
   const int L = a.L;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __shared__ unsigned long long s_red_u[WNW];
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
 
   for (int64_t qb = blockIdx.x; qb < a.nqb; qb += gridDim.x) {
     const float* lbrow = a.lb2 + qb * a.total_leaves;
@@ -505,7 +575,16 @@ __global__ void __launch_bounds__(WT, 4) k_walk(WalkArgs a) {
     __syncthreads();
     int t_end = tcap;
     for (int t = 0; t <= tcap; ++t) {
-      for (int i = 0; i < L; ++i) {
+      // a round whose points cannot bring |S| to T is taken in one step: the
+      // order of its trees does not change S
+      unsigned long long rpts = 0;
+      for (int i = 0; i < L; ++i) rpts += s_pts[t * L + i];
+      const bool whole_round = misc[W_S] + rpts < T;
+      if (whole_round) {
+        const uint32_t nl = s_boff[(t + 1) * L] - s_boff[t * L];
+        if (nl) walk_add(a, list + s_boff[t * L], nl, false, ~0ull, lbrow, sm, ly, bitmap, cand);
+      }
+      for (int i = 0; i < L && !whole_round; ++i) {
         const int b = t * L + i;
         const uint32_t nl = s_boff[b + 1] - s_boff[b];
         if (nl == 0) continue;
@@ -515,28 +594,7 @@ __global__ void __launch_bounds__(WT, 4) k_walk(WalkArgs a) {
         bool cut = false;
         if (S0 + bpts >= T) {
           // new points of every leaf of the bucket (bitmap read only)
-          unsigned long long tot = 0;
-          for (uint32_t j = (uint32_t)w; j < nl; j += WNW) {
-            const uint32_t lf = bl[j];
-            const uint32_t st = a.leaf_range[2 * (int64_t)lf], ct = a.leaf_range[2 * (int64_t)lf + 1];
-            const uint32_t* ids = a.leaf_ids + (int64_t)i * a.n + st;
-            uint32_t nw = 0;
-            for (uint32_t e = lane; e < ct; e += 32) {
-              const uint32_t id = ids[e];
-              nw += (bitmap[id >> 5] >> (id & 31)) & 1u ? 0u : 1u;
-            }
-            nw = __reduce_add_sync(0xffffffffu, nw);
-            if (lane == 0) newcnt[j] = nw;
-            tot += nw;
-          }
-          if (lane == 0) s_red_u[w] = tot;
-          __syncthreads();
-          if (threadIdx.x == 0) {
-            unsigned long long sum = 0;
-            for (int qq = 0; qq < WNW; ++qq) sum += s_red_u[qq];
-            misc[W_TOTNEW] = sum;
-          }
-          __syncthreads();
+          walk_add(a, bl, nl, false, ~0ull, lbrow, sm, ly, bitmap, cand, true, newcnt, lbk);
           cut = (S0 + misc[W_TOTNEW] >= T);
         }
         unsigned long long kstar = ~0ull;
@@ -553,12 +611,20 @@ __global__ void __launch_bounds__(WT, 4) k_walk(WalkArgs a) {
           for (int p = 7; p >= 0; --p) {
             for (int i2 = threadIdx.x; i2 < 256; i2 += WT) sel[i2] = 0;
             __syncthreads();
-            for (uint32_t j = threadIdx.x; j < nl; j += WT) {
-              const uint32_t lf = bl[j];
-              const unsigned long long key =
-                  ((unsigned long long)__float_as_uint(lbrow[lf]) << 32) | (unsigned long long)lf;
-              if ((key & pmask) == prefix && newcnt[j])
-                atomicAdd(&sel[(key >> (8 * p)) & 255ull], (unsigned long long)newcnt[j]);
+            const uint32_t iters_j = (nl + WT - 1) / WT * WT;
+            for (uint32_t j = threadIdx.x; j < iters_j; j += WT) {
+              uint32_t dg = 0xffffffffu, wgt = 0;
+              if (j < nl) {
+                const uint32_t c = newcnt[j];
+                const unsigned long long key = ((unsigned long long)lbk[j] << 32) | (unsigned long long)bl[j];
+                if (c && (key & pmask) == prefix) {
+                  dg = (uint32_t)((key >> (8 * p)) & 255ull);
+                  wgt = c;
+                }
+              }
+              const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+              const uint32_t sum = __reduce_add_sync(peers, wgt);
+              if (dg != 0xffffffffu && (peers & lt) == 0) atomicAdd(&sel[dg], (unsigned long long)sum);
             }
             __syncthreads();
             if (threadIdx.x < 32) {
@@ -601,7 +667,7 @@ __global__ void __launch_bounds__(WT, 4) k_walk(WalkArgs a) {
           }
           kstar = prefix;
         }
-        walk_add(a, bl, nl, cut, kstar, lbrow, i, sm, ly, bitmap, cand);
+        walk_add(a, bl, nl, cut, kstar, lbrow, sm, ly, bitmap, cand);
         if (cut) {
           if (threadIdx.x == 0) misc[W_STOP] = 1;
           break;
@@ -971,7 +1037,10 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
   DL_TRY(rend.alloc(sizeof(uint32_t) * qb * kRoundCap, s));
   DL_TRY(thr.alloc(sizeof(float) * 2 * qb * kRoundCap, s));
   DL_TRY(meta.alloc(sizeof(uint32_t) * qb * MQ_WORDS, s));
-  DL_TRY(ws_new.alloc(sizeof(uint32_t) * wgrid * TL, s));
+  int64_t max_tree_leaves = 1;
+  for (int t = 0; t < L; ++t)
+    max_tree_leaves = std::max<int64_t>(max_tree_leaves, idx->leaf_base_h[t + 1] - idx->leaf_base_h[t]);
+  DL_TRY(ws_new.alloc(sizeof(uint32_t) * 2 * wgrid * max_tree_leaves, s));
   if (!smem_bitmap) DL_TRY(ws_bm.alloc(sizeof(uint32_t) * wgrid * words, s));
   uint32_t* d_min = mm.as<uint32_t>();
   uint32_t* d_max = d_min + qb;
@@ -1014,6 +1083,7 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
     wa.L = L;
     wa.leaf_ids = idx->leaf_ids;
     wa.leaf_range = idx->leaf_range;
+    wa.leaf_tree = idx->leaf_tree;
     wa.total_leaves = TL;
     wa.nqb = nqb;
     wa.lb2 = lb.as<float>();
@@ -1025,6 +1095,7 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
     wa.cap = cap;
     wa.round_end = rend.as<uint32_t>();
     wa.ws_newcnt = ws_new.as<uint32_t>();
+    wa.max_bucket = max_tree_leaves;
     wa.ws_bitmap = smem_bitmap ? nullptr : ws_bm.as<uint32_t>();
     wa.bitmap_words = words;
     wa.smem_bitmap = smem_bitmap ? 1 : 0;
