@@ -193,6 +193,7 @@ def gpu_arm(args, rank, world, local_rank):
     from workloads import gaussian_projection, make_workload, sample_ids
 
     pkg.build()
+    proj_mode = 1 if args.proj == "bf16" else 0
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w = WORKLOAD
@@ -209,7 +210,8 @@ def gpu_arm(args, rank, world, local_rank):
            torch.empty(nq, 4, dtype=torch.int32, device=dev))
 
     def step():
-        idx = pkg.detlsh_build(X, A, ids, w["K"], w["L"], w["n_regions"], w["max_leaf"], borrow=True)
+        idx = pkg.detlsh_build(X, A, ids, w["K"], w["L"], w["n_regions"], w["max_leaf"], borrow=True,
+                               proj_mode=proj_mode)
         pkg.detlsh_query(idx, Q, kk, cc, rr, k_max=w["k"], eps=eps, beta=w["beta"], out=out)
         tr = pkg.detlsh_trace_get()
         info = idx.info()
@@ -255,7 +257,8 @@ def gpu_arm(args, rank, world, local_rank):
     mean_S = float(stats[:, 0].astype("float64").mean())
     s_in = 4
     total_leaves = info["total_leaves"]
-    enc_bytes = w["n"] * (w["d"] * s_in + w["K"] * w["L"])
+    # encoding reads the points (FP32, or the BF16 copy on the tensor-core path) and writes codes
+    enc_bytes = w["n"] * (w["d"] * (2 if proj_mode else s_in) + w["K"] * w["L"])
     # algorithmic bytes per step of each query kernel: the candidate rows and
     # ids (k_dist), the lower-bound rows plus leaf ids (k_walk), the candidate
     # distances and ids (k_finalize), the leaf table and lower bounds (k_leaf_lb)
@@ -264,7 +267,7 @@ def gpu_arm(args, rank, world, local_rank):
         "k_dist": (n_cand * (w["d"] * s_in + 4 + 4), ph["dist_ms"], ph["dist_launches"]),
         "k_walk": (nq * total_leaves * 4.0 + n_cand * 8, ph["walk_ms"], ph["dist_launches"]),
         "k_finalize": (n_cand * 8.0, ph["finalize_ms"], ph["dist_launches"]),
-        "k_project_encode": (enc_bytes, ph["encode_ms"], 1.0),
+        ("k_project_tc" if proj_mode else "k_project_encode"): (enc_bytes, ph["encode_ms"], 1.0),
         "k_leaf_lb": (nq * total_leaves * 4.0 + ph["lb_launches"] * total_leaves * (2 * w["K"] + 10.0),
                       ph["lb_ms"], ph["lb_launches"]),
     }
@@ -301,7 +304,7 @@ def gpu_arm(args, rank, world, local_rank):
     pkg.detlsh_trace_enable(False)
 
     def step_host():
-        idx = pkg.detlsh_build(Xh, Ah, idh, w["K"], w["L"], w["n_regions"], w["max_leaf"])
+        idx = pkg.detlsh_build(Xh, Ah, idh, w["K"], w["L"], w["n_regions"], w["max_leaf"], proj_mode=proj_mode)
         pkg.detlsh_query(idx, Qh, kh, ch, rh, k_max=w["k"], eps=eps, beta=w["beta"], out=outh)
         idx.free()
 
@@ -332,7 +335,8 @@ def gpu_arm(args, rank, world, local_rank):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": workload_desc(), **w, "parallelism": f"replicas x{world}",
+                "config": {"workload": workload_desc(), **w, "projection": args.proj,
+                           "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (X is 512 MB)"},
                 "clocks": clk,
                 "e2e": {"value": world * nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
@@ -358,6 +362,8 @@ def main():
     ap.add_argument("--cpu-queries", type=int, default=8)
     ap.add_argument("--nq", type=int, default=WORKLOAD["nq"], help="queries per step (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--proj", default="fp32", choices=["fp32", "bf16"],
+                    help="projection arithmetic of the build (bf16: tensor cores)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

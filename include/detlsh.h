@@ -43,7 +43,13 @@ typedef enum { DETLSH_MEM_HOST = 0, DETLSH_MEM_DEVICE = 1 } detlsh_mem;
 
 /* projection arithmetic of the build (Eq. 1 for every point) */
 typedef enum {
-  DETLSH_PROJ_FP32 = 0   /* FP32 fused multiply-add on the CUDA cores */
+  DETLSH_PROJ_FP32 = 0,  /* FP32 fused multiply-add on the CUDA cores */
+  DETLSH_PROJ_BF16 = 1   /* BF16 inputs (points and hash vectors rounded to
+                            BF16; the index keeps a BF16 copy of X) on the
+                            tensor cores with FP32 accumulation; needs
+                            d % 8 == 0 and L*K <= 64. Codes are exact for
+                            their BF16 inputs; queries are projected the same
+                            way; the exact re-rank still uses FP32 X. */
 } detlsh_proj_mode;
 
 /* detlsh_params.flags */
@@ -100,7 +106,8 @@ typedef struct {
  * DETLSH_BORROW_X). The index is read-only afterwards; concurrent queries on
  * different streams are safe.
  * Errors: DETLSH_EINVAL for sizes or parameters outside the limits above,
- * DETLSH_ENOMEM, DETLSH_ECUDA.
+ * DETLSH_ENOMEM, DETLSH_ECUDA, DETLSH_ETIMEOUT (a bounded wait of the
+ * tensor-core kernel ran out).
  */
 int detlsh_build(const void* X, int64_t n, int32_t d, int32_t dtype,
                  const float* A, const int64_t* sample_ids,

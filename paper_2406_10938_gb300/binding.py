@@ -157,13 +157,16 @@ class Index:
         return detlsh_info(self)
 
 
+PROJ_FP32, PROJ_BF16 = 0, 1
+
+
 def detlsh_build(X: torch.Tensor, A: torch.Tensor, sample_ids: torch.Tensor, K: int, L: int,
-                 n_regions: int, max_leaf: int, borrow: bool = False) -> Index:
+                 n_regions: int, max_leaf: int, borrow: bool = False, proj_mode: int = 0) -> Index:
     X = X.contiguous()
     A = A.contiguous().to(torch.float32)
     sample_ids = sample_ids.contiguous().to(torch.int64)
     mem = _mem_of(X, A, sample_ids)
-    p = Params(K=K, L=L, n_regions=n_regions, max_leaf=max_leaf, n_s=sample_ids.numel(), proj_mode=0,
+    p = Params(K=K, L=L, n_regions=n_regions, max_leaf=max_leaf, n_s=sample_ids.numel(), proj_mode=proj_mode,
                flags=BORROW_X if (borrow and mem == MEM_DEVICE) else 0)
     out = ctypes.c_void_p(0)
     st = lib().detlsh_build(_ptr(X), X.shape[0], X.shape[1], _dtype_code(X), _ptr(A), _ptr(sample_ids),

@@ -138,7 +138,7 @@ void free_index(detlsh_index* idx) {
   if (idx->owns_x && idx->X) cudaFree(const_cast<void*>(idx->X));
   void* arrays[] = {idx->A, idx->At, idx->E, idx->Ps, idx->codes, idx->leaf_ids, idx->leaf_base,
                     idx->leaf_range, idx->leaf_plen, idx->leaf_prefix, idx->leaf_lo, idx->leaf_hi,
-                    idx->leaf_tree};
+                    idx->leaf_tree, idx->Xb, idx->Ab, idx->d_err};
   for (void* p : arrays)
     if (p) cudaFree(p);
   delete idx;
@@ -158,6 +158,7 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
   idx->bits = log2i(Nr);
   idx->max_leaf = prm->max_leaf;
   idx->n_s = prm->n_s;
+  idx->proj_mode = prm->proj_mode;
   DL_CUDA(cudaGetDevice(&idx->device));
 
   const size_t xbytes = (size_t)n * d * dtype_size(dtype);
@@ -195,17 +196,44 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
   DL_CUDA(cudaMalloc(&idx->E, sizeof(float) * LK * (Nr + 1)));
   DL_CUDA(cudaMalloc(&idx->codes, (size_t)n * LK));
   DL_CUDA(cudaMalloc(&idx->leaf_ids, sizeof(uint32_t) * n * L));
-  tm.begin(TR_SAMPLE_PROJ);
-  DL_TRY(launch_project_t(idx->X, dtype, prm->n_s, d, static_cast<const int64_t*>(ids.d), idx->At, LK,
-                          idx->Ps, 1, prm->n_s, s));
-  tm.end();
-  tm.begin(TR_BREAKPOINTS);
-  DL_TRY(select_breakpoints(idx->Ps, prm->n_s, LK, Nr, idx->E, s));
-  tm.end();
-  // Alg. 2: codes of every point, fused with the projection
-  tm.begin(TR_ENCODE);
-  DL_TRY(launch_project_encode_t(idx->X, dtype, n, d, idx->At, K, L, idx->E, Nr, idx->codes, s));
-  tm.end();
+  if (prm->proj_mode == DETLSH_PROJ_BF16) {
+    // BF16 copies of X and A; projections on the tensor cores
+    const int N = (LK + 15) / 16 * 16;
+    DL_CUDA(cudaMalloc(&idx->Xb, (size_t)n * d * 2));
+    DL_CUDA(cudaMalloc(&idx->Ab, (size_t)N * d * 2));
+    DL_CUDA(cudaMalloc(&idx->d_err, sizeof(int)));
+    DL_CUDA(cudaMemsetAsync(idx->Ab, 0, (size_t)N * d * 2, s));
+    DL_CUDA(cudaMemsetAsync(idx->d_err, 0, sizeof(int), s));
+    tm.begin(TR_SAMPLE_PROJ);
+    DL_TRY(to_bf16(idx->X, dtype, n * d, idx->Xb, s));
+    DL_TRY(to_bf16(idx->A, DETLSH_F32, (int64_t)LK * d, idx->Ab, s));
+    Scratch xs;
+    DL_TRY(xs.alloc((size_t)prm->n_s * d * 2, s));
+    DL_TRY(gather_rows_bf16(idx->Xb, d, static_cast<const int64_t*>(ids.d), prm->n_s, xs.p, s));
+    DL_TRY(launch_project_tc(xs.p, prm->n_s, d, idx->Ab, LK, K, nullptr, Nr, nullptr, idx->Ps, 1,
+                             prm->n_s, idx->d_err, s));
+    tm.end();
+    tm.begin(TR_BREAKPOINTS);
+    DL_TRY(select_breakpoints(idx->Ps, prm->n_s, LK, Nr, idx->E, s));
+    tm.end();
+    tm.begin(TR_ENCODE);
+    DL_TRY(launch_project_tc(idx->Xb, n, d, idx->Ab, LK, K, idx->E, Nr, idx->codes, nullptr, 0, 0,
+                             idx->d_err, s));
+    tm.end();
+    DL_TRY(check_tc_error(idx->d_err, s));
+  } else {
+    tm.begin(TR_SAMPLE_PROJ);
+    DL_TRY(launch_project_t(idx->X, dtype, prm->n_s, d, static_cast<const int64_t*>(ids.d), idx->At, LK,
+                            idx->Ps, 1, prm->n_s, s));
+    tm.end();
+    tm.begin(TR_BREAKPOINTS);
+    DL_TRY(select_breakpoints(idx->Ps, prm->n_s, LK, Nr, idx->E, s));
+    tm.end();
+    // Alg. 2: codes of every point, fused with the projection
+    tm.begin(TR_ENCODE);
+    DL_TRY(launch_project_encode_t(idx->X, dtype, n, d, idx->At, K, L, idx->E, Nr, idx->codes, s));
+    tm.end();
+  }
   // Alg. 3: leaves
   tm.begin(TR_LEAVES);
   DL_TRY(build_leaves(idx, s));
@@ -277,7 +305,9 @@ int detlsh_build(const void* X, int64_t n, int32_t d, int32_t dtype, const float
   DL_REQUIRE(d >= 1 && d <= 65536, "d must be in [1, 65536]");
   DL_REQUIRE(n >= 1 && n * (int64_t)p.L < ((int64_t)1 << 32), "need 1 <= n and n*L < 2^32");
   DL_REQUIRE(p.n_s >= p.n_regions && p.n_s <= n, "need n_regions <= n_s <= n");
-  DL_REQUIRE(p.proj_mode == DETLSH_PROJ_FP32, "unsupported proj_mode");
+  DL_REQUIRE(p.proj_mode == DETLSH_PROJ_FP32 || p.proj_mode == DETLSH_PROJ_BF16, "unsupported proj_mode");
+  DL_REQUIRE(p.proj_mode != DETLSH_PROJ_BF16 || (d % 8 == 0 && p.K * p.L <= 64),
+             "the BF16 projection needs d %% 8 == 0 and L*K <= 64");
   DL_REQUIRE(p.n_s * (int64_t)p.K * p.L < ((int64_t)1 << 32), "n_s*L*K must be < 2^32");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   trace_reset(TR_SAMPLE_PROJ, TR_LEAVES);

@@ -117,6 +117,10 @@ struct detlsh_index {
   int32_t d = 0, dtype = 0, K = 0, L = 0, Nr = 0, bits = 0, max_leaf = 0;
   int64_t n_s = 0;
   int32_t device = 0;
+  int32_t proj_mode = 0;
+  void* Xb = nullptr;               // [n][d] BF16 copy of X (BF16 projection mode)
+  void* Ab = nullptr;               // [N][d] BF16 hash vectors, N = L*K rounded up to 16
+  int* d_err = nullptr;             // error word of the tensor-core kernel
   bool owns_x = true;
   const void* X = nullptr;          // [n][d] f32 or u8
   float* A = nullptr;               // [LK][d]
@@ -152,6 +156,14 @@ int launch_project_encode_t(const void* X, int dtype, int64_t n, int d, const fl
                             cudaStream_t s);
 int launch_encode_values(const float* P, int64_t n, int LK, const float* E, int Nr,
                          uint8_t* codes, cudaStream_t s);
+
+// ---- tensor-core projection (project_tc.cu)
+int to_bf16(const void* X, int dtype, int64_t count, void* Y, cudaStream_t s);
+int gather_rows_bf16(const void* Xb, int d, const int64_t* ids, int64_t m, void* Y, cudaStream_t s);
+int launch_project_tc(const void* Xb, int64_t rows, int d, const void* Ab, int LK, int K,
+                      const float* E, int Nr, uint8_t* codes, float* P, int64_t p_so, int64_t p_sr,
+                      int* d_err, cudaStream_t s);
+int check_tc_error(int* d_err, cudaStream_t s);
 
 // ---- sorting / scans (sort.cu)
 // Stable LSD radix sort of (key, value) pairs on key bits [bit_lo, bit_hi).

@@ -1,0 +1,449 @@
+// Eq. 1 projection on the 5th-generation tensor cores (BF16 inputs, FP32
+// accumulation in tensor memory), fused with the Alg. 2 encoding.
+//
+// P = Xb * Abᵀ for a BF16 copy Xb [rows][d] of the points and the BF16 hash
+// matrix Ab [N][d] (N = L*K padded to a multiple of 16, extra rows zero).
+// Persistent CTAs, one per SM, 256 threads in four roles:
+//   warp 0  TMA producer: 128-row tiles of Xb and the matching chunk of Ab,
+//           64 elements (128 B) of d per stage, 128-byte swizzle, a ring of
+//           stages guarded by full/empty mbarriers;
+//   warp 1  MMA issuer (one thread): tcgen05.mma M=128, N, K=16 into one of
+//           two TMEM accumulators, tcgen05.commit frees a stage / publishes
+//           an accumulator;
+//   warp 2  owns the TMEM allocation;
+//   warps 4-7 epilogue: tcgen05.ld of the 128 x N accumulator (one row per
+//           thread), then either the breakpoint search of Alg. 2 (shared
+//           memory) and 16-byte code stores, or the FP32 projections.
+// Every mbarrier wait is bounded by %globaltimer; a wait that runs out sets
+// an error word (the host reports DETLSH_ETIMEOUT) and the roles wind down.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace detlsh {
+namespace {
+
+constexpr int TC_M = 128;          // rows (points) per tile
+constexpr int TC_KC = 64;          // d elements per stage (128 bytes of BF16)
+constexpr int TC_STAGES = 4;
+constexpr int TC_THREADS = 256;
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;   // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity; false (and *err set) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (globaltimer() - t0 > TC_WAIT_NS || *(volatile int*)err) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(dst),
+      "l"(tm), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptor: K-major tile of 128-byte rows with the
+// 128-byte swizzle (8-row groups 1024 bytes apart), tcgen05 format.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);          // start address
+  d |= (uint64_t)(16u >> 4) << 16;                   // leading byte offset (unused here)
+  d |= (uint64_t)(1024u >> 4) << 32;                 // stride byte offset: 8 rows
+  d |= (uint64_t)1 << 46;                            // descriptor version
+  d |= (uint64_t)2 << 61;                            // 128-byte swizzle
+  return d;
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Number of interior breakpoints e_z (z = 1..Nr-1, e[z]) with e_z <= p.
+__device__ __forceinline__ int region_of_tc(const float* e, int Nr, float p) {
+  int pos = 0;
+  for (int step = Nr >> 1; step > 0; step >>= 1) pos += (e[pos + step] <= p) ? step : 0;
+  return pos;
+}
+
+struct TcArgs {
+  int64_t rows;
+  int d, LK, K, Nr;
+  const float* E;        // [LK][Nr+1] (encode mode)
+  uint8_t* codes;        // [L][rows][K] (encode mode)
+  float* P;              // projections (store mode)
+  int64_t p_so, p_sr;
+  int* err;
+};
+
+template <int N, bool ENCODE>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA,
+             TcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  // 1024-byte aligned base for the swizzled tiles
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  constexpr uint32_t XBYTES = TC_M * 128;
+  constexpr uint32_t ABYTES = N * 128;
+  uint8_t* sx = base;                                  // [STAGES][XBYTES]
+  uint8_t* sa = sx + TC_STAGES * XBYTES;               // [STAGES][ABYTES]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sa + TC_STAGES * ABYTES);
+  // full[0..S), empty[S..2S), tfull[2S..2S+2), tempty[2S+2..2S+4)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 4);
+  float* Es = reinterpret_cast<float*>(bars + 2 * TC_STAGES + 8);   // [LK][Nr] (ENCODE)
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = (a.rows + TC_M - 1) / TC_M;
+  const int nk = (a.d + TC_KC - 1) / TC_KC;
+  int* err = a.err;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[TC_STAGES + s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bars[2 * TC_STAGES + b]), 1);
+      mbar_init(smem_u32(&bars[2 * TC_STAGES + 2 + b]), 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (ENCODE) {
+    for (int i = threadIdx.x; i < a.LK * a.Nr; i += TC_THREADS) {
+      const int h = i / a.Nr, z = i % a.Nr;
+      Es[i] = z > 0 ? a.E[(int64_t)h * (a.Nr + 1) + z] : 0.f;
+    }
+  }
+  constexpr uint32_t TCOLS = (2 * N <= 32) ? 32 : (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : 256;
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    uint32_t it = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (int kc = 0; kc < nk && ok; ++kc, ++it) {
+        const uint32_t s = it % TC_STAGES, r = it / TC_STAGES;
+        ok = mbar_wait(smem_u32(&bars[TC_STAGES + s]), (r & 1) ^ 1, err);
+        if (!ok) break;
+        const uint32_t full = smem_u32(&bars[s]);
+        mbar_expect_tx(full, XBYTES + ABYTES);
+        tma_load_2d(smem_u32(sx + s * XBYTES), &tmX, kc * TC_KC, (int)(tile * TC_M), full);
+        tma_load_2d(smem_u32(sa + s * ABYTES), &tmA, kc * TC_KC, 0, full);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    constexpr uint32_t idesc = (1u << 4)            // D: FP32
+                               | (1u << 7)          // A: BF16
+                               | (1u << 10)         // B: BF16
+                               | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+    uint32_t it = 0, lt = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
+      const uint32_t ab = lt & 1, use = lt >> 1;
+      ok = mbar_wait(smem_u32(&bars[2 * TC_STAGES + 2 + ab]), (use & 1) ^ 1, err);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t dt = tmem + ab * (TCOLS / 2);
+      for (int kc = 0; kc < nk; ++kc, ++it) {
+        const uint32_t s = it % TC_STAGES, r = it / TC_STAGES;
+        ok = mbar_wait(smem_u32(&bars[s]), r & 1, err);
+        if (!ok) break;
+        tc_fence_after();
+        const uint64_t ad = smem_desc(smem_u32(sx + s * XBYTES));
+        const uint64_t bd = smem_desc(smem_u32(sa + s * ABYTES));
+#pragma unroll
+        for (int k = 0; k < TC_KC / 16; ++k)   // 16 BF16 = 32 bytes = 2 in descriptor units
+          mma_bf16(dt, ad + 2 * k, bd + 2 * k, idesc, (kc > 0 || k > 0) ? 1u : 0u);
+        mma_commit(smem_u32(&bars[TC_STAGES + s]));
+      }
+      if (!ok) break;
+      mma_commit(smem_u32(&bars[2 * TC_STAGES + ab]));
+    }
+  } else if (warp >= 4) {
+    // ---- epilogue: one accumulator row (point) per thread
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    uint32_t lt = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+      const uint32_t ab = lt & 1, use = lt >> 1;
+      if (!mbar_wait(smem_u32(&bars[2 * TC_STAGES + ab]), use & 1, err)) break;
+      tc_fence_after();
+      float v[(N + 31) / 32 * 32];
+#pragma unroll
+      for (int c = 0; c < N; c += 32)
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + ab * (TCOLS / 2) + c, v + c);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars[2 * TC_STAGES + 2 + ab]));
+      const int64_t p = tile * TC_M + row;
+      if (p < a.rows) {
+        if (ENCODE) {
+          if (a.K == 16) {
+#pragma unroll
+            for (int g = 0; g < N / 16; ++g) {
+              if (g * 16 < a.LK) {
+                uint32_t wv[4];
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                  uint32_t x = 0;
+#pragma unroll
+                  for (int b = 0; b < 4; ++b) {
+                    const int h = g * 16 + qq * 4 + b;
+                    x |= (uint32_t)region_of_tc(Es + h * a.Nr, a.Nr, v[h]) << (8 * b);
+                  }
+                  wv[qq] = x;
+                }
+                *reinterpret_cast<uint4*>(a.codes + ((int64_t)g * a.rows + p) * 16) =
+                    make_uint4(wv[0], wv[1], wv[2], wv[3]);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int h = 0; h < N; ++h) {
+              if (h < a.LK) {
+                const int tree = h / a.K, j = h % a.K;
+                a.codes[((int64_t)tree * a.rows + p) * a.K + j] =
+                    (uint8_t)region_of_tc(Es + h * a.Nr, a.Nr, v[h]);
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int h = 0; h < N; ++h)
+            if (h < a.LK) a.P[p * a.p_so + (int64_t)h * a.p_sr] = v[h];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 2)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
+}
+
+__global__ void k_to_bf16_f32(const float* __restrict__ x, int64_t count, __nv_bfloat16* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+__global__ void k_to_bf16_u8(const uint8_t* __restrict__ x, int64_t count, __nv_bfloat16* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn((float)x[i]);
+}
+// rows of a BF16 matrix gathered by id (the sample)
+__global__ void k_gather_rows_bf16(const __nv_bfloat16* __restrict__ x, int d, const int64_t* __restrict__ ids,
+                                   int64_t m, __nv_bfloat16* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m * d;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / d, c = i % d;
+    y[i] = x[ids[r] * d + c];
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+int make_map(CUtensorMap* tm, const void* ptr, int64_t rows, int d, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is unavailable");
+    return DETLSH_ECUDA;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)d * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_KC, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  const CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box,
+                        es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return DETLSH_ECUDA;
+  }
+  return DETLSH_OK;
+}
+
+template <int N, bool ENCODE>
+int launch_tc(const CUtensorMap& tx, const CUtensorMap& ta, const TcArgs& args, cudaStream_t s) {
+  size_t smem = 1024 + TC_STAGES * (TC_M * 128 + N * 128) + (2 * TC_STAGES + 8) * 8;
+  if (ENCODE) smem += sizeof(float) * (size_t)args.LK * args.Nr;
+  auto kern = k_project_tc<N, ENCODE>;
+  DL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, nsm = 0;
+  DL_CUDA(cudaGetDevice(&dev));
+  DL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t ntiles = (args.rows + TC_M - 1) / TC_M;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, nsm));
+  kern<<<grid, TC_THREADS, smem, s>>>(tx, ta, args);
+  DL_LAUNCH();
+  return DETLSH_OK;
+}
+
+}  // namespace
+
+int to_bf16(const void* X, int dtype, int64_t count, void* Y, cudaStream_t s) {
+  if (count == 0) return DETLSH_OK;
+  const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(count, 256), 152 * 32);
+  if (dtype == DETLSH_U8)
+    k_to_bf16_u8<<<blocks, 256, 0, s>>>(static_cast<const uint8_t*>(X), count,
+                                        static_cast<__nv_bfloat16*>(Y));
+  else
+    k_to_bf16_f32<<<blocks, 256, 0, s>>>(static_cast<const float*>(X), count,
+                                         static_cast<__nv_bfloat16*>(Y));
+  DL_LAUNCH();
+  return DETLSH_OK;
+}
+
+int gather_rows_bf16(const void* Xb, int d, const int64_t* ids, int64_t m, void* Y, cudaStream_t s) {
+  if (m == 0) return DETLSH_OK;
+  const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(m * d, 256), 152 * 32);
+  k_gather_rows_bf16<<<blocks, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(Xb), d, ids, m,
+                                            static_cast<__nv_bfloat16*>(Y));
+  DL_LAUNCH();
+  return DETLSH_OK;
+}
+
+int check_tc_error(int* d_err, cudaStream_t s) {
+  int h = 0;
+  DL_CUDA(cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DL_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    set_error("a bounded wait in the tensor-core projection ran out");
+    return DETLSH_ETIMEOUT;
+  }
+  return DETLSH_OK;
+}
+
+// P = Xb * Abᵀ on the tensor cores; with E/codes: encoded, else FP32 into P.
+int launch_project_tc(const void* Xb, int64_t rows, int d, const void* Ab, int LK, int K,
+                      const float* E, int Nr, uint8_t* codes, float* P, int64_t p_so, int64_t p_sr,
+                      int* d_err, cudaStream_t s) {
+  if (rows == 0) return DETLSH_OK;
+  const int N = (LK + 15) / 16 * 16;
+  if (N > 64 || d % 8 != 0) {
+    set_error("tensor-core projection needs L*K <= 64 and d a multiple of 8");
+    return DETLSH_EINVAL;
+  }
+  CUtensorMap tx, ta;
+  DL_TRY(make_map(&tx, Xb, rows, d, TC_M));
+  DL_TRY(make_map(&ta, Ab, N, d, N));
+  TcArgs args{};
+  args.rows = rows;
+  args.d = d;
+  args.LK = LK;
+  args.K = K;
+  args.Nr = Nr;
+  args.E = E;
+  args.codes = codes;
+  args.P = P;
+  args.p_so = p_so;
+  args.p_sr = p_sr;
+  args.err = d_err;
+  const bool enc = codes != nullptr;
+#define DL_TC_CASE(NN)                                                        \
+  case NN:                                                                    \
+    return enc ? launch_tc<NN, true>(tx, ta, args, s) : launch_tc<NN, false>(tx, ta, args, s);
+  switch (N) {
+    DL_TC_CASE(16)
+    DL_TC_CASE(32)
+    DL_TC_CASE(48)
+    DL_TC_CASE(64)
+    default:
+      break;
+  }
+#undef DL_TC_CASE
+  set_error("unsupported projection width %d", N);
+  return DETLSH_EINVAL;
+}
+
+}  // namespace detlsh

@@ -995,8 +995,17 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
   DL_TRY(qp.alloc(sizeof(float) * nq * LK, s));
   PhaseTimer tm(s);
   tm.begin(TR_QUERY_PROJ);
-  DL_TRY(launch_project_t(Q, idx->dtype, nq, idx->d, nullptr, idx->At, LK, qp.as<float>(), LK, 1,
-                          s));
+  if (idx->proj_mode == DETLSH_PROJ_BF16) {
+    Scratch qb16;
+    DL_TRY(qb16.alloc((size_t)nq * idx->d * 2, s));
+    DL_TRY(to_bf16(Q, idx->dtype, nq * idx->d, qb16.p, s));
+    DL_TRY(launch_project_tc(qb16.p, nq, idx->d, idx->Ab, LK, idx->K, nullptr, idx->Nr, nullptr,
+                             qp.as<float>(), LK, 1, idx->d_err, s));
+    DL_TRY(check_tc_error(idx->d_err, s));
+  } else {
+    DL_TRY(launch_project_t(Q, idx->dtype, nq, idx->d, nullptr, idx->At, LK, qp.as<float>(), LK, 1,
+                            s));
+  }
   tm.end();
 
   // walk configuration: the dedup bitmap in shared memory when it fits
