@@ -212,7 +212,8 @@ def gpu_arm(args, rank, world, local_rank):
     def step():
         idx = pkg.detlsh_build(X, A, ids, w["K"], w["L"], w["n_regions"], w["max_leaf"], borrow=True,
                                proj_mode=proj_mode)
-        pkg.detlsh_query(idx, Q, kk, cc, rr, k_max=w["k"], eps=eps, beta=w["beta"], out=out)
+        pkg.detlsh_query(idx, Q, kk, cc, rr, k_max=w["k"], eps=eps, beta=w["beta"], out=out,
+                         shortlist=args.shortlist)
         tr = pkg.detlsh_trace_get()
         info = idx.info()
         idx.free()
@@ -264,7 +265,8 @@ def gpu_arm(args, rank, world, local_rank):
     # distances and ids (k_finalize), the leaf table and lower bounds (k_leaf_lb)
     n_cand = float(stats[:, 0].astype("float64").sum())
     cand = {
-        "k_dist": (n_cand * (w["d"] * s_in + 4 + 4), ph["dist_ms"], ph["dist_launches"]),
+        ("k_dist_bf16" if args.shortlist else "k_dist"): (
+            n_cand * (w["d"] * (2 if args.shortlist else s_in) + 4 + 4), ph["dist_ms"], ph["dist_launches"]),
         "k_walk": (nq * total_leaves * 4.0 + n_cand * 8, ph["walk_ms"], ph["dist_launches"]),
         "k_finalize": (n_cand * 8.0, ph["finalize_ms"], ph["dist_launches"]),
         ("k_project_tc" if proj_mode else "k_project_encode"): (enc_bytes, ph["encode_ms"], 1.0),
@@ -305,7 +307,8 @@ def gpu_arm(args, rank, world, local_rank):
 
     def step_host():
         idx = pkg.detlsh_build(Xh, Ah, idh, w["K"], w["L"], w["n_regions"], w["max_leaf"], proj_mode=proj_mode)
-        pkg.detlsh_query(idx, Qh, kh, ch, rh, k_max=w["k"], eps=eps, beta=w["beta"], out=outh)
+        pkg.detlsh_query(idx, Qh, kh, ch, rh, k_max=w["k"], eps=eps, beta=w["beta"], out=outh,
+                         shortlist=args.shortlist)
         idx.free()
 
     step_host()
@@ -336,6 +339,7 @@ def gpu_arm(args, rank, world, local_rank):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": workload_desc(), **w, "projection": args.proj,
+                           "shortlist": args.shortlist,
                            "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (X is 512 MB)"},
                 "clocks": clk,
@@ -364,6 +368,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--proj", default="fp32", choices=["fp32", "bf16"],
                     help="projection arithmetic of the build (bf16: tensor cores)")
+    ap.add_argument("--shortlist", type=int, default=0,
+                    help="with --proj bf16: coarse BF16 candidate distances, FP32 re-rank of this many")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -371,6 +377,8 @@ def main():
     WORKLOAD["nq"] = args.nq
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.shortlist and args.proj != "bf16":
+        ap.error("--shortlist needs --proj bf16")
     if world > 1:
         import torch
         import torch.distributed as dist

@@ -81,6 +81,13 @@ typedef struct {
                          query (unordered ids; the first |S| entries), in
                          the call's `mem` space; NULL to skip               */
   int64_t cand_cap;   /* capacity per query of cand_ids                      */
+  int32_t shortlist;  /* 0: exact FP32 distances for every candidate. > 0
+                         (index built with DETLSH_PROJ_BF16, at most 4096):
+                         candidate distances from the BF16 copy of X (FP32
+                         accumulation, used also by the "within c*r" test),
+                         then the `shortlist` nearest are re-ranked with
+                         exact FP32 distances before the top-k            */
+  int32_t reserved;
 } detlsh_query_params;
 
 /*

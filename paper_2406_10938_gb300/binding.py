@@ -49,7 +49,8 @@ class Params(ctypes.Structure):
 
 class QueryParams(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("beta", ctypes.c_double),
-                ("cand_ids", ctypes.c_void_p), ("cand_cap", ctypes.c_int64)]
+                ("cand_ids", ctypes.c_void_p), ("cand_cap", ctypes.c_int64),
+                ("shortlist", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -177,7 +178,7 @@ def detlsh_build(X: torch.Tensor, A: torch.Tensor, sample_ids: torch.Tensor, K: 
 
 def detlsh_query(index: Index, Q: torch.Tensor, k, c, r_min=None, k_max: Optional[int] = None,
                  eps: float = 0.0, beta: float = 0.1, cand_cap: int = 0,
-                 out=None):
+                 out=None, shortlist: int = 0):
     """Returns (ids int64 [nq,k_max], dist fp32 [nq,k_max], stats int32 [nq,4], cand or None).
 
     ``k``, ``c``, ``r_min`` are per-query tensors (or scalars, broadcast).
@@ -202,7 +203,7 @@ def detlsh_query(index: Index, Q: torch.Tensor, k, c, r_min=None, k_max: Optiona
         ids, dist, stats = out
     cand = torch.empty(nq, cand_cap, dtype=torch.int32, device=dev) if cand_cap > 0 else None
     qp = QueryParams(eps=eps, beta=beta, cand_ids=cand.data_ptr() if cand is not None else None,
-                     cand_cap=cand_cap)
+                     cand_cap=cand_cap, shortlist=shortlist, reserved=0)
     st = lib().detlsh_query(index.handle, _ptr(Q), nq, _dtype_code(Q), _ptr(k), _ptr(c), _ptr(r_min),
                             k_max, ctypes.byref(qp), _ptr(ids), _ptr(dist), _ptr(stats), mem, _stream(mem))
     _check(st, "detlsh_query")

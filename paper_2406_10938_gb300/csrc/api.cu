@@ -353,6 +353,8 @@ int detlsh_query(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dty
   DL_REQUIRE(std::isfinite(eps) && eps > 0.0, "eps must be finite and > 0");
   uint32_t* cand = qp ? qp->cand_ids : nullptr;
   const int64_t cand_cap = qp ? qp->cand_cap : 0;
+  const int32_t shortlist = qp ? qp->shortlist : 0;
+  DL_REQUIRE(shortlist >= 0, "shortlist must be >= 0");
   DL_REQUIRE(cand == nullptr || cand_cap >= 1, "cand_cap must be >= 1 with cand_ids");
   if (mem == DETLSH_MEM_HOST) {
     for (int64_t i = 0; i < nq; ++i) {
@@ -390,7 +392,7 @@ int detlsh_query(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dty
   DL_TRY(run_query(idx, dQ.d, nq, static_cast<const int32_t*>(dk.d), static_cast<const float*>(dc.d),
                    static_cast<const float*>(dr.d), k_max, eps, beta, static_cast<int64_t*>(oi.d),
                    static_cast<float*>(od.d), static_cast<int32_t*>(os.d), static_cast<uint32_t*>(oc.d),
-                   cand_cap, s));
+                   cand_cap, shortlist, s));
   DL_TRY(oi.finish(s));
   DL_TRY(od.finish(s));
   DL_TRY(os.finish(s));

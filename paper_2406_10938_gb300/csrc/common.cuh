@@ -186,7 +186,7 @@ int build_leaves(detlsh_index* idx, cudaStream_t s);
 int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t* k,
               const float* c, const float* r_min, int k_max, double eps, double beta,
               int64_t* out_ids, float* out_dist, int32_t* out_stats, uint32_t* cand_ids,
-              int64_t cand_cap, cudaStream_t s);
+              int64_t cand_cap, int shortlist, cudaStream_t s);
 
 // ---- host math (chi2.cpp)
 double chi2_upper_quantile(double alpha, int K);

@@ -28,6 +28,8 @@
 // The result equals the sequential walk: the rule that needs distances can
 // only end the walk at a round boundary, and S at a round boundary is a
 // prefix of the list.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cfloat>
 
@@ -819,17 +821,78 @@ k_dist(const TX* __restrict__ X, int d, const TX* __restrict__ Q, int64_t q0,
   }
 }
 
+// Coarse squared distances from the BF16 copy of X (FP32 accumulation):
+// half the bytes of the FP32 rows for the same candidates.
+__device__ __forceinline__ void rows_dist2_bf16(const __nv_bfloat16* __restrict__ Xb, int d,
+                                                const uint32_t* ids, const float* __restrict__ q,
+                                                int lane, float* acc) {
+  const int d4 = d >> 2;
+  for (int i = lane; i < d4; i += 32) {
+    const float4 qf = __ldg(reinterpret_cast<const float4*>(q) + i);
+    uint2 xv[ILP];
+#pragma unroll
+    for (int u = 0; u < ILP; ++u)
+      xv[u] = (ids[u] != 0xffffffffu)
+                  ? __ldg(reinterpret_cast<const uint2*>(Xb + (int64_t)ids[u] * d) + i)
+                  : make_uint2(0u, 0u);
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) {
+      if (ids[u] == 0xffffffffu) continue;
+      const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&xv[u].x));
+      const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&xv[u].y));
+      const float d0 = lo.x - qf.x, d1 = lo.y - qf.y, d2 = hi.x - qf.z, d3 = hi.y - qf.w;
+      acc[u] = fmaf(d0, d0, acc[u]);
+      acc[u] = fmaf(d1, d1, acc[u]);
+      acc[u] = fmaf(d2, d2, acc[u]);
+      acc[u] = fmaf(d3, d3, acc[u]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(DT, 3)
+k_dist_bf16(const __nv_bfloat16* __restrict__ Xb, int d, const float* __restrict__ Qf, int64_t q0,
+            const uint32_t* __restrict__ cand, int64_t cap, const uint32_t* __restrict__ meta,
+            float* __restrict__ d2out) {
+  const int64_t qb = blockIdx.y;
+  const uint32_t nS = meta[qb * MQ_WORDS + MQ_NS];
+  const int64_t r0 = (int64_t)blockIdx.x * DROWS;
+  if (r0 >= nS) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const float* q = Qf + (q0 + qb) * (int64_t)d;
+  const uint32_t* cl = cand + qb * cap;
+  float* out = d2out + qb * cap;
+  const int64_t r1 = min(r0 + (int64_t)DROWS, (int64_t)nS);
+  for (int64_t e0 = r0 + (int64_t)w * ILP; e0 < r1; e0 += DNW * ILP) {
+    uint32_t ids[ILP];
+    float acc[ILP];
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) {
+      ids[u] = (e0 + u < r1) ? __ldg(cl + e0 + u) : 0xffffffffu;
+      acc[u] = 0.f;
+    }
+    rows_dist2_bf16(Xb, d, ids, q, lane, acc);
+    const float v = transpose_reduce8(acc, lane);
+    const int r = (lane >> 2) & 7;
+    if ((lane & 3) == 0 && e0 + r < r1) out[e0 + r] = v;
+  }
+}
+
+__global__ void k_widen_f32(const void* __restrict__ Q, int dtype, int64_t count, float* __restrict__ Qf) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    Qf[i] = dtype == DETLSH_U8 ? (float)static_cast<const uint8_t*>(Q)[i] : static_cast<const float*>(Q)[i];
+}
+
 // ------------------------------------------------------------------ finalize
 constexpr int FT = 256;
-constexpr int TK_CAP = 4096;       // top-k buffer entries
-constexpr int TK_CHUNK = TK_CAP - kMaxTopK;
+constexpr int TKC_MAX = 8192;      // top-k / shortlist buffer entries (dynamic shared memory)
 
-// Bitonic sort of TK_CAP keys ascending (block-wide).
-__device__ void sort_topk(unsigned long long* tk) {
-  for (int size = 2; size <= TK_CAP; size <<= 1) {
+// Bitonic sort of tk[0..m) ascending, m a power of two (block-wide).
+__device__ void sort_keys(unsigned long long* tk, int m) {
+  for (int size = 2; size <= m; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       __syncthreads();
-      for (int i = threadIdx.x; i < TK_CAP / 2; i += FT) {
+      for (int i = threadIdx.x; i < m / 2; i += FT) {
         const int lo = 2 * i - (i & (stride - 1));
         const int hi = lo + stride;
         const bool up = ((lo & size) == 0);
@@ -842,6 +905,98 @@ __device__ void sort_topk(unsigned long long* tk) {
     }
   }
   __syncthreads();
+}
+
+__device__ __forceinline__ int pow2_at_least(int v) {
+  int m = 2;
+  while (m < v) m <<= 1;
+  return m;
+}
+
+// Keep the `keep` smallest of the cnt distinct keys tk[0..cnt) (moved, in any
+// order, to the front) and return the largest kept key: a radix select of the
+// keep-th key over 8-bit digits, then an in-place compaction in which every
+// thread first holds its TKC/FT strided keys in registers.
+template <int TKC>
+__device__ unsigned long long prune_keys(unsigned long long* tk, int cnt, int keep, uint32_t* hist,
+                                         unsigned long long* s_pref, int* s_need, uint32_t* s_warp) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  unsigned long long prefix = 0, pmask = 0;
+  int need = keep;   // rank (1-based) of the wanted key among the keys matching the prefix
+  for (int p = 7; p >= 0; --p) {
+    for (int i = threadIdx.x; i < 256; i += FT) hist[i] = 0;
+    __syncthreads();
+    const int it = (cnt + FT - 1) / FT * FT;
+    for (int i = threadIdx.x; i < it; i += FT) {
+      uint32_t dg = 0xffffffffu;
+      if (i < cnt) {
+        const unsigned long long k = tk[i];
+        if ((k & pmask) == prefix) dg = (uint32_t)((k >> (8 * p)) & 255ull);
+      }
+      const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+      if (dg != 0xffffffffu && (peers & lt) == 0) atomicAdd(&hist[dg], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    if (w == 0) {
+      // first digit whose cumulative count reaches `need` (8 bins per lane, warp scan)
+      uint32_t v[8], run = 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        v[e] = hist[lane * 8 + e];
+        run += v[e];
+      }
+      uint32_t incl = run;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t bal = __ballot_sync(0xffffffffu, incl >= (uint32_t)need);
+      const int first = bal ? __ffs(bal) - 1 : 31;
+      if (lane == first) {
+        int acc = (int)(incl - run), dg = lane * 8;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          if (acc + (int)v[e] >= need) break;
+          acc += (int)v[e];
+          ++dg;
+        }
+        *s_pref = prefix | ((unsigned long long)min(dg, 255) << (8 * p));
+        *s_need = need - acc;
+      }
+    }
+    __syncthreads();
+    prefix = *s_pref;
+    need = *s_need;
+    pmask |= 255ull << (8 * p);
+  }
+  const unsigned long long kth = prefix;
+  constexpr int PER = TKC / FT;
+  unsigned long long v[PER];
+  uint32_t mask = 0;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int i = threadIdx.x + j * FT;
+    v[j] = i < cnt ? tk[i] : ~0ull;
+    if (i < cnt && v[j] <= kth) mask |= 1u << j;
+  }
+  const uint32_t mine = __popc(mask);
+  uint32_t x = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();   // also: every key has been read before any is moved
+  uint32_t base = x - mine;
+  for (int q = 0; q < w; ++q) base += s_warp[q];
+#pragma unroll
+  for (int j = 0; j < PER; ++j)
+    if ((mask >> j) & 1u) tk[base + __popc(mask & ((1u << j) - 1u))] = v[j];
+  __syncthreads();
+  return kth;
 }
 
 struct FinalArgs {
@@ -859,24 +1014,37 @@ struct FinalArgs {
   int32_t* out_stats;
   uint32_t* cand_ids;
   int64_t cand_cap;
+  // shortlist re-rank (coarse distances): keep `shortlist` candidates and
+  // recompute their distances exactly from X before the top-k
+  int shortlist;
+  const void* X;
+  const void* Q;
+  int d;
+  bool vec4;
 };
 
+template <typename TX, int TKC>
 __global__ void __launch_bounds__(FT) k_finalize(FinalArgs a) {
-  __shared__ unsigned long long tk[TK_CAP];
+  extern __shared__ __align__(16) unsigned long long tk[];   // [TKC]
   __shared__ uint32_t s_rend[kRoundCap];
   __shared__ float s_thr[kRoundCap];
   __shared__ uint32_t s_hist[kRoundCap + 1];
   __shared__ unsigned long long s_tkn, s_tau;
   __shared__ uint32_t s_nsf, s_stop, s_rounds;
+  __shared__ uint32_t s_sel[256], s_warp[FT / 32];
+  __shared__ unsigned long long s_pref;
+  __shared__ int s_need;
   const int64_t qb = blockIdx.x;
   const int64_t qg = a.q0 + qb;
   const uint32_t* m = a.meta + qb * MQ_WORDS;
   const uint32_t nS = m[MQ_NS], t_end = m[MQ_TEND], stopT = m[MQ_STOP];
   const int Ru = (int)m[MQ_RU];
   const int kq = a.k[qg];
+  const int keep = a.shortlist > 0 ? max(a.shortlist, kq) : kq;   // entries the buffer keeps
+  const int chunk = TKC - keep;
   const uint32_t* cl = a.cand + qb * a.cap;
   const float* dl = a.d2 + qb * a.cap;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   const int nr = (int)t_end + 1;
   for (int i = threadIdx.x; i < kRoundCap; i += FT) {
@@ -887,17 +1055,27 @@ __global__ void __launch_bounds__(FT) k_finalize(FinalArgs a) {
   __syncthreads();
   // a candidate inserted in round r counts as within c*r_t for every t >= max(r, u),
   // u = first round whose exact threshold (c*r_u)^2 covers its distance
-  const uint32_t iters = (nS + FT - 1) / FT * FT;
-  for (uint32_t p = threadIdx.x; p < iters; p += FT) {
-    uint32_t key = 0xffffffffu;
-    if (p < nS) {
-      const int r = upper_bound_u(s_rend, nr, p);
-      const int u = lower_bound_f(s_thr, Ru, dl[p]);
-      const int x = max(r, u);
-      if (x < nr) key = (uint32_t)x;
+  constexpr int FU = 4;   // candidates per thread in flight
+  const uint32_t iters = (nS + FT * FU - 1) / (FT * FU) * (FT * FU);
+  for (uint32_t p0 = threadIdx.x; p0 < iters; p0 += FT * FU) {
+    float dv[FU];
+#pragma unroll
+    for (int u = 0; u < FU; ++u) {
+      const uint32_t p = p0 + u * FT;
+      dv[u] = p < nS ? dl[p] : 0.f;
     }
-    const uint32_t peers = __match_any_sync(0xffffffffu, key);
-    if (key != 0xffffffffu && (peers & lt) == 0) atomicAdd(&s_hist[key], (uint32_t)__popc(peers));
+#pragma unroll
+    for (int u = 0; u < FU; ++u) {
+      const uint32_t p = p0 + u * FT;
+      uint32_t key = 0xffffffffu;
+      if (p < nS) {
+        const int r = upper_bound_u(s_rend, nr, p);
+        const int x = max(r, lower_bound_f(s_thr, Ru, dv[u]));
+        if (x < nr) key = (uint32_t)x;
+      }
+      const uint32_t peers = __match_any_sync(0xffffffffu, key);
+      if (key != 0xffffffffu && (peers & lt) == 0) atomicAdd(&s_hist[key], (uint32_t)__popc(peers));
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -923,46 +1101,82 @@ __global__ void __launch_bounds__(FT) k_finalize(FinalArgs a) {
   }
   __syncthreads();
   const uint32_t nsf = s_nsf;
-  // k nearest of the first nsf candidates by (distance, id)
-  for (uint32_t c0 = 0; c0 < nsf; c0 += TK_CHUNK) {
-    if (s_tkn + TK_CHUNK > TK_CAP) {
-      const int cnt = (int)min(s_tkn, (unsigned long long)TK_CAP);
-      for (int i = cnt + threadIdx.x; i < TK_CAP; i += FT) tk[i] = ~0ull;
-      sort_topk(tk);
-      if (threadIdx.x == 0) {
-        const int keep = min(cnt, kq);
-        s_tkn = keep;
-        if (keep == kq) s_tau = tk[kq - 1];
+  // the `keep` smallest of the first nsf candidates by (distance, id)
+  for (uint32_t c0 = 0; c0 < nsf; c0 += chunk) {
+    if (s_tkn + chunk > TKC) {
+      const int cnt = (int)min(s_tkn, (unsigned long long)TKC);
+      __syncthreads();
+      if (cnt > keep) {
+        const unsigned long long kth = prune_keys<TKC>(tk, cnt, keep, s_sel, &s_pref, &s_need, s_warp);
+        if (threadIdx.x == 0) {
+          s_tkn = keep;
+          s_tau = kth;
+        }
       }
       __syncthreads();
     }
     const unsigned long long tau = s_tau;
-    const uint32_t c1 = min(nsf, c0 + (uint32_t)TK_CHUNK);
-    for (uint32_t p = c0 + threadIdx.x; p < c1; p += FT) {
-      const unsigned long long key = ((unsigned long long)__float_as_uint(dl[p]) << 32) | cl[p];
-      if (key < tau) {
-        const unsigned long long slot = atomicAdd(&s_tkn, 1ull);
-        if (slot < TK_CAP) tk[slot] = key;
+    const uint32_t c1 = min(nsf, c0 + (uint32_t)chunk);
+    for (uint32_t p0 = c0 + threadIdx.x; p0 < c1; p0 += FT * FU) {
+      unsigned long long kv[FU];
+#pragma unroll
+      for (int u = 0; u < FU; ++u) {
+        const uint32_t p = p0 + u * FT;
+        kv[u] = p < c1 ? (((unsigned long long)__float_as_uint(dl[p]) << 32) | cl[p]) : ~0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < FU; ++u) {
+        if (kv[u] < tau) {
+          const unsigned long long slot = atomicAdd(&s_tkn, 1ull);
+          if (slot < TKC) tk[slot] = kv[u];
+        }
       }
     }
     __syncthreads();
   }
+  int have;
   {
-    const int cnt = (int)min(s_tkn, (unsigned long long)TK_CAP);
-    for (int i = cnt + threadIdx.x; i < TK_CAP; i += FT) tk[i] = ~0ull;
-    sort_topk(tk);
-    const int have = min(cnt, kq);
-    for (int r = threadIdx.x; r < a.k_max; r += FT) {
-      int64_t id = -1;
-      float dist = INFINITY;
-      if (r < have) {
-        const unsigned long long key = tk[r];
-        id = (int64_t)(key & 0xffffffffull);
-        dist = sqrtf(__uint_as_float((uint32_t)(key >> 32)));
+    const int cnt = (int)min(s_tkn, (unsigned long long)TKC);
+    const int m = pow2_at_least(cnt);
+    for (int i = cnt + threadIdx.x; i < m; i += FT) tk[i] = ~0ull;
+    sort_keys(tk, m);
+    have = min(cnt, keep);
+  }
+  if (a.shortlist > 0) {
+    // exact FP32 distances of the shortlist, 8 rows per warp, then re-sort
+    const TX* X = static_cast<const TX*>(a.X);
+    const TX* q = static_cast<const TX*>(a.Q) + qg * (int64_t)a.d;
+    for (int e0 = w * ILP; e0 < have; e0 += (FT / 32) * ILP) {
+      uint32_t ids[ILP];
+      float acc[ILP];
+#pragma unroll
+      for (int u = 0; u < ILP; ++u) {
+        ids[u] = (e0 + u < have) ? (uint32_t)(tk[e0 + u] & 0xffffffffull) : 0xffffffffu;
+        acc[u] = 0.f;
       }
-      a.out_ids[qg * a.k_max + r] = id;
-      a.out_dist[qg * a.k_max + r] = dist;
+      rows_dist2<TX>(X, a.d, ids, q, a.vec4, lane, acc);
+      const float v = transpose_reduce8(acc, lane);
+      const int r = (lane >> 2) & 7;
+      __syncwarp();
+      if ((lane & 3) == 0 && e0 + r < have)
+        tk[e0 + r] = ((unsigned long long)__float_as_uint(v) << 32) | (tk[e0 + r] & 0xffffffffull);
     }
+    __syncthreads();
+    const int m = pow2_at_least(have);
+    for (int i = have + threadIdx.x; i < m; i += FT) tk[i] = ~0ull;
+    sort_keys(tk, m);
+    have = min(have, kq);
+  }
+  for (int r = threadIdx.x; r < a.k_max; r += FT) {
+    int64_t id = -1;
+    float dist = INFINITY;
+    if (r < have && r < kq) {
+      const unsigned long long key = tk[r];
+      id = (int64_t)(key & 0xffffffffull);
+      dist = sqrtf(__uint_as_float((uint32_t)(key >> 32)));
+    }
+    a.out_ids[qg * a.k_max + r] = id;
+    a.out_dist[qg * a.k_max + r] = dist;
   }
   if (a.cand_ids) {
     for (uint32_t p = threadIdx.x; p < nsf && (int64_t)p < a.cand_cap; p += FT)
@@ -981,8 +1195,19 @@ __global__ void __launch_bounds__(FT) k_finalize(FinalArgs a) {
 int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t* k, const float* c,
               const float* r_min, int k_max, double eps, double beta, int64_t* out_ids,
               float* out_dist, int32_t* out_stats, uint32_t* cand_ids, int64_t cand_cap,
-              cudaStream_t s) {
+              int shortlist, cudaStream_t s) {
   if (nq == 0) return DETLSH_OK;
+  if (shortlist > 0 && (idx->Xb == nullptr || shortlist > TKC_MAX / 2)) {
+    set_error("a shortlist needs an index built with the BF16 projection and at most %d entries", TKC_MAX / 2);
+    return DETLSH_EINVAL;
+  }
+  // the top-k buffer: 4096 keys for k <= 1024, 8192 to hold a shortlist of up to 4096
+  const int tkc = shortlist > 0 ? 8192 : 4096;
+  const size_t fin_smem = sizeof(unsigned long long) * tkc;
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<uint8_t, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<uint8_t, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
   const int LK = idx->K * idx->L, L = idx->L;
   const int64_t TL = idx->total_leaves;
   int dev = 0, nsm = 0, smem_optin = 0;
@@ -1007,6 +1232,15 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
                             s));
   }
   tm.end();
+
+  // FP32 queries for the coarse distances
+  Scratch qf;
+  if (shortlist > 0) {
+    DL_TRY(qf.alloc(sizeof(float) * nq * idx->d, s));
+    k_widen_f32<<<(unsigned)std::min<int64_t>(ceil_div(nq * idx->d, 256), 152 * 16), 256, 0, s>>>(
+        Q, idx->dtype, nq * idx->d, qf.as<float>());
+    DL_LAUNCH();
+  }
 
   // walk configuration: the dedup bitmap in shared memory when it fits
   const int64_t words = (idx->n + 31) / 32;
@@ -1115,7 +1349,10 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
 
     dim3 g3(ceil_div(cap, DROWS), (unsigned)nqb);
     tm.begin(TR_DIST);
-    if (idx->dtype == DETLSH_U8)
+    if (shortlist > 0)
+      k_dist_bf16<<<g3, DT, 0, s>>>(static_cast<const __nv_bfloat16*>(idx->Xb), idx->d, qf.as<float>(), q0,
+                                    candb.as<uint32_t>(), cap, meta.as<uint32_t>(), d2b.as<float>());
+    else if (idx->dtype == DETLSH_U8)
       k_dist<uint8_t><<<g3, DT, 0, s>>>(static_cast<const uint8_t*>(idx->X), idx->d,
                                         static_cast<const uint8_t*>(Q), q0, candb.as<uint32_t>(), cap,
                                         meta.as<uint32_t>(), d2b.as<float>(), vec4);
@@ -1143,8 +1380,16 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
     fa.out_stats = out_stats;
     fa.cand_ids = cand_ids;
     fa.cand_cap = cand_cap;
+    fa.shortlist = shortlist;
+    fa.X = idx->X;
+    fa.Q = Q;
+    fa.d = idx->d;
+    fa.vec4 = vec4;
     tm.begin(TR_FINALIZE);
-    k_finalize<<<(unsigned)nqb, FT, 0, s>>>(fa);
+    if (idx->dtype == DETLSH_U8)
+      (tkc == 4096 ? k_finalize<uint8_t, 4096> : k_finalize<uint8_t, 8192>)<<<(unsigned)nqb, FT, fin_smem, s>>>(fa);
+    else
+      (tkc == 4096 ? k_finalize<float, 4096> : k_finalize<float, 8192>)<<<(unsigned)nqb, FT, fin_smem, s>>>(fa);
     DL_LAUNCH();
     tm.end();
   }

@@ -95,3 +95,46 @@ def test_bf16_projection_of_rounded_inputs(name, n, d, n_s):
     tol = proj_tolerance(Ar, Xr[ids.numpy()])
     assert (np.abs(Ps - ref) <= tol).all()
     idx.free()
+
+
+def test_shortlist_exact_inputs_match_the_oracle():
+    """Integer data is exact in BF16, so the coarse distances are the exact
+    ones and the shortlist path must return the oracle's results."""
+    n, d, K, L, Nr, n_s, max_leaf, nq, k = 20_000, 128, 16, 4, 256, 2_000, 64, 20, 50
+    X, Q = make_workload("mid", n=n, nq=nq, exact=True)
+    A = gaussian_projection(L, K, d, exact=True)
+    ids = sample_ids(n, n_s)
+    eps = O.eps_from_lemma3(K, L)
+    idx = pkg.detlsh_build(X.to(DEV), A.to(DEV), ids.to(DEV), K, L, Nr, max_leaf, proj_mode=BF16)
+    oid, od, st, _ = pkg.detlsh_query(idx, Q.to(DEV), k, 1.5, 0.0, k_max=k, eps=eps, beta=0.1, shortlist=512)
+    ref = O.build_index(X.numpy(), A.numpy(), ids.numpy(), K, L, Nr, max_leaf)
+    oid, od, st = oid.cpu().numpy(), od.cpu().numpy(), st.cpu().numpy()
+    for qi in range(nq):
+        r = O.c2k_ann(ref, Q[qi].numpy(), k, 1.5, 0.0, eps, 0.1)
+        assert (st[qi, 0], st[qi, 1], st[qi, 2]) == (r.n_cand, r.rounds, r.stop)
+        assert np.array_equal(oid[qi], r.ids)
+        assert np.array_equal(od[qi], np.float32(r.dist))
+    idx.free()
+
+
+def test_shortlist_float_inputs_recall_and_exact_distances():
+    """FP32 data: the shortlist's distances are recomputed in FP32 (1e-5 of the
+    FP64 value) and recall stays close to the plain FP32 path's."""
+    n, d, K, L, Nr, n_s, nq, k = 8_000, 960, 16, 4, 64, 800, 16, 20
+    X, Q = make_workload("precision", n=n, nq=nq)
+    A = gaussian_projection(L, K, d)
+    ids = sample_ids(n, n_s)
+    idx = pkg.detlsh_build(X.to(DEV), A.to(DEV), ids.to(DEV), K, L, Nr, 256, proj_mode=BF16)
+    o1, d1, _, _ = pkg.detlsh_query(idx, Q.to(DEV), k, 1.5, 0.0, k_max=k, beta=0.1)
+    o2, d2, _, _ = pkg.detlsh_query(idx, Q.to(DEV), k, 1.5, 0.0, k_max=k, beta=0.1, shortlist=1024)
+    Xn, Qn = X.numpy().astype(np.float64), Q.numpy().astype(np.float64)
+    o1, o2, d2 = o1.cpu().numpy(), o2.cpu().numpy(), d2.cpu().numpy()
+    r1, r2 = [], []
+    for qi in range(nq):
+        e, _ = O.exact_knn(Xn, Qn[qi], k)
+        r1.append(O.recall(o1[qi], e))
+        r2.append(O.recall(o2[qi], e))
+        true = np.sqrt(((Xn[o2[qi]] - Qn[qi]) ** 2).sum(axis=1))
+        assert np.allclose(d2[qi], true, rtol=1e-5, atol=1e-6)
+    assert np.mean(r2) >= np.mean(r1) - 0.02, (np.mean(r1), np.mean(r2))
+    idx.free()
