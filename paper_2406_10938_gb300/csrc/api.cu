@@ -1,4 +1,5 @@
 // C ABI of libdetlsh: argument checks, host/device staging and index lifetime.
+#include <mutex>
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -49,6 +50,32 @@ int PhaseTimer::finish() {
     g_trace[phase_[i]] += ms;
   }
   return DETLSH_OK;
+}
+
+cudaMemPool_t scratch_pool() {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static cudaMemPool_t pools[kMaxDev] = {};
+  static bool tried[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!tried[dev]) {
+    tried[dev] = true;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+      uint64_t keep = (uint64_t)16 << 30;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      pools[dev] = pool;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  return pools[dev];
 }
 
 void set_error(const char* fmt, ...) {

@@ -83,6 +83,11 @@ class PhaseTimer {
   } while (0)
 
 // Stream-ordered scratch allocation that frees itself on scope exit.
+// The library's stream-ordered pool on the current device (created on first
+// use; it keeps up to 16 GiB of freed scratch mapped between calls), or null
+// when a pool cannot be created (then the device's default pool serves).
+cudaMemPool_t scratch_pool();
+
 struct Scratch {
   void* p = nullptr;
   cudaStream_t s = nullptr;
@@ -95,7 +100,8 @@ struct Scratch {
   int alloc(size_t bytes, cudaStream_t stream) {
     s = stream;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    cudaMemPool_t pool = scratch_pool();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, stream) : cudaMallocAsync(&p, bytes, stream);
     if (e != cudaSuccess) {
       p = nullptr;
       set_error("cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));

@@ -343,6 +343,7 @@ struct WalkArgs {
   uint32_t* ws_bitmap;        // [grid][bitmap_words] when not in shared memory
   int64_t bitmap_words;
   int smem_bitmap;
+  uint32_t* work;             // query counter, zero at launch
 };
 
 struct WalkLayout {
@@ -480,11 +481,14 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
         }
       }
       if (count_only) {
+        uint32_t word[WILP];
+#pragma unroll
+        for (int u = 0; u < WILP; ++u) word[u] = ids[u] != 0xffffffffu ? bitmap[ids[u] >> 5] : 0xffffffffu;
 #pragma unroll
         for (int u = 0; u < WILP; ++u) {
           const uint32_t f = f0 + u * WT + threadIdx.x;
           const uint32_t id = ids[u];
-          const bool fresh = id != 0xffffffffu && !((bitmap[id >> 5] >> (id & 31)) & 1u);
+          const bool fresh = id != 0xffffffffu && !((word[u] >> (id & 31)) & 1u);
           const uint32_t key = fresh ? (uint32_t)fmap[f] : 0xffffffffu;
           const uint32_t peers = __match_any_sync(0xffffffffu, key);
           if (fresh && (peers & lt) == 0) atomicAdd(&s_newc[key], (uint32_t)__popc(peers));
@@ -493,24 +497,29 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
         }
         continue;
       }
+      // all test-and-sets of the step are in flight before any result is used
+      uint32_t old[WILP];
+#pragma unroll
+      for (int u = 0; u < WILP; ++u)
+        old[u] = ids[u] != 0xffffffffu ? atomicOr(bitmap + (ids[u] >> 5), 1u << (ids[u] & 31)) : 0xffffffffu;
+      uint32_t fm[WILP], tot = 0;
 #pragma unroll
       for (int u = 0; u < WILP; ++u) {
-        bool fresh = false;
-        const uint32_t id = ids[u];
-        if (id != 0xffffffffu) {
-          const uint32_t bit = 1u << (id & 31);
-          const uint32_t old = atomicOr(bitmap + (id >> 5), bit);
-          fresh = !(old & bit);
-        }
-        const uint32_t m = __ballot_sync(0xffffffffu, fresh);
-        uint32_t base = 0;
-        if (lane == 0 && m) base = (uint32_t)atomicAdd(&misc[W_QN], (unsigned long long)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (fresh) {
-          const unsigned long long pos = S0 + base + __popc(m & lt);
-          if ((int64_t)pos < a.cap) cand[pos] = id;
+        const bool fresh = ids[u] != 0xffffffffu && !((old[u] >> (ids[u] & 31)) & 1u);
+        fm[u] = __ballot_sync(0xffffffffu, fresh);
+        tot += __popc(fm[u]);
+      }
+      uint32_t base = 0;   // one reservation per warp for the step's new points
+      if (lane == 0 && tot) base = (uint32_t)atomicAdd(&misc[W_QN], (unsigned long long)tot);
+      base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+      for (int u = 0; u < WILP; ++u) {
+        if ((fm[u] >> lane) & 1u) {
+          const unsigned long long pos = S0 + base + __popc(fm[u] & lt);
+          if ((int64_t)pos < a.cap) cand[pos] = ids[u];
           else misc[W_OVF] = 1;
         }
+        base += __popc(fm[u]);
       }
     }
     __syncthreads();
@@ -556,7 +565,14 @@ __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
 
-  for (int64_t qb = blockIdx.x; qb < a.nqb; qb += gridDim.x) {
+  __shared__ long long s_qb;
+  while (true) {
+    // queries are taken from a counter in global memory, so a CTA that drew
+    // short queries takes more of them
+    if (threadIdx.x == 0) s_qb = (long long)atomicAdd(a.work, 1u);
+    __syncthreads();
+    const int64_t qb = s_qb;
+    if (qb >= a.nqb) break;
     const float* lbrow = a.lb2 + qb * a.total_leaves;
     const uint32_t* list = a.list + qb * a.total_leaves;
     uint32_t* cand = a.cand + qb * a.cap;
@@ -566,7 +582,8 @@ __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
     const int tcap = (int)m[MQ_TCAP];
     const int tlast = (int)m[MQ_TLAST];
     const int nbk = (tcap + 1) * L;
-    for (int64_t i = threadIdx.x; i < a.bitmap_words; i += WT) bitmap[i] = 0u;
+    if (a.smem_bitmap)
+      for (int64_t i = threadIdx.x; i < a.bitmap_words; i += WT) bitmap[i] = 0u;
     for (int i = threadIdx.x; i <= nbk; i += WT) s_boff[i] = a.boff[qb * (kRoundCap * L + 1) + i];
     for (int i = threadIdx.x; i < nbk; i += WT) s_pts[i] = a.hist_pts[qb * kRoundCap * L + i];
     if (threadIdx.x == 0) {
@@ -691,6 +708,17 @@ __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
       m[MQ_TEND] = (uint32_t)t_end;
       m[MQ_STOP] = misc[W_STOP] ? (uint32_t)misc[W_STOP] : 3u;
       m[MQ_OVERFLOW] = (uint32_t)misc[W_OVF];
+    }
+    __syncthreads();
+    if (!a.smem_bitmap) {
+      // leave the global bitmap zeroed: through the candidate list when it
+      // holds every set bit and is much shorter than the bitmap
+      const unsigned long long S = misc[W_S];
+      if (!misc[W_OVF] && (int64_t)S * 8 < a.bitmap_words) {
+        for (unsigned long long p = threadIdx.x; p < S; p += WT) bitmap[cand[p] >> 5] = 0u;
+      } else {
+        for (int64_t i = threadIdx.x; i < a.bitmap_words; i += WT) bitmap[i] = 0u;
+      }
     }
     __syncthreads();
   }
@@ -821,32 +849,67 @@ k_dist(const TX* __restrict__ X, int d, const TX* __restrict__ Q, int64_t q0,
   }
 }
 
-// Coarse squared distances from the BF16 copy of X (FP32 accumulation):
-// half the bytes of the FP32 rows for the same candidates.
+// Coarse squared distances from the BF16 copy of X (FP32 accumulation): half
+// the bytes of the FP32 rows for the same candidates. Each half-warp reads one
+// row with 16-byte loads (8 values per lane, d % 8 == 0), so a warp keeps
+// 2*ILP rows in flight; hl is the lane within the half-warp.
 __device__ __forceinline__ void rows_dist2_bf16(const __nv_bfloat16* __restrict__ Xb, int d,
                                                 const uint32_t* ids, const float* __restrict__ q,
-                                                int lane, float* acc) {
-  const int d4 = d >> 2;
-  for (int i = lane; i < d4; i += 32) {
-    const float4 qf = __ldg(reinterpret_cast<const float4*>(q) + i);
-    uint2 xv[ILP];
+                                                int hl, float* acc) {
+  const int d8 = d >> 3;
+  for (int i = hl; i < d8; i += 16) {
+    const float4 qa = __ldg(reinterpret_cast<const float4*>(q) + 2 * i);
+    const float4 qb = __ldg(reinterpret_cast<const float4*>(q) + 2 * i + 1);
+    uint4 xv[ILP];
 #pragma unroll
     for (int u = 0; u < ILP; ++u)
       xv[u] = (ids[u] != 0xffffffffu)
-                  ? __ldg(reinterpret_cast<const uint2*>(Xb + (int64_t)ids[u] * d) + i)
-                  : make_uint2(0u, 0u);
+                  ? __ldg(reinterpret_cast<const uint4*>(Xb + (int64_t)ids[u] * d) + i)
+                  : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
       if (ids[u] == 0xffffffffu) continue;
-      const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&xv[u].x));
-      const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&xv[u].y));
-      const float d0 = lo.x - qf.x, d1 = lo.y - qf.y, d2 = hi.x - qf.z, d3 = hi.y - qf.w;
-      acc[u] = fmaf(d0, d0, acc[u]);
-      acc[u] = fmaf(d1, d1, acc[u]);
-      acc[u] = fmaf(d2, d2, acc[u]);
-      acc[u] = fmaf(d3, d3, acc[u]);
+      const float2 x0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&xv[u].x));
+      const float2 x1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&xv[u].y));
+      const float2 x2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&xv[u].z));
+      const float2 x3 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&xv[u].w));
+      const float t0 = x0.x - qa.x, t1 = x0.y - qa.y, t2 = x1.x - qa.z, t3 = x1.y - qa.w;
+      const float t4 = x2.x - qb.x, t5 = x2.y - qb.y, t6 = x3.x - qb.z, t7 = x3.y - qb.w;
+      acc[u] = fmaf(t0, t0, acc[u]);
+      acc[u] = fmaf(t1, t1, acc[u]);
+      acc[u] = fmaf(t2, t2, acc[u]);
+      acc[u] = fmaf(t3, t3, acc[u]);
+      acc[u] = fmaf(t4, t4, acc[u]);
+      acc[u] = fmaf(t5, t5, acc[u]);
+      acc[u] = fmaf(t6, t6, acc[u]);
+      acc[u] = fmaf(t7, t7, acc[u]);
     }
   }
+}
+
+// Sum 8 per-lane partials over each half-warp so that lane l ends with the
+// total of partial (l >> 1) & 7 of its half: three halving exchanges (8, 4, 2)
+// each keep half of the partials, then one butterfly step.
+__device__ __forceinline__ float transpose_reduce8_half(const float* acc, int lane) {
+  float a4[4], a2[2];
+  const bool b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = b3 ? acc[i] : acc[i + 4];
+    const float keep = b3 ? acc[i + 4] : acc[i];
+    a4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = b2 ? a4[i] : a4[i + 2];
+    const float keep = b2 ? a4[i + 2] : a4[i];
+    a2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  const float send = b1 ? a2[0] : a2[1];
+  const float keep = b1 ? a2[1] : a2[0];
+  float v = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
 }
 
 __global__ void __launch_bounds__(DT, 3)
@@ -857,23 +920,25 @@ k_dist_bf16(const __nv_bfloat16* __restrict__ Xb, int d, const float* __restrict
   const uint32_t nS = meta[qb * MQ_WORDS + MQ_NS];
   const int64_t r0 = (int64_t)blockIdx.x * DROWS;
   if (r0 >= nS) return;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, h = lane >> 4;
   const float* q = Qf + (q0 + qb) * (int64_t)d;
   const uint32_t* cl = cand + qb * cap;
   float* out = d2out + qb * cap;
   const int64_t r1 = min(r0 + (int64_t)DROWS, (int64_t)nS);
-  for (int64_t e0 = r0 + (int64_t)w * ILP; e0 < r1; e0 += DNW * ILP) {
+  // warp step: 2*ILP rows, rows e0 + h*ILP + u of half-warp h
+  for (int64_t e0 = r0 + (int64_t)w * 2 * ILP; e0 < r1; e0 += DNW * 2 * ILP) {
     uint32_t ids[ILP];
     float acc[ILP];
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
-      ids[u] = (e0 + u < r1) ? __ldg(cl + e0 + u) : 0xffffffffu;
+      const int64_t e = e0 + h * ILP + u;
+      ids[u] = (e < r1) ? __ldg(cl + e) : 0xffffffffu;
       acc[u] = 0.f;
     }
-    rows_dist2_bf16(Xb, d, ids, q, lane, acc);
-    const float v = transpose_reduce8(acc, lane);
-    const int r = (lane >> 2) & 7;
-    if ((lane & 3) == 0 && e0 + r < r1) out[e0 + r] = v;
+    rows_dist2_bf16(Xb, d, ids, q, lane & 15, acc);
+    const float v = transpose_reduce8_half(acc, lane);
+    const int64_t e = e0 + (lane >> 1);   // = e0 + h*ILP + ((lane >> 1) & 7)
+    if ((lane & 1) == 0 && e < r1) out[e] = v;
   }
 }
 
@@ -1201,8 +1266,9 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
     set_error("a shortlist needs an index built with the BF16 projection and at most %d entries", TKC_MAX / 2);
     return DETLSH_EINVAL;
   }
-  // the top-k buffer: 4096 keys for k <= 1024, 8192 to hold a shortlist of up to 4096
-  const int tkc = shortlist > 0 ? 8192 : 4096;
+  // the top-k buffer: 4096 keys while it keeps at most 1024 (k, or a shortlist
+  // of up to 1024), else 8192 for a shortlist of up to 4096
+  const int tkc = shortlist > 1024 ? 8192 : 4096;
   const size_t fin_smem = sizeof(unsigned long long) * tkc;
   DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
   DL_CUDA(cudaFuncSetAttribute(k_finalize<uint8_t, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
@@ -1262,13 +1328,18 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
   const double tmax = std::ceil(beta * (double)idx->n + (double)k_max);
   const int64_t cap = std::max<int64_t>(
       1, std::min<int64_t>(idx->n, (int64_t)std::min(tmax, 9.0e18) - 1 + idx->max_leaf_count));
-  // batch size bounded by the per-query buffers (<= ~3 GiB)
+  // batch size bounded by the per-query buffers: at most 12 GiB and a quarter
+  // of the free device memory (fewer, larger batches shorten the tails of the
+  // per-query kernels)
   const int64_t RL = (int64_t)kRoundCap * L;
   const int64_t per_q = TL * 9 + cap * 8 + RL * 16 + kRoundCap * 12 + MQ_WORDS * 4 + 64;
-  int64_t qb = std::max<int64_t>(1, std::min<int64_t>(nq, ((int64_t)3 << 30) / per_q));
-  qb = std::min<int64_t>(qb, 8192);
+  size_t mem_free = 0, mem_total = 0;
+  DL_CUDA(cudaMemGetInfo(&mem_free, &mem_total));
+  const int64_t budget = std::min<int64_t>((int64_t)12 << 30, (int64_t)(mem_free / 4));
+  int64_t qb = std::max<int64_t>(1, std::min<int64_t>(nq, budget / per_q));
+  qb = std::min<int64_t>(qb, 16384);
   const int wgrid = (int)std::min<int64_t>(qb, (int64_t)nsm * walk_per_sm);
-  Scratch lb, mm, lround, hist, boff, list, candb, d2b, rend, thr, meta, ws_new, ws_bm;
+  Scratch lb, mm, lround, hist, boff, list, candb, d2b, rend, thr, meta, ws_new, ws_bm, work;
   DL_TRY(lb.alloc(sizeof(float) * qb * TL, s));
   DL_TRY(mm.alloc(sizeof(uint32_t) * 2 * qb, s));
   DL_TRY(lround.alloc((size_t)qb * TL, s));
@@ -1284,7 +1355,12 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
   for (int t = 0; t < L; ++t)
     max_tree_leaves = std::max<int64_t>(max_tree_leaves, idx->leaf_base_h[t + 1] - idx->leaf_base_h[t]);
   DL_TRY(ws_new.alloc(sizeof(uint32_t) * 2 * wgrid * max_tree_leaves, s));
-  if (!smem_bitmap) DL_TRY(ws_bm.alloc(sizeof(uint32_t) * wgrid * words, s));
+  if (!smem_bitmap) {
+    // the walk leaves each CTA's bitmap zeroed after every query
+    DL_TRY(ws_bm.alloc(sizeof(uint32_t) * wgrid * words, s));
+    DL_CUDA(cudaMemsetAsync(ws_bm.p, 0, sizeof(uint32_t) * wgrid * words, s));
+  }
+  DL_TRY(work.alloc(sizeof(uint32_t), s));
   uint32_t* d_min = mm.as<uint32_t>();
   uint32_t* d_max = d_min + qb;
   uint32_t* h_pts = hist.as<uint32_t>();
@@ -1342,6 +1418,8 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
     wa.ws_bitmap = smem_bitmap ? nullptr : ws_bm.as<uint32_t>();
     wa.bitmap_words = words;
     wa.smem_bitmap = smem_bitmap ? 1 : 0;
+    wa.work = work.as<uint32_t>();
+    DL_CUDA(cudaMemsetAsync(work.p, 0, sizeof(uint32_t), s));
     tm.begin(TR_WALK);
     k_walk<<<(unsigned)std::min<int64_t>(nqb, wgrid), WT, wl.total, s>>>(wa);
     DL_LAUNCH();
