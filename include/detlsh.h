@@ -71,6 +71,22 @@ typedef struct {
   int32_t flags;      /* DETLSH_BORROW_X or 0                              */
 } detlsh_params;
 
+/* Launch shapes of the query pipeline (no counterpart in the paper). The
+ * results do not depend on them; detlsh_autotune picks them by timing. Zero
+ * fields take the defaults. */
+typedef struct {
+  int64_t batch;             /* queries per batch (0: sized from free device memory,
+                                at most 16384)                                   */
+  int32_t walk_ctas_per_sm;  /* bucket-walk CTAs per SM, 1..3 (0: as many as fit)  */
+  int32_t dist_rows;         /* candidate rows per distance work item, a multiple
+                                of 64 in [64, 8192] (0: 1024)                     */
+  int32_t dist_ctas_per_sm;  /* persistent distance CTAs per SM, 1..3 (0: 3)       */
+  int32_t shortlist;         /* detlsh_autotune's pick for
+                                detlsh_query_params.shortlist; the query ignores
+                                this field                                        */
+  int32_t reserved[2];
+} detlsh_tuning;
+
 /* Query parameters shared by a batch (Alg. 7 inputs besides q, k, c, r_min). */
 typedef struct {
   double eps;         /* projected-radius factor of Lemma 3 (Eq. 2); <= 0 selects
@@ -88,6 +104,7 @@ typedef struct {
                          then the `shortlist` nearest are re-ranked with
                          exact FP32 distances before the top-k            */
   int32_t reserved;
+  const detlsh_tuning* tuning;  /* launch shapes; NULL: defaults             */
 } detlsh_query_params;
 
 /*
@@ -223,6 +240,64 @@ int detlsh_select_breakpoints(const float* Ps, int64_t n_s, int32_t LK, int32_t 
 #define DETLSH_NOALLOC_MAX_ITEMS 262144
 int detlsh_select_breakpoints_noalloc(const float* Ps, int64_t n_s, int32_t LK, int32_t n_regions,
                                       float* E, void* stream);
+
+/*
+ * Query plans (no counterpart in the paper: a serving form of detlsh_query).
+ *
+ * detlsh_plan_create -- allocates, once, the scratch of a batch of up to
+ *   nq_max queries (or tuning->batch if smaller) with input and output staging,
+ *   for results of k_max entries per query under qp (cand_ids must be NULL).
+ *   flags: DETLSH_PLAN_GRAPH captures the batch's kernels in a CUDA graph (on a
+ *   private stream) that every later batch replays with one launch; every
+ *   kernel reads the batch size from device memory, so the graph serves any
+ *   batch size up to the capacity. Synchronizes `stream`. The plan keeps a
+ *   reference to idx, which must outlive it.
+ * detlsh_plan_query -- the same results as detlsh_query for nq queries, run in
+ *   chunks of the plan's capacity: each chunk's inputs are copied into the
+ *   staging buffers, its size written to device memory, the batch run (graph
+ *   launch or direct launches) and its outputs copied to out_*, all on
+ *   `stream`, in the `mem` space of the arguments. No device allocation. With
+ *   DETLSH_MEM_HOST the arguments are checked on the host and the call
+ *   synchronizes and returns detlsh_plan_status. With DETLSH_MEM_DEVICE it
+ *   returns after enqueueing: per-query arguments are checked on the device,
+ *   a chunk with a bad one runs as an empty batch (its out_* rows are then
+ *   unspecified) and detlsh_plan_status reports it. Calls on one plan must be
+ *   serialized on one stream (they share the staging buffers).
+ * detlsh_plan_status -- synchronizes `stream`; DETLSH_EINVAL if a chunk since
+ *   the last status call had a bad per-query argument, DETLSH_ETIMEOUT if a
+ *   bounded wait of the tensor-core projection ran out, else DETLSH_OK.
+ * detlsh_plan_info -- out[0] batch capacity, [1] scratch bytes, [2] graph
+ *   launches so far, [3] batches so far, [4] kernels in the captured graph.
+ * detlsh_plan_destroy -- synchronizes the device and frees the plan.
+ */
+#define DETLSH_PLAN_GRAPH 1
+typedef struct detlsh_plan detlsh_plan;
+int detlsh_plan_create(const detlsh_index* idx, int64_t nq_max, int32_t k_max,
+                       const detlsh_query_params* qp, int32_t flags, void* stream,
+                       detlsh_plan** out);
+int detlsh_plan_query(detlsh_plan* plan, const void* Q, int64_t nq, const int32_t* k,
+                      const float* c, const float* r_min, int64_t* out_ids, float* out_dist,
+                      int32_t* out_stats, int32_t mem, void* stream);
+int detlsh_plan_status(detlsh_plan* plan, void* stream);
+int detlsh_plan_info(const detlsh_plan* plan, int64_t* out5);
+void detlsh_plan_destroy(detlsh_plan* plan);
+
+/*
+ * detlsh_autotune -- times the query pipeline on a sample of queries (the
+ * arguments as for detlsh_query; qp->tuning, if set, is the starting point)
+ * and writes the fastest launch shapes to *out: walk CTAs per SM, distance
+ * rows per work item and distance CTAs per SM by coordinate descent, and the
+ * batch size among the sizes that fit. For an index built with
+ * DETLSH_PROJ_BF16 and min_agreement in (0, 1], out->shortlist is the
+ * smallest shortlist in {64, 128, ..., 4096} (at least k_max) whose top-k
+ * holds, averaged over the sample, at least min_agreement of the ids of the
+ * exact FP32 top-k, if it is also faster than exact distances; else 0.
+ * Synchronizes `stream`. Errors as detlsh_query.
+ */
+int detlsh_autotune(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dtype,
+                    const int32_t* k, const float* c, const float* r_min, int32_t k_max,
+                    const detlsh_query_params* qp, double min_agreement, int32_t mem,
+                    void* stream, detlsh_tuning* out);
 
 /* detlsh_eps_lemma3 -- eps of Lemma 3 (Eq. 2): eps^2 is the upper
  * alpha1-quantile of chi2(K), alpha1 = exp(-1/L). Returns < 0 on bad input. */

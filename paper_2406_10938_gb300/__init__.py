@@ -7,6 +7,11 @@ The computation lives in ``libdetlsh.so`` (CUDA kernels behind the C ABI of
 from .binding import (  # noqa: F401
     DetlshError,
     Index,
+    Plan,
+    Tuning,
+    detlsh_autotune,
+    detlsh_plan_query,
+    detlsh_plan_status,
     detlsh_build,
     detlsh_encode_values,
     detlsh_eps_lemma3,

@@ -29,7 +29,10 @@ _EXPORT_DTYPE = {"A": torch.float32, "EDGES": torch.float32, "CODES": torch.uint
 SYMBOLS = ("detlsh_build", "detlsh_query", "detlsh_free", "detlsh_export_size", "detlsh_export",
            "detlsh_info", "detlsh_project", "detlsh_encode_values", "detlsh_select_breakpoints",
            "detlsh_eps_lemma3", "detlsh_strerror", "detlsh_last_error", "detlsh_trace_enable",
-           "detlsh_trace_get", "detlsh_launch_count", "detlsh_select_breakpoints_noalloc")
+           "detlsh_trace_get", "detlsh_launch_count", "detlsh_select_breakpoints_noalloc",
+           "detlsh_plan_create", "detlsh_plan_query", "detlsh_plan_status", "detlsh_plan_info",
+           "detlsh_plan_destroy", "detlsh_autotune")
+PLAN_GRAPH = 1
 TRACE_KEYS = ("sample_proj_ms", "breakpoints_ms", "encode_ms", "leaves_ms", "query_proj_ms", "lb_ms",
               "dist_ms", "dist_launches", "lb_launches", "build_ms", "query_ms", "walk_ms", "finalize_ms",
               "bucket_ms")
@@ -47,10 +50,29 @@ class Params(ctypes.Structure):
                 ("flags", ctypes.c_int32)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int64), ("walk_ctas_per_sm", ctypes.c_int32),
+                ("dist_rows", ctypes.c_int32), ("dist_ctas_per_sm", ctypes.c_int32),
+                ("shortlist", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+    def as_dict(self):
+        return {"batch": self.batch, "walk_ctas_per_sm": self.walk_ctas_per_sm, "dist_rows": self.dist_rows,
+                "dist_ctas_per_sm": self.dist_ctas_per_sm, "shortlist": self.shortlist}
+
+
+def _tuning(t) -> Optional[Tuning]:
+    if t is None or isinstance(t, Tuning):
+        return t
+    return Tuning(batch=t.get("batch", 0), walk_ctas_per_sm=t.get("walk_ctas_per_sm", 0),
+                  dist_rows=t.get("dist_rows", 0), dist_ctas_per_sm=t.get("dist_ctas_per_sm", 0),
+                  shortlist=t.get("shortlist", 0))
+
+
 class QueryParams(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("beta", ctypes.c_double),
                 ("cand_ids", ctypes.c_void_p), ("cand_cap", ctypes.c_int64),
-                ("shortlist", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("shortlist", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tuning", ctypes.POINTER(Tuning))]
 
 
 _lib = None
@@ -100,6 +122,19 @@ def lib(path: Optional[str] = None):
     L.detlsh_launch_count.restype = i64
     L.detlsh_select_breakpoints_noalloc.argtypes = [vp, i64, i32, i32, vp, vp]
     L.detlsh_select_breakpoints_noalloc.restype = ctypes.c_int
+    L.detlsh_plan_create.argtypes = [vp, i64, i32, ctypes.POINTER(QueryParams), i32, vp, ctypes.POINTER(vp)]
+    L.detlsh_plan_create.restype = ctypes.c_int
+    L.detlsh_plan_query.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, i32, vp]
+    L.detlsh_plan_query.restype = ctypes.c_int
+    L.detlsh_plan_status.argtypes = [vp, vp]
+    L.detlsh_plan_status.restype = ctypes.c_int
+    L.detlsh_plan_info.argtypes = [vp, ctypes.POINTER(i64)]
+    L.detlsh_plan_info.restype = ctypes.c_int
+    L.detlsh_plan_destroy.argtypes = [vp]
+    L.detlsh_plan_destroy.restype = None
+    L.detlsh_autotune.argtypes = [vp, vp, i64, i32, vp, vp, vp, i32, ctypes.POINTER(QueryParams), dbl, i32,
+                                  vp, ctypes.POINTER(Tuning)]
+    L.detlsh_autotune.restype = ctypes.c_int
     if path is None:
         _lib = L
     return L
@@ -176,25 +211,36 @@ def detlsh_build(X: torch.Tensor, A: torch.Tensor, sample_ids: torch.Tensor, K: 
     return Index(out.value, keep=X if p.flags else None)
 
 
+def _per_query(v, nq, dtype, dev):
+    if not torch.is_tensor(v) or v.dim() == 0:
+        return torch.as_tensor(v, dtype=dtype, device=dev).expand(nq).contiguous()
+    return v.to(dev, dtype).contiguous()
+
+
+def _query_args(Q, k, c, r_min):
+    Q = Q.contiguous()
+    nq, dev = Q.shape[0], Q.device
+    k = _per_query(k, nq, torch.int32, dev)
+    c = _per_query(c, nq, torch.float32, dev)
+    r_min = _per_query(0.0 if r_min is None else r_min, nq, torch.float32, dev)
+    return Q, k, c, r_min
+
+
 def detlsh_query(index: Index, Q: torch.Tensor, k, c, r_min=None, k_max: Optional[int] = None,
                  eps: float = 0.0, beta: float = 0.1, cand_cap: int = 0,
-                 out=None, shortlist: int = 0):
+                 out=None, shortlist: int = 0, tuning=None):
     """Returns (ids int64 [nq,k_max], dist fp32 [nq,k_max], stats int32 [nq,4], cand or None).
 
     ``k``, ``c``, ``r_min`` are per-query tensors (or scalars, broadcast).
-    ``out`` optionally supplies preallocated (ids, dist, stats) tensors.
+    ``out`` optionally supplies preallocated (ids, dist, stats) tensors;
+    ``tuning`` is a ``Tuning`` or a dict of its fields (launch shapes).
     """
-    Q = Q.contiguous()
-    nq = Q.shape[0]
-    dev = Q.device
-    k = torch.as_tensor(k, dtype=torch.int32, device=dev).expand(nq).contiguous() if not torch.is_tensor(k) or k.dim() == 0 else k.to(dev, torch.int32).contiguous()
-    c = torch.as_tensor(c, dtype=torch.float32, device=dev).expand(nq).contiguous() if not torch.is_tensor(c) or c.dim() == 0 else c.to(dev, torch.float32).contiguous()
-    if r_min is None:
-        r_min = 0.0
-    r_min = torch.as_tensor(r_min, dtype=torch.float32, device=dev).expand(nq).contiguous() if not torch.is_tensor(r_min) or r_min.dim() == 0 else r_min.to(dev, torch.float32).contiguous()
+    Q, k, c, r_min = _query_args(Q, k, c, r_min)
+    nq, dev = Q.shape[0], Q.device
     if k_max is None:
         k_max = int(k.max().item()) if nq else 1
     mem = _mem_of(Q, k, c, r_min)
+    tu = _tuning(tuning)
     if out is None:
         ids = torch.empty(nq, k_max, dtype=torch.int64, device=dev)
         dist = torch.empty(nq, k_max, dtype=torch.float32, device=dev)
@@ -203,11 +249,86 @@ def detlsh_query(index: Index, Q: torch.Tensor, k, c, r_min=None, k_max: Optiona
         ids, dist, stats = out
     cand = torch.empty(nq, cand_cap, dtype=torch.int32, device=dev) if cand_cap > 0 else None
     qp = QueryParams(eps=eps, beta=beta, cand_ids=cand.data_ptr() if cand is not None else None,
-                     cand_cap=cand_cap, shortlist=shortlist, reserved=0)
+                     cand_cap=cand_cap, shortlist=shortlist, reserved=0,
+                     tuning=ctypes.pointer(tu) if tu is not None else None)
     st = lib().detlsh_query(index.handle, _ptr(Q), nq, _dtype_code(Q), _ptr(k), _ptr(c), _ptr(r_min),
                             k_max, ctypes.byref(qp), _ptr(ids), _ptr(dist), _ptr(stats), mem, _stream(mem))
     _check(st, "detlsh_query")
     return ids, dist, stats, cand
+
+
+class Plan:
+    """Owner of a detlsh_plan* (preallocated batch buffers, optional CUDA graph)."""
+
+    def __init__(self, index: Index, nq_max: int, k_max: int, eps: float = 0.0, beta: float = 0.1,
+                 shortlist: int = 0, tuning=None, graph: bool = True):
+        self.index = index          # the plan refers to the index
+        self.k_max = k_max
+        self._tuning = _tuning(tuning)
+        qp = QueryParams(eps=eps, beta=beta, cand_ids=None, cand_cap=0, shortlist=shortlist, reserved=0,
+                         tuning=ctypes.pointer(self._tuning) if self._tuning is not None else None)
+        out = ctypes.c_void_p(0)
+        st = lib().detlsh_plan_create(index.handle, nq_max, k_max, ctypes.byref(qp), PLAN_GRAPH if graph else 0,
+                                      _stream(MEM_DEVICE), ctypes.byref(out))
+        _check(st, "detlsh_plan_create")
+        self.handle = ctypes.c_void_p(out.value)
+
+    def destroy(self):
+        if self.handle:
+            lib().detlsh_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        out = (ctypes.c_int64 * 5)()
+        _check(lib().detlsh_plan_info(self.handle, out), "detlsh_plan_info")
+        return {"batch": out[0], "scratch_bytes": out[1], "graph_launches": out[2], "batches": out[3],
+                "graph_kernels": out[4]}
+
+
+def detlsh_plan_query(plan: Plan, Q: torch.Tensor, k, c, r_min=None, out=None):
+    """Returns (ids, dist, stats) like detlsh_query, through the plan."""
+    Q, k, c, r_min = _query_args(Q, k, c, r_min)
+    nq, dev = Q.shape[0], Q.device
+    mem = _mem_of(Q, k, c, r_min)
+    if out is None:
+        ids = torch.empty(nq, plan.k_max, dtype=torch.int64, device=dev)
+        dist = torch.empty(nq, plan.k_max, dtype=torch.float32, device=dev)
+        stats = torch.empty(nq, 4, dtype=torch.int32, device=dev)
+    else:
+        ids, dist, stats = out
+    st = lib().detlsh_plan_query(plan.handle, _ptr(Q), nq, _ptr(k), _ptr(c), _ptr(r_min), _ptr(ids), _ptr(dist),
+                                 _ptr(stats), mem, _stream(mem))
+    _check(st, "detlsh_plan_query")
+    return ids, dist, stats
+
+
+def detlsh_plan_status(plan: Plan) -> int:
+    """Synchronizes torch's current stream; returns the plan's status code."""
+    return lib().detlsh_plan_status(plan.handle, _stream(MEM_DEVICE))
+
+
+def detlsh_autotune(index: Index, Q: torch.Tensor, k, c, r_min=None, k_max: Optional[int] = None,
+                    eps: float = 0.0, beta: float = 0.1, shortlist: int = 0, min_agreement: float = 0.0,
+                    tuning=None) -> dict:
+    """Launch shapes (and, for a BF16 index, a shortlist) timed on the sample Q."""
+    Q, k, c, r_min = _query_args(Q, k, c, r_min)
+    if k_max is None:
+        k_max = int(k.max().item())
+    mem = _mem_of(Q, k, c, r_min)
+    tu = _tuning(tuning)
+    qp = QueryParams(eps=eps, beta=beta, cand_ids=None, cand_cap=0, shortlist=shortlist, reserved=0,
+                     tuning=ctypes.pointer(tu) if tu is not None else None)
+    res = Tuning()
+    st = lib().detlsh_autotune(index.handle, _ptr(Q), Q.shape[0], _dtype_code(Q), _ptr(k), _ptr(c), _ptr(r_min),
+                               k_max, ctypes.byref(qp), float(min_agreement), mem, _stream(mem), ctypes.byref(res))
+    _check(st, "detlsh_autotune")
+    return res.as_dict()
 
 
 def detlsh_export(index: Index, what: str, device="cpu") -> torch.Tensor:

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -21,7 +22,7 @@ void trace_reset(int first, int last) {
 }
 void trace_add(int phase, double v) { g_trace[phase] += v; }
 
-PhaseTimer::PhaseTimer(cudaStream_t s) : s_(s), on_(g_trace_on) {}
+PhaseTimer::PhaseTimer(cudaStream_t s, bool allow) : s_(s), on_(g_trace_on && allow) {}
 PhaseTimer::~PhaseTimer() {
   for (int i = 0; i < n_; ++i) {
     cudaEventDestroy(a_[i]);
@@ -275,6 +276,60 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
 
 using namespace detlsh;
 
+namespace detlsh {
+namespace {
+
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
+struct TuneCtx {
+  const detlsh_index* idx;
+  const void* Q;
+  int64_t nq;
+  const int32_t* k;
+  const float* c;
+  const float* r;
+  int k_max;
+  double eps, beta;
+  int64_t* ids;
+  float* dist;
+  cudaStream_t s;
+};
+
+int run_tuned(const TuneCtx& x, int shortlist, const QueryTuning& tu) {
+  return run_query(x.idx, x.Q, x.nq, x.k, x.c, x.r, x.k_max, x.eps, x.beta, x.ids, x.dist, nullptr,
+                   nullptr, 0, shortlist, tu, x.s);
+}
+
+// device milliseconds of the query (the faster of two runs after one warm-up)
+int time_tuned(const TuneCtx& x, int shortlist, const QueryTuning& tu, float* ms) {
+  EventPair ev;
+  DL_CUDA(cudaEventCreate(&ev.a));
+  DL_CUDA(cudaEventCreate(&ev.b));
+  DL_TRY(run_tuned(x, shortlist, tu));
+  float best = INFINITY;
+  for (int rep = 0; rep < 2; ++rep) {
+    DL_CUDA(cudaEventRecord(ev.a, x.s));
+    DL_TRY(run_tuned(x, shortlist, tu));
+    DL_CUDA(cudaEventRecord(ev.b, x.s));
+    DL_CUDA(cudaEventSynchronize(ev.b));
+    float t = 0.f;
+    DL_CUDA(cudaEventElapsedTime(&t, ev.a, ev.b));
+    best = std::min(best, t);
+  }
+  *ms = best;
+  return DETLSH_OK;
+}
+
+}  // namespace
+
+}  // namespace detlsh
+
 extern "C" {
 
 const char* detlsh_strerror(int status) {
@@ -416,10 +471,12 @@ int detlsh_query(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dty
   DL_TRY(od.stage(out_dist, sizeof(float) * nq * k_max, mem, s));
   DL_TRY(os.stage(out_stats, sizeof(int32_t) * nq * 4, mem, s));
   DL_TRY(oc.stage(cand, cand ? sizeof(uint32_t) * nq * cand_cap : 0, mem, s));
+  QueryTuning tu;
+  DL_TRY(tuning_from_params(qp, &tu));
   DL_TRY(run_query(idx, dQ.d, nq, static_cast<const int32_t*>(dk.d), static_cast<const float*>(dc.d),
                    static_cast<const float*>(dr.d), k_max, eps, beta, static_cast<int64_t*>(oi.d),
                    static_cast<float*>(od.d), static_cast<int32_t*>(os.d), static_cast<uint32_t*>(oc.d),
-                   cand_cap, shortlist, s));
+                   cand_cap, shortlist, tu, s));
   DL_TRY(oi.finish(s));
   DL_TRY(od.finish(s));
   DL_TRY(os.finish(s));
@@ -427,6 +484,140 @@ int detlsh_query(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dty
   total.end();
   DL_TRY(total.finish());
   if (mem == DETLSH_MEM_HOST) DL_CUDA(cudaStreamSynchronize(s));
+  return DETLSH_OK;
+}
+
+int detlsh_autotune(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dtype, const int32_t* k,
+                    const float* c, const float* r_min, int32_t k_max, const detlsh_query_params* qp,
+                    double min_agreement, int32_t mem, void* stream, detlsh_tuning* out) {
+  g_err[0] = 0;
+  DL_REQUIRE(idx != nullptr && out != nullptr, "NULL argument");
+  DL_REQUIRE(mem == DETLSH_MEM_HOST || mem == DETLSH_MEM_DEVICE, "bad mem flag");
+  DL_REQUIRE(dtype == idx->dtype, "query dtype differs from the index's");
+  DL_REQUIRE(nq >= 1, "autotuning needs at least one query");
+  DL_REQUIRE(k_max >= 1 && k_max <= kMaxTopK, "k_max must be in [1, %d]", kMaxTopK);
+  DL_REQUIRE(Q && k && c && r_min, "NULL query argument");
+  DL_REQUIRE(std::isfinite(min_agreement) && min_agreement <= 1.0, "min_agreement must be <= 1");
+  DL_REQUIRE(!qp || !qp->cand_ids, "autotuning does not export candidate lists");
+  double eps = qp ? qp->eps : 0.0;
+  const double beta = qp ? qp->beta : 0.1;
+  DL_REQUIRE(beta >= 0.0 && std::isfinite(beta), "beta must be finite and >= 0");
+  if (!(eps > 0.0)) eps = detlsh_eps_lemma3(idx->K, idx->L);
+  const int32_t shortlist0 = qp ? qp->shortlist : 0;
+  DL_REQUIRE(shortlist0 >= 0, "shortlist must be >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<int32_t> hk(nq);
+  if (mem == DETLSH_MEM_HOST) {
+    std::memcpy(hk.data(), k, sizeof(int32_t) * nq);
+  } else {
+    DL_CUDA(cudaMemcpyAsync(hk.data(), k, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, s));
+    DL_CUDA(cudaStreamSynchronize(s));
+  }
+  for (int64_t i = 0; i < nq; ++i)
+    DL_REQUIRE(hk[i] >= 1 && hk[i] <= k_max, "k[%lld] must be in [1, k_max]", (long long)i);
+  In dQ, dk, dc, dr;
+  DL_TRY(dQ.stage(Q, (size_t)nq * idx->d * dtype_size(dtype), mem, s));
+  DL_TRY(dk.stage(k, sizeof(int32_t) * nq, mem, s));
+  DL_TRY(dc.stage(c, sizeof(float) * nq, mem, s));
+  DL_TRY(dr.stage(r_min, sizeof(float) * nq, mem, s));
+  Scratch ids, dist;
+  DL_TRY(ids.alloc(sizeof(int64_t) * nq * k_max, s));
+  DL_TRY(dist.alloc(sizeof(float) * nq * k_max, s));
+  const TuneCtx x{idx, dQ.d, nq, static_cast<const int32_t*>(dk.d), static_cast<const float*>(dc.d),
+                  static_cast<const float*>(dr.d), k_max, eps, beta, ids.as<int64_t>(),
+                  dist.as<float>(), s};
+  const bool trace = g_trace_on;
+  g_trace_on = false;
+  QueryTuning best;
+  int st = tuning_from_params(qp, &best);
+  float tbest = INFINITY;
+  if (st == DETLSH_OK) st = time_tuned(x, shortlist0, best, &tbest);
+  // coordinate descent over the launch shapes; a shape that does not fit
+  // (shared memory, device memory) is skipped
+  auto attempt = [&](const QueryTuning& t) {
+    if (st != DETLSH_OK) return;
+    float ms = 0.f;
+    const int r = time_tuned(x, shortlist0, t, &ms);
+    if (r == DETLSH_OK && ms < tbest) {
+      tbest = ms;
+      best = t;
+    } else if (r == DETLSH_ECUDA) {
+      st = r;
+    }
+  };
+  for (int w : {1, 2, 3}) {
+    QueryTuning t = best;
+    t.walk_ctas_per_sm = w;
+    attempt(t);
+  }
+  for (int rows : {128, 256, 512, 1024}) {
+    QueryTuning t = best;
+    t.dist_rows = rows;
+    attempt(t);
+  }
+  for (int dc3 : {1, 2, 3}) {
+    QueryTuning t = best;
+    t.dist_ctas_per_sm = dc3;
+    attempt(t);
+  }
+  for (int64_t b : {(int64_t)1024, (int64_t)2048, (int64_t)4096, (int64_t)8192, (int64_t)16384}) {
+    if (b >= nq) break;
+    QueryTuning t = best;
+    t.batch = b;
+    attempt(t);
+  }
+  int32_t pick = 0;
+  if (st == DETLSH_OK && idx->Xb != nullptr && min_agreement > 0.0) {
+    // the exact FP32 top-k of the sample, then the smallest agreeing shortlist
+    float t_exact = 0.f;
+    st = time_tuned(x, 0, best, &t_exact);
+    std::vector<int64_t> ref((size_t)nq * k_max), got((size_t)nq * k_max);
+    if (st == DETLSH_OK) {
+      cudaMemcpyAsync(ref.data(), x.ids, sizeof(int64_t) * ref.size(), cudaMemcpyDeviceToHost, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) st = DETLSH_ECUDA;
+    }
+    for (int32_t sl = 64; st == DETLSH_OK && sl <= 4096; sl *= 2) {
+      if (sl < k_max) continue;
+      st = run_tuned(x, sl, best);
+      if (st != DETLSH_OK) break;
+      cudaMemcpyAsync(got.data(), x.ids, sizeof(int64_t) * got.size(), cudaMemcpyDeviceToHost, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) {
+        st = DETLSH_ECUDA;
+        break;
+      }
+      double agree = 0.0;
+      for (int64_t q = 0; q < nq; ++q) {
+        const int64_t* a = &ref[(size_t)q * k_max];
+        const int64_t* g = &got[(size_t)q * k_max];
+        int64_t have = 0, hit = 0;
+        for (int j = 0; j < hk[q]; ++j) {
+          if (a[j] < 0) continue;
+          ++have;
+          for (int i = 0; i < hk[q]; ++i)
+            if (g[i] == a[j]) {
+              ++hit;
+              break;
+            }
+        }
+        agree += have ? (double)hit / (double)have : 1.0;
+      }
+      agree /= (double)nq;
+      if (agree >= min_agreement) {
+        float t_sl = 0.f;
+        st = time_tuned(x, sl, best, &t_sl);
+        if (st == DETLSH_OK && t_sl < t_exact) pick = sl;
+        break;
+      }
+    }
+  }
+  g_trace_on = trace;
+  if (st != DETLSH_OK) return st;
+  std::memset(out, 0, sizeof(*out));
+  out->batch = best.batch;
+  out->walk_ctas_per_sm = best.walk_ctas_per_sm;
+  out->dist_rows = best.dist_rows;
+  out->dist_ctas_per_sm = best.dist_ctas_per_sm;
+  out->shortlist = pick;
   return DETLSH_OK;
 }
 

@@ -33,7 +33,8 @@ void trace_add(int phase, double v);
 // Records CUDA events around phases on one stream when tracing is on.
 class PhaseTimer {
  public:
-  explicit PhaseTimer(cudaStream_t s);
+  // records only while tracing is on and `allow` (false inside a graph capture)
+  explicit PhaseTimer(cudaStream_t s, bool allow = true);
   ~PhaseTimer();
   void begin(int phase);
   void end();
@@ -189,10 +190,53 @@ int select_breakpoints(const float* Ps, int64_t n_s, int LK, int Nr, float* E,
 int build_leaves(detlsh_index* idx, cudaStream_t s);
 
 // ---- query (query.cu)
+// Launch shapes of the query pipeline (results do not depend on them).
+struct QueryTuning {
+  int64_t batch = 0;         // queries per batch; 0: sized from free device memory
+  int walk_ctas_per_sm = 0;  // walk CTAs per SM, 1..3; 0: as many as fit
+  int dist_rows = 1024;      // candidate rows per distance work item (multiple of 64)
+  int dist_ctas_per_sm = 3;  // persistent distance CTAs per SM, 1..3
+};
+
+// Sizes and scratch layout (byte offsets into one device block) of a batch.
+struct QueryShape {
+  int64_t B, cap, TL, RL, words, max_tree_leaves, items_per_q;
+  int LK, L, wgrid, dgrid, dist_rows, tkc, k_max, shortlist;
+  bool smem_bitmap;
+  size_t wl_total, bk_smem, bytes;
+  size_t o_ctr, o_qp, o_qb16, o_qf, o_lb, o_mm, o_lround, o_hist, o_boff, o_list, o_cand, o_d2,
+      o_rend, o_thr, o_meta, o_wsnew, o_wsbm, o_items;
+};
+
+// control words of a batch (uint32, at QueryShape::o_ctr): queries in the
+// batch, walk query counter, distance items queued, argument error flag,
+// distance items taken
+enum { CT_NQ = 0, CT_WORK, CT_QTAIL, CT_BAD, CT_HEAD, CT_WORDS = 64 };
+
+// the launch shapes of detlsh_query_params::tuning (defaults for zero fields)
+int tuning_from_params(const detlsh_query_params* qp, QueryTuning* tu);
+int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int shortlist,
+                const QueryTuning& tu, QueryShape* out);
+int init_query_scratch(const QueryShape& sh, void* base, cudaStream_t s);
+uint32_t* query_ctr(const QueryShape& sh, void* base);
+// the batch size lives in device memory (one captured graph serves any size
+// up to the shape's B); set it before the batch's kernels
+int set_batch_size(const QueryShape& sh, void* base, int64_t nq, cudaStream_t s);
+// device-side argument check; a batch with a bad argument runs empty and
+// leaves its error word set
+int check_batch_args(const QueryShape& sh, void* base, const int32_t* k, const float* c,
+                     const float* r_min, cudaStream_t s);
+// the query pipeline of one batch: queries q0.. of Q, k, c, r_min and the
+// outputs; nqg bounds the grids (the batch size word may be smaller)
+int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, const void* Q, int64_t q0,
+                  int64_t nqg, const int32_t* k, const float* c, const float* r_min, double eps,
+                  double beta, int64_t* out_ids, float* out_dist, int32_t* out_stats,
+                  uint32_t* cand_ids, int64_t cand_cap, bool vec4, bool timed, cudaStream_t s);
+bool query_vec4(const detlsh_index* idx, const void* Q);
 int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t* k,
               const float* c, const float* r_min, int k_max, double eps, double beta,
               int64_t* out_ids, float* out_dist, int32_t* out_stats, uint32_t* cand_ids,
-              int64_t cand_cap, int shortlist, cudaStream_t s);
+              int64_t cand_cap, int shortlist, const QueryTuning& tu, cudaStream_t s);
 
 // ---- host math (chi2.cpp)
 double chi2_upper_quantile(double alpha, int K);

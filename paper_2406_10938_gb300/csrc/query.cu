@@ -44,7 +44,7 @@ constexpr int LB_THREADS = 256;
 constexpr int LB_QCH = 32;
 
 __global__ void __launch_bounds__(LB_THREADS)
-k_leaf_lb(const float* __restrict__ qp, int64_t nqb, int LK, const float* __restrict__ E, int Nr,
+k_leaf_lb(const float* __restrict__ qp, const uint32_t* __restrict__ nqd, int LK, const float* __restrict__ E, int Nr,
           int K, const uint8_t* __restrict__ leaf_lo, const uint8_t* __restrict__ leaf_hi,
           const uint16_t* __restrict__ leaf_tree, int64_t total_leaves, float* __restrict__ lb2,
           uint32_t* __restrict__ minpos, uint32_t* __restrict__ maxlb) {
@@ -52,6 +52,8 @@ k_leaf_lb(const float* __restrict__ qp, int64_t nqb, int LK, const float* __rest
   __shared__ uint32_t s_min[LB_QCH], s_max[LB_QCH];
   const int64_t leaf = (int64_t)blockIdx.x * LB_THREADS + threadIdx.x;
   const int64_t qb0 = (int64_t)blockIdx.y * LB_QCH;
+  const int64_t nqb = *nqd;
+  if (qb0 >= nqb) return;
   const int nqc = (int)((nqb - qb0) < LB_QCH ? (nqb - qb0) : LB_QCH);
   for (int i = threadIdx.x; i < nqc * LK; i += LB_THREADS) {
     const int q = i / LK, r = i % LK;
@@ -149,12 +151,12 @@ enum {
 // table ends at the first round covering every leaf, or at the round cap with
 // infinite thresholds.
 __global__ void k_thresh(const uint32_t* __restrict__ minpos, const uint32_t* __restrict__ maxlb,
-                         int64_t q0, int64_t nqb, const int32_t* __restrict__ k,
+                         int64_t q0, const uint32_t* __restrict__ nqd, const int32_t* __restrict__ k,
                          const float* __restrict__ c, const float* __restrict__ r_min, double eps,
                          double beta, int64_t n, float* __restrict__ thrP, float* __restrict__ thrC,
                          uint32_t* __restrict__ meta) {
   const int64_t qb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (qb >= nqb) return;
+  if (qb >= (int64_t)*nqd) return;
   const int64_t qg = q0 + qb;
   float* tp = thrP + qb * kRoundCap;
   float* tc = thrC + qb * kRoundCap;
@@ -200,8 +202,9 @@ __global__ void __launch_bounds__(BT)
 k_buckets(const float* __restrict__ lb2, int64_t total_leaves, const float* __restrict__ thrP,
           const uint16_t* __restrict__ leaf_tree, const uint32_t* __restrict__ leaf_range, int L,
           uint8_t* __restrict__ lround, uint32_t* __restrict__ boff, uint32_t* __restrict__ bpts,
-          uint32_t* __restrict__ list, uint32_t* __restrict__ meta) {
+          uint32_t* __restrict__ list, uint32_t* __restrict__ meta, const uint32_t* __restrict__ nqd) {
   extern __shared__ __align__(16) unsigned char smb[];
+  if (blockIdx.x >= *nqd) return;
   const int RL = kRoundCap * L;
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smb);          // [RL]
   uint32_t* s_pts = s_cnt + RL;                                  // [RL]
@@ -329,7 +332,7 @@ struct WalkArgs {
   const uint32_t* leaf_range;
   const uint16_t* leaf_tree;
   int64_t total_leaves;
-  int64_t nqb;
+  const uint32_t* nqd;        // queries in the batch
   const float* lb2;
   const uint32_t* list;       // [nqb][total_leaves] bucket lists
   const uint32_t* boff;       // [nqb][kRoundCap*L+1]
@@ -344,6 +347,9 @@ struct WalkArgs {
   int64_t bitmap_words;
   int smem_bitmap;
   uint32_t* work;             // query counter, zero at launch
+  uint4* items;               // distance work queue: (query, first row, end row) per item
+  uint32_t* qtail;            // items queued, zero at launch
+  int dist_rows;              // candidate rows per item
 };
 
 struct WalkLayout {
@@ -566,13 +572,14 @@ __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
   const uint32_t lt = (1u << lane) - 1u;
 
   __shared__ long long s_qb;
+  const int64_t nqb = *a.nqd;
   while (true) {
     // queries are taken from a counter in global memory, so a CTA that drew
     // short queries takes more of them
     if (threadIdx.x == 0) s_qb = (long long)atomicAdd(a.work, 1u);
     __syncthreads();
     const int64_t qb = s_qb;
-    if (qb >= a.nqb) break;
+    if (qb >= nqb) break;
     const float* lbrow = a.lb2 + qb * a.total_leaves;
     const uint32_t* list = a.list + qb * a.total_leaves;
     uint32_t* cand = a.cand + qb * a.cap;
@@ -709,6 +716,21 @@ __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
       m[MQ_STOP] = misc[W_STOP] ? (uint32_t)misc[W_STOP] : 3u;
       m[MQ_OVERFLOW] = (uint32_t)misc[W_OVF];
     }
+    // queue the distance work of the listed candidates
+    {
+      __shared__ uint32_t s_ib, s_ni;
+      if (threadIdx.x == 0) {
+        const int64_t ns = min((int64_t)misc[W_S], a.cap);
+        s_ni = (uint32_t)((ns + a.dist_rows - 1) / a.dist_rows);
+        s_ib = s_ni ? atomicAdd(a.qtail, s_ni) : 0u;
+      }
+      __syncthreads();
+      const uint32_t ns = (uint32_t)min((int64_t)misc[W_S], a.cap);
+      for (uint32_t i = threadIdx.x; i < s_ni; i += WT) {
+        const uint32_t r0 = i * (uint32_t)a.dist_rows;
+        a.items[s_ib + i] = make_uint4((uint32_t)qb, r0, min(r0 + (uint32_t)a.dist_rows, ns), 0u);
+      }
+    }
     __syncthreads();
     if (!a.smem_bitmap) {
       // leave the global bitmap zeroed: through the candidate list when it
@@ -820,32 +842,47 @@ __device__ __forceinline__ float transpose_reduce8(const float* acc, int lane) {
   return v;
 }
 
+// Persistent over the work queue the walk filled: item (query, r0, r1)
+// covers rows [r0, r1) of that query's candidate list. Each warp takes items
+// from a counter in global memory (so the warps finish together), asking for
+// its next item as soon as it starts one.
+__device__ __forceinline__ uint32_t next_item(uint32_t* head, int lane) {
+  uint32_t it = 0;
+  if (lane == 0) it = atomicAdd(head, 1u);
+  return __shfl_sync(0xffffffffu, it, 0);
+}
+
 template <typename TX>
 __global__ void __launch_bounds__(DT, 3)
 k_dist(const TX* __restrict__ X, int d, const TX* __restrict__ Q, int64_t q0,
-       const uint32_t* __restrict__ cand, int64_t cap, const uint32_t* __restrict__ meta,
-       float* __restrict__ d2out, bool vec4) {
-  const int64_t qb = blockIdx.y;
-  const uint32_t nS = meta[qb * MQ_WORDS + MQ_NS];
-  const int64_t r0 = (int64_t)blockIdx.x * DROWS;
-  if (r0 >= nS) return;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const TX* q = Q + (q0 + qb) * (int64_t)d;
-  const uint32_t* cl = cand + qb * cap;
-  float* out = d2out + qb * cap;
-  const int64_t r1 = min(r0 + (int64_t)DROWS, (int64_t)nS);
-  for (int64_t e0 = r0 + (int64_t)w * ILP; e0 < r1; e0 += DNW * ILP) {
-    uint32_t ids[ILP];
-    float acc[ILP];
+       const uint32_t* __restrict__ cand, int64_t cap, const uint4* __restrict__ items,
+       const uint32_t* __restrict__ qtail, uint32_t* __restrict__ head, float* __restrict__ d2out,
+       bool vec4) {
+  const uint32_t nit = *qtail;
+  const int lane = threadIdx.x & 31;
+  uint32_t it = next_item(head, lane);
+  while (it < nit) {
+    const uint4 item = items[it];
+    const uint32_t nx = next_item(head, lane);
+    const int64_t qb = item.x;
+    const int64_t r0 = item.y, r1 = item.z;
+    const TX* q = Q + (q0 + qb) * (int64_t)d;
+    const uint32_t* cl = cand + qb * cap;
+    float* out = d2out + qb * cap;
+    for (int64_t e0 = r0; e0 < r1; e0 += ILP) {
+      uint32_t ids[ILP];
+      float acc[ILP];
 #pragma unroll
-    for (int u = 0; u < ILP; ++u) {
-      ids[u] = (e0 + u < r1) ? __ldg(cl + e0 + u) : 0xffffffffu;
-      acc[u] = 0.f;
+      for (int u = 0; u < ILP; ++u) {
+        ids[u] = (e0 + u < r1) ? __ldg(cl + e0 + u) : 0xffffffffu;
+        acc[u] = 0.f;
+      }
+      rows_dist2<TX>(X, d, ids, q, vec4, lane, acc);
+      const float v = transpose_reduce8(acc, lane);
+      const int r = (lane >> 2) & 7;
+      if ((lane & 3) == 0 && e0 + r < r1) out[e0 + r] = v;
     }
-    rows_dist2<TX>(X, d, ids, q, vec4, lane, acc);
-    const float v = transpose_reduce8(acc, lane);
-    const int r = (lane >> 2) & 7;
-    if ((lane & 3) == 0 && e0 + r < r1) out[e0 + r] = v;
+    it = nx;
   }
 }
 
@@ -914,31 +951,35 @@ __device__ __forceinline__ float transpose_reduce8_half(const float* acc, int la
 
 __global__ void __launch_bounds__(DT, 3)
 k_dist_bf16(const __nv_bfloat16* __restrict__ Xb, int d, const float* __restrict__ Qf, int64_t q0,
-            const uint32_t* __restrict__ cand, int64_t cap, const uint32_t* __restrict__ meta,
-            float* __restrict__ d2out) {
-  const int64_t qb = blockIdx.y;
-  const uint32_t nS = meta[qb * MQ_WORDS + MQ_NS];
-  const int64_t r0 = (int64_t)blockIdx.x * DROWS;
-  if (r0 >= nS) return;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, h = lane >> 4;
-  const float* q = Qf + (q0 + qb) * (int64_t)d;
-  const uint32_t* cl = cand + qb * cap;
-  float* out = d2out + qb * cap;
-  const int64_t r1 = min(r0 + (int64_t)DROWS, (int64_t)nS);
-  // warp step: 2*ILP rows, rows e0 + h*ILP + u of half-warp h
-  for (int64_t e0 = r0 + (int64_t)w * 2 * ILP; e0 < r1; e0 += DNW * 2 * ILP) {
-    uint32_t ids[ILP];
-    float acc[ILP];
+            const uint32_t* __restrict__ cand, int64_t cap, const uint4* __restrict__ items,
+            const uint32_t* __restrict__ qtail, uint32_t* __restrict__ head, float* __restrict__ d2out) {
+  const uint32_t nit = *qtail;
+  const int lane = threadIdx.x & 31, h = lane >> 4;
+  uint32_t it = next_item(head, lane);
+  while (it < nit) {
+    const uint4 item = items[it];
+    const uint32_t nx = next_item(head, lane);
+    const int64_t qb = item.x;
+    const int64_t r0 = item.y, r1 = item.z;
+    const float* q = Qf + (q0 + qb) * (int64_t)d;
+    const uint32_t* cl = cand + qb * cap;
+    float* out = d2out + qb * cap;
+    // warp step: 2*ILP rows, rows e0 + h*ILP + u of half-warp h
+    for (int64_t e0 = r0; e0 < r1; e0 += 2 * ILP) {
+      uint32_t ids[ILP];
+      float acc[ILP];
 #pragma unroll
-    for (int u = 0; u < ILP; ++u) {
-      const int64_t e = e0 + h * ILP + u;
-      ids[u] = (e < r1) ? __ldg(cl + e) : 0xffffffffu;
-      acc[u] = 0.f;
+      for (int u = 0; u < ILP; ++u) {
+        const int64_t e = e0 + h * ILP + u;
+        ids[u] = (e < r1) ? __ldg(cl + e) : 0xffffffffu;
+        acc[u] = 0.f;
+      }
+      rows_dist2_bf16(Xb, d, ids, q, lane & 15, acc);
+      const float v = transpose_reduce8_half(acc, lane);
+      const int64_t e = e0 + (lane >> 1);   // = e0 + h*ILP + ((lane >> 1) & 7)
+      if ((lane & 1) == 0 && e < r1) out[e] = v;
     }
-    rows_dist2_bf16(Xb, d, ids, q, lane & 15, acc);
-    const float v = transpose_reduce8_half(acc, lane);
-    const int64_t e = e0 + (lane >> 1);   // = e0 + h*ILP + ((lane >> 1) & 7)
-    if ((lane & 1) == 0 && e < r1) out[e] = v;
+    it = nx;
   }
 }
 
@@ -1071,7 +1112,8 @@ struct FinalArgs {
   const uint32_t* round_end;
   const float* thrC;
   const uint32_t* meta;
-  int64_t q0, nqb;
+  int64_t q0;
+  const uint32_t* nqd;
   const int32_t* k;
   int k_max;
   int64_t* out_ids;
@@ -1099,6 +1141,7 @@ __global__ void __launch_bounds__(FT) k_finalize(FinalArgs a) {
   __shared__ uint32_t s_sel[256], s_warp[FT / 32];
   __shared__ unsigned long long s_pref;
   __shared__ int s_need;
+  if (blockIdx.x >= *a.nqd) return;
   const int64_t qb = blockIdx.x;
   const int64_t qg = a.q0 + qb;
   const uint32_t* m = a.meta + qb * MQ_WORDS;
@@ -1257,221 +1300,370 @@ __global__ void __launch_bounds__(FT) k_finalize(FinalArgs a) {
 
 }  // namespace
 
-int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t* k, const float* c,
-              const float* r_min, int k_max, double eps, double beta, int64_t* out_ids,
-              float* out_dist, int32_t* out_stats, uint32_t* cand_ids, int64_t cand_cap,
-              int shortlist, cudaStream_t s) {
-  if (nq == 0) return DETLSH_OK;
+namespace {
+
+__global__ void k_begin_batch(uint32_t* ctr, uint32_t nq) {
+  ctr[CT_NQ] = nq;
+  ctr[CT_BAD] = 0;
+}
+
+__global__ void k_batch_init(uint32_t* __restrict__ ctr, uint32_t* __restrict__ minpos,
+                             uint32_t* __restrict__ maxlb, int64_t B) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < B) {
+    minpos[i] = 0xffffffffu;
+    maxlb[i] = 0u;
+  }
+  if (i == 0) {
+    ctr[CT_WORK] = 0;
+    ctr[CT_QTAIL] = 0;
+    ctr[CT_HEAD] = 0;
+  }
+}
+
+// per-query arguments of the batch: 1 <= k <= k_max, finite c > 1, finite r_min
+__global__ void k_check_batch(const uint32_t* __restrict__ ctr_nq, const int32_t* __restrict__ k,
+                              const float* __restrict__ c, const float* __restrict__ r_min, int k_max,
+                              uint32_t* bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)*ctr_nq) return;
+  const bool ok = k[i] >= 1 && k[i] <= k_max && isfinite(c[i]) && c[i] > 1.0f && isfinite(r_min[i]);
+  if (!ok) atomicExch(bad, 1u);
+}
+
+// a batch with a bad argument runs as an empty batch
+__global__ void k_gate_batch(uint32_t* ctr) {
+  if (ctr[CT_BAD]) ctr[CT_NQ] = 0;
+}
+
+size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+int tuning_from_params(const detlsh_query_params* qp, QueryTuning* tu) {
+  *tu = QueryTuning{};
+  if (!qp || !qp->tuning) return DETLSH_OK;
+  const detlsh_tuning& t = *qp->tuning;
+  DL_REQUIRE(t.batch >= 0, "tuning.batch must be >= 0");
+  tu->batch = t.batch;
+  tu->walk_ctas_per_sm = t.walk_ctas_per_sm;
+  if (t.dist_rows) tu->dist_rows = t.dist_rows;
+  if (t.dist_ctas_per_sm) tu->dist_ctas_per_sm = t.dist_ctas_per_sm;
+  return DETLSH_OK;
+}
+
+int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int shortlist,
+                const QueryTuning& tu, QueryShape* out) {
+  QueryShape sh{};
   if (shortlist > 0 && (idx->Xb == nullptr || shortlist > TKC_MAX / 2)) {
-    set_error("a shortlist needs an index built with the BF16 projection and at most %d entries", TKC_MAX / 2);
+    set_error("a shortlist needs an index built with the BF16 projection and at most %d entries",
+              TKC_MAX / 2);
     return DETLSH_EINVAL;
   }
+  if (tu.dist_rows < 64 || tu.dist_rows > 8192 || tu.dist_rows % 64 != 0) {
+    set_error("dist_rows must be a multiple of 64 in [64, 8192]");
+    return DETLSH_EINVAL;
+  }
+  if (tu.walk_ctas_per_sm < 0 || tu.walk_ctas_per_sm > 3 || tu.dist_ctas_per_sm < 1 ||
+      tu.dist_ctas_per_sm > 3 || tu.batch < 0) {
+    set_error("walk_ctas_per_sm must be in [0, 3], dist_ctas_per_sm in [1, 3], batch >= 0");
+    return DETLSH_EINVAL;
+  }
+  sh.L = idx->L;
+  sh.LK = idx->K * idx->L;
+  sh.TL = idx->total_leaves;
+  sh.RL = (int64_t)kRoundCap * idx->L;
+  sh.k_max = k_max;
+  sh.shortlist = shortlist;
+  sh.dist_rows = tu.dist_rows;
   // the top-k buffer: 4096 keys while it keeps at most 1024 (k, or a shortlist
   // of up to 1024), else 8192 for a shortlist of up to 4096
-  const int tkc = shortlist > 1024 ? 8192 : 4096;
-  const size_t fin_smem = sizeof(unsigned long long) * tkc;
-  DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
-  DL_CUDA(cudaFuncSetAttribute(k_finalize<uint8_t, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
-  DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
-  DL_CUDA(cudaFuncSetAttribute(k_finalize<uint8_t, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
-  const int LK = idx->K * idx->L, L = idx->L;
-  const int64_t TL = idx->total_leaves;
-  int dev = 0, nsm = 0, smem_optin = 0;
+  sh.tkc = shortlist > 1024 ? 8192 : 4096;
+  int dev = 0, nsm = 0, smem_optin = 0, smem_sm = 0;
   DL_CUDA(cudaGetDevice(&dev));
   DL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   DL_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-
-  // projected queries
-  Scratch qp;
-  DL_TRY(qp.alloc(sizeof(float) * nq * LK, s));
-  PhaseTimer tm(s);
-  tm.begin(TR_QUERY_PROJ);
-  if (idx->proj_mode == DETLSH_PROJ_BF16) {
-    Scratch qb16;
-    DL_TRY(qb16.alloc((size_t)nq * idx->d * 2, s));
-    DL_TRY(to_bf16(Q, idx->dtype, nq * idx->d, qb16.p, s));
-    DL_TRY(launch_project_tc(qb16.p, nq, idx->d, idx->Ab, LK, idx->K, nullptr, idx->Nr, nullptr,
-                             qp.as<float>(), LK, 1, idx->d_err, s));
-    DL_TRY(check_tc_error(idx->d_err, s));
-  } else {
-    DL_TRY(launch_project_t(Q, idx->dtype, nq, idx->d, nullptr, idx->At, LK, qp.as<float>(), LK, 1,
-                            s));
-  }
-  tm.end();
-
-  // FP32 queries for the coarse distances
-  Scratch qf;
-  if (shortlist > 0) {
-    DL_TRY(qf.alloc(sizeof(float) * nq * idx->d, s));
-    k_widen_f32<<<(unsigned)std::min<int64_t>(ceil_div(nq * idx->d, 256), 152 * 16), 256, 0, s>>>(
-        Q, idx->dtype, nq * idx->d, qf.as<float>());
-    DL_LAUNCH();
-  }
+  DL_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
 
   // walk configuration: the dedup bitmap in shared memory when it fits
-  const int64_t words = (idx->n + 31) / 32;
-  int smem_sm = 0;
-  DL_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-  const WalkLayout with_bm = walk_layout(L, words);
-  const bool smem_bitmap = 4 * ((int64_t)with_bm.total + 2048) <= (int64_t)smem_sm;
-  const WalkLayout wl = walk_layout(L, smem_bitmap ? words : 0);
+  sh.words = (idx->n + 31) / 32;
+  const WalkLayout with_bm = walk_layout(sh.L, sh.words);
+  sh.smem_bitmap = 4 * ((int64_t)with_bm.total + 2048) <= (int64_t)smem_sm;
+  const WalkLayout wl = walk_layout(sh.L, sh.smem_bitmap ? sh.words : 0);
   if ((int64_t)wl.total + 1024 > smem_optin) {
     set_error("walk kernel needs %zu bytes of shared memory", wl.total);
     return DETLSH_EINVAL;
   }
+  sh.wl_total = wl.total;
   DL_CUDA(cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wl.total));
   int walk_per_sm = 0;
   DL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&walk_per_sm, k_walk, WT, wl.total));
   walk_per_sm = std::max(walk_per_sm, 1);
+  if (tu.walk_ctas_per_sm > 0) walk_per_sm = std::min(walk_per_sm, tu.walk_ctas_per_sm);
+  sh.dgrid = nsm * tu.dist_ctas_per_sm;
+  sh.bk_smem = sizeof(uint32_t) * 2 * sh.RL + sizeof(float) * kRoundCap;
+  if (sh.bk_smem > 48 * 1024)
+    DL_CUDA(cudaFuncSetAttribute(k_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.bk_smem));
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<uint8_t, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<uint8_t, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
 
   // candidate capacity per query: S stays below beta*n+k until its last leaf
   const double tmax = std::ceil(beta * (double)idx->n + (double)k_max);
-  const int64_t cap = std::max<int64_t>(
+  sh.cap = std::max<int64_t>(
       1, std::min<int64_t>(idx->n, (int64_t)std::min(tmax, 9.0e18) - 1 + idx->max_leaf_count));
-  // batch size bounded by the per-query buffers: at most 12 GiB and a quarter
-  // of the free device memory (fewer, larger batches shorten the tails of the
-  // per-query kernels)
-  const int64_t RL = (int64_t)kRoundCap * L;
-  const int64_t per_q = TL * 9 + cap * 8 + RL * 16 + kRoundCap * 12 + MQ_WORDS * 4 + 64;
-  size_t mem_free = 0, mem_total = 0;
-  DL_CUDA(cudaMemGetInfo(&mem_free, &mem_total));
-  const int64_t budget = std::min<int64_t>((int64_t)12 << 30, (int64_t)(mem_free / 4));
-  int64_t qb = std::max<int64_t>(1, std::min<int64_t>(nq, budget / per_q));
-  qb = std::min<int64_t>(qb, 16384);
-  const int wgrid = (int)std::min<int64_t>(qb, (int64_t)nsm * walk_per_sm);
-  Scratch lb, mm, lround, hist, boff, list, candb, d2b, rend, thr, meta, ws_new, ws_bm, work;
-  DL_TRY(lb.alloc(sizeof(float) * qb * TL, s));
-  DL_TRY(mm.alloc(sizeof(uint32_t) * 2 * qb, s));
-  DL_TRY(lround.alloc((size_t)qb * TL, s));
-  DL_TRY(hist.alloc(sizeof(uint32_t) * qb * RL, s));
-  DL_TRY(boff.alloc(sizeof(uint32_t) * qb * (RL + 1), s));
-  DL_TRY(list.alloc(sizeof(uint32_t) * qb * TL, s));
-  DL_TRY(candb.alloc(sizeof(uint32_t) * qb * cap, s));
-  DL_TRY(d2b.alloc(sizeof(float) * qb * cap, s));
-  DL_TRY(rend.alloc(sizeof(uint32_t) * qb * kRoundCap, s));
-  DL_TRY(thr.alloc(sizeof(float) * 2 * qb * kRoundCap, s));
-  DL_TRY(meta.alloc(sizeof(uint32_t) * qb * MQ_WORDS, s));
+  sh.items_per_q = (sh.cap + sh.dist_rows - 1) / sh.dist_rows;
+  // batch size: the tuning's, else bounded by the per-query buffers (at most
+  // 12 GiB and a quarter of the free device memory; fewer, larger batches
+  // shorten the tails of the per-query kernels)
+  const int64_t per_q = sh.TL * 9 + sh.cap * 8 + sh.RL * 16 + kRoundCap * 12 + MQ_WORDS * 4 +
+                        sh.LK * 4 + sh.items_per_q * 16 +
+                        (idx->Xb ? (int64_t)idx->d * 2 : 0) + (shortlist > 0 ? (int64_t)idx->d * 4 : 0) +
+                        64;
+  int64_t B = tu.batch;
+  if (B == 0) {
+    size_t mem_free = 0, mem_total = 0;
+    DL_CUDA(cudaMemGetInfo(&mem_free, &mem_total));
+    const int64_t budget = std::min<int64_t>((int64_t)12 << 30, (int64_t)(mem_free / 4));
+    B = std::max<int64_t>(1, budget / per_q);
+    B = std::min<int64_t>(B, 16384);
+  }
+  B = std::max<int64_t>(1, std::min<int64_t>(B, std::max<int64_t>(nq, 1)));
+  sh.B = B;
+  sh.wgrid = (int)std::min<int64_t>(B, (int64_t)nsm * walk_per_sm);
   int64_t max_tree_leaves = 1;
-  for (int t = 0; t < L; ++t)
+  for (int t = 0; t < sh.L; ++t)
     max_tree_leaves = std::max<int64_t>(max_tree_leaves, idx->leaf_base_h[t + 1] - idx->leaf_base_h[t]);
-  DL_TRY(ws_new.alloc(sizeof(uint32_t) * 2 * wgrid * max_tree_leaves, s));
-  if (!smem_bitmap) {
-    // the walk leaves each CTA's bitmap zeroed after every query
-    DL_TRY(ws_bm.alloc(sizeof(uint32_t) * wgrid * words, s));
-    DL_CUDA(cudaMemsetAsync(ws_bm.p, 0, sizeof(uint32_t) * wgrid * words, s));
+  sh.max_tree_leaves = max_tree_leaves;
+
+  size_t p = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = p;
+    p += al256(bytes);
+    return at;
+  };
+  sh.o_ctr = take(sizeof(uint32_t) * CT_WORDS);
+  sh.o_qp = take(sizeof(float) * B * sh.LK);
+  sh.o_qb16 = take(idx->Xb ? (size_t)B * idx->d * 2 : 0);
+  sh.o_qf = take(shortlist > 0 ? sizeof(float) * B * idx->d : 0);
+  sh.o_lb = take(sizeof(float) * B * sh.TL);
+  sh.o_mm = take(sizeof(uint32_t) * 2 * B);
+  sh.o_lround = take((size_t)B * sh.TL);
+  sh.o_hist = take(sizeof(uint32_t) * B * sh.RL);
+  sh.o_boff = take(sizeof(uint32_t) * B * (sh.RL + 1));
+  sh.o_list = take(sizeof(uint32_t) * B * sh.TL);
+  sh.o_cand = take(sizeof(uint32_t) * B * sh.cap);
+  sh.o_d2 = take(sizeof(float) * B * sh.cap);
+  sh.o_rend = take(sizeof(uint32_t) * B * kRoundCap);
+  sh.o_thr = take(sizeof(float) * 2 * B * kRoundCap);
+  sh.o_meta = take(sizeof(uint32_t) * B * MQ_WORDS);
+  sh.o_wsnew = take(sizeof(uint32_t) * 2 * sh.wgrid * max_tree_leaves);
+  sh.o_wsbm = take(sh.smem_bitmap ? 0 : sizeof(uint32_t) * sh.wgrid * sh.words);
+  sh.o_items = take(sizeof(uint4) * B * sh.items_per_q);
+  sh.bytes = p;
+  *out = sh;
+  return DETLSH_OK;
+}
+
+int init_query_scratch(const QueryShape& sh, void* base, cudaStream_t s) {
+  char* b = static_cast<char*>(base);
+  DL_CUDA(cudaMemsetAsync(b + sh.o_ctr, 0, sizeof(uint32_t) * CT_WORDS, s));
+  // the walk leaves each CTA's bitmap zeroed after every query
+  if (!sh.smem_bitmap)
+    DL_CUDA(cudaMemsetAsync(b + sh.o_wsbm, 0, sizeof(uint32_t) * sh.wgrid * sh.words, s));
+  return DETLSH_OK;
+}
+
+uint32_t* query_ctr(const QueryShape& sh, void* base) {
+  return reinterpret_cast<uint32_t*>(static_cast<char*>(base) + sh.o_ctr);
+}
+
+int set_batch_size(const QueryShape& sh, void* base, int64_t nq, cudaStream_t s) {
+  k_begin_batch<<<1, 1, 0, s>>>(query_ctr(sh, base), (uint32_t)nq);
+  DL_LAUNCH();
+  return DETLSH_OK;
+}
+
+int check_batch_args(const QueryShape& sh, void* base, const int32_t* k, const float* c,
+                     const float* r_min, cudaStream_t s) {
+  uint32_t* ctr = query_ctr(sh, base);
+  k_check_batch<<<ceil_div(sh.B, 256), 256, 0, s>>>(ctr + CT_NQ, k, c, r_min, sh.k_max, ctr + CT_BAD);
+  DL_LAUNCH();
+  k_gate_batch<<<1, 1, 0, s>>>(ctr);
+  DL_LAUNCH();
+  return DETLSH_OK;
+}
+
+int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, const void* Q, int64_t q0,
+                  int64_t nqg, const int32_t* k, const float* c, const float* r_min, double eps,
+                  double beta, int64_t* out_ids, float* out_dist, int32_t* out_stats,
+                  uint32_t* cand_ids, int64_t cand_cap, bool vec4, bool timed, cudaStream_t s) {
+  char* b = static_cast<char*>(base);
+  uint32_t* ctr = reinterpret_cast<uint32_t*>(b + sh.o_ctr);
+  const uint32_t* nqd = ctr + CT_NQ;
+  float* qp = reinterpret_cast<float*>(b + sh.o_qp);
+  float* lb = reinterpret_cast<float*>(b + sh.o_lb);
+  uint32_t* d_min = reinterpret_cast<uint32_t*>(b + sh.o_mm);
+  uint32_t* d_max = d_min + sh.B;
+  uint8_t* lround = reinterpret_cast<uint8_t*>(b + sh.o_lround);
+  uint32_t* h_pts = reinterpret_cast<uint32_t*>(b + sh.o_hist);
+  uint32_t* boff = reinterpret_cast<uint32_t*>(b + sh.o_boff);
+  uint32_t* list = reinterpret_cast<uint32_t*>(b + sh.o_list);
+  uint32_t* candb = reinterpret_cast<uint32_t*>(b + sh.o_cand);
+  float* d2b = reinterpret_cast<float*>(b + sh.o_d2);
+  uint32_t* rend = reinterpret_cast<uint32_t*>(b + sh.o_rend);
+  float* thrP = reinterpret_cast<float*>(b + sh.o_thr);
+  float* thrC = thrP + sh.B * kRoundCap;
+  uint32_t* meta = reinterpret_cast<uint32_t*>(b + sh.o_meta);
+  uint4* items = reinterpret_cast<uint4*>(b + sh.o_items);
+  const int LK = sh.LK, L = sh.L;
+  const int64_t TL = sh.TL;
+  const size_t srow = (size_t)idx->d * (idx->dtype == DETLSH_U8 ? 1 : 4);
+  const void* Qb = static_cast<const char*>(Q) + (size_t)q0 * srow;
+
+  PhaseTimer tm(s, timed);
+  k_batch_init<<<ceil_div(sh.B, 256), 256, 0, s>>>(ctr, d_min, d_max, sh.B);
+  DL_LAUNCH();
+  // projected queries of the batch
+  tm.begin(TR_QUERY_PROJ);
+  if (idx->proj_mode == DETLSH_PROJ_BF16) {
+    void* qb16 = b + sh.o_qb16;
+    DL_TRY(to_bf16(Qb, idx->dtype, nqg * idx->d, qb16, s));
+    DL_TRY(launch_project_tc(qb16, nqg, idx->d, idx->Ab, LK, idx->K, nullptr, idx->Nr, nullptr, qp, LK,
+                             1, idx->d_err, s));
+  } else {
+    DL_TRY(launch_project_t(Qb, idx->dtype, nqg, idx->d, nullptr, idx->At, LK, qp, LK, 1, s));
   }
-  DL_TRY(work.alloc(sizeof(uint32_t), s));
-  uint32_t* d_min = mm.as<uint32_t>();
-  uint32_t* d_max = d_min + qb;
-  uint32_t* h_pts = hist.as<uint32_t>();
-  const size_t bk_smem = sizeof(uint32_t) * 2 * RL + sizeof(float) * kRoundCap;
-  if (bk_smem > 48 * 1024)
-    DL_CUDA(cudaFuncSetAttribute(k_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bk_smem));
-  float* thrP = thr.as<float>();
-  float* thrC = thrP + qb * kRoundCap;
-
-  const bool vec4 = (idx->d % 4 == 0) &&
-                    (reinterpret_cast<uintptr_t>(idx->X) % (idx->dtype == DETLSH_U8 ? 4 : 16) == 0) &&
-                    (reinterpret_cast<uintptr_t>(Q) % (idx->dtype == DETLSH_U8 ? 4 : 16) == 0);
-
-  for (int64_t q0 = 0; q0 < nq; q0 += qb) {
-    const int64_t nqb = std::min<int64_t>(qb, nq - q0);
-    DL_CUDA(cudaMemsetAsync(d_min, 0xff, sizeof(uint32_t) * nqb, s));
-    DL_CUDA(cudaMemsetAsync(d_max, 0x00, sizeof(uint32_t) * nqb, s));
-    dim3 g1(ceil_div(TL, LB_THREADS), ceil_div(nqb, LB_QCH));
-    tm.begin(TR_LB);
-    k_leaf_lb<<<g1, LB_THREADS, 0, s>>>(qp.as<float>() + q0 * LK, nqb, LK, idx->E, idx->Nr, idx->K,
-                                        idx->leaf_lo, idx->leaf_hi, idx->leaf_tree, TL, lb.as<float>(),
-                                        d_min, d_max);
+  tm.end();
+  // FP32 queries of the batch for the coarse distances
+  float* qf = reinterpret_cast<float*>(b + sh.o_qf);
+  if (sh.shortlist > 0) {
+    k_widen_f32<<<(unsigned)std::min<int64_t>(ceil_div(nqg * idx->d, 256), 152 * 16), 256, 0, s>>>(
+        Qb, idx->dtype, nqg * idx->d, qf);
     DL_LAUNCH();
-    tm.end();
-    trace_add(TR_LB_LAUNCHES, 1.0);
-
-    tm.begin(TR_BUCKET);
-    k_thresh<<<ceil_div(nqb, 128), 128, 0, s>>>(d_min, d_max, q0, nqb, k, c, r_min, eps, beta, idx->n,
-                                                thrP, thrC, meta.as<uint32_t>());
-    DL_LAUNCH();
-    k_buckets<<<(unsigned)nqb, BT, bk_smem, s>>>(lb.as<float>(), TL, thrP, idx->leaf_tree,
-                                                 idx->leaf_range, L, lround.as<uint8_t>(),
-                                                 boff.as<uint32_t>(), h_pts, list.as<uint32_t>(),
-                                                 meta.as<uint32_t>());
-    DL_LAUNCH();
-    tm.end();
-    WalkArgs wa{};
-    wa.n = idx->n;
-    wa.L = L;
-    wa.leaf_ids = idx->leaf_ids;
-    wa.leaf_range = idx->leaf_range;
-    wa.leaf_tree = idx->leaf_tree;
-    wa.total_leaves = TL;
-    wa.nqb = nqb;
-    wa.lb2 = lb.as<float>();
-    wa.list = list.as<uint32_t>();
-    wa.boff = boff.as<uint32_t>();
-    wa.hist_pts = h_pts;
-    wa.meta = meta.as<uint32_t>();
-    wa.cand = candb.as<uint32_t>();
-    wa.cap = cap;
-    wa.round_end = rend.as<uint32_t>();
-    wa.ws_newcnt = ws_new.as<uint32_t>();
-    wa.max_bucket = max_tree_leaves;
-    wa.ws_bitmap = smem_bitmap ? nullptr : ws_bm.as<uint32_t>();
-    wa.bitmap_words = words;
-    wa.smem_bitmap = smem_bitmap ? 1 : 0;
-    wa.work = work.as<uint32_t>();
-    DL_CUDA(cudaMemsetAsync(work.p, 0, sizeof(uint32_t), s));
-    tm.begin(TR_WALK);
-    k_walk<<<(unsigned)std::min<int64_t>(nqb, wgrid), WT, wl.total, s>>>(wa);
-    DL_LAUNCH();
-    tm.end();
-
-    dim3 g3(ceil_div(cap, DROWS), (unsigned)nqb);
-    tm.begin(TR_DIST);
-    if (shortlist > 0)
-      k_dist_bf16<<<g3, DT, 0, s>>>(static_cast<const __nv_bfloat16*>(idx->Xb), idx->d, qf.as<float>(), q0,
-                                    candb.as<uint32_t>(), cap, meta.as<uint32_t>(), d2b.as<float>());
-    else if (idx->dtype == DETLSH_U8)
-      k_dist<uint8_t><<<g3, DT, 0, s>>>(static_cast<const uint8_t*>(idx->X), idx->d,
-                                        static_cast<const uint8_t*>(Q), q0, candb.as<uint32_t>(), cap,
-                                        meta.as<uint32_t>(), d2b.as<float>(), vec4);
-    else
-      k_dist<float><<<g3, DT, 0, s>>>(static_cast<const float*>(idx->X), idx->d,
-                                      static_cast<const float*>(Q), q0, candb.as<uint32_t>(), cap,
-                                      meta.as<uint32_t>(), d2b.as<float>(), vec4);
-    DL_LAUNCH();
-    tm.end();
-    trace_add(TR_DIST_LAUNCHES, 1.0);
-
-    FinalArgs fa{};
-    fa.cand = candb.as<uint32_t>();
-    fa.cap = cap;
-    fa.d2 = d2b.as<float>();
-    fa.round_end = rend.as<uint32_t>();
-    fa.thrC = thrC;
-    fa.meta = meta.as<uint32_t>();
-    fa.q0 = q0;
-    fa.nqb = nqb;
-    fa.k = k;
-    fa.k_max = k_max;
-    fa.out_ids = out_ids;
-    fa.out_dist = out_dist;
-    fa.out_stats = out_stats;
-    fa.cand_ids = cand_ids;
-    fa.cand_cap = cand_cap;
-    fa.shortlist = shortlist;
-    fa.X = idx->X;
-    fa.Q = Q;
-    fa.d = idx->d;
-    fa.vec4 = vec4;
-    tm.begin(TR_FINALIZE);
-    if (idx->dtype == DETLSH_U8)
-      (tkc == 4096 ? k_finalize<uint8_t, 4096> : k_finalize<uint8_t, 8192>)<<<(unsigned)nqb, FT, fin_smem, s>>>(fa);
-    else
-      (tkc == 4096 ? k_finalize<float, 4096> : k_finalize<float, 8192>)<<<(unsigned)nqb, FT, fin_smem, s>>>(fa);
-    DL_LAUNCH();
-    tm.end();
   }
+
+  dim3 g1(ceil_div(TL, LB_THREADS), ceil_div(nqg, LB_QCH));
+  tm.begin(TR_LB);
+  k_leaf_lb<<<g1, LB_THREADS, 0, s>>>(qp, nqd, LK, idx->E, idx->Nr, idx->K, idx->leaf_lo, idx->leaf_hi,
+                                      idx->leaf_tree, TL, lb, d_min, d_max);
+  DL_LAUNCH();
+  tm.end();
+  trace_add(TR_LB_LAUNCHES, timed ? 1.0 : 0.0);
+
+  tm.begin(TR_BUCKET);
+  k_thresh<<<ceil_div(nqg, 128), 128, 0, s>>>(d_min, d_max, q0, nqd, k, c, r_min, eps, beta, idx->n,
+                                              thrP, thrC, meta);
+  DL_LAUNCH();
+  k_buckets<<<(unsigned)nqg, BT, sh.bk_smem, s>>>(lb, TL, thrP, idx->leaf_tree, idx->leaf_range, L,
+                                                  lround, boff, h_pts, list, meta, nqd);
+  DL_LAUNCH();
+  tm.end();
+
+  WalkArgs wa{};
+  wa.n = idx->n;
+  wa.L = L;
+  wa.leaf_ids = idx->leaf_ids;
+  wa.leaf_range = idx->leaf_range;
+  wa.leaf_tree = idx->leaf_tree;
+  wa.total_leaves = TL;
+  wa.nqd = nqd;
+  wa.lb2 = lb;
+  wa.list = list;
+  wa.boff = boff;
+  wa.hist_pts = h_pts;
+  wa.meta = meta;
+  wa.cand = candb;
+  wa.cap = sh.cap;
+  wa.round_end = rend;
+  wa.ws_newcnt = reinterpret_cast<uint32_t*>(b + sh.o_wsnew);
+  wa.max_bucket = sh.max_tree_leaves;
+  wa.ws_bitmap = sh.smem_bitmap ? nullptr : reinterpret_cast<uint32_t*>(b + sh.o_wsbm);
+  wa.bitmap_words = sh.words;
+  wa.smem_bitmap = sh.smem_bitmap ? 1 : 0;
+  wa.work = ctr + CT_WORK;
+  wa.items = items;
+  wa.qtail = ctr + CT_QTAIL;
+  wa.dist_rows = sh.dist_rows;
+  tm.begin(TR_WALK);
+  k_walk<<<(unsigned)std::min<int64_t>(nqg, sh.wgrid), WT, sh.wl_total, s>>>(wa);
+  DL_LAUNCH();
+  tm.end();
+
+  tm.begin(TR_DIST);
+  if (sh.shortlist > 0)
+    k_dist_bf16<<<sh.dgrid, DT, 0, s>>>(static_cast<const __nv_bfloat16*>(idx->Xb), idx->d, qf, 0, candb,
+                                         sh.cap, items, ctr + CT_QTAIL, ctr + CT_HEAD, d2b);
+  else if (idx->dtype == DETLSH_U8)
+    k_dist<uint8_t><<<sh.dgrid, DT, 0, s>>>(static_cast<const uint8_t*>(idx->X), idx->d,
+                                             static_cast<const uint8_t*>(Q), q0, candb, sh.cap, items,
+                                             ctr + CT_QTAIL, ctr + CT_HEAD, d2b, vec4);
+  else
+    k_dist<float><<<sh.dgrid, DT, 0, s>>>(static_cast<const float*>(idx->X), idx->d,
+                                           static_cast<const float*>(Q), q0, candb, sh.cap, items,
+                                           ctr + CT_QTAIL, ctr + CT_HEAD, d2b, vec4);
+  DL_LAUNCH();
+  tm.end();
+  trace_add(TR_DIST_LAUNCHES, timed ? 1.0 : 0.0);
+
+  FinalArgs fa{};
+  fa.cand = candb;
+  fa.cap = sh.cap;
+  fa.d2 = d2b;
+  fa.round_end = rend;
+  fa.thrC = thrC;
+  fa.meta = meta;
+  fa.q0 = q0;
+  fa.nqd = nqd;
+  fa.k = k;
+  fa.k_max = sh.k_max;
+  fa.out_ids = out_ids;
+  fa.out_dist = out_dist;
+  fa.out_stats = out_stats;
+  fa.cand_ids = cand_ids;
+  fa.cand_cap = cand_cap;
+  fa.shortlist = sh.shortlist;
+  fa.X = idx->X;
+  fa.Q = Q;
+  fa.d = idx->d;
+  fa.vec4 = vec4;
+  const size_t fin_smem = sizeof(unsigned long long) * sh.tkc;
+  tm.begin(TR_FINALIZE);
+  if (idx->dtype == DETLSH_U8)
+    (sh.tkc == 4096 ? k_finalize<uint8_t, 4096> : k_finalize<uint8_t, 8192>)<<<(unsigned)nqg, FT, fin_smem, s>>>(fa);
+  else
+    (sh.tkc == 4096 ? k_finalize<float, 4096> : k_finalize<float, 8192>)<<<(unsigned)nqg, FT, fin_smem, s>>>(fa);
+  DL_LAUNCH();
+  tm.end();
   DL_TRY(tm.finish());
+  return DETLSH_OK;
+}
+
+bool query_vec4(const detlsh_index* idx, const void* Q) {
+  const uintptr_t al = idx->dtype == DETLSH_U8 ? 4 : 16;
+  return (idx->d % 4 == 0) && (reinterpret_cast<uintptr_t>(idx->X) % al == 0) &&
+         (reinterpret_cast<uintptr_t>(Q) % al == 0);
+}
+
+int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t* k, const float* c,
+              const float* r_min, int k_max, double eps, double beta, int64_t* out_ids,
+              float* out_dist, int32_t* out_stats, uint32_t* cand_ids, int64_t cand_cap,
+              int shortlist, const QueryTuning& tu, cudaStream_t s) {
+  if (nq == 0) return DETLSH_OK;
+  QueryShape sh;
+  DL_TRY(query_shape(idx, nq, k_max, beta, shortlist, tu, &sh));
+  Scratch ws;
+  DL_TRY(ws.alloc(sh.bytes, s));
+  DL_TRY(init_query_scratch(sh, ws.p, s));
+  const bool vec4 = query_vec4(idx, Q);
+  for (int64_t q0 = 0; q0 < nq; q0 += sh.B) {
+    const int64_t nqb = std::min<int64_t>(sh.B, nq - q0);
+    DL_TRY(set_batch_size(sh, ws.p, nqb, s));
+    DL_TRY(enqueue_batch(idx, sh, ws.p, Q, q0, nqb, k, c, r_min, eps, beta, out_ids, out_dist, out_stats,
+                         cand_ids, cand_cap, vec4, true, s));
+  }
+  if (idx->proj_mode == DETLSH_PROJ_BF16) DL_TRY(check_tc_error(idx->d_err, s));
   return DETLSH_OK;
 }
 
