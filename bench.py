@@ -357,6 +357,169 @@ def gpu_arm(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------------------ batching workload
+BATCHING = dict(name="batching", n=10_000_000, d=96, nq=100_000, K=16, L=4, n_regions=256, n_s=100_000,
+                max_leaf=256, beta=0.01, k_max=100)
+
+
+def batching_desc():
+    return ("batching: n=10,000,000 d=96 fp32 unit vectors, 10,000 clusters on the sphere (Deep-like), "
+            f"{BATCHING['nq']:,} queries per step with k~U[1,100] and c in {{1.2,1.5,2.0}}; K=16 L=4 N_r=256 "
+            "n_s=1% max_leaf=256 beta=0.01 (recall@k >= 0.9); index built once before the timed steps")
+
+
+def batching_arm(args, rank, world, local_rank):
+    """Query throughput on the batching workload through one of three routes:
+    detlsh_query (per-call scratch, direct launches), a plan with direct
+    launches, or a plan replaying its captured CUDA graph per batch."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2406_10938_gb300 as pkg
+    from workloads import gaussian_projection, make_workload, sample_ids
+
+    pkg.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = BATCHING
+    nq, km = w["nq"], w["k_max"]
+    X, Q = make_workload("batching", n=w["n"], nq=nq, seed_query=2 + rank, device=dev)
+    A = gaussian_projection(w["L"], w["K"], w["d"], device=dev)
+    ids = sample_ids(w["n"], w["n_s"], device=dev)
+    g = torch.Generator().manual_seed(17 + rank)
+    kk = torch.randint(1, km + 1, (nq,), generator=g, dtype=torch.int32).to(dev)
+    cc = torch.tensor([1.2, 1.5, 2.0])[torch.randint(0, 3, (nq,), generator=g)].to(dev)
+    rr = torch.zeros(nq, dtype=torch.float32, device=dev)
+    proj_mode = 1 if args.proj == "bf16" else 0
+    pkg.detlsh_trace_enable(True)
+    idx = pkg.detlsh_build(X, A, ids, w["K"], w["L"], w["n_regions"], w["max_leaf"], borrow=True,
+                           proj_mode=proj_mode)
+    idx.free()
+    idx = pkg.detlsh_build(X, A, ids, w["K"], w["L"], w["n_regions"], w["max_leaf"], borrow=True,
+                           proj_mode=proj_mode)
+    build_ms = pkg.detlsh_trace_get()["build_ms"]
+    info = idx.info()
+    out = (torch.empty(nq, km, dtype=torch.int64, device=dev), torch.empty(nq, km, dtype=torch.float32, device=dev),
+           torch.empty(nq, 4, dtype=torch.int32, device=dev))
+    plan = None
+    if args.route != "query":
+        plan = pkg.Plan(idx, nq_max=args.plan_batch, k_max=km, beta=w["beta"], shortlist=args.shortlist,
+                        graph=args.route == "graph")
+
+    def step():
+        if plan is None:
+            pkg.detlsh_query(idx, Q, kk, cc, rr, k_max=km, beta=w["beta"], out=out, shortlist=args.shortlist)
+        else:
+            pkg.detlsh_plan_query(plan, Q, kk, cc, rr, out=out)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # phase times of the same batch through detlsh_query (graph replays cannot be traced per kernel)
+    pkg.detlsh_query(idx, Q, kk, cc, rr, k_max=km, beta=w["beta"], out=out, shortlist=args.shortlist)
+    ph = pkg.detlsh_trace_get()
+    pkg.detlsh_trace_enable(False)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    l0 = pkg.detlsh_launch_count()
+    g0 = plan.info()["graph_launches"] if plan is not None else 0
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = pkg.detlsh_launch_count() - l0
+    if plan is not None:
+        pi = plan.info()
+        launches += (pi["graph_launches"] - g0) * pi["graph_kernels"]
+    t = torch.tensor([ev0.elapsed_time(ev1)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / args.steps
+    value = world * nq / (ms_per_step / 1000.0)
+
+    stats = out[2].cpu().numpy()
+    n_cand = float(stats[:, 0].astype("float64").sum())
+    # per-k recall on 400 sampled queries against an exact scan (untimed)
+    sel = torch.linspace(0, nq - 1, 400).long()
+    rec, kq_all = [], kk.cpu()
+    for i0 in range(0, len(sel), 8):
+        qs = sel[i0:i0 + 8]
+        d = torch.cdist(Q[qs.to(dev)], X, compute_mode="donot_use_mm_for_euclid_dist")
+        top = torch.topk(d, km, largest=False).indices.cpu()
+        got = out[0][qs.to(dev)].cpu()
+        for j, qi in enumerate(qs.tolist()):
+            kq = int(kq_all[qi])
+            rec.append((kq, len(set(top[j, :kq].tolist()) & set(got[j, :kq].tolist())) / kq))
+    by_k = {}
+    for lo, hi in ((1, 25), (26, 50), (51, 75), (76, 100)):
+        v = [r for kq, r in rec if lo <= kq <= hi]
+        by_k[f"k{lo}-{hi}"] = round(sum(v) / max(1, len(v)), 4)
+    recall = sum(r for _, r in rec) / len(rec)
+
+    dbytes = w["d"] * (2 if args.shortlist else 4) + 8
+    cand = {("k_dist_bf16" if args.shortlist else "k_dist"): (n_cand * dbytes, ph["dist_ms"], ph["dist_launches"]),
+            "k_walk": (nq * info["total_leaves"] * 4.0 + n_cand * 8, ph["walk_ms"], ph["dist_launches"]),
+            "k_leaf_lb": (nq * info["total_leaves"] * 4.0, ph["lb_ms"], ph["lb_launches"])}
+    dom = max(cand, key=lambda k_: cand[k_][1])
+    b, ms, nl = cand[dom]
+    peak, peak_kind = _peaks()
+    achieved = (b / nl) / ((ms / nl) / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                "algorithmic_bytes_per_launch": b / nl, "launches_per_step": nl, "avg_launch_ms": ms / nl,
+                "source": "CUDA events around each kernel in a traced detlsh_query of the same batch"}
+
+    # end to end with host buffers through the same route
+    Qh = Q.cpu().pin_memory()
+    kh, ch, rh = kk.cpu(), cc.cpu(), rr.cpu()
+    outh = (torch.empty(nq, km, dtype=torch.int64).pin_memory(), torch.empty(nq, km).pin_memory(),
+            torch.empty(nq, 4, dtype=torch.int32).pin_memory())
+
+    def step_host():
+        if plan is None:
+            pkg.detlsh_query(idx, Qh, kh, ch, rh, k_max=km, beta=w["beta"], out=outh, shortlist=args.shortlist)
+        else:
+            pkg.detlsh_plan_query(plan, Qh, kh, ch, rh, out=outh)
+
+    step_host()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        step_host()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if plan is not None:
+        plan.destroy()
+    idx.free()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": batching_desc(), **w, "route": args.route, "plan_batch": args.plan_batch,
+                           "projection": args.proj, "shortlist": args.shortlist,
+                           "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (X is 3.84 GB)"},
+                "clocks": clk,
+                "e2e": {"value": world * nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * (w["d"] * 4 + 12),
+                        "d2h_bytes_per_step": nq * (km * 12 + 16)},
+                "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": None,
+                "build_mpts_per_s": w["n"] / (build_ms / 1000.0) / 1e6, "recall_at_k": round(recall, 4),
+                "recall_by_k": by_k, "mean_candidates": n_cand / nq,
+                "phase_ms": {k_: round(v, 4) for k_, v in ph.items()}}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -370,11 +533,20 @@ def main():
                     help="projection arithmetic of the build (bf16: tensor cores)")
     ap.add_argument("--shortlist", type=int, default=0,
                     help="with --proj bf16: coarse BF16 candidate distances, FP32 re-rank of this many")
+    ap.add_argument("--workload", default="mid", choices=["mid", "batching"],
+                    help="mid: build + 10,000 queries per step (default); batching: 100,000 mixed queries "
+                         "per step against a 10,000,000-point index")
+    ap.add_argument("--route", default="query", choices=["query", "plan", "graph"],
+                    help="batching workload: detlsh_query, a plan with direct launches, or a plan replaying "
+                         "its CUDA graph")
+    ap.add_argument("--plan-batch", type=int, default=8192, help="queries per plan batch")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     WORKLOAD["nq"] = args.nq
+    if args.impl == "reference" and args.workload != "mid":
+        ap.error("the reference arm times the mid workload")
     if args.impl == "reference":
         return reference_arm(args, rank, world)
     if args.shortlist and args.proj != "bf16":
@@ -385,6 +557,8 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     try:
+        if args.workload == "batching":
+            return batching_arm(args, rank, world, local_rank)
         return gpu_arm(args, rank, world, local_rank)
     finally:
         if world > 1:
