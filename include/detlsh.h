@@ -29,6 +29,7 @@ extern "C" {
 #endif
 
 typedef enum {
+  DETLSH_PENDING = 1,    /* detlsh_server_poll: the request has not finished */
   DETLSH_OK = 0,
   DETLSH_EINVAL = -1,    /* an argument is out of range or inconsistent   */
   DETLSH_ENOMEM = -2,    /* device or host allocation failed              */
@@ -298,6 +299,76 @@ int detlsh_autotune(const detlsh_index* idx, const void* Q, int64_t nq, int32_t 
                     const int32_t* k, const float* c, const float* r_min, int32_t k_max,
                     const detlsh_query_params* qp, double min_agreement, int32_t mem,
                     void* stream, detlsh_tuning* out);
+
+/*
+ * Continuous-batching server (no counterpart in the paper: Alg. 7 queries
+ * that arrive one at a time, answered in batches against a resident index).
+ *
+ * A server admits requests into a fixed pool of queue_cap slots; a worker
+ * thread forms batches of up to `slots` queries in arrival order and runs
+ * each through one of `pipelines` query plans (own stream, preallocated
+ * device buffers, CUDA-graph replay), so that consecutive batches overlap. A
+ * batch starts when it is full, when no batch is running, or when its oldest
+ * request has waited max_delay_us. Each query's result is the one
+ * detlsh_query gives for it alone: it does not depend on the batch.
+ */
+typedef struct {
+  int32_t k_max;           /* largest k of a request, 1..1024                     */
+  int32_t slots;           /* queries per batch; 0: the largest power of two
+                              <= 4096 whose buffers for all pipelines fit
+                              mem_budget                                          */
+  int32_t pipelines;       /* batches in flight, 1..4 (0: 2)                      */
+  int32_t queue_cap;       /* requests admitted and not yet collected
+                              (0: 4 * slots * pipelines)                          */
+  int32_t max_delay_us;    /* wait of a partial batch while another runs (0: 200) */
+  int32_t shortlist;       /* as detlsh_query_params.shortlist                    */
+  double eps, beta;        /* as detlsh_query_params                              */
+  int64_t mem_budget;      /* device bytes for the batch buffers of all pipelines
+                              (0: 8 GiB); creation fails with DETLSH_EADMIT if
+                              `slots` does not fit                                */
+  const detlsh_tuning* tuning;  /* launch shapes (NULL: defaults)                */
+  int32_t test_fail_batch; /* > 0: the N-th batch is reported failed
+                              (DETLSH_ECUDA) without running, to exercise
+                              failure handling on the host; 0 in service       */
+  int32_t reserved;
+} detlsh_server_config;
+typedef struct detlsh_server detlsh_server;
+
+/* detlsh_server_create -- plans, streams and the worker thread over idx (which
+ * must outlive the server); errors as detlsh_plan_create, DETLSH_EADMIT as
+ * above. */
+int detlsh_server_create(const detlsh_index* idx, const detlsh_server_config* cfg,
+                         detlsh_server** out);
+/* detlsh_server_submit -- copies the query q (host memory, d values of the
+ * index dtype) with its k, c and r_min into a free slot and queues it;
+ * *ticket identifies it. DETLSH_EADMIT when every slot is in use (collect
+ * finished requests with detlsh_server_poll), DETLSH_EINVAL on bad arguments. */
+int detlsh_server_submit(detlsh_server* srv, const void* q, int32_t k, float c, float r_min,
+                         uint64_t* ticket);
+/* detlsh_server_poll -- waits up to wait_us for the request; DETLSH_PENDING if
+ * it has not finished, else the batch's status (DETLSH_OK or an error) with
+ * the results copied to ids/dist [k_max] and stats [4] (as detlsh_query; any
+ * may be NULL) and *latency_us (optional) = completion - submission; the
+ * ticket is then released. */
+int detlsh_server_poll(detlsh_server* srv, uint64_t ticket, int32_t wait_us, int64_t* ids,
+                       float* dist, int32_t* stats, double* latency_us);
+/* detlsh_server_replay -- open-loop load: submits query i (host arrays) at
+ * arrival_us[i] microseconds after the call starts (non-decreasing; a full
+ * pool delays the submission), collects every result into out_ids/out_dist
+ * [nq][k_max] and out_stats [nq][4] (each optional) and writes latency_us[i] =
+ * completion - scheduled arrival (-1 for a failed request). Returns the first
+ * error of any request, else DETLSH_OK. */
+int detlsh_server_replay(detlsh_server* srv, const void* Q, int64_t nq, const int32_t* k,
+                         const float* c, const float* r_min, const double* arrival_us,
+                         int64_t* out_ids, float* out_dist, int32_t* out_stats,
+                         double* latency_us);
+/* detlsh_server_stats -- out[0] submitted, [1] completed, [2] rejected by
+ * admission, [3] batches, [4] queries in batches, [5] largest batch,
+ * [6] requests failed, [7] batch capacity. */
+int detlsh_server_stats(detlsh_server* srv, int64_t* out8);
+/* detlsh_server_destroy -- runs the queued requests, stops the worker and
+ * frees the server (uncollected results are dropped). */
+void detlsh_server_destroy(detlsh_server* srv);
 
 /* detlsh_eps_lemma3 -- eps of Lemma 3 (Eq. 2): eps^2 is the upper
  * alpha1-quantile of chi2(K), alpha1 = exp(-1/L). Returns < 0 on bad input. */

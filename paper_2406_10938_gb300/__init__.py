@@ -8,6 +8,7 @@ from .binding import (  # noqa: F401
     DetlshError,
     Index,
     Plan,
+    Server,
     Tuning,
     detlsh_autotune,
     detlsh_plan_query,

@@ -31,7 +31,9 @@ SYMBOLS = ("detlsh_build", "detlsh_query", "detlsh_free", "detlsh_export_size", 
            "detlsh_eps_lemma3", "detlsh_strerror", "detlsh_last_error", "detlsh_trace_enable",
            "detlsh_trace_get", "detlsh_launch_count", "detlsh_select_breakpoints_noalloc",
            "detlsh_plan_create", "detlsh_plan_query", "detlsh_plan_status", "detlsh_plan_info",
-           "detlsh_plan_destroy", "detlsh_autotune")
+           "detlsh_plan_destroy", "detlsh_autotune", "detlsh_server_create", "detlsh_server_submit",
+           "detlsh_server_poll", "detlsh_server_replay", "detlsh_server_stats", "detlsh_server_destroy")
+PENDING, EADMIT = 1, -5
 PLAN_GRAPH = 1
 TRACE_KEYS = ("sample_proj_ms", "breakpoints_ms", "encode_ms", "leaves_ms", "query_proj_ms", "lb_ms",
               "dist_ms", "dist_launches", "lb_launches", "build_ms", "query_ms", "walk_ms", "finalize_ms",
@@ -66,6 +68,14 @@ def _tuning(t) -> Optional[Tuning]:
     return Tuning(batch=t.get("batch", 0), walk_ctas_per_sm=t.get("walk_ctas_per_sm", 0),
                   dist_rows=t.get("dist_rows", 0), dist_ctas_per_sm=t.get("dist_ctas_per_sm", 0),
                   shortlist=t.get("shortlist", 0))
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("k_max", ctypes.c_int32), ("slots", ctypes.c_int32), ("pipelines", ctypes.c_int32),
+                ("queue_cap", ctypes.c_int32), ("max_delay_us", ctypes.c_int32), ("shortlist", ctypes.c_int32),
+                ("eps", ctypes.c_double), ("beta", ctypes.c_double), ("mem_budget", ctypes.c_int64),
+                ("tuning", ctypes.POINTER(Tuning)), ("test_fail_batch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class QueryParams(ctypes.Structure):
@@ -135,6 +145,18 @@ def lib(path: Optional[str] = None):
     L.detlsh_autotune.argtypes = [vp, vp, i64, i32, vp, vp, vp, i32, ctypes.POINTER(QueryParams), dbl, i32,
                                   vp, ctypes.POINTER(Tuning)]
     L.detlsh_autotune.restype = ctypes.c_int
+    L.detlsh_server_create.argtypes = [vp, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    L.detlsh_server_create.restype = ctypes.c_int
+    L.detlsh_server_submit.argtypes = [vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_uint64)]
+    L.detlsh_server_submit.restype = ctypes.c_int
+    L.detlsh_server_poll.argtypes = [vp, ctypes.c_uint64, i32, vp, vp, vp, ctypes.POINTER(dbl)]
+    L.detlsh_server_poll.restype = ctypes.c_int
+    L.detlsh_server_replay.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.detlsh_server_replay.restype = ctypes.c_int
+    L.detlsh_server_stats.argtypes = [vp, ctypes.POINTER(i64)]
+    L.detlsh_server_stats.restype = ctypes.c_int
+    L.detlsh_server_destroy.argtypes = [vp]
+    L.detlsh_server_destroy.restype = None
     if path is None:
         _lib = L
     return L
@@ -329,6 +351,81 @@ def detlsh_autotune(index: Index, Q: torch.Tensor, k, c, r_min=None, k_max: Opti
                                k_max, ctypes.byref(qp), float(min_agreement), mem, _stream(mem), ctypes.byref(res))
     _check(st, "detlsh_autotune")
     return res.as_dict()
+
+
+class Server:
+    """Owner of a detlsh_server* (continuous batching over a resident index).
+
+    Queries and results live in host memory (CPU tensors)."""
+
+    def __init__(self, index: Index, k_max: int, slots: int = 0, pipelines: int = 0, queue_cap: int = 0,
+                 max_delay_us: int = 0, eps: float = 0.0, beta: float = 0.1, shortlist: int = 0,
+                 mem_budget: int = 0, tuning=None, test_fail_batch: int = 0):
+        self.index = index
+        self.k_max = k_max
+        self._tuning = _tuning(tuning)
+        cfg = ServerConfig(k_max=k_max, slots=slots, pipelines=pipelines, queue_cap=queue_cap,
+                           max_delay_us=max_delay_us, shortlist=shortlist, eps=eps, beta=beta,
+                           mem_budget=mem_budget,
+                           tuning=ctypes.pointer(self._tuning) if self._tuning is not None else None,
+                           test_fail_batch=test_fail_batch, reserved=0)
+        out = ctypes.c_void_p(0)
+        _check(lib().detlsh_server_create(index.handle, ctypes.byref(cfg), ctypes.byref(out)),
+               "detlsh_server_create")
+        self.handle = ctypes.c_void_p(out.value)
+
+    def submit(self, q: torch.Tensor, k: int, c: float, r_min: float = 0.0) -> int:
+        """Queues one query (a CPU tensor of d values); returns its ticket.
+        Raises DetlshError (status EADMIT when every slot is in use)."""
+        q = q.contiguous()
+        if q.device.type != "cpu":
+            raise ValueError("server queries are host tensors")
+        t = ctypes.c_uint64(0)
+        _check(lib().detlsh_server_submit(self.handle, _ptr(q), int(k), float(c), float(r_min), ctypes.byref(t)),
+               "detlsh_server_submit")
+        return t.value
+
+    def poll(self, ticket: int, wait_us: int = 0):
+        """(status, ids, dist, stats, latency_us); ids/dist/stats are None unless status is 0."""
+        ids = torch.empty(self.k_max, dtype=torch.int64)
+        dist = torch.empty(self.k_max, dtype=torch.float32)
+        stats = torch.empty(4, dtype=torch.int32)
+        lat = ctypes.c_double(0.0)
+        st = lib().detlsh_server_poll(self.handle, ctypes.c_uint64(ticket), int(wait_us), _ptr(ids), _ptr(dist),
+                                      _ptr(stats), ctypes.byref(lat))
+        if st != 0:
+            return st, None, None, None, (lat.value if st != PENDING else None)
+        return st, ids, dist, stats, lat.value
+
+    def replay(self, Q: torch.Tensor, k, c, r_min, arrival_us: torch.Tensor):
+        """Open-loop load: returns (status, ids, dist, stats, latency_us) for all queries."""
+        Q, k, c, r_min = _query_args(Q, k, c, r_min)
+        nq = Q.shape[0]
+        arr = arrival_us.to(torch.float64).contiguous()
+        ids = torch.empty(nq, self.k_max, dtype=torch.int64)
+        dist = torch.empty(nq, self.k_max, dtype=torch.float32)
+        stats = torch.empty(nq, 4, dtype=torch.int32)
+        lat = torch.empty(nq, dtype=torch.float64)
+        st = lib().detlsh_server_replay(self.handle, _ptr(Q), nq, _ptr(k), _ptr(c), _ptr(r_min), _ptr(arr), _ptr(ids),
+                                        _ptr(dist), _ptr(stats), _ptr(lat))
+        return st, ids, dist, stats, lat
+
+    def stats(self) -> dict:
+        out = (ctypes.c_int64 * 8)()
+        _check(lib().detlsh_server_stats(self.handle, out), "detlsh_server_stats")
+        keys = ("submitted", "completed", "rejected", "batches", "batched_queries", "max_batch", "errors", "slots")
+        return dict(zip(keys, list(out)))
+
+    def destroy(self):
+        if self.handle:
+            lib().detlsh_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def detlsh_export(index: Index, what: str, device="cpu") -> torch.Tensor:

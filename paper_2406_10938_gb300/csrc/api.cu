@@ -334,6 +334,7 @@ extern "C" {
 
 const char* detlsh_strerror(int status) {
   switch (status) {
+    case DETLSH_PENDING: return "pending";
     case DETLSH_OK: return "success";
     case DETLSH_EINVAL: return "invalid argument";
     case DETLSH_ENOMEM: return "out of memory";

@@ -233,6 +233,15 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
                   double beta, int64_t* out_ids, float* out_dist, int32_t* out_stats,
                   uint32_t* cand_ids, int64_t cand_cap, bool vec4, bool timed, cudaStream_t s);
 bool query_vec4(const detlsh_index* idx, const void* Q);
+
+// ---- plans (plan.cu), for the server
+int64_t plan_capacity(const detlsh_plan* p);
+size_t plan_bytes(const detlsh_plan* p);
+// a plan batch from caller buffers with the given copy kinds (cudaMemcpyDefault
+// for pinned host memory), fully asynchronous on s; no host argument checks
+int plan_enqueue(detlsh_plan* p, const void* Q, int64_t nq, const int32_t* k, const float* c,
+                 const float* r_min, int64_t* out_ids, float* out_dist, int32_t* out_stats,
+                 cudaMemcpyKind in, cudaMemcpyKind outk, cudaStream_t s);
 int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t* k,
               const float* c, const float* r_min, int k_max, double eps, double beta,
               int64_t* out_ids, float* out_dist, int32_t* out_stats, uint32_t* cand_ids,

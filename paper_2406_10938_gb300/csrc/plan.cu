@@ -169,24 +169,16 @@ int detlsh_plan_create(const detlsh_index* idx, int64_t nq_max, int32_t k_max,
   return DETLSH_OK;
 }
 
-int detlsh_plan_query(detlsh_plan* p, const void* Q, int64_t nq, const int32_t* k, const float* c,
-                      const float* r_min, int64_t* out_ids, float* out_dist, int32_t* out_stats,
-                      int32_t mem, void* stream) {
-  DL_REQUIRE(p != nullptr, "plan is NULL");
-  DL_REQUIRE(mem == DETLSH_MEM_HOST || mem == DETLSH_MEM_DEVICE, "bad mem flag");
-  DL_REQUIRE(nq >= 0, "nq must be >= 0");
-  if (nq == 0) return DETLSH_OK;
-  DL_REQUIRE(Q && k && c && r_min && out_ids && out_dist, "NULL query argument");
-  if (mem == DETLSH_MEM_HOST) {
-    for (int64_t i = 0; i < nq; ++i) {
-      DL_REQUIRE(k[i] >= 1 && k[i] <= p->k_max, "k[%lld] must be in [1, k_max]", (long long)i);
-      DL_REQUIRE(std::isfinite(c[i]) && c[i] > 1.0f, "c[%lld] must be finite and > 1", (long long)i);
-      DL_REQUIRE(std::isfinite(r_min[i]), "r_min[%lld] must be finite", (long long)i);
-    }
-  }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const cudaMemcpyKind in = mem == DETLSH_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  const cudaMemcpyKind outk = mem == DETLSH_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+}  // extern "C"
+
+namespace detlsh {
+
+int64_t plan_capacity(const detlsh_plan* p) { return p->sh.B; }
+size_t plan_bytes(const detlsh_plan* p) { return p->sh.bytes; }
+
+int plan_enqueue(detlsh_plan* p, const void* Q, int64_t nq, const int32_t* k, const float* c,
+                 const float* r_min, int64_t* out_ids, float* out_dist, int32_t* out_stats,
+                 cudaMemcpyKind in, cudaMemcpyKind outk, cudaStream_t s) {
   const size_t qrow = (size_t)p->idx->d * (p->idx->dtype == DETLSH_U8 ? 1 : 4);
   const int64_t B = p->sh.B;
   const int km = p->k_max;
@@ -209,6 +201,32 @@ int detlsh_plan_query(detlsh_plan* p, const void* Q, int64_t nq, const int32_t* 
     if (out_stats)
       DL_CUDA(cudaMemcpyAsync(out_stats + q0 * 4, p->stats, sizeof(int32_t) * m * 4, outk, s));
   }
+  return DETLSH_OK;
+}
+
+}  // namespace detlsh
+
+extern "C" {
+
+int detlsh_plan_query(detlsh_plan* p, const void* Q, int64_t nq, const int32_t* k, const float* c,
+                      const float* r_min, int64_t* out_ids, float* out_dist, int32_t* out_stats,
+                      int32_t mem, void* stream) {
+  DL_REQUIRE(p != nullptr, "plan is NULL");
+  DL_REQUIRE(mem == DETLSH_MEM_HOST || mem == DETLSH_MEM_DEVICE, "bad mem flag");
+  DL_REQUIRE(nq >= 0, "nq must be >= 0");
+  if (nq == 0) return DETLSH_OK;
+  DL_REQUIRE(Q && k && c && r_min && out_ids && out_dist, "NULL query argument");
+  if (mem == DETLSH_MEM_HOST) {
+    for (int64_t i = 0; i < nq; ++i) {
+      DL_REQUIRE(k[i] >= 1 && k[i] <= p->k_max, "k[%lld] must be in [1, k_max]", (long long)i);
+      DL_REQUIRE(std::isfinite(c[i]) && c[i] > 1.0f, "c[%lld] must be finite and > 1", (long long)i);
+      DL_REQUIRE(std::isfinite(r_min[i]), "r_min[%lld] must be finite", (long long)i);
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cudaMemcpyKind in = mem == DETLSH_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind outk = mem == DETLSH_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  DL_TRY(plan_enqueue(p, Q, nq, k, c, r_min, out_ids, out_dist, out_stats, in, outk, s));
   if (mem == DETLSH_MEM_HOST) return detlsh_plan_status(p, stream);
   return DETLSH_OK;
 }
