@@ -189,6 +189,12 @@ int select_breakpoints(const float* Ps, int64_t n_s, int LK, int Nr, float* E,
 // ---- leaves (leaves.cu)
 int build_leaves(detlsh_index* idx, cudaStream_t s);
 
+// ---- sorts with caller storage (sort.cu)
+size_t radix_ws_bytes(int64_t n, int bit_lo, int bit_hi);
+int radix_sort_pairs_ws(const uint32_t* keys_in, const uint32_t* vals_in, int64_t n, int bit_lo,
+                        int bit_hi, uint32_t* keys_out, uint32_t* vals_out, void* ws, size_t ws_bytes,
+                        cudaStream_t s);
+
 // ---- query (query.cu)
 // Launch shapes of the query pipeline (results do not depend on them).
 struct QueryTuning {
@@ -205,7 +211,7 @@ struct QueryShape {
   bool smem_bitmap;
   size_t wl_total, bk_smem, bytes;
   size_t o_ctr, o_qp, o_qb16, o_qf, o_lb, o_mm, o_lround, o_hist, o_boff, o_list, o_cand, o_d2,
-      o_rend, o_thr, o_meta, o_wsnew, o_wsbm, o_items;
+      o_rend, o_thr, o_meta, o_wsnew, o_wsbm, o_items, o_qk, o_qsort, qsort_bytes;
 };
 
 // control words of a batch (uint32, at QueryShape::o_ctr): queries in the

@@ -43,12 +43,39 @@ namespace {
 constexpr int LB_THREADS = 256;
 constexpr int LB_QCH = 32;
 
+// Packed FP32 pair arithmetic (two independent IEEE round-to-nearest
+// operations per instruction) and a three-input maximum.
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float lo2(unsigned long long v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi2(unsigned long long v) { return __uint_as_float((uint32_t)(v >> 32)); }
+
+// Leaf lower bound: sum over j = 0..K-1, in that order, of
+// max(e_lo - x, x - e_hi, 0)^2 in FP32 (no contraction). Dimensions are taken
+// in pairs with packed FP32x2 subtractions and products; the sum keeps the
+// scalar order.
 __global__ void __launch_bounds__(LB_THREADS)
 k_leaf_lb(const float* __restrict__ qp, const uint32_t* __restrict__ nqd, int LK, const float* __restrict__ E, int Nr,
           int K, const uint8_t* __restrict__ leaf_lo, const uint8_t* __restrict__ leaf_hi,
           const uint16_t* __restrict__ leaf_tree, int64_t total_leaves, float* __restrict__ lb2,
           uint32_t* __restrict__ minpos, uint32_t* __restrict__ maxlb) {
-  __shared__ float s_q[LB_QCH][kMaxLK + 1];
+  __shared__ __align__(16) float s_q[LB_QCH][kMaxLK + 2];
   __shared__ uint32_t s_min[LB_QCH], s_max[LB_QCH];
   const int64_t leaf = (int64_t)blockIdx.x * LB_THREADS + threadIdx.x;
   const int64_t qb0 = (int64_t)blockIdx.y * LB_QCH;
@@ -78,17 +105,41 @@ k_leaf_lb(const float* __restrict__ qp, const uint32_t* __restrict__ nqd, int LK
       if (hi < Nr - 1) eh[j] = __ldg(E + (int64_t)r * (Nr + 1) + hi + 1);
     }
   }
+  unsigned long long el2[kMaxK / 2], eh2[kMaxK / 2];
+#pragma unroll
+  for (int j = 0; j < kMaxK / 2; ++j) {
+    el2[j] = pack2(el[2 * j], el[2 * j + 1]);
+    eh2[j] = pack2(eh[2 * j], eh[2 * j + 1]);
+  }
   const int rbase = tree * K;
+  const bool paired = (rbase % 2) == 0;   // s_q row offsets of an even base are 8-byte aligned
   for (int q = 0; q < nqc; ++q) {
     float acc = 0.f;
+    if (paired) {
+      const float* xq = &s_q[q][rbase];
 #pragma unroll
-    for (int j = 0; j < kMaxK; ++j) {
-      if (j < K) {
-        const float x = s_q[q][rbase + j];
-        const float a = __fsub_rn(el[j], x);
-        const float b = __fsub_rn(x, eh[j]);
-        const float dl = fmaxf(fmaxf(a, b), 0.f);
-        acc = __fadd_rn(acc, __fmul_rn(dl, dl));
+      for (int j = 0; j < kMaxK; j += 2) {
+        if (j + 1 < K) {
+          const unsigned long long x2 = *reinterpret_cast<const unsigned long long*>(xq + j);
+          const unsigned long long a2 = sub2(el2[j / 2], x2), b2 = sub2(x2, eh2[j / 2]);
+          const float d0 = max3f(lo2(a2), lo2(b2), 0.f), d1 = max3f(hi2(a2), hi2(b2), 0.f);
+          const unsigned long long dd = mul2(pack2(d0, d1), pack2(d0, d1));
+          acc = __fadd_rn(acc, lo2(dd));
+          acc = __fadd_rn(acc, hi2(dd));
+        } else if (j < K) {
+          const float x = xq[j];
+          const float dl = max3f(__fsub_rn(el[j], x), __fsub_rn(x, eh[j]), 0.f);
+          acc = __fadd_rn(acc, __fmul_rn(dl, dl));
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < kMaxK; ++j) {
+        if (j < K) {
+          const float x = s_q[q][rbase + j];
+          const float dl = max3f(__fsub_rn(el[j], x), __fsub_rn(x, eh[j]), 0.f);
+          acc = __fadd_rn(acc, __fmul_rn(dl, dl));
+        }
       }
     }
     if (valid) lb2[(qb0 + q) * total_leaves + leaf] = acc;
@@ -318,6 +369,40 @@ k_buckets(const float* __restrict__ lb2, int64_t total_leaves, const float* __re
   }
 }
 
+// ------------------------------------------------------------------ query order
+// Locality key of a query: the top bit-planes of its region codes in the first
+// projected space (bit 7 of every dimension, then bit 6, ...), 32 bits. Queries
+// with equal high bits lie in the same DE-Tree root cells, so they share
+// candidates. Positions at or past the batch size get the largest key.
+__global__ void k_query_keys(const float* __restrict__ qp, int LK, const uint32_t* __restrict__ nqd,
+                             const float* __restrict__ E, int Nr, int K, int64_t B,
+                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  vals[i] = (uint32_t)i;
+  if (i >= (int64_t)*nqd) {
+    keys[i] = 0xffffffffu;
+    return;
+  }
+  uint32_t code[kMaxK];
+  for (int j = 0; j < K; ++j) {
+    const float p = qp[i * LK + j];
+    const float* e = E + (int64_t)j * (Nr + 1);
+    int lo = 1, hi = Nr;   // number of interior edges e[1..Nr-1] that are <= p
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (e[mid] <= p) lo = mid + 1;
+      else hi = mid;
+    }
+    code[j] = (uint32_t)(lo - 1);
+  }
+  uint32_t key = 0;
+  int nb = 0;
+  for (int plane = 7; plane >= 0 && nb < 32; --plane)
+    for (int j = 0; j < K && nb < 32; ++j, ++nb) key = (key << 1) | ((code[j] >> plane) & 1u);
+  keys[i] = key << (32 - nb);
+}
+
 // ------------------------------------------------------------------ walk
 constexpr int WT = 256;            // threads per walk CTA (several per SM)
 constexpr int WNW = WT / 32;
@@ -347,6 +432,7 @@ struct WalkArgs {
   int64_t bitmap_words;
   int smem_bitmap;
   uint32_t* work;             // query counter, zero at launch
+  const uint32_t* order;      // [nqb] the batch's queries in locality order
   uint4* items;               // distance work queue: (query, first row, end row) per item
   uint32_t* qtail;            // items queued, zero at launch
   int dist_rows;              // candidate rows per item
@@ -576,7 +662,12 @@ __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
   while (true) {
     // queries are taken from a counter in global memory, so a CTA that drew
     // short queries takes more of them
-    if (threadIdx.x == 0) s_qb = (long long)atomicAdd(a.work, 1u);
+    // ... in locality order (queries with similar codes in turn, so that
+    // their distance work, queued in this order, shares rows in L2)
+    if (threadIdx.x == 0) {
+      const uint32_t i = atomicAdd(a.work, 1u);
+      s_qb = (int64_t)i < nqb ? (long long)a.order[i] : (long long)nqb;
+    }
     __syncthreads();
     const int64_t qb = s_qb;
     if (qb >= nqb) break;
@@ -1461,6 +1552,9 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   sh.o_wsnew = take(sizeof(uint32_t) * 2 * sh.wgrid * max_tree_leaves);
   sh.o_wsbm = take(sh.smem_bitmap ? 0 : sizeof(uint32_t) * sh.wgrid * sh.words);
   sh.o_items = take(sizeof(uint4) * B * sh.items_per_q);
+  sh.o_qk = take(sizeof(uint32_t) * 4 * B);
+  sh.qsort_bytes = radix_ws_bytes(B, 0, 32);
+  sh.o_qsort = take(sh.qsort_bytes);
   sh.bytes = p;
   *out = sh;
   return DETLSH_OK;
@@ -1517,6 +1611,7 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   float* thrC = thrP + sh.B * kRoundCap;
   uint32_t* meta = reinterpret_cast<uint32_t*>(b + sh.o_meta);
   uint4* items = reinterpret_cast<uint4*>(b + sh.o_items);
+  uint32_t* qk = reinterpret_cast<uint32_t*>(b + sh.o_qk);   // keys, ids, sorted keys, order
   const int LK = sh.LK, L = sh.L;
   const int64_t TL = sh.TL;
   const size_t srow = (size_t)idx->d * (idx->dtype == DETLSH_U8 ? 1 : 4);
@@ -1535,6 +1630,11 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   } else {
     DL_TRY(launch_project_t(Qb, idx->dtype, nqg, idx->d, nullptr, idx->At, LK, qp, LK, 1, s));
   }
+  // the walk's query order: by locality key
+  k_query_keys<<<ceil_div(nqg, 256), 256, 0, s>>>(qp, LK, nqd, idx->E, idx->Nr, idx->K, nqg, qk, qk + sh.B);
+  DL_LAUNCH();
+  DL_TRY(radix_sort_pairs_ws(qk, qk + sh.B, nqg, 0, 32, qk + 2 * sh.B, qk + 3 * sh.B, b + sh.o_qsort,
+                             sh.qsort_bytes, s));
   tm.end();
   // FP32 queries of the batch for the coarse distances
   float* qf = reinterpret_cast<float*>(b + sh.o_qf);
@@ -1583,6 +1683,7 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   wa.bitmap_words = sh.words;
   wa.smem_bitmap = sh.smem_bitmap ? 1 : 0;
   wa.work = ctr + CT_WORK;
+  wa.order = qk + 3 * sh.B;
   wa.items = items;
   wa.qtail = ctr + CT_QTAIL;
   wa.dist_rows = sh.dist_rows;
@@ -1646,6 +1747,42 @@ bool query_vec4(const detlsh_index* idx, const void* Q) {
          (reinterpret_cast<uintptr_t>(Q) % al == 0);
 }
 
+namespace {
+
+// dst row i = src row perm[i] (gather) or dst row perm[i] = src row i
+// (scatter), rows of `words` 32-bit words or of `bytes` bytes
+template <typename W, bool GATHER>
+__global__ void k_permute_rows(const W* __restrict__ src, W* __restrict__ dst, const uint32_t* __restrict__ perm,
+                               int64_t rows, int64_t row_len) {
+  const int64_t total = rows * row_len;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / row_len, j = e - i * row_len;
+    const int64_t pi = perm[i];
+    if (GATHER) dst[i * row_len + j] = src[pi * row_len + j];
+    else dst[pi * row_len + j] = src[i * row_len + j];
+  }
+}
+
+template <bool GATHER>
+int permute_rows(const void* src, void* dst, const uint32_t* perm, int64_t rows, size_t row_bytes, cudaStream_t s) {
+  if (rows == 0 || row_bytes == 0) return DETLSH_OK;
+  const bool w4 = row_bytes % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 4 == 0 &&
+                  reinterpret_cast<uintptr_t>(dst) % 4 == 0;
+  const int64_t len = w4 ? (int64_t)(row_bytes / 4) : (int64_t)row_bytes;
+  const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(rows * len, 256), 152 * 16);
+  if (w4)
+    k_permute_rows<uint32_t, GATHER><<<blocks, 256, 0, s>>>(static_cast<const uint32_t*>(src),
+                                                            static_cast<uint32_t*>(dst), perm, rows, len);
+  else
+    k_permute_rows<uint8_t, GATHER><<<blocks, 256, 0, s>>>(static_cast<const uint8_t*>(src),
+                                                           static_cast<uint8_t*>(dst), perm, rows, len);
+  DL_LAUNCH();
+  return DETLSH_OK;
+}
+
+}  // namespace
+
 int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t* k, const float* c,
               const float* r_min, int k_max, double eps, double beta, int64_t* out_ids,
               float* out_dist, int32_t* out_stats, uint32_t* cand_ids, int64_t cand_cap,
@@ -1656,12 +1793,68 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
   Scratch ws;
   DL_TRY(ws.alloc(sh.bytes, s));
   DL_TRY(init_query_scratch(sh, ws.p, s));
-  const bool vec4 = query_vec4(idx, Q);
+  const size_t srow = (size_t)idx->d * (idx->dtype == DETLSH_U8 ? 1 : 4);
+  const void* Qr = Q;
+  const int32_t* kr = k;
+  const float *cr = c, *rr = r_min;
+  int64_t* oi = out_ids;
+  float* od = out_dist;
+  int32_t* os = out_stats;
+  uint32_t* oc = cand_ids;
+  Scratch ord, inq, outq;
+  const uint32_t* perm = nullptr;
+  if (nq > sh.B) {
+    // several batches: all queries in locality order first, so that each
+    // batch holds neighbouring queries (their candidate rows meet in L2);
+    // inputs are gathered in that order and results scattered back
+    const int LK = sh.LK;
+    const size_t keys_b = (sizeof(uint32_t) * 4 * nq + 255) & ~size_t(255);
+    const size_t sort_b = radix_ws_bytes(nq, 0, 32);
+    DL_TRY(ord.alloc(sizeof(float) * nq * LK + keys_b + sort_b, s));
+    float* qpa = ord.as<float>();
+    uint32_t* keys = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(ord.p) + sizeof(float) * nq * LK);
+    DL_TRY(launch_project_t(Q, idx->dtype, nq, idx->d, nullptr, idx->At, LK, qpa, LK, 1, s));
+    DL_TRY(set_batch_size(sh, ws.p, nq, s));
+    k_query_keys<<<ceil_div(nq, 256), 256, 0, s>>>(qpa, LK, query_ctr(sh, ws.p) + CT_NQ, idx->E, idx->Nr,
+                                                  idx->K, nq, keys, keys + nq);
+    DL_LAUNCH();
+    DL_TRY(radix_sort_pairs_ws(keys, keys + nq, nq, 0, 32, keys + 2 * nq, keys + 3 * nq,
+                               reinterpret_cast<char*>(keys) + keys_b, sort_b, s));
+    perm = keys + 3 * nq;
+    const size_t q_b = (srow * nq + 255) & ~size_t(255), a_b = (sizeof(float) * nq + 255) & ~size_t(255);
+    DL_TRY(inq.alloc(q_b + 3 * a_b, s));
+    char* ib = static_cast<char*>(inq.p);
+    DL_TRY(permute_rows<true>(Q, ib, perm, nq, srow, s));
+    DL_TRY(permute_rows<true>(k, ib + q_b, perm, nq, 4, s));
+    DL_TRY(permute_rows<true>(c, ib + q_b + a_b, perm, nq, 4, s));
+    DL_TRY(permute_rows<true>(r_min, ib + q_b + 2 * a_b, perm, nq, 4, s));
+    Qr = ib;
+    kr = reinterpret_cast<const int32_t*>(ib + q_b);
+    cr = reinterpret_cast<const float*>(ib + q_b + a_b);
+    rr = reinterpret_cast<const float*>(ib + q_b + 2 * a_b);
+    const size_t ids_b = (sizeof(int64_t) * nq * k_max + 255) & ~size_t(255);
+    const size_t dist_b = (sizeof(float) * nq * k_max + 255) & ~size_t(255);
+    const size_t st_b = (sizeof(int32_t) * nq * 4 + 255) & ~size_t(255);
+    const size_t cand_b = cand_ids ? sizeof(uint32_t) * nq * cand_cap : 0;
+    DL_TRY(outq.alloc(ids_b + dist_b + st_b + cand_b, s));
+    char* obuf = static_cast<char*>(outq.p);
+    oi = reinterpret_cast<int64_t*>(obuf);
+    od = reinterpret_cast<float*>(obuf + ids_b);
+    os = out_stats ? reinterpret_cast<int32_t*>(obuf + ids_b + dist_b) : nullptr;
+    oc = cand_ids ? reinterpret_cast<uint32_t*>(obuf + ids_b + dist_b + st_b) : nullptr;
+  }
+  const bool vec4 = query_vec4(idx, Qr);
   for (int64_t q0 = 0; q0 < nq; q0 += sh.B) {
     const int64_t nqb = std::min<int64_t>(sh.B, nq - q0);
     DL_TRY(set_batch_size(sh, ws.p, nqb, s));
-    DL_TRY(enqueue_batch(idx, sh, ws.p, Q, q0, nqb, k, c, r_min, eps, beta, out_ids, out_dist, out_stats,
-                         cand_ids, cand_cap, vec4, true, s));
+    DL_TRY(enqueue_batch(idx, sh, ws.p, Qr, q0, nqb, kr, cr, rr, eps, beta, oi, od, os, oc, cand_cap, vec4,
+                         true, s));
+  }
+  if (perm) {
+    DL_TRY(permute_rows<false>(oi, out_ids, perm, nq, sizeof(int64_t) * k_max, s));
+    DL_TRY(permute_rows<false>(od, out_dist, perm, nq, sizeof(float) * k_max, s));
+    if (out_stats) DL_TRY(permute_rows<false>(os, out_stats, perm, nq, sizeof(int32_t) * 4, s));
+    if (cand_ids) DL_TRY(permute_rows<false>(oc, cand_ids, perm, nq, sizeof(uint32_t) * cand_cap, s));
   }
   if (idx->proj_mode == DETLSH_PROJ_BF16) DL_TRY(check_tc_error(idx->d_err, s));
   return DETLSH_OK;
