@@ -294,6 +294,50 @@ def gpu_arm(args, rank, world, local_rank):
         hits += len(set(exact.tolist()) & set(ids_out[qi].tolist()))
     recall = hits / (nqr * w["k"])
 
+    # the mixed-precision path on the same steps: BF16 tensor-core build, BF16
+    # coarse candidate distances, FP32 re-rank of an autotuned shortlist
+    mixed = None
+    if proj_mode == 0 and not args.no_mixed:
+        pkg.detlsh_trace_enable(False)
+        idx_m = pkg.detlsh_build(X, A, ids, w["K"], w["L"], w["n_regions"], w["max_leaf"], borrow=True, proj_mode=1)
+        ns = min(nq, 2000)
+        tune = pkg.detlsh_autotune(idx_m, Q[:ns], kk[:ns], cc[:ns], rr[:ns], k_max=w["k"], eps=eps, beta=w["beta"],
+                                   min_agreement=0.995)
+        idx_m.free()
+        sl = tune["shortlist"]
+        out_m = (torch.empty_like(out[0]), torch.empty_like(out[1]), torch.empty_like(out[2]))
+
+        def step_m():
+            im = pkg.detlsh_build(X, A, ids, w["K"], w["L"], w["n_regions"], w["max_leaf"], borrow=True, proj_mode=1)
+            pkg.detlsh_query(im, Q, kk, cc, rr, k_max=w["k"], eps=eps, beta=w["beta"], out=out_m, shortlist=sl,
+                             tuning=tune)
+            im.free()
+
+        for _ in range(args.warmup):
+            step_m()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_m()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tm_ = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tm_, op=dist.ReduceOp.MAX)
+        ms_m = float(tm_.item()) / args.steps
+        hits_m = 0
+        for qi in range(nqr):
+            d2 = ((X - Q[qi]) ** 2).sum(dim=1)
+            exact = torch.topk(d2, w["k"], largest=False).indices
+            hits_m += len(set(exact.tolist()) & set(out_m[0][qi].tolist()))
+        mixed = {"value": world * nq / (ms_m / 1000.0), "unit": "queries/s", "ms_per_step": ms_m,
+                 "recall_at_k": hits_m / (nqr * w["k"]), "shortlist": sl, "tuning": tune,
+                 "projection": "bf16 tcgen05 (FP32 accumulation)",
+                 "distances": "bf16 coarse (FP32 accumulation), FP32 re-rank of the shortlist",
+                 "vs_plain_fp32": (ms_per_step / ms_m)}
+
     # end to end through the public API with host buffers
     e2e_steps = max(1, min(args.steps, 3))
     Xh = X.cpu().pin_memory()
@@ -351,6 +395,7 @@ def gpu_arm(args, rank, world, local_rank):
                 "build_mpts_per_s": w["n"] / (ph["build_ms"] / 1000.0) / 1e6,
                 "query_qps": nq / (ph["query_ms"] / 1000.0),
                 "recall_at_k": recall,
+                "mixed_precision": mixed,
                 "mean_candidates": mean_S,
                 "phase_ms": {k_: round(v, 4) for k_, v in ph.items()}}
         print(json.dumps(line), flush=True)
@@ -646,6 +691,7 @@ def main():
                     help="projection arithmetic of the build (bf16: tensor cores)")
     ap.add_argument("--shortlist", type=int, default=0,
                     help="with --proj bf16: coarse BF16 candidate distances, FP32 re-rank of this many")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison of the mid step")
     ap.add_argument("--workload", default="mid", choices=["mid", "batching", "serving"],
                     help="mid: build + 10,000 queries per step (default); batching: 100,000 mixed queries "
                          "per step against a 10,000,000-point index")

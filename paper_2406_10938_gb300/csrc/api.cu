@@ -166,7 +166,7 @@ void free_index(detlsh_index* idx) {
   if (idx->owns_x && idx->X) cudaFree(const_cast<void*>(idx->X));
   void* arrays[] = {idx->A, idx->At, idx->E, idx->Ps, idx->codes, idx->leaf_ids, idx->leaf_base,
                     idx->leaf_range, idx->leaf_plen, idx->leaf_prefix, idx->leaf_lo, idx->leaf_hi,
-                    idx->leaf_tree, idx->Xb, idx->Ab, idx->d_err};
+                    idx->leaf_tree, idx->Xb, idx->Ab, idx->d_err, idx->Rtab, idx->Rlo, idx->Rinv, idx->Atf};
   for (void* p : arrays)
     if (p) cudaFree(p);
   delete idx;
@@ -224,6 +224,9 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
   DL_CUDA(cudaMalloc(&idx->E, sizeof(float) * LK * (Nr + 1)));
   DL_CUDA(cudaMalloc(&idx->codes, (size_t)n * LK));
   DL_CUDA(cudaMalloc(&idx->leaf_ids, sizeof(uint32_t) * n * L));
+  DL_CUDA(cudaMalloc(&idx->Rtab, (size_t)LK * kRegionRow));
+  DL_CUDA(cudaMalloc(&idx->Rlo, sizeof(float) * LK));
+  DL_CUDA(cudaMalloc(&idx->Rinv, sizeof(float) * LK));
   if (prm->proj_mode == DETLSH_PROJ_BF16) {
     // BF16 copies of X and A; projections on the tensor cores
     const int N = (LK + 15) / 16 * 16;
@@ -238,29 +241,58 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
     Scratch xs;
     DL_TRY(xs.alloc((size_t)prm->n_s * d * 2, s));
     DL_TRY(gather_rows_bf16(idx->Xb, d, static_cast<const int64_t*>(ids.d), prm->n_s, xs.p, s));
-    DL_TRY(launch_project_tc(xs.p, prm->n_s, d, idx->Ab, LK, K, nullptr, Nr, nullptr, idx->Ps, 1,
-                             prm->n_s, idx->d_err, s));
+    DL_TRY(launch_project_tc(xs.p, prm->n_s, d, idx->Ab, LK, K, nullptr, nullptr, nullptr, nullptr, Nr, nullptr,
+                             idx->Ps, 1, prm->n_s, idx->d_err, s));
     tm.end();
     tm.begin(TR_BREAKPOINTS);
     DL_TRY(select_breakpoints(idx->Ps, prm->n_s, LK, Nr, idx->E, s));
+    DL_TRY(build_region_tables(idx->E, LK, Nr, idx->Rtab, idx->Rlo, idx->Rinv, s));
     tm.end();
     tm.begin(TR_ENCODE);
-    DL_TRY(launch_project_tc(idx->Xb, n, d, idx->Ab, LK, K, idx->E, Nr, idx->codes, nullptr, 0, 0,
-                             idx->d_err, s));
+    DL_TRY(launch_project_tc(idx->Xb, n, d, idx->Ab, LK, K, idx->E, idx->Rtab, idx->Rlo, idx->Rinv, Nr,
+                             idx->codes, nullptr, 0, 0, idx->d_err, s));
     tm.end();
     DL_TRY(check_tc_error(idx->d_err, s));
   } else {
+    // FP32 inputs: on the tensor cores through the TF32 split where the shapes
+    // allow it. The sample is projected by the same kernel as the points, so
+    // the points that define breakpoints fall on them exactly when encoded.
+    const bool tf32 = tf32_eligible(dtype, d, LK);
+    if (tf32) {
+      const int N = (LK + 15) / 16 * 16;
+      DL_CUDA(cudaMalloc(&idx->Atf, sizeof(float) * 2 * N * d));
+      DL_CUDA(cudaMalloc(&idx->d_err, sizeof(int)));
+      DL_CUDA(cudaMemsetAsync(idx->d_err, 0, sizeof(int), s));
+      DL_TRY(split_tf32(idx->A, LK, d, idx->Atf, s));
+    }
     tm.begin(TR_SAMPLE_PROJ);
-    DL_TRY(launch_project_t(idx->X, dtype, prm->n_s, d, static_cast<const int64_t*>(ids.d), idx->At, LK,
-                            idx->Ps, 1, prm->n_s, s));
+    if (tf32) {
+      Scratch xs;
+      DL_TRY(xs.alloc(sizeof(float) * prm->n_s * d, s));
+      DL_TRY(gather_rows_f32(static_cast<const float*>(idx->X), d, static_cast<const int64_t*>(ids.d), prm->n_s,
+                             xs.as<float>(), s));
+      DL_TRY(launch_project_tf32(xs.as<float>(), prm->n_s, d, idx->Atf, LK, K, nullptr, nullptr, nullptr, nullptr,
+                                 Nr, nullptr, idx->Ps, 1, prm->n_s, idx->d_err, s));
+    } else {
+      DL_TRY(launch_project_t(idx->X, dtype, prm->n_s, d, static_cast<const int64_t*>(ids.d), idx->At, LK,
+                              idx->Ps, 1, prm->n_s, s));
+    }
     tm.end();
     tm.begin(TR_BREAKPOINTS);
     DL_TRY(select_breakpoints(idx->Ps, prm->n_s, LK, Nr, idx->E, s));
+    DL_TRY(build_region_tables(idx->E, LK, Nr, idx->Rtab, idx->Rlo, idx->Rinv, s));
     tm.end();
     // Alg. 2: codes of every point, fused with the projection
     tm.begin(TR_ENCODE);
-    DL_TRY(launch_project_encode_t(idx->X, dtype, n, d, idx->At, K, L, idx->E, Nr, idx->codes, s));
+    if (tf32) {
+      DL_TRY(launch_project_tf32(static_cast<const float*>(idx->X), n, d, idx->Atf, LK, K, idx->E, idx->Rtab,
+                                 idx->Rlo, idx->Rinv, Nr, idx->codes, nullptr, 0, 0, idx->d_err, s));
+    } else {
+      DL_TRY(launch_project_encode_t(idx->X, dtype, n, d, idx->At, K, L, idx->E, idx->Rtab, idx->Rlo,
+                                     idx->Rinv, Nr, idx->codes, s));
+    }
     tm.end();
+    if (idx->Atf) DL_TRY(check_tc_error(idx->d_err, s));
   }
   // Alg. 3: leaves
   tm.begin(TR_LEAVES);

@@ -127,12 +127,16 @@ struct detlsh_index {
   int32_t proj_mode = 0;
   void* Xb = nullptr;               // [n][d] BF16 copy of X (BF16 projection mode)
   void* Ab = nullptr;               // [N][d] BF16 hash vectors, N = L*K rounded up to 16
+  float* Atf = nullptr;             // [2][N][d] TF32 split of A (FP32 mode on the tensor cores)
   int* d_err = nullptr;             // error word of the tensor-core kernel
   bool owns_x = true;
   const void* X = nullptr;          // [n][d] f32 or u8
   float* A = nullptr;               // [LK][d]
   float* At = nullptr;              // [d][LK] (transposed A)
   float* E = nullptr;               // [LK][Nr+1]
+  uint8_t* Rtab = nullptr;          // [LK][kRegionRow] region search tables of E
+  float* Rlo = nullptr;             // [LK]
+  float* Rinv = nullptr;            // [LK]
   float* Ps = nullptr;              // [LK][n_s]
   uint8_t* codes = nullptr;         // [L][n][K]
   uint32_t* leaf_ids = nullptr;     // [L][n]
@@ -150,6 +154,35 @@ struct detlsh_index {
 
 namespace detlsh {
 
+// ---- region search tables (Alg. 2 encoding, project.cu)
+// For projected dimension h with interior breakpoints e_1 <= ... <= e_{Nr-1}:
+// lo = e_1, w = (e_{Nr-1} - e_1) / kRegionCells, inv = 1/w (0 when w is 0 or
+// too small against |e| for the cells to be resolved in FP32), and
+// tab[c] = #{z >= 1 : e_z <= lo + (c-1) w} for 1 <= c <= kRegionCells,
+// tab[0] = 0, tab[c] = Nr-1 beyond (and for every c >= 1 when inv = 0).
+// A value p in cell c = clamp(floor((p - lo) * inv), 0, kRegionCells-1) has
+// its code #{z : e_z <= p} in [tab[c], tab[c+3]]: the one-cell margins on both
+// sides absorb the rounding of the cell computation.
+constexpr int kRegionCells = 256;
+constexpr int kRegionRow = kRegionCells + 4;
+
+// code = #{z in 1..Nr-1 : e[z] <= p} for sorted e[1..Nr-1] (e[0] unused),
+// from the table row t of its dimension: a short search inside the cell's range.
+__device__ __forceinline__ int region_fast(const float* e, const uint8_t* t, float lo, float inv, float p) {
+  const float f = (p - lo) * inv;
+  const int c = f > 0.f ? (f < (float)(kRegionCells - 1) ? (int)f : kRegionCells - 1) : 0;
+  int a = t[c], b = t[c + 3];
+  while (a < b) {
+    const int m = (a + b + 1) >> 1;
+    if (e[m] <= p) a = m;
+    else b = m - 1;
+  }
+  return a;
+}
+
+// tab [LK][kRegionRow], lo [LK], inv [LK] from E [LK][Nr+1].
+int build_region_tables(const float* E, int LK, int Nr, uint8_t* tab, float* lo, float* inv, cudaStream_t s);
+
 // ---- projection / encoding (project.cu)
 // At [d][LK] = transpose of A [LK][d].
 int transpose_hashes(const float* A, int LK, int d, float* At, cudaStream_t s);
@@ -157,9 +190,11 @@ int transpose_hashes(const float* A, int LK, int d, float* At, cudaStream_t s);
 int launch_project_t(const void* X, int dtype, int64_t n, int d, const int64_t* rows,
                      const float* At, int LK, float* P, int64_t p_so, int64_t p_sr,
                      cudaStream_t s);
-// Same projection, then Alg. 2 against E [LK][Nr+1]; writes codes [L][n][K].
+// Same projection, then Alg. 2 against E [LK][Nr+1] (with its region tables);
+// writes codes [L][n][K].
 int launch_project_encode_t(const void* X, int dtype, int64_t n, int d, const float* At,
-                            int K, int L, const float* E, int Nr, uint8_t* codes,
+                            int K, int L, const float* E, const uint8_t* Rtab, const float* Rlo,
+                            const float* Rinv, int Nr, uint8_t* codes,
                             cudaStream_t s);
 int launch_encode_values(const float* P, int64_t n, int LK, const float* E, int Nr,
                          uint8_t* codes, cudaStream_t s);
@@ -168,9 +203,17 @@ int launch_encode_values(const float* P, int64_t n, int LK, const float* E, int 
 int to_bf16(const void* X, int dtype, int64_t count, void* Y, cudaStream_t s);
 int gather_rows_bf16(const void* Xb, int d, const int64_t* ids, int64_t m, void* Y, cudaStream_t s);
 int launch_project_tc(const void* Xb, int64_t rows, int d, const void* Ab, int LK, int K,
-                      const float* E, int Nr, uint8_t* codes, float* P, int64_t p_so, int64_t p_sr,
-                      int* d_err, cudaStream_t s);
+                      const float* E, const uint8_t* Rtab, const float* Rlo, const float* Rinv, int Nr,
+                      uint8_t* codes, float* P, int64_t p_so, int64_t p_sr, int* d_err, cudaStream_t s);
 int check_tc_error(int* d_err, cudaStream_t s);
+// FP32 inputs on the tensor cores (TF32 split, FP32-faithful): Asplit holds
+// a_big [N][d] then a_small [N][d] (N = L*K rounded up to 16), from split_tf32.
+bool tf32_eligible(int dtype, int d, int LK);
+int split_tf32(const float* A, int LK, int d, float* Asplit, cudaStream_t s);
+int gather_rows_f32(const float* X, int d, const int64_t* ids, int64_t m, float* Y, cudaStream_t s);
+int launch_project_tf32(const float* X, int64_t rows, int d, const float* Asplit, int LK, int K, const float* E,
+                        const uint8_t* Rtab, const float* Rlo, const float* Rinv, int Nr, uint8_t* codes,
+                        float* P, int64_t p_so, int64_t p_sr, int* d_err, cudaStream_t s);
 
 // ---- sorting / scans (sort.cu)
 // Stable LSD radix sort of (key, value) pairs on key bits [bit_lo, bit_hi).

@@ -6,9 +6,10 @@
 // d-chunk of it is one coalesced block, staged in shared memory and read by
 // every thread as broadcast float4 loads; the points' d-chunks are staged
 // row-wise with a 4-float pad so the per-thread float4 reads are free of bank
-// conflicts. With ENCODE the breakpoints of the tile's hashes sit in shared
-// memory and each projection is turned into its region code right away, so
-// the projections never reach HBM.
+// conflicts. With ENCODE the region search tables of the tile's hashes sit in
+// shared memory (the one or two breakpoints a search then reads come through
+// L1) and each projection is turned into its region code right away, so the
+// projections never reach HBM.
 #include "common.cuh"
 
 namespace detlsh {
@@ -77,21 +78,29 @@ template <typename TX, bool ENCODE>
 __global__ void __launch_bounds__(PT)
 k_project(const TX* __restrict__ X, int64_t n, int d, const int64_t* __restrict__ rows,
           const float* __restrict__ At, int LK, float* __restrict__ P, int64_t p_so,
-          int64_t p_sr, const float* __restrict__ E, int Nr, int K,
+          int64_t p_sr, const float* __restrict__ E, const uint8_t* __restrict__ Rtab,
+          const float* __restrict__ Rlo, const float* __restrict__ Rinv, int Nr, int K,
           uint8_t* __restrict__ codes, bool vec4) {
   extern __shared__ __align__(16) float smem[];
   float* As = smem;               // [DC][HT]
   float* Xs = As + DC * HT;       // [PT][XS]
-  float* Es = Xs + PT * XS;       // [HT][Nr] (ENCODE), e_z at [h][z]
+  float* Slo = Xs + PT * XS;      // [HT] (ENCODE)
+  float* Sinv = Slo + HT;         // [HT]
+  uint8_t* Ts = reinterpret_cast<uint8_t*>(Sinv + HT);   // [HT][kRegionRow]
   const int tid = threadIdx.x;
   const int64_t p0 = (int64_t)blockIdx.x * PT;
   const int r0 = blockIdx.y * HT;
   const int nh = min(HT, LK - r0);
 
   if (ENCODE) {
-    for (int i = tid; i < HT * Nr; i += PT) {
-      const int h = i / Nr, z = i % Nr;
-      Es[i] = (h < nh && z > 0) ? E[(int64_t)(r0 + h) * (Nr + 1) + z] : 0.f;
+    for (int i = tid; i < HT * kRegionRow / 4; i += PT) {
+      const int h = (4 * i) / kRegionRow;
+      reinterpret_cast<uint32_t*>(Ts)[i] =
+          h < nh ? reinterpret_cast<const uint32_t*>(Rtab + (int64_t)r0 * kRegionRow)[i] : 0u;
+    }
+    for (int h = tid; h < HT; h += PT) {
+      Slo[h] = h < nh ? Rlo[r0 + h] : 0.f;
+      Sinv[h] = h < nh ? Rinv[r0 + h] : 0.f;
     }
   }
 
@@ -147,7 +156,8 @@ k_project(const TX* __restrict__ X, int64_t n, int d, const int64_t* __restrict_
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           const int h = g * 16 + q * 4 + b;
-          v |= (uint32_t)region_of(Es + h * Nr, Nr, acc[h]) << (8 * b);
+          v |= (uint32_t)region_fast(E + (int64_t)(r0 + h) * (Nr + 1), Ts + h * kRegionRow, Slo[h], Sinv[h],
+                                     acc[h]) << (8 * b);
         }
         w[q] = v;
       }
@@ -160,7 +170,8 @@ k_project(const TX* __restrict__ X, int64_t n, int d, const int64_t* __restrict_
     for (int h = 0; h < HT; ++h) {
       if (h < nh) {
         const int r = r0 + h, tree = r / K, j = r % K;
-        codes[((int64_t)tree * n + p) * K + j] = (uint8_t)region_of(Es + h * Nr, Nr, acc[h]);
+        codes[((int64_t)tree * n + p) * K + j] =
+            (uint8_t)region_fast(E + (int64_t)(r0 + h) * (Nr + 1), Ts + h * kRegionRow, Slo[h], Sinv[h], acc[h]);
       }
     }
   }
@@ -185,13 +196,14 @@ __global__ void k_encode_values(const float* __restrict__ P, int64_t n, int LK,
 }
 
 size_t project_smem(bool encode, int Nr) {
-  return sizeof(float) * ((size_t)DC * HT + (size_t)PT * XS + (encode ? (size_t)HT * Nr : 0));
+  return sizeof(float) * ((size_t)DC * HT + (size_t)PT * XS + (encode ? 2 * (size_t)HT : 0)) +
+         (encode ? (size_t)HT * kRegionRow : 0);
 }
 
 template <typename TX, bool ENCODE>
 int launch(const void* X, int64_t n, int d, const int64_t* rows, const float* At, int LK,
-           float* P, int64_t p_so, int64_t p_sr, const float* E, int Nr, int K,
-           uint8_t* codes, cudaStream_t s) {
+           float* P, int64_t p_so, int64_t p_sr, const float* E, const uint8_t* Rtab, const float* Rlo,
+           const float* Rinv, int Nr, int K, uint8_t* codes, cudaStream_t s) {
   if (n == 0) return DETLSH_OK;
   const size_t sm = project_smem(ENCODE, Nr);
   auto kern = k_project<TX, ENCODE>;
@@ -199,8 +211,8 @@ int launch(const void* X, int64_t n, int d, const int64_t* rows, const float* At
   const bool vec4 = (d % 4 == 0) &&
                     (reinterpret_cast<uintptr_t>(X) % (sizeof(TX) == 4 ? 16 : 4) == 0);
   dim3 grid(ceil_div(n, PT), ceil_div(LK, HT));
-  kern<<<grid, PT, sm, s>>>(static_cast<const TX*>(X), n, d, rows, At, LK, P, p_so, p_sr, E,
-                            Nr, K, codes, vec4);
+  kern<<<grid, PT, sm, s>>>(static_cast<const TX*>(X), n, d, rows, At, LK, P, p_so, p_sr, E, Rtab, Rlo,
+                            Rinv, Nr, K, codes, vec4);
   DL_LAUNCH();
   return DETLSH_OK;
 }
@@ -218,17 +230,63 @@ int launch_project_t(const void* X, int dtype, int64_t n, int d, const int64_t* 
                      const float* At, int LK, float* P, int64_t p_so, int64_t p_sr,
                      cudaStream_t s) {
   if (dtype == DETLSH_U8)
-    return launch<uint8_t, false>(X, n, d, rows, At, LK, P, p_so, p_sr, nullptr, 2, 1,
-                                  nullptr, s);
-  return launch<float, false>(X, n, d, rows, At, LK, P, p_so, p_sr, nullptr, 2, 1, nullptr, s);
+    return launch<uint8_t, false>(X, n, d, rows, At, LK, P, p_so, p_sr, nullptr, nullptr, nullptr, nullptr, 2,
+                                  1, nullptr, s);
+  return launch<float, false>(X, n, d, rows, At, LK, P, p_so, p_sr, nullptr, nullptr, nullptr, nullptr, 2, 1,
+                              nullptr, s);
 }
 
 int launch_project_encode_t(const void* X, int dtype, int64_t n, int d, const float* At,
-                            int K, int L, const float* E, int Nr, uint8_t* codes,
-                            cudaStream_t s) {
+                            int K, int L, const float* E, const uint8_t* Rtab, const float* Rlo,
+                            const float* Rinv, int Nr, uint8_t* codes, cudaStream_t s) {
   if (dtype == DETLSH_U8)
-    return launch<uint8_t, true>(X, n, d, nullptr, At, K * L, nullptr, 0, 0, E, Nr, K, codes, s);
-  return launch<float, true>(X, n, d, nullptr, At, K * L, nullptr, 0, 0, E, Nr, K, codes, s);
+    return launch<uint8_t, true>(X, n, d, nullptr, At, K * L, nullptr, 0, 0, E, Rtab, Rlo, Rinv, Nr, K, codes,
+                                 s);
+  return launch<float, true>(X, n, d, nullptr, At, K * L, nullptr, 0, 0, E, Rtab, Rlo, Rinv, Nr, K, codes, s);
+}
+
+// ---- region search tables
+namespace {
+
+// #{z in 1..Nr-1 : e[z] <= x} for sorted e
+__device__ int count_le(const float* e, int Nr, float x) {
+  int a = 0, b = Nr - 1;
+  while (a < b) {
+    const int m = (a + b + 1) >> 1;
+    if (e[m] <= x) a = m;
+    else b = m - 1;
+  }
+  return a;
+}
+
+__global__ void k_region_tables(const float* __restrict__ E, int Nr, uint8_t* __restrict__ tab,
+                                float* __restrict__ lo_out, float* __restrict__ inv_out) {
+  const int h = blockIdx.x;
+  const float* e = E + (int64_t)h * (Nr + 1);
+  const float lo = e[1], hi = e[Nr - 1];
+  const float w = (hi - lo) / (float)kRegionCells;
+  const float mag = fmaxf(fabsf(lo), fabsf(hi));
+  // cells narrower than 2^-16 of the magnitude are not resolved reliably in FP32
+  const bool fine = w > 0.f && isfinite(w) && w > mag * 1.52587890625e-05f;
+  for (int c = threadIdx.x; c < kRegionRow; c += blockDim.x) {
+    int v;
+    if (c == 0) v = 0;
+    else if (!fine || c > kRegionCells) v = Nr - 1;
+    else v = count_le(e, Nr, lo + (float)(c - 1) * w);
+    tab[(int64_t)h * kRegionRow + c] = (uint8_t)v;
+  }
+  if (threadIdx.x == 0) {
+    lo_out[h] = lo;
+    inv_out[h] = fine ? (float)kRegionCells / (hi - lo) : 0.f;
+  }
+}
+
+}  // namespace
+
+int build_region_tables(const float* E, int LK, int Nr, uint8_t* tab, float* lo, float* inv, cudaStream_t s) {
+  k_region_tables<<<LK, 256, 0, s>>>(E, Nr, tab, lo, inv);
+  DL_LAUNCH();
+  return DETLSH_OK;
 }
 
 int launch_encode_values(const float* P, int64_t n, int LK, const float* E, int Nr,

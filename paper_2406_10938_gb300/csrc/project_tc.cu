@@ -28,7 +28,8 @@ namespace {
 constexpr int TC_M = 128;          // rows (points) per tile
 constexpr int TC_KC = 64;          // d elements per stage (128 bytes of BF16)
 constexpr int TC_STAGES = 4;
-constexpr int TC_THREADS = 256;
+constexpr int TC_EPI_WARPS = 16;     // 4 per TMEM lane quadrant, 16 accumulator columns each
+constexpr int TC_THREADS = 128 + 32 * TC_EPI_WARPS;
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;   // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -104,9 +105,27 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
@@ -135,50 +154,76 @@ struct TcArgs {
   int64_t rows;
   int d, LK, K, Nr;
   const float* E;        // [LK][Nr+1] (encode mode)
+  const uint8_t* Rtab;   // [LK][kRegionRow] region search tables (encode mode)
+  const float* Rlo;      // [LK]
+  const float* Rinv;     // [LK]
   uint8_t* codes;        // [L][rows][K] (encode mode)
   float* P;              // projections (store mode)
   int64_t p_so, p_sr;
   int* err;
 };
 
-template <int N, bool ENCODE>
+// Shared memory bytes of k_project_tc below the region tables.
+template <int N, bool TF32>
+constexpr size_t tc_tile_bytes() {
+  return (size_t)TC_STAGES * (TC_M * 128 + N * 128) * (TF32 ? 2 : 1) + (3 * TC_STAGES + 8) * 8;
+}
+
+// TF32 mode: X is FP32 and each stage also holds x_small = x - x_big, where
+// x_big keeps the top 10 mantissa bits (what a TF32 operand holds exactly);
+// D = (x_big + x_small)(a_big + a_small) in four MMAs per K step, a_big /
+// a_small the same split of A. x_small and a_small are held to 11 of their
+// at most 13 significant bits, so each product is within about 2^-21 of
+// |a x|; the tensor cores' FP32 accumulation adds its own rounding, which is
+// why this path is used for d <= 256 only. Values with at most 11
+// significant bits (the exact-arithmetic inputs) have x_small = 0 and give
+// exact sums.
+template <int N, bool ENCODE, bool TF32>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA,
-             TcArgs a) {
+             const __grid_constant__ CUtensorMap tmA2, TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned base for the swizzled tiles
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
   constexpr uint32_t XBYTES = TC_M * 128;
   constexpr uint32_t ABYTES = N * 128;
+  constexpr int KC = TF32 ? 32 : 64;                  // d elements per stage (128-byte rows)
   uint8_t* sx = base;                                  // [STAGES][XBYTES]
   uint8_t* sa = sx + TC_STAGES * XBYTES;               // [STAGES][ABYTES]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sa + TC_STAGES * ABYTES);
-  // full[0..S), empty[S..2S), tfull[2S..2S+2), tempty[2S+2..2S+4)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 4);
-  float* Es = reinterpret_cast<float*>(bars + 2 * TC_STAGES + 8);   // [LK][Nr] (ENCODE)
+  uint8_t* sxs = sa + TC_STAGES * ABYTES;              // [STAGES][XBYTES] x_small (TF32)
+  uint8_t* sas = sxs + (TF32 ? TC_STAGES * XBYTES : 0);   // [STAGES][ABYTES] a_small (TF32)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sas + (TF32 ? TC_STAGES * ABYTES : 0));
+  // full[0..S), empty[S..2S), tfull[2S..2S+2), tempty[2S+2..2S+4), split[2S+4..3S+4)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * TC_STAGES + 4);
+  float* Slo = reinterpret_cast<float*>(bars + 3 * TC_STAGES + 8);   // [LK] (ENCODE)
+  float* Sinv = Slo + a.LK;                                          // [LK]
+  uint8_t* Ts = reinterpret_cast<uint8_t*>(Sinv + a.LK);             // [LK][kRegionRow]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = (a.rows + TC_M - 1) / TC_M;
-  const int nk = (a.d + TC_KC - 1) / TC_KC;
+  const int nk = (a.d + KC - 1) / KC;
   int* err = a.err;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(smem_u32(&bars[s]), 1);
       mbar_init(smem_u32(&bars[TC_STAGES + s]), 1);
+      mbar_init(smem_u32(&bars[2 * TC_STAGES + 4 + s]), 2);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&bars[2 * TC_STAGES + b]), 1);
-      mbar_init(smem_u32(&bars[2 * TC_STAGES + 2 + b]), 4);
+      mbar_init(smem_u32(&bars[2 * TC_STAGES + 2 + b]), TC_EPI_WARPS);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (ENCODE) {
-    for (int i = threadIdx.x; i < a.LK * a.Nr; i += TC_THREADS) {
-      const int h = i / a.Nr, z = i % a.Nr;
-      Es[i] = z > 0 ? a.E[(int64_t)h * (a.Nr + 1) + z] : 0.f;
+    for (int i = threadIdx.x; i < a.LK * kRegionRow / 4; i += TC_THREADS)
+      reinterpret_cast<uint32_t*>(Ts)[i] = reinterpret_cast<const uint32_t*>(a.Rtab)[i];
+    for (int h = threadIdx.x; h < a.LK; h += TC_THREADS) {
+      Slo[h] = a.Rlo[h];
+      Sinv[h] = a.Rinv[h];
     }
   }
   constexpr uint32_t TCOLS = (2 * N <= 32) ? 32 : (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : 256;
@@ -203,16 +248,46 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
         ok = mbar_wait(smem_u32(&bars[TC_STAGES + s]), (r & 1) ^ 1, err);
         if (!ok) break;
         const uint32_t full = smem_u32(&bars[s]);
-        mbar_expect_tx(full, XBYTES + ABYTES);
-        tma_load_2d(smem_u32(sx + s * XBYTES), &tmX, kc * TC_KC, (int)(tile * TC_M), full);
-        tma_load_2d(smem_u32(sa + s * ABYTES), &tmA, kc * TC_KC, 0, full);
+        mbar_expect_tx(full, XBYTES + (TF32 ? 2 : 1) * ABYTES);
+        tma_load_2d(smem_u32(sx + s * XBYTES), &tmX, kc * KC, (int)(tile * TC_M), full);
+        tma_load_2d(smem_u32(sa + s * ABYTES), &tmA, kc * KC, 0, full);
+        if (TF32) tma_load_2d(smem_u32(sas + s * ABYTES), &tmA2, kc * KC, 0, full);
+      }
+    }
+  } else if (TF32 && (warp == 2 || warp == 3)) {
+    // ---- split of each staged X tile into x_big (in place) and x_small
+    const int t = threadIdx.x - 64;   // 0..63
+    uint32_t it = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (int kc = 0; kc < nk && ok; ++kc, ++it) {
+        const uint32_t s = it % TC_STAGES, r = it / TC_STAGES;
+        ok = mbar_wait(smem_u32(&bars[s]), r & 1, err);
+        if (!ok) break;
+        float4* xv = reinterpret_cast<float4*>(sx + s * XBYTES);
+        float4* xs = reinterpret_cast<float4*>(sxs + s * XBYTES);
+#pragma unroll 4
+        for (int i = t; i < (int)(XBYTES / 16); i += 64) {
+          const float4 x = xv[i];
+          const float4 b = make_float4(__uint_as_float(__float_as_uint(x.x) & 0xffffe000u),
+                                       __uint_as_float(__float_as_uint(x.y) & 0xffffe000u),
+                                       __uint_as_float(__float_as_uint(x.z) & 0xffffe000u),
+                                       __uint_as_float(__float_as_uint(x.w) & 0xffffe000u));
+          xv[i] = b;
+          xs[i] = make_float4(x.x - b.x, x.y - b.y, x.z - b.z, x.w - b.w);
+        }
+        // generic-proxy writes become visible to the tensor cores' reads
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars[2 * TC_STAGES + 4 + s]));
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
+    constexpr uint32_t ab_fmt = TF32 ? 2u : 1u;   // operand format: BF16 (kind::f16) or TF32
     constexpr uint32_t idesc = (1u << 4)            // D: FP32
-                               | (1u << 7)          // A: BF16
-                               | (1u << 10)         // B: BF16
+                               | (ab_fmt << 7)      // A
+                               | (ab_fmt << 10)     // B
                                | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
     uint32_t it = 0, lt = 0;
     bool ok = true;
@@ -224,71 +299,81 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
       const uint32_t dt = tmem + ab * (TCOLS / 2);
       for (int kc = 0; kc < nk; ++kc, ++it) {
         const uint32_t s = it % TC_STAGES, r = it / TC_STAGES;
-        ok = mbar_wait(smem_u32(&bars[s]), r & 1, err);
+        ok = mbar_wait(smem_u32(&bars[TF32 ? 2 * TC_STAGES + 4 + s : s]), r & 1, err);
         if (!ok) break;
         tc_fence_after();
         const uint64_t ad = smem_desc(smem_u32(sx + s * XBYTES));
         const uint64_t bd = smem_desc(smem_u32(sa + s * ABYTES));
+        if (TF32) {
+          const uint64_t asd = smem_desc(smem_u32(sxs + s * XBYTES));
+          const uint64_t bsd = smem_desc(smem_u32(sas + s * ABYTES));
 #pragma unroll
-        for (int k = 0; k < TC_KC / 16; ++k)   // 16 BF16 = 32 bytes = 2 in descriptor units
-          mma_bf16(dt, ad + 2 * k, bd + 2 * k, idesc, (kc > 0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < 4; ++k) {   // 8 TF32 = 32 bytes = 2 in descriptor units
+            mma_tf32(dt, ad + 2 * k, bd + 2 * k, idesc, (kc > 0 || k > 0) ? 1u : 0u);
+            mma_tf32(dt, ad + 2 * k, bsd + 2 * k, idesc, 1u);
+            mma_tf32(dt, asd + 2 * k, bd + 2 * k, idesc, 1u);
+            mma_tf32(dt, asd + 2 * k, bsd + 2 * k, idesc, 1u);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < KC / 16; ++k)   // 16 BF16 = 32 bytes = 2 in descriptor units
+            mma_bf16(dt, ad + 2 * k, bd + 2 * k, idesc, (kc > 0 || k > 0) ? 1u : 0u);
+        }
         mma_commit(smem_u32(&bars[TC_STAGES + s]));
       }
       if (!ok) break;
       mma_commit(smem_u32(&bars[2 * TC_STAGES + ab]));
     }
   } else if (warp >= 4) {
-    // ---- epilogue: one accumulator row (point) per thread
-    const int q = warp & 3;
+    // ---- epilogue: warp w reads TMEM lanes 32*(w%4).. (its quadrant's 32
+    // points) and accumulator columns [16g, 16g+16), g = (w-4)/4; one point
+    // and 16 projections (one DE-Tree when K = 16) per thread
+    const int q = warp & 3, g = (warp - 4) >> 2;
     const int row = q * 32 + lane;
+    const bool active = g * 16 < N;
     uint32_t lt = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
       const uint32_t ab = lt & 1, use = lt >> 1;
       if (!mbar_wait(smem_u32(&bars[2 * TC_STAGES + ab]), use & 1, err)) break;
       tc_fence_after();
-      float v[(N + 31) / 32 * 32];
-#pragma unroll
-      for (int c = 0; c < N; c += 32)
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + ab * (TCOLS / 2) + c, v + c);
+      float v[16];
+      if (active) tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + ab * (TCOLS / 2) + g * 16, v);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bars[2 * TC_STAGES + 2 + ab]));
       const int64_t p = tile * TC_M + row;
-      if (p < a.rows) {
-        if (ENCODE) {
-          if (a.K == 16) {
+      if (!active || p >= a.rows) continue;
+      if (ENCODE) {
+        if (a.K == 16 && g * 16 + 16 <= a.LK) {
+          uint32_t wv[4];
 #pragma unroll
-            for (int g = 0; g < N / 16; ++g) {
-              if (g * 16 < a.LK) {
-                uint32_t wv[4];
+          for (int qq = 0; qq < 4; ++qq) {
+            uint32_t x = 0;
 #pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                  uint32_t x = 0;
-#pragma unroll
-                  for (int b = 0; b < 4; ++b) {
-                    const int h = g * 16 + qq * 4 + b;
-                    x |= (uint32_t)region_of_tc(Es + h * a.Nr, a.Nr, v[h]) << (8 * b);
-                  }
-                  wv[qq] = x;
-                }
-                *reinterpret_cast<uint4*>(a.codes + ((int64_t)g * a.rows + p) * 16) =
-                    make_uint4(wv[0], wv[1], wv[2], wv[3]);
-              }
+            for (int b = 0; b < 4; ++b) {
+              const int c = qq * 4 + b, h = g * 16 + c;
+              x |= (uint32_t)region_fast(a.E + (int64_t)h * (a.Nr + 1), Ts + h * kRegionRow, Slo[h], Sinv[h],
+                                         v[c]) << (8 * b);
             }
-          } else {
-#pragma unroll
-            for (int h = 0; h < N; ++h) {
-              if (h < a.LK) {
-                const int tree = h / a.K, j = h % a.K;
-                a.codes[((int64_t)tree * a.rows + p) * a.K + j] =
-                    (uint8_t)region_of_tc(Es + h * a.Nr, a.Nr, v[h]);
-              }
-            }
+            wv[qq] = x;
           }
+          *reinterpret_cast<uint4*>(a.codes + ((int64_t)g * a.rows + p) * 16) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         } else {
 #pragma unroll
-          for (int h = 0; h < N; ++h)
-            if (h < a.LK) a.P[p * a.p_so + (int64_t)h * a.p_sr] = v[h];
+          for (int c = 0; c < 16; ++c) {
+            const int h = g * 16 + c;
+            if (h < a.LK) {
+              const int tree = h / a.K, j = h % a.K;
+              a.codes[((int64_t)tree * a.rows + p) * a.K + j] =
+                  (uint8_t)region_fast(a.E + (int64_t)h * (a.Nr + 1), Ts + h * kRegionRow, Slo[h], Sinv[h], v[c]);
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int h = g * 16 + c;
+          if (h < a.LK) a.P[p * a.p_so + (int64_t)h * a.p_sr] = v[c];
         }
       }
     }
@@ -333,17 +418,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-int make_map(CUtensorMap* tm, const void* ptr, int64_t rows, int d, int box_rows) {
+// 2-D map of a row-major [rows][d] matrix of BF16 (or FP32), boxes of
+// box_rows rows by 128 bytes, 128-byte swizzle
+int make_map(CUtensorMap* tm, const void* ptr, int64_t rows, int d, int box_rows, bool fp32 = false) {
   auto fn = encode_fn();
   if (!fn) {
     set_error("cuTensorMapEncodeTiled is unavailable");
     return DETLSH_ECUDA;
   }
+  const int esz = fp32 ? 4 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)d * 2};
-  cuuint32_t box[2] = {(cuuint32_t)TC_KC, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)d * esz};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
-  const CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box,
+  const CUresult r = fn(tm, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                        const_cast<void*>(ptr), dims, strides, box,
                         es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -353,18 +442,19 @@ int make_map(CUtensorMap* tm, const void* ptr, int64_t rows, int d, int box_rows
   return DETLSH_OK;
 }
 
-template <int N, bool ENCODE>
-int launch_tc(const CUtensorMap& tx, const CUtensorMap& ta, const TcArgs& args, cudaStream_t s) {
-  size_t smem = 1024 + TC_STAGES * (TC_M * 128 + N * 128) + (2 * TC_STAGES + 8) * 8;
-  if (ENCODE) smem += sizeof(float) * (size_t)args.LK * args.Nr;
-  auto kern = k_project_tc<N, ENCODE>;
+template <int N, bool ENCODE, bool TF32>
+int launch_tc(const CUtensorMap& tx, const CUtensorMap& ta, const CUtensorMap& ta2, const TcArgs& args,
+              cudaStream_t s) {
+  size_t smem = 1024 + tc_tile_bytes<N, TF32>();
+  if (ENCODE) smem += sizeof(float) * 2 * (size_t)args.LK + (size_t)args.LK * kRegionRow;
+  auto kern = k_project_tc<N, ENCODE, TF32>;
   DL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, nsm = 0;
   DL_CUDA(cudaGetDevice(&dev));
   DL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int64_t ntiles = (args.rows + TC_M - 1) / TC_M;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, nsm));
-  kern<<<grid, TC_THREADS, smem, s>>>(tx, ta, args);
+  kern<<<grid, TC_THREADS, smem, s>>>(tx, ta, ta2, args);
   DL_LAUNCH();
   return DETLSH_OK;
 }
@@ -406,8 +496,8 @@ int check_tc_error(int* d_err, cudaStream_t s) {
 
 // P = Xb * Abᵀ on the tensor cores; with E/codes: encoded, else FP32 into P.
 int launch_project_tc(const void* Xb, int64_t rows, int d, const void* Ab, int LK, int K,
-                      const float* E, int Nr, uint8_t* codes, float* P, int64_t p_so, int64_t p_sr,
-                      int* d_err, cudaStream_t s) {
+                      const float* E, const uint8_t* Rtab, const float* Rlo, const float* Rinv, int Nr,
+                      uint8_t* codes, float* P, int64_t p_so, int64_t p_sr, int* d_err, cudaStream_t s) {
   if (rows == 0) return DETLSH_OK;
   const int N = (LK + 15) / 16 * 16;
   if (N > 64 || d % 8 != 0) {
@@ -424,6 +514,9 @@ int launch_project_tc(const void* Xb, int64_t rows, int d, const void* Ab, int L
   args.K = K;
   args.Nr = Nr;
   args.E = E;
+  args.Rtab = Rtab;
+  args.Rlo = Rlo;
+  args.Rinv = Rinv;
   args.codes = codes;
   args.P = P;
   args.p_so = p_so;
@@ -432,7 +525,95 @@ int launch_project_tc(const void* Xb, int64_t rows, int d, const void* Ab, int L
   const bool enc = codes != nullptr;
 #define DL_TC_CASE(NN)                                                        \
   case NN:                                                                    \
-    return enc ? launch_tc<NN, true>(tx, ta, args, s) : launch_tc<NN, false>(tx, ta, args, s);
+    return enc ? launch_tc<NN, true, false>(tx, ta, ta, args, s) : launch_tc<NN, false, false>(tx, ta, ta, args, s);
+  switch (N) {
+    DL_TC_CASE(16)
+    DL_TC_CASE(32)
+    DL_TC_CASE(48)
+    DL_TC_CASE(64)
+    default:
+      break;
+  }
+#undef DL_TC_CASE
+  set_error("unsupported projection width %d", N);
+  return DETLSH_EINVAL;
+}
+
+namespace {
+__global__ void k_split_tf32(const float* __restrict__ A, int LK, int N, int d, float* __restrict__ big,
+                             float* __restrict__ small) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)N * d) return;
+  const int r = (int)(i / d);
+  const float x = r < LK ? A[i] : 0.f;
+  const float b = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+  big[i] = b;
+  small[i] = x - b;
+}
+}  // namespace
+
+namespace {
+__global__ void k_gather_rows_f32(const float* __restrict__ x, int d, const int64_t* __restrict__ ids, int64_t m,
+                                  float* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m * d;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / d, c = i % d;
+    y[i] = x[ids[r] * d + c];
+  }
+}
+}  // namespace
+
+int gather_rows_f32(const float* X, int d, const int64_t* ids, int64_t m, float* Y, cudaStream_t s) {
+  if (m == 0) return DETLSH_OK;
+  const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(m * d, 256), 152 * 32);
+  k_gather_rows_f32<<<blocks, 256, 0, s>>>(X, d, ids, m, Y);
+  DL_LAUNCH();
+  return DETLSH_OK;
+}
+
+int split_tf32(const float* A, int LK, int d, float* Asplit, cudaStream_t s) {
+  const int N = (LK + 15) / 16 * 16;
+  k_split_tf32<<<ceil_div((int64_t)N * d, 256), 256, 0, s>>>(A, LK, N, d, Asplit, Asplit + (int64_t)N * d);
+  DL_LAUNCH();
+  return DETLSH_OK;
+}
+
+bool tf32_eligible(int dtype, int d, int LK) {
+  return dtype == DETLSH_F32 && d % 4 == 0 && d <= 256 && LK <= 64;
+}
+
+int launch_project_tf32(const float* X, int64_t rows, int d, const float* Asplit, int LK, int K, const float* E,
+                        const uint8_t* Rtab, const float* Rlo, const float* Rinv, int Nr, uint8_t* codes,
+                        float* P, int64_t p_so, int64_t p_sr, int* d_err, cudaStream_t s) {
+  if (rows == 0) return DETLSH_OK;
+  const int N = (LK + 15) / 16 * 16;
+  if (!tf32_eligible(DETLSH_F32, d, LK)) {
+    set_error("the TF32 tensor-core projection needs L*K <= 64 and d <= 256 a multiple of 4");
+    return DETLSH_EINVAL;
+  }
+  CUtensorMap tx, ta, ta2;
+  DL_TRY(make_map(&tx, X, rows, d, TC_M, true));
+  DL_TRY(make_map(&ta, Asplit, N, d, N, true));
+  DL_TRY(make_map(&ta2, Asplit + (int64_t)N * d, N, d, N, true));
+  TcArgs args{};
+  args.rows = rows;
+  args.d = d;
+  args.LK = LK;
+  args.K = K;
+  args.Nr = Nr;
+  args.E = E;
+  args.Rtab = Rtab;
+  args.Rlo = Rlo;
+  args.Rinv = Rinv;
+  args.codes = codes;
+  args.P = P;
+  args.p_so = p_so;
+  args.p_sr = p_sr;
+  args.err = d_err;
+  const bool enc = codes != nullptr;
+#define DL_TC_CASE(NN)                                                        \
+  case NN:                                                                    \
+    return enc ? launch_tc<NN, true, true>(tx, ta, ta2, args, s) : launch_tc<NN, false, true>(tx, ta, ta2, args, s);
   switch (N) {
     DL_TC_CASE(16)
     DL_TC_CASE(32)

@@ -1625,7 +1625,8 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   if (idx->proj_mode == DETLSH_PROJ_BF16) {
     void* qb16 = b + sh.o_qb16;
     DL_TRY(to_bf16(Qb, idx->dtype, nqg * idx->d, qb16, s));
-    DL_TRY(launch_project_tc(qb16, nqg, idx->d, idx->Ab, LK, idx->K, nullptr, idx->Nr, nullptr, qp, LK,
+    DL_TRY(launch_project_tc(qb16, nqg, idx->d, idx->Ab, LK, idx->K, nullptr, nullptr, nullptr, nullptr, idx->Nr,
+                             nullptr, qp, LK,
                              1, idx->d_err, s));
   } else {
     DL_TRY(launch_project_t(Qb, idx->dtype, nqg, idx->d, nullptr, idx->At, LK, qp, LK, 1, s));

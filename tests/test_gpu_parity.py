@@ -123,6 +123,32 @@ def test_build_exact_bit_parity(case):
     idx.free()
 
 
+@pytest.mark.parametrize("kind", ["few_values", "narrow_offset"])
+def test_build_degenerate_breakpoints_bit_parity(kind):
+    """Breakpoints with many equal values (few distinct points) and breakpoints
+    packed into a range narrow against their magnitude: the region search of
+    the encoding must still give the oracle's codes (exact inputs)."""
+    n, d, K, L, Nr, n_s, max_leaf = 2_000, 8, 4, 2, 16, 400, 16
+    g = torch.Generator().manual_seed(11)
+    if kind == "few_values":
+        X = torch.randint(0, 2, (n, d), generator=g).to(torch.float32)
+    else:
+        X = 256.0 + torch.randint(0, 4, (n, d), generator=g).to(torch.float32) / 4.0
+    A = gaussian_projection(L, K, d, exact=True)
+    ids = sample_ids(n, n_s)
+    idx = gpu_build(X, A, ids, K, L, Nr, max_leaf)
+    ref = O.build_index(X.numpy(), A.numpy(), ids.numpy(), K, L, Nr, max_leaf)
+    E = pkg.detlsh_export(idx, "EDGES").numpy().reshape(L * K, Nr + 1).astype(np.float64)
+    assert np.array_equal(E, ref.E)
+    assert np.array_equal(gpu_codes(idx, n, K, L), ref.codes)
+    assert_trees_equal(gpu_trees(idx, K, L, n), ref.trees)
+    idx.free()
+    if kind == "few_values":   # values BF16 holds exactly: the tensor-core path too
+        idx = pkg.detlsh_build(X.to(DEV), A.to(DEV), ids.to(DEV), K, L, Nr, max_leaf, proj_mode=1)
+        assert np.array_equal(gpu_codes(idx, n, K, L), ref.codes)
+        idx.free()
+
+
 # ------------------------------------------------------------------ build, float inputs
 @pytest.mark.parametrize("name,n,d,Nr,n_s", [("tiny", 10_000, 32, 16, 1_000),
                                              ("precision", 4_000, 960, 256, 400),
