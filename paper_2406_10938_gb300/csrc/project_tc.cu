@@ -163,10 +163,15 @@ struct TcArgs {
   int* err;
 };
 
-// Shared memory bytes of k_project_tc below the region tables.
+// Pipeline stages: a TF32 stage holds twice the tiles of a BF16 one.
+template <bool TF32>
+__host__ __device__ constexpr int tc_stages() {
+  return TF32 ? 3 : TC_STAGES;
+}
+// Shared memory bytes of k_project_tc below the breakpoints and tables.
 template <int N, bool TF32>
-constexpr size_t tc_tile_bytes() {
-  return (size_t)TC_STAGES * (TC_M * 128 + N * 128) * (TF32 ? 2 : 1) + (3 * TC_STAGES + 8) * 8;
+__host__ __device__ constexpr size_t tc_tile_bytes() {
+  return (size_t)tc_stages<TF32>() * (TC_M * 128 + N * 128) * (TF32 ? 2 : 1) + (3 * tc_stages<TF32>() + 8) * 8;
 }
 
 // TF32 mode: X is FP32 and each stage also holds x_small = x - x_big, where
@@ -182,6 +187,7 @@ template <int N, bool ENCODE, bool TF32>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA,
              const __grid_constant__ CUtensorMap tmA2, TcArgs a) {
+  constexpr int S = tc_stages<TF32>();
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned base for the swizzled tiles
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -190,13 +196,14 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
   constexpr uint32_t ABYTES = N * 128;
   constexpr int KC = TF32 ? 32 : 64;                  // d elements per stage (128-byte rows)
   uint8_t* sx = base;                                  // [STAGES][XBYTES]
-  uint8_t* sa = sx + TC_STAGES * XBYTES;               // [STAGES][ABYTES]
-  uint8_t* sxs = sa + TC_STAGES * ABYTES;              // [STAGES][XBYTES] x_small (TF32)
-  uint8_t* sas = sxs + (TF32 ? TC_STAGES * XBYTES : 0);   // [STAGES][ABYTES] a_small (TF32)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sas + (TF32 ? TC_STAGES * ABYTES : 0));
+  uint8_t* sa = sx + S * XBYTES;               // [STAGES][ABYTES]
+  uint8_t* sxs = sa + S * ABYTES;              // [STAGES][XBYTES] x_small (TF32)
+  uint8_t* sas = sxs + (TF32 ? S * XBYTES : 0);   // [STAGES][ABYTES] a_small (TF32)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sas + (TF32 ? S * ABYTES : 0));
   // full[0..S), empty[S..2S), tfull[2S..2S+2), tempty[2S+2..2S+4), split[2S+4..3S+4)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * TC_STAGES + 4);
-  float* Slo = reinterpret_cast<float*>(bars + 3 * TC_STAGES + 8);   // [LK] (ENCODE)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 4);
+  float* Es = reinterpret_cast<float*>(bars + 3 * S + 8);    // [LK][Nr] (ENCODE), e_z at [h][z]
+  float* Slo = Es + a.LK * a.Nr;                                     // [LK]
   float* Sinv = Slo + a.LK;                                          // [LK]
   uint8_t* Ts = reinterpret_cast<uint8_t*>(Sinv + a.LK);             // [LK][kRegionRow]
 
@@ -206,19 +213,23 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
   int* err = a.err;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(smem_u32(&bars[s]), 1);
-      mbar_init(smem_u32(&bars[TC_STAGES + s]), 1);
-      mbar_init(smem_u32(&bars[2 * TC_STAGES + 4 + s]), 2);
+      mbar_init(smem_u32(&bars[S + s]), 1);
+      mbar_init(smem_u32(&bars[2 * S + 4 + s]), 2);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(smem_u32(&bars[2 * TC_STAGES + b]), 1);
-      mbar_init(smem_u32(&bars[2 * TC_STAGES + 2 + b]), TC_EPI_WARPS);
+      mbar_init(smem_u32(&bars[2 * S + b]), 1);
+      mbar_init(smem_u32(&bars[2 * S + 2 + b]), TC_EPI_WARPS);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (ENCODE) {
+    for (int i = threadIdx.x; i < a.LK * a.Nr; i += TC_THREADS) {
+      const int h = i / a.Nr, z = i % a.Nr;
+      Es[i] = z > 0 ? a.E[(int64_t)h * (a.Nr + 1) + z] : 0.f;
+    }
     for (int i = threadIdx.x; i < a.LK * kRegionRow / 4; i += TC_THREADS)
       reinterpret_cast<uint32_t*>(Ts)[i] = reinterpret_cast<const uint32_t*>(a.Rtab)[i];
     for (int h = threadIdx.x; h < a.LK; h += TC_THREADS) {
@@ -244,8 +255,8 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       for (int kc = 0; kc < nk && ok; ++kc, ++it) {
-        const uint32_t s = it % TC_STAGES, r = it / TC_STAGES;
-        ok = mbar_wait(smem_u32(&bars[TC_STAGES + s]), (r & 1) ^ 1, err);
+        const uint32_t s = it % S, r = it / S;
+        ok = mbar_wait(smem_u32(&bars[S + s]), (r & 1) ^ 1, err);
         if (!ok) break;
         const uint32_t full = smem_u32(&bars[s]);
         mbar_expect_tx(full, XBYTES + (TF32 ? 2 : 1) * ABYTES);
@@ -261,7 +272,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       for (int kc = 0; kc < nk && ok; ++kc, ++it) {
-        const uint32_t s = it % TC_STAGES, r = it / TC_STAGES;
+        const uint32_t s = it % S, r = it / S;
         ok = mbar_wait(smem_u32(&bars[s]), r & 1, err);
         if (!ok) break;
         float4* xv = reinterpret_cast<float4*>(sx + s * XBYTES);
@@ -279,7 +290,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
         // generic-proxy writes become visible to the tensor cores' reads
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&bars[2 * TC_STAGES + 4 + s]));
+        if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + s]));
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -293,13 +304,13 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
       const uint32_t ab = lt & 1, use = lt >> 1;
-      ok = mbar_wait(smem_u32(&bars[2 * TC_STAGES + 2 + ab]), (use & 1) ^ 1, err);
+      ok = mbar_wait(smem_u32(&bars[2 * S + 2 + ab]), (use & 1) ^ 1, err);
       if (!ok) break;
       tc_fence_after();
       const uint32_t dt = tmem + ab * (TCOLS / 2);
       for (int kc = 0; kc < nk; ++kc, ++it) {
-        const uint32_t s = it % TC_STAGES, r = it / TC_STAGES;
-        ok = mbar_wait(smem_u32(&bars[TF32 ? 2 * TC_STAGES + 4 + s : s]), r & 1, err);
+        const uint32_t s = it % S, r = it / S;
+        ok = mbar_wait(smem_u32(&bars[TF32 ? 2 * S + 4 + s : s]), r & 1, err);
         if (!ok) break;
         tc_fence_after();
         const uint64_t ad = smem_desc(smem_u32(sx + s * XBYTES));
@@ -319,10 +330,10 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
           for (int k = 0; k < KC / 16; ++k)   // 16 BF16 = 32 bytes = 2 in descriptor units
             mma_bf16(dt, ad + 2 * k, bd + 2 * k, idesc, (kc > 0 || k > 0) ? 1u : 0u);
         }
-        mma_commit(smem_u32(&bars[TC_STAGES + s]));
+        mma_commit(smem_u32(&bars[S + s]));
       }
       if (!ok) break;
-      mma_commit(smem_u32(&bars[2 * TC_STAGES + ab]));
+      mma_commit(smem_u32(&bars[2 * S + ab]));
     }
   } else if (warp >= 4) {
     // ---- epilogue: warp w reads TMEM lanes 32*(w%4).. (its quadrant's 32
@@ -334,13 +345,13 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
     uint32_t lt = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
       const uint32_t ab = lt & 1, use = lt >> 1;
-      if (!mbar_wait(smem_u32(&bars[2 * TC_STAGES + ab]), use & 1, err)) break;
+      if (!mbar_wait(smem_u32(&bars[2 * S + ab]), use & 1, err)) break;
       tc_fence_after();
       float v[16];
       if (active) tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + ab * (TCOLS / 2) + g * 16, v);
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&bars[2 * TC_STAGES + 2 + ab]));
+      if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 2 + ab]));
       const int64_t p = tile * TC_M + row;
       if (!active || p >= a.rows) continue;
       if (ENCODE) {
@@ -352,8 +363,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
               const int c = qq * 4 + b, h = g * 16 + c;
-              x |= (uint32_t)region_fast(a.E + (int64_t)h * (a.Nr + 1), Ts + h * kRegionRow, Slo[h], Sinv[h],
-                                         v[c]) << (8 * b);
+              x |= (uint32_t)region_fast(Es + h * a.Nr, Ts + h * kRegionRow, Slo[h], Sinv[h], v[c]) << (8 * b);
             }
             wv[qq] = x;
           }
@@ -365,7 +375,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
             if (h < a.LK) {
               const int tree = h / a.K, j = h % a.K;
               a.codes[((int64_t)tree * a.rows + p) * a.K + j] =
-                  (uint8_t)region_fast(a.E + (int64_t)h * (a.Nr + 1), Ts + h * kRegionRow, Slo[h], Sinv[h], v[c]);
+                  (uint8_t)region_fast(Es + h * a.Nr, Ts + h * kRegionRow, Slo[h], Sinv[h], v[c]);
             }
           }
         }
@@ -446,7 +456,7 @@ template <int N, bool ENCODE, bool TF32>
 int launch_tc(const CUtensorMap& tx, const CUtensorMap& ta, const CUtensorMap& ta2, const TcArgs& args,
               cudaStream_t s) {
   size_t smem = 1024 + tc_tile_bytes<N, TF32>();
-  if (ENCODE) smem += sizeof(float) * 2 * (size_t)args.LK + (size_t)args.LK * kRegionRow;
+  if (ENCODE) smem += sizeof(float) * ((size_t)args.LK * args.Nr + 2 * args.LK) + (size_t)args.LK * kRegionRow;
   auto kern = k_project_tc<N, ENCODE, TF32>;
   DL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, nsm = 0;
