@@ -85,7 +85,14 @@ typedef struct {
   int32_t shortlist;         /* detlsh_autotune's pick for
                                 detlsh_query_params.shortlist; the query ignores
                                 this field                                        */
-  int32_t reserved[2];
+  int32_t streams;           /* 0 or 1: batches one after another on the call's
+                                stream; 2: with several batches, batches
+                                alternate between the call's stream and a
+                                second one, each with its own scratch of half
+                                the memory budget, so that one batch's kernels
+                                may overlap the next one's. Plans run one batch
+                                at a time.                                        */
+  int32_t reserved;
 } detlsh_tuning;
 
 /* Query parameters shared by a batch (Alg. 7 inputs besides q, k, c, r_min). */

@@ -593,6 +593,11 @@ int detlsh_autotune(const detlsh_index* idx, const void* Q, int64_t nq, int32_t 
     t.dist_ctas_per_sm = dc3;
     attempt(t);
   }
+  for (int st : {1, 2}) {
+    QueryTuning t = best;
+    t.streams = st;
+    attempt(t);
+  }
   for (int64_t b : {(int64_t)1024, (int64_t)2048, (int64_t)4096, (int64_t)8192, (int64_t)16384}) {
     if (b >= nq) break;
     QueryTuning t = best;
@@ -650,6 +655,7 @@ int detlsh_autotune(const detlsh_index* idx, const void* Q, int64_t nq, int32_t 
   out->walk_ctas_per_sm = best.walk_ctas_per_sm;
   out->dist_rows = best.dist_rows;
   out->dist_ctas_per_sm = best.dist_ctas_per_sm;
+  out->streams = best.streams;
   out->shortlist = pick;
   return DETLSH_OK;
 }

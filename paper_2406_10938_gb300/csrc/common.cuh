@@ -244,7 +244,8 @@ struct QueryTuning {
   int64_t batch = 0;         // queries per batch; 0: sized from free device memory
   int walk_ctas_per_sm = 0;  // walk CTAs per SM, 1..3; 0: as many as fit
   int dist_rows = 1024;      // candidate rows per distance work item (multiple of 64)
-  int dist_ctas_per_sm = 3;  // persistent distance CTAs per SM, 1..3
+  int dist_ctas_per_sm = 0;  // persistent distance CTAs per SM, 1..3; 0: 3
+  int streams = 0;           // 2: batches alternate between two streams; 0 or 1: one stream
 };
 
 // Sizes and scratch layout (byte offsets into one device block) of a batch.
@@ -280,7 +281,7 @@ int check_batch_args(const QueryShape& sh, void* base, const int32_t* k, const f
 int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, const void* Q, int64_t q0,
                   int64_t nqg, const int32_t* k, const float* c, const float* r_min, double eps,
                   double beta, int64_t* out_ids, float* out_dist, int32_t* out_stats,
-                  uint32_t* cand_ids, int64_t cand_cap, bool vec4, bool timed, cudaStream_t s);
+                  uint32_t* cand_ids, int64_t cand_cap, bool vec4, PhaseTimer* timer, cudaStream_t s);
 bool query_vec4(const detlsh_index* idx, const void* Q);
 
 // ---- plans (plan.cu), for the server

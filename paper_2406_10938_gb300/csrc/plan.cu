@@ -52,11 +52,13 @@ void release(detlsh_plan* p) {
 
 // the batch's device-side pipeline, all on plan buffers (what the graph holds)
 int enqueue_plan_batch(detlsh_plan* p, int64_t nqg, bool timed, cudaStream_t s) {
+  PhaseTimer tm(s, timed);
   DL_TRY(check_batch_args(p->sh, p->scratch, p->k_in, p->c_in, p->r_in, s));
   k_stick<<<1, 1, 0, s>>>(query_ctr(p->sh, p->scratch) + CT_BAD, p->sticky);
   DL_LAUNCH();
-  return enqueue_batch(p->idx, p->sh, p->scratch, p->q_in, 0, nqg, p->k_in, p->c_in, p->r_in, p->eps,
-                       p->beta, p->ids, p->dist, p->stats, nullptr, 0, p->vec4, timed, s);
+  DL_TRY(enqueue_batch(p->idx, p->sh, p->scratch, p->q_in, 0, nqg, p->k_in, p->c_in, p->r_in, p->eps, p->beta,
+                       p->ids, p->dist, p->stats, nullptr, 0, p->vec4, timed ? &tm : nullptr, s));
+  return tm.finish();
 }
 
 int capture(detlsh_plan* p) {

@@ -31,6 +31,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cfloat>
 
 #include "common.cuh"
@@ -1439,7 +1440,8 @@ int tuning_from_params(const detlsh_query_params* qp, QueryTuning* tu) {
   tu->batch = t.batch;
   tu->walk_ctas_per_sm = t.walk_ctas_per_sm;
   if (t.dist_rows) tu->dist_rows = t.dist_rows;
-  if (t.dist_ctas_per_sm) tu->dist_ctas_per_sm = t.dist_ctas_per_sm;
+  tu->dist_ctas_per_sm = t.dist_ctas_per_sm;
+  tu->streams = t.streams;
   return DETLSH_OK;
 }
 
@@ -1455,9 +1457,9 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
     set_error("dist_rows must be a multiple of 64 in [64, 8192]");
     return DETLSH_EINVAL;
   }
-  if (tu.walk_ctas_per_sm < 0 || tu.walk_ctas_per_sm > 3 || tu.dist_ctas_per_sm < 1 ||
-      tu.dist_ctas_per_sm > 3 || tu.batch < 0) {
-    set_error("walk_ctas_per_sm must be in [0, 3], dist_ctas_per_sm in [1, 3], batch >= 0");
+  if (tu.walk_ctas_per_sm < 0 || tu.walk_ctas_per_sm > 3 || tu.dist_ctas_per_sm < 0 ||
+      tu.dist_ctas_per_sm > 3 || tu.batch < 0 || tu.streams < 0 || tu.streams > 2) {
+    set_error("walk_ctas_per_sm and dist_ctas_per_sm must be in [0, 3], streams in [0, 2], batch >= 0");
     return DETLSH_EINVAL;
   }
   sh.L = idx->L;
@@ -1491,7 +1493,7 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   DL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&walk_per_sm, k_walk, WT, wl.total));
   walk_per_sm = std::max(walk_per_sm, 1);
   if (tu.walk_ctas_per_sm > 0) walk_per_sm = std::min(walk_per_sm, tu.walk_ctas_per_sm);
-  sh.dgrid = nsm * tu.dist_ctas_per_sm;
+  sh.dgrid = nsm * (tu.dist_ctas_per_sm ? tu.dist_ctas_per_sm : 3);
   sh.bk_smem = sizeof(uint32_t) * 2 * sh.RL + sizeof(float) * kRoundCap;
   if (sh.bk_smem > 48 * 1024)
     DL_CUDA(cudaFuncSetAttribute(k_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.bk_smem));
@@ -1592,7 +1594,7 @@ int check_batch_args(const QueryShape& sh, void* base, const int32_t* k, const f
 int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, const void* Q, int64_t q0,
                   int64_t nqg, const int32_t* k, const float* c, const float* r_min, double eps,
                   double beta, int64_t* out_ids, float* out_dist, int32_t* out_stats,
-                  uint32_t* cand_ids, int64_t cand_cap, bool vec4, bool timed, cudaStream_t s) {
+                  uint32_t* cand_ids, int64_t cand_cap, bool vec4, PhaseTimer* timer, cudaStream_t s) {
   char* b = static_cast<char*>(base);
   uint32_t* ctr = reinterpret_cast<uint32_t*>(b + sh.o_ctr);
   const uint32_t* nqd = ctr + CT_NQ;
@@ -1617,7 +1619,9 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   const size_t srow = (size_t)idx->d * (idx->dtype == DETLSH_U8 ? 1 : 4);
   const void* Qb = static_cast<const char*>(Q) + (size_t)q0 * srow;
 
-  PhaseTimer tm(s, timed);
+  PhaseTimer off(s, false);
+  PhaseTimer& tm = timer ? *timer : off;
+  const bool timed = timer != nullptr;
   k_batch_init<<<ceil_div(sh.B, 256), 256, 0, s>>>(ctr, d_min, d_max, sh.B);
   DL_LAUNCH();
   // projected queries of the batch
@@ -1738,7 +1742,6 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
     (sh.tkc == 4096 ? k_finalize<float, 4096> : k_finalize<float, 8192>)<<<(unsigned)nqg, FT, fin_smem, s>>>(fa);
   DL_LAUNCH();
   tm.end();
-  DL_TRY(tm.finish());
   return DETLSH_OK;
 }
 
@@ -1749,6 +1752,54 @@ bool query_vec4(const detlsh_index* idx, const void* Q) {
 }
 
 namespace {
+
+// A second stream per device for pipelined batches (created on first use).
+cudaStream_t side_stream() {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static cudaStream_t streams[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    streams[dev] = nullptr;
+    cudaGetLastError();
+  }
+  return streams[dev];
+}
+
+// s2 starts after the work already on s, and s waits for s2 at the join. The
+// destructor joins a fork left open by an early return, so that memory freed
+// in stream order on s is never freed under work still queued on s2.
+struct StreamFork {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t s = nullptr, s2 = nullptr;
+  bool open = false;
+  ~StreamFork() {
+    if (open) {
+      cudaEventRecord(e1, s2);
+      cudaStreamWaitEvent(s, e1, 0);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+  int begin(cudaStream_t a, cudaStream_t b) {
+    s = a;
+    s2 = b;
+    DL_CUDA(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
+    DL_CUDA(cudaEventCreateWithFlags(&e1, cudaEventDisableTiming));
+    DL_CUDA(cudaEventRecord(e0, s));
+    DL_CUDA(cudaStreamWaitEvent(s2, e0, 0));
+    open = true;
+    return DETLSH_OK;
+  }
+  int join() {
+    open = false;
+    DL_CUDA(cudaEventRecord(e1, s2));
+    DL_CUDA(cudaStreamWaitEvent(s, e1, 0));
+    return DETLSH_OK;
+  }
+};
 
 // dst row i = src row perm[i] (gather) or dst row perm[i] = src row i
 // (scatter), rows of `words` 32-bit words or of `bytes` bytes
@@ -1789,11 +1840,28 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
               float* out_dist, int32_t* out_stats, uint32_t* cand_ids, int64_t cand_cap,
               int shortlist, const QueryTuning& tu, cudaStream_t s) {
   if (nq == 0) return DETLSH_OK;
+  // with streams = 2 and several batches, batches alternate between two
+  // streams (one batch's distance gather may overlap the next one's walk),
+  // each with its own scratch of half the memory budget
+  QueryTuning t1 = tu;
   QueryShape sh;
-  DL_TRY(query_shape(idx, nq, k_max, beta, shortlist, tu, &sh));
-  Scratch ws;
+  DL_TRY(query_shape(idx, nq, k_max, beta, shortlist, t1, &sh));
+  const int nstreams = (tu.streams == 2 && nq > sh.B) ? 2 : 1;
+  if (nstreams == 2 && tu.batch == 0) t1.batch = std::max<int64_t>(1, (sh.B + 1) / 2);
+  DL_TRY(query_shape(idx, nq, k_max, beta, shortlist, t1, &sh));
+  Scratch ws, ws2;
   DL_TRY(ws.alloc(sh.bytes, s));
   DL_TRY(init_query_scratch(sh, ws.p, s));
+  cudaStream_t s2 = nullptr;
+  if (nstreams == 2) {
+    DL_TRY(ws2.alloc(sh.bytes, s));
+    DL_TRY(init_query_scratch(sh, ws2.p, s));
+    s2 = side_stream();
+    if (!s2) {
+      set_error("could not create a query stream");
+      return DETLSH_ECUDA;
+    }
+  }
   const size_t srow = (size_t)idx->d * (idx->dtype == DETLSH_U8 ? 1 : 4);
   const void* Qr = Q;
   const int32_t* kr = k;
@@ -1845,12 +1913,22 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
     oc = cand_ids ? reinterpret_cast<uint32_t*>(obuf + ids_b + dist_b + st_b) : nullptr;
   }
   const bool vec4 = query_vec4(idx, Qr);
-  for (int64_t q0 = 0; q0 < nq; q0 += sh.B) {
+  PhaseTimer tm0(s), tm1(s2 ? s2 : s);
+  StreamFork fork;
+  if (nstreams == 2) DL_TRY(fork.begin(s, s2));
+  int64_t bi = 0;
+  for (int64_t q0 = 0; q0 < nq; q0 += sh.B, ++bi) {
     const int64_t nqb = std::min<int64_t>(sh.B, nq - q0);
-    DL_TRY(set_batch_size(sh, ws.p, nqb, s));
-    DL_TRY(enqueue_batch(idx, sh, ws.p, Qr, q0, nqb, kr, cr, rr, eps, beta, oi, od, os, oc, cand_cap, vec4,
-                         true, s));
+    const bool odd = nstreams == 2 && (bi & 1);
+    cudaStream_t sb = odd ? s2 : s;
+    void* wb = odd ? ws2.p : ws.p;
+    DL_TRY(set_batch_size(sh, wb, nqb, sb));
+    DL_TRY(enqueue_batch(idx, sh, wb, Qr, q0, nqb, kr, cr, rr, eps, beta, oi, od, os, oc, cand_cap, vec4,
+                         odd ? &tm1 : &tm0, sb));
   }
+  if (nstreams == 2) DL_TRY(fork.join());
+  DL_TRY(tm0.finish());
+  DL_TRY(tm1.finish());
   if (perm) {
     DL_TRY(permute_rows<false>(oi, out_ids, perm, nq, sizeof(int64_t) * k_max, s));
     DL_TRY(permute_rows<false>(od, out_dist, perm, nq, sizeof(float) * k_max, s));
