@@ -117,6 +117,23 @@ def _ncu_traffic_per_unit(kernel):
     return None
 
 
+# ------------------------------------------------------------------ replicas
+def max_over_ranks(x, world, device="cpu"):
+    """The largest x over the ranks (each replica's time; the job ends with the slowest)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` replicas that each processed units_per_rank
+    in at most `seconds` (weak scaling)."""
+    return world * units_per_rank / seconds
+
+
 # ------------------------------------------------------------------ CPU oracle
 CPU_SCRIPT = r"""
 import json, sys, time
@@ -246,11 +263,8 @@ def gpu_arm(args, rank, world, local_rank):
     launches = pkg.detlsh_launch_count() - launches0
     clk = clocks.stop()
     ms_total = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_per_step = float(t.item()) / args.steps
-    value = world * nq / (ms_per_step / 1000.0)
+    ms_per_step = max_over_ranks(ms_total, world, dev) / args.steps
+    value = job_throughput(nq, world, ms_per_step / 1000.0)
 
     # phases (mean over timed steps)
     ph = {k: statistics.mean(tr[k] for tr in traces) for k in traces[0]}
@@ -323,16 +337,13 @@ def gpu_arm(args, rank, world, local_rank):
             step_m()
         e1.record(stream)
         torch.cuda.synchronize()
-        tm_ = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tm_, op=dist.ReduceOp.MAX)
-        ms_m = float(tm_.item()) / args.steps
+        ms_m = max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
         hits_m = 0
         for qi in range(nqr):
             d2 = ((X - Q[qi]) ** 2).sum(dim=1)
             exact = torch.topk(d2, w["k"], largest=False).indices
             hits_m += len(set(exact.tolist()) & set(out_m[0][qi].tolist()))
-        mixed = {"value": world * nq / (ms_m / 1000.0), "unit": "queries/s", "ms_per_step": ms_m,
+        mixed = {"value": job_throughput(nq, world, ms_m / 1000.0), "unit": "queries/s", "ms_per_step": ms_m,
                  "recall_at_k": hits_m / (nqr * w["k"]), "shortlist": sl, "tuning": tune,
                  "projection": "bf16 tcgen05 (FP32 accumulation)",
                  "distances": "bf16 coarse (FP32 accumulation), FP32 re-rank of the shortlist",
@@ -363,10 +374,7 @@ def gpu_arm(args, rank, world, local_rank):
         step_host()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te.item())
+    e2e_s = max_over_ranks(e2e_s, world, dev)
     h2d = X.numel() * 4 + Q.numel() * 4 + A.numel() * 4 + ids.numel() * 8 + nq * 12
     d2h = nq * w["k"] * 12 + nq * 16
 
@@ -387,7 +395,7 @@ def gpu_arm(args, rank, world, local_rank):
                            "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (X is 512 MB)"},
                 "clocks": clk,
-                "e2e": {"value": world * nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
+                "e2e": {"value": job_throughput(nq, world, e2e_s), "unit": "queries/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches),
                 "roofline": roofline,
@@ -487,11 +495,8 @@ def batching_arm(args, rank, world, local_rank):
     if plan is not None:
         pi = plan.info()
         launches += (pi["graph_launches"] - g0) * pi["graph_kernels"]
-    t = torch.tensor([ev0.elapsed_time(ev1)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_per_step = float(t.item()) / args.steps
-    value = world * nq / (ms_per_step / 1000.0)
+    ms_per_step = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / args.steps
+    value = job_throughput(nq, world, ms_per_step / 1000.0)
 
     stats = out[2].cpu().numpy()
     n_cand = float(stats[:, 0].astype("float64").sum())
@@ -555,7 +560,8 @@ def batching_arm(args, rank, world, local_rank):
                            "projection": args.proj, "shortlist": args.shortlist,
                            "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (X is 3.84 GB)"},
                 "clocks": clk,
-                "e2e": {"value": world * nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * (w["d"] * 4 + 12),
+                "e2e": {"value": job_throughput(nq, world, max_over_ranks(e2e_s, world, dev)), "unit": "queries/s",
+                        "h2d_bytes_per_step": nq * (w["d"] * 4 + 12),
                         "d2h_bytes_per_step": nq * (km * 12 + 16)},
                 "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": None,
                 "build_mpts_per_s": w["n"] / (build_ms / 1000.0) / 1e6, "recall_at_k": round(recall, 4),
