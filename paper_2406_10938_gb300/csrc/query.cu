@@ -427,7 +427,7 @@ struct WalkArgs {
   uint32_t* cand;             // [nqb][cap]
   int64_t cap;
   uint32_t* round_end;        // [nqb][kRoundCap] |S| after each round
-  uint32_t* ws_newcnt;        // [grid][2][max_bucket] new counts and lower-bound bits
+  uint32_t* ws_newcnt;        // [grid][3][max_bucket] new counts, lower-bound bits, leaf sizes
   int64_t max_bucket;         // most leaves a (round, tree) bucket can hold
   uint32_t* ws_bitmap;        // [grid][bitmap_words] when not in shared memory
   int64_t bitmap_words;
@@ -468,7 +468,7 @@ __host__ __device__ inline WalkLayout walk_layout(int L, int64_t smem_bitmap_wor
 enum { W_S = 0, W_STOP, W_NEED, W_KSTAR, W_ACC, W_TOTNEW, W_QN, W_LEAFA, W_OFFA, W_OVF };
 
 // Append the new points of bucket leaves list[0..nl) (only leaves whose select
-// key is <= kstar when filtered) to the candidate list, in batches of at most
+// key lies in (kmin, kstar] when filtered) to the candidate list, in batches of at most
 // WCAP examined points: each point is tested-and-set in the bitmap and, if
 // new, written at the list's end.
 // With count_only the bitmap is only read: newcnt[j] receives the number of
@@ -478,7 +478,7 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
                          unsigned long long kstar, const float* lbrow, unsigned char* sm,
                          const WalkLayout& ly, uint32_t* bitmap, uint32_t* cand,
                          bool count_only = false, uint32_t* newcnt = nullptr,
-                         uint32_t* lbk = nullptr) {
+                         uint32_t* lbk = nullptr, bool has_kmin = false, unsigned long long kmin = 0) {
   unsigned long long* misc = reinterpret_cast<unsigned long long*>(sm + ly.misc);
   uint32_t* bpref = reinterpret_cast<uint32_t*>(sm + ly.bpref);
   uint32_t* bstart = reinterpret_cast<uint32_t*>(sm + ly.bstart);
@@ -515,7 +515,7 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
         if (filtered) {
           const unsigned long long key =
               ((unsigned long long)__float_as_uint(lbrow[leaf]) << 32) | (unsigned long long)leaf;
-          if (key > kstar) cnt = 0;
+          if (key > kstar || (has_kmin && key <= kmin)) cnt = 0;
         }
         if (j == 0) cnt = cnt >= offa ? cnt - offa : 0u;
         c2[h] = cnt;
@@ -642,6 +642,99 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
   __syncthreads();
 }
 
+// Weighted radix select over the leaves j < nl of a bucket with key(j) =
+// (lower-bound bits << 32 | leaf) above kmin (when has_kmin): the smallest key
+// K such that the weights wt[j] of the keys in (kmin, K] add up to `need`, or
+// ~0 when all of them add up to less. Block-wide; ends with a barrier.
+__device__ unsigned long long select_key(const uint32_t* bl, const uint32_t* lbk, const uint32_t* wt, uint32_t nl,
+                                         bool has_kmin, unsigned long long kmin, unsigned long long need,
+                                         unsigned long long* sel, unsigned long long* misc) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t iters_j = (nl + WT - 1) / WT * WT;
+  // total weight above kmin
+  if (threadIdx.x == 0) misc[W_ACC] = 0;
+  __syncthreads();
+  {
+    unsigned long long part = 0;
+    for (uint32_t j = threadIdx.x; j < nl; j += WT) {
+      const unsigned long long key = ((unsigned long long)lbk[j] << 32) | (unsigned long long)bl[j];
+      if (!has_kmin || key > kmin) part += wt[j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0 && part) atomicAdd(&misc[W_ACC], part);
+  }
+  __syncthreads();
+  const bool enough = misc[W_ACC] >= need;
+  __syncthreads();
+  if (!enough) return ~0ull;
+  if (threadIdx.x == 0) {
+    misc[W_NEED] = need;
+    misc[W_KSTAR] = 0;
+    misc[W_ACC] = 0;
+  }
+  __syncthreads();
+  unsigned long long prefix = 0, pmask = 0;
+  for (int p = 7; p >= 0; --p) {
+    for (int i2 = threadIdx.x; i2 < 256; i2 += WT) sel[i2] = 0;
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < iters_j; j += WT) {
+      uint32_t dg = 0xffffffffu, wgt = 0;
+      if (j < nl) {
+        const uint32_t c = wt[j];
+        const unsigned long long key = ((unsigned long long)lbk[j] << 32) | (unsigned long long)bl[j];
+        if (c && (key & pmask) == prefix && (!has_kmin || key > kmin)) {
+          dg = (uint32_t)((key >> (8 * p)) & 255ull);
+          wgt = c;
+        }
+      }
+      const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+      const uint32_t sum = __reduce_add_sync(peers, wgt);
+      if (dg != 0xffffffffu && (peers & lt) == 0) atomicAdd(&sel[dg], (unsigned long long)sum);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      // the first digit whose cumulative weight reaches the need (a warp scan)
+      const unsigned long long nd = misc[W_NEED];
+      unsigned long long acc0 = misc[W_ACC];
+      unsigned long long v[8], run = 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        v[e] = sel[lane * 8 + e];
+        run += v[e];
+      }
+      unsigned long long incl = run;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned long long before = incl - run;
+      const bool reaches = acc0 + incl >= nd;
+      const uint32_t bal = __ballot_sync(0xffffffffu, reaches);
+      // a lane always reaches: the selected bin's weight covers the need
+      const int first = bal ? __ffs(bal) - 1 : 31;
+      if (lane == first) {
+        unsigned long long acc = acc0 + before;
+        int dg = lane * 8;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          if (acc + v[e] >= nd) break;
+          acc += v[e];
+          ++dg;
+        }
+        misc[W_ACC] = acc;
+        misc[W_KSTAR] = prefix | ((unsigned long long)min(dg, 255) << (8 * p));
+      }
+    }
+    __syncthreads();
+    prefix = misc[W_KSTAR];
+    pmask |= 255ull << (8 * p);
+  }
+  return prefix;
+}
+
 // One CTA per query (persistent over the batch): the buckets in Alg. 7 order.
 __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -652,11 +745,10 @@ __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
   unsigned long long* misc = reinterpret_cast<unsigned long long*>(sm + ly.misc);
   uint32_t* bitmap = a.smem_bitmap ? reinterpret_cast<uint32_t*>(sm + ly.bitmap)
                                    : a.ws_bitmap + (int64_t)blockIdx.x * a.bitmap_words;
-  uint32_t* newcnt = a.ws_newcnt + (int64_t)blockIdx.x * 2 * a.max_bucket;
+  uint32_t* newcnt = a.ws_newcnt + (int64_t)blockIdx.x * 3 * a.max_bucket;
   uint32_t* lbk = newcnt + a.max_bucket;
+  uint32_t* tcnt = lbk + a.max_bucket;
   const int L = a.L;
-  const int lane = threadIdx.x & 31;
-  const uint32_t lt = (1u << lane) - 1u;
 
   __shared__ long long s_qb;
   const int64_t nqb = *a.nqd;
@@ -708,84 +800,42 @@ __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
         if (nl == 0) continue;
         const uint32_t* bl = list + s_boff[b];
         const unsigned long long bpts = s_pts[b];   // all of the bucket's points
-        const unsigned long long S0 = misc[W_S];
         bool cut = false;
-        if (S0 + bpts >= T) {
-          // new points of every leaf of the bucket (bitmap read only)
-          walk_add(a, bl, nl, false, ~0ull, lbrow, sm, ly, bitmap, cand, true, newcnt, lbk);
-          cut = (S0 + misc[W_TOTNEW] >= T);
-        }
-        unsigned long long kstar = ~0ull;
-        if (cut) {
-          // weighted radix select: the smallest key (lower bound, leaf) whose
-          // prefix of new points reaches T - |S|
-          if (threadIdx.x == 0) {
-            misc[W_NEED] = T - S0;
-            misc[W_KSTAR] = 0;
-            misc[W_ACC] = 0;
+        if (misc[W_S] + bpts < T) {
+          walk_add(a, bl, nl, false, ~0ull, lbrow, sm, ly, bitmap, cand);
+        } else {
+          // the bucket may hold the cut: its leaves in key order (lower bound,
+          // leaf) are taken in chunks of about twice the points still needed
+          // (a select on the leaves' sizes); the new points of a chunk are
+          // counted (bitmap read only) and the chunk is added whole, or, if it
+          // holds the cut, up to the leaf where |S| reaches T (a select on the
+          // new counts). Only the chunks up to the cut are examined.
+          for (uint32_t j = threadIdx.x; j < nl; j += WT) {
+            const uint32_t leaf = bl[j];
+            lbk[j] = __float_as_uint(lbrow[leaf]);
+            tcnt[j] = a.leaf_range[2 * (int64_t)leaf + 1];
           }
           __syncthreads();
-          unsigned long long prefix = 0, pmask = 0;
-          for (int p = 7; p >= 0; --p) {
-            for (int i2 = threadIdx.x; i2 < 256; i2 += WT) sel[i2] = 0;
-            __syncthreads();
-            const uint32_t iters_j = (nl + WT - 1) / WT * WT;
-            for (uint32_t j = threadIdx.x; j < iters_j; j += WT) {
-              uint32_t dg = 0xffffffffu, wgt = 0;
-              if (j < nl) {
-                const uint32_t c = newcnt[j];
-                const unsigned long long key = ((unsigned long long)lbk[j] << 32) | (unsigned long long)bl[j];
-                if (c && (key & pmask) == prefix) {
-                  dg = (uint32_t)((key >> (8 * p)) & 255ull);
-                  wgt = c;
-                }
-              }
-              const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-              const uint32_t sum = __reduce_add_sync(peers, wgt);
-              if (dg != 0xffffffffu && (peers & lt) == 0) atomicAdd(&sel[dg], (unsigned long long)sum);
+          bool has_kmin = false;
+          unsigned long long kmin = 0;
+          while (true) {
+            const unsigned long long S0 = misc[W_S];
+            const unsigned long long need = T - S0;
+            const unsigned long long kc =
+                select_key(bl, lbk, tcnt, nl, has_kmin, kmin, 2 * need, sel, misc);
+            walk_add(a, bl, nl, true, kc, lbrow, sm, ly, bitmap, cand, true, newcnt, lbk, has_kmin, kmin);
+            if (S0 + misc[W_TOTNEW] >= T) {
+              const unsigned long long kstar = select_key(bl, lbk, newcnt, nl, has_kmin, kmin, need, sel, misc);
+              walk_add(a, bl, nl, true, kstar, lbrow, sm, ly, bitmap, cand, false, nullptr, nullptr, has_kmin, kmin);
+              cut = true;
+              break;
             }
-            __syncthreads();
-            if (threadIdx.x < 32) {
-              // the first digit whose cumulative weight reaches the need (a warp scan)
-              const unsigned long long need = misc[W_NEED];
-              unsigned long long acc0 = misc[W_ACC];
-              unsigned long long v[8], run = 0;
-#pragma unroll
-              for (int e = 0; e < 8; ++e) {
-                v[e] = sel[lane * 8 + e];
-                run += v[e];
-              }
-              unsigned long long incl = run;
-#pragma unroll
-              for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-              }
-              const unsigned long long before = incl - run;
-              const bool reaches = acc0 + incl >= need;
-              const uint32_t bal = __ballot_sync(0xffffffffu, reaches);
-              // a lane always reaches: the selected bin's weight covers the need
-              const int first = bal ? __ffs(bal) - 1 : 31;
-              if (lane == first) {
-                unsigned long long acc = acc0 + before;
-                int dg = lane * 8;
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                  if (acc + v[e] >= need) break;
-                  acc += v[e];
-                  ++dg;
-                }
-                misc[W_ACC] = acc;
-                misc[W_KSTAR] = prefix | ((unsigned long long)min(dg, 255) << (8 * p));
-              }
-            }
-            __syncthreads();
-            prefix = misc[W_KSTAR];
-            pmask |= 255ull << (8 * p);
+            walk_add(a, bl, nl, true, kc, lbrow, sm, ly, bitmap, cand, false, nullptr, nullptr, has_kmin, kmin);
+            if (kc == ~0ull) break;   // the bucket is exhausted without a cut
+            has_kmin = true;
+            kmin = kc;
           }
-          kstar = prefix;
         }
-        walk_add(a, bl, nl, cut, kstar, lbrow, sm, ly, bitmap, cand);
         if (cut) {
           if (threadIdx.x == 0) misc[W_STOP] = 1;
           break;
@@ -1551,7 +1601,7 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   sh.o_rend = take(sizeof(uint32_t) * B * kRoundCap);
   sh.o_thr = take(sizeof(float) * 2 * B * kRoundCap);
   sh.o_meta = take(sizeof(uint32_t) * B * MQ_WORDS);
-  sh.o_wsnew = take(sizeof(uint32_t) * 2 * sh.wgrid * max_tree_leaves);
+  sh.o_wsnew = take(sizeof(uint32_t) * 3 * sh.wgrid * max_tree_leaves);
   sh.o_wsbm = take(sh.smem_bitmap ? 0 : sizeof(uint32_t) * sh.wgrid * sh.words);
   sh.o_items = take(sizeof(uint4) * B * sh.items_per_q);
   sh.o_qk = take(sizeof(uint32_t) * 4 * B);
