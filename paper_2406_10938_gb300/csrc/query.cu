@@ -458,14 +458,14 @@ __host__ __device__ inline WalkLayout walk_layout(int L, int64_t smem_bitmap_wor
   o.bstart = take(sizeof(uint32_t) * WBATCH);
   o.newc = take(sizeof(uint32_t) * WBATCH);
   o.fmap = take(sizeof(uint16_t) * WCAP);
-  o.sel = take(sizeof(unsigned long long) * 256);
+  o.sel = take(sizeof(unsigned long long) * 256 + sizeof(uint32_t) * 256);
   o.misc = take(sizeof(unsigned long long) * 32);
   o.bitmap = take(sizeof(uint32_t) * (size_t)smem_bitmap_words);
   o.total = p;
   return o;
 }
 
-enum { W_S = 0, W_STOP, W_NEED, W_KSTAR, W_ACC, W_TOTNEW, W_QN, W_LEAFA, W_OFFA, W_OVF };
+enum { W_S = 0, W_STOP, W_NEED, W_KSTAR, W_ACC, W_TOTNEW, W_QN, W_LEAFA, W_OFFA, W_OVF, W_ONE };
 
 // Append the new points of bucket leaves list[0..nl) (only leaves whose select
 // key lies in (kmin, kstar] when filtered) to the candidate list, in batches of at most
@@ -675,9 +675,16 @@ __device__ unsigned long long select_key(const uint32_t* bl, const uint32_t* lbk
     misc[W_ACC] = 0;
   }
   __syncthreads();
+  // sel[0..256): weight per digit; the second half counts the leaves of
+  // positive weight per digit, so that a digit holding a single such leaf
+  // ends the select early (that leaf's key is the answer)
+  uint32_t* selc = reinterpret_cast<uint32_t*>(sel + 256);
   unsigned long long prefix = 0, pmask = 0;
   for (int p = 7; p >= 0; --p) {
-    for (int i2 = threadIdx.x; i2 < 256; i2 += WT) sel[i2] = 0;
+    for (int i2 = threadIdx.x; i2 < 256; i2 += WT) {
+      sel[i2] = 0;
+      selc[i2] = 0;
+    }
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < iters_j; j += WT) {
       uint32_t dg = 0xffffffffu, wgt = 0;
@@ -691,7 +698,10 @@ __device__ unsigned long long select_key(const uint32_t* bl, const uint32_t* lbk
       }
       const uint32_t peers = __match_any_sync(0xffffffffu, dg);
       const uint32_t sum = __reduce_add_sync(peers, wgt);
-      if (dg != 0xffffffffu && (peers & lt) == 0) atomicAdd(&sel[dg], (unsigned long long)sum);
+      if (dg != 0xffffffffu && (peers & lt) == 0) {
+        atomicAdd(&sel[dg], (unsigned long long)sum);
+        atomicAdd(&selc[dg], (uint32_t)__popc(peers));
+      }
     }
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -726,11 +736,24 @@ __device__ unsigned long long select_key(const uint32_t* bl, const uint32_t* lbk
         }
         misc[W_ACC] = acc;
         misc[W_KSTAR] = prefix | ((unsigned long long)min(dg, 255) << (8 * p));
+        misc[W_ONE] = (selc[min(dg, 255)] == 1u) ? 1ull : 0ull;
       }
     }
     __syncthreads();
     prefix = misc[W_KSTAR];
     pmask |= 255ull << (8 * p);
+    if (p > 0 && misc[W_ONE]) {
+      // one leaf of positive weight carries this prefix: its key is the answer
+      __syncthreads();
+      for (uint32_t j = threadIdx.x; j < nl; j += WT) {
+        const unsigned long long key = ((unsigned long long)lbk[j] << 32) | (unsigned long long)bl[j];
+        if (wt[j] && (key & pmask) == prefix && (!has_kmin || key > kmin)) misc[W_KSTAR] = key;
+      }
+      __syncthreads();
+      prefix = misc[W_KSTAR];
+      __syncthreads();
+      return prefix;
+    }
   }
   return prefix;
 }
