@@ -42,24 +42,26 @@ __device__ __forceinline__ uint4 load_code(const uint8_t* __restrict__ codes, in
 }
 
 // ---- root level
-__global__ void k_root_keys(const uint8_t* __restrict__ codes, int64_t n, int K, int bits,
+// Root key of (tree, point) g = t*n + i: the tree above the K top bits of the
+// point's codes in that tree (dimension 0 most significant).
+__global__ void k_root_keys(const uint8_t* __restrict__ codes, int64_t n, int64_t total, int K, int bits,
                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint4 c = load_code(codes, i, K);
-  uint32_t key = 0;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  const int64_t t = g / n;
+  const uint4 c = load_code(codes, g, K);
+  uint32_t key = (uint32_t)t;
 #pragma unroll
   for (int j = 0; j < kMaxK; ++j)
     if (j < K) key = (key << 1) | ((byte_of(c, j) >> (bits - 1)) & 1u);
-  keys[i] = key;
-  vals[i] = (uint32_t)i;
+  keys[g] = key;
+  vals[g] = (uint32_t)(g - t * n);
 }
 
-__global__ void k_root_flags(const uint32_t* __restrict__ keys, int64_t n, int64_t tree_off,
-                             uint32_t* __restrict__ flags) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  flags[tree_off + i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+__global__ void k_root_flags(const uint32_t* __restrict__ keys, int64_t total, uint32_t* __restrict__ flags) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  flags[g] = (g == 0 || keys[g] != keys[g - 1]) ? 1u : 0u;
 }
 
 __global__ void k_root_segments(const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos,
@@ -118,12 +120,22 @@ __global__ void k_tile_map(const uint32_t* __restrict__ tiles_needed,
   for (uint32_t t = 0; t < nt; ++t) tile_seg[t0 + t] = (uint32_t)s;
 }
 
+// The code vector of every (tree, leaf-ordered position), so that the level
+// passes read codes as contiguous streams instead of gathering them by id.
+__global__ void k_gather_codes(const uint8_t* __restrict__ codes, const uint32_t* __restrict__ ids, int64_t n,
+                               int64_t total, int K, uint4* __restrict__ lcodes) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tree_row = (g / n) * n;
+    lcodes[g] = load_code(codes, tree_row + ids[g], K);
+  }
+}
+
 // Per tile: number of points whose next unresolved bit is 1, for every dimension.
 __global__ void __launch_bounds__(LT)
 k_tile_count(const uint32_t* __restrict__ tile_seg, const uint32_t* __restrict__ tile_base,
              const uint32_t* __restrict__ seg_start, const uint32_t* __restrict__ seg_count,
-             const uint4* __restrict__ seg_plen, const uint32_t* __restrict__ ids,
-             const uint8_t* __restrict__ codes, int64_t n, int K, int bits,
+             const uint4* __restrict__ seg_plen, const uint4* __restrict__ lcodes, int K, int bits,
              uint32_t* __restrict__ tile_cnt) {
   __shared__ uint32_t s_cnt[kMaxK];
   const uint32_t tile = blockIdx.x;
@@ -131,7 +143,6 @@ k_tile_count(const uint32_t* __restrict__ tile_seg, const uint32_t* __restrict__
   const uint32_t chunk = tile - tile_base[s];
   const uint32_t start = seg_start[s], count = seg_count[s];
   const uint4 pl = seg_plen[s];
-  const int64_t tree_row = ((int64_t)start / n) * n;
   if (threadIdx.x < kMaxK) s_cnt[threadIdx.x] = 0;
   __syncthreads();
   uint32_t cnt[kMaxK];
@@ -140,8 +151,7 @@ k_tile_count(const uint32_t* __restrict__ tile_seg, const uint32_t* __restrict__
   for (int r = 0; r < LIPT; ++r) {
     const uint32_t off = chunk * LTILE + r * LT + threadIdx.x;
     if (off < count) {
-      const uint32_t id = ids[start + off];
-      const uint4 c = load_code(codes, tree_row + id, K);
+      const uint4 c = lcodes[start + off];
 #pragma unroll
       for (int j = 0; j < kMaxK; ++j) {
         const uint32_t l = byte_of(pl, j);
@@ -206,8 +216,8 @@ k_tile_scatter(const uint32_t* __restrict__ tile_seg, const uint32_t* __restrict
                const uint32_t* __restrict__ seg_start, const uint32_t* __restrict__ seg_count,
                const uint4* __restrict__ seg_plen, const uint32_t* __restrict__ seg_dim,
                const uint32_t* __restrict__ seg_ones, const uint32_t* __restrict__ tile_ones_before,
-               const uint32_t* __restrict__ ids, const uint8_t* __restrict__ codes, int64_t n,
-               int K, int bits, uint32_t* __restrict__ tmp) {
+               const uint32_t* __restrict__ ids, const uint4* __restrict__ lcodes, int bits,
+               uint32_t* __restrict__ tmp, uint4* __restrict__ tmpc) {
   __shared__ uint32_t s_warp[LT / 32];
   const uint32_t tile = blockIdx.x;
   const uint32_t s = tile_seg[tile];
@@ -216,9 +226,9 @@ k_tile_scatter(const uint32_t* __restrict__ tile_seg, const uint32_t* __restrict
   const int j = (int)seg_dim[s];
   const uint32_t shift = (uint32_t)(bits - 1) - byte_of(seg_plen[s], j);
   const uint32_t zeros_total = count - seg_ones[s];
-  const int64_t tree_row = ((int64_t)start / n) * n;
   // contiguous items per thread keep the in-tile order for the scan
   uint32_t id[LIPT], bit[LIPT];
+  uint4 cv[LIPT];
   uint32_t my_ones = 0;
 #pragma unroll
   for (int r = 0; r < LIPT; ++r) {
@@ -226,8 +236,8 @@ k_tile_scatter(const uint32_t* __restrict__ tile_seg, const uint32_t* __restrict
     bit[r] = 2;
     if (off < count) {
       id[r] = ids[start + off];
-      const uint4 c = load_code(codes, tree_row + id[r], K);
-      bit[r] = (byte_of(c, j) >> shift) & 1u;
+      cv[r] = lcodes[start + off];
+      bit[r] = (byte_of(cv[r], j) >> shift) & 1u;
       my_ones += bit[r];
     }
   }
@@ -256,20 +266,25 @@ k_tile_scatter(const uint32_t* __restrict__ tile_seg, const uint32_t* __restrict
       dest = start + (off - ones_before);
     }
     tmp[dest] = id[r];
+    tmpc[dest] = cv[r];
   }
 }
 
 __global__ void __launch_bounds__(LT)
 k_tile_copyback(const uint32_t* __restrict__ tile_seg, const uint32_t* __restrict__ tile_base,
                 const uint32_t* __restrict__ seg_start, const uint32_t* __restrict__ seg_count,
-                const uint32_t* __restrict__ tmp, uint32_t* __restrict__ ids) {
+                const uint32_t* __restrict__ tmp, uint32_t* __restrict__ ids,
+                const uint4* __restrict__ tmpc, uint4* __restrict__ lcodes) {
   const uint32_t tile = blockIdx.x;
   const uint32_t s = tile_seg[tile];
   const uint32_t chunk = tile - tile_base[s];
   const uint32_t start = seg_start[s], count = seg_count[s];
   for (int r = 0; r < LIPT; ++r) {
     const uint32_t off = chunk * LTILE + r * LT + threadIdx.x;
-    if (off < count) ids[start + off] = tmp[start + off];
+    if (off < count) {
+      ids[start + off] = tmp[start + off];
+      lcodes[start + off] = tmpc[start + off];
+    }
   }
 }
 
@@ -356,24 +371,24 @@ int read_u32(const uint32_t* d, uint32_t* h, cudaStream_t s) {
 int build_leaves(detlsh_index* idx, cudaStream_t s) {
   const int64_t n = idx->n, L = idx->L, total = n * L;
   const int K = idx->K, bits = idx->bits;
-  // ---- root level: per tree stable sort of ids by the top-bit vector
+  // ---- root level: one stable sort of all (tree, point) entries by (tree,
+  // top-bit vector); the tree occupies the key bits above the K top bits
   Scratch keys_all, flags, pos, k0, v0, d_tot;
   DL_TRY(keys_all.alloc(sizeof(uint32_t) * total, s));
   DL_TRY(flags.alloc(sizeof(uint32_t) * total, s));
   DL_TRY(pos.alloc(sizeof(uint32_t) * total, s));
-  DL_TRY(k0.alloc(sizeof(uint32_t) * n, s));
-  DL_TRY(v0.alloc(sizeof(uint32_t) * n, s));
+  DL_TRY(k0.alloc(sizeof(uint32_t) * total, s));
+  DL_TRY(v0.alloc(sizeof(uint32_t) * total, s));
   DL_TRY(d_tot.alloc(sizeof(uint32_t) * 4, s));
-  for (int64_t t = 0; t < L; ++t) {
-    k_root_keys<<<ceil_div(n, 256), 256, 0, s>>>(idx->codes + t * n * K, n, K, bits,
-                                                 k0.as<uint32_t>(), v0.as<uint32_t>());
-    DL_LAUNCH();
-    DL_TRY(radix_sort_pairs(k0.as<uint32_t>(), v0.as<uint32_t>(), n, 0, K,
-                            keys_all.as<uint32_t>() + t * n, idx->leaf_ids + t * n, s));
-    k_root_flags<<<ceil_div(n, 256), 256, 0, s>>>(keys_all.as<uint32_t>() + t * n, n, t * n,
-                                                  flags.as<uint32_t>());
-    DL_LAUNCH();
-  }
+  int tbits = 0;
+  while ((1ll << tbits) < L) ++tbits;
+  k_root_keys<<<ceil_div(total, 256), 256, 0, s>>>(idx->codes, n, total, K, bits, k0.as<uint32_t>(),
+                                                   v0.as<uint32_t>());
+  DL_LAUNCH();
+  DL_TRY(radix_sort_pairs(k0.as<uint32_t>(), v0.as<uint32_t>(), total, 0, K + tbits, keys_all.as<uint32_t>(),
+                          idx->leaf_ids, s));
+  k_root_flags<<<ceil_div(total, 256), 256, 0, s>>>(keys_all.as<uint32_t>(), total, flags.as<uint32_t>());
+  DL_LAUNCH();
   DL_TRY(exclusive_scan_u32(flags.as<uint32_t>(), pos.as<uint32_t>(), total, d_tot.as<uint32_t>(), s));
   uint32_t nseg = 0;
   DL_TRY(read_u32(d_tot.as<uint32_t>(), &nseg, s));
@@ -413,6 +428,14 @@ int build_leaves(detlsh_index* idx, cudaStream_t s) {
   DL_TRY(tile_cnt.alloc(sizeof(uint32_t) * kMaxK * tile_alloc, s));
   DL_TRY(tile_ones_before.alloc(sizeof(uint32_t) * tile_alloc, s));
 
+  // codes in leaf order (and their partition buffer)
+  Scratch lcodes, tmpc;
+  DL_TRY(lcodes.alloc(sizeof(uint4) * total, s));
+  DL_TRY(tmpc.alloc(sizeof(uint4) * total, s));
+  k_gather_codes<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 32), 256, 0, s>>>(
+      idx->codes, idx->leaf_ids, n, total, K, lcodes.as<uint4>());
+  DL_LAUNCH();
+
   uint32_t* cs = a_start.as<uint32_t>();
   uint32_t* cc = a_count.as<uint32_t>();
   uint4* cpl = a_plen.as<uint4>();
@@ -440,8 +463,7 @@ int build_leaves(detlsh_index* idx, cudaStream_t s) {
                                                    tile_seg.as<uint32_t>());
     DL_LAUNCH();
     k_tile_count<<<ntiles, LT, 0, s>>>(tile_seg.as<uint32_t>(), tile_base.as<uint32_t>(), cs, cc,
-                                       cpl, idx->leaf_ids, idx->codes, n, K, bits,
-                                       tile_cnt.as<uint32_t>());
+                                       cpl, lcodes.as<uint4>(), K, bits, tile_cnt.as<uint32_t>());
     DL_LAUNCH();
     k_choose<<<ceil_div(nseg, 256), 256, 0, s>>>(
         tiles_needed.as<uint32_t>(), tile_base.as<uint32_t>(), cc, cpl, nseg, K, bits,
@@ -451,10 +473,11 @@ int build_leaves(detlsh_index* idx, cudaStream_t s) {
     k_tile_scatter<<<ntiles, LT, 0, s>>>(tile_seg.as<uint32_t>(), tile_base.as<uint32_t>(), cs, cc,
                                          cpl, seg_dim.as<uint32_t>(), seg_ones.as<uint32_t>(),
                                          tile_ones_before.as<uint32_t>(), idx->leaf_ids,
-                                         idx->codes, n, K, bits, tmp.as<uint32_t>());
+                                         lcodes.as<uint4>(), bits, tmp.as<uint32_t>(), tmpc.as<uint4>());
     DL_LAUNCH();
     k_tile_copyback<<<ntiles, LT, 0, s>>>(tile_seg.as<uint32_t>(), tile_base.as<uint32_t>(), cs,
-                                          cc, tmp.as<uint32_t>(), idx->leaf_ids);
+                                          cc, tmp.as<uint32_t>(), idx->leaf_ids, tmpc.as<uint4>(),
+                                          lcodes.as<uint4>());
     DL_LAUNCH();
     DL_TRY(exclusive_scan_u32(out_n.as<uint32_t>(), out_pos.as<uint32_t>(), nseg,
                               d_tot.as<uint32_t>(), s));
