@@ -571,6 +571,95 @@ def batching_arm(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------------------ precision workload
+PRECISION = dict(name="precision", n=1_000_000, d=960, nq=10_000, K=16, L=4, n_regions=256, n_s=10_000,
+                 max_leaf=256, c=1.5, k=100, beta=0.1, shortlist=4096)
+
+
+def precision_desc():
+    return ("precision: n=1,000,000 d=960 fp32 Gaussian mixture of 500 anisotropic clusters (per-dimension "
+            "sigma log-uniform in [0.1,1]), 10,000 queries; K=16 L=4 N_r=256 n_s=1% c=1.5 k=100 beta=0.1; "
+            "FP32 path vs BF16 path (tcgen05 projection, BF16 coarse distances, FP32 re-rank of a 4,096 "
+            "shortlist); recall@100 against an exact scan and distance error against FP64")
+
+
+def precision_arm(args, rank, world, local_rank):
+    """Both paths on the precision workload: QPS (build + queries per step),
+    recall@100 and the relative error of the returned distances against FP64."""
+    import torch
+
+    import paper_2406_10938_gb300 as pkg
+    from workloads import gaussian_projection, make_workload, sample_ids
+
+    pkg.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = PRECISION
+    n, d, nq, k = w["n"], w["d"], w["nq"], w["k"]
+    X, Q = make_workload("precision", n=n, nq=nq, seed_query=2 + rank, device=dev)
+    A = gaussian_projection(w["L"], w["K"], d, device=dev)
+    ids = sample_ids(n, w["n_s"], device=dev)
+    kk = torch.full((nq,), k, dtype=torch.int32, device=dev)
+    cc = torch.full((nq,), w["c"], dtype=torch.float32, device=dev)
+    rr = torch.zeros(nq, dtype=torch.float32, device=dev)
+    eps = pkg.detlsh_eps_lemma3(w["K"], w["L"])
+    # exact neighbours of sampled queries (FP64 distances)
+    nqr = 300
+    sel = torch.linspace(0, nq - 1, nqr).long().to(dev)
+    gt = []
+    for i0 in range(0, nqr, 10):
+        qs = Q[sel[i0:i0 + 10]]
+        dd = torch.cdist(qs, X, compute_mode="donot_use_mm_for_euclid_dist")
+        gt.append(torch.topk(dd, k, largest=False).indices)
+    gt = torch.cat(gt)
+
+    def run(proj_mode, shortlist):
+        out = (torch.empty(nq, k, dtype=torch.int64, device=dev), torch.empty(nq, k, device=dev),
+               torch.empty(nq, 4, dtype=torch.int32, device=dev))
+
+        def step():
+            idx = pkg.detlsh_build(X, A, ids, w["K"], w["L"], w["n_regions"], w["max_leaf"], borrow=True,
+                                   proj_mode=proj_mode)
+            pkg.detlsh_query(idx, Q, kk, cc, rr, k_max=k, eps=eps, beta=w["beta"], out=out, shortlist=shortlist)
+            idx.free()
+
+        for _ in range(max(1, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        got = out[0][sel]
+        rec = sum(len(set(got[i].tolist()) & set(gt[i].tolist())) for i in range(nqr)) / (nqr * k)
+        # returned distances against FP64 distances of the same ids
+        rows = got.reshape(-1)
+        d64 = ((X[rows].double() - Q[sel].double().repeat_interleave(k, 0)) ** 2).sum(1).sqrt()
+        g32 = out[1][sel].reshape(-1).double()
+        rel = ((g32 - d64).abs() / d64.clamp_min(1e-30))
+        return {"qps": nq / (ms / 1000.0), "ms_per_step": ms, "recall_at_100": rec,
+                "dist_rel_err_max": float(rel.max()), "dist_rel_err_mean": float(rel.mean()),
+                "mean_candidates": float(out[2][:, 0].float().mean())}
+
+    fp32 = run(0, 0)
+    bf16 = run(1, w["shortlist"])
+    if rank == 0:
+        line = {"metric": METRIC, "value": bf16["qps"], "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": bf16["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16 inputs, f32 accumulation, f32 re-rank",
+                "data": "synthetic",
+                "config": {"workload": precision_desc(), **w, "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (X is 3.84 GB)"},
+                "bf16_path": bf16, "fp32_path": fp32, "bf16_vs_fp32_qps": bf16["qps"] / fp32["qps"],
+                "recall_sample": f"{nqr} queries, exact neighbours by an FP32 scan without the matmul shortcut",
+                "e2e": None, "gpu_launches": None, "roofline": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ serving workload
 SERVING = dict(name="serving", n=100_000_000, d=128, nq=20_000, K=16, L=4, n_regions=256, n_s=1_000_000,
                max_leaf=256, k_max=100, betas=(1e-3, 2e-3, 5e-3, 1e-2, 2e-2, 5e-2),
@@ -698,7 +787,7 @@ def main():
     ap.add_argument("--shortlist", type=int, default=0,
                     help="with --proj bf16: coarse BF16 candidate distances, FP32 re-rank of this many")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison of the mid step")
-    ap.add_argument("--workload", default="mid", choices=["mid", "batching", "serving"],
+    ap.add_argument("--workload", default="mid", choices=["mid", "batching", "serving", "precision"],
                     help="mid: build + 10,000 queries per step (default); batching: 100,000 mixed queries "
                          "per step against a 10,000,000-point index")
     ap.add_argument("--route", default="query", choices=["query", "plan", "graph"],
@@ -726,6 +815,8 @@ def main():
             return batching_arm(args, rank, world, local_rank)
         if args.workload == "serving":
             return serving_arm(args, rank, world, local_rank)
+        if args.workload == "precision":
+            return precision_arm(args, rank, world, local_rank)
         return gpu_arm(args, rank, world, local_rank)
     finally:
         if world > 1:
