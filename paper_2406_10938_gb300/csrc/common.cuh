@@ -250,12 +250,12 @@ struct QueryTuning {
 
 // Sizes and scratch layout (byte offsets into one device block) of a batch.
 struct QueryShape {
-  int64_t B, cap, TL, RL, words, max_tree_leaves, items_per_q;
-  int LK, L, wgrid, dgrid, dist_rows, tkc, k_max, shortlist;
+  int64_t B, cap, TL, RL, words, max_tree_leaves, items_per_q, bsplit;
+  int LK, L, wgrid, dgrid, dist_rows, tkc, k_max, shortlist, rq;
   bool smem_bitmap;
-  size_t wl_total, bk_smem, bytes;
+  size_t wl_total, bk_smem, bp_smem, bytes;
   size_t o_ctr, o_qp, o_qb16, o_qf, o_lb, o_mm, o_lround, o_hist, o_boff, o_list, o_cand, o_d2,
-      o_rend, o_thr, o_meta, o_wsnew, o_wsbm, o_items, o_qk, o_qsort, qsort_bytes;
+      o_rend, o_thr, o_meta, o_wsnew, o_wsbm, o_items, o_qk, o_qsort, qsort_bytes, o_hcnt, o_hcta;
 };
 
 // control words of a batch (uint32, at QueryShape::o_ctr): queries in the

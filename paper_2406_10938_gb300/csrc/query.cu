@@ -1,25 +1,30 @@
 // Query phase: Alg. 7 (c^2-k-ANN) with the optimised range query of
-// Sec. 6.2.2, for a batch of queries, in four kernels.
+// Sec. 6.2.2, for a batch of queries.
 //
 // k_leaf_lb   -- squared lower-bound distance (Alg. 5, first step) of every
 //               (query, leaf) pair. One thread owns one leaf and keeps its box
 //               edges in registers while it loops over a chunk of queries whose
 //               projections sit in shared memory; it also folds each query's
 //               smallest positive and largest bound into two per-query words.
-// k_walk      -- one CTA per query. Each leaf gets the first round t whose
-//               projected threshold (eps*r_t)^2 covers its lower bound; leaves
-//               are bucketed by (round, tree) and the buckets visited in
-//               Alg. 7's order. A bucket that cannot bring |S| to beta*n+k is
-//               taken whole (order inside it does not change S); the one that
-//               can is cut at the first leaf, in (lower bound, leaf number)
-//               order, where |S| reaches it, found by a weighted radix select.
+// k_thresh    -- per query, the FP64 round table r_0, c*r_0, ... (Alg. 7).
+// k_round_hist, k_bucket_plan, k_bucket_scatter
+//             -- each leaf gets the first round t whose projected threshold
+//               (eps*r_t)^2 covers its lower bound; leaves are bucketed by
+//               (round, tree), up to the first round in which some tree alone
+//               holds beta*n+k points.
+// k_walk      -- one CTA per query: the buckets in Alg. 7's order. A bucket
+//               that cannot bring |S| to beta*n+k is taken whole (order inside
+//               it does not change S); the one that can is cut at the first
+//               leaf, in (lower bound, leaf number) order, where |S| reaches
+//               it, found by weighted radix selects over key-ordered chunks.
 //               New points (deduplicated in a bitmap) are appended to the
-//               query's candidate list with the round boundaries. The walk
-//               needs no distances because it only applies the |S| >= beta*n+k
-//               rule and the every-leaf-active rule.
+//               query's candidate list with the round boundaries, and the
+//               list's distance work is queued in HBM. The walk needs no
+//               distances because it only applies the |S| >= beta*n+k rule and
+//               the every-leaf-active rule.
 // k_dist      -- the exact FP32 squared distance of every listed candidate: a
-//               pure row gather from HBM, 8 rows per warp in flight, many warps
-//               per SM.
+//               pure row gather from HBM by persistent warps taking work items
+//               from the queue, 8 rows per warp in flight.
 // k_finalize  -- one CTA per query. Replays the ">= k candidates within c*r"
 //               rule of Alg. 7 after each completed round from the distances
 //               and insertion rounds; where it fires first, S is the list's
@@ -243,50 +248,57 @@ __global__ void k_thresh(const uint32_t* __restrict__ minpos, const uint32_t* __
 }
 
 // ------------------------------------------------------------------ buckets
-// One CTA per query, many CTAs per SM: pass A gives every leaf its first round
-// t with (eps*r_t)^2 >= its lower bound and counts leaves and points per
-// (round, tree); the last reachable round is the first one in which some tree
-// alone holds T points; pass B scatters the leaves of rounds up to it into
-// their (round, tree) bucket lists (order inside a bucket is free).
 constexpr int BT = 256;
 
+// ------------------------------------------------------------------ buckets, split
+// Every leaf gets the first round t with (eps*r_t)^2 >= its lower bound; the
+// last reachable round is the first one in which some tree alone holds T
+// points; the leaves of rounds up to it go to their (round, tree) bucket
+// lists. Several CTAs per query, each over a contiguous range of the leaves:
+// (1) every leaf's
+// round, counted per (round, tree) in
+// shared memory and added to the query's histograms (one global atomic per
+// bucket and CTA); (2) per query, the last reachable round and the bucket
+// offsets; (3) each CTA counts its leaves per bucket, reserves their places
+// with one global atomic per bucket, and scatters them (order inside a bucket
+// is free).
+
 __global__ void __launch_bounds__(BT)
-k_buckets(const float* __restrict__ lb2, int64_t total_leaves, const float* __restrict__ thrP,
-          const uint16_t* __restrict__ leaf_tree, const uint32_t* __restrict__ leaf_range, int L,
-          uint8_t* __restrict__ lround, uint32_t* __restrict__ boff, uint32_t* __restrict__ bpts,
-          uint32_t* __restrict__ list, uint32_t* __restrict__ meta, const uint32_t* __restrict__ nqd) {
-  extern __shared__ __align__(16) unsigned char smb[];
-  if (blockIdx.x >= *nqd) return;
+k_round_hist(const float* __restrict__ lb2, int64_t total_leaves, int64_t lpc, const float* __restrict__ thrP,
+             const uint16_t* __restrict__ leaf_tree, const uint32_t* __restrict__ leaf_range, int L,
+             const uint32_t* __restrict__ nqd, uint8_t* __restrict__ lround, uint32_t* __restrict__ hcnt,
+             uint32_t* __restrict__ hpts, uint32_t* __restrict__ hcta, uint32_t* __restrict__ meta) {
+  extern __shared__ __align__(16) unsigned char smr[];
   const int RL = kRoundCap * L;
-  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smb);          // [RL]
-  uint32_t* s_pts = s_cnt + RL;                                  // [RL]
-  float* s_thr = reinterpret_cast<float*>(s_pts + RL);           // [kRoundCap]
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smr);   // [RL]
+  uint32_t* s_pts = s_cnt + RL;                          // [RL]
+  float* s_thr = reinterpret_cast<float*>(s_pts + RL);  // [kRoundCap]
   __shared__ uint32_t s_tl;
-  __shared__ int s_tcap;
-  const int64_t qb = blockIdx.x;
-  uint32_t* m = meta + qb * MQ_WORDS;
-  const int Ru = (int)m[MQ_RU];
-  const float* lbrow = lb2 + qb * total_leaves;
-  uint8_t* lr = lround + qb * total_leaves;
+  const int64_t qb = blockIdx.y;
+  if (qb >= (int64_t)*nqd) return;
+  const int Ru = (int)meta[qb * MQ_WORDS + MQ_RU];
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
-  for (int i = threadIdx.x; i < RL; i += BT) {
+  for (int i = threadIdx.x; i < Ru * L; i += BT) {
     s_cnt[i] = 0;
     s_pts[i] = 0;
   }
   for (int i = threadIdx.x; i < Ru; i += BT) s_thr[i] = thrP[qb * kRoundCap + i];
   if (threadIdx.x == 0) s_tl = 0;
   __syncthreads();
-  constexpr int BU = 4;   // leaves per thread in flight
-  const int64_t iters = (total_leaves + BT * BU - 1) / (BT * BU) * (BT * BU);
+  const int64_t la = (int64_t)blockIdx.x * lpc;
+  const int64_t lb_end = min(total_leaves, la + lpc);
+  const float* lbrow = lb2 + qb * total_leaves;
+  uint8_t* lr = lround + qb * total_leaves;
+  constexpr int BU = 4;
   uint32_t tl = 0;
-  for (int64_t l0 = threadIdx.x; l0 < iters; l0 += BT * BU) {
+  for (int64_t l0 = la + threadIdx.x; l0 < la + (lb_end - la + BT * BU - 1) / (BT * BU) * (BT * BU); l0 += BT * BU) {
     float lbv[BU];
     uint32_t tr[BU], pc[BU];
 #pragma unroll
     for (int u = 0; u < BU; ++u) {
       const int64_t l = l0 + (int64_t)u * BT;
-      if (l < total_leaves) {
+      if (l < lb_end) {
         lbv[u] = lbrow[l];
         tr[u] = leaf_tree[l];
         pc[u] = leaf_range[2 * l + 1];
@@ -295,7 +307,7 @@ k_buckets(const float* __restrict__ lb2, int64_t total_leaves, const float* __re
 #pragma unroll
     for (int u = 0; u < BU; ++u) {
       const int64_t l = l0 + (int64_t)u * BT;
-      const bool valid = l < total_leaves;
+      const bool valid = l < lb_end;
       uint32_t key = 0xffffffffu, pts = 0;
       if (valid) {
         const uint32_t t = (uint32_t)lower_bound_f(s_thr, Ru, lbv[u]);
@@ -315,8 +327,40 @@ k_buckets(const float* __restrict__ lb2, int64_t total_leaves, const float* __re
   tl = __reduce_max_sync(0xffffffffu, tl);
   if (lane == 0) atomicMax(&s_tl, tl);
   __syncthreads();
+  uint32_t* hc = hcta + (qb * gridDim.x + blockIdx.x) * RL;   // this CTA's counts per bucket
+  for (int i = threadIdx.x; i < Ru * L; i += BT) {
+    const uint32_t c = s_cnt[i];
+    hc[i] = c;
+    if (c) {
+      atomicAdd(&hcnt[qb * RL + i], c);
+      atomicAdd(&hpts[qb * RL + i], s_pts[i]);
+    }
+  }
+  if (threadIdx.x == 0) atomicMax(&meta[qb * MQ_WORDS + MQ_TLAST], s_tl);
+}
+
+// Per query: the last reachable round (the first one in which some tree alone
+// holds T points), bucket offsets, and the count array zeroed into cursors.
+__global__ void __launch_bounds__(BT)
+k_bucket_plan(int L, int nsplit, const uint32_t* __restrict__ nqd, uint32_t* __restrict__ hcnt,
+              const uint32_t* __restrict__ hpts, uint32_t* __restrict__ hcta, uint32_t* __restrict__ boff,
+              uint32_t* __restrict__ meta) {
+  extern __shared__ __align__(16) unsigned char smp[];
+  const int RL = kRoundCap * L;
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smp);   // [RL]
+  uint32_t* s_pts = s_cnt + RL;                          // [RL]
+  __shared__ int s_tcap;
+  const int64_t qb = blockIdx.x;
+  if (qb >= (int64_t)*nqd) return;
+  uint32_t* m = meta + qb * MQ_WORDS;
+  const int tlast = (int)m[MQ_TLAST];
+  const int nb = (tlast + 1) * L;
+  for (int i = threadIdx.x; i < nb; i += BT) {
+    s_cnt[i] = hcnt[qb * RL + i];
+    s_pts[i] = hpts[qb * RL + i];
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    const int tlast = (int)s_tl;
     const unsigned long long T = ((unsigned long long)m[MQ_T_HI] << 32) | m[MQ_T_LO];
     int tcap = tlast;
     unsigned long long cum[kMaxL];
@@ -327,46 +371,63 @@ k_buckets(const float* __restrict__ lb2, int64_t total_leaves, const float* __re
         if (cum[i] >= T) tcap = t;
       }
     }
-    m[MQ_TLAST] = (uint32_t)tlast;
     m[MQ_TCAP] = (uint32_t)tcap;
     s_tcap = tcap;
     uint32_t* bo = boff + qb * (RL + 1);
-    uint32_t* bp = bpts + qb * RL;
     uint32_t run = 0;
     for (int b = 0; b < (tcap + 1) * L; ++b) {
       bo[b] = run;
-      bp[b] = s_pts[b];
-      const uint32_t c = s_cnt[b];
-      s_cnt[b] = run;   // becomes the bucket cursor
-      run += c;
+      run += s_cnt[b];
     }
     bo[(tcap + 1) * L] = run;
   }
   __syncthreads();
-  const uint32_t tcap = (uint32_t)s_tcap;
+  // where each CTA's leaves of a bucket start: the bucket's offset plus the
+  // counts of the CTAs before it
+  const uint32_t* bo = boff + qb * (RL + 1);
+  uint32_t* hc = hcta + qb * (int64_t)nsplit * RL;
+  for (int i = threadIdx.x; i < (s_tcap + 1) * L; i += BT) {
+    uint32_t run = bo[i];
+    for (int c = 0; c < nsplit; ++c) {
+      const uint32_t v = hc[(int64_t)c * RL + i];
+      hc[(int64_t)c * RL + i] = run;
+      run += v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(BT)
+k_bucket_scatter(int64_t total_leaves, int64_t lpc, const uint16_t* __restrict__ leaf_tree, int L,
+                 const uint32_t* __restrict__ nqd, const uint8_t* __restrict__ lround,
+                 const uint32_t* __restrict__ hcta, const uint32_t* __restrict__ meta, uint32_t* __restrict__ list) {
+  extern __shared__ __align__(16) unsigned char sms[];
+  const int RL = kRoundCap * L;
+  uint32_t* s_next = reinterpret_cast<uint32_t*>(sms);   // [RL]: this CTA's next place per bucket
+  const int64_t qb = blockIdx.y;
+  if (qb >= (int64_t)*nqd) return;
+  const uint32_t tcap = meta[qb * MQ_WORDS + MQ_TCAP];
+  const int nb = ((int)tcap + 1) * L;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t* hc = hcta + (qb * gridDim.x + blockIdx.x) * RL;
+  for (int i = threadIdx.x; i < nb; i += BT) s_next[i] = hc[i];
+  __syncthreads();
+  const int64_t la = (int64_t)blockIdx.x * lpc;
+  const int64_t lb_end = min(total_leaves, la + lpc);
+  const uint8_t* lr = lround + qb * total_leaves;
   uint32_t* ql = list + qb * total_leaves;
-  for (int64_t l0 = threadIdx.x; l0 < iters; l0 += BT * BU) {
-    uint32_t tv[BU], tr[BU];
-#pragma unroll
-    for (int u = 0; u < BU; ++u) {
-      const int64_t l = l0 + (int64_t)u * BT;
-      tv[u] = 0xffffffffu;
-      if (l < total_leaves) {
-        tv[u] = lr[l];
-        tr[u] = leaf_tree[l];
-      }
+  for (int64_t l = la + threadIdx.x; l < la + (lb_end - la + BT - 1) / BT * BT; l += BT) {
+    uint32_t key = 0xffffffffu;
+    if (l < lb_end) {
+      const uint32_t t = lr[l];
+      if (t <= tcap) key = t * (uint32_t)L + leaf_tree[l];
     }
-#pragma unroll
-    for (int u = 0; u < BU; ++u) {
-      const int64_t l = l0 + (int64_t)u * BT;
-      const uint32_t key = (tv[u] <= tcap) ? tv[u] * (uint32_t)L + tr[u] : 0xffffffffu;
-      const uint32_t peers = __match_any_sync(0xffffffffu, key);
-      const int leader = __ffs(peers) - 1;
-      uint32_t base = 0;
-      if (key != 0xffffffffu && lane == leader) base = atomicAdd(&s_cnt[key], (uint32_t)__popc(peers));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (key != 0xffffffffu) ql[base + __popc(peers & lt)] = (uint32_t)l;
-    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (key != 0xffffffffu && lane == leader) base = atomicAdd(&s_next[key], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (key != 0xffffffffu) ql[base + __popc(peers & lt)] = (uint32_t)l;
   }
 }
 
@@ -1567,9 +1628,17 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   walk_per_sm = std::max(walk_per_sm, 1);
   if (tu.walk_ctas_per_sm > 0) walk_per_sm = std::min(walk_per_sm, tu.walk_ctas_per_sm);
   sh.dgrid = nsm * (tu.dist_ctas_per_sm ? tu.dist_ctas_per_sm : 3);
+  // split bucketing: per-CTA histograms over (round, tree)
+  sh.rq = 1;
   sh.bk_smem = sizeof(uint32_t) * 2 * sh.RL + sizeof(float) * kRoundCap;
+  sh.bp_smem = sizeof(uint32_t) * 2 * sh.RL;
   if (sh.bk_smem > 48 * 1024)
-    DL_CUDA(cudaFuncSetAttribute(k_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.bk_smem));
+    DL_CUDA(cudaFuncSetAttribute(k_round_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.bk_smem));
+  if (sh.bp_smem > 48 * 1024)
+    DL_CUDA(cudaFuncSetAttribute(k_bucket_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.bp_smem));
+  if (sh.RL * sizeof(uint32_t) > 48 * 1024)
+    DL_CUDA(cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sh.RL * sizeof(uint32_t))));
   DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
   DL_CUDA(cudaFuncSetAttribute(k_finalize<uint8_t, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
   DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
@@ -1584,7 +1653,7 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   // 12 GiB and a quarter of the free device memory; fewer, larger batches
   // shorten the tails of the per-query kernels)
   const int64_t per_q = sh.TL * 9 + sh.cap * 8 + sh.RL * 16 + kRoundCap * 12 + MQ_WORDS * 4 +
-                        sh.LK * 4 + sh.items_per_q * 16 +
+                        sh.LK * 4 + sh.items_per_q * 16 + ((sh.TL + 16383) / 16384) * sh.RL * 4 +
                         (idx->Xb ? (int64_t)idx->d * 2 : 0) + (shortlist > 0 ? (int64_t)idx->d * 4 : 0) +
                         64;
   int64_t B = tu.batch;
@@ -1617,6 +1686,9 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   sh.o_mm = take(sizeof(uint32_t) * 2 * B);
   sh.o_lround = take((size_t)B * sh.TL);
   sh.o_hist = take(sizeof(uint32_t) * B * sh.RL);
+  sh.o_hcnt = take(sizeof(uint32_t) * B * sh.RL);
+  sh.bsplit = (sh.TL + 16383) / 16384;
+  sh.o_hcta = take(sizeof(uint32_t) * B * sh.bsplit * sh.RL);
   sh.o_boff = take(sizeof(uint32_t) * B * (sh.RL + 1));
   sh.o_list = take(sizeof(uint32_t) * B * sh.TL);
   sh.o_cand = take(sizeof(uint32_t) * B * sh.cap);
@@ -1734,9 +1806,24 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   k_thresh<<<ceil_div(nqg, 128), 128, 0, s>>>(d_min, d_max, q0, nqd, k, c, r_min, eps, beta, idx->n,
                                               thrP, thrC, meta);
   DL_LAUNCH();
-  k_buckets<<<(unsigned)nqg, BT, sh.bk_smem, s>>>(lb, TL, thrP, idx->leaf_tree, idx->leaf_range, L,
-                                                  lround, boff, h_pts, list, meta, nqd);
-  DL_LAUNCH();
+  {
+    uint32_t* hcnt = reinterpret_cast<uint32_t*>(b + sh.o_hcnt);
+    DL_CUDA(cudaMemsetAsync(hcnt, 0, sizeof(uint32_t) * nqg * sh.RL, s));
+    DL_CUDA(cudaMemsetAsync(h_pts, 0, sizeof(uint32_t) * nqg * sh.RL, s));
+    // 16,384 leaves per CTA (measured best on the mid and batching workloads;
+    // a small serving batch still gets TL/16,384 CTAs per query)
+    const int64_t lpc = 16384;
+    const dim3 gb((unsigned)sh.bsplit, (unsigned)nqg);
+    uint32_t* hcta = reinterpret_cast<uint32_t*>(b + sh.o_hcta);
+    k_round_hist<<<gb, BT, sh.bk_smem, s>>>(lb, TL, lpc, thrP, idx->leaf_tree, idx->leaf_range, L, nqd, lround, hcnt,
+                                           h_pts, hcta, meta);
+    DL_LAUNCH();
+    k_bucket_plan<<<(unsigned)nqg, BT, sh.bp_smem, s>>>(L, (int)sh.bsplit, nqd, hcnt, h_pts, hcta, boff, meta);
+    DL_LAUNCH();
+    k_bucket_scatter<<<gb, BT, sizeof(uint32_t) * sh.RL, s>>>(TL, lpc, idx->leaf_tree, L, nqd, lround, hcta, meta,
+                                                               list);
+    DL_LAUNCH();
+  }
   tm.end();
 
   WalkArgs wa{};
