@@ -166,7 +166,7 @@ void free_index(detlsh_index* idx) {
   if (idx->owns_x && idx->X) cudaFree(const_cast<void*>(idx->X));
   void* arrays[] = {idx->A, idx->At, idx->E, idx->Ps, idx->codes, idx->leaf_ids, idx->leaf_base,
                     idx->leaf_range, idx->leaf_plen, idx->leaf_prefix, idx->leaf_lo, idx->leaf_hi,
-                    idx->leaf_tree, idx->Xb, idx->Ab, idx->d_err, idx->Rtab, idx->Rlo, idx->Rinv, idx->Atf};
+                    idx->leaf_tree, idx->Xb, idx->Ab, idx->d_err, idx->Rtab, idx->Rlo, idx->Rinv, idx->Atf, idx->Ab3};
   for (void* p : arrays)
     if (p) cudaFree(p);
   delete idx;
@@ -257,16 +257,33 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
     // FP32 inputs: on the tensor cores through the TF32 split where the shapes
     // allow it. The sample is projected by the same kernel as the points, so
     // the points that define breakpoints fall on them exactly when encoded.
+    // uint8 points likewise, as BF16 values (exact) against A in three BF16 parts
     const bool tf32 = tf32_eligible(dtype, d, LK);
-    if (tf32) {
-      const int N = (LK + 15) / 16 * 16;
-      DL_CUDA(cudaMalloc(&idx->Atf, sizeof(float) * 2 * N * d));
+    const bool b3 = bf16x3_eligible(dtype, d, LK);
+    const int Nh = (LK + 15) / 16 * 16;
+    if (tf32 || b3) {
       DL_CUDA(cudaMalloc(&idx->d_err, sizeof(int)));
       DL_CUDA(cudaMemsetAsync(idx->d_err, 0, sizeof(int), s));
+    }
+    if (tf32) {
+      DL_CUDA(cudaMalloc(&idx->Atf, sizeof(float) * 2 * Nh * d));
       DL_TRY(split_tf32(idx->A, LK, d, idx->Atf, s));
     }
+    Scratch xb16;   // BF16 copy of uint8 points, during the build only
+    if (b3) {
+      DL_CUDA(cudaMalloc(&idx->Ab3, (size_t)3 * Nh * d * 2));
+      DL_TRY(split_bf16x3(idx->A, LK, d, idx->Ab3, s));
+      DL_TRY(xb16.alloc((size_t)n * d * 2, s));
+      DL_TRY(to_bf16(idx->X, dtype, n * d, xb16.p, s));
+    }
     tm.begin(TR_SAMPLE_PROJ);
-    if (tf32) {
+    if (b3) {
+      Scratch xs;
+      DL_TRY(xs.alloc((size_t)prm->n_s * d * 2, s));
+      DL_TRY(gather_rows_bf16(xb16.p, d, static_cast<const int64_t*>(ids.d), prm->n_s, xs.p, s));
+      DL_TRY(launch_project_bf16x3(xs.p, prm->n_s, d, idx->Ab3, LK, K, nullptr, nullptr, nullptr, nullptr, Nr,
+                                   nullptr, idx->Ps, 1, prm->n_s, idx->d_err, s));
+    } else if (tf32) {
       Scratch xs;
       DL_TRY(xs.alloc(sizeof(float) * prm->n_s * d, s));
       DL_TRY(gather_rows_f32(static_cast<const float*>(idx->X), d, static_cast<const int64_t*>(ids.d), prm->n_s,
@@ -284,7 +301,10 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
     tm.end();
     // Alg. 2: codes of every point, fused with the projection
     tm.begin(TR_ENCODE);
-    if (tf32) {
+    if (b3) {
+      DL_TRY(launch_project_bf16x3(xb16.p, n, d, idx->Ab3, LK, K, idx->E, idx->Rtab, idx->Rlo, idx->Rinv, Nr,
+                                   idx->codes, nullptr, 0, 0, idx->d_err, s));
+    } else if (tf32) {
       DL_TRY(launch_project_tf32(static_cast<const float*>(idx->X), n, d, idx->Atf, LK, K, idx->E, idx->Rtab,
                                  idx->Rlo, idx->Rinv, Nr, idx->codes, nullptr, 0, 0, idx->d_err, s));
     } else {
@@ -292,7 +312,7 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
                                      idx->Rinv, Nr, idx->codes, s));
     }
     tm.end();
-    if (idx->Atf) DL_TRY(check_tc_error(idx->d_err, s));
+    if (idx->Atf || idx->Ab3) DL_TRY(check_tc_error(idx->d_err, s));
   }
   // Alg. 3: leaves
   tm.begin(TR_LEAVES);

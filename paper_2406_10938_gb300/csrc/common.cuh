@@ -128,6 +128,7 @@ struct detlsh_index {
   void* Xb = nullptr;               // [n][d] BF16 copy of X (BF16 projection mode)
   void* Ab = nullptr;               // [N][d] BF16 hash vectors, N = L*K rounded up to 16
   float* Atf = nullptr;             // [2][N][d] TF32 split of A (FP32 mode on the tensor cores)
+  void* Ab3 = nullptr;              // [3][N][d] BF16 three-part split of A (uint8 points on the tensor cores)
   int* d_err = nullptr;             // error word of the tensor-core kernel
   bool owns_x = true;
   const void* X = nullptr;          // [n][d] f32 or u8
@@ -211,6 +212,13 @@ int check_tc_error(int* d_err, cudaStream_t s);
 bool tf32_eligible(int dtype, int d, int LK);
 int split_tf32(const float* A, int LK, int d, float* Asplit, cudaStream_t s);
 int gather_rows_f32(const float* X, int d, const int64_t* ids, int64_t m, float* Y, cudaStream_t s);
+// uint8 inputs on the tensor cores: BF16 points (exact) against A split into
+// three BF16 parts (Ab3 [3][N][d], from split_bf16x3), FP32-faithful.
+bool bf16x3_eligible(int dtype, int d, int LK);
+int split_bf16x3(const float* A, int LK, int d, void* Ab3, cudaStream_t s);
+int launch_project_bf16x3(const void* Xb, int64_t rows, int d, const void* Ab3, int LK, int K, const float* E,
+                          const uint8_t* Rtab, const float* Rlo, const float* Rinv, int Nr, uint8_t* codes,
+                          float* P, int64_t p_so, int64_t p_sr, int* d_err, cudaStream_t s);
 int launch_project_tf32(const float* X, int64_t rows, int d, const float* Asplit, int LK, int K, const float* E,
                         const uint8_t* Rtab, const float* Rlo, const float* Rinv, int Nr, uint8_t* codes,
                         float* P, int64_t p_so, int64_t p_sr, int* d_err, cudaStream_t s);

@@ -163,15 +163,21 @@ struct TcArgs {
   int* err;
 };
 
-// Pipeline stages: a TF32 stage holds twice the tiles of a BF16 one.
-template <bool TF32>
+// Pipeline stages: a TF32 or three-part stage holds more tiles than a BF16 one.
+template <bool TF32, bool A3>
 __host__ __device__ constexpr int tc_stages() {
-  return TF32 ? 3 : TC_STAGES;
+  return (TF32 || A3) ? 3 : TC_STAGES;
+}
+// A tiles per stage: 1 (BF16), 2 (TF32: a_big, a_small), 3 (BF16, A in three parts)
+template <bool TF32, bool A3>
+__host__ __device__ constexpr int tc_aparts() {
+  return TF32 ? 2 : (A3 ? 3 : 1);
 }
 // Shared memory bytes of k_project_tc below the breakpoints and tables.
-template <int N, bool TF32>
+template <int N, bool TF32, bool A3>
 __host__ __device__ constexpr size_t tc_tile_bytes() {
-  return (size_t)tc_stages<TF32>() * (TC_M * 128 + N * 128) * (TF32 ? 2 : 1) + (3 * tc_stages<TF32>() + 8) * 8;
+  return (size_t)tc_stages<TF32, A3>() * ((size_t)TC_M * 128 * (TF32 ? 2 : 1) + (size_t)N * 128 * tc_aparts<TF32, A3>()) +
+         (3 * tc_stages<TF32, A3>() + 8) * 8;
 }
 
 // TF32 mode: X is FP32 and each stage also holds x_small = x - x_big, where
@@ -183,11 +189,14 @@ __host__ __device__ constexpr size_t tc_tile_bytes() {
 // why this path is used for d <= 256 only. Values with at most 11
 // significant bits (the exact-arithmetic inputs) have x_small = 0 and give
 // exact sums.
-template <int N, bool ENCODE, bool TF32>
+// A3 mode: BF16 X (uint8 points, exact in BF16) against A split into three
+// BF16 parts a1 + a2 + a3 (about 24 significant bits, an FP32 value to within
+// 2^-24 of itself): three MMAs per K step.
+template <int N, bool ENCODE, bool TF32, bool A3>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA,
-             const __grid_constant__ CUtensorMap tmA2, TcArgs a) {
-  constexpr int S = tc_stages<TF32>();
+             const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmA3, TcArgs a) {
+  constexpr int S = tc_stages<TF32, A3>();
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned base for the swizzled tiles
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -198,8 +207,9 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
   uint8_t* sx = base;                                  // [STAGES][XBYTES]
   uint8_t* sa = sx + S * XBYTES;               // [STAGES][ABYTES]
   uint8_t* sxs = sa + S * ABYTES;              // [STAGES][XBYTES] x_small (TF32)
-  uint8_t* sas = sxs + (TF32 ? S * XBYTES : 0);   // [STAGES][ABYTES] a_small (TF32)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sas + (TF32 ? S * ABYTES : 0));
+  uint8_t* sas = sxs + (TF32 ? S * XBYTES : 0);   // [STAGES][ABYTES] a_small (TF32) or a2 (A3)
+  uint8_t* sa3 = sas + ((TF32 || A3) ? S * ABYTES : 0);   // [STAGES][ABYTES] a3 (A3)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sa3 + (A3 ? S * ABYTES : 0));
   // full[0..S), empty[S..2S), tfull[2S..2S+2), tempty[2S+2..2S+4), split[2S+4..3S+4)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 4);
   float* Es = reinterpret_cast<float*>(bars + 3 * S + 8);    // [LK][Nr] (ENCODE), e_z at [h][z]
@@ -259,10 +269,11 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
         ok = mbar_wait(smem_u32(&bars[S + s]), (r & 1) ^ 1, err);
         if (!ok) break;
         const uint32_t full = smem_u32(&bars[s]);
-        mbar_expect_tx(full, XBYTES + (TF32 ? 2 : 1) * ABYTES);
+        mbar_expect_tx(full, XBYTES + tc_aparts<TF32, A3>() * ABYTES);
         tma_load_2d(smem_u32(sx + s * XBYTES), &tmX, kc * KC, (int)(tile * TC_M), full);
         tma_load_2d(smem_u32(sa + s * ABYTES), &tmA, kc * KC, 0, full);
-        if (TF32) tma_load_2d(smem_u32(sas + s * ABYTES), &tmA2, kc * KC, 0, full);
+        if (TF32 || A3) tma_load_2d(smem_u32(sas + s * ABYTES), &tmA2, kc * KC, 0, full);
+        if (A3) tma_load_2d(smem_u32(sa3 + s * ABYTES), &tmA3, kc * KC, 0, full);
       }
     }
   } else if (TF32 && (warp == 2 || warp == 3)) {
@@ -324,6 +335,15 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
             mma_tf32(dt, ad + 2 * k, bsd + 2 * k, idesc, 1u);
             mma_tf32(dt, asd + 2 * k, bd + 2 * k, idesc, 1u);
             mma_tf32(dt, asd + 2 * k, bsd + 2 * k, idesc, 1u);
+          }
+        } else if (A3) {
+          const uint64_t b2 = smem_desc(smem_u32(sas + s * ABYTES));
+          const uint64_t b3 = smem_desc(smem_u32(sa3 + s * ABYTES));
+#pragma unroll
+          for (int k = 0; k < KC / 16; ++k) {   // 16 BF16 = 32 bytes = 2 in descriptor units
+            mma_bf16(dt, ad + 2 * k, bd + 2 * k, idesc, (kc > 0 || k > 0) ? 1u : 0u);
+            mma_bf16(dt, ad + 2 * k, b2 + 2 * k, idesc, 1u);
+            mma_bf16(dt, ad + 2 * k, b3 + 2 * k, idesc, 1u);
           }
         } else {
 #pragma unroll
@@ -452,19 +472,19 @@ int make_map(CUtensorMap* tm, const void* ptr, int64_t rows, int d, int box_rows
   return DETLSH_OK;
 }
 
-template <int N, bool ENCODE, bool TF32>
-int launch_tc(const CUtensorMap& tx, const CUtensorMap& ta, const CUtensorMap& ta2, const TcArgs& args,
-              cudaStream_t s) {
-  size_t smem = 1024 + tc_tile_bytes<N, TF32>();
+template <int N, bool ENCODE, bool TF32, bool A3>
+int launch_tc(const CUtensorMap& tx, const CUtensorMap& ta, const CUtensorMap& ta2, const CUtensorMap& ta3,
+              const TcArgs& args, cudaStream_t s) {
+  size_t smem = 1024 + tc_tile_bytes<N, TF32, A3>();
   if (ENCODE) smem += sizeof(float) * ((size_t)args.LK * args.Nr + 2 * args.LK) + (size_t)args.LK * kRegionRow;
-  auto kern = k_project_tc<N, ENCODE, TF32>;
+  auto kern = k_project_tc<N, ENCODE, TF32, A3>;
   DL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, nsm = 0;
   DL_CUDA(cudaGetDevice(&dev));
   DL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int64_t ntiles = (args.rows + TC_M - 1) / TC_M;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, nsm));
-  kern<<<grid, TC_THREADS, smem, s>>>(tx, ta, ta2, args);
+  kern<<<grid, TC_THREADS, smem, s>>>(tx, ta, ta2, ta3, args);
   DL_LAUNCH();
   return DETLSH_OK;
 }
@@ -535,7 +555,8 @@ int launch_project_tc(const void* Xb, int64_t rows, int d, const void* Ab, int L
   const bool enc = codes != nullptr;
 #define DL_TC_CASE(NN)                                                        \
   case NN:                                                                    \
-    return enc ? launch_tc<NN, true, false>(tx, ta, ta, args, s) : launch_tc<NN, false, false>(tx, ta, ta, args, s);
+    return enc ? launch_tc<NN, true, false, false>(tx, ta, ta, ta, args, s)          \
+               : launch_tc<NN, false, false, false>(tx, ta, ta, ta, args, s);
   switch (N) {
     DL_TC_CASE(16)
     DL_TC_CASE(32)
@@ -588,6 +609,82 @@ int split_tf32(const float* A, int LK, int d, float* Asplit, cudaStream_t s) {
   return DETLSH_OK;
 }
 
+namespace {
+__global__ void k_split_bf16x3(const float* __restrict__ A, int LK, int N, int d, __nv_bfloat16* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nd = (int64_t)N * d;
+  if (i >= nd) return;
+  const int r = (int)(i / d);
+  const float x = r < LK ? A[i] : 0.f;
+  const __nv_bfloat16 a1 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(a1);
+  const __nv_bfloat16 a2 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(a2);
+  out[i] = a1;
+  out[nd + i] = a2;
+  out[2 * nd + i] = __float2bfloat16_rn(r2);
+}
+}  // namespace
+
+int split_bf16x3(const float* A, int LK, int d, void* Ab3, cudaStream_t s) {
+  const int N = (LK + 15) / 16 * 16;
+  k_split_bf16x3<<<ceil_div((int64_t)N * d, 256), 256, 0, s>>>(A, LK, N, d, static_cast<__nv_bfloat16*>(Ab3));
+  DL_LAUNCH();
+  return DETLSH_OK;
+}
+
+bool bf16x3_eligible(int dtype, int d, int LK) {
+  return dtype == DETLSH_U8 && d % 8 == 0 && d <= 256 && LK <= 64;
+}
+
+int launch_project_bf16x3(const void* Xb, int64_t rows, int d, const void* Ab3, int LK, int K, const float* E,
+                          const uint8_t* Rtab, const float* Rlo, const float* Rinv, int Nr, uint8_t* codes,
+                          float* P, int64_t p_so, int64_t p_sr, int* d_err, cudaStream_t s) {
+  if (rows == 0) return DETLSH_OK;
+  const int N = (LK + 15) / 16 * 16;
+  if (N > 64 || d % 8 != 0) {
+    set_error("tensor-core projection needs L*K <= 64 and d a multiple of 8");
+    return DETLSH_EINVAL;
+  }
+  const int64_t nd = (int64_t)N * d;
+  CUtensorMap tx, ta, ta2, ta3;
+  DL_TRY(make_map(&tx, Xb, rows, d, TC_M));
+  DL_TRY(make_map(&ta, Ab3, N, d, N));
+  DL_TRY(make_map(&ta2, static_cast<const __nv_bfloat16*>(Ab3) + nd, N, d, N));
+  DL_TRY(make_map(&ta3, static_cast<const __nv_bfloat16*>(Ab3) + 2 * nd, N, d, N));
+  TcArgs args{};
+  args.rows = rows;
+  args.d = d;
+  args.LK = LK;
+  args.K = K;
+  args.Nr = Nr;
+  args.E = E;
+  args.Rtab = Rtab;
+  args.Rlo = Rlo;
+  args.Rinv = Rinv;
+  args.codes = codes;
+  args.P = P;
+  args.p_so = p_so;
+  args.p_sr = p_sr;
+  args.err = d_err;
+  const bool enc = codes != nullptr;
+#define DL_TC_CASE(NN)                                                        \
+  case NN:                                                                    \
+    return enc ? launch_tc<NN, true, false, true>(tx, ta, ta2, ta3, args, s)  \
+               : launch_tc<NN, false, false, true>(tx, ta, ta2, ta3, args, s);
+  switch (N) {
+    DL_TC_CASE(16)
+    DL_TC_CASE(32)
+    DL_TC_CASE(48)
+    DL_TC_CASE(64)
+    default:
+      break;
+  }
+#undef DL_TC_CASE
+  set_error("unsupported projection width %d", N);
+  return DETLSH_EINVAL;
+}
+
 bool tf32_eligible(int dtype, int d, int LK) {
   return dtype == DETLSH_F32 && d % 4 == 0 && d <= 256 && LK <= 64;
 }
@@ -623,7 +720,8 @@ int launch_project_tf32(const float* X, int64_t rows, int d, const float* Asplit
   const bool enc = codes != nullptr;
 #define DL_TC_CASE(NN)                                                        \
   case NN:                                                                    \
-    return enc ? launch_tc<NN, true, true>(tx, ta, ta2, args, s) : launch_tc<NN, false, true>(tx, ta, ta2, args, s);
+    return enc ? launch_tc<NN, true, true, false>(tx, ta, ta2, ta2, args, s)          \
+               : launch_tc<NN, false, true, false>(tx, ta, ta2, ta2, args, s);
   switch (N) {
     DL_TC_CASE(16)
     DL_TC_CASE(32)

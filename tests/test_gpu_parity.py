@@ -152,7 +152,9 @@ def test_build_degenerate_breakpoints_bit_parity(kind):
 # ------------------------------------------------------------------ build, float inputs
 @pytest.mark.parametrize("name,n,d,Nr,n_s", [("tiny", 10_000, 32, 16, 1_000),
                                              ("precision", 4_000, 960, 256, 400),
-                                             ("batching", 20_000, 96, 256, 2_000)])
+                                             ("batching", 20_000, 96, 256, 2_000),
+                                             ("mid", 20_000, 128, 256, 2_000),
+                                             ("serving", 20_000, 128, 256, 2_000)])
 def test_build_float_within_tolerance(name, n, d, Nr, n_s):
     K, L, max_leaf = 16, 4, 128
     X, _ = make_workload(name, n=n, nq=1)
