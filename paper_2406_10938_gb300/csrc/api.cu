@@ -257,7 +257,8 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
     // FP32 inputs: on the tensor cores through the TF32 split where the shapes
     // allow it. The sample is projected by the same kernel as the points, so
     // the points that define breakpoints fall on them exactly when encoded.
-    // uint8 points likewise, as BF16 values (exact) against A in three BF16 parts
+    // uint8 points likewise, widened to BF16 (exact) in the kernel against A in
+    // three BF16 parts
     const bool tf32 = tf32_eligible(dtype, d, LK);
     const bool b3 = bf16x3_eligible(dtype, d, LK);
     const int Nh = (LK + 15) / 16 * 16;
@@ -269,19 +270,17 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
       DL_CUDA(cudaMalloc(&idx->Atf, sizeof(float) * 2 * Nh * d));
       DL_TRY(split_tf32(idx->A, LK, d, idx->Atf, s));
     }
-    Scratch xb16;   // BF16 copy of uint8 points, during the build only
     if (b3) {
       DL_CUDA(cudaMalloc(&idx->Ab3, (size_t)3 * Nh * d * 2));
       DL_TRY(split_bf16x3(idx->A, LK, d, idx->Ab3, s));
-      DL_TRY(xb16.alloc((size_t)n * d * 2, s));
-      DL_TRY(to_bf16(idx->X, dtype, n * d, xb16.p, s));
     }
     tm.begin(TR_SAMPLE_PROJ);
     if (b3) {
       Scratch xs;
-      DL_TRY(xs.alloc((size_t)prm->n_s * d * 2, s));
-      DL_TRY(gather_rows_bf16(xb16.p, d, static_cast<const int64_t*>(ids.d), prm->n_s, xs.p, s));
-      DL_TRY(launch_project_bf16x3(xs.p, prm->n_s, d, idx->Ab3, LK, K, nullptr, nullptr, nullptr, nullptr, Nr,
+      DL_TRY(xs.alloc((size_t)prm->n_s * d, s));
+      DL_TRY(gather_rows_u8(static_cast<const uint8_t*>(idx->X), d, static_cast<const int64_t*>(ids.d), prm->n_s,
+                            xs.as<uint8_t>(), s));
+      DL_TRY(launch_project_bf16x3(xs.as<uint8_t>(), prm->n_s, d, idx->Ab3, LK, K, nullptr, nullptr, nullptr, nullptr, Nr,
                                    nullptr, idx->Ps, 1, prm->n_s, idx->d_err, s));
     } else if (tf32) {
       Scratch xs;
@@ -302,7 +301,7 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
     // Alg. 2: codes of every point, fused with the projection
     tm.begin(TR_ENCODE);
     if (b3) {
-      DL_TRY(launch_project_bf16x3(xb16.p, n, d, idx->Ab3, LK, K, idx->E, idx->Rtab, idx->Rlo, idx->Rinv, Nr,
+      DL_TRY(launch_project_bf16x3(static_cast<const uint8_t*>(idx->X), n, d, idx->Ab3, LK, K, idx->E, idx->Rtab, idx->Rlo, idx->Rinv, Nr,
                                    idx->codes, nullptr, 0, 0, idx->d_err, s));
     } else if (tf32) {
       DL_TRY(launch_project_tf32(static_cast<const float*>(idx->X), n, d, idx->Atf, LK, K, idx->E, idx->Rtab,
@@ -447,6 +446,7 @@ int detlsh_build(const void* X, int64_t n, int32_t d, int32_t dtype, const float
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   trace_reset(TR_SAMPLE_PROJ, TR_LEAVES);
   trace_reset(TR_BUILD_TOTAL, TR_BUILD_TOTAL);
+  trace_reset(TR_LEAF_ROOT, TR_LEAF_ITERS);
   PhaseTimer total(s);
   total.begin(TR_BUILD_TOTAL);
   detlsh_index* idx = new (std::nothrow) detlsh_index();

@@ -24,7 +24,7 @@ void count_launch();
 enum TracePhase {
   TR_SAMPLE_PROJ = 0, TR_BREAKPOINTS, TR_ENCODE, TR_LEAVES, TR_QUERY_PROJ, TR_LB, TR_DIST,
   TR_DIST_LAUNCHES, TR_LB_LAUNCHES, TR_BUILD_TOTAL, TR_QUERY_TOTAL, TR_WALK, TR_FINALIZE, TR_BUCKET,
-  TR_COUNT
+  TR_LEAF_ROOT, TR_LEAF_GATHER, TR_LEAF_LEVELS, TR_LEAF_ITERS, TR_COUNT
 };
 bool trace_on();
 void trace_reset(int first, int last);
@@ -95,6 +95,16 @@ struct Scratch {
   Scratch() = default;
   Scratch(const Scratch&) = delete;
   Scratch& operator=(const Scratch&) = delete;
+  Scratch(Scratch&& o) noexcept : p(o.p), s(o.s) { o.p = nullptr; }
+  Scratch& operator=(Scratch&& o) noexcept {
+    if (this != &o) {
+      if (p) cudaFreeAsync(p, s);
+      p = o.p;
+      s = o.s;
+      o.p = nullptr;
+    }
+    return *this;
+  }
   ~Scratch() {
     if (p) cudaFreeAsync(p, s);
   }
@@ -157,28 +167,82 @@ namespace detlsh {
 
 // ---- region search tables (Alg. 2 encoding, project.cu)
 // For projected dimension h with interior breakpoints e_1 <= ... <= e_{Nr-1}:
-// lo = e_1, w = (e_{Nr-1} - e_1) / kRegionCells, inv = 1/w (0 when w is 0 or
-// too small against |e| for the cells to be resolved in FP32), and
-// tab[c] = #{z >= 1 : e_z <= lo + (c-1) w} for 1 <= c <= kRegionCells,
-// tab[0] = 0, tab[c] = Nr-1 beyond (and for every c >= 1 when inv = 0).
-// A value p in cell c = clamp(floor((p - lo) * inv), 0, kRegionCells-1) has
-// its code #{z : e_z <= p} in [tab[c], tab[c+3]]: the one-cell margins on both
-// sides absorb the rounding of the cell computation.
+// cell(x) = round(clamp((x - lo) * inv, 0, kRegionCells-1)) with lo = e_1 and
+// inv = kRegionCells / (e_{Nr-1} - e_1) (0 when that is not finite and
+// positive), every step rounded to nearest in FP32 and never contracted (the
+// final rounding to an integer by adding 1.5 * 2^23). Each step is monotone
+// (a NaN clamps to 0), so cell is monotone non-decreasing in x:
+// for p in cell c every e_z of a lower cell is < p and every e_z of a higher
+// cell is > p. With tab[c] = #{z >= 1 : cell(e_z) < c} (c = 0..kRegionCells,
+// padded with Nr-1), the code of Alg. 2 is
+//   #{z : e_z <= p} = tab[c] + #{z : cell(e_z) = c, e_z <= p},
+// a search among the breakpoints of p's own cell only, whatever the rounding.
 constexpr int kRegionCells = 256;
 constexpr int kRegionRow = kRegionCells + 4;
 
-// code = #{z in 1..Nr-1 : e[z] <= p} for sorted e[1..Nr-1] (e[0] unused),
-// from the table row t of its dimension: a short search inside the cell's range.
-__device__ __forceinline__ int region_fast(const float* e, const uint8_t* t, float lo, float inv, float p) {
-  const float f = (p - lo) * inv;
-  const int c = f > 0.f ? (f < (float)(kRegionCells - 1) ? (int)f : kRegionCells - 1) : 0;
-  int a = t[c], b = t[c + 3];
+__device__ __forceinline__ int region_cell(float lo, float inv, float p) {
+  const float f = fminf(fmaxf(__fmul_rn(__fsub_rn(p, lo), inv), 0.f), (float)(kRegionCells - 1));
+  return __float_as_int(__fadd_rn(f, 12582912.f)) & 0x1ff;
+}
+
+// The common case, at most three breakpoints in p's cell: three independent
+// compares against e[min(a+j, b)], a = tab[c], b = tab[c+1] (e sorted, so the
+// true compares form a prefix and the last true index is the code; e[a] < p
+// when a >= 1, so a clamped index never overcounts). slow is set when the
+// cell holds more than three breakpoints; region_slow then gives the code.
+__device__ __forceinline__ int region_fast_part(const float* e, const uint8_t* t, float lo, float inv, float p,
+                                                bool& slow) {
+  const int c = region_cell(lo, inv, p);
+  const int a = t[c], b = t[c + 1];
+  const int i1 = min(a + 1, b), i2 = min(a + 2, b), i3 = min(a + 3, b);
+  const float x1 = e[i1], x2 = e[i2], x3 = e[i3];
+  int r = a;
+  r = x1 <= p ? i1 : r;
+  r = x2 <= p ? i2 : r;
+  r = x3 <= p ? i3 : r;
+  slow = b - a > 3;
+  return r;
+}
+// Binary search for the code among the breakpoints of p's cell.
+__device__ __forceinline__ int region_slow(const float* e, const uint8_t* t, float lo, float inv, float p) {
+  const int c = region_cell(lo, inv, p);
+  int a = t[c], b = t[c + 1];
   while (a < b) {
     const int m = (a + b + 1) >> 1;
     if (e[m] <= p) a = m;
     else b = m - 1;
   }
   return a;
+}
+// code = #{z in 1..Nr-1 : e[z] <= p} for the sorted row e[0..Nr-1] (e[0]
+// only read when no breakpoint lies below p's cell) and its table row t.
+__device__ __forceinline__ int region_fast(const float* e, const uint8_t* t, float lo, float inv, float p) {
+  bool slow;
+  const int r = region_fast_part(e, t, lo, inv, p, slow);
+  return slow ? region_slow(e, t, lo, inv, p) : r;
+}
+// Sixteen codes (dimensions h0..h0+15, rows es floats apart from e0) packed
+// four per word: the fast parts of all sixteen first, so that their loads
+// overlap, then the rare crowded cells.
+__device__ __forceinline__ void region_codes16(const float* e0, int es, const uint8_t* t0, const float* lo,
+                                               const float* inv, const float* v, uint32_t* w) {
+  int r[16];
+  uint32_t slow = 0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    bool sl;
+    r[i] = region_fast_part(e0 + i * es, t0 + i * kRegionRow, lo[i], inv[i], v[i], sl);
+    slow |= (uint32_t)sl << i;
+  }
+  if (slow) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if ((slow >> i) & 1u) r[i] = region_slow(e0 + i * es, t0 + i * kRegionRow, lo[i], inv[i], v[i]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    w[q] = (uint32_t)r[4 * q] | ((uint32_t)r[4 * q + 1] << 8) | ((uint32_t)r[4 * q + 2] << 16) |
+           ((uint32_t)r[4 * q + 3] << 24);
 }
 
 // tab [LK][kRegionRow], lo [LK], inv [LK] from E [LK][Nr+1].
@@ -212,11 +276,13 @@ int check_tc_error(int* d_err, cudaStream_t s);
 bool tf32_eligible(int dtype, int d, int LK);
 int split_tf32(const float* A, int LK, int d, float* Asplit, cudaStream_t s);
 int gather_rows_f32(const float* X, int d, const int64_t* ids, int64_t m, float* Y, cudaStream_t s);
-// uint8 inputs on the tensor cores: BF16 points (exact) against A split into
-// three BF16 parts (Ab3 [3][N][d], from split_bf16x3), FP32-faithful.
+// uint8 inputs on the tensor cores: the points widened to BF16 (exact) in the
+// kernel against A split into three BF16 parts (Ab3 [3][N][d], from
+// split_bf16x3), FP32-faithful.
 bool bf16x3_eligible(int dtype, int d, int LK);
 int split_bf16x3(const float* A, int LK, int d, void* Ab3, cudaStream_t s);
-int launch_project_bf16x3(const void* Xb, int64_t rows, int d, const void* Ab3, int LK, int K, const float* E,
+int gather_rows_u8(const uint8_t* X, int d, const int64_t* ids, int64_t m, uint8_t* Y, cudaStream_t s);
+int launch_project_bf16x3(const uint8_t* X, int64_t rows, int d, const void* Ab3, int LK, int K, const float* E,
                           const uint8_t* Rtab, const float* Rlo, const float* Rinv, int Nr, uint8_t* codes,
                           float* P, int64_t p_so, int64_t p_sr, int* d_err, cudaStream_t s);
 int launch_project_tf32(const float* X, int64_t rows, int d, const float* Asplit, int LK, int K, const float* E,

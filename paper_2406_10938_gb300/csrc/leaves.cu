@@ -10,6 +10,13 @@
 // partitioned bit 0 first. Empty children vanish. Because every split is a
 // stable in-place partition, the final segments are the leaves in
 // depth-first order with ascending ids inside each leaf.
+//
+// A splittable segment of at most SCAP entries is finished in one pass by one
+// block in shared memory (k_small): the same split rule applied depth-first
+// (bit-0 child first) down to its leaves, whose records are staged and then
+// placed at scanned positions, so the segment list stays in depth-first order
+// without a sort. Larger segments take the level passes above until their
+// children fit.
 #include <algorithm>
 #include <vector>
 
@@ -21,6 +28,9 @@ namespace {
 constexpr int LT = 256;          // threads per tile block
 constexpr int LIPT = 4;          // items per thread
 constexpr int LTILE = LT * LIPT; // items per tile
+constexpr int SCAP = 2048;       // entries of a segment finished in shared memory
+constexpr int ST = 256;          // threads of that block
+constexpr int SSTACK = kMaxK * 8 + 2;   // split stack: one entry per level of the path, plus one
 
 __device__ __forceinline__ uint32_t byte_of(const uint4& v, int j) {
   const uint32_t w = (j < 4) ? v.x : (j < 8) ? v.y : (j < 12) ? v.z : v.w;
@@ -97,9 +107,11 @@ __global__ void k_seg_counts(const uint32_t* __restrict__ seg_start, uint32_t ns
 }
 
 // ---- split iteration
+// Per segment: tiles of the level pass (large segments), or the flag of a
+// segment finished in shared memory (small), or neither (a leaf).
 __global__ void k_plan(const uint32_t* __restrict__ seg_count, const uint4* __restrict__ seg_plen,
                        uint32_t nseg, int K, int bits, int max_leaf,
-                       uint32_t* __restrict__ tiles_needed) {
+                       uint32_t* __restrict__ tiles_needed, uint32_t* __restrict__ small) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nseg) return;
   const uint32_t cnt = seg_count[s];
@@ -108,7 +120,221 @@ __global__ void k_plan(const uint32_t* __restrict__ seg_count, const uint4* __re
 #pragma unroll
   for (int j = 0; j < kMaxK; ++j)
     if (j < K && byte_of(pl, j) < (uint32_t)bits) splittable = true;
-  tiles_needed[s] = (cnt > (uint32_t)max_leaf && splittable) ? (cnt + LTILE - 1) / LTILE : 0u;
+  const bool active = cnt > (uint32_t)max_leaf && splittable;
+  const bool sm = active && cnt <= (uint32_t)SCAP;
+  tiles_needed[s] = (active && !sm) ? (cnt + LTILE - 1) / LTILE : 0u;
+  small[s] = sm ? 1u : 0u;
+}
+
+__global__ void k_small_list(const uint32_t* __restrict__ small, const uint32_t* __restrict__ small_pos,
+                             uint32_t nseg, uint32_t* __restrict__ small_seg) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nseg && small[s]) small_seg[small_pos[s]] = (uint32_t)s;
+}
+
+// One small segment per block: its entries (ids and codes, leaf order) in
+// two shared buffers, a stack of pending nodes (offset, count, buffer,
+// prefix lengths and prefixes). A node that is a leaf (at most max_leaf
+// entries, or no unresolved bit) is emitted; another is split as in the level
+// passes: ones of every unresolved next bit counted per warp (each warp owns
+// a contiguous range, visited lane-strided), the dimension minimising
+// |2*ones - count| (lowest on ties) chosen, the node stably partitioned into
+// the other buffer by warp ballots, and its non-empty children pushed, the
+// bit-1 child first so that the bit-0 child is popped first. The stack depth
+// is uniform over the block and kept in registers; only splits synchronise.
+// Each leaf's ids go to ids[] and its record (start, count, prefix lengths as
+// 16 nibbles) to rec[start + leaf number], inside the segment's own range of
+// the level passes' partition buffer; out_n[seg] = number of leaves.
+__global__ void __launch_bounds__(ST)
+k_small(const uint32_t* __restrict__ small_seg, const uint32_t* __restrict__ seg_start,
+        const uint32_t* __restrict__ seg_count, const uint4* __restrict__ seg_plen,
+        const uint4* __restrict__ seg_prefix, const uint4* __restrict__ lcodes, int K, int bits, int max_leaf,
+        uint32_t* __restrict__ ids, uint32_t* __restrict__ out_n, uint4* __restrict__ rec) {
+  extern __shared__ uint4 smem_u4[];
+  uint4* sc = smem_u4;                                              // [2][SCAP] codes
+  uint32_t* si = reinterpret_cast<uint32_t*>(smem_u4 + 2 * SCAP);   // [2][SCAP] ids
+  __shared__ uint4 st_pl[SSTACK], st_pf[SSTACK];
+  __shared__ uint16_t st_o[SSTACK], st_m[SSTACK];
+  __shared__ uint8_t st_b[SSTACK];
+  __shared__ uint32_t s_wcnt[ST / 32][kMaxK];
+  __shared__ uint32_t s_best[2];
+  constexpr int NW = ST / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+
+  const uint32_t seg = small_seg[blockIdx.x];
+  const uint32_t start = seg_start[seg], count = seg_count[seg];
+  for (uint32_t i = threadIdx.x; i < count; i += ST) {
+    sc[i] = lcodes[start + i];
+    si[i] = ids[start + i];
+  }
+  if (threadIdx.x == 0) {
+    st_o[0] = 0;
+    st_m[0] = (uint16_t)count;
+    st_b[0] = 0;
+    st_pl[0] = seg_plen[seg];
+    st_pf[0] = seg_prefix[seg];
+  }
+  __syncthreads();
+  int sp = 1;
+  uint32_t nleaf = 0;
+  while (sp > 0) {
+    --sp;
+    const uint32_t o = st_o[sp], m = st_m[sp], b = st_b[sp];
+    const uint4 pl = st_pl[sp], pf = st_pf[sp];
+    bool splittable = false;
+#pragma unroll
+    for (int j = 0; j < kMaxK; ++j)
+      if (j < K && byte_of(pl, j) < (uint32_t)bits) splittable = true;
+    const uint4* cb = sc + b * SCAP + o;
+    const uint32_t* ib = si + b * SCAP + o;
+    if (m <= (uint32_t)max_leaf || !splittable) {
+      for (uint32_t i = threadIdx.x; i < m; i += ST) ids[start + o + i] = ib[i];
+      if (threadIdx.x == 0) {
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          lo |= byte_of(pl, j) << (4 * j);
+          hi |= byte_of(pl, j + 8) << (4 * j);
+        }
+        rec[start + nleaf] = make_uint4(start + o, m, lo, hi);
+      }
+      ++nleaf;
+      continue;
+    }
+    // warp w owns [w*wc, min(m, (w+1)*wc)), wc a multiple of 32
+    const uint32_t wc = ((m + NW * 32 - 1) / (NW * 32)) * 32;
+    const uint32_t w0 = min(m, w * wc), w1 = min(m, w0 + wc);
+    uint32_t cnt[kMaxK];
+#pragma unroll
+    for (int j = 0; j < kMaxK; ++j) cnt[j] = 0;
+    for (uint32_t i = w0; i < w1; i += 32) {
+      const bool valid = i + lane < w1;
+      const uint4 c = valid ? cb[i + lane] : make_uint4(0, 0, 0, 0);
+#pragma unroll
+      for (int j = 0; j < kMaxK; ++j) {
+        const uint32_t l = byte_of(pl, j);
+        if (j < K && l < (uint32_t)bits)
+          cnt[j] += __popc(__ballot_sync(0xffffffffu, valid && ((byte_of(c, j) >> (bits - 1 - l)) & 1u)));
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < kMaxK; ++j) s_wcnt[w][j] = cnt[j];
+    }
+    __syncthreads();
+    if (w == 0) {
+      // lane j: dimension j's ones and gap; argmin over lanes, lowest j on ties
+      uint32_t v = 0, gap = 0xffffffffu;
+      if (lane < K && byte_of(pl, lane & 15) < (uint32_t)bits) {
+#pragma unroll
+        for (int q = 0; q < NW; ++q) v += s_wcnt[q][lane];
+        gap = (2u * v > m) ? 2u * v - m : m - 2u * v;
+      }
+      uint32_t bj = (uint32_t)lane;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const uint32_t g2 = __shfl_xor_sync(0xffffffffu, gap, off);
+        const uint32_t j2 = __shfl_xor_sync(0xffffffffu, bj, off);
+        const uint32_t v2 = __shfl_xor_sync(0xffffffffu, v, off);
+        if (g2 < gap || (g2 == gap && j2 < bj)) {
+          gap = g2;
+          bj = j2;
+          v = v2;
+        }
+      }
+      if (lane == 0) {
+        s_best[0] = bj;
+        s_best[1] = v;
+      }
+    }
+    __syncthreads();
+    const int best = (int)s_best[0];
+    const uint32_t ones = s_best[1];
+    const uint32_t zeros = m - ones;
+    const uint32_t shift = (uint32_t)(bits - 1) - byte_of(pl, best);
+    uint32_t ob = 0;   // ones before this warp's range
+    for (int q = 0; q < w; ++q) ob += s_wcnt[q][best];
+    uint4* cd = sc + (b ^ 1u) * SCAP + o;
+    uint32_t* id = si + (b ^ 1u) * SCAP + o;
+    for (uint32_t i = w0; i < w1; i += 32) {
+      const bool valid = i + lane < w1;
+      uint4 c = make_uint4(0, 0, 0, 0);
+      uint32_t v = 0;
+      if (valid) {
+        c = cb[i + lane];
+        v = ib[i + lane];
+      }
+      const bool bit = valid && ((byte_of(c, best) >> shift) & 1u);
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      const uint32_t before = ob + __popc(bal & lt_mask);
+      if (valid) {
+        const uint32_t dst = bit ? zeros + before : i + lane - before;
+        cd[dst] = c;
+        id[dst] = v;
+      }
+      ob += __popc(bal);
+    }
+    if (threadIdx.x == 0) {
+      uint4 cpl = pl;
+      set_byte(cpl, best, byte_of(pl, best) + 1);
+      const uint32_t p2 = byte_of(pf, best) * 2;
+      int t = sp;
+      if (ones) {
+        uint4 cpf = pf;
+        set_byte(cpf, best, p2 + 1);
+        st_o[t] = (uint16_t)(o + zeros);
+        st_m[t] = (uint16_t)ones;
+        st_b[t] = (uint8_t)(b ^ 1u);
+        st_pl[t] = cpl;
+        st_pf[t] = cpf;
+        ++t;
+      }
+      if (zeros) {
+        uint4 cpf = pf;
+        set_byte(cpf, best, p2);
+        st_o[t] = (uint16_t)o;
+        st_m[t] = (uint16_t)zeros;
+        st_b[t] = (uint8_t)(b ^ 1u);
+        st_pl[t] = cpl;
+        st_pf[t] = cpf;
+      }
+    }
+    sp += (ones ? 1 : 0) + (zeros ? 1 : 0);
+    __syncthreads();   // the children's entries and stack slots are in place
+  }
+  if (threadIdx.x == 0) out_n[seg] = nleaf;
+}
+
+// The leaf records of the small segments into the next segment list, at
+// out_pos[seg] + leaf number; a leaf's prefixes are the top prefix-length
+// bits of the codes of any of its points (its first).
+__global__ void k_small_expand(const uint32_t* __restrict__ small_seg, uint32_t nsmall,
+                               const uint32_t* __restrict__ seg_start, const uint32_t* __restrict__ out_n,
+                               const uint32_t* __restrict__ out_pos, const uint4* __restrict__ rec,
+                               const uint32_t* __restrict__ ids, const uint8_t* __restrict__ codes, int64_t n, int K,
+                               int bits, uint32_t* __restrict__ n_start, uint32_t* __restrict__ n_count,
+                               uint4* __restrict__ n_plen, uint4* __restrict__ n_prefix) {
+  const uint32_t t = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (t >= nsmall) return;
+  const uint32_t seg = small_seg[t];
+  const uint32_t start = seg_start[seg], nl = out_n[seg], base = out_pos[seg];
+  for (uint32_t q = threadIdx.x & 31; q < nl; q += 32) {
+    const uint4 r = rec[start + q];
+    const int64_t tree = (int64_t)r.x / n;
+    const uint4 c = load_code(codes, tree * n + ids[r.x], K);
+    uint4 pl = make_uint4(0, 0, 0, 0), pf = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int j = 0; j < kMaxK; ++j) {
+      const uint32_t l = ((j < 8 ? r.z : r.w) >> (4 * (j & 7))) & 15u;
+      set_byte(pl, j, l);
+      set_byte(pf, j, byte_of(c, j) >> (bits - l));
+    }
+    n_start[base + q] = r.x;
+    n_count[base + q] = r.y;
+    n_plen[base + q] = pl;
+    n_prefix[base + q] = pf;
+  }
 }
 
 __global__ void k_tile_map(const uint32_t* __restrict__ tiles_needed,
@@ -175,11 +401,12 @@ __global__ void k_choose(const uint32_t* __restrict__ tiles_needed,
                          const uint32_t* __restrict__ tile_base,
                          const uint32_t* __restrict__ seg_count, const uint4* __restrict__ seg_plen,
                          uint32_t nseg, int K, int bits, const uint32_t* __restrict__ tile_cnt,
+                         const uint32_t* __restrict__ small,
                          uint32_t* __restrict__ seg_dim, uint32_t* __restrict__ seg_ones,
                          uint32_t* __restrict__ tile_ones_before,
                          uint32_t* __restrict__ out_n) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nseg) return;
+  if (s >= nseg || small[s]) return;   // (a small segment's out_n comes from k_small)
   const uint32_t nt = tiles_needed[s];
   if (nt == 0) {
     out_n[s] = 1;
@@ -292,10 +519,11 @@ __global__ void k_emit(const uint32_t* __restrict__ tiles_needed, const uint32_t
                        const uint32_t* __restrict__ seg_start, const uint32_t* __restrict__ seg_count,
                        const uint4* __restrict__ seg_plen, const uint4* __restrict__ seg_prefix,
                        const uint32_t* __restrict__ seg_dim, const uint32_t* __restrict__ seg_ones,
+                       const uint32_t* __restrict__ small,
                        uint32_t nseg, uint32_t* __restrict__ n_start, uint32_t* __restrict__ n_count,
                        uint4* __restrict__ n_plen, uint4* __restrict__ n_prefix) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nseg) return;
+  if (s >= nseg || small[s]) return;   // (k_small writes a small segment's leaves)
   uint32_t o = out_pos[s];
   const uint32_t start = seg_start[s], cnt = seg_count[s];
   const uint4 pl = seg_plen[s], pf = seg_prefix[s];
@@ -360,6 +588,53 @@ __global__ void k_finalize(const uint32_t* __restrict__ seg_start, const uint32_
   atomicMax(max_count, (unsigned long long)seg_count[s]);
 }
 
+// Segment list: start, count, prefix lengths and prefixes of each segment.
+struct SegTable {
+  Scratch st, cn, pl, pf;
+  int64_t cap = 0;
+  int reserve(int64_t n, cudaStream_t s) {
+    if (n <= cap) return DETLSH_OK;
+    cap = std::max<int64_t>(n, cap + cap / 2);
+    st = Scratch();
+    cn = Scratch();
+    pl = Scratch();
+    pf = Scratch();
+    DL_TRY(st.alloc(sizeof(uint32_t) * cap, s));
+    DL_TRY(cn.alloc(sizeof(uint32_t) * cap, s));
+    DL_TRY(pl.alloc(sizeof(uint4) * cap, s));
+    DL_TRY(pf.alloc(sizeof(uint4) * cap, s));
+    return DETLSH_OK;
+  }
+  uint32_t* start() { return st.as<uint32_t>(); }
+  uint32_t* count() { return cn.as<uint32_t>(); }
+  uint4* plen() { return pl.as<uint4>(); }
+  uint4* prefix() { return pf.as<uint4>(); }
+};
+// Per-segment work arrays of one level iteration (contents do not outlive it).
+struct SegWork {
+  static constexpr int kArrays = 9;
+  Scratch a[kArrays];
+  int64_t cap = 0;
+  int reserve(int64_t n, cudaStream_t s) {
+    if (n <= cap) return DETLSH_OK;
+    cap = std::max<int64_t>(n, cap + cap / 2);
+    for (auto& x : a) {
+      x = Scratch();
+      DL_TRY(x.alloc(sizeof(uint32_t) * cap, s));
+    }
+    return DETLSH_OK;
+  }
+  uint32_t* tiles_needed() { return a[0].as<uint32_t>(); }
+  uint32_t* tile_base() { return a[1].as<uint32_t>(); }
+  uint32_t* seg_dim() { return a[2].as<uint32_t>(); }
+  uint32_t* seg_ones() { return a[3].as<uint32_t>(); }
+  uint32_t* out_n() { return a[4].as<uint32_t>(); }
+  uint32_t* out_pos() { return a[5].as<uint32_t>(); }
+  uint32_t* small() { return a[6].as<uint32_t>(); }
+  uint32_t* small_pos() { return a[7].as<uint32_t>(); }
+  uint32_t* small_seg() { return a[8].as<uint32_t>(); }
+};
+
 int read_u32(const uint32_t* d, uint32_t* h, cudaStream_t s) {
   DL_CUDA(cudaMemcpyAsync(h, d, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   DL_CUDA(cudaStreamSynchronize(s));
@@ -382,6 +657,8 @@ int build_leaves(detlsh_index* idx, cudaStream_t s) {
   DL_TRY(d_tot.alloc(sizeof(uint32_t) * 4, s));
   int tbits = 0;
   while ((1ll << tbits) < L) ++tbits;
+  PhaseTimer tm(s);
+  tm.begin(TR_LEAF_ROOT);
   k_root_keys<<<ceil_div(total, 256), 256, 0, s>>>(idx->codes, n, total, K, bits, k0.as<uint32_t>(),
                                                    v0.as<uint32_t>());
   DL_LAUNCH();
@@ -390,125 +667,139 @@ int build_leaves(detlsh_index* idx, cudaStream_t s) {
   k_root_flags<<<ceil_div(total, 256), 256, 0, s>>>(keys_all.as<uint32_t>(), total, flags.as<uint32_t>());
   DL_LAUNCH();
   DL_TRY(exclusive_scan_u32(flags.as<uint32_t>(), pos.as<uint32_t>(), total, d_tot.as<uint32_t>(), s));
+  tm.end();
   uint32_t nseg = 0;
   DL_TRY(read_u32(d_tot.as<uint32_t>(), &nseg, s));
 
-  // segment tables (ping-pong); capacity: at most one segment per point
-  const int64_t cap = total;
-  Scratch a_start, a_count, a_plen, a_prefix, b_start, b_count, b_plen, b_prefix;
-  DL_TRY(a_start.alloc(sizeof(uint32_t) * cap, s));
-  DL_TRY(a_count.alloc(sizeof(uint32_t) * cap, s));
-  DL_TRY(a_plen.alloc(sizeof(uint4) * cap, s));
-  DL_TRY(a_prefix.alloc(sizeof(uint4) * cap, s));
-  DL_TRY(b_start.alloc(sizeof(uint32_t) * cap, s));
-  DL_TRY(b_count.alloc(sizeof(uint32_t) * cap, s));
-  DL_TRY(b_plen.alloc(sizeof(uint4) * cap, s));
-  DL_TRY(b_prefix.alloc(sizeof(uint4) * cap, s));
-  k_root_segments<<<ceil_div(total, 256), 256, 0, s>>>(
-      flags.as<uint32_t>(), pos.as<uint32_t>(), keys_all.as<uint32_t>(), total, n, K, bits,
-      a_start.as<uint32_t>(), a_plen.as<uint4>(), a_prefix.as<uint4>());
+  // segment tables (ping-pong), grown to the segment count as it rises
+  SegTable ta, tb;
+  DL_TRY(ta.reserve(nseg, s));
+  k_root_segments<<<ceil_div(total, 256), 256, 0, s>>>(flags.as<uint32_t>(), pos.as<uint32_t>(),
+                                                       keys_all.as<uint32_t>(), total, n, K, bits, ta.start(),
+                                                       ta.plen(), ta.prefix());
   DL_LAUNCH();
-  k_seg_counts<<<ceil_div(nseg, 256), 256, 0, s>>>(a_start.as<uint32_t>(), nseg, n, total,
-                                                   a_count.as<uint32_t>());
+  k_seg_counts<<<ceil_div(nseg, 256), 256, 0, s>>>(ta.start(), nseg, n, total, ta.count());
   DL_LAUNCH();
+  keys_all = Scratch();
+  flags = Scratch();
+  pos = Scratch();
+  k0 = Scratch();
+  v0 = Scratch();
 
-  // per-segment and per-tile work arrays
-  Scratch tiles_needed, tile_base, seg_dim, seg_ones, out_n, out_pos, tmp;
-  DL_TRY(tiles_needed.alloc(sizeof(uint32_t) * cap, s));
-  DL_TRY(tile_base.alloc(sizeof(uint32_t) * cap, s));
-  DL_TRY(seg_dim.alloc(sizeof(uint32_t) * cap, s));
-  DL_TRY(seg_ones.alloc(sizeof(uint32_t) * cap, s));
-  DL_TRY(out_n.alloc(sizeof(uint32_t) * cap, s));
-  DL_TRY(out_pos.alloc(sizeof(uint32_t) * cap, s));
+  // per-segment work arrays (grown with the segment count) and the partition
+  // buffers of the level passes
+  SegWork wk;
+  Scratch tmp;
   DL_TRY(tmp.alloc(sizeof(uint32_t) * total, s));
-  const int64_t tile_cap = ceil_div(total, LTILE) + cap / 1;  // every segment may add one partial tile
+  int64_t tile_alloc = ceil_div(total, LTILE) + (int64_t)nseg + 1;
   Scratch tile_seg, tile_cnt, tile_ones_before;
-  int64_t tile_alloc = std::min<int64_t>(tile_cap, ceil_div(total, LTILE) + (int64_t)nseg + 1);
   DL_TRY(tile_seg.alloc(sizeof(uint32_t) * tile_alloc, s));
   DL_TRY(tile_cnt.alloc(sizeof(uint32_t) * kMaxK * tile_alloc, s));
   DL_TRY(tile_ones_before.alloc(sizeof(uint32_t) * tile_alloc, s));
+  uint32_t h_tot[2] = {0, 0};
 
   // codes in leaf order (and their partition buffer)
   Scratch lcodes, tmpc;
   DL_TRY(lcodes.alloc(sizeof(uint4) * total, s));
   DL_TRY(tmpc.alloc(sizeof(uint4) * total, s));
+  tm.begin(TR_LEAF_GATHER);
   k_gather_codes<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 32), 256, 0, s>>>(
       idx->codes, idx->leaf_ids, n, total, K, lcodes.as<uint4>());
   DL_LAUNCH();
+  const size_t small_smem = (size_t)2 * SCAP * (sizeof(uint4) + sizeof(uint32_t));
+  DL_CUDA(cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
 
-  uint32_t* cs = a_start.as<uint32_t>();
-  uint32_t* cc = a_count.as<uint32_t>();
-  uint4* cpl = a_plen.as<uint4>();
-  uint4* cpf = a_prefix.as<uint4>();
-  uint32_t* ns = b_start.as<uint32_t>();
-  uint32_t* nc = b_count.as<uint32_t>();
-  uint4* npl = b_plen.as<uint4>();
-  uint4* npf = b_prefix.as<uint4>();
-
-  for (int iter = 0; iter < kMaxK * 8 + 2; ++iter) {
-    k_plan<<<ceil_div(nseg, 256), 256, 0, s>>>(cc, cpl, nseg, K, bits, idx->max_leaf,
-                                               tiles_needed.as<uint32_t>());
+  tm.end();
+  SegTable* cur = &ta;
+  SegTable* nxt = &tb;
+  tm.begin(TR_LEAF_LEVELS);
+  int iters = 0;
+  for (int iter = 0; iter < kMaxK * 8 + 2; ++iter, ++iters) {
+    DL_TRY(wk.reserve(nseg, s));
+    k_plan<<<ceil_div(nseg, 256), 256, 0, s>>>(cur->count(), cur->plen(), nseg, K, bits, idx->max_leaf,
+                                               wk.tiles_needed(), wk.small());
     DL_LAUNCH();
-    DL_TRY(exclusive_scan_u32(tiles_needed.as<uint32_t>(), tile_base.as<uint32_t>(), nseg,
-                              d_tot.as<uint32_t>(), s));
-    uint32_t ntiles = 0;
-    DL_TRY(read_u32(d_tot.as<uint32_t>(), &ntiles, s));
-    if (ntiles == 0) break;
+    DL_TRY(exclusive_scan_u32(wk.tiles_needed(), wk.tile_base(), nseg, d_tot.as<uint32_t>(), s));
+    DL_TRY(exclusive_scan_u32(wk.small(), wk.small_pos(), nseg, d_tot.as<uint32_t>() + 1, s));
+    DL_CUDA(cudaMemcpyAsync(h_tot, d_tot.p, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, s));
+    DL_CUDA(cudaStreamSynchronize(s));
+    const uint32_t ntiles = h_tot[0], nsmall = h_tot[1];
+    if (ntiles == 0 && nsmall == 0) break;
     if ((int64_t)ntiles > tile_alloc) {
       set_error("leaf build: tile table overflow (%u > %lld)", ntiles, (long long)tile_alloc);
       return DETLSH_EINTERNAL;
     }
-    k_tile_map<<<ceil_div(nseg, 256), 256, 0, s>>>(tiles_needed.as<uint32_t>(),
-                                                   tile_base.as<uint32_t>(), nseg,
-                                                   tile_seg.as<uint32_t>());
+    if (nsmall) {
+      k_small_list<<<ceil_div(nseg, 256), 256, 0, s>>>(wk.small(), wk.small_pos(), nseg, wk.small_seg());
+      DL_LAUNCH();
+      k_small<<<nsmall, ST, small_smem, s>>>(wk.small_seg(), cur->start(), cur->count(), cur->plen(),
+                                             cur->prefix(), lcodes.as<uint4>(), K, bits, idx->max_leaf,
+                                             idx->leaf_ids, wk.out_n(), tmpc.as<uint4>());
+      DL_LAUNCH();
+    }
+    if (ntiles) {
+      k_tile_map<<<ceil_div(nseg, 256), 256, 0, s>>>(wk.tiles_needed(), wk.tile_base(), nseg,
+                                                     tile_seg.as<uint32_t>());
+      DL_LAUNCH();
+      k_tile_count<<<ntiles, LT, 0, s>>>(tile_seg.as<uint32_t>(), wk.tile_base(), cur->start(), cur->count(),
+                                         cur->plen(), lcodes.as<uint4>(), K, bits, tile_cnt.as<uint32_t>());
+      DL_LAUNCH();
+    }
+    k_choose<<<ceil_div(nseg, 256), 256, 0, s>>>(wk.tiles_needed(), wk.tile_base(), cur->count(), cur->plen(), nseg,
+                                                 K, bits, tile_cnt.as<uint32_t>(), wk.small(), wk.seg_dim(),
+                                                 wk.seg_ones(), tile_ones_before.as<uint32_t>(), wk.out_n());
     DL_LAUNCH();
-    k_tile_count<<<ntiles, LT, 0, s>>>(tile_seg.as<uint32_t>(), tile_base.as<uint32_t>(), cs, cc,
-                                       cpl, lcodes.as<uint4>(), K, bits, tile_cnt.as<uint32_t>());
-    DL_LAUNCH();
-    k_choose<<<ceil_div(nseg, 256), 256, 0, s>>>(
-        tiles_needed.as<uint32_t>(), tile_base.as<uint32_t>(), cc, cpl, nseg, K, bits,
-        tile_cnt.as<uint32_t>(), seg_dim.as<uint32_t>(), seg_ones.as<uint32_t>(),
-        tile_ones_before.as<uint32_t>(), out_n.as<uint32_t>());
-    DL_LAUNCH();
-    k_tile_scatter<<<ntiles, LT, 0, s>>>(tile_seg.as<uint32_t>(), tile_base.as<uint32_t>(), cs, cc,
-                                         cpl, seg_dim.as<uint32_t>(), seg_ones.as<uint32_t>(),
-                                         tile_ones_before.as<uint32_t>(), idx->leaf_ids,
-                                         lcodes.as<uint4>(), bits, tmp.as<uint32_t>(), tmpc.as<uint4>());
-    DL_LAUNCH();
-    k_tile_copyback<<<ntiles, LT, 0, s>>>(tile_seg.as<uint32_t>(), tile_base.as<uint32_t>(), cs,
-                                          cc, tmp.as<uint32_t>(), idx->leaf_ids, tmpc.as<uint4>(),
-                                          lcodes.as<uint4>());
-    DL_LAUNCH();
-    DL_TRY(exclusive_scan_u32(out_n.as<uint32_t>(), out_pos.as<uint32_t>(), nseg,
-                              d_tot.as<uint32_t>(), s));
+    if (ntiles) {
+      k_tile_scatter<<<ntiles, LT, 0, s>>>(tile_seg.as<uint32_t>(), wk.tile_base(), cur->start(), cur->count(),
+                                           cur->plen(), wk.seg_dim(), wk.seg_ones(), tile_ones_before.as<uint32_t>(),
+                                           idx->leaf_ids, lcodes.as<uint4>(), bits, tmp.as<uint32_t>(),
+                                           tmpc.as<uint4>());
+      DL_LAUNCH();
+      k_tile_copyback<<<ntiles, LT, 0, s>>>(tile_seg.as<uint32_t>(), wk.tile_base(), cur->start(), cur->count(),
+                                            tmp.as<uint32_t>(), idx->leaf_ids, tmpc.as<uint4>(), lcodes.as<uint4>());
+      DL_LAUNCH();
+    }
+    DL_TRY(exclusive_scan_u32(wk.out_n(), wk.out_pos(), nseg, d_tot.as<uint32_t>(), s));
     uint32_t nseg_new = 0;
     DL_TRY(read_u32(d_tot.as<uint32_t>(), &nseg_new, s));
-    if ((int64_t)nseg_new > cap) {
+    if ((int64_t)nseg_new > total) {
       set_error("leaf build: segment table overflow");
       return DETLSH_EINTERNAL;
     }
-    k_emit<<<ceil_div(nseg, 256), 256, 0, s>>>(tiles_needed.as<uint32_t>(), out_pos.as<uint32_t>(),
-                                               cs, cc, cpl, cpf, seg_dim.as<uint32_t>(),
-                                               seg_ones.as<uint32_t>(), nseg, ns, nc, npl, npf);
+    DL_TRY(nxt->reserve(nseg_new, s));
+    k_emit<<<ceil_div(nseg, 256), 256, 0, s>>>(wk.tiles_needed(), wk.out_pos(), cur->start(), cur->count(),
+                                               cur->plen(), cur->prefix(), wk.seg_dim(), wk.seg_ones(), wk.small(),
+                                               nseg, nxt->start(), nxt->count(), nxt->plen(), nxt->prefix());
     DL_LAUNCH();
-    std::swap(cs, ns);
-    std::swap(cc, nc);
-    std::swap(cpl, npl);
-    std::swap(cpf, npf);
+    if (nsmall) {
+      k_small_expand<<<ceil_div(nsmall, 8), 256, 0, s>>>(wk.small_seg(), nsmall, cur->start(), wk.out_n(),
+                                                        wk.out_pos(), tmpc.as<uint4>(), idx->leaf_ids, idx->codes,
+                                                        n, K, bits, nxt->start(), nxt->count(), nxt->plen(),
+                                                        nxt->prefix());
+      DL_LAUNCH();
+    }
+    std::swap(cur, nxt);
     nseg = nseg_new;
     // the tile tables must cover the next iteration's active segments
     const int64_t need = ceil_div(total, LTILE) + (int64_t)nseg + 1;
     if (need > tile_alloc) {
       tile_alloc = need;
-      Scratch a, b2, c2;
-      DL_TRY(a.alloc(sizeof(uint32_t) * tile_alloc, s));
+      Scratch a2, b2, c2;
+      DL_TRY(a2.alloc(sizeof(uint32_t) * tile_alloc, s));
       DL_TRY(b2.alloc(sizeof(uint32_t) * kMaxK * tile_alloc, s));
       DL_TRY(c2.alloc(sizeof(uint32_t) * tile_alloc, s));
-      std::swap(tile_seg.p, a.p);
+      std::swap(tile_seg.p, a2.p);
       std::swap(tile_cnt.p, b2.p);
       std::swap(tile_ones_before.p, c2.p);
     }
   }
+  tm.end();
+  DL_TRY(tm.finish());
+  if (trace_on()) trace_add(TR_LEAF_ITERS, iters);
+  uint32_t* cs = cur->start();
+  uint32_t* cc = cur->count();
+  uint4* cpl = cur->plen();
+  uint4* cpf = cur->prefix();
 
   // ---- leaf table
   idx->total_leaves = nseg;

@@ -150,17 +150,8 @@ k_project(const TX* __restrict__ X, int64_t n, int d, const int64_t* __restrict_
     for (int g = 0; g < HT / 16; ++g) {
       if (g * 16 >= nh) break;
       uint32_t w[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint32_t v = 0;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int h = g * 16 + q * 4 + b;
-          v |= (uint32_t)region_fast(E + (int64_t)(r0 + h) * (Nr + 1), Ts + h * kRegionRow, Slo[h], Sinv[h],
-                                     acc[h]) << (8 * b);
-        }
-        w[q] = v;
-      }
+      region_codes16(E + (int64_t)(r0 + g * 16) * (Nr + 1), Nr + 1, Ts + g * 16 * kRegionRow, Slo + g * 16,
+                     Sinv + g * 16, acc + g * 16, w);
       const int tree = (r0 + g * 16) / 16;
       *reinterpret_cast<uint4*>(codes + ((int64_t)tree * n + p) * 16) =
           make_uint4(w[0], w[1], w[2], w[3]);
@@ -248,36 +239,24 @@ int launch_project_encode_t(const void* X, int dtype, int64_t n, int d, const fl
 // ---- region search tables
 namespace {
 
-// #{z in 1..Nr-1 : e[z] <= x} for sorted e
-__device__ int count_le(const float* e, int Nr, float x) {
-  int a = 0, b = Nr - 1;
-  while (a < b) {
-    const int m = (a + b + 1) >> 1;
-    if (e[m] <= x) a = m;
-    else b = m - 1;
-  }
-  return a;
-}
-
 __global__ void k_region_tables(const float* __restrict__ E, int Nr, uint8_t* __restrict__ tab,
                                 float* __restrict__ lo_out, float* __restrict__ inv_out) {
   const int h = blockIdx.x;
   const float* e = E + (int64_t)h * (Nr + 1);
   const float lo = e[1], hi = e[Nr - 1];
-  const float w = (hi - lo) / (float)kRegionCells;
-  const float mag = fmaxf(fabsf(lo), fabsf(hi));
-  // cells narrower than 2^-16 of the magnitude are not resolved reliably in FP32
-  const bool fine = w > 0.f && isfinite(w) && w > mag * 1.52587890625e-05f;
+  float inv = (float)kRegionCells / (hi - lo);
+  if (!(inv > 0.f) || !isfinite(inv)) inv = 0.f;
+  // tab[c] = #{z >= 1 : cell(e_z) < c}; cell is non-decreasing in z
   for (int c = threadIdx.x; c < kRegionRow; c += blockDim.x) {
-    int v;
-    if (c == 0) v = 0;
-    else if (!fine || c > kRegionCells) v = Nr - 1;
-    else v = count_le(e, Nr, lo + (float)(c - 1) * w);
+    int v = 0;
+    if (c > kRegionCells) v = Nr - 1;
+    else
+      for (int z = 1; z < Nr; ++z) v += region_cell(lo, inv, e[z]) < c ? 1 : 0;
     tab[(int64_t)h * kRegionRow + c] = (uint8_t)v;
   }
   if (threadIdx.x == 0) {
     lo_out[h] = lo;
-    inv_out[h] = fine ? (float)kRegionCells / (hi - lo) : 0.f;
+    inv_out[h] = inv;
   }
 }
 

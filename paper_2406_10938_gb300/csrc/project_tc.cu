@@ -174,10 +174,24 @@ __host__ __device__ constexpr int tc_aparts() {
   return TF32 ? 2 : (A3 ? 3 : 1);
 }
 // Shared memory bytes of k_project_tc below the breakpoints and tables.
+// (A3 stages also hold the uint8 tile as loaded, TC_M rows of 64 bytes)
 template <int N, bool TF32, bool A3>
 __host__ __device__ constexpr size_t tc_tile_bytes() {
-  return (size_t)tc_stages<TF32, A3>() * ((size_t)TC_M * 128 * (TF32 ? 2 : 1) + (size_t)N * 128 * tc_aparts<TF32, A3>()) +
+  return (size_t)tc_stages<TF32, A3>() * ((size_t)TC_M * 128 * (TF32 ? 2 : 1) + (A3 ? (size_t)TC_M * 64 : 0) +
+                                          (size_t)N * 128 * tc_aparts<TF32, A3>()) +
          (3 * tc_stages<TF32, A3>() + 8) * 8;
+}
+
+// Four uint8 values (one word) to four BF16 values (two words), exactly:
+// 2^23 + u is an FP32 value whose low byte is u, less 2^23 it is u itself,
+// and an integer below 256 keeps its value in BF16's top 16 bits.
+__device__ __forceinline__ void widen4(uint32_t w, uint32_t& lo, uint32_t& hi) {
+  const float f0 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440)) - 8388608.f;
+  const float f1 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7441)) - 8388608.f;
+  const float f2 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7442)) - 8388608.f;
+  const float f3 = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7443)) - 8388608.f;
+  lo = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+  hi = __byte_perm(__float_as_uint(f2), __float_as_uint(f3), 0x7632);
 }
 
 // TF32 mode: X is FP32 and each stage also holds x_small = x - x_big, where
@@ -189,9 +203,11 @@ __host__ __device__ constexpr size_t tc_tile_bytes() {
 // why this path is used for d <= 256 only. Values with at most 11
 // significant bits (the exact-arithmetic inputs) have x_small = 0 and give
 // exact sums.
-// A3 mode: BF16 X (uint8 points, exact in BF16) against A split into three
-// BF16 parts a1 + a2 + a3 (about 24 significant bits, an FP32 value to within
-// 2^-24 of itself): three MMAs per K step.
+// A3 mode: uint8 X against A split into three BF16 parts a1 + a2 + a3 (about
+// 24 significant bits, an FP32 value to within 2^-24 of itself): three MMAs
+// per K step. The uint8 tile arrives by TMA as loaded (64 bytes of a row per
+// stage) and warps 2-3 widen it to BF16 (exact) into the swizzled operand
+// layout, so the points are read from HBM once, one byte per coordinate.
 template <int N, bool ENCODE, bool TF32, bool A3>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA,
@@ -199,8 +215,9 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
   constexpr int S = tc_stages<TF32, A3>();
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned base for the swizzled tiles
-  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                             ~uintptr_t(1023));
+  // (pointer arithmetic on the shared array, so that every access below stays
+  // a shared-memory access rather than a generic one)
+  uint8_t* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   constexpr uint32_t XBYTES = TC_M * 128;
   constexpr uint32_t ABYTES = N * 128;
   constexpr int KC = TF32 ? 32 : 64;                  // d elements per stage (128-byte rows)
@@ -209,7 +226,9 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
   uint8_t* sxs = sa + S * ABYTES;              // [STAGES][XBYTES] x_small (TF32)
   uint8_t* sas = sxs + (TF32 ? S * XBYTES : 0);   // [STAGES][ABYTES] a_small (TF32) or a2 (A3)
   uint8_t* sa3 = sas + ((TF32 || A3) ? S * ABYTES : 0);   // [STAGES][ABYTES] a3 (A3)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sa3 + (A3 ? S * ABYTES : 0));
+  constexpr uint32_t XUBYTES = TC_M * 64;
+  uint8_t* sxu = sa3 + (A3 ? S * ABYTES : 0);     // [STAGES][XUBYTES] uint8 tile (A3)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sxu + (A3 ? S * XUBYTES : 0));
   // full[0..S), empty[S..2S), tfull[2S..2S+2), tempty[2S+2..2S+4), split[2S+4..3S+4)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 4);
   float* Es = reinterpret_cast<float*>(bars + 3 * S + 8);    // [LK][Nr] (ENCODE), e_z at [h][z]
@@ -269,8 +288,8 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
         ok = mbar_wait(smem_u32(&bars[S + s]), (r & 1) ^ 1, err);
         if (!ok) break;
         const uint32_t full = smem_u32(&bars[s]);
-        mbar_expect_tx(full, XBYTES + tc_aparts<TF32, A3>() * ABYTES);
-        tma_load_2d(smem_u32(sx + s * XBYTES), &tmX, kc * KC, (int)(tile * TC_M), full);
+        mbar_expect_tx(full, (A3 ? XUBYTES : XBYTES) + tc_aparts<TF32, A3>() * ABYTES);
+        tma_load_2d(smem_u32(A3 ? sxu + s * XUBYTES : sx + s * XBYTES), &tmX, kc * KC, (int)(tile * TC_M), full);
         tma_load_2d(smem_u32(sa + s * ABYTES), &tmA, kc * KC, 0, full);
         if (TF32 || A3) tma_load_2d(smem_u32(sas + s * ABYTES), &tmA2, kc * KC, 0, full);
         if (A3) tma_load_2d(smem_u32(sa3 + s * ABYTES), &tmA3, kc * KC, 0, full);
@@ -304,6 +323,39 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
         if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + s]));
       }
     }
+  } else if (A3 && (warp == 2 || warp == 3)) {
+    // ---- widening of each staged uint8 tile into the BF16 operand tile:
+    // 16 bytes of row r (elements 16j..16j+15 of the stage) become the 16-byte
+    // chunks 2j and 2j+1 of the 128-byte row, each stored at chunk ^ (r % 8)
+    // (the 128-byte swizzle)
+    const int t = threadIdx.x - 64;   // 0..63
+    uint32_t it = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (int kc = 0; kc < nk && ok; ++kc, ++it) {
+        const uint32_t s = it % S, r = it / S;
+        ok = mbar_wait(smem_u32(&bars[s]), r & 1, err);
+        if (!ok) break;
+        const uint4* src = reinterpret_cast<const uint4*>(sxu + s * XUBYTES);
+        uint8_t* dst = sx + s * XBYTES;
+#pragma unroll 4
+        for (int i = t; i < TC_M * 4; i += 64) {
+          const int row = i >> 2, j = i & 3;
+          const uint4 u = src[i];
+          uint4 lo, hi;
+          widen4(u.x, lo.x, lo.y);
+          widen4(u.y, lo.z, lo.w);
+          widen4(u.z, hi.x, hi.y);
+          widen4(u.w, hi.z, hi.w);
+          uint8_t* drow = dst + row * 128;
+          *reinterpret_cast<uint4*>(drow + (((2 * j) ^ (row & 7)) << 4)) = lo;
+          *reinterpret_cast<uint4*>(drow + (((2 * j + 1) ^ (row & 7)) << 4)) = hi;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + s]));
+      }
+    }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
     constexpr uint32_t ab_fmt = TF32 ? 2u : 1u;   // operand format: BF16 (kind::f16) or TF32
@@ -321,7 +373,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
       const uint32_t dt = tmem + ab * (TCOLS / 2);
       for (int kc = 0; kc < nk; ++kc, ++it) {
         const uint32_t s = it % S, r = it / S;
-        ok = mbar_wait(smem_u32(&bars[TF32 ? 2 * S + 4 + s : s]), r & 1, err);
+        ok = mbar_wait(smem_u32(&bars[(TF32 || A3) ? 2 * S + 4 + s : s]), r & 1, err);
         if (!ok) break;
         tc_fence_after();
         const uint64_t ad = smem_desc(smem_u32(sx + s * XBYTES));
@@ -377,16 +429,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
       if (ENCODE) {
         if (a.K == 16 && g * 16 + 16 <= a.LK) {
           uint32_t wv[4];
-#pragma unroll
-          for (int qq = 0; qq < 4; ++qq) {
-            uint32_t x = 0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              const int c = qq * 4 + b, h = g * 16 + c;
-              x |= (uint32_t)region_fast(Es + h * a.Nr, Ts + h * kRegionRow, Slo[h], Sinv[h], v[c]) << (8 * b);
-            }
-            wv[qq] = x;
-          }
+          region_codes16(Es + g * 16 * a.Nr, a.Nr, Ts + g * 16 * kRegionRow, Slo + g * 16, Sinv + g * 16, v, wv);
           *reinterpret_cast<uint4*>(a.codes + ((int64_t)g * a.rows + p) * 16) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         } else {
 #pragma unroll
@@ -448,22 +491,26 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2-D map of a row-major [rows][d] matrix of BF16 (or FP32), boxes of
-// box_rows rows by 128 bytes, 128-byte swizzle
-int make_map(CUtensorMap* tm, const void* ptr, int64_t rows, int d, int box_rows, bool fp32 = false) {
+enum MapKind { MAP_BF16, MAP_F32, MAP_U8 };
+// 2-D map of a row-major [rows][d] matrix: BF16 or FP32 in boxes of box_rows
+// rows by 128 bytes with the 128-byte swizzle, or uint8 in boxes of box_rows
+// rows by 64 bytes, unswizzled (widened in the kernel)
+int make_map(CUtensorMap* tm, const void* ptr, int64_t rows, int d, int box_rows, MapKind kind = MAP_BF16) {
   auto fn = encode_fn();
   if (!fn) {
     set_error("cuTensorMapEncodeTiled is unavailable");
     return DETLSH_ECUDA;
   }
-  const int esz = fp32 ? 4 : 2;
+  const int esz = kind == MAP_F32 ? 4 : kind == MAP_BF16 ? 2 : 1;
   cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)d * esz};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)(kind == MAP_U8 ? 64 : 128 / esz), (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
-  const CUresult r = fn(tm, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                        const_cast<void*>(ptr), dims, strides, box,
-                        es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  const CUtensorMapDataType dt = kind == MAP_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : kind == MAP_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                    : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  const CUresult r = fn(tm, dt, 2, const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        kind == MAP_U8 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -594,6 +641,32 @@ __global__ void k_gather_rows_f32(const float* __restrict__ x, int d, const int6
 }
 }  // namespace
 
+namespace {
+// rows of a uint8 matrix gathered by id, 16 bytes at a time (d % 16 == 0)
+__global__ void k_gather_rows_u8(const uint4* __restrict__ x, int dv, const int64_t* __restrict__ ids, int64_t m,
+                                 uint4* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m * dv;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / dv, c = i % dv;
+    y[i] = x[ids[r] * dv + c];
+  }
+}
+}  // namespace
+
+int gather_rows_u8(const uint8_t* X, int d, const int64_t* ids, int64_t m, uint8_t* Y, cudaStream_t s) {
+  if (m == 0) return DETLSH_OK;
+  if (d % 16 != 0) {
+    set_error("gather_rows_u8 needs d a multiple of 16");
+    return DETLSH_EINVAL;
+  }
+  const int dv = d / 16;
+  const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(m * dv, 256), 152 * 32);
+  k_gather_rows_u8<<<blocks, 256, 0, s>>>(reinterpret_cast<const uint4*>(X), dv, ids, m,
+                                          reinterpret_cast<uint4*>(Y));
+  DL_LAUNCH();
+  return DETLSH_OK;
+}
+
 int gather_rows_f32(const float* X, int d, const int64_t* ids, int64_t m, float* Y, cudaStream_t s) {
   if (m == 0) return DETLSH_OK;
   const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(m * d, 256), 152 * 32);
@@ -634,21 +707,21 @@ int split_bf16x3(const float* A, int LK, int d, void* Ab3, cudaStream_t s) {
 }
 
 bool bf16x3_eligible(int dtype, int d, int LK) {
-  return dtype == DETLSH_U8 && d % 8 == 0 && d <= 256 && LK <= 64;
+  return dtype == DETLSH_U8 && d % 16 == 0 && d <= 256 && LK <= 64;
 }
 
-int launch_project_bf16x3(const void* Xb, int64_t rows, int d, const void* Ab3, int LK, int K, const float* E,
+int launch_project_bf16x3(const uint8_t* X, int64_t rows, int d, const void* Ab3, int LK, int K, const float* E,
                           const uint8_t* Rtab, const float* Rlo, const float* Rinv, int Nr, uint8_t* codes,
                           float* P, int64_t p_so, int64_t p_sr, int* d_err, cudaStream_t s) {
   if (rows == 0) return DETLSH_OK;
   const int N = (LK + 15) / 16 * 16;
-  if (N > 64 || d % 8 != 0) {
-    set_error("tensor-core projection needs L*K <= 64 and d a multiple of 8");
+  if (!bf16x3_eligible(DETLSH_U8, d, LK)) {
+    set_error("the uint8 tensor-core projection needs L*K <= 64 and d <= 256 a multiple of 16");
     return DETLSH_EINVAL;
   }
   const int64_t nd = (int64_t)N * d;
   CUtensorMap tx, ta, ta2, ta3;
-  DL_TRY(make_map(&tx, Xb, rows, d, TC_M));
+  DL_TRY(make_map(&tx, X, rows, d, TC_M, MAP_U8));
   DL_TRY(make_map(&ta, Ab3, N, d, N));
   DL_TRY(make_map(&ta2, static_cast<const __nv_bfloat16*>(Ab3) + nd, N, d, N));
   DL_TRY(make_map(&ta3, static_cast<const __nv_bfloat16*>(Ab3) + 2 * nd, N, d, N));
@@ -699,9 +772,9 @@ int launch_project_tf32(const float* X, int64_t rows, int d, const float* Asplit
     return DETLSH_EINVAL;
   }
   CUtensorMap tx, ta, ta2;
-  DL_TRY(make_map(&tx, X, rows, d, TC_M, true));
-  DL_TRY(make_map(&ta, Asplit, N, d, N, true));
-  DL_TRY(make_map(&ta2, Asplit + (int64_t)N * d, N, d, N, true));
+  DL_TRY(make_map(&tx, X, rows, d, TC_M, MAP_F32));
+  DL_TRY(make_map(&ta, Asplit, N, d, N, MAP_F32));
+  DL_TRY(make_map(&ta2, Asplit + (int64_t)N * d, N, d, N, MAP_F32));
   TcArgs args{};
   args.rows = rows;
   args.d = d;

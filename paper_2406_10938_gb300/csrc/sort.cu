@@ -99,27 +99,39 @@ k_digit_hist(const uint32_t* __restrict__ keys, int64_t n, int bit, uint32_t* __
   hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = s_h[threadIdx.x];
 }
 
+// Stable scatter of one tile: each item's rank among the equal digits of the
+// tile (in input order: warp match, per-warp counts, a running count per
+// digit) places it in shared memory in digit order, and the tile then leaves
+// as runs of equal digits, consecutive threads writing consecutive outputs.
 __global__ void __launch_bounds__(ST)
 k_digit_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-                int64_t n, int bit, const uint32_t* __restrict__ offs, int64_t n_tiles,
-                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
-  __shared__ uint32_t s_base[256];
+                int64_t n, int bit, const uint32_t* __restrict__ hist, const uint32_t* __restrict__ offs,
+                int64_t n_tiles, uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
+  __shared__ uint32_t s_base[256];     // global output of the tile's first item of each digit
+  __shared__ uint32_t s_lstart[256];   // the tile's first local position of each digit
+  __shared__ uint32_t s_run[256];      // items of each digit placed so far
   __shared__ uint32_t s_wc[NW][256];
+  __shared__ uint32_t s_warp[NW];
+  __shared__ uint32_t s_key[TILE], s_val[TILE];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * TILE;
+  const int tile_n = n - base < TILE ? (int)(n - base) : TILE;
   s_base[threadIdx.x] = offs[(int64_t)threadIdx.x * n_tiles + blockIdx.x];
+  const uint32_t h = hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x];
+  s_lstart[threadIdx.x] = block_exclusive_scan(h, s_warp, nullptr);
+  s_run[threadIdx.x] = 0;
 #pragma unroll
   for (int q = 0; q < NW; ++q) s_wc[q][threadIdx.x] = 0;
   __syncthreads();
   const uint32_t lt = (1u << lane) - 1u;
-  const int64_t base = (int64_t)blockIdx.x * TILE;
   for (int r = 0; r < IPT; ++r) {
-    const int64_t i = base + (int64_t)r * ST + threadIdx.x;
-    const bool valid = i < n;
+    const int li = r * ST + threadIdx.x;
+    const bool valid = li < tile_n;
     uint32_t key = 0, val = 0;
     int digit = 256;
     if (valid) {
-      key = keys_in[i];
-      val = vals_in[i];
+      key = keys_in[base + li];
+      val = vals_in[base + li];
       digit = (int)((key >> bit) & 255u);
     }
     const uint32_t peers = __match_any_sync(0xffffffffu, digit);
@@ -127,10 +139,10 @@ k_digit_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     if (valid && rank_in_warp == 0) s_wc[w][digit] = __popc(peers);
     __syncthreads();
     if (valid) {
-      uint32_t pos = s_base[digit] + rank_in_warp;
+      uint32_t pos = s_lstart[digit] + s_run[digit] + rank_in_warp;
       for (int q = 0; q < w; ++q) pos += s_wc[q][digit];
-      keys_out[pos] = key;
-      vals_out[pos] = val;
+      s_key[pos] = key;
+      s_val[pos] = val;
     }
     __syncthreads();
     uint32_t add = 0;
@@ -139,8 +151,15 @@ k_digit_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
       add += s_wc[q][threadIdx.x];
       s_wc[q][threadIdx.x] = 0;
     }
-    s_base[threadIdx.x] += add;
+    s_run[threadIdx.x] += add;
     __syncthreads();
+  }
+  for (int j = threadIdx.x; j < tile_n; j += ST) {
+    const uint32_t key = s_key[j];
+    const uint32_t d = (key >> bit) & 255u;
+    const uint32_t pos = s_base[d] + (uint32_t)j - s_lstart[d];
+    keys_out[pos] = key;
+    vals_out[pos] = s_val[j];
   }
 }
 
@@ -193,8 +212,8 @@ int radix_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, int64_t n
     k_digit_hist<<<(unsigned)n_tiles, ST, 0, s>>>(ki, n, bit, hist.as<uint32_t>(), n_tiles);
     DL_LAUNCH();
     DL_TRY(exclusive_scan_u32(hist.as<uint32_t>(), offs.as<uint32_t>(), 256 * n_tiles, nullptr, s));
-    k_digit_scatter<<<(unsigned)n_tiles, ST, 0, s>>>(ki, vi, n, bit, offs.as<uint32_t>(), n_tiles,
-                                                     ko, vo);
+    k_digit_scatter<<<(unsigned)n_tiles, ST, 0, s>>>(ki, vi, n, bit, hist.as<uint32_t>(), offs.as<uint32_t>(),
+                                                     n_tiles, ko, vo);
     DL_LAUNCH();
     ki = ko;
     vi = vo;
@@ -296,7 +315,7 @@ int radix_sort_pairs_ws(const uint32_t* keys_in, const uint32_t* vals_in, int64_
     k_digit_hist<<<(unsigned)n_tiles, ST, 0, s>>>(ki, n, bit, hist, n_tiles);
     DL_LAUNCH();
     DL_TRY(exclusive_scan_u32_ws(hist, offs, 256 * n_tiles, nullptr, scan_ws, scan_b, s));
-    k_digit_scatter<<<(unsigned)n_tiles, ST, 0, s>>>(ki, vi, n, bit, offs, n_tiles, ko, vo);
+    k_digit_scatter<<<(unsigned)n_tiles, ST, 0, s>>>(ki, vi, n, bit, hist, offs, n_tiles, ko, vo);
     DL_LAUNCH();
     ki = ko;
     vi = vo;
