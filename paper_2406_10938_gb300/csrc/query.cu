@@ -1112,6 +1112,76 @@ k_dist(const TX* __restrict__ X, int d, const TX* __restrict__ Q, int64_t q0,
   }
 }
 
+// uint8 rows, d a power of two from 16 to 512: d/16 lanes per row, 16 bytes a
+// lane, so one load instruction covers 32/(d/16) rows and a warp keeps eight
+// of them (32 rows at d = 128) in flight. The squared distance is
+// sum x^2 - 2 sum x q + sum q^2 in 32-bit integers (dp4a), exact whatever the
+// order of the sums (at most 512 * 255^2 < 2^31), converted to FP32 once.
+__global__ void __launch_bounds__(DT, 3)
+k_dist_u8(const uint8_t* __restrict__ X, int d, const uint8_t* __restrict__ Q, int64_t q0,
+          const uint32_t* __restrict__ cand, int64_t cap, const uint4* __restrict__ items,
+          const uint32_t* __restrict__ qtail, uint32_t* __restrict__ head, float* __restrict__ d2out) {
+  const uint32_t nit = *qtail;
+  const int lane = threadIdx.x & 31;
+  const int gs = d >> 4;       // lanes per row
+  const int rpl = 32 / gs;     // rows per load instruction
+  const int sub = lane & (gs - 1), grp = lane / gs;
+  uint32_t it = next_item(head, lane);
+  while (it < nit) {
+    const uint4 item = items[it];
+    const uint32_t nx = next_item(head, lane);
+    const int64_t qb = item.x;
+    const int64_t r0 = item.y, r1 = item.z;
+    const uint4 qv = __ldg(reinterpret_cast<const uint4*>(Q + (q0 + qb) * (int64_t)d) + sub);
+    int qsq = (int)(__dp4a(qv.x, qv.x, 0u) + __dp4a(qv.y, qv.y, 0u) + __dp4a(qv.z, qv.z, 0u) +
+                    __dp4a(qv.w, qv.w, 0u));
+    for (int off = gs >> 1; off > 0; off >>= 1) qsq += __shfl_xor_sync(0xffffffffu, qsq, off);
+    const uint32_t* cl = cand + qb * cap;
+    float* out = d2out + qb * cap;
+    for (int64_t e0 = r0; e0 < r1; e0 += 8 * rpl) {
+      uint32_t ids[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t e = e0 + u * rpl + grp;
+        ids[u] = e < r1 ? __ldg(cl + e) : 0xffffffffu;
+      }
+      uint4 xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        xv[u] = ids[u] != 0xffffffffu ? __ldg(reinterpret_cast<const uint4*>(X + (int64_t)ids[u] * d) + sub)
+                                      : make_uint4(0u, 0u, 0u, 0u);
+      int part[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const uint32_t xx = __dp4a(xv[u].x, xv[u].x, __dp4a(xv[u].y, xv[u].y,
+                                   __dp4a(xv[u].z, xv[u].z, __dp4a(xv[u].w, xv[u].w, 0u))));
+        const uint32_t xq = __dp4a(xv[u].x, qv.x, __dp4a(xv[u].y, qv.y,
+                                   __dp4a(xv[u].z, qv.z, __dp4a(xv[u].w, qv.w, 0u))));
+        part[u] = (int)xx - 2 * (int)xq;
+      }
+      for (int off = gs >> 1; off > 0; off >>= 1) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], off);
+      }
+      if (sub == 0) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int64_t e = e0 + u * rpl + grp;
+          if (e < r1) out[e] = (float)(part[u] + qsq);
+        }
+      }
+    }
+    it = nx;
+  }
+}
+
+// k_dist_u8 applies: uint8 rows and queries 16-byte aligned, d in {16, ..., 512}.
+bool dist_u8_eligible(const detlsh_index* idx, const void* Q) {
+  const int d = idx->d;
+  return idx->dtype == DETLSH_U8 && d >= 16 && d <= 512 && (d & (d - 1)) == 0 &&
+         reinterpret_cast<uintptr_t>(idx->X) % 16 == 0 && reinterpret_cast<uintptr_t>(Q) % 16 == 0;
+}
+
 // Coarse squared distances from the BF16 copy of X (FP32 accumulation): half
 // the bytes of the FP32 rows for the same candidates. Each half-warp reads one
 // row with 16-byte loads (8 values per lane, d % 8 == 0), so a warp keeps
@@ -1861,6 +1931,10 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   if (sh.shortlist > 0)
     k_dist_bf16<<<sh.dgrid, DT, 0, s>>>(static_cast<const __nv_bfloat16*>(idx->Xb), idx->d, qf, 0, candb,
                                          sh.cap, items, ctr + CT_QTAIL, ctr + CT_HEAD, d2b);
+  else if (dist_u8_eligible(idx, Q))
+    k_dist_u8<<<sh.dgrid, DT, 0, s>>>(static_cast<const uint8_t*>(idx->X), idx->d,
+                                      static_cast<const uint8_t*>(Q), q0, candb, sh.cap, items,
+                                      ctr + CT_QTAIL, ctr + CT_HEAD, d2b);
   else if (idx->dtype == DETLSH_U8)
     k_dist<uint8_t><<<sh.dgrid, DT, 0, s>>>(static_cast<const uint8_t*>(idx->X), idx->d,
                                              static_cast<const uint8_t*>(Q), q0, candb, sh.cap, items,

@@ -196,6 +196,11 @@ QUERY_CASES = [
     ("tiny", 500, 32, 16, 1, 2, 64, 1, 20, 3, 0.0, 0.0),
     ("mid", 20_000, 128, 16, 4, 256, 2_000, 64, 30, 50, 0.1, 0.0),
     ("serving", 20_000, 128, 16, 4, 256, 2_000, 32, 30, 10, 0.02, 0.0),
+    # uint8 rows with d/16 lanes per row (2 and 32), and a d the integer
+    # distance kernel does not take
+    ("serving", 3_000, 32, 16, 4, 16, 300, 32, 12, 10, 0.1, 0.0),
+    ("serving", 3_000, 512, 16, 4, 16, 300, 32, 12, 10, 0.1, 0.0),
+    ("serving", 3_000, 48, 16, 4, 16, 300, 32, 12, 10, 0.1, 0.0),
 ]
 
 
