@@ -412,13 +412,13 @@ def gpu_arm(args, rank, world, local_rank):
 
 # ------------------------------------------------------------------ batching workload
 BATCHING = dict(name="batching", n=10_000_000, d=96, nq=100_000, K=16, L=4, n_regions=256, n_s=100_000,
-                max_leaf=256, beta=0.01, k_max=100)
+                max_leaf=1024, beta=0.01, k_max=100)
 
 
 def batching_desc():
     return ("batching: n=10,000,000 d=96 fp32 unit vectors, 10,000 clusters on the sphere (Deep-like), "
             f"{BATCHING['nq']:,} queries per step with k~U[1,100] and c in {{1.2,1.5,2.0}}; K=16 L=4 N_r=256 "
-            "n_s=1% max_leaf=256 beta=0.01 (recall@k >= 0.9); index built once before the timed steps")
+            "n_s=1% max_leaf=1024 beta=0.01 (recall@k >= 0.9); index built once before the timed steps")
 
 
 def batching_arm(args, rank, world, local_rank):
@@ -662,14 +662,14 @@ def precision_arm(args, rank, world, local_rank):
 
 # ------------------------------------------------------------------ serving workload
 SERVING = dict(name="serving", n=100_000_000, d=128, nq=20_000, K=16, L=4, n_regions=256, n_s=1_000_000,
-               max_leaf=256, k_max=100, betas=(1e-3, 2e-3, 5e-3, 1e-2, 2e-2, 5e-2),
+               max_leaf=1024, k_max=100, betas=(1e-3, 1.5e-3, 2e-3, 2.5e-3, 3e-3, 4e-3, 5e-3, 1e-2, 2e-2, 5e-2),
                rates=(5_000, 20_000, 50_000, 100_000, 200_000))
 
 
 def serving_desc():
     return ("serving: n=100,000,000 d=128 uint8 Gaussian mixture of 1,000 clusters (12.8 GB, widened in the "
             "kernels), Poisson arrivals through the continuous-batching server, k in {1,10,100}, c in "
-            "{1.2,1.5,2.0}; K=16 L=4 N_r=256 n_s=1% max_leaf=256; beta = the smallest of "
+            "{1.2,1.5,2.0}; K=16 L=4 N_r=256 n_s=1% max_leaf=1024; beta = the smallest of "
             f"{SERVING['betas']} with recall@10 >= 0.9 on 200 queries")
 
 
