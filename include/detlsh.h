@@ -57,6 +57,12 @@ typedef enum {
 #define DETLSH_BORROW_X 1  /* with DETLSH_MEM_DEVICE: keep a reference to the
                               caller's X instead of copying it; X must then
                               stay alive and unchanged until detlsh_free */
+#define DETLSH_DEDUP_POS 2 /* index the query walk's duplicate test by each
+                              point's position in the first tree's leaf order
+                              (4*L bytes more per point). Chosen automatically
+                              when the walk's per-CTA bitmaps of n bits do not
+                              fit in L2 together; results are the same either
+                              way. */
 
 typedef struct detlsh_index detlsh_index;
 
@@ -69,7 +75,7 @@ typedef struct {
   int32_t max_leaf;   /* max_size of Alg. 3 (>= 1)                         */
   int64_t n_s;        /* sample size: number of entries in sample_ids      */
   int32_t proj_mode;  /* detlsh_proj_mode                                  */
-  int32_t flags;      /* DETLSH_BORROW_X or 0                              */
+  int32_t flags;      /* DETLSH_BORROW_X | DETLSH_DEDUP_POS, or 0          */
 } detlsh_params;
 
 /* Launch shapes of the query pipeline (no counterpart in the paper). The

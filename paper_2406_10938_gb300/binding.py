@@ -19,6 +19,7 @@ from .build_lib import LIB
 F32, U8 = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 BORROW_X = 1
+DEDUP_POS = 2
 EXPORT = {"A": 0, "EDGES": 1, "CODES": 2, "LEAF_IDS": 3, "LEAF_BASE": 4, "LEAF_RANGE": 5,
           "LEAF_PLEN": 6, "LEAF_PREFIX": 7, "SAMPLE_PROJ": 8}
 _EXPORT_DTYPE = {"A": torch.float32, "EDGES": torch.float32, "CODES": torch.uint8,
@@ -219,18 +220,19 @@ PROJ_FP32, PROJ_BF16 = 0, 1
 
 
 def detlsh_build(X: torch.Tensor, A: torch.Tensor, sample_ids: torch.Tensor, K: int, L: int,
-                 n_regions: int, max_leaf: int, borrow: bool = False, proj_mode: int = 0) -> Index:
+                 n_regions: int, max_leaf: int, borrow: bool = False, proj_mode: int = 0,
+                 dedup_pos: bool = False) -> Index:
     X = X.contiguous()
     A = A.contiguous().to(torch.float32)
     sample_ids = sample_ids.contiguous().to(torch.int64)
     mem = _mem_of(X, A, sample_ids)
     p = Params(K=K, L=L, n_regions=n_regions, max_leaf=max_leaf, n_s=sample_ids.numel(), proj_mode=proj_mode,
-               flags=BORROW_X if (borrow and mem == MEM_DEVICE) else 0)
+               flags=(BORROW_X if (borrow and mem == MEM_DEVICE) else 0) | (DEDUP_POS if dedup_pos else 0))
     out = ctypes.c_void_p(0)
     st = lib().detlsh_build(_ptr(X), X.shape[0], X.shape[1], _dtype_code(X), _ptr(A), _ptr(sample_ids),
                             ctypes.byref(p), mem, _stream(mem), ctypes.byref(out))
     _check(st, "detlsh_build")
-    return Index(out.value, keep=X if p.flags else None)
+    return Index(out.value, keep=X if p.flags & BORROW_X else None)
 
 
 def _per_query(v, nq, dtype, dev):

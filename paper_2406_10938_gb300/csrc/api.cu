@@ -164,7 +164,7 @@ int check_flag(int* d_bad, cudaStream_t s, const char* what) {
 void free_index(detlsh_index* idx) {
   if (!idx) return;
   if (idx->owns_x && idx->X) cudaFree(const_cast<void*>(idx->X));
-  void* arrays[] = {idx->A, idx->At, idx->E, idx->Ps, idx->codes, idx->leaf_ids, idx->leaf_base,
+  void* arrays[] = {idx->A, idx->At, idx->E, idx->Ps, idx->codes, idx->leaf_ids, idx->leaf_pos, idx->leaf_base,
                     idx->leaf_range, idx->leaf_plen, idx->leaf_prefix, idx->leaf_lo, idx->leaf_hi,
                     idx->leaf_tree, idx->Xb, idx->Ab, idx->d_err, idx->Rtab, idx->Rlo, idx->Rinv, idx->Atf, idx->Ab3};
   for (void* p : arrays)
@@ -187,6 +187,7 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
   idx->max_leaf = prm->max_leaf;
   idx->n_s = prm->n_s;
   idx->proj_mode = prm->proj_mode;
+  idx->flags = prm->flags;
   DL_CUDA(cudaGetDevice(&idx->device));
 
   const size_t xbytes = (size_t)n * d * dtype_size(dtype);
@@ -440,6 +441,7 @@ int detlsh_build(const void* X, int64_t n, int32_t d, int32_t dtype, const float
   DL_REQUIRE(n >= 1 && n * (int64_t)p.L < ((int64_t)1 << 32), "need 1 <= n and n*L < 2^32");
   DL_REQUIRE(p.n_s >= p.n_regions && p.n_s <= n, "need n_regions <= n_s <= n");
   DL_REQUIRE(p.proj_mode == DETLSH_PROJ_FP32 || p.proj_mode == DETLSH_PROJ_BF16, "unsupported proj_mode");
+  DL_REQUIRE((p.flags & ~(DETLSH_BORROW_X | DETLSH_DEDUP_POS)) == 0, "unknown flags");
   DL_REQUIRE(p.proj_mode != DETLSH_PROJ_BF16 || (d % 8 == 0 && p.K * p.L <= 64),
              "the BF16 projection needs d %% 8 == 0 and L*K <= 64");
   DL_REQUIRE(p.n_s * (int64_t)p.K * p.L < ((int64_t)1 << 32), "n_s*L*K must be < 2^32");

@@ -135,6 +135,7 @@ struct detlsh_index {
   int64_t n_s = 0;
   int32_t device = 0;
   int32_t proj_mode = 0;
+  int32_t flags = 0;                // detlsh_params.flags of the build
   void* Xb = nullptr;               // [n][d] BF16 copy of X (BF16 projection mode)
   void* Ab = nullptr;               // [N][d] BF16 hash vectors, N = L*K rounded up to 16
   float* Atf = nullptr;             // [2][N][d] TF32 split of A (FP32 mode on the tensor cores)
@@ -151,6 +152,8 @@ struct detlsh_index {
   float* Ps = nullptr;              // [LK][n_s]
   uint8_t* codes = nullptr;         // [L][n][K]
   uint32_t* leaf_ids = nullptr;     // [L][n]
+  uint32_t* leaf_pos = nullptr;     // [L][n] each entry's point as its position in tree 0's leaf order
+                                    // (built for large n only: the walk's dedup bitmap index)
   int64_t* leaf_base = nullptr;     // [L+1]
   uint32_t* leaf_range = nullptr;   // [total][2] (start within tree, count)
   uint8_t* leaf_plen = nullptr;     // [total][K]
@@ -329,7 +332,7 @@ struct QueryShape {
   bool smem_bitmap;
   size_t wl_total, bk_smem, bp_smem, bytes;
   size_t o_ctr, o_qp, o_qb16, o_qf, o_lb, o_mm, o_lround, o_hist, o_boff, o_list, o_cand, o_d2,
-      o_rend, o_thr, o_meta, o_wsnew, o_wsbm, o_items, o_qk, o_qsort, qsort_bytes, o_hcnt, o_hcta;
+      o_rend, o_thr, o_meta, o_wsnew, o_wsbm, o_wspos, o_items, o_qk, o_qsort, qsort_bytes, o_hcnt, o_hcta;
 };
 
 // control words of a batch (uint32, at QueryShape::o_ctr): queries in the

@@ -558,6 +558,19 @@ __global__ void k_emit(const uint32_t* __restrict__ tiles_needed, const uint32_t
   }
 }
 
+// ---- dedup positions: pos0[p] = position of point p in tree 0's leaf order,
+// then every entry of every tree mapped through it
+__global__ void k_pos0(const uint32_t* __restrict__ ids0, int64_t n, uint32_t* __restrict__ pos0) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    pos0[ids0[j]] = (uint32_t)j;
+}
+__global__ void k_leaf_pos(const uint32_t* __restrict__ ids, int64_t total, const uint32_t* __restrict__ pos0,
+                           uint32_t* __restrict__ pos) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < total;
+       j += (int64_t)gridDim.x * blockDim.x)
+    pos[j] = pos0[ids[j]];
+}
+
 // ---- leaf table
 __global__ void k_finalize(const uint32_t* __restrict__ seg_start, const uint32_t* __restrict__ seg_count,
                            const uint4* __restrict__ seg_plen, const uint4* __restrict__ seg_prefix,
@@ -824,6 +837,24 @@ int build_leaves(detlsh_index* idx, cudaStream_t s) {
   DL_CUDA(cudaMemcpyAsync(&mx, d_max.p, sizeof(mx), cudaMemcpyDeviceToHost, s));
   DL_CUDA(cudaStreamSynchronize(s));
   idx->max_leaf_count = (int64_t)mx;
+  // When the walk CTAs' dedup bitmaps (n bits each, about three CTAs per SM)
+  // do not fit in L2 together, the bitmap is indexed by tree-0 leaf position,
+  // so that the points of one query's leaves set neighbouring bits instead of
+  // bits spread over the whole id range.
+  int dev = 0, nsm = 0, l2 = 0;
+  DL_CUDA(cudaGetDevice(&dev));
+  DL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  DL_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+  if ((idx->flags & DETLSH_DEDUP_POS) || (n + 7) / 8 * 3 * (int64_t)nsm > (int64_t)l2) {
+    Scratch pos0;
+    DL_TRY(pos0.alloc(sizeof(uint32_t) * n, s));
+    DL_CUDA(cudaMalloc(&idx->leaf_pos, sizeof(uint32_t) * total));
+    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 32);
+    k_pos0<<<g, 256, 0, s>>>(idx->leaf_ids, n, pos0.as<uint32_t>());
+    DL_LAUNCH();
+    k_leaf_pos<<<g, 256, 0, s>>>(idx->leaf_ids, total, pos0.as<uint32_t>(), idx->leaf_pos);
+    DL_LAUNCH();
+  }
   return DETLSH_OK;
 }
 

@@ -491,6 +491,9 @@ struct WalkArgs {
   uint32_t* ws_newcnt;        // [grid][3][max_bucket] new counts, lower-bound bits, leaf sizes
   int64_t max_bucket;         // most leaves a (round, tree) bucket can hold
   uint32_t* ws_bitmap;        // [grid][bitmap_words] when not in shared memory
+  uint32_t* ws_pos;           // [grid][cap] bitmap positions of the query's candidates (global bitmap)
+  const uint32_t* leaf_pos;   // [L][n] tree-0 leaf position of each entry's point (the bitmap
+                              // index), or null: the point id is the index
   int64_t bitmap_words;
   int smem_bitmap;
   uint32_t* work;             // query counter, zero at launch
@@ -535,6 +538,8 @@ enum { W_S = 0, W_STOP, W_NEED, W_KSTAR, W_ACC, W_TOTNEW, W_QN, W_LEAFA, W_OFFA,
 // With count_only the bitmap is only read: newcnt[j] receives the number of
 // points of leaf list[j] not yet in S, lbk[j] its lower-bound bits, and
 // misc[W_TOTNEW] their total.
+// POS: the bitmap is indexed by a.leaf_pos (tree-0 leaf positions) instead of point ids.
+template <bool POS>
 __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, bool filtered,
                          unsigned long long kstar, const float* lbrow, unsigned char* sm,
                          const WalkLayout& ly, uint32_t* bitmap, uint32_t* cand,
@@ -624,24 +629,33 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
     __syncthreads();
     const unsigned long long S0 = misc[W_S];
     for (uint32_t f0 = 0; f0 < take_pts; f0 += WT * WILP) {
-      uint32_t ids[WILP];
+      // ids[u]: the point (appended to the list); bp[u]: its bit in the bitmap
+      uint32_t ids[WILP], bp[WILP];
 #pragma unroll
       for (int u = 0; u < WILP; ++u) {
         const uint32_t f = f0 + u * WT + threadIdx.x;
         ids[u] = 0xffffffffu;
+        bp[u] = 0xffffffffu;
         if (f < take_pts) {
           const uint32_t j = fmap[f];
-          ids[u] = __ldg(a.leaf_ids + bstart[j] + (f - bpref[j]));
+          const int64_t e = bstart[j] + (f - bpref[j]);
+          if (POS) {
+            bp[u] = __ldg(a.leaf_pos + e);
+            if (!count_only) ids[u] = __ldg(a.leaf_ids + e);
+          } else {
+            ids[u] = __ldg(a.leaf_ids + e);
+            bp[u] = ids[u];
+          }
         }
       }
       if (count_only) {
         uint32_t word[WILP];
 #pragma unroll
-        for (int u = 0; u < WILP; ++u) word[u] = ids[u] != 0xffffffffu ? bitmap[ids[u] >> 5] : 0xffffffffu;
+        for (int u = 0; u < WILP; ++u) word[u] = bp[u] != 0xffffffffu ? bitmap[bp[u] >> 5] : 0xffffffffu;
 #pragma unroll
         for (int u = 0; u < WILP; ++u) {
           const uint32_t f = f0 + u * WT + threadIdx.x;
-          const uint32_t id = ids[u];
+          const uint32_t id = bp[u];
           const bool fresh = id != 0xffffffffu && !((word[u] >> (id & 31)) & 1u);
           const uint32_t key = fresh ? (uint32_t)fmap[f] : 0xffffffffu;
           const uint32_t peers = __match_any_sync(0xffffffffu, key);
@@ -655,11 +669,11 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
       uint32_t old[WILP];
 #pragma unroll
       for (int u = 0; u < WILP; ++u)
-        old[u] = ids[u] != 0xffffffffu ? atomicOr(bitmap + (ids[u] >> 5), 1u << (ids[u] & 31)) : 0xffffffffu;
+        old[u] = bp[u] != 0xffffffffu ? atomicOr(bitmap + (bp[u] >> 5), 1u << (bp[u] & 31)) : 0xffffffffu;
       uint32_t fm[WILP], tot = 0;
 #pragma unroll
       for (int u = 0; u < WILP; ++u) {
-        const bool fresh = ids[u] != 0xffffffffu && !((old[u] >> (ids[u] & 31)) & 1u);
+        const bool fresh = bp[u] != 0xffffffffu && !((old[u] >> (bp[u] & 31)) & 1u);
         fm[u] = __ballot_sync(0xffffffffu, fresh);
         tot += __popc(fm[u]);
       }
@@ -670,8 +684,12 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
       for (int u = 0; u < WILP; ++u) {
         if ((fm[u] >> lane) & 1u) {
           const unsigned long long pos = S0 + base + __popc(fm[u] & lt);
-          if ((int64_t)pos < a.cap) cand[pos] = ids[u];
-          else misc[W_OVF] = 1;
+          if ((int64_t)pos < a.cap) {
+            cand[pos] = ids[u];
+            if (POS && !a.smem_bitmap) a.ws_pos[(int64_t)blockIdx.x * a.cap + pos] = bp[u];
+          } else {
+            misc[W_OVF] = 1;
+          }
         }
         base += __popc(fm[u]);
       }
@@ -820,6 +838,7 @@ __device__ unsigned long long select_key(const uint32_t* bl, const uint32_t* lbk
 }
 
 // One CTA per query (persistent over the batch): the buckets in Alg. 7 order.
+template <bool POS>
 __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
   const WalkLayout ly = walk_layout(a.L, a.smem_bitmap ? a.bitmap_words : 0);
@@ -876,7 +895,7 @@ __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
       const bool whole_round = misc[W_S] + rpts < T;
       if (whole_round) {
         const uint32_t nl = s_boff[(t + 1) * L] - s_boff[t * L];
-        if (nl) walk_add(a, list + s_boff[t * L], nl, false, ~0ull, lbrow, sm, ly, bitmap, cand);
+        if (nl) walk_add<POS>(a, list + s_boff[t * L], nl, false, ~0ull, lbrow, sm, ly, bitmap, cand);
       }
       for (int i = 0; i < L && !whole_round; ++i) {
         const int b = t * L + i;
@@ -886,7 +905,7 @@ __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
         const unsigned long long bpts = s_pts[b];   // all of the bucket's points
         bool cut = false;
         if (misc[W_S] + bpts < T) {
-          walk_add(a, bl, nl, false, ~0ull, lbrow, sm, ly, bitmap, cand);
+          walk_add<POS>(a, bl, nl, false, ~0ull, lbrow, sm, ly, bitmap, cand);
         } else {
           // the bucket may hold the cut: its leaves in key order (lower bound,
           // leaf) are taken in chunks of about twice the points still needed
@@ -907,14 +926,14 @@ __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
             const unsigned long long need = T - S0;
             const unsigned long long kc =
                 select_key(bl, lbk, tcnt, nl, has_kmin, kmin, 2 * need, sel, misc);
-            walk_add(a, bl, nl, true, kc, lbrow, sm, ly, bitmap, cand, true, newcnt, lbk, has_kmin, kmin);
+            walk_add<POS>(a, bl, nl, true, kc, lbrow, sm, ly, bitmap, cand, true, newcnt, lbk, has_kmin, kmin);
             if (S0 + misc[W_TOTNEW] >= T) {
               const unsigned long long kstar = select_key(bl, lbk, newcnt, nl, has_kmin, kmin, need, sel, misc);
-              walk_add(a, bl, nl, true, kstar, lbrow, sm, ly, bitmap, cand, false, nullptr, nullptr, has_kmin, kmin);
+              walk_add<POS>(a, bl, nl, true, kstar, lbrow, sm, ly, bitmap, cand, false, nullptr, nullptr, has_kmin, kmin);
               cut = true;
               break;
             }
-            walk_add(a, bl, nl, true, kc, lbrow, sm, ly, bitmap, cand, false, nullptr, nullptr, has_kmin, kmin);
+            walk_add<POS>(a, bl, nl, true, kc, lbrow, sm, ly, bitmap, cand, false, nullptr, nullptr, has_kmin, kmin);
             if (kc == ~0ull) break;   // the bucket is exhausted without a cut
             has_kmin = true;
             kmin = kc;
@@ -963,7 +982,8 @@ __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
       // holds every set bit and is much shorter than the bitmap
       const unsigned long long S = misc[W_S];
       if (!misc[W_OVF] && (int64_t)S * 8 < a.bitmap_words) {
-        for (unsigned long long p = threadIdx.x; p < S; p += WT) bitmap[cand[p] >> 5] = 0u;
+        const uint32_t* bpl = POS ? a.ws_pos + (int64_t)blockIdx.x * a.cap : cand;
+        for (unsigned long long p = threadIdx.x; p < S; p += WT) bitmap[bpl[p] >> 5] = 0u;
       } else {
         for (int64_t i = threadIdx.x; i < a.bitmap_words; i += WT) bitmap[i] = 0u;
       }
@@ -1692,9 +1712,10 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
     return DETLSH_EINVAL;
   }
   sh.wl_total = wl.total;
-  DL_CUDA(cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wl.total));
+  DL_CUDA(cudaFuncSetAttribute(k_walk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wl.total));
+  DL_CUDA(cudaFuncSetAttribute(k_walk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wl.total));
   int walk_per_sm = 0;
-  DL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&walk_per_sm, k_walk, WT, wl.total));
+  DL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&walk_per_sm, k_walk<false>, WT, wl.total));
   walk_per_sm = std::max(walk_per_sm, 1);
   if (tu.walk_ctas_per_sm > 0) walk_per_sm = std::min(walk_per_sm, tu.walk_ctas_per_sm);
   sh.dgrid = nsm * (tu.dist_ctas_per_sm ? tu.dist_ctas_per_sm : 3);
@@ -1768,6 +1789,7 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   sh.o_meta = take(sizeof(uint32_t) * B * MQ_WORDS);
   sh.o_wsnew = take(sizeof(uint32_t) * 3 * sh.wgrid * max_tree_leaves);
   sh.o_wsbm = take(sh.smem_bitmap ? 0 : sizeof(uint32_t) * sh.wgrid * sh.words);
+  sh.o_wspos = take(sh.smem_bitmap || !idx->leaf_pos ? 0 : sizeof(uint32_t) * sh.wgrid * sh.cap);
   sh.o_items = take(sizeof(uint4) * B * sh.items_per_q);
   sh.o_qk = take(sizeof(uint32_t) * 4 * B);
   sh.qsort_bytes = radix_ws_bytes(B, 0, 32);
@@ -1915,6 +1937,8 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   wa.ws_newcnt = reinterpret_cast<uint32_t*>(b + sh.o_wsnew);
   wa.max_bucket = sh.max_tree_leaves;
   wa.ws_bitmap = sh.smem_bitmap ? nullptr : reinterpret_cast<uint32_t*>(b + sh.o_wsbm);
+  wa.ws_pos = sh.smem_bitmap || !idx->leaf_pos ? nullptr : reinterpret_cast<uint32_t*>(b + sh.o_wspos);
+  wa.leaf_pos = idx->leaf_pos;
   wa.bitmap_words = sh.words;
   wa.smem_bitmap = sh.smem_bitmap ? 1 : 0;
   wa.work = ctr + CT_WORK;
@@ -1923,7 +1947,10 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   wa.qtail = ctr + CT_QTAIL;
   wa.dist_rows = sh.dist_rows;
   tm.begin(TR_WALK);
-  k_walk<<<(unsigned)std::min<int64_t>(nqg, sh.wgrid), WT, sh.wl_total, s>>>(wa);
+  if (idx->leaf_pos)
+    k_walk<true><<<(unsigned)std::min<int64_t>(nqg, sh.wgrid), WT, sh.wl_total, s>>>(wa);
+  else
+    k_walk<false><<<(unsigned)std::min<int64_t>(nqg, sh.wgrid), WT, sh.wl_total, s>>>(wa);
   DL_LAUNCH();
   tm.end();
 

@@ -234,6 +234,38 @@ def test_query_exact_bit_parity(case):
     idx.free()
 
 
+@pytest.mark.parametrize("case", [QUERY_CASES[0], QUERY_CASES[3], QUERY_CASES[6], QUERY_CASES[7]])
+def test_query_dedup_by_leaf_position_same_results(case):
+    """The walk's duplicate test indexed by tree-0 leaf position (the layout
+    large indexes get) gives the same candidates and results as by point id,
+    and the oracle's on the first queries."""
+    name, n, d, K, L, Nr, n_s, max_leaf, nq, k, beta, r_min = case
+    X, Q, A, ids = _exact_inputs(name, n, d, K, L, n_s, nq=nq)
+    eps = O.eps_from_lemma3(K, L)
+    g = torch.Generator().manual_seed(nq + 1)
+    cs = torch.tensor([1.2, 1.5, 2.0])[torch.randint(0, 3, (nq,), generator=g)]
+    ks = torch.randint(1, k + 1, (nq,), generator=g, dtype=torch.int32)
+    rm = torch.full((nq,), r_min, dtype=torch.float32)
+    outs = []
+    for pos in (False, True):
+        idx = pkg.detlsh_build(X.to(DEV), A.to(DEV), ids.to(DEV), K, L, Nr, max_leaf, dedup_pos=pos)
+        o = pkg.detlsh_query(idx, Q.to(DEV), ks.to(DEV), cs.to(DEV), rm.to(DEV), k_max=k, eps=eps, beta=beta,
+                             cand_cap=n)
+        outs.append([t.cpu() for t in o])
+        idx.free()
+    (i0, d0, s0, c0), (i1, d1, s1, c1) = outs
+    assert torch.equal(i0, i1) and torch.equal(d0, d1) and torch.equal(s0, s1)
+    for qi in range(nq):
+        m = int(s0[qi, 0])
+        assert torch.equal(torch.sort(c0[qi, :m])[0], torch.sort(c1[qi, :m])[0]), qi
+    ref = O.build_index(X.numpy(), A.numpy(), ids.numpy(), K, L, Nr, max_leaf)
+    res = oracle_queries(ref, Q.numpy()[:3], ks.numpy()[:3], cs.numpy()[:3], rm.numpy()[:3], eps, beta)
+    for qi, r in enumerate(res):
+        kq = int(ks[qi])
+        assert np.array_equal(i1.numpy()[qi, :kq], r.ids[:kq]), qi
+        assert int(s1[qi, 0]) == r.n_cand
+
+
 # ------------------------------------------------------------------ query, float inputs
 @pytest.mark.parametrize("name,n,d,Nr,n_s,nq,k", [("tiny", 10_000, 32, 16, 1_000, 100, 10),
                                                   ("batching", 30_000, 96, 256, 3_000, 24, 50),
