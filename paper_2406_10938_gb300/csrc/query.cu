@@ -47,7 +47,7 @@ namespace {
 
 // ------------------------------------------------------------------ lower bounds
 constexpr int LB_THREADS = 256;
-constexpr int LB_QCH = 32;
+constexpr int LB_QCH = 128;   // queries per lower-bound CTA (their q' rows staged in shared memory)
 
 // Packed FP32 pair arithmetic (two independent IEEE round-to-nearest
 // operations per instruction) and a three-input maximum.
@@ -81,7 +81,10 @@ k_leaf_lb(const float* __restrict__ qp, const uint32_t* __restrict__ nqd, int LK
           int K, const uint8_t* __restrict__ leaf_lo, const uint8_t* __restrict__ leaf_hi,
           const uint16_t* __restrict__ leaf_tree, int64_t total_leaves, float* __restrict__ lb2,
           uint32_t* __restrict__ minpos, uint32_t* __restrict__ maxlb) {
-  __shared__ __align__(16) float s_q[LB_QCH][kMaxLK + 2];
+  // q' rows of the CTA's queries, LKP = L*K rounded up to even, + 2 floats
+  // apart (every row starts 8-byte aligned)
+  extern __shared__ __align__(16) float s_qrows[];
+  const int LKP = (LK + 1) / 2 * 2 + 2;
   __shared__ uint32_t s_min[LB_QCH], s_max[LB_QCH];
   const int64_t leaf = (int64_t)blockIdx.x * LB_THREADS + threadIdx.x;
   const int64_t qb0 = (int64_t)blockIdx.y * LB_QCH;
@@ -90,7 +93,7 @@ k_leaf_lb(const float* __restrict__ qp, const uint32_t* __restrict__ nqd, int LK
   const int nqc = (int)((nqb - qb0) < LB_QCH ? (nqb - qb0) : LB_QCH);
   for (int i = threadIdx.x; i < nqc * LK; i += LB_THREADS) {
     const int q = i / LK, r = i % LK;
-    s_q[q][r] = qp[(qb0 + q) * LK + r];
+    s_qrows[q * LKP + r] = qp[(qb0 + q) * LK + r];
   }
   if (threadIdx.x < LB_QCH) {
     s_min[threadIdx.x] = 0xffffffffu;
@@ -118,11 +121,11 @@ k_leaf_lb(const float* __restrict__ qp, const uint32_t* __restrict__ nqd, int LK
     eh2[j] = pack2(eh[2 * j], eh[2 * j + 1]);
   }
   const int rbase = tree * K;
-  const bool paired = (rbase % 2) == 0;   // s_q row offsets of an even base are 8-byte aligned
+  const bool paired = (rbase % 2) == 0;   // q' rows at an even base are 8-byte aligned
   for (int q = 0; q < nqc; ++q) {
     float acc = 0.f;
     if (paired) {
-      const float* xq = &s_q[q][rbase];
+      const float* xq = s_qrows + q * LKP + rbase;
 #pragma unroll
       for (int j = 0; j < kMaxK; j += 2) {
         if (j + 1 < K) {
@@ -142,7 +145,7 @@ k_leaf_lb(const float* __restrict__ qp, const uint32_t* __restrict__ nqd, int LK
 #pragma unroll
       for (int j = 0; j < kMaxK; ++j) {
         if (j < K) {
-          const float x = s_q[q][rbase + j];
+          const float x = s_qrows[q * LKP + rbase + j];
           const float dl = max3f(__fsub_rn(el[j], x), __fsub_rn(x, eh[j]), 0.f);
           acc = __fadd_rn(acc, __fmul_rn(dl, dl));
         }
@@ -165,6 +168,9 @@ k_leaf_lb(const float* __restrict__ qp, const uint32_t* __restrict__ nqd, int LK
     atomicMax(&maxlb[qb0 + threadIdx.x], s_max[threadIdx.x]);
   }
 }
+
+// dynamic shared memory of k_leaf_lb for L*K projected dimensions
+size_t lb_smem_bytes(int LK) { return sizeof(float) * LB_QCH * (size_t)((LK + 1) / 2 * 2 + 2); }
 
 // index of the first element >= v in a non-decreasing array (n if none)
 __device__ __forceinline__ int lower_bound_f(const float* a, int n, float v) {
@@ -1712,6 +1718,7 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
     return DETLSH_EINVAL;
   }
   sh.wl_total = wl.total;
+  DL_CUDA(cudaFuncSetAttribute(k_leaf_lb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lb_smem_bytes(sh.LK)));
   DL_CUDA(cudaFuncSetAttribute(k_walk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wl.total));
   DL_CUDA(cudaFuncSetAttribute(k_walk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wl.total));
   int walk_per_sm = 0;
@@ -1888,7 +1895,7 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
 
   dim3 g1(ceil_div(TL, LB_THREADS), ceil_div(nqg, LB_QCH));
   tm.begin(TR_LB);
-  k_leaf_lb<<<g1, LB_THREADS, 0, s>>>(qp, nqd, LK, idx->E, idx->Nr, idx->K, idx->leaf_lo, idx->leaf_hi,
+  k_leaf_lb<<<g1, LB_THREADS, lb_smem_bytes(LK), s>>>(qp, nqd, LK, idx->E, idx->Nr, idx->K, idx->leaf_lo, idx->leaf_hi,
                                       idx->leaf_tree, TL, lb, d_min, d_max);
   DL_LAUNCH();
   tm.end();
