@@ -84,7 +84,7 @@ typedef struct {
 typedef struct {
   int64_t batch;             /* queries per batch (0: sized from free device memory,
                                 at most 16384)                                   */
-  int32_t walk_ctas_per_sm;  /* bucket-walk CTAs per SM, 1..3 (0: as many as fit)  */
+  int32_t walk_ctas_per_sm;  /* bucket-walk CTAs per SM, 1..4 (0: as many as fit)  */
   int32_t dist_rows;         /* candidate rows per distance work item, a multiple
                                 of 64 in [64, 8192] (0: 1024)                     */
   int32_t dist_ctas_per_sm;  /* persistent distance CTAs per SM, 1..3 (0: 3)       */

@@ -600,7 +600,7 @@ int detlsh_autotune(const detlsh_index* idx, const void* Q, int64_t nq, int32_t 
       st = r;
     }
   };
-  for (int w : {1, 2, 3}) {
+  for (int w : {1, 2, 3, 4}) {
     QueryTuning t = best;
     t.walk_ctas_per_sm = w;
     attempt(t);

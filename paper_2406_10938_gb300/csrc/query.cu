@@ -845,7 +845,7 @@ __device__ unsigned long long select_key(const uint32_t* bl, const uint32_t* lbk
 
 // One CTA per query (persistent over the batch): the buckets in Alg. 7 order.
 template <bool POS>
-__global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
+__global__ void __launch_bounds__(WT, 4) k_walk(WalkArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
   const WalkLayout ly = walk_layout(a.L, a.smem_bitmap ? a.bitmap_words : 0);
   uint32_t* s_boff = reinterpret_cast<uint32_t*>(sm + ly.boff);
@@ -1687,9 +1687,9 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
     set_error("dist_rows must be a multiple of 64 in [64, 8192]");
     return DETLSH_EINVAL;
   }
-  if (tu.walk_ctas_per_sm < 0 || tu.walk_ctas_per_sm > 3 || tu.dist_ctas_per_sm < 0 ||
+  if (tu.walk_ctas_per_sm < 0 || tu.walk_ctas_per_sm > 4 || tu.dist_ctas_per_sm < 0 ||
       tu.dist_ctas_per_sm > 3 || tu.batch < 0 || tu.streams < 0 || tu.streams > 2) {
-    set_error("walk_ctas_per_sm and dist_ctas_per_sm must be in [0, 3], streams in [0, 2], batch >= 0");
+    set_error("walk_ctas_per_sm must be in [0, 4], dist_ctas_per_sm in [0, 3], streams in [0, 2], batch >= 0");
     return DETLSH_EINVAL;
   }
   sh.L = idx->L;

@@ -140,7 +140,7 @@ def test_tuning_rejects_bad_shapes():
 def test_autotune_fp32_index():
     X, Q, A, ids, ks, cs, idx = _case("mid", n=20_000, d=128, Nr=256, n_s=2_000, max_leaf=64, nq=300, k=50)
     t = pkg.detlsh_autotune(idx, Q.to(DEV), ks.to(DEV), cs.to(DEV), 0.0, k_max=50, beta=0.1, min_agreement=0.99)
-    assert t["walk_ctas_per_sm"] in (0, 1, 2, 3)
+    assert t["walk_ctas_per_sm"] in (0, 1, 2, 3, 4)
     assert t["dist_rows"] % 64 == 0 and 64 <= t["dist_rows"] <= 8192
     assert t["dist_ctas_per_sm"] in (0, 1, 2, 3)
     assert t["streams"] in (0, 1, 2)
