@@ -86,6 +86,18 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
+int index_alloc_raw(void** p, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  cudaMemPool_t pool = scratch_pool();
+  const cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    set_error("cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    return DETLSH_ENOMEM;
+  }
+  return DETLSH_OK;
+}
+
 namespace {
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -163,12 +175,15 @@ int check_flag(int* d_bad, cudaStream_t s, const char* what) {
 
 void free_index(detlsh_index* idx) {
   if (!idx) return;
-  if (idx->owns_x && idx->X) cudaFree(const_cast<void*>(idx->X));
+  // no kernel of any stream may still use the arrays
+  cudaDeviceSynchronize();
+  if (idx->owns_x && idx->X) cudaFreeAsync(const_cast<void*>(idx->X), 0);
   void* arrays[] = {idx->A, idx->At, idx->E, idx->Ps, idx->codes, idx->leaf_ids, idx->leaf_pos, idx->leaf_base,
                     idx->leaf_range, idx->leaf_plen, idx->leaf_prefix, idx->leaf_lo, idx->leaf_hi,
                     idx->leaf_tree, idx->Xb, idx->Ab, idx->d_err, idx->Rtab, idx->Rlo, idx->Rinv, idx->Atf, idx->Ab3};
   for (void* p : arrays)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, 0);
+  cudaStreamSynchronize(0);
   delete idx;
 }
 
@@ -196,16 +211,16 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
     idx->owns_x = false;
   } else {
     void* xd = nullptr;
-    DL_CUDA(cudaMalloc(&xd, xbytes));
+    DL_TRY(index_alloc(&xd, xbytes, s));
     idx->X = xd;
     DL_CUDA(cudaMemcpyAsync(xd, X, xbytes,
                             mem == DETLSH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                             s));
   }
-  DL_CUDA(cudaMalloc(&idx->A, sizeof(float) * LK * d));
+  DL_TRY(index_alloc(&idx->A, sizeof(float) * LK * d, s));
   DL_CUDA(cudaMemcpyAsync(idx->A, A, sizeof(float) * LK * d,
                           mem == DETLSH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-  DL_CUDA(cudaMalloc(&idx->At, sizeof(float) * LK * d));
+  DL_TRY(index_alloc(&idx->At, sizeof(float) * LK * d, s));
   DL_TRY(transpose_hashes(idx->A, LK, d, idx->At, s));
 
   In ids;
@@ -221,19 +236,19 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
   }
   PhaseTimer tm(s);
   // Alg. 1: projections of the sample, [LK][n_s]
-  DL_CUDA(cudaMalloc(&idx->Ps, sizeof(float) * LK * prm->n_s));
-  DL_CUDA(cudaMalloc(&idx->E, sizeof(float) * LK * (Nr + 1)));
-  DL_CUDA(cudaMalloc(&idx->codes, (size_t)n * LK));
-  DL_CUDA(cudaMalloc(&idx->leaf_ids, sizeof(uint32_t) * n * L));
-  DL_CUDA(cudaMalloc(&idx->Rtab, (size_t)LK * kRegionRow));
-  DL_CUDA(cudaMalloc(&idx->Rlo, sizeof(float) * LK));
-  DL_CUDA(cudaMalloc(&idx->Rinv, sizeof(float) * LK));
+  DL_TRY(index_alloc(&idx->Ps, sizeof(float) * LK * prm->n_s, s));
+  DL_TRY(index_alloc(&idx->E, sizeof(float) * LK * (Nr + 1), s));
+  DL_TRY(index_alloc(&idx->codes, (size_t)n * LK, s));
+  DL_TRY(index_alloc(&idx->leaf_ids, sizeof(uint32_t) * n * L, s));
+  DL_TRY(index_alloc(&idx->Rtab, (size_t)LK * kRegionRow, s));
+  DL_TRY(index_alloc(&idx->Rlo, sizeof(float) * LK, s));
+  DL_TRY(index_alloc(&idx->Rinv, sizeof(float) * LK, s));
   if (prm->proj_mode == DETLSH_PROJ_BF16) {
     // BF16 copies of X and A; projections on the tensor cores
     const int N = (LK + 15) / 16 * 16;
-    DL_CUDA(cudaMalloc(&idx->Xb, (size_t)n * d * 2));
-    DL_CUDA(cudaMalloc(&idx->Ab, (size_t)N * d * 2));
-    DL_CUDA(cudaMalloc(&idx->d_err, sizeof(int)));
+    DL_TRY(index_alloc(&idx->Xb, (size_t)n * d * 2, s));
+    DL_TRY(index_alloc(&idx->Ab, (size_t)N * d * 2, s));
+    DL_TRY(index_alloc(&idx->d_err, sizeof(int), s));
     DL_CUDA(cudaMemsetAsync(idx->Ab, 0, (size_t)N * d * 2, s));
     DL_CUDA(cudaMemsetAsync(idx->d_err, 0, sizeof(int), s));
     tm.begin(TR_SAMPLE_PROJ);
@@ -264,15 +279,15 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
     const bool b3 = bf16x3_eligible(dtype, d, LK);
     const int Nh = (LK + 15) / 16 * 16;
     if (tf32 || b3) {
-      DL_CUDA(cudaMalloc(&idx->d_err, sizeof(int)));
+      DL_TRY(index_alloc(&idx->d_err, sizeof(int), s));
       DL_CUDA(cudaMemsetAsync(idx->d_err, 0, sizeof(int), s));
     }
     if (tf32) {
-      DL_CUDA(cudaMalloc(&idx->Atf, sizeof(float) * 2 * Nh * d));
+      DL_TRY(index_alloc(&idx->Atf, sizeof(float) * 2 * Nh * d, s));
       DL_TRY(split_tf32(idx->A, LK, d, idx->Atf, s));
     }
     if (b3) {
-      DL_CUDA(cudaMalloc(&idx->Ab3, (size_t)3 * Nh * d * 2));
+      DL_TRY(index_alloc(&idx->Ab3, (size_t)3 * Nh * d * 2, s));
       DL_TRY(split_bf16x3(idx->A, LK, d, idx->Ab3, s));
     }
     tm.begin(TR_SAMPLE_PROJ);

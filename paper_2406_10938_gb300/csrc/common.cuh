@@ -126,6 +126,18 @@ struct Scratch {
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
+// Index arrays come from the same stream-ordered pool (fast once the pool
+// holds memory, e.g. from an earlier build); free_index synchronises the
+// device and returns them to it.
+int index_alloc_raw(void** p, size_t bytes, cudaStream_t s);
+template <class T>
+int index_alloc(T** p, size_t bytes, cudaStream_t s) {
+  void* v = nullptr;
+  const int r = index_alloc_raw(&v, bytes, s);
+  *p = static_cast<T*>(v);
+  return r;
+}
+
 }  // namespace detlsh
 
 // The index. Device arrays unless marked _h.

@@ -816,13 +816,13 @@ int build_leaves(detlsh_index* idx, cudaStream_t s) {
 
   // ---- leaf table
   idx->total_leaves = nseg;
-  DL_CUDA(cudaMalloc(&idx->leaf_range, sizeof(uint32_t) * 2 * nseg));
-  DL_CUDA(cudaMalloc(&idx->leaf_plen, (size_t)nseg * K));
-  DL_CUDA(cudaMalloc(&idx->leaf_prefix, (size_t)nseg * K));
-  DL_CUDA(cudaMalloc(&idx->leaf_lo, (size_t)nseg * K));
-  DL_CUDA(cudaMalloc(&idx->leaf_hi, (size_t)nseg * K));
-  DL_CUDA(cudaMalloc(&idx->leaf_tree, sizeof(uint16_t) * nseg));
-  DL_CUDA(cudaMalloc(&idx->leaf_base, sizeof(int64_t) * (L + 1)));
+  DL_TRY(index_alloc(&idx->leaf_range, sizeof(uint32_t) * 2 * nseg, s));
+  DL_TRY(index_alloc(&idx->leaf_plen, (size_t)nseg * K, s));
+  DL_TRY(index_alloc(&idx->leaf_prefix, (size_t)nseg * K, s));
+  DL_TRY(index_alloc(&idx->leaf_lo, (size_t)nseg * K, s));
+  DL_TRY(index_alloc(&idx->leaf_hi, (size_t)nseg * K, s));
+  DL_TRY(index_alloc(&idx->leaf_tree, sizeof(uint16_t) * nseg, s));
+  DL_TRY(index_alloc(&idx->leaf_base, sizeof(int64_t) * (L + 1), s));
   Scratch d_max;
   DL_TRY(d_max.alloc(sizeof(unsigned long long), s));
   DL_CUDA(cudaMemsetAsync(d_max.p, 0, sizeof(unsigned long long), s));
@@ -848,7 +848,7 @@ int build_leaves(detlsh_index* idx, cudaStream_t s) {
   if ((idx->flags & DETLSH_DEDUP_POS) || (n + 7) / 8 * 3 * (int64_t)nsm > (int64_t)l2) {
     Scratch pos0;
     DL_TRY(pos0.alloc(sizeof(uint32_t) * n, s));
-    DL_CUDA(cudaMalloc(&idx->leaf_pos, sizeof(uint32_t) * total));
+    DL_TRY(index_alloc(&idx->leaf_pos, sizeof(uint32_t) * total, s));
     const unsigned g = (unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 32);
     k_pos0<<<g, 256, 0, s>>>(idx->leaf_ids, n, pos0.as<uint32_t>());
     DL_LAUNCH();
