@@ -472,7 +472,7 @@ __global__ void k_query_keys(const float* __restrict__ qp, int LK, const uint32_
 }
 
 // ------------------------------------------------------------------ walk
-constexpr int WT = 256;            // threads per walk CTA (several per SM)
+constexpr int WT = 512;            // threads per walk CTA (two per SM)
 constexpr int WNW = WT / 32;
 constexpr int WBATCH = 2 * WT;     // leaves examined per batch step (two per thread)
 constexpr int WCAP = 8192;         // points examined per batch step
@@ -845,7 +845,7 @@ __device__ unsigned long long select_key(const uint32_t* bl, const uint32_t* lbk
 
 // One CTA per query (persistent over the batch): the buckets in Alg. 7 order.
 template <bool POS>
-__global__ void __launch_bounds__(WT, 4) k_walk(WalkArgs a) {
+__global__ void __launch_bounds__(WT, 2) k_walk(WalkArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
   const WalkLayout ly = walk_layout(a.L, a.smem_bitmap ? a.bitmap_words : 0);
   uint32_t* s_boff = reinterpret_cast<uint32_t*>(sm + ly.boff);
