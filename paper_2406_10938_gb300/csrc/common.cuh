@@ -340,6 +340,7 @@ struct QueryTuning {
 // Sizes and scratch layout (byte offsets into one device block) of a batch.
 struct QueryShape {
   int64_t B, cap, TL, RL, words, max_tree_leaves, items_per_q, bsplit;
+  int64_t nsm = 0;   // SMs of the device
   int LK, L, wgrid, dgrid, dist_rows, tkc, k_max, shortlist, rq;
   bool smem_bitmap;
   size_t wl_total, bk_smem, bp_smem, bytes;

@@ -1312,15 +1312,17 @@ __global__ void k_widen_f32(const void* __restrict__ Q, int dtype, int64_t count
 }
 
 // ------------------------------------------------------------------ finalize
-constexpr int FT = 256;
+constexpr int FT = 256;            // threads per finalize CTA (a query each)
+constexpr int FT_WIDE = 512;       // ... for batches of fewer queries than SMs
 constexpr int TKC_MAX = 8192;      // top-k / shortlist buffer entries (dynamic shared memory)
 
-// Bitonic sort of tk[0..m) ascending, m a power of two (block-wide).
+// Bitonic sort of tk[0..m) ascending, m a power of two (block-wide, NT threads).
+template <int NT>
 __device__ void sort_keys(unsigned long long* tk, int m) {
   for (int size = 2; size <= m; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       __syncthreads();
-      for (int i = threadIdx.x; i < m / 2; i += FT) {
+      for (int i = threadIdx.x; i < m / 2; i += NT) {
         const int lo = 2 * i - (i & (stride - 1));
         const int hi = lo + stride;
         const bool up = ((lo & size) == 0);
@@ -1344,8 +1346,8 @@ __device__ __forceinline__ int pow2_at_least(int v) {
 // Keep the `keep` smallest of the cnt distinct keys tk[0..cnt) (moved, in any
 // order, to the front) and return the largest kept key: a radix select of the
 // keep-th key over 8-bit digits, then an in-place compaction in which every
-// thread first holds its TKC/FT strided keys in registers.
-template <int TKC>
+// thread first holds its TKC/NT strided keys in registers.
+template <int TKC, int NT>
 __device__ unsigned long long prune_keys(unsigned long long* tk, int cnt, int keep, uint32_t* hist,
                                          unsigned long long* s_pref, int* s_need, uint32_t* s_warp) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1353,10 +1355,10 @@ __device__ unsigned long long prune_keys(unsigned long long* tk, int cnt, int ke
   unsigned long long prefix = 0, pmask = 0;
   int need = keep;   // rank (1-based) of the wanted key among the keys matching the prefix
   for (int p = 7; p >= 0; --p) {
-    for (int i = threadIdx.x; i < 256; i += FT) hist[i] = 0;
+    for (int i = threadIdx.x; i < 256; i += NT) hist[i] = 0;
     __syncthreads();
-    const int it = (cnt + FT - 1) / FT * FT;
-    for (int i = threadIdx.x; i < it; i += FT) {
+    const int it = (cnt + NT - 1) / NT * NT;
+    for (int i = threadIdx.x; i < it; i += NT) {
       uint32_t dg = 0xffffffffu;
       if (i < cnt) {
         const unsigned long long k = tk[i];
@@ -1400,12 +1402,12 @@ __device__ unsigned long long prune_keys(unsigned long long* tk, int cnt, int ke
     pmask |= 255ull << (8 * p);
   }
   const unsigned long long kth = prefix;
-  constexpr int PER = TKC / FT;
+  constexpr int PER = TKC / NT;
   unsigned long long v[PER];
   uint32_t mask = 0;
 #pragma unroll
   for (int j = 0; j < PER; ++j) {
-    const int i = threadIdx.x + j * FT;
+    const int i = threadIdx.x + j * NT;
     v[j] = i < cnt ? tk[i] : ~0ull;
     if (i < cnt && v[j] <= kth) mask |= 1u << j;
   }
@@ -1450,19 +1452,26 @@ struct FinalArgs {
   const void* Q;
   int d;
   bool vec4;
+  int64_t wide_below;   // batches of fewer queries take the FT_WIDE-thread kernel
 };
 
-template <typename TX, int TKC>
-__global__ void __launch_bounds__(FT) k_finalize(FinalArgs a) {
+// NT threads per query: FT_WIDE for batches of fewer than a.wide_below
+// queries (few CTAs, so each query's candidates are spread over more
+// threads), else FT. Both widths are launched for such a batch size range (so
+// one captured graph serves any batch size); the one that does not apply to
+// the batch returns at once.
+template <typename TX, int TKC, int NT>
+__global__ void __launch_bounds__(NT) k_finalize(FinalArgs a) {
   extern __shared__ __align__(16) unsigned long long tk[];   // [TKC]
   __shared__ uint32_t s_rend[kRoundCap];
   __shared__ float s_thr[kRoundCap];
   __shared__ uint32_t s_hist[kRoundCap + 1];
   __shared__ unsigned long long s_tkn, s_tau;
   __shared__ uint32_t s_nsf, s_stop, s_rounds;
-  __shared__ uint32_t s_sel[256], s_warp[FT / 32];
+  __shared__ uint32_t s_sel[256], s_warp[NT / 32];
   __shared__ unsigned long long s_pref;
   __shared__ int s_need;
+  if (((int64_t)*a.nqd < a.wide_below) != (NT == FT_WIDE)) return;
   if (blockIdx.x >= *a.nqd) return;
   const int64_t qb = blockIdx.x;
   const int64_t qg = a.q0 + qb;
@@ -1477,26 +1486,26 @@ __global__ void __launch_bounds__(FT) k_finalize(FinalArgs a) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   const int nr = (int)t_end + 1;
-  for (int i = threadIdx.x; i < kRoundCap; i += FT) {
+  for (int i = threadIdx.x; i < kRoundCap; i += NT) {
     s_rend[i] = i < nr ? a.round_end[qb * kRoundCap + i] : 0u;
     s_thr[i] = i < Ru ? a.thrC[qb * kRoundCap + i] : INFINITY;
   }
-  for (int i = threadIdx.x; i <= kRoundCap; i += FT) s_hist[i] = 0;
+  for (int i = threadIdx.x; i <= kRoundCap; i += NT) s_hist[i] = 0;
   __syncthreads();
   // a candidate inserted in round r counts as within c*r_t for every t >= max(r, u),
   // u = first round whose exact threshold (c*r_u)^2 covers its distance
   constexpr int FU = 4;   // candidates per thread in flight
-  const uint32_t iters = (nS + FT * FU - 1) / (FT * FU) * (FT * FU);
-  for (uint32_t p0 = threadIdx.x; p0 < iters; p0 += FT * FU) {
+  const uint32_t iters = (nS + NT * FU - 1) / (NT * FU) * (NT * FU);
+  for (uint32_t p0 = threadIdx.x; p0 < iters; p0 += NT * FU) {
     float dv[FU];
 #pragma unroll
     for (int u = 0; u < FU; ++u) {
-      const uint32_t p = p0 + u * FT;
+      const uint32_t p = p0 + u * NT;
       dv[u] = p < nS ? dl[p] : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < FU; ++u) {
-      const uint32_t p = p0 + u * FT;
+      const uint32_t p = p0 + u * NT;
       uint32_t key = 0xffffffffu;
       if (p < nS) {
         const int r = upper_bound_u(s_rend, nr, p);
@@ -1537,7 +1546,7 @@ __global__ void __launch_bounds__(FT) k_finalize(FinalArgs a) {
       const int cnt = (int)min(s_tkn, (unsigned long long)TKC);
       __syncthreads();
       if (cnt > keep) {
-        const unsigned long long kth = prune_keys<TKC>(tk, cnt, keep, s_sel, &s_pref, &s_need, s_warp);
+        const unsigned long long kth = prune_keys<TKC, NT>(tk, cnt, keep, s_sel, &s_pref, &s_need, s_warp);
         if (threadIdx.x == 0) {
           s_tkn = keep;
           s_tau = kth;
@@ -1547,11 +1556,11 @@ __global__ void __launch_bounds__(FT) k_finalize(FinalArgs a) {
     }
     const unsigned long long tau = s_tau;
     const uint32_t c1 = min(nsf, c0 + (uint32_t)chunk);
-    for (uint32_t p0 = c0 + threadIdx.x; p0 < c1; p0 += FT * FU) {
+    for (uint32_t p0 = c0 + threadIdx.x; p0 < c1; p0 += NT * FU) {
       unsigned long long kv[FU];
 #pragma unroll
       for (int u = 0; u < FU; ++u) {
-        const uint32_t p = p0 + u * FT;
+        const uint32_t p = p0 + u * NT;
         kv[u] = p < c1 ? (((unsigned long long)__float_as_uint(dl[p]) << 32) | cl[p]) : ~0ull;
       }
 #pragma unroll
@@ -1568,15 +1577,15 @@ __global__ void __launch_bounds__(FT) k_finalize(FinalArgs a) {
   {
     const int cnt = (int)min(s_tkn, (unsigned long long)TKC);
     const int m = pow2_at_least(cnt);
-    for (int i = cnt + threadIdx.x; i < m; i += FT) tk[i] = ~0ull;
-    sort_keys(tk, m);
+    for (int i = cnt + threadIdx.x; i < m; i += NT) tk[i] = ~0ull;
+    sort_keys<NT>(tk, m);
     have = min(cnt, keep);
   }
   if (a.shortlist > 0) {
     // exact FP32 distances of the shortlist, 8 rows per warp, then re-sort
     const TX* X = static_cast<const TX*>(a.X);
     const TX* q = static_cast<const TX*>(a.Q) + qg * (int64_t)a.d;
-    for (int e0 = w * ILP; e0 < have; e0 += (FT / 32) * ILP) {
+    for (int e0 = w * ILP; e0 < have; e0 += (NT / 32) * ILP) {
       uint32_t ids[ILP];
       float acc[ILP];
 #pragma unroll
@@ -1593,11 +1602,11 @@ __global__ void __launch_bounds__(FT) k_finalize(FinalArgs a) {
     }
     __syncthreads();
     const int m = pow2_at_least(have);
-    for (int i = have + threadIdx.x; i < m; i += FT) tk[i] = ~0ull;
-    sort_keys(tk, m);
+    for (int i = have + threadIdx.x; i < m; i += NT) tk[i] = ~0ull;
+    sort_keys<NT>(tk, m);
     have = min(have, kq);
   }
-  for (int r = threadIdx.x; r < a.k_max; r += FT) {
+  for (int r = threadIdx.x; r < a.k_max; r += NT) {
     int64_t id = -1;
     float dist = INFINITY;
     if (r < have && r < kq) {
@@ -1609,7 +1618,7 @@ __global__ void __launch_bounds__(FT) k_finalize(FinalArgs a) {
     a.out_dist[qg * a.k_max + r] = dist;
   }
   if (a.cand_ids) {
-    for (uint32_t p = threadIdx.x; p < nsf && (int64_t)p < a.cand_cap; p += FT)
+    for (uint32_t p = threadIdx.x; p < nsf && (int64_t)p < a.cand_cap; p += NT)
       a.cand_ids[qg * a.cand_cap + p] = cl[p];
   }
   if (threadIdx.x == 0 && a.out_stats) {
@@ -1726,6 +1735,7 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   walk_per_sm = std::max(walk_per_sm, 1);
   if (tu.walk_ctas_per_sm > 0) walk_per_sm = std::min(walk_per_sm, tu.walk_ctas_per_sm);
   sh.dgrid = nsm * (tu.dist_ctas_per_sm ? tu.dist_ctas_per_sm : 3);
+  sh.nsm = nsm;
   // split bucketing: per-CTA histograms over (round, tree)
   sh.rq = 1;
   sh.bk_smem = sizeof(uint32_t) * 2 * sh.RL + sizeof(float) * kRoundCap;
@@ -1737,10 +1747,14 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   if (sh.RL * sizeof(uint32_t) > 48 * 1024)
     DL_CUDA(cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sh.RL * sizeof(uint32_t))));
-  DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
-  DL_CUDA(cudaFuncSetAttribute(k_finalize<uint8_t, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
-  DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
-  DL_CUDA(cudaFuncSetAttribute(k_finalize<uint8_t, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 4096, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<uint8_t, 4096, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 8192, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<uint8_t, 8192, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 4096, FT_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<uint8_t, 4096, FT_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 8192, FT_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+  DL_CUDA(cudaFuncSetAttribute(k_finalize<uint8_t, 8192, FT_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
 
   // candidate capacity per query: S stays below beta*n+k until its last leaf
   const double tmax = std::ceil(beta * (double)idx->n + (double)k_max);
@@ -2002,13 +2016,28 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   fa.Q = Q;
   fa.d = idx->d;
   fa.vec4 = vec4;
+  fa.wide_below = sh.nsm;
   const size_t fin_smem = sizeof(unsigned long long) * sh.tkc;
   tm.begin(TR_FINALIZE);
-  if (idx->dtype == DETLSH_U8)
-    (sh.tkc == 4096 ? k_finalize<uint8_t, 4096> : k_finalize<uint8_t, 8192>)<<<(unsigned)nqg, FT, fin_smem, s>>>(fa);
-  else
-    (sh.tkc == 4096 ? k_finalize<float, 4096> : k_finalize<float, 8192>)<<<(unsigned)nqg, FT, fin_smem, s>>>(fa);
-  DL_LAUNCH();
+  if (idx->dtype == DETLSH_U8) {
+    (sh.tkc == 4096 ? k_finalize<uint8_t, 4096, FT> : k_finalize<uint8_t, 8192, FT>)<<<(unsigned)nqg, FT, fin_smem, s>>>(fa);
+    DL_LAUNCH();
+    if (nqg > 0) {
+      (sh.tkc == 4096 ? k_finalize<uint8_t, 4096, FT_WIDE>
+                      : k_finalize<uint8_t, 8192, FT_WIDE>)<<<(unsigned)std::min<int64_t>(nqg, sh.nsm), FT_WIDE,
+                                                             fin_smem, s>>>(fa);
+      DL_LAUNCH();
+    }
+  } else {
+    (sh.tkc == 4096 ? k_finalize<float, 4096, FT> : k_finalize<float, 8192, FT>)<<<(unsigned)nqg, FT, fin_smem, s>>>(fa);
+    DL_LAUNCH();
+    if (nqg > 0) {
+      (sh.tkc == 4096 ? k_finalize<float, 4096, FT_WIDE>
+                      : k_finalize<float, 8192, FT_WIDE>)<<<(unsigned)std::min<int64_t>(nqg, sh.nsm), FT_WIDE,
+                                                           fin_smem, s>>>(fa);
+      DL_LAUNCH();
+    }
+  }
   tm.end();
   return DETLSH_OK;
 }
