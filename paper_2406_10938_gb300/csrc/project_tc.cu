@@ -26,7 +26,6 @@ namespace detlsh {
 namespace {
 
 constexpr int TC_M = 128;          // rows (points) per tile
-constexpr int TC_KC = 64;          // d elements per stage (128 bytes of BF16)
 constexpr int TC_STAGES = 4;
 constexpr int TC_EPI_WARPS = 16;     // 4 per TMEM lane quadrant, 16 accumulator columns each
 constexpr int TC_THREADS = 128 + 32 * TC_EPI_WARPS;
@@ -127,29 +126,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Number of interior breakpoints e_z (z = 1..Nr-1, e[z]) with e_z <= p.
-__device__ __forceinline__ int region_of_tc(const float* e, int Nr, float p) {
-  int pos = 0;
-  for (int step = Nr >> 1; step > 0; step >>= 1) pos += (e[pos + step] <= p) ? step : 0;
-  return pos;
-}
-
 struct TcArgs {
   int64_t rows;
   int d, LK, K, Nr;
