@@ -275,8 +275,10 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
     // the points that define breakpoints fall on them exactly when encoded.
     // uint8 points likewise, widened to BF16 (exact) in the kernel against A in
     // three BF16 parts
-    const bool tf32 = tf32_eligible(dtype, d, LK);
-    const bool b3 = bf16x3_eligible(dtype, d, LK);
+    // (the tensor-core kernels read X by TMA, which needs a 16-byte aligned base)
+    const bool x16 = reinterpret_cast<uintptr_t>(idx->X) % 16 == 0;
+    const bool tf32 = x16 && tf32_eligible(dtype, d, LK);
+    const bool b3 = x16 && bf16x3_eligible(dtype, d, LK);
     const int Nh = (LK + 15) / 16 * 16;
     if (tf32 || b3) {
       DL_TRY(index_alloc(&idx->d_err, sizeof(int), s));

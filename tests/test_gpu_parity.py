@@ -123,6 +123,24 @@ def test_build_exact_bit_parity(case):
     idx.free()
 
 
+@pytest.mark.parametrize("name,d", [("tiny", 32), ("serving", 32), ("mid", 128)])
+def test_build_from_misaligned_borrowed_points(name, d):
+    """A borrowed device X whose base is not 16-byte aligned (a view one
+    element into a buffer) takes the CUDA-core encoding instead of the TMA
+    path and still gives the oracle's index (exact inputs)."""
+    n, K, L, Nr, n_s, max_leaf = 3_000, 16, 4, 16, 300, 32
+    X, _, A, ids = _exact_inputs(name, n, d, K, L, n_s)
+    buf = torch.empty(n * d + 1, dtype=X.dtype, device=DEV)
+    Xm = buf[1:].view(n, d)
+    Xm.copy_(X.to(DEV))
+    assert Xm.data_ptr() % 16 != 0
+    idx = pkg.detlsh_build(Xm, A.to(DEV), ids.to(DEV), K, L, Nr, max_leaf, borrow=True)
+    ref = O.build_index(X.numpy(), A.numpy(), ids.numpy(), K, L, Nr, max_leaf)
+    assert np.array_equal(gpu_codes(idx, n, K, L), ref.codes)
+    assert_trees_equal(gpu_trees(idx, K, L, n), ref.trees)
+    idx.free()
+
+
 @pytest.mark.parametrize("kind", ["few_values", "narrow_offset"])
 def test_build_degenerate_breakpoints_bit_parity(kind):
     """Breakpoints with many equal values (few distinct points) and breakpoints
