@@ -27,9 +27,22 @@ METRIC = "index Mpts/s; QPS@recall≥0.9 vs plain FP32 GPU; p99 latency; % HBM p
 WORKLOAD = dict(name="mid", n=1_000_000, d=128, nq=10_000, K=16, L=4, n_regions=256, n_s=10_000,
                 max_leaf=256, c=1.5, k=50, beta=0.1)
 def workload_desc():
+    if WORKLOAD.get("method") == "det-only":
+        return ("mid, DET-ONLY: n=1,000,000 d=128 fp32 integer 0-255 Gaussian mixture of 1,000 clusters, "
+                f"{WORKLOAD['nq']:,} queries from the same mixture; one DE-Tree over the PAA reduction "
+                "(K=16 segment means of 8 coordinates), N_r=256 n_s=1% c=1.5 k=50 beta=0.1 max_leaf=256")
     return ("mid: n=1,000,000 d=128 fp32 integer 0-255 Gaussian mixture of 1,000 clusters, "
             f"{WORKLOAD['nq']:,} queries from the same mixture; K=16 L=4 N_r=256 n_s=1% c=1.5 k=50 "
             "beta=0.1 max_leaf=256")
+
+
+def projection_for(w, device="cpu"):
+    """The index's projection matrix: L*K Gaussian hash vectors (DET-LSH, Eq. 1),
+    or the PAA segment means of DET-ONLY (L = 1)."""
+    from workloads import gaussian_projection, paa_projection
+    if w.get("method") == "det-only":
+        return paa_projection(w["K"], w["d"], device=device)
+    return gaussian_projection(w["L"], w["K"], w["d"], device=device)
 
 
 def _peaks():
@@ -139,12 +152,15 @@ CPU_SCRIPT = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
 import numpy as np
-from workloads import make_workload, gaussian_projection, sample_ids
+from workloads import make_workload, gaussian_projection, paa_projection, sample_ids
 from oracle import detlsh_oracle as O
 w = {w!r}
 nqs = {nqs}
 X, Q = make_workload(w["name"], n=w["n"], nq=nqs, seed_query=2)
-A = gaussian_projection(w["L"], w["K"], w["d"]).numpy()
+if w.get("method") == "det-only":
+    A = paa_projection(w["K"], w["d"]).numpy()
+else:
+    A = gaussian_projection(w["L"], w["K"], w["d"]).numpy()
 ids = sample_ids(w["n"], w["n_s"]).numpy()
 Xn, Qn = X.numpy(), Q.numpy()
 t0 = time.perf_counter()
@@ -207,7 +223,7 @@ def gpu_arm(args, rank, world, local_rank):
     import torch.distributed as dist
 
     import paper_2406_10938_gb300 as pkg
-    from workloads import gaussian_projection, make_workload, sample_ids
+    from workloads import make_workload, sample_ids
 
     pkg.build()
     proj_mode = 1 if args.proj == "bf16" else 0
@@ -215,7 +231,7 @@ def gpu_arm(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     w = WORKLOAD
     X, Q = make_workload(w["name"], n=w["n"], nq=w["nq"], seed_query=2 + rank, device=dev)
-    A = gaussian_projection(w["L"], w["K"], w["d"], device=dev)
+    A = projection_for(w, device=dev)
     ids = sample_ids(w["n"], w["n_s"], device=dev)
     nq = w["nq"]
     kk = torch.full((nq,), w["k"], dtype=torch.int32, device=dev)
@@ -781,6 +797,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-queries", type=int, default=8)
     ap.add_argument("--nq", type=int, default=WORKLOAD["nq"], help="queries per step (default: the workload's)")
+    ap.add_argument("--method", default="det-lsh", choices=["det-lsh", "det-only"],
+                    help="mid workload: DET-LSH (L Gaussian projections) or DET-ONLY (one tree over PAA)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--proj", default="fp32", choices=["fp32", "bf16"],
                     help="projection arithmetic of the build (bf16: tensor cores)")
@@ -799,6 +817,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     WORKLOAD["nq"] = args.nq
+    if args.method == "det-only":
+        WORKLOAD["method"] = "det-only"
+        WORKLOAD["L"] = 1
     if args.impl == "reference" and args.workload != "mid":
         ap.error("the reference arm times the mid workload")
     if args.impl == "reference":

@@ -19,7 +19,7 @@ import paper_2406_10938_gb300 as pkg
 from oracle import detlsh_oracle as O
 from parity_helpers import (DEV, assert_trees_equal, check_tree_properties, gpu_build, gpu_codes,
                             gpu_trees, oracle_queries, proj_tolerance)
-from workloads import gaussian_projection, make_workload, sample_ids
+from workloads import gaussian_projection, make_workload, paa_projection, sample_ids
 from workloads.synthetic import query_params
 
 pytestmark = pytest.mark.gpu
@@ -282,6 +282,37 @@ def test_query_dedup_by_leaf_position_same_results(case):
         kq = int(ks[qi])
         assert np.array_equal(i1.numpy()[qi, :kq], r.ids[:kq]), qi
         assert int(s1[qi, 0]) == r.n_cand
+
+
+@pytest.mark.parametrize("name,n,d,Nr,n_s,max_leaf,nq,k", [("tiny", 10_000, 32, 16, 1_000, 64, 30, 10),
+                                                         ("mid", 20_000, 128, 256, 2_000, 64, 20, 50)])
+def test_det_only_exact_bit_parity(name, n, d, Nr, n_s, max_leaf, nq, k):
+    """DET-ONLY (Sec. 6.1): one DE-Tree over the PAA reduction (segment means,
+    exact here: 1/w with w a power of two) and the same query. Index and
+    results equal the oracle's bit for bit."""
+    K, L, beta = 16, 1, 0.1
+    X, Q = make_workload(name, n=n, nq=nq, exact=True, d=d)
+    A = paa_projection(K, d)
+    ids = sample_ids(n, n_s)
+    eps = O.eps_from_lemma3(K, L)
+    g = torch.Generator().manual_seed(nq)
+    cs = torch.tensor([1.2, 1.5, 2.0])[torch.randint(0, 3, (nq,), generator=g)]
+    ks = torch.randint(1, k + 1, (nq,), generator=g, dtype=torch.int32)
+    rm = torch.zeros(nq, dtype=torch.float32)
+    idx = gpu_build(X, A, ids, K, L, Nr, max_leaf)
+    ref = O.build_index(X.numpy(), A.numpy(), ids.numpy(), K, L, Nr, max_leaf)
+    assert np.array_equal(gpu_codes(idx, n, K, L), ref.codes)
+    assert_trees_equal(gpu_trees(idx, K, L, n), ref.trees)
+    out_ids, out_dist, stats, _ = pkg.detlsh_query(idx, Q.to(DEV), ks.to(DEV), cs.to(DEV), rm.to(DEV), k_max=k,
+                                                   eps=eps, beta=beta)
+    out_ids, out_dist, stats = out_ids.cpu().numpy(), out_dist.cpu().numpy(), stats.cpu().numpy()
+    res = oracle_queries(ref, Q.numpy(), ks.numpy(), cs.numpy(), rm.numpy(), eps, beta, keep=False)
+    for qi, r in enumerate(res):
+        kq = int(ks[qi])
+        assert (stats[qi, 0], stats[qi, 1], stats[qi, 2]) == (r.n_cand, r.rounds, r.stop), qi
+        assert np.array_equal(out_ids[qi, :kq], r.ids[:kq]), qi
+        assert np.array_equal(out_dist[qi, :kq], np.float32(r.dist[:kq])), qi
+    idx.free()
 
 
 # ------------------------------------------------------------------ query, float inputs

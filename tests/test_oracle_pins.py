@@ -12,7 +12,7 @@ import pytest
 import torch
 
 from oracle import detlsh_oracle as O
-from workloads import gaussian_projection, make_workload, sample_ids
+from workloads import gaussian_projection, make_workload, paa_projection, sample_ids
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -283,6 +283,33 @@ def test_query_all_leaves_is_exact_knn():
     X, Q = X.numpy(), Q.numpy()
     A = gaussian_projection(2, 8, X.shape[1]).numpy()
     idx = O.build_index(X, A, sample_ids(2000, 200).numpy(), 8, 2, 16, 32)
+    for q in Q:
+        res = O.c2k_ann(idx, q, 7, 1.5, 1e6, 3.0, 1.0, keep_candidates=True)
+        ids, dist = O.exact_knn(X, q, 7)
+        assert res.n_cand == 2000
+        assert res.ids.tolist() == ids.tolist()
+        assert np.allclose(res.dist, dist, rtol=0, atol=0)
+
+
+def test_paa_projection_is_segment_means():
+    """DET-ONLY's projection (Sec. 6.1): coordinate j of the reduced point is the
+    mean of segment j of floor(d/K) coordinates; leftover coordinates are unused."""
+    rng = np.random.default_rng(5)
+    for K, d in ((16, 32), (16, 128), (5, 23), (1, 7)):
+        A = paa_projection(K, d).numpy().astype(np.float64)
+        x = rng.standard_normal(d)
+        w = d // K
+        want = np.array([x[j * w:(j + 1) * w].mean() for j in range(K)])
+        assert np.allclose(A @ x, want, rtol=1e-6, atol=1e-7)
+        assert (A[:, K * w:] == 0).all()
+
+
+def test_det_only_all_leaves_is_exact_knn():
+    """DET-ONLY (one DE-Tree over PAA, the same query) with S = D returns the exact kNN."""
+    X, Q = make_workload("tiny", n=2000, nq=8)
+    X, Q = X.numpy(), Q.numpy()
+    A = paa_projection(16, X.shape[1]).numpy()
+    idx = O.build_index(X, A, sample_ids(2000, 200).numpy(), 16, 1, 16, 32)
     for q in Q:
         res = O.c2k_ann(idx, q, 7, 1.5, 1e6, 3.0, 1.0, keep_candidates=True)
         ids, dist = O.exact_knn(X, q, 7)

@@ -10,5 +10,6 @@ from .synthetic import (  # noqa: F401
     Workload,
     gaussian_projection,
     make_workload,
+    paa_projection,
     sample_ids,
 )

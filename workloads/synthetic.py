@@ -164,6 +164,21 @@ def gaussian_projection(L: int, K: int, d: int, seed: int = 3, device="cpu",
     return A
 
 
+def paa_projection(K: int, d: int, device="cpu") -> torch.Tensor:
+    """The Piecewise Aggregate Approximation of DET-ONLY (the paper's single-tree
+    baseline, Sec. 6.1) as a projection matrix [K, d]: row j averages the
+    coordinates of segment j, w = floor(d/K) consecutive coordinates from j*w
+    (the last d - K*w coordinates belong to no segment). Entries 1/w: exact
+    in FP32 when w is a power of two."""
+    if not 1 <= K <= d:
+        raise ValueError("need 1 <= K <= d")
+    w = d // K
+    A = torch.zeros(K, d, dtype=torch.float32, device=device)
+    for j in range(K):
+        A[j, j * w:(j + 1) * w] = 1.0 / w
+    return A
+
+
 def sample_ids(n: int, n_s: int, seed: int = 3, device="cpu") -> torch.Tensor:
     """n_s distinct point ids drawn uniformly from [0, n), ascending (int64)."""
     if not 0 < n_s <= n:
