@@ -38,6 +38,12 @@ notes):
      with no positive lower bound r_min = 1.
  R8  eps = sqrt(chi2 upper alpha1-quantile with K degrees of freedom),
      alpha1 = exp(-1/L) (Lemma 3, Eq. 2).
+ R11 exact range query (Alg. 4/5): the upper bound of a leaf box also takes
+     -inf/+inf for the outermost edges (a point can lie beyond the sample's
+     range), so leaves on the outside are always checked point by point.
+ R12 range tests compare squared distances in FP64.
+ R13 (r,c)-ANN (Alg. 6): |S| >= beta*n + 1 compared as real numbers; a
+     query that returns nothing reports id -1.
 """
 
 from __future__ import annotations
@@ -371,6 +377,111 @@ def c2k_ann(index: Index, q: np.ndarray, k: int, c: float, r_min: float, eps: fl
     dist[:len(order)] = np.sqrt(d2[order])
     return QueryResult(ids=ids, dist=dist, n_cand=int(n_S), rounds=t + 1, stop=stop,
                        cand=np.sort(cand) if keep_candidates else np.zeros(0, np.int64))
+
+
+# ---------------------------------------------------------------- exact range query and (r,c)-ANN
+def leaf_bounds2(index: Index, i: int, qp: np.ndarray):
+    """Squared lower and upper bound distances (FP64) between the projected
+    query qp [K] and every leaf box of tree i (the bounds Alg. 4 asks for).
+
+    A leaf covers [e_lo, e_{hi+1}] in every dimension, with the outermost
+    edges -inf / +inf (reading R4, and R11 for the upper bound: a box that
+    reaches an outer region has an infinite upper bound, so its points are
+    always checked one by one). Per dimension the lower bound takes
+    max(e_lo - x, x - e_{hi+1}, 0) and the upper bound max(|x - e_lo|,
+    |x - e_{hi+1}|); both are squared and summed.
+    """
+    K, Nr = index.K, index.n_regions
+    t = index.trees[i]
+    lo, hi = t.box(int(round(math.log2(Nr))))
+    lb2 = np.zeros(t.n_leaves)
+    ub2 = np.zeros(t.n_leaves)
+    for j in range(K):
+        e = index.E[i * K + j]
+        x = float(qp[j])
+        el = np.where(lo[:, j] == 0, -np.inf, e[lo[:, j]])
+        eh = np.where(hi[:, j] == Nr - 1, np.inf, e[np.minimum(hi[:, j] + 1, Nr)])
+        delta = np.maximum(np.maximum(el - x, x - eh), 0.0)
+        far = np.maximum(np.abs(x - el), np.abs(x - eh))
+        lb2 += delta * delta
+        ub2 += far * far
+    return lb2, ub2
+
+
+def det_range_query(index: Index, i: int, qp: np.ndarray, r_proj: float, stats: Optional[dict] = None):
+    """Alg. 4 (DET range query) with Alg. 5 (traverse subtree) in tree i: the
+    ids of the points whose projection lies within r_proj of qp, ascending.
+
+    A leaf whose lower bound exceeds r_proj is skipped; a leaf whose upper
+    bound is at most r_proj gives all its points; any other leaf gives the
+    points whose projected distance is at most r_proj. An internal node's box
+    contains its leaves' boxes, so its lower bound is not above theirs and
+    pruning it never drops a leaf the leaf test keeps: visiting the leaves
+    one by one gives the same set as the recursion. Distances are compared
+    squared (FP64). stats, if given, counts the leaves of each kind.
+    """
+    K = index.K
+    t = index.trees[i]
+    lb2, ub2 = leaf_bounds2(index, i, qp)
+    r2 = float(r_proj) * float(r_proj)
+    P = index.P[:, i * K:(i + 1) * K]
+    out = []
+    n_skip = n_all = n_ref = 0
+    for leaf in range(t.n_leaves):
+        members = t.ids[t.offset[leaf]:t.offset[leaf + 1]]
+        if lb2[leaf] > r2:
+            n_skip += 1
+        elif ub2[leaf] <= r2:
+            n_all += 1
+            out.append(members)
+        else:
+            n_ref += 1
+            diff = P[members] - np.asarray(qp, dtype=np.float64)[None, :]
+            d2 = np.einsum("ij,ij->i", diff, diff)
+            out.append(members[d2 <= r2])
+    if stats is not None:
+        stats.update(skipped=n_skip, accepted=n_all, refined=n_ref)
+    return np.sort(np.concatenate(out)) if out else np.zeros(0, np.int64)
+
+
+@dataclass
+class RCResult:
+    id: int                  # the returned point, or -1 (nothing returned)
+    dist: float              # its distance to q (+inf when nothing is returned)
+    n_cand: int              # |S| when the query ended
+    trees: int               # trees range-queried
+    stop: int                # 1: |S| >= beta n + 1; 2: a point of S within c r; 0: nothing returned
+
+
+def rc_ann(index: Index, q: np.ndarray, r: float, c: float, eps: float, beta: float) -> RCResult:
+    """Alg. 6, the (r,c)-ANN query: range-query the trees in order with the
+    projected radius eps*r, adding each result to S; once |S| >= beta*n + 1
+    (reading R13: the real-valued bound) return the point of S closest to q;
+    after all L trees return it if some point of S lies within c*r of q, else
+    nothing. Closest by (distance, id), distances in FP64.
+    """
+    q = np.asarray(q, dtype=np.float64)
+    K = index.K
+    S = np.zeros(0, np.int64)
+    bound = beta * index.n + 1.0
+
+    def closest(ids):
+        diff = np.asarray(index.X, dtype=np.float64)[ids] - q[None, :]
+        d2 = np.einsum("ij,ij->i", diff, diff)
+        o = np.lexsort((ids, d2))[0]
+        return int(ids[o]), float(np.sqrt(d2[o]))
+
+    for i in range(index.L):
+        qp = project(index.A[i * K:(i + 1) * K], q[None, :])[0]
+        S = np.union1d(S, det_range_query(index, i, qp, eps * r))
+        if len(S) >= bound:
+            o, dist = closest(S)
+            return RCResult(id=o, dist=dist, n_cand=len(S), trees=i + 1, stop=1)
+    if len(S):
+        o, dist = closest(S)
+        if dist <= c * r:
+            return RCResult(id=o, dist=dist, n_cand=len(S), trees=index.L, stop=2)
+    return RCResult(id=-1, dist=math.inf, n_cand=len(S), trees=index.L, stop=0)
 
 
 # ---------------------------------------------------------------- evaluation measures

@@ -318,6 +318,76 @@ def test_det_only_all_leaves_is_exact_knn():
         assert np.allclose(res.dist, dist, rtol=0, atol=0)
 
 
+def _range_index(K=8, max_leaf=32):
+    X, Q = make_workload("tiny", n=3000, nq=6)
+    X, Q = X.numpy(), Q.numpy()
+    A = gaussian_projection(2, K, X.shape[1]).numpy()
+    idx = O.build_index(X, A, sample_ids(3000, 300).numpy(), K, 2, 16, max_leaf)
+    return X, Q, idx
+
+
+def test_leaf_bounds_bracket_every_point():
+    """Alg. 4's bounds: lb^2 <= ||o' - q'||^2 <= ub^2 for every point of every leaf."""
+    X, Q, idx = _range_index()
+    K = idx.K
+    for i in range(idx.L):
+        t = idx.trees[i]
+        P = idx.P[:, i * K:(i + 1) * K]
+        for q in list(Q[:3]) + [X[7]]:
+            qp = O.project(idx.A[i * K:(i + 1) * K], q[None, :])[0]
+            lb2, ub2 = O.leaf_bounds2(idx, i, qp)
+            d2 = ((P - qp[None, :]) ** 2).sum(1)
+            for leaf in range(t.n_leaves):
+                m = t.ids[t.offset[leaf]:t.offset[leaf + 1]]
+                assert (lb2[leaf] <= d2[m] * (1 + 1e-12) + 1e-12).all()
+                assert (d2[m] <= ub2[leaf] * (1 + 1e-12) + 1e-12).all()
+
+
+def test_det_range_query_is_the_projected_ball():
+    """Alg. 4/5 return exactly the points whose projection lies within r' of q'
+    (brute force over all points), through all three leaf cases (small K and
+    leaves so that some boxes lie inside the ball)."""
+    X, Q, idx = _range_index(K=2, max_leaf=4)
+    K = idx.K
+    seen = dict(skipped=0, accepted=0, refined=0)
+    for i in range(idx.L):
+        P = idx.P[:, i * K:(i + 1) * K]
+        # fresh queries, and one placed exactly on a point's projection (the
+        # radius-0 ball then holds that point: the test is <=, not <)
+        qps = [O.project(idx.A[i * K:(i + 1) * K], q[None, :])[0] for q in Q] + [P[7].copy()]
+        for qp in qps:
+            d = np.sqrt(((P - qp[None, :]) ** 2).sum(1))
+            for r in (0.0, np.quantile(d, 0.01), np.quantile(d, 0.2), np.quantile(d, 0.9), d.max() * 2):
+                st = {}
+                got = O.det_range_query(idx, i, qp, r, stats=st)
+                want = np.nonzero(d * d <= r * r)[0]
+                assert np.array_equal(got, want), (i, r)
+                for key in seen:
+                    seen[key] += st[key]
+    assert all(v > 0 for v in seen.values()), seen
+
+
+def test_rc_ann_special_cases():
+    """Alg. 6 in cases with a known answer: a radius covering everything gives
+    the exact nearest neighbour (with or without the |S| exit); radius 0 gives
+    nothing; a projected radius covering everything with c*r below the
+    nearest distance and no |S| exit gives nothing."""
+    X, Q, idx = _range_index()
+    n = idx.n
+    for q in Q:
+        nn_id, nn_d = O.exact_knn(X, q, 1)
+        r = O.rc_ann(idx, q, 1e9, 1.5, 1.0, beta=2.0)             # beta*n + 1 > n: no |S| exit
+        assert (r.id, r.stop, r.n_cand, r.trees) == (int(nn_id[0]), 2, n, idx.L)
+        assert r.dist == nn_d[0]
+        r = O.rc_ann(idx, q, 1e9, 1.5, 1.0, beta=1.0 / n)         # exit after the first tree
+        assert (r.id, r.stop, r.n_cand, r.trees) == (int(nn_id[0]), 1, n, 1)
+        r = O.rc_ann(idx, q, 0.0, 1.5, 3.0, beta=0.1)
+        assert (r.id, r.stop, r.n_cand) == (-1, 0, 0)
+        tiny = nn_d[0] / 10.0
+        r = O.rc_ann(idx, q, tiny, 1.5, 1e12 / tiny, beta=2.0)   # eps*r huge, c*r < nearest distance
+        assert (r.id, r.stop, r.n_cand) == (-1, 0, n)
+
+
 def test_tiny_config_quality():
     """Theorem 2 (statistical): on the tiny workload the result is a c^2-k-ANN for
     well over a (1/2 - 1/e) fraction of queries, and recall is high."""
