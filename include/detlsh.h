@@ -236,6 +236,28 @@ int detlsh_select_breakpoints(const float* Ps, int64_t n_s, int32_t LK, int32_t 
                               float* E, int32_t mem, void* stream);
 
 /*
+ * detlsh_rc_ann -- the (r,c)-ANN query of Alg. 6 on the index's L DE-Trees,
+ * with the exact range query of Alg. 4/5: in tree i (in order) a leaf whose
+ * lower-bound distance to q'_i exceeds eps*r is skipped, a leaf whose upper
+ * bound does not is taken whole, and any other leaf gives the points whose own
+ * projection lies within eps*r of q'_i (the outermost breakpoint edges count
+ * as -inf/+inf in both bounds); the results are added to S. Once
+ * |S| >= beta*n + 1 the point of S closest to q is returned; after the last
+ * tree it is returned if it lies within c*r, else nothing (id -1).
+ *
+ * Q [nq][d] in the index's dtype, r [nq] and c [nq] (FP32), out_id [nq]
+ * int64, out_dist [nq] FP64 (Euclidean; +inf when nothing is returned),
+ * out_stats [nq][3] int32 (|S| at the end, trees range-queried, stop: 1 the
+ * |S| bound, 2 within c*r, 0 nothing returned): all device pointers; the call
+ * only enqueues work on `stream`. Every value is FP64 with a fixed operation
+ * order, one CTA per query: a reference path for the paper's un-optimised
+ * query semantics, not a throughput path. Temporary storage: n bits per query.
+ */
+int detlsh_rc_ann(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dtype, const float* r,
+                  const float* c, double eps, double beta, int64_t* out_id, double* out_dist,
+                  int32_t* out_stats, void* stream);
+
+/*
  * detlsh_select_breakpoints_noalloc -- detlsh_select_breakpoints for callers
  * that must not allocate device memory, e.g. a serving process that keeps a
  * fixed device-memory footprint (an allocation may fail under memory pressure

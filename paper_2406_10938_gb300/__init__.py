@@ -21,6 +21,7 @@ from .binding import (  # noqa: F401
     detlsh_launch_count,
     detlsh_project,
     detlsh_query,
+    detlsh_rc_ann,
     detlsh_select_breakpoints,
     detlsh_trace_enable,
     detlsh_trace_get,

@@ -33,7 +33,8 @@ SYMBOLS = ("detlsh_build", "detlsh_query", "detlsh_free", "detlsh_export_size", 
            "detlsh_trace_get", "detlsh_launch_count", "detlsh_select_breakpoints_noalloc",
            "detlsh_plan_create", "detlsh_plan_query", "detlsh_plan_status", "detlsh_plan_info",
            "detlsh_plan_destroy", "detlsh_autotune", "detlsh_server_create", "detlsh_server_submit",
-           "detlsh_server_poll", "detlsh_server_replay", "detlsh_server_stats", "detlsh_server_destroy")
+           "detlsh_server_poll", "detlsh_server_replay", "detlsh_server_stats", "detlsh_server_destroy",
+           "detlsh_rc_ann")
 PENDING, EADMIT = 1, -5
 PLAN_GRAPH = 1
 TRACE_KEYS = ("sample_proj_ms", "breakpoints_ms", "encode_ms", "leaves_ms", "query_proj_ms", "lb_ms",
@@ -131,6 +132,8 @@ def lib(path: Optional[str] = None):
     L.detlsh_trace_get.restype = ctypes.c_int
     L.detlsh_launch_count.argtypes = []
     L.detlsh_launch_count.restype = i64
+    L.detlsh_rc_ann.argtypes = [vp, vp, i64, i32, vp, vp, dbl, dbl, vp, vp, vp, vp]
+    L.detlsh_rc_ann.restype = ctypes.c_int
     L.detlsh_select_breakpoints_noalloc.argtypes = [vp, i64, i32, i32, vp, vp]
     L.detlsh_select_breakpoints_noalloc.restype = ctypes.c_int
     L.detlsh_plan_create.argtypes = [vp, i64, i32, ctypes.POINTER(QueryParams), i32, vp, ctypes.POINTER(vp)]
@@ -248,6 +251,27 @@ def _query_args(Q, k, c, r_min):
     c = _per_query(c, nq, torch.float32, dev)
     r_min = _per_query(0.0 if r_min is None else r_min, nq, torch.float32, dev)
     return Q, k, c, r_min
+
+
+def detlsh_rc_ann(index: Index, Q: torch.Tensor, r, c, eps: float, beta: float):
+    """The (r,c)-ANN query of Alg. 6 (exact range query of Alg. 4/5 per tree,
+    FP64). Q [nq, d] on the GPU in the index's dtype; r, c scalars or [nq].
+    Returns (ids int64 [nq], -1 for nothing; distances float64 [nq];
+    stats int32 [nq, 3]: |S|, trees queried, stop rule)."""
+    Q = Q.contiguous()
+    if not Q.is_cuda:
+        raise DetlshError(-1, "detlsh_rc_ann", "takes device tensors")
+    nq = Q.shape[0]
+    dev = Q.device
+    r = torch.as_tensor(r, dtype=torch.float32, device=dev).expand(nq).contiguous()
+    c = torch.as_tensor(c, dtype=torch.float32, device=dev).expand(nq).contiguous()
+    ids = torch.empty(nq, dtype=torch.int64, device=dev)
+    dist = torch.empty(nq, dtype=torch.float64, device=dev)
+    stats = torch.empty(nq, 3, dtype=torch.int32, device=dev)
+    st = lib().detlsh_rc_ann(index.handle, _ptr(Q), nq, _dtype_code(Q), _ptr(r), _ptr(c), float(eps), float(beta),
+                             _ptr(ids), _ptr(dist), _ptr(stats), _stream(MEM_DEVICE))
+    _check(st, "detlsh_rc_ann")
+    return ids, dist, stats
 
 
 def detlsh_query(index: Index, Q: torch.Tensor, k, c, r_min=None, k_max: Optional[int] = None,

@@ -315,6 +315,32 @@ def test_det_only_exact_bit_parity(name, n, d, Nr, n_s, max_leaf, nq, k):
     idx.free()
 
 
+@pytest.mark.parametrize("name,d,K,L,Nr,max_leaf", [("tiny", 32, 8, 2, 16, 32), ("tiny", 32, 2, 2, 16, 4),
+                                                    ("serving", 32, 8, 3, 16, 16)])
+def test_rc_ann_exact_bit_parity(name, d, K, L, Nr, max_leaf):
+    """Alg. 6 with the exact range query of Alg. 4/5: id, distance, |S|, trees
+    queried and stop rule equal the oracle's bit for bit (exact inputs) over
+    radii from nothing found to everything found, with and without the |S|
+    exit."""
+    n, n_s, nq = 3_000, 300, 8
+    X, Q = make_workload(name, n=n, nq=nq, exact=True, d=d)
+    A = gaussian_projection(L, K, d, exact=True)
+    ids = sample_ids(n, n_s)
+    idx = gpu_build(X, A, ids, K, L, Nr, max_leaf)
+    ref = O.build_index(X.numpy(), A.numpy(), ids.numpy(), K, L, Nr, max_leaf)
+    nn = np.array([O.exact_knn(X.numpy(), q, 1)[1][0] for q in Q.numpy()])
+    for scale, c, eps, beta in ((0.0, 1.5, 3.0, 0.1), (0.5, 1.5, 3.0, 2.0), (1.0, 1.2, 1.0, 0.05),
+                                (1.5, 2.0, 2.0, 2.0), (4.0, 1.5, 3.0, 0.01), (1e3, 1.5, 3.0, 2.0)):
+        r = np.float32(nn * scale)
+        got_id, got_d, got_st = (t.cpu().numpy() for t in
+                                 pkg.detlsh_rc_ann(idx, Q.to(DEV), torch.from_numpy(r), c, eps, beta))
+        for qi in range(nq):
+            want = O.rc_ann(ref, Q.numpy()[qi], float(r[qi]), float(np.float32(c)), eps, beta)
+            assert (int(got_id[qi]), float(got_d[qi])) == (want.id, want.dist), (scale, qi)
+            assert tuple(got_st[qi]) == (want.n_cand, want.trees, want.stop), (scale, qi)
+    idx.free()
+
+
 # ------------------------------------------------------------------ query, float inputs
 @pytest.mark.parametrize("name,n,d,Nr,n_s,nq,k", [("tiny", 10_000, 32, 16, 1_000, 100, 10),
                                                   ("batching", 30_000, 96, 256, 3_000, 24, 50),
