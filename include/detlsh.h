@@ -182,6 +182,20 @@ int detlsh_query(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dty
 /* detlsh_free -- release an index and all its device memory (NULL is a no-op). */
 void detlsh_free(detlsh_index* idx);
 
+/*
+ * detlsh_insert -- add m points (ids n .. n+m-1, rows of X [m][d] in the
+ * index's dtype) to an index built with DETLSH_PROJ_FP32 (reading R14): their
+ * Alg. 2 codes against the index's breakpoints (Alg. 1 is not run again), by
+ * the projection kernel the build used, then the DE-Trees of all n+m points
+ * as Alg. 3 bulk-loads them (reading R3: order-free, so the index equals one
+ * built from all points with these breakpoints). The index then owns a copy
+ * of all points (a borrowed X is no longer referenced). Plans and servers of
+ * the index must be destroyed first; queries see the new points after the
+ * call returns (it synchronizes `stream`). On an error other than
+ * DETLSH_EINVAL the index must be freed.
+ */
+int detlsh_insert(detlsh_index* idx, const void* X, int64_t m, int32_t dtype, int32_t mem, void* stream);
+
 /* What detlsh_export copies out (test introspection and persistence). */
 typedef enum {
   DETLSH_EXPORT_A = 0,            /* float   [L*K][d]                          */

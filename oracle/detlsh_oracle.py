@@ -44,6 +44,9 @@ notes):
  R12 range tests compare squared distances in FP64.
  R13 (r,c)-ANN (Alg. 6): |S| >= beta*n + 1 compared as real numbers; a
      query that returns nothing reports id -1.
+ R14 insertion: new points are encoded against the existing breakpoints and
+     the trees of all points are those of R3 (order-free), not the result of
+     Alg. 3's on-line splits in arrival order.
 """
 
 from __future__ import annotations
@@ -225,6 +228,7 @@ class Index:
     n_regions: int
     P: Optional[np.ndarray] = None       # FP64 projections [n, L*K] (kept for tests)
     codes: Optional[np.ndarray] = None   # uint8 [n, L*K]
+    max_size: int = 0                    # max_size of Alg. 3
 
     @property
     def n(self) -> int:
@@ -240,7 +244,23 @@ def build_index(X, A, sample, K: int, L: int, n_regions: int, max_size: int) -> 
     E = select_breakpoints(P[sample], n_regions)
     codes = encode(P, E)
     trees = [build_tree(codes[:, i * K:(i + 1) * K], n_regions, max_size) for i in range(L)]
-    return Index(X=X, A=A, E=E, trees=trees, K=K, L=L, n_regions=n_regions, P=P, codes=codes)
+    return Index(X=X, A=A, E=E, trees=trees, K=K, L=L, n_regions=n_regions, P=P, codes=codes, max_size=max_size)
+
+
+def insert_points(index: Index, X_new) -> Index:
+    """Insertion of new points (ids n, n+1, ...) into an index (reading R14):
+    their codes by Alg. 2 against the index's breakpoints (Alg. 1 is not run
+    again), then the DE-Trees of all points as Alg. 3 builds them under
+    reading R3 (bulk-loaded, so the result does not depend on the order in
+    which points arrive)."""
+    X_new = np.asarray(X_new)
+    X = np.concatenate([index.X, X_new.astype(index.X.dtype)], axis=0)
+    P = np.concatenate([index.P, project(index.A, X_new)], axis=0)
+    codes = np.concatenate([index.codes, encode(P[index.n:], index.E)], axis=0)
+    K, L = index.K, index.L
+    trees = [build_tree(codes[:, i * K:(i + 1) * K], index.n_regions, index.max_size) for i in range(L)]
+    return Index(X=X, A=index.A, E=index.E, trees=trees, K=K, L=L, n_regions=index.n_regions, P=P, codes=codes,
+                 max_size=index.max_size)
 
 
 # ---------------------------------------------------------------- query phase

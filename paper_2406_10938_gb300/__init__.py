@@ -18,6 +18,7 @@ from .binding import (  # noqa: F401
     detlsh_eps_lemma3,
     detlsh_export,
     detlsh_info,
+    detlsh_insert,
     detlsh_launch_count,
     detlsh_project,
     detlsh_query,

@@ -34,7 +34,7 @@ SYMBOLS = ("detlsh_build", "detlsh_query", "detlsh_free", "detlsh_export_size", 
            "detlsh_plan_create", "detlsh_plan_query", "detlsh_plan_status", "detlsh_plan_info",
            "detlsh_plan_destroy", "detlsh_autotune", "detlsh_server_create", "detlsh_server_submit",
            "detlsh_server_poll", "detlsh_server_replay", "detlsh_server_stats", "detlsh_server_destroy",
-           "detlsh_rc_ann")
+           "detlsh_rc_ann", "detlsh_insert")
 PENDING, EADMIT = 1, -5
 PLAN_GRAPH = 1
 TRACE_KEYS = ("sample_proj_ms", "breakpoints_ms", "encode_ms", "leaves_ms", "query_proj_ms", "lb_ms",
@@ -134,6 +134,8 @@ def lib(path: Optional[str] = None):
     L.detlsh_launch_count.restype = i64
     L.detlsh_rc_ann.argtypes = [vp, vp, i64, i32, vp, vp, dbl, dbl, vp, vp, vp, vp]
     L.detlsh_rc_ann.restype = ctypes.c_int
+    L.detlsh_insert.argtypes = [vp, vp, i64, i32, i32, vp]
+    L.detlsh_insert.restype = ctypes.c_int
     L.detlsh_select_breakpoints_noalloc.argtypes = [vp, i64, i32, i32, vp, vp]
     L.detlsh_select_breakpoints_noalloc.restype = ctypes.c_int
     L.detlsh_plan_create.argtypes = [vp, i64, i32, ctypes.POINTER(QueryParams), i32, vp, ctypes.POINTER(vp)]
@@ -251,6 +253,16 @@ def _query_args(Q, k, c, r_min):
     c = _per_query(c, nq, torch.float32, dev)
     r_min = _per_query(0.0 if r_min is None else r_min, nq, torch.float32, dev)
     return Q, k, c, r_min
+
+
+def detlsh_insert(index: Index, X: torch.Tensor) -> None:
+    """Add the rows of X (host or device, the index's dtype) as points
+    n, n+1, ...: codes against the index's breakpoints, then the leaves of all
+    points rebuilt (the index then owns a copy of every point)."""
+    X = X.contiguous()
+    mem = MEM_DEVICE if X.is_cuda else MEM_HOST
+    st = lib().detlsh_insert(index.handle, _ptr(X), X.shape[0], _dtype_code(X), mem, _stream(mem))
+    _check(st, "detlsh_insert")
 
 
 def detlsh_rc_ann(index: Index, Q: torch.Tensor, r, c, eps: float, beta: float):

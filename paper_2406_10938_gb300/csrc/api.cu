@@ -705,6 +705,78 @@ void detlsh_free(detlsh_index* idx) {
   free_index(idx);
 }
 
+int detlsh_insert(detlsh_index* idx, const void* X, int64_t m, int32_t dtype, int32_t mem, void* stream) {
+  g_err[0] = 0;
+  DL_REQUIRE(idx, "NULL index");
+  DL_REQUIRE(m >= 0, "m must be >= 0");
+  if (m == 0) return DETLSH_OK;
+  DL_REQUIRE(X, "NULL points");
+  DL_REQUIRE(mem == DETLSH_MEM_HOST || mem == DETLSH_MEM_DEVICE, "bad mem flag");
+  DL_REQUIRE(dtype == idx->dtype, "the points must have the index's dtype");
+  DL_REQUIRE(idx->proj_mode == DETLSH_PROJ_FP32, "insertion needs an index built with the FP32 projection");
+  const int64_t n = idx->n, n2 = n + m;
+  DL_REQUIRE(n2 * (int64_t)idx->L < ((int64_t)1 << 32), "need (n+m)*L < 2^32");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int K = idx->K, L = idx->L, LK = K * L, d = (int)idx->d, Nr = idx->Nr;
+  const size_t row = (size_t)d * dtype_size(dtype);
+  // the points: one array of n+m rows, owned by the index from now on
+  void* Xn = nullptr;
+  DL_TRY(index_alloc(&Xn, row * n2, s));
+  DL_CUDA(cudaMemcpyAsync(Xn, idx->X, row * n, cudaMemcpyDeviceToDevice, s));
+  DL_CUDA(cudaMemcpyAsync(static_cast<char*>(Xn) + row * n, X, row * m,
+                          mem == DETLSH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  if (idx->owns_x) cudaFreeAsync(const_cast<void*>(idx->X), s);
+  idx->X = Xn;
+  idx->owns_x = true;
+  // Alg. 2 codes of the new points against the index's breakpoints, by the
+  // projection kernel the build used (the new rows start 16-byte aligned
+  // whenever the tensor-core paths apply: d*4 % 16 == 0 resp. d % 16 == 0)
+  const void* Xm = static_cast<const char*>(Xn) + row * n;
+  Scratch cnew;
+  DL_TRY(cnew.alloc((size_t)m * LK, s));
+  if (idx->Atf) {
+    DL_TRY(launch_project_tf32(static_cast<const float*>(Xm), m, d, idx->Atf, LK, K, idx->E, idx->Rtab, idx->Rlo,
+                               idx->Rinv, Nr, cnew.as<uint8_t>(), nullptr, 0, 0, idx->d_err, s));
+  } else if (idx->Ab3) {
+    DL_TRY(launch_project_bf16x3(static_cast<const uint8_t*>(Xm), m, d, idx->Ab3, LK, K, idx->E, idx->Rtab,
+                                 idx->Rlo, idx->Rinv, Nr, cnew.as<uint8_t>(), nullptr, 0, 0, idx->d_err, s));
+  } else {
+    DL_TRY(launch_project_encode_t(Xm, dtype, m, d, idx->At, K, L, idx->E, idx->Rtab, idx->Rlo, idx->Rinv, Nr,
+                                   cnew.as<uint8_t>(), s));
+  }
+  if (idx->Atf || idx->Ab3) DL_TRY(check_tc_error(idx->d_err, s));
+  // codes [L][n+m][K]: per tree the old rows, then the new ones
+  uint8_t* codes2 = nullptr;
+  DL_TRY(index_alloc(&codes2, (size_t)n2 * LK, s));
+  for (int t = 0; t < L; ++t) {
+    DL_CUDA(cudaMemcpyAsync(codes2 + (size_t)t * n2 * K, idx->codes + (size_t)t * n * K, (size_t)n * K,
+                            cudaMemcpyDeviceToDevice, s));
+    DL_CUDA(cudaMemcpyAsync(codes2 + ((size_t)t * n2 + n) * K, cnew.as<uint8_t>() + (size_t)t * m * K,
+                            (size_t)m * K, cudaMemcpyDeviceToDevice, s));
+  }
+  cudaFreeAsync(idx->codes, s);
+  idx->codes = codes2;
+  // Alg. 3 over all points (reading R3): the leaf tables are rebuilt
+  void* old[] = {idx->leaf_ids, idx->leaf_pos, idx->leaf_base, idx->leaf_range, idx->leaf_plen,
+                 idx->leaf_prefix, idx->leaf_lo, idx->leaf_hi, idx->leaf_tree};
+  for (void* p : old)
+    if (p) cudaFreeAsync(p, s);
+  idx->leaf_ids = nullptr;
+  idx->leaf_pos = nullptr;
+  idx->leaf_base = nullptr;
+  idx->leaf_range = nullptr;
+  idx->leaf_plen = nullptr;
+  idx->leaf_prefix = nullptr;
+  idx->leaf_lo = nullptr;
+  idx->leaf_hi = nullptr;
+  idx->leaf_tree = nullptr;
+  idx->n = n2;
+  DL_TRY(index_alloc(&idx->leaf_ids, sizeof(uint32_t) * n2 * L, s));
+  DL_TRY(build_leaves(idx, s));
+  DL_CUDA(cudaStreamSynchronize(s));
+  return DETLSH_OK;
+}
+
 int64_t detlsh_export_size(const detlsh_index* idx, int32_t what) {
   if (!idx) return DETLSH_EINVAL;
   const int64_t LK = (int64_t)idx->K * idx->L;

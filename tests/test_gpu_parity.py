@@ -341,6 +341,41 @@ def test_rc_ann_exact_bit_parity(name, d, K, L, Nr, max_leaf):
     idx.free()
 
 
+@pytest.mark.parametrize("name,d", [("tiny", 32), ("serving", 32), ("mid", 128), ("tiny", 30)])
+def test_insert_exact_bit_parity(name, d):
+    """Insertion (reading R14): points added in two batches (device, then host
+    memory) to an index of the first 2,000 get the oracle's codes, leaves and
+    query results bit for bit (exact inputs), through the TF32, uint8 tensor-
+    core and CUDA-core (d = 30) encodings."""
+    n1, n, K, L, Nr, max_leaf, nq, k, beta = 2_000, 3_000, 16, 4, 16, 32, 12, 10, 0.1
+    X, Q = make_workload(name, n=n, nq=nq, exact=True, d=d)
+    A = gaussian_projection(L, K, d, exact=True)
+    ids = sample_ids(n1, 300)
+    idx = gpu_build(X[:n1], A, ids, K, L, Nr, max_leaf)
+    pkg.detlsh_insert(idx, X[n1:2_600].to(DEV))
+    pkg.detlsh_insert(idx, X[2_600:])
+    assert idx.info()["n"] == n
+    ref = O.build_index(X[:n1].numpy(), A.numpy(), ids.numpy(), K, L, Nr, max_leaf)
+    ref = O.insert_points(O.insert_points(ref, X[n1:2_600].numpy()), X[2_600:].numpy())
+    assert np.array_equal(gpu_codes(idx, n, K, L), ref.codes)
+    assert_trees_equal(gpu_trees(idx, K, L, n), ref.trees)
+    eps = O.eps_from_lemma3(K, L)
+    g = torch.Generator().manual_seed(3)
+    cs = torch.tensor([1.2, 1.5, 2.0])[torch.randint(0, 3, (nq,), generator=g)]
+    ks = torch.randint(1, k + 1, (nq,), generator=g, dtype=torch.int32)
+    rm = torch.zeros(nq, dtype=torch.float32)
+    out_ids, out_dist, stats, _ = pkg.detlsh_query(idx, Q.to(DEV), ks.to(DEV), cs.to(DEV), rm.to(DEV), k_max=k,
+                                                   eps=eps, beta=beta)
+    out_ids, out_dist, stats = out_ids.cpu().numpy(), out_dist.cpu().numpy(), stats.cpu().numpy()
+    res = oracle_queries(ref, Q.numpy(), ks.numpy(), cs.numpy(), rm.numpy(), eps, beta, keep=False)
+    for qi, r in enumerate(res):
+        kq = int(ks[qi])
+        assert (stats[qi, 0], stats[qi, 1], stats[qi, 2]) == (r.n_cand, r.rounds, r.stop), qi
+        assert np.array_equal(out_ids[qi, :kq], r.ids[:kq]), qi
+        assert np.array_equal(out_dist[qi, :kq], np.float32(r.dist[:kq])), qi
+    idx.free()
+
+
 # ------------------------------------------------------------------ query, float inputs
 @pytest.mark.parametrize("name,n,d,Nr,n_s,nq,k", [("tiny", 10_000, 32, 16, 1_000, 100, 10),
                                                   ("batching", 30_000, 96, 256, 3_000, 24, 50),

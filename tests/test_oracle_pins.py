@@ -388,6 +388,32 @@ def test_rc_ann_special_cases():
         assert (r.id, r.stop, r.n_cand) == (-1, 0, n)
 
 
+def test_insert_equals_building_from_all_points():
+    """Inserting points whose arrival leaves the breakpoints unchanged (the
+    sample lies among the first points) gives the index built from all points
+    at once: codes, trees and query results; inserting nothing changes nothing."""
+    X, Q = make_workload("tiny", n=3000, nq=4)
+    X, Q = X.numpy(), Q.numpy()
+    A = gaussian_projection(3, 8, X.shape[1]).numpy()
+    ids = sample_ids(2000, 300).numpy()            # all among the first 2,000 points
+    base = O.build_index(X[:2000], A, ids, 8, 3, 16, 24)
+    grown = O.insert_points(O.insert_points(base, X[2000:2600]), X[2600:])
+    full = O.build_index(X, A, ids, 8, 3, 16, 24)
+    assert np.array_equal(grown.E, full.E)
+    assert np.array_equal(grown.codes, full.codes)
+    for a, b in zip(grown.trees, full.trees):
+        assert np.array_equal(a.ids, b.ids) and np.array_equal(a.offset, b.offset)
+        assert np.array_equal(a.plen, b.plen) and np.array_equal(a.prefix, b.prefix)
+    eps = O.eps_from_lemma3(8, 3)
+    for q in Q:
+        ra = O.c2k_ann(grown, q, 5, 1.5, 0.0, eps, 0.1)
+        rb = O.c2k_ann(full, q, 5, 1.5, 0.0, eps, 0.1)
+        assert ra.ids.tolist() == rb.ids.tolist() and (ra.n_cand, ra.rounds, ra.stop) == (rb.n_cand, rb.rounds, rb.stop)
+    same = O.insert_points(base, X[:0])
+    assert np.array_equal(same.codes, base.codes)
+    assert all(np.array_equal(a.ids, b.ids) for a, b in zip(same.trees, base.trees))
+
+
 def test_tiny_config_quality():
     """Theorem 2 (statistical): on the tiny workload the result is a c^2-k-ANN for
     well over a (1/2 - 1/e) fraction of queries, and recall is high."""
