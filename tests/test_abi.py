@@ -68,6 +68,13 @@ def test_build_rejects_bad_arguments_before_any_device_work(L):
         assert L.detlsh_last_error()
 
 
+def test_insert_and_rc_ann_reject_bad_arguments(L):
+    assert L.detlsh_insert(None, None, 5, 0, 1, None) == -1
+    assert L.detlsh_last_error()
+    assert L.detlsh_rc_ann(None, None, 4, 0, None, None, 3.0, 0.1, None, None, None, None) == -1
+    assert L.detlsh_last_error()
+
+
 def test_query_rejects_null_index(L):
     st = L.detlsh_query(None, None, 0, 0, None, None, None, 1, None, None, None, None, 0, None)
     assert st == -1
