@@ -44,7 +44,15 @@ typedef enum { DETLSH_MEM_HOST = 0, DETLSH_MEM_DEVICE = 1 } detlsh_mem;
 
 /* projection arithmetic of the build (Eq. 1 for every point) */
 typedef enum {
-  DETLSH_PROJ_FP32 = 0,  /* FP32 fused multiply-add on the CUDA cores */
+  DETLSH_PROJ_FP32 = 0,  /* FP32-faithful projections: on the tensor cores
+                            as a TF32 split of points and hash vectors (FP32
+                            points, d <= 256, d % 4 == 0, L*K <= 64) or as
+                            uint8 points against the hash vectors in three
+                            BF16 parts (d <= 256, d % 16 == 0, L*K <= 64),
+                            both with a 16-byte aligned X; otherwise FP32
+                            fused multiply-add on the CUDA cores. Exact
+                            whenever the products and sums are exact in FP32;
+                            else within about 1e-5 of sum |a x| (d <= 256). */
   DETLSH_PROJ_BF16 = 1   /* BF16 inputs (points and hash vectors rounded to
                             BF16; the index keeps a BF16 copy of X) on the
                             tensor cores with FP32 accumulation; needs
