@@ -381,6 +381,10 @@ def test_rc_ann_special_cases():
         assert r.dist == nn_d[0]
         r = O.rc_ann(idx, q, 1e9, 1.5, 1.0, beta=1.0 / n)         # exit after the first tree
         assert (r.id, r.stop, r.n_cand, r.trees) == (int(nn_id[0]), 1, n, 1)
+        # |S| = n after the first tree, beta*n = n - 1/2: the bound beta*n + 1 is
+        # not reached, so every tree is queried and the c*r test decides
+        r = O.rc_ann(idx, q, 1e9, 1.5, 1.0, beta=(n - 0.5) / n)
+        assert (r.id, r.stop, r.n_cand, r.trees) == (int(nn_id[0]), 2, n, idx.L)
         r = O.rc_ann(idx, q, 0.0, 1.5, 3.0, beta=0.1)
         assert (r.id, r.stop, r.n_cand) == (-1, 0, 0)
         tiny = nn_d[0] / 10.0
