@@ -77,13 +77,18 @@ typedef struct detlsh_index detlsh_index;
 /* Index parameters (Alg. 1-3 inputs; Sec. 5.2 and Sec. 6.1 give the paper's
  * defaults K=16, L=4, N_r=256, n_s=0.1n; max_size is not given there). */
 typedef struct {
-  int32_t K;          /* hash functions per projected space                */
-  int32_t L;          /* projected spaces = DE-Trees                       */
-  int32_t n_regions;  /* N_r: regions per projected dimension              */
-  int32_t max_leaf;   /* max_size of Alg. 3 (>= 1)                         */
-  int64_t n_s;        /* sample size: number of entries in sample_ids      */
-  int32_t proj_mode;  /* detlsh_proj_mode                                  */
-  int32_t flags;      /* DETLSH_BORROW_X | DETLSH_DEDUP_POS, or 0          */
+  int32_t K;            /* hash functions per projected space                */
+  int32_t L;            /* projected spaces = DE-Trees                       */
+  int32_t n_regions;    /* N_r: regions per projected dimension              */
+  int32_t max_leaf;     /* max_size of Alg. 3 (>= 1)                         */
+  int64_t sample_size;  /* n_s of Alg. 1: the number of entries of sample_ids,
+                           or, when the library draws the sample, its size
+                           (0: ceil(0.1*n), the paper's n_s = 0.1n, Sec. 6.1) */
+  int32_t proj_mode;    /* detlsh_proj_mode                                  */
+  int32_t flags;        /* DETLSH_BORROW_X | DETLSH_DEDUP_POS, or 0          */
+  uint64_t seed;        /* seed of the draws the library makes when A or
+                           sample_ids is NULL (detlsh_draw_hashes,
+                           detlsh_draw_sample)                               */
 } detlsh_params;
 
 /* Launch shapes of the query pipeline (no counterpart in the paper). The
@@ -127,6 +132,10 @@ typedef struct {
                          exact FP32 distances before the top-k            */
   int32_t reserved;
   const detlsh_tuning* tuning;  /* launch shapes; NULL: defaults             */
+  float* qproj;       /* optional [nq][L*K]: the projected queries q' (Alg. 7,
+                         H_i(q)) in FP32 exactly as the query's later steps
+                         read them, in the call's `mem` space; NULL to skip
+                         (plans and detlsh_autotune take NULL)             */
 } detlsh_query_params;
 
 /*
@@ -135,11 +144,16 @@ typedef struct {
  *
  *   X           [n][d] row-major points, dtype DETLSH_F32 or DETLSH_U8 (uint8
  *               values are widened to FP32 inside the kernels).
- *   A           [L*K][d] row-major FP32 hash vectors of Eq. 1 (entries drawn
- *               from N(0,1) by the caller); row r = i*K + j is a_ij, the j-th
- *               hash of projected space i.
+ *   A           [L*K][d] row-major FP32 hash vectors of Eq. 1 (entries from
+ *               N(0,1)); row r = i*K + j is a_ij, the j-th hash of projected
+ *               space i. NULL: drawn by the library, detlsh_draw_hashes with
+ *               params->seed (the paper's problem statement needs only the
+ *               dataset and K, L, N_r).
  *   sample_ids  [n_s] distinct point ids in [0, n) whose projections select the
- *               breakpoints (Alg. 1: the sample of the n points).
+ *               breakpoints (Alg. 1: the sample of the n points), n_s =
+ *               params->sample_size. NULL: drawn by the library,
+ *               detlsh_draw_sample with params->seed, of params->sample_size
+ *               points (0: ceil(0.1*n)).
  *   params      see detlsh_params.
  *   out         receives the new index (free it with detlsh_free).
  *
@@ -215,8 +229,10 @@ typedef enum {
                                      tree's part of LEAF_IDS), count           */
   DETLSH_EXPORT_LEAF_PLEN = 6,    /* uint8   [n_leaves][K] prefix bits per dim  */
   DETLSH_EXPORT_LEAF_PREFIX = 7,  /* uint8   [n_leaves][K] prefix value per dim */
-  DETLSH_EXPORT_SAMPLE_PROJ = 8   /* float   [L*K][n_s] projections of the
+  DETLSH_EXPORT_SAMPLE_PROJ = 8,  /* float   [L*K][n_s] projections of the
                                      sampled points                            */
+  DETLSH_EXPORT_SAMPLE_IDS = 9    /* int64   [n_s] the sampled point ids,
+                                     ascending as given or drawn               */
 } detlsh_export_what;
 
 /* detlsh_export_size -- bytes detlsh_export needs for `what` (< 0 on error). */
@@ -284,14 +300,16 @@ int detlsh_rc_ann(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dt
  * that must not allocate device memory, e.g. a serving process that keeps a
  * fixed device-memory footprint (an allocation may fail under memory pressure
  * mid-request; freeing synchronizes the device) or an application whose own
- * allocator owns all device memory. The paper has no counterpart: this is an
- * integration variant of the same Alg. 1 selection, with the same results.
+ * allocator owns all device memory. The paper has no counterpart; the results
+ * are those of detlsh_select_breakpoints.
  *
- * Ps [LK][n_s] and E [LK][N_r+1] are device pointers; the call only enqueues
- * work on `stream`. Temporary storage comes from one fixed 7 MiB array built
- * into the library (held by every GPU that loads it, until process exit), so
- * n_s*LK must not exceed DETLSH_NOALLOC_MAX_ITEMS (DETLSH_EINVAL otherwise).
- * The first call on each device looks up that array's device address; make it
+ * Ps [LK][n_s] and E [LK][N_r+1] must be device (or managed) pointers, else
+ * DETLSH_EINVAL before any device work; the call only enqueues work on
+ * `stream`. Temporary storage comes from one fixed 7 MiB array built into the
+ * library (held by every GPU that loads it, until process exit), so n_s*LK
+ * must not exceed DETLSH_NOALLOC_MAX_ITEMS (DETLSH_EINVAL otherwise). Each
+ * call looks up that array's device address on the current device; the first
+ * call on a device may load the library's device code there, so make it
  * before any stream capture. All calls share the array: calls whose GPU work
  * overlaps (e.g. on two streams) race and must be serialized by the caller.
  */
@@ -427,6 +445,31 @@ int detlsh_server_stats(detlsh_server* srv, int64_t* out8);
  * frees the server (uncollected results are dropped). */
 void detlsh_server_destroy(detlsh_server* srv);
 
+/*
+ * The random draws of the method from a seed (the paper fixes no generator;
+ * these are the library's, documented so that others can reproduce them).
+ * Both run on the host, write host memory and need no GPU. The generator is
+ * splitmix64 (Steele, Lea, Flood, OOPSLA 2014): state += 0x9E3779B97F4A7C15;
+ * z = state; z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9;
+ * z = (z ^ (z >> 27)) * 0x94D049BB133111EB; output z ^ (z >> 31).
+ *
+ * detlsh_draw_hashes -- the hash vectors of Eq. 1, A [LK][d] FP32 (row-major,
+ *   row r = i*K + j): state = seed; entries in row-major order two at a time
+ *   by Box-Muller in FP64 from two consecutive outputs z1, z2:
+ *   u1 = ((z1 >> 11) + 1) * 2^-53, u2 = (z2 >> 11) * 2^-53,
+ *   rho = sqrt(-2 ln u1), theta = (2 pi) u2, entries rho cos theta and
+ *   rho sin theta (the second dropped past the end), each rounded to FP32.
+ *   DETLSH_EINVAL unless 1 <= LK <= 256 and 1 <= d <= 65536.
+ * detlsh_draw_sample -- the sample of Alg. 1, n_s distinct ids of [0, n)
+ *   ascending: state = seed ^ 0x5A; a partial Fisher-Yates shuffle of the
+ *   positions 0..n-1 where step i = 0..n_s-1 swaps positions i and
+ *   i + ((z * (n - i)) >> 64) (z the next output, 128-bit product); the
+ *   sample is the first n_s positions, sorted. DETLSH_EINVAL unless
+ *   1 <= n_s <= n < 2^32.
+ */
+int detlsh_draw_hashes(uint64_t seed, int32_t LK, int32_t d, float* A);
+int detlsh_draw_sample(uint64_t seed, int64_t n, int64_t n_s, int64_t* ids);
+
 /* detlsh_eps_lemma3 -- eps of Lemma 3 (Eq. 2): eps^2 is the upper
  * alpha1-quantile of chi2(K), alpha1 = exp(-1/L). Returns < 0 on bad input. */
 double detlsh_eps_lemma3(int32_t K, int32_t L);
@@ -450,6 +493,16 @@ double detlsh_eps_lemma3(int32_t K, int32_t L);
 int detlsh_trace_enable(int32_t on);
 int detlsh_trace_get(double* out, int32_t len);
 int64_t detlsh_launch_count(void);
+
+/*
+ * detlsh_memory_stats -- device memory in use by stream-ordered allocation on
+ * the current device (no counterpart in the paper): out[0] bytes in use in the
+ * library's own pool (index arrays and scratch), out[1] its high-water mark,
+ * out[2] bytes in use in the device's default pool, out[3] its high-water
+ * mark. With reset_peak != 0 both high-water marks are reset to the current
+ * use after they are read. Returns the number of entries written (<= len).
+ */
+int detlsh_memory_stats(int32_t reset_peak, int64_t* out, int32_t len);
 
 /* detlsh_strerror -- static text for a detlsh_status value. */
 const char* detlsh_strerror(int status);

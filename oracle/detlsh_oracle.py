@@ -47,6 +47,9 @@ notes):
  R14 insertion: new points are encoded against the existing breakpoints and
      the trees of all points are those of R3 (order-free), not the result of
      Alg. 3's on-line splits in arrival order.
+ R15 random draws (the paper names no generator): splitmix64 feeding
+     Box-Muller for the N(0,1) hash vectors and a partial Fisher-Yates
+     shuffle for the sample (``draw_hashes``, ``draw_sample``).
 """
 
 from __future__ import annotations
@@ -58,6 +61,70 @@ from typing import List, Optional
 import numpy as np
 
 ROUND_CAP = 256
+
+
+# ---------------------------------------------------------------- random draws
+# The paper draws the hash vectors from N(0,1) (Eq. 1) and samples the points
+# for Alg. 1 without fixing a generator. Reading R15: one splitmix64 stream
+# (Steele, Lea and Flood, OOPSLA 2014) feeds the Box-Muller transform for the
+# hash vectors (state = seed) and a partial Fisher-Yates shuffle for the sample
+# (state = seed XOR 0x5A).
+_MASK64 = (1 << 64) - 1
+
+
+def splitmix64(state: int):
+    """The splitmix64 output sequence from an initial 64-bit state: the state
+    advances by 0x9E3779B97F4A7C15 and each output is the new state mixed by
+    two xor-shift-multiply steps and a final xor-shift."""
+    while True:
+        state = (state + 0x9E3779B97F4A7C15) & _MASK64
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+        yield z ^ (z >> 31)
+
+
+def draw_hashes(seed: int, L: int, K: int, d: int) -> np.ndarray:
+    """The L*K hash vectors of Eq. 1 as A [L*K, d] FP32 (row r = i*K + j),
+    entries N(0,1) by Box-Muller (Box and Muller, 1958) in FP64: two outputs
+    give u1 in (0, 1] and u2 in [0, 1) (53 bits each), rho = sqrt(-2 ln u1),
+    theta = 2 pi u2, and the next two entries in row-major order are
+    rho cos theta and rho sin theta, each rounded to FP32 (reading R15)."""
+    count = L * K * d
+    out = np.empty(count, dtype=np.float32)
+    g = splitmix64(int(seed) & _MASK64)
+    for e in range(0, count, 2):
+        u1 = float((next(g) >> 11) + 1) * 2.0 ** -53
+        u2 = float(next(g) >> 11) * 2.0 ** -53
+        rho = math.sqrt(-2.0 * math.log(u1))
+        theta = 2.0 * math.pi * u2
+        out[e] = np.float32(rho * math.cos(theta))
+        if e + 1 < count:
+            out[e + 1] = np.float32(rho * math.sin(theta))
+    return out.reshape(L * K, d)
+
+
+def draw_sample(seed: int, n: int, n_s: int) -> np.ndarray:
+    """The sample of Alg. 1: n_s distinct ids of [0, n), ascending, from a
+    partial Fisher-Yates shuffle of the positions 0..n-1 where step i swaps
+    position i with i + floor(z (n - i) / 2^64), z the next output (reading
+    R15)."""
+    if not 1 <= n_s <= n:
+        raise ValueError("need 1 <= n_s <= n")
+    g = splitmix64((int(seed) ^ 0x5A) & _MASK64)
+    moved = {}
+    out = np.empty(n_s, dtype=np.int64)
+    for i in range(n_s):
+        j = i + ((next(g) * (n - i)) >> 64)
+        vi, vj = moved.get(i, i), moved.get(j, j)
+        moved[i], moved[j] = vj, vi
+        out[i] = vj
+    return np.sort(out)
+
+
+def default_sample_size(n: int) -> int:
+    """Sec. 6.1 sets n_s = 0.1 n; as an integer, ceil(0.1 n)."""
+    return (int(n) + 9) // 10
 
 
 # ---------------------------------------------------------------- parameters

@@ -14,6 +14,9 @@ from .binding import (  # noqa: F401
     detlsh_plan_query,
     detlsh_plan_status,
     detlsh_build,
+    detlsh_draw_hashes,
+    detlsh_draw_sample,
+    detlsh_memory_stats,
     detlsh_encode_values,
     detlsh_eps_lemma3,
     detlsh_export,

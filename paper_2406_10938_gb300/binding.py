@@ -21,10 +21,11 @@ MEM_HOST, MEM_DEVICE = 0, 1
 BORROW_X = 1
 DEDUP_POS = 2
 EXPORT = {"A": 0, "EDGES": 1, "CODES": 2, "LEAF_IDS": 3, "LEAF_BASE": 4, "LEAF_RANGE": 5,
-          "LEAF_PLEN": 6, "LEAF_PREFIX": 7, "SAMPLE_PROJ": 8}
+          "LEAF_PLEN": 6, "LEAF_PREFIX": 7, "SAMPLE_PROJ": 8, "SAMPLE_IDS": 9}
 _EXPORT_DTYPE = {"A": torch.float32, "EDGES": torch.float32, "CODES": torch.uint8,
                  "LEAF_IDS": torch.int32, "LEAF_BASE": torch.int64, "LEAF_RANGE": torch.int32,
-                 "LEAF_PLEN": torch.uint8, "LEAF_PREFIX": torch.uint8, "SAMPLE_PROJ": torch.float32}
+                 "LEAF_PLEN": torch.uint8, "LEAF_PREFIX": torch.uint8, "SAMPLE_PROJ": torch.float32,
+                 "SAMPLE_IDS": torch.int64}
 
 # every symbol declared in include/detlsh.h
 SYMBOLS = ("detlsh_build", "detlsh_query", "detlsh_free", "detlsh_export_size", "detlsh_export",
@@ -34,7 +35,8 @@ SYMBOLS = ("detlsh_build", "detlsh_query", "detlsh_free", "detlsh_export_size", 
            "detlsh_plan_create", "detlsh_plan_query", "detlsh_plan_status", "detlsh_plan_info",
            "detlsh_plan_destroy", "detlsh_autotune", "detlsh_server_create", "detlsh_server_submit",
            "detlsh_server_poll", "detlsh_server_replay", "detlsh_server_stats", "detlsh_server_destroy",
-           "detlsh_rc_ann", "detlsh_insert")
+           "detlsh_rc_ann", "detlsh_insert", "detlsh_memory_stats", "detlsh_draw_hashes",
+           "detlsh_draw_sample")
 PENDING, EADMIT = 1, -5
 PLAN_GRAPH = 1
 TRACE_KEYS = ("sample_proj_ms", "breakpoints_ms", "encode_ms", "leaves_ms", "query_proj_ms", "lb_ms",
@@ -50,8 +52,8 @@ class DetlshError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("L", ctypes.c_int32), ("n_regions", ctypes.c_int32),
-                ("max_leaf", ctypes.c_int32), ("n_s", ctypes.c_int64), ("proj_mode", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("max_leaf", ctypes.c_int32), ("sample_size", ctypes.c_int64), ("proj_mode", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
 class Tuning(ctypes.Structure):
@@ -84,7 +86,7 @@ class QueryParams(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("beta", ctypes.c_double),
                 ("cand_ids", ctypes.c_void_p), ("cand_cap", ctypes.c_int64),
                 ("shortlist", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("tuning", ctypes.POINTER(Tuning))]
+                ("tuning", ctypes.POINTER(Tuning)), ("qproj", ctypes.c_void_p)]
 
 
 _lib = None
@@ -136,6 +138,12 @@ def lib(path: Optional[str] = None):
     L.detlsh_rc_ann.restype = ctypes.c_int
     L.detlsh_insert.argtypes = [vp, vp, i64, i32, i32, vp]
     L.detlsh_insert.restype = ctypes.c_int
+    L.detlsh_draw_hashes.argtypes = [ctypes.c_uint64, i32, i32, vp]
+    L.detlsh_draw_hashes.restype = ctypes.c_int
+    L.detlsh_draw_sample.argtypes = [ctypes.c_uint64, i64, i64, vp]
+    L.detlsh_draw_sample.restype = ctypes.c_int
+    L.detlsh_memory_stats.argtypes = [i32, ctypes.POINTER(i64), i32]
+    L.detlsh_memory_stats.restype = ctypes.c_int
     L.detlsh_select_breakpoints_noalloc.argtypes = [vp, i64, i32, i32, vp, vp]
     L.detlsh_select_breakpoints_noalloc.restype = ctypes.c_int
     L.detlsh_plan_create.argtypes = [vp, i64, i32, ctypes.POINTER(QueryParams), i32, vp, ctypes.POINTER(vp)]
@@ -224,15 +232,20 @@ class Index:
 PROJ_FP32, PROJ_BF16 = 0, 1
 
 
-def detlsh_build(X: torch.Tensor, A: torch.Tensor, sample_ids: torch.Tensor, K: int, L: int,
+def detlsh_build(X: torch.Tensor, A: Optional[torch.Tensor], sample_ids: Optional[torch.Tensor], K: int, L: int,
                  n_regions: int, max_leaf: int, borrow: bool = False, proj_mode: int = 0,
-                 dedup_pos: bool = False) -> Index:
+                 dedup_pos: bool = False, seed: int = 0, sample_size: int = 0) -> Index:
+    """A or sample_ids None: the library draws them from ``seed``
+    (detlsh_draw_hashes / detlsh_draw_sample), the sample of ``sample_size``
+    points (0: ceil(0.1 n))."""
     X = X.contiguous()
-    A = A.contiguous().to(torch.float32)
-    sample_ids = sample_ids.contiguous().to(torch.int64)
+    A = A.contiguous().to(torch.float32) if A is not None else None
+    sample_ids = sample_ids.contiguous().to(torch.int64) if sample_ids is not None else None
     mem = _mem_of(X, A, sample_ids)
-    p = Params(K=K, L=L, n_regions=n_regions, max_leaf=max_leaf, n_s=sample_ids.numel(), proj_mode=proj_mode,
-               flags=(BORROW_X if (borrow and mem == MEM_DEVICE) else 0) | (DEDUP_POS if dedup_pos else 0))
+    n_s = sample_ids.numel() if sample_ids is not None else int(sample_size)
+    p = Params(K=K, L=L, n_regions=n_regions, max_leaf=max_leaf, sample_size=n_s, proj_mode=proj_mode,
+               flags=(BORROW_X if (borrow and mem == MEM_DEVICE) else 0) | (DEDUP_POS if dedup_pos else 0),
+               seed=int(seed) & 0xFFFFFFFFFFFFFFFF)
     out = ctypes.c_void_p(0)
     st = lib().detlsh_build(_ptr(X), X.shape[0], X.shape[1], _dtype_code(X), _ptr(A), _ptr(sample_ids),
                             ctypes.byref(p), mem, _stream(mem), ctypes.byref(out))
@@ -288,12 +301,13 @@ def detlsh_rc_ann(index: Index, Q: torch.Tensor, r, c, eps: float, beta: float):
 
 def detlsh_query(index: Index, Q: torch.Tensor, k, c, r_min=None, k_max: Optional[int] = None,
                  eps: float = 0.0, beta: float = 0.1, cand_cap: int = 0,
-                 out=None, shortlist: int = 0, tuning=None):
+                 out=None, shortlist: int = 0, tuning=None, qproj: Optional[torch.Tensor] = None):
     """Returns (ids int64 [nq,k_max], dist fp32 [nq,k_max], stats int32 [nq,4], cand or None).
 
     ``k``, ``c``, ``r_min`` are per-query tensors (or scalars, broadcast).
     ``out`` optionally supplies preallocated (ids, dist, stats) tensors;
-    ``tuning`` is a ``Tuning`` or a dict of its fields (launch shapes).
+    ``tuning`` is a ``Tuning`` or a dict of its fields (launch shapes);
+    ``qproj`` (fp32 [nq, L*K], on Q's device) receives the projected queries.
     """
     Q, k, c, r_min = _query_args(Q, k, c, r_min)
     nq, dev = Q.shape[0], Q.device
@@ -310,7 +324,10 @@ def detlsh_query(index: Index, Q: torch.Tensor, k, c, r_min=None, k_max: Optiona
     cand = torch.empty(nq, cand_cap, dtype=torch.int32, device=dev) if cand_cap > 0 else None
     qp = QueryParams(eps=eps, beta=beta, cand_ids=cand.data_ptr() if cand is not None else None,
                      cand_cap=cand_cap, shortlist=shortlist, reserved=0,
-                     tuning=ctypes.pointer(tu) if tu is not None else None)
+                     tuning=ctypes.pointer(tu) if tu is not None else None,
+                     qproj=qproj.data_ptr() if qproj is not None else None)
+    if qproj is not None and (qproj.device != dev or qproj.dtype != torch.float32 or not qproj.is_contiguous()):
+        raise ValueError("qproj must be a contiguous fp32 tensor on the queries' device")
     st = lib().detlsh_query(index.handle, _ptr(Q), nq, _dtype_code(Q), _ptr(k), _ptr(c), _ptr(r_min),
                             k_max, ctypes.byref(qp), _ptr(ids), _ptr(dist), _ptr(stats), mem, _stream(mem))
     _check(st, "detlsh_query")
@@ -527,6 +544,29 @@ def detlsh_select_breakpoints_noalloc(Ps: torch.Tensor, n_regions: int, E: torch
     Ps = Ps.contiguous()
     _check(lib().detlsh_select_breakpoints_noalloc(_ptr(Ps), Ps.shape[1], Ps.shape[0], n_regions, _ptr(E),
                                                    _stream(MEM_DEVICE)), "detlsh_select_breakpoints_noalloc")
+
+
+def detlsh_draw_hashes(seed: int, LK: int, d: int) -> torch.Tensor:
+    """The library's hash vectors of Eq. 1 for ``seed`` (host, no GPU): fp32 [LK, d]."""
+    A = torch.empty(LK, d, dtype=torch.float32)
+    _check(lib().detlsh_draw_hashes(int(seed) & 0xFFFFFFFFFFFFFFFF, LK, d, _ptr(A)), "detlsh_draw_hashes")
+    return A
+
+
+def detlsh_draw_sample(seed: int, n: int, n_s: int) -> torch.Tensor:
+    """The library's Alg. 1 sample for ``seed`` (host, no GPU): int64 [n_s], ascending."""
+    ids = torch.empty(n_s, dtype=torch.int64)
+    _check(lib().detlsh_draw_sample(int(seed) & 0xFFFFFFFFFFFFFFFF, n, n_s, _ptr(ids)), "detlsh_draw_sample")
+    return ids
+
+
+def detlsh_memory_stats(reset_peak: bool = False) -> dict:
+    """Stream-ordered device memory in use (library pool, device default pool) and high-water marks."""
+    out = (ctypes.c_int64 * 4)()
+    m = lib().detlsh_memory_stats(1 if reset_peak else 0, out, 4)
+    if m < 0:
+        _check(m, "detlsh_memory_stats")
+    return {"lib_used": out[0], "lib_peak": out[1], "default_used": out[2], "default_peak": out[3]}
 
 
 def detlsh_eps_lemma3(K: int, L: int) -> float:

@@ -48,7 +48,10 @@ def _compile(src, obj, verbose):
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
     else:
-        cmd = [nvcc, "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-c", src, "-o", obj]
+        # host-only code: no contraction of a*b+c into a fused multiply-add,
+        # so that host arithmetic rounds the same way on every CPU
+        cmd = [nvcc, "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off", "-I", INCLUDE, "-c", src,
+               "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

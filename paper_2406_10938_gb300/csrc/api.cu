@@ -79,6 +79,23 @@ cudaMemPool_t scratch_pool() {
   return pools[dev];
 }
 
+void clear_error() { g_err[0] = 0; }
+
+int require_device_ptr(const void* p, const char* name) {
+  cudaPointerAttributes at{};
+  const cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("%s: cudaPointerGetAttributes failed: %s", name, cudaGetErrorString(e));
+    return e == cudaErrorInvalidValue ? DETLSH_EINVAL : DETLSH_ECUDA;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) {
+    set_error("%s must be a device (or managed) address", name);
+    return DETLSH_EINVAL;
+  }
+  return DETLSH_OK;
+}
+
 void set_error(const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -178,7 +195,7 @@ void free_index(detlsh_index* idx) {
   // no kernel of any stream may still use the arrays
   cudaDeviceSynchronize();
   if (idx->owns_x && idx->X) cudaFreeAsync(const_cast<void*>(idx->X), 0);
-  void* arrays[] = {idx->A, idx->At, idx->E, idx->Ps, idx->codes, idx->leaf_ids, idx->leaf_pos, idx->leaf_base,
+  void* arrays[] = {idx->A, idx->At, idx->E, idx->Ps, idx->sample, idx->codes, idx->leaf_ids, idx->leaf_pos, idx->leaf_base,
                     idx->leaf_range, idx->leaf_plen, idx->leaf_prefix, idx->leaf_lo, idx->leaf_hi,
                     idx->leaf_tree, idx->Xb, idx->Ab, idx->d_err, idx->Rtab, idx->Rlo, idx->Rinv, idx->Atf, idx->Ab3};
   for (void* p : arrays)
@@ -187,9 +204,9 @@ void free_index(detlsh_index* idx) {
   delete idx;
 }
 
-int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* A,
-               const int64_t* sample_ids, const detlsh_params* prm, int32_t mem,
-               cudaStream_t s, detlsh_index* idx) {
+int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* A, int32_t mem_a,
+               const int64_t* sample_ids, int32_t mem_ids, int64_t n_s, const detlsh_params* prm,
+               int32_t mem, cudaStream_t s, detlsh_index* idx) {
   const int K = prm->K, L = prm->L, Nr = prm->n_regions;
   const int LK = K * L;
   idx->n = n;
@@ -200,7 +217,7 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
   idx->Nr = Nr;
   idx->bits = log2i(Nr);
   idx->max_leaf = prm->max_leaf;
-  idx->n_s = prm->n_s;
+  idx->n_s = n_s;
   idx->proj_mode = prm->proj_mode;
   idx->flags = prm->flags;
   DL_CUDA(cudaGetDevice(&idx->device));
@@ -219,24 +236,26 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
   }
   DL_TRY(index_alloc(&idx->A, sizeof(float) * LK * d, s));
   DL_CUDA(cudaMemcpyAsync(idx->A, A, sizeof(float) * LK * d,
-                          mem == DETLSH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+                          mem_a == DETLSH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   DL_TRY(index_alloc(&idx->At, sizeof(float) * LK * d, s));
   DL_TRY(transpose_hashes(idx->A, LK, d, idx->At, s));
 
-  In ids;
-  DL_TRY(ids.stage(sample_ids, sizeof(int64_t) * prm->n_s, mem, s));
+  DL_TRY(index_alloc(&idx->sample, sizeof(int64_t) * n_s, s));
+  DL_CUDA(cudaMemcpyAsync(idx->sample, sample_ids, sizeof(int64_t) * n_s,
+                          mem_ids == DETLSH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  const int64_t* sid = idx->sample;
   {
     Scratch bad;
     DL_TRY(bad.alloc(sizeof(int), s));
     DL_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
-    k_check_ids<<<ceil_div(prm->n_s, 256), 256, 0, s>>>(static_cast<const int64_t*>(ids.d), prm->n_s, n,
+    k_check_ids<<<ceil_div(n_s, 256), 256, 0, s>>>(sid, n_s, n,
                                                        bad.as<int>());
     DL_LAUNCH();
     DL_TRY(check_flag(bad.as<int>(), s, "sample_ids must lie in [0, n)"));
   }
   PhaseTimer tm(s);
   // Alg. 1: projections of the sample, [LK][n_s]
-  DL_TRY(index_alloc(&idx->Ps, sizeof(float) * LK * prm->n_s, s));
+  DL_TRY(index_alloc(&idx->Ps, sizeof(float) * LK * n_s, s));
   DL_TRY(index_alloc(&idx->E, sizeof(float) * LK * (Nr + 1), s));
   DL_TRY(index_alloc(&idx->codes, (size_t)n * LK, s));
   DL_TRY(index_alloc(&idx->leaf_ids, sizeof(uint32_t) * n * L, s));
@@ -255,13 +274,13 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
     DL_TRY(to_bf16(idx->X, dtype, n * d, idx->Xb, s));
     DL_TRY(to_bf16(idx->A, DETLSH_F32, (int64_t)LK * d, idx->Ab, s));
     Scratch xs;
-    DL_TRY(xs.alloc((size_t)prm->n_s * d * 2, s));
-    DL_TRY(gather_rows_bf16(idx->Xb, d, static_cast<const int64_t*>(ids.d), prm->n_s, xs.p, s));
-    DL_TRY(launch_project_tc(xs.p, prm->n_s, d, idx->Ab, LK, K, nullptr, nullptr, nullptr, nullptr, Nr, nullptr,
-                             idx->Ps, 1, prm->n_s, idx->d_err, s));
+    DL_TRY(xs.alloc((size_t)n_s * d * 2, s));
+    DL_TRY(gather_rows_bf16(idx->Xb, d, sid, n_s, xs.p, s));
+    DL_TRY(launch_project_tc(xs.p, n_s, d, idx->Ab, LK, K, nullptr, nullptr, nullptr, nullptr, Nr, nullptr,
+                             idx->Ps, 1, n_s, idx->d_err, s));
     tm.end();
     tm.begin(TR_BREAKPOINTS);
-    DL_TRY(select_breakpoints(idx->Ps, prm->n_s, LK, Nr, idx->E, s));
+    DL_TRY(select_breakpoints(idx->Ps, n_s, LK, Nr, idx->E, s));
     DL_TRY(build_region_tables(idx->E, LK, Nr, idx->Rtab, idx->Rlo, idx->Rinv, s));
     tm.end();
     tm.begin(TR_ENCODE);
@@ -295,25 +314,25 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
     tm.begin(TR_SAMPLE_PROJ);
     if (b3) {
       Scratch xs;
-      DL_TRY(xs.alloc((size_t)prm->n_s * d, s));
-      DL_TRY(gather_rows_u8(static_cast<const uint8_t*>(idx->X), d, static_cast<const int64_t*>(ids.d), prm->n_s,
+      DL_TRY(xs.alloc((size_t)n_s * d, s));
+      DL_TRY(gather_rows_u8(static_cast<const uint8_t*>(idx->X), d, sid, n_s,
                             xs.as<uint8_t>(), s));
-      DL_TRY(launch_project_bf16x3(xs.as<uint8_t>(), prm->n_s, d, idx->Ab3, LK, K, nullptr, nullptr, nullptr, nullptr, Nr,
-                                   nullptr, idx->Ps, 1, prm->n_s, idx->d_err, s));
+      DL_TRY(launch_project_bf16x3(xs.as<uint8_t>(), n_s, d, idx->Ab3, LK, K, nullptr, nullptr, nullptr, nullptr, Nr,
+                                   nullptr, idx->Ps, 1, n_s, idx->d_err, s));
     } else if (tf32) {
       Scratch xs;
-      DL_TRY(xs.alloc(sizeof(float) * prm->n_s * d, s));
-      DL_TRY(gather_rows_f32(static_cast<const float*>(idx->X), d, static_cast<const int64_t*>(ids.d), prm->n_s,
+      DL_TRY(xs.alloc(sizeof(float) * n_s * d, s));
+      DL_TRY(gather_rows_f32(static_cast<const float*>(idx->X), d, sid, n_s,
                              xs.as<float>(), s));
-      DL_TRY(launch_project_tf32(xs.as<float>(), prm->n_s, d, idx->Atf, LK, K, nullptr, nullptr, nullptr, nullptr,
-                                 Nr, nullptr, idx->Ps, 1, prm->n_s, idx->d_err, s));
+      DL_TRY(launch_project_tf32(xs.as<float>(), n_s, d, idx->Atf, LK, K, nullptr, nullptr, nullptr, nullptr,
+                                 Nr, nullptr, idx->Ps, 1, n_s, idx->d_err, s));
     } else {
-      DL_TRY(launch_project_t(idx->X, dtype, prm->n_s, d, static_cast<const int64_t*>(ids.d), idx->At, LK,
-                              idx->Ps, 1, prm->n_s, s));
+      DL_TRY(launch_project_t(idx->X, dtype, n_s, d, sid, idx->At, LK,
+                              idx->Ps, 1, n_s, s));
     }
     tm.end();
     tm.begin(TR_BREAKPOINTS);
-    DL_TRY(select_breakpoints(idx->Ps, prm->n_s, LK, Nr, idx->E, s));
+    DL_TRY(select_breakpoints(idx->Ps, n_s, LK, Nr, idx->E, s));
     DL_TRY(build_region_tables(idx->E, LK, Nr, idx->Rtab, idx->Rlo, idx->Rinv, s));
     tm.end();
     // Alg. 2: codes of every point, fused with the projection
@@ -372,7 +391,7 @@ struct TuneCtx {
 
 int run_tuned(const TuneCtx& x, int shortlist, const QueryTuning& tu) {
   return run_query(x.idx, x.Q, x.nq, x.k, x.c, x.r, x.k_max, x.eps, x.beta, x.ids, x.dist, nullptr,
-                   nullptr, 0, shortlist, tu, x.s);
+                   nullptr, 0, nullptr, shortlist, tu, x.s);
 }
 
 // device milliseconds of the query (the faster of two runs after one warm-up)
@@ -430,6 +449,31 @@ int detlsh_trace_get(double* out, int32_t len) {
   return m;
 }
 
+int detlsh_memory_stats(int32_t reset_peak, int64_t* out, int32_t len) {
+  clear_error();
+  DL_REQUIRE(out != nullptr && len >= 0, "out must be non-NULL and len >= 0");
+  int dev = 0;
+  DL_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pools[2] = {scratch_pool(), nullptr};
+  DL_CUDA(cudaDeviceGetDefaultMemPool(&pools[1], dev));
+  int64_t v[4] = {0, 0, 0, 0};
+  for (int i = 0; i < 2; ++i) {
+    if (!pools[i]) continue;
+    uint64_t cur = 0, peak = 0;
+    DL_CUDA(cudaMemPoolGetAttribute(pools[i], cudaMemPoolAttrUsedMemCurrent, &cur));
+    DL_CUDA(cudaMemPoolGetAttribute(pools[i], cudaMemPoolAttrUsedMemHigh, &peak));
+    v[2 * i] = (int64_t)cur;
+    v[2 * i + 1] = (int64_t)peak;
+    if (reset_peak) {
+      uint64_t zero = 0;   // resets the high-water mark to the current use
+      DL_CUDA(cudaMemPoolSetAttribute(pools[i], cudaMemPoolAttrUsedMemHigh, &zero));
+    }
+  }
+  const int m = std::min<int>(len, 4);
+  for (int i = 0; i < m; ++i) out[i] = v[i];
+  return m;
+}
+
 int64_t detlsh_launch_count(void) {
   return (int64_t)__atomic_load_n(&g_launches, __ATOMIC_RELAXED);
 }
@@ -445,7 +489,7 @@ int detlsh_build(const void* X, int64_t n, int32_t d, int32_t dtype, const float
   g_err[0] = 0;
   DL_REQUIRE(out != nullptr && params != nullptr, "out and params must be non-NULL");
   *out = nullptr;
-  DL_REQUIRE(X && A && sample_ids, "X, A and sample_ids must be non-NULL");
+  DL_REQUIRE(X != nullptr, "X must be non-NULL");
   DL_REQUIRE(mem == DETLSH_MEM_HOST || mem == DETLSH_MEM_DEVICE, "bad mem flag");
   DL_REQUIRE(dtype == DETLSH_F32 || dtype == DETLSH_U8, "bad dtype");
   const detlsh_params& p = *params;
@@ -456,12 +500,16 @@ int detlsh_build(const void* X, int64_t n, int32_t d, int32_t dtype, const float
   DL_REQUIRE(p.max_leaf >= 1, "max_leaf must be >= 1");
   DL_REQUIRE(d >= 1 && d <= 65536, "d must be in [1, 65536]");
   DL_REQUIRE(n >= 1 && n * (int64_t)p.L < ((int64_t)1 << 32), "need 1 <= n and n*L < 2^32");
-  DL_REQUIRE(p.n_s >= p.n_regions && p.n_s <= n, "need n_regions <= n_s <= n");
+  DL_REQUIRE(p.sample_size >= 0, "sample_size must be >= 0");
+  DL_REQUIRE(sample_ids == nullptr || p.sample_size > 0, "sample_size must give the length of sample_ids");
+  // Sec. 6.1: n_s = 0.1 n unless given
+  const int64_t n_s = p.sample_size > 0 ? p.sample_size : (n + 9) / 10;
+  DL_REQUIRE(n_s >= p.n_regions && n_s <= n, "need n_regions <= n_s <= n (n_s = %lld)", (long long)n_s);
   DL_REQUIRE(p.proj_mode == DETLSH_PROJ_FP32 || p.proj_mode == DETLSH_PROJ_BF16, "unsupported proj_mode");
   DL_REQUIRE((p.flags & ~(DETLSH_BORROW_X | DETLSH_DEDUP_POS)) == 0, "unknown flags");
   DL_REQUIRE(p.proj_mode != DETLSH_PROJ_BF16 || (d % 8 == 0 && p.K * p.L <= 64),
              "the BF16 projection needs d %% 8 == 0 and L*K <= 64");
-  DL_REQUIRE(p.n_s * (int64_t)p.K * p.L < ((int64_t)1 << 32), "n_s*L*K must be < 2^32");
+  DL_REQUIRE(n_s * (int64_t)p.K * p.L < ((int64_t)1 << 32), "n_s*L*K must be < 2^32");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   trace_reset(TR_SAMPLE_PROJ, TR_LEAVES);
   trace_reset(TR_BUILD_TOTAL, TR_BUILD_TOTAL);
@@ -473,7 +521,23 @@ int detlsh_build(const void* X, int64_t n, int32_t d, int32_t dtype, const float
     set_error("host allocation failed");
     return DETLSH_ENOMEM;
   }
-  const int st = build_impl(X, n, d, dtype, A, sample_ids, params, mem, s, idx);
+  // the random draws of the method, when the caller leaves them to the library
+  std::vector<float> A_h;
+  std::vector<int64_t> ids_h;
+  int32_t mem_a = mem, mem_ids = mem;
+  if (A == nullptr) {
+    A_h.resize((size_t)p.K * p.L * d);
+    draw_hashes(p.seed, (int64_t)A_h.size(), A_h.data());
+    A = A_h.data();
+    mem_a = DETLSH_MEM_HOST;
+  }
+  if (sample_ids == nullptr) {
+    ids_h.resize((size_t)n_s);
+    draw_sample(p.seed, n, n_s, ids_h.data());
+    sample_ids = ids_h.data();
+    mem_ids = DETLSH_MEM_HOST;
+  }
+  const int st = build_impl(X, n, d, dtype, A, mem_a, sample_ids, mem_ids, n_s, params, mem, s, idx);
   if (st != DETLSH_OK) {
     cudaStreamSynchronize(s);
     free_index(idx);
@@ -538,21 +602,24 @@ int detlsh_query(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dty
   trace_reset(TR_QUERY_TOTAL, TR_BUCKET);
   PhaseTimer total(s);
   total.begin(TR_QUERY_TOTAL);
-  Out oi, od, os, oc;
+  Out oi, od, os, oc, oq;
   DL_TRY(oi.stage(out_ids, sizeof(int64_t) * nq * k_max, mem, s));
   DL_TRY(od.stage(out_dist, sizeof(float) * nq * k_max, mem, s));
   DL_TRY(os.stage(out_stats, sizeof(int32_t) * nq * 4, mem, s));
   DL_TRY(oc.stage(cand, cand ? sizeof(uint32_t) * nq * cand_cap : 0, mem, s));
+  float* qproj = qp ? qp->qproj : nullptr;
+  DL_TRY(oq.stage(qproj, qproj ? sizeof(float) * nq * idx->K * idx->L : 0, mem, s));
   QueryTuning tu;
   DL_TRY(tuning_from_params(qp, &tu));
   DL_TRY(run_query(idx, dQ.d, nq, static_cast<const int32_t*>(dk.d), static_cast<const float*>(dc.d),
                    static_cast<const float*>(dr.d), k_max, eps, beta, static_cast<int64_t*>(oi.d),
                    static_cast<float*>(od.d), static_cast<int32_t*>(os.d), static_cast<uint32_t*>(oc.d),
-                   cand_cap, shortlist, tu, s));
+                   cand_cap, static_cast<float*>(oq.d), shortlist, tu, s));
   DL_TRY(oi.finish(s));
   DL_TRY(od.finish(s));
   DL_TRY(os.finish(s));
   DL_TRY(oc.finish(s));
+  DL_TRY(oq.finish(s));
   total.end();
   DL_TRY(total.finish());
   if (mem == DETLSH_MEM_HOST) DL_CUDA(cudaStreamSynchronize(s));
@@ -570,7 +637,7 @@ int detlsh_autotune(const detlsh_index* idx, const void* Q, int64_t nq, int32_t 
   DL_REQUIRE(k_max >= 1 && k_max <= kMaxTopK, "k_max must be in [1, %d]", kMaxTopK);
   DL_REQUIRE(Q && k && c && r_min, "NULL query argument");
   DL_REQUIRE(std::isfinite(min_agreement) && min_agreement <= 1.0, "min_agreement must be <= 1");
-  DL_REQUIRE(!qp || !qp->cand_ids, "autotuning does not export candidate lists");
+  DL_REQUIRE(!qp || (!qp->cand_ids && !qp->qproj), "autotuning does not export candidate lists or projections");
   double eps = qp ? qp->eps : 0.0;
   const double beta = qp ? qp->beta : 0.1;
   DL_REQUIRE(beta >= 0.0 && std::isfinite(beta), "beta must be finite and >= 0");
@@ -790,6 +857,7 @@ int64_t detlsh_export_size(const detlsh_index* idx, int32_t what) {
     case DETLSH_EXPORT_LEAF_PLEN:
     case DETLSH_EXPORT_LEAF_PREFIX: return idx->total_leaves * idx->K;
     case DETLSH_EXPORT_SAMPLE_PROJ: return sizeof(float) * LK * idx->n_s;
+    case DETLSH_EXPORT_SAMPLE_IDS: return sizeof(int64_t) * idx->n_s;
     default: set_error("unknown export item %d", what); return DETLSH_EINVAL;
   }
 }
@@ -814,6 +882,7 @@ int detlsh_export(const detlsh_index* idx, int32_t what, void* dst, int64_t byte
     case DETLSH_EXPORT_LEAF_PLEN: src = idx->leaf_plen; break;
     case DETLSH_EXPORT_LEAF_PREFIX: src = idx->leaf_prefix; break;
     case DETLSH_EXPORT_SAMPLE_PROJ: src = idx->Ps; break;
+    case DETLSH_EXPORT_SAMPLE_IDS: src = idx->sample; break;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DL_CUDA(cudaMemcpyAsync(dst, src, need,

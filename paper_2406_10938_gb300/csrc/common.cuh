@@ -18,7 +18,10 @@ constexpr int kRoundCap = 256;   // rounds of Alg. 7; the last one has infinite 
 constexpr int kMaxTopK = 1024;
 
 void set_error(const char* fmt, ...);
+void clear_error();
 void count_launch();
+// DETLSH_EINVAL (with the message) unless p is a device or managed address
+int require_device_ptr(const void* p, const char* name);
 
 // Per-phase device times of the last build/query on this thread (tracing).
 enum TracePhase {
@@ -162,6 +165,7 @@ struct detlsh_index {
   float* Rlo = nullptr;             // [LK]
   float* Rinv = nullptr;            // [LK]
   float* Ps = nullptr;              // [LK][n_s]
+  int64_t* sample = nullptr;        // [n_s] sampled point ids (Alg. 1)
   uint8_t* codes = nullptr;         // [L][n][K]
   uint32_t* leaf_ids = nullptr;     // [L][n]
   uint32_t* leaf_pos = nullptr;     // [L][n] each entry's point as its position in tree 0's leaf order
@@ -179,6 +183,10 @@ struct detlsh_index {
 };
 
 namespace detlsh {
+
+// ---- the method's random draws from a seed (rng.cpp, host code)
+void draw_hashes(uint64_t seed, int64_t count, float* A);
+void draw_sample(uint64_t seed, int64_t n, int64_t n_s, int64_t* ids);
 
 // ---- region search tables (Alg. 2 encoding, project.cu)
 // For projected dimension h with interior breakpoints e_1 <= ... <= e_{Nr-1}:
@@ -371,7 +379,8 @@ int check_batch_args(const QueryShape& sh, void* base, const int32_t* k, const f
 int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, const void* Q, int64_t q0,
                   int64_t nqg, const int32_t* k, const float* c, const float* r_min, double eps,
                   double beta, int64_t* out_ids, float* out_dist, int32_t* out_stats,
-                  uint32_t* cand_ids, int64_t cand_cap, bool vec4, PhaseTimer* timer, cudaStream_t s);
+                  uint32_t* cand_ids, int64_t cand_cap, float* qproj, bool vec4, PhaseTimer* timer,
+                  cudaStream_t s);
 bool query_vec4(const detlsh_index* idx, const void* Q);
 
 // ---- plans (plan.cu), for the server
@@ -385,7 +394,7 @@ int plan_enqueue(detlsh_plan* p, const void* Q, int64_t nq, const int32_t* k, co
 int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t* k,
               const float* c, const float* r_min, int k_max, double eps, double beta,
               int64_t* out_ids, float* out_dist, int32_t* out_stats, uint32_t* cand_ids,
-              int64_t cand_cap, int shortlist, const QueryTuning& tu, cudaStream_t s);
+              int64_t cand_cap, float* qproj, int shortlist, const QueryTuning& tu, cudaStream_t s);
 
 // ---- host math (chi2.cpp)
 double chi2_upper_quantile(double alpha, int K);

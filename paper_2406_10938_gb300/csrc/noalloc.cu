@@ -10,15 +10,16 @@
 //
 // The array below is a file-scope __device__ variable: every GPU that loads
 // the library holds it (kNoallocScratchBytes) until the process exits. Host
-// code cannot use its name as a device address, so the first call on each
-// device looks the address up with cudaGetSymbolAddress (with that device
-// current) and caches it; that first call should therefore come before any
-// stream capture. All calls share the array and it keeps the last call's
-// contents; nothing in it needs to start at zero (every kernel writes the
-// entries it later reads). Calls whose GPU work overlaps (for example on two
-// streams) race on it and must be serialized by the caller.
-#include <mutex>
-
+// code cannot use its name as a device address, so every call looks the
+// address up with cudaGetSymbolAddress on the current device (cheap, and it
+// allocates nothing). The first lookup on a device may load the library's
+// device code there, so the first call on each device should come before any
+// stream capture. Looking the address up per call also keeps it valid after a
+// cudaDeviceReset, which destroys the context the array lived in. All calls
+// share the array and it keeps the last call's contents; nothing in it needs
+// to start at zero (every kernel writes the entries it later reads). Calls
+// whose GPU work overlaps (for example on two streams) race on it and must be
+// serialized by the caller.
 #include "common.cuh"
 
 namespace detlsh {
@@ -33,24 +34,11 @@ constexpr size_t kNoallocScratchBytes = 7u << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {nullptr};
-
+// device address of the array on the current device
 int scratch_address(void** out) {
-  int dev = 0;
-  DL_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("device ordinal %d out of range", dev);
-    return DETLSH_EINVAL;
-  }
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    DL_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  void* p = nullptr;
+  DL_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  *out = p;
   return DETLSH_OK;
 }
 
@@ -63,6 +51,7 @@ using namespace detlsh;
 
 extern "C" int detlsh_select_breakpoints_noalloc(const float* Ps, int64_t n_s, int32_t LK,
                                                  int32_t n_regions, float* E, void* stream) {
+  clear_error();
   DL_REQUIRE(Ps && E, "NULL argument");
   DL_REQUIRE(LK >= 1 && LK <= kMaxLK, "LK must be in [1, %d]", kMaxLK);
   DL_REQUIRE(is_pow2(n_regions) && n_regions >= 2 && n_regions <= 256, "bad n_regions");
@@ -70,6 +59,8 @@ extern "C" int detlsh_select_breakpoints_noalloc(const float* Ps, int64_t n_s, i
   DL_REQUIRE(n_s * (int64_t)LK <= DETLSH_NOALLOC_MAX_ITEMS,
              "n_s*LK = %lld exceeds the fixed scratch limit of %d values",
              (long long)(n_s * (int64_t)LK), DETLSH_NOALLOC_MAX_ITEMS);
+  DL_TRY(require_device_ptr(Ps, "Ps"));
+  DL_TRY(require_device_ptr(E, "E"));
   const size_t need = select_breakpoints_ws_bytes(n_s, LK);
   if (need > kNoallocScratchBytes) {
     set_error("scratch need %zu exceeds %zu bytes", need, kNoallocScratchBytes);

@@ -57,7 +57,7 @@ int enqueue_plan_batch(detlsh_plan* p, int64_t nqg, bool timed, cudaStream_t s) 
   k_stick<<<1, 1, 0, s>>>(query_ctr(p->sh, p->scratch) + CT_BAD, p->sticky);
   DL_LAUNCH();
   DL_TRY(enqueue_batch(p->idx, p->sh, p->scratch, p->q_in, 0, nqg, p->k_in, p->c_in, p->r_in, p->eps, p->beta,
-                       p->ids, p->dist, p->stats, nullptr, 0, p->vec4, timed ? &tm : nullptr, s));
+                       p->ids, p->dist, p->stats, nullptr, 0, nullptr, p->vec4, timed ? &tm : nullptr, s));
   return tm.finish();
 }
 
@@ -102,7 +102,7 @@ int detlsh_plan_create(const detlsh_index* idx, int64_t nq_max, int32_t k_max,
   DL_REQUIRE(nq_max >= 1, "nq_max must be >= 1");
   DL_REQUIRE(k_max >= 1 && k_max <= kMaxTopK, "k_max must be in [1, %d]", kMaxTopK);
   DL_REQUIRE((flags & ~DETLSH_PLAN_GRAPH) == 0, "unknown plan flags");
-  DL_REQUIRE(!qp || !qp->cand_ids, "a plan does not export candidate lists");
+  DL_REQUIRE(!qp || (!qp->cand_ids && !qp->qproj), "a plan does not export candidate lists or projections");
   double eps = qp ? qp->eps : 0.0;
   const double beta = qp ? qp->beta : 0.1;
   DL_REQUIRE(beta >= 0.0 && std::isfinite(beta), "beta must be finite and >= 0");

@@ -1852,7 +1852,8 @@ int check_batch_args(const QueryShape& sh, void* base, const int32_t* k, const f
 int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, const void* Q, int64_t q0,
                   int64_t nqg, const int32_t* k, const float* c, const float* r_min, double eps,
                   double beta, int64_t* out_ids, float* out_dist, int32_t* out_stats,
-                  uint32_t* cand_ids, int64_t cand_cap, bool vec4, PhaseTimer* timer, cudaStream_t s) {
+                  uint32_t* cand_ids, int64_t cand_cap, float* qproj, bool vec4, PhaseTimer* timer,
+                  cudaStream_t s) {
   char* b = static_cast<char*>(base);
   uint32_t* ctr = reinterpret_cast<uint32_t*>(b + sh.o_ctr);
   const uint32_t* nqd = ctr + CT_NQ;
@@ -1893,6 +1894,9 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   } else {
     DL_TRY(launch_project_t(Qb, idx->dtype, nqg, idx->d, nullptr, idx->At, LK, qp, LK, 1, s));
   }
+  // optional copy of the projected queries (what every later kernel reads)
+  if (qproj)
+    DL_CUDA(cudaMemcpyAsync(qproj + q0 * LK, qp, sizeof(float) * nqg * LK, cudaMemcpyDeviceToDevice, s));
   // the walk's query order: by locality key
   k_query_keys<<<ceil_div(nqg, 256), 256, 0, s>>>(qp, LK, nqd, idx->E, idx->Nr, idx->K, nqg, qk, qk + sh.B);
   DL_LAUNCH();
@@ -2135,7 +2139,7 @@ int permute_rows(const void* src, void* dst, const uint32_t* perm, int64_t rows,
 int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t* k, const float* c,
               const float* r_min, int k_max, double eps, double beta, int64_t* out_ids,
               float* out_dist, int32_t* out_stats, uint32_t* cand_ids, int64_t cand_cap,
-              int shortlist, const QueryTuning& tu, cudaStream_t s) {
+              float* qproj, int shortlist, const QueryTuning& tu, cudaStream_t s) {
   if (nq == 0) return DETLSH_OK;
   // with streams = 2 and several batches, batches alternate between two
   // streams (one batch's distance gather may overlap the next one's walk),
@@ -2167,6 +2171,7 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
   float* od = out_dist;
   int32_t* os = out_stats;
   uint32_t* oc = cand_ids;
+  float* oq = qproj;
   Scratch ord, inq, outq;
   const uint32_t* perm = nullptr;
   if (nq > sh.B) {
@@ -2201,13 +2206,15 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
     const size_t ids_b = (sizeof(int64_t) * nq * k_max + 255) & ~size_t(255);
     const size_t dist_b = (sizeof(float) * nq * k_max + 255) & ~size_t(255);
     const size_t st_b = (sizeof(int32_t) * nq * 4 + 255) & ~size_t(255);
-    const size_t cand_b = cand_ids ? sizeof(uint32_t) * nq * cand_cap : 0;
-    DL_TRY(outq.alloc(ids_b + dist_b + st_b + cand_b, s));
+    const size_t cand_b = cand_ids ? (sizeof(uint32_t) * nq * cand_cap + 255) & ~size_t(255) : 0;
+    const size_t qp_b = qproj ? sizeof(float) * nq * LK : 0;
+    DL_TRY(outq.alloc(ids_b + dist_b + st_b + cand_b + qp_b, s));
     char* obuf = static_cast<char*>(outq.p);
     oi = reinterpret_cast<int64_t*>(obuf);
     od = reinterpret_cast<float*>(obuf + ids_b);
     os = out_stats ? reinterpret_cast<int32_t*>(obuf + ids_b + dist_b) : nullptr;
     oc = cand_ids ? reinterpret_cast<uint32_t*>(obuf + ids_b + dist_b + st_b) : nullptr;
+    oq = qproj ? reinterpret_cast<float*>(obuf + ids_b + dist_b + st_b + cand_b) : nullptr;
   }
   const bool vec4 = query_vec4(idx, Qr);
   PhaseTimer tm0(s), tm1(s2 ? s2 : s);
@@ -2220,7 +2227,7 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
     cudaStream_t sb = odd ? s2 : s;
     void* wb = odd ? ws2.p : ws.p;
     DL_TRY(set_batch_size(sh, wb, nqb, sb));
-    DL_TRY(enqueue_batch(idx, sh, wb, Qr, q0, nqb, kr, cr, rr, eps, beta, oi, od, os, oc, cand_cap, vec4,
+    DL_TRY(enqueue_batch(idx, sh, wb, Qr, q0, nqb, kr, cr, rr, eps, beta, oi, od, os, oc, cand_cap, oq, vec4,
                          odd ? &tm1 : &tm0, sb));
   }
   if (nstreams == 2) DL_TRY(fork.join());
@@ -2231,6 +2238,7 @@ int run_query(const detlsh_index* idx, const void* Q, int64_t nq, const int32_t*
     DL_TRY(permute_rows<false>(od, out_dist, perm, nq, sizeof(float) * k_max, s));
     if (out_stats) DL_TRY(permute_rows<false>(os, out_stats, perm, nq, sizeof(int32_t) * 4, s));
     if (cand_ids) DL_TRY(permute_rows<false>(oc, cand_ids, perm, nq, sizeof(uint32_t) * cand_cap, s));
+    if (qproj) DL_TRY(permute_rows<false>(oq, qproj, perm, nq, sizeof(float) * sh.LK, s));
   }
   if (idx->proj_mode == DETLSH_PROJ_BF16) DL_TRY(check_tc_error(idx->d_err, s));
   return DETLSH_OK;

@@ -179,6 +179,7 @@ using namespace detlsh;
 extern "C" int detlsh_rc_ann(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dtype, const float* r,
                              const float* c, double eps, double beta, int64_t* out_id, double* out_dist,
                              int32_t* out_stats, void* stream) {
+  clear_error();
   DL_REQUIRE(idx, "NULL index");
   DL_REQUIRE(nq >= 0, "nq must be >= 0");
   if (nq == 0) return DETLSH_OK;
@@ -186,6 +187,12 @@ extern "C" int detlsh_rc_ann(const detlsh_index* idx, const void* Q, int64_t nq,
   DL_REQUIRE(dtype == idx->dtype, "the queries must have the index's dtype");
   DL_REQUIRE(eps > 0.0 && std::isfinite(eps), "eps must be positive and finite");
   DL_REQUIRE(beta >= 0.0 && std::isfinite(beta), "beta must be >= 0 and finite");
+  DL_TRY(require_device_ptr(Q, "Q"));
+  DL_TRY(require_device_ptr(r, "r"));
+  DL_TRY(require_device_ptr(c, "c"));
+  DL_TRY(require_device_ptr(out_id, "out_id"));
+  DL_TRY(require_device_ptr(out_dist, "out_dist"));
+  DL_TRY(require_device_ptr(out_stats, "out_stats"));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   RcArgs a{};
   a.X = idx->X;

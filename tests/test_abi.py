@@ -57,9 +57,9 @@ def test_build_rejects_bad_arguments_before_any_device_work(L):
     a = (ctypes.c_float * 64)()
     ids = (ctypes.c_int64 * 4)(0, 1, 2, 3)
     bad = [dict(K=0), dict(K=17), dict(L=0), dict(n_regions=3), dict(n_regions=512),
-           dict(max_leaf=0), dict(n_s=2), dict(proj_mode=7), dict(flags=4), dict(flags=-1)]
+           dict(max_leaf=0), dict(sample_size=2), dict(sample_size=-1), dict(proj_mode=7), dict(flags=4), dict(flags=-1)]
     for change in bad:
-        p = dict(K=4, L=1, n_regions=4, max_leaf=4, n_s=4, proj_mode=0, flags=0)
+        p = dict(K=4, L=1, n_regions=4, max_leaf=4, sample_size=4, proj_mode=0, flags=0)
         p.update(change)
         st = L.detlsh_build(x, 16, 4, 0, a, ids, ctypes.byref(binding.Params(**p)), 0, None,
                             ctypes.byref(out))

@@ -167,6 +167,33 @@ def test_build_degenerate_breakpoints_bit_parity(kind):
         idx.free()
 
 
+# ------------------------------------------------------------------ build from a seed (reading R15)
+@pytest.mark.parametrize("name,n,d,sample_size,dtype_mode", [("tiny", 10_000, 32, 0, 0), ("mid", 20_000, 128, 2_000, 0),
+                                                             ("serving", 30_000, 128, 0, 0), ("mid", 20_000, 128, 0, 1)])
+def test_build_from_seed_alone(name, n, d, sample_size, dtype_mode):
+    """detlsh_build with only the dataset, K, L, N_r and a seed: the library
+    draws A and the sample itself, bit-equal to the oracle's generator, with
+    n_s = ceil(0.1 n) by default (Sec. 6.1); the index equals one built from
+    the same draws passed in explicitly."""
+    K, L, Nr, max_leaf, seed = 16, 4, 256, 64, 2024
+    X, _ = make_workload(name, n=n, nq=1)
+    Xd = X.to(DEV)
+    idx = pkg.detlsh_build(Xd, None, None, K, L, Nr, max_leaf, seed=seed, sample_size=sample_size,
+                           proj_mode=dtype_mode)
+    n_s = sample_size or O.default_sample_size(n)
+    A_ref = O.draw_hashes(seed, L, K, d)
+    ids_ref = O.draw_sample(seed, n, n_s)
+    assert idx.info()["n_s"] == n_s
+    assert np.array_equal(pkg.detlsh_export(idx, "A").numpy().reshape(L * K, d), A_ref)
+    assert np.array_equal(pkg.detlsh_export(idx, "SAMPLE_IDS").numpy(), ids_ref)
+    idx2 = pkg.detlsh_build(Xd, torch.from_numpy(A_ref).to(DEV), torch.from_numpy(ids_ref).to(DEV), K, L, Nr,
+                            max_leaf, proj_mode=dtype_mode)
+    for what in ("EDGES", "CODES", "LEAF_IDS", "LEAF_RANGE", "LEAF_PLEN", "LEAF_PREFIX"):
+        assert torch.equal(pkg.detlsh_export(idx, what), pkg.detlsh_export(idx2, what)), what
+    idx.free()
+    idx2.free()
+
+
 # ------------------------------------------------------------------ build, float inputs
 @pytest.mark.parametrize("name,n,d,Nr,n_s", [("tiny", 10_000, 32, 16, 1_000),
                                              ("precision", 4_000, 960, 256, 400),
