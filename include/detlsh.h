@@ -504,6 +504,19 @@ int64_t detlsh_launch_count(void);
  */
 int detlsh_memory_stats(int32_t reset_peak, int64_t* out, int32_t len);
 
+/*
+ * detlsh_test_set_wait_limit_ns -- for tests of the failure path (no
+ * counterpart in the paper): sets the limit of each bounded wait in the
+ * tensor-core projection kernel for launches made after the call (default
+ * 2,000,000,000 ns; 0 makes the first wait that does not succeed at once run
+ * out) and returns the previous limit. A wait that runs out makes the kernel
+ * wind down (its issued copies and MMAs completed, its tensor memory freed)
+ * and the call return DETLSH_ETIMEOUT; later calls are unaffected once the
+ * limit is restored. Process-wide; not for use while other threads run
+ * builds or queries.
+ */
+uint64_t detlsh_test_set_wait_limit_ns(uint64_t ns);
+
 /* detlsh_strerror -- static text for a detlsh_status value. */
 const char* detlsh_strerror(int status);
 

@@ -156,6 +156,22 @@ def project(A: np.ndarray, X: np.ndarray) -> np.ndarray:
     return np.asarray(X, dtype=np.float64) @ np.asarray(A, dtype=np.float64).T
 
 
+def paa_reduce(X: np.ndarray, K: int) -> np.ndarray:
+    """DET-ONLY's reduction (Sec. 6.1): the Piecewise Aggregate Approximation
+    of each point to K dimensions, coordinate j the mean of the j-th segment
+    of w = floor(d/K) consecutive coordinates (the last d - K*w coordinates
+    belong to no segment). Returns FP64 [n, K]."""
+    X = np.asarray(X, dtype=np.float64)
+    n, d = X.shape
+    w = d // K
+    if w < 1:
+        raise ValueError("need K <= d")
+    out = np.empty((n, K), dtype=np.float64)
+    for j in range(K):
+        out[:, j] = X[:, j * w:(j + 1) * w].sum(axis=1) / w
+    return out
+
+
 def select_breakpoints(Ps: np.ndarray, n_regions: int) -> np.ndarray:
     """Alg. 1 / Sec. 4.1: N_r+1 breakpoints per projected dimension from the sample.
 
@@ -296,10 +312,17 @@ class Index:
     P: Optional[np.ndarray] = None       # FP64 projections [n, L*K] (kept for tests)
     codes: Optional[np.ndarray] = None   # uint8 [n, L*K]
     max_size: int = 0                    # max_size of Alg. 3
+    reduction: str = "hash"              # "hash": Eq. 1 with A; "paa": DET-ONLY's segment means
 
     @property
     def n(self) -> int:
         return self.X.shape[0]
+
+    def project(self, X) -> np.ndarray:
+        """The projected points the index encodes (FP64 [m, L*K])."""
+        if self.reduction == "paa":
+            return paa_reduce(X, self.K)
+        return project(self.A, X)
 
 
 def build_index(X, A, sample, K: int, L: int, n_regions: int, max_size: int) -> Index:
@@ -314,6 +337,33 @@ def build_index(X, A, sample, K: int, L: int, n_regions: int, max_size: int) -> 
     return Index(X=X, A=A, E=E, trees=trees, K=K, L=L, n_regions=n_regions, P=P, codes=codes, max_size=max_size)
 
 
+def build_index_det_only(X, sample, K: int, n_regions: int, max_size: int) -> Index:
+    """DET-ONLY (Sec. 6.1): the encoding and indexing phases of DET-LSH with
+    one projected space (L = 1) given by the PAA reduction of the points
+    instead of Gaussian projections."""
+    X = np.asarray(X)
+    sample = np.asarray(sample, dtype=np.int64)
+    P = paa_reduce(X, K)
+    E = select_breakpoints(P[sample], n_regions)
+    codes = encode(P, E)
+    trees = [build_tree(codes, n_regions, max_size)]
+    return Index(X=X, A=np.zeros((K, X.shape[1])), E=E, trees=trees, K=K, L=1, n_regions=n_regions, P=P,
+                 codes=codes, max_size=max_size, reduction="paa")
+
+
+def index_from_codes(X, A, E, codes, K: int, L: int, n_regions: int, max_size: int) -> Index:
+    """The indexing phase (Alg. 3, reading R3) over given breakpoints E
+    [L*K, N_r+1] and region codes [n, L*K], e.g. those another implementation
+    computed from its own FP32 projections. With the projected queries passed
+    to c2k_ann as well (its qp32 argument), the query phase then runs on
+    exactly that implementation's FP32 inputs: the FP32-mirror form of the
+    oracle."""
+    codes = np.asarray(codes, dtype=np.uint8)
+    trees = [build_tree(codes[:, i * K:(i + 1) * K], n_regions, max_size) for i in range(L)]
+    return Index(X=np.asarray(X), A=np.asarray(A), E=np.asarray(E, dtype=np.float64), trees=trees, K=K, L=L,
+                 n_regions=n_regions, codes=codes, max_size=max_size)
+
+
 def insert_points(index: Index, X_new) -> Index:
     """Insertion of new points (ids n, n+1, ...) into an index (reading R14):
     their codes by Alg. 2 against the index's breakpoints (Alg. 1 is not run
@@ -322,7 +372,7 @@ def insert_points(index: Index, X_new) -> Index:
     which points arrive)."""
     X_new = np.asarray(X_new)
     X = np.concatenate([index.X, X_new.astype(index.X.dtype)], axis=0)
-    P = np.concatenate([index.P, project(index.A, X_new)], axis=0)
+    P = np.concatenate([index.P, index.project(X_new)], axis=0)
     codes = np.concatenate([index.codes, encode(P[index.n:], index.E)], axis=0)
     K, L = index.K, index.L
     trees = [build_tree(codes[:, i * K:(i + 1) * K], index.n_regions, index.max_size) for i in range(L)]
@@ -389,11 +439,21 @@ class QueryResult:
     rounds: int              # rounds started (t* + 1)
     stop: int                # 1: |S| >= beta n + k; 2: >= k within c r; 3: all leaves active
     cand: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))  # sorted S
+    tie_band: bool = False   # some tested distance lay within tie_rel of its round's (c r)^2
 
 
 def c2k_ann(index: Index, q: np.ndarray, k: int, c: float, r_min: float, eps: float,
-            beta: float, keep_candidates: bool = False) -> QueryResult:
-    """Alg. 7 (c^2-k-ANN) with the optimised range query of Sec. 6.2.2 (readings R5-R7)."""
+            beta: float, keep_candidates: bool = False, qp32: Optional[np.ndarray] = None,
+            tie_rel: float = 0.0) -> QueryResult:
+    """Alg. 7 (c^2-k-ANN) with the optimised range query of Sec. 6.2.2 (readings R5-R7).
+
+    qp32 (FP32 [L*K]) replaces the projected query H(q) (FP64, rounded to FP32
+    for the lower bounds) by given values: with index_from_codes this is the
+    FP32-mirror form. tie_rel > 0 flags the query (``tie_band``) when, in a
+    round whose ">= k within c*r" test ran, some candidate's FP64 squared
+    distance lies within tie_rel (relative) of (c*r_t)^2, where an FP32
+    distance could decide that test the other way.
+    """
     X = index.X
     n = X.shape[0]
     K, L, Nr = index.K, index.L, index.n_regions
@@ -401,8 +461,10 @@ def c2k_ann(index: Index, q: np.ndarray, k: int, c: float, r_min: float, eps: fl
     T = math.ceil(float(beta) * float(n) + float(k))
 
     q64 = np.asarray(q, dtype=np.float64)
-    qp = project(index.A, q64[None, :])[0]               # Alg. 7: H_i(q), hoisted out of the loop
-    qp32 = qp.astype(np.float32)
+    if qp32 is None:
+        qp = index.project(q64[None, :])[0]              # Alg. 7: H_i(q), hoisted out of the loop
+        qp32 = qp.astype(np.float32)
+    qp32 = np.asarray(qp32, dtype=np.float32)
     E32 = index.E.astype(np.float32)
 
     lb2 = []
@@ -420,6 +482,7 @@ def c2k_ann(index: Index, q: np.ndarray, k: int, c: float, r_min: float, eps: fl
     first_round = [np.searchsorted(thr_p, x, side="left") for x in lb2]
 
     in_S = np.zeros(n, dtype=bool)
+    tie_band = False
     S_order: List[np.ndarray] = []
     dist2_of = {}
     n_S = 0
@@ -447,7 +510,10 @@ def c2k_ann(index: Index, q: np.ndarray, k: int, c: float, r_min: float, eps: fl
                 break
         if stop:
             break
-        within = sum(1 for v in dist2_of.values() if v <= float(thr_c[t]))
+        thr = float(thr_c[t])
+        within = sum(1 for v in dist2_of.values() if v <= thr)
+        if tie_rel > 0 and any(abs(v - thr) <= tie_rel * thr for v in dist2_of.values()):
+            tie_band = True
         if within >= k:
             stop = 2
             break
@@ -463,7 +529,7 @@ def c2k_ann(index: Index, q: np.ndarray, k: int, c: float, r_min: float, eps: fl
     ids[:len(order)] = cand[order]
     dist[:len(order)] = np.sqrt(d2[order])
     return QueryResult(ids=ids, dist=dist, n_cand=int(n_S), rounds=t + 1, stop=stop,
-                       cand=np.sort(cand) if keep_candidates else np.zeros(0, np.int64))
+                       cand=np.sort(cand) if keep_candidates else np.zeros(0, np.int64), tie_band=tie_band)
 
 
 # ---------------------------------------------------------------- exact range query and (r,c)-ANN

@@ -36,7 +36,7 @@ SYMBOLS = ("detlsh_build", "detlsh_query", "detlsh_free", "detlsh_export_size", 
            "detlsh_plan_destroy", "detlsh_autotune", "detlsh_server_create", "detlsh_server_submit",
            "detlsh_server_poll", "detlsh_server_replay", "detlsh_server_stats", "detlsh_server_destroy",
            "detlsh_rc_ann", "detlsh_insert", "detlsh_memory_stats", "detlsh_draw_hashes",
-           "detlsh_draw_sample")
+           "detlsh_draw_sample", "detlsh_test_set_wait_limit_ns")
 PENDING, EADMIT = 1, -5
 PLAN_GRAPH = 1
 TRACE_KEYS = ("sample_proj_ms", "breakpoints_ms", "encode_ms", "leaves_ms", "query_proj_ms", "lb_ms",
@@ -142,6 +142,8 @@ def lib(path: Optional[str] = None):
     L.detlsh_draw_hashes.restype = ctypes.c_int
     L.detlsh_draw_sample.argtypes = [ctypes.c_uint64, i64, i64, vp]
     L.detlsh_draw_sample.restype = ctypes.c_int
+    L.detlsh_test_set_wait_limit_ns.argtypes = [ctypes.c_uint64]
+    L.detlsh_test_set_wait_limit_ns.restype = ctypes.c_uint64
     L.detlsh_memory_stats.argtypes = [i32, ctypes.POINTER(i64), i32]
     L.detlsh_memory_stats.restype = ctypes.c_int
     L.detlsh_select_breakpoints_noalloc.argtypes = [vp, i64, i32, i32, vp, vp]

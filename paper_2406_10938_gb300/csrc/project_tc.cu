@@ -15,10 +15,15 @@
 //           thread), then either the breakpoint search of Alg. 2 (shared
 //           memory) and 16-byte code stores, or the FP32 projections.
 // Every mbarrier wait is bounded by %globaltimer; a wait that runs out sets
-// an error word (the host reports DETLSH_ETIMEOUT) and the roles wind down.
+// an error word (the host reports DETLSH_ETIMEOUT) and the roles wind down:
+// the producer waits (bounded) for the copies it has issued to land and the
+// MMA issuer for its MMAs to complete before the TMEM is freed and the CTA
+// exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
+
+#include <atomic>
 
 #include "common.cuh"
 
@@ -30,6 +35,7 @@ constexpr int TC_STAGES = 4;
 constexpr int TC_EPI_WARPS = 16;     // 4 per TMEM lane quadrant, 16 accumulator columns each
 constexpr int TC_THREADS = 128 + 32 * TC_EPI_WARPS;
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;   // 2 s per wait
+constexpr unsigned long long TC_DRAIN_NS = 2000000000ull;  // 2 s per wait while winding down
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -53,17 +59,28 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase of the given parity; false (and *err set) on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+// Bounded wait for the phase of the given parity; false (and *err set) when
+// it runs out after limit_ns (limit 0: at the first retry) or another role
+// has set *err.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err,
+                                          unsigned long long limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   while (true) {
     if (mbar_try(bar, parity)) return true;
-    if (globaltimer() - t0 > TC_WAIT_NS || *(volatile int*)err) {
+    if (limit_ns == 0 || globaltimer() - t0 > limit_ns || *(volatile int*)err) {
       atomicExch(err, 1);
       return false;
     }
   }
+}
+// Bounded wait used while winding down: ignores the error word.
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (globaltimer() - t0 <= TC_DRAIN_NS)
+    if (mbar_try(bar, parity)) return true;
+  return false;
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -137,6 +154,7 @@ struct TcArgs {
   float* P;              // projections (store mode)
   int64_t p_so, p_sr;
   int* err;
+  unsigned long long wait_ns;   // limit of each pipeline wait
 };
 
 // Pipeline stages: a TF32 or three-part stage holds more tiles than a BF16 one.
@@ -205,8 +223,10 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
   constexpr uint32_t XUBYTES = TC_M * 64;
   uint8_t* sxu = sa3 + (A3 ? S * ABYTES : 0);     // [STAGES][XUBYTES] uint8 tile (A3)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sxu + (A3 ? S * XUBYTES : 0));
-  // full[0..S), empty[S..2S), tfull[2S..2S+2), tempty[2S+2..2S+4), split[2S+4..3S+4)
+  // full[0..S), empty[S..2S), tfull[2S..2S+2), tempty[2S+2..2S+4), split[2S+4..3S+4),
+  // the TMEM address word at 3S+4, drain at 3S+5
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 4);
+  const uint32_t drain_bar = smem_u32(&bars[3 * S + 5]);
   float* Es = reinterpret_cast<float*>(bars + 3 * S + 8);    // [LK][Nr] (ENCODE), e_z at [h][z]
   float* Slo = Es + a.LK * a.Nr;                                     // [LK]
   float* Sinv = Slo + a.LK;                                          // [LK]
@@ -227,6 +247,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
       mbar_init(smem_u32(&bars[2 * S + b]), 1);
       mbar_init(smem_u32(&bars[2 * S + 2 + b]), TC_EPI_WARPS);
     }
+    mbar_init(drain_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -261,7 +282,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       for (int kc = 0; kc < nk && ok; ++kc, ++it) {
         const uint32_t s = it % S, r = it / S;
-        ok = mbar_wait(smem_u32(&bars[S + s]), (r & 1) ^ 1, err);
+        ok = mbar_wait(smem_u32(&bars[S + s]), (r & 1) ^ 1, err, a.wait_ns);
         if (!ok) break;
         const uint32_t full = smem_u32(&bars[s]);
         mbar_expect_tx(full, (A3 ? XUBYTES : XBYTES) + tc_aparts<TF32, A3>() * ABYTES);
@@ -271,6 +292,10 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
         if (A3) tma_load_2d(smem_u32(sa3 + s * ABYTES), &tmA3, kc * KC, 0, full);
       }
     }
+    // `it` stages were issued; the last one of each stage must have landed
+    // before the CTA exits (at once unless a wait ran out)
+    for (uint32_t j = it > (uint32_t)S ? it - S : 0; j < it; ++j)
+      mbar_drain(smem_u32(&bars[j % S]), (j / S) & 1);
   } else if (TF32 && (warp == 2 || warp == 3)) {
     // ---- split of each staged X tile into x_big (in place) and x_small
     const int t = threadIdx.x - 64;   // 0..63
@@ -279,7 +304,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       for (int kc = 0; kc < nk && ok; ++kc, ++it) {
         const uint32_t s = it % S, r = it / S;
-        ok = mbar_wait(smem_u32(&bars[s]), r & 1, err);
+        ok = mbar_wait(smem_u32(&bars[s]), r & 1, err, a.wait_ns);
         if (!ok) break;
         float4* xv = reinterpret_cast<float4*>(sx + s * XBYTES);
         float4* xs = reinterpret_cast<float4*>(sxs + s * XBYTES);
@@ -310,7 +335,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       for (int kc = 0; kc < nk && ok; ++kc, ++it) {
         const uint32_t s = it % S, r = it / S;
-        ok = mbar_wait(smem_u32(&bars[s]), r & 1, err);
+        ok = mbar_wait(smem_u32(&bars[s]), r & 1, err, a.wait_ns);
         if (!ok) break;
         const uint4* src = reinterpret_cast<const uint4*>(sxu + s * XUBYTES);
         uint8_t* dst = sx + s * XBYTES;
@@ -343,13 +368,13 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
       const uint32_t ab = lt & 1, use = lt >> 1;
-      ok = mbar_wait(smem_u32(&bars[2 * S + 2 + ab]), (use & 1) ^ 1, err);
+      ok = mbar_wait(smem_u32(&bars[2 * S + 2 + ab]), (use & 1) ^ 1, err, a.wait_ns);
       if (!ok) break;
       tc_fence_after();
       const uint32_t dt = tmem + ab * (TCOLS / 2);
       for (int kc = 0; kc < nk; ++kc, ++it) {
         const uint32_t s = it % S, r = it / S;
-        ok = mbar_wait(smem_u32(&bars[(TF32 || A3) ? 2 * S + 4 + s : s]), r & 1, err);
+        ok = mbar_wait(smem_u32(&bars[(TF32 || A3) ? 2 * S + 4 + s : s]), r & 1, err, a.wait_ns);
         if (!ok) break;
         tc_fence_after();
         const uint64_t ad = smem_desc(smem_u32(sx + s * XBYTES));
@@ -383,6 +408,9 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
       if (!ok) break;
       mma_commit(smem_u32(&bars[2 * S + ab]));
     }
+    // every MMA issued has completed before the TMEM is freed
+    mma_commit(drain_bar);
+    mbar_drain(drain_bar, 0);
   } else if (warp >= 4) {
     // ---- epilogue: warp w reads TMEM lanes 32*(w%4).. (its quadrant's 32
     // points) and accumulator columns [16g, 16g+16), g = (w-4)/4; one point
@@ -393,7 +421,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CU
     uint32_t lt = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
       const uint32_t ab = lt & 1, use = lt >> 1;
-      if (!mbar_wait(smem_u32(&bars[2 * S + ab]), use & 1, err)) break;
+      if (!mbar_wait(smem_u32(&bars[2 * S + ab]), use & 1, err, a.wait_ns)) break;
       tc_fence_after();
       float v[16];
       if (active) tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + ab * (TCOLS / 2) + g * 16, v);
@@ -536,6 +564,8 @@ int gather_rows_bf16(const void* Xb, int d, const int64_t* ids, int64_t m, void*
   return DETLSH_OK;
 }
 
+std::atomic<unsigned long long> g_tc_wait_ns{TC_WAIT_NS};
+
 int check_tc_error(int* d_err, cudaStream_t s) {
   int h = 0;
   DL_CUDA(cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -575,6 +605,7 @@ int launch_project_tc(const void* Xb, int64_t rows, int d, const void* Ab, int L
   args.p_so = p_so;
   args.p_sr = p_sr;
   args.err = d_err;
+  args.wait_ns = g_tc_wait_ns.load();
   const bool enc = codes != nullptr;
 #define DL_TC_CASE(NN)                                                        \
   case NN:                                                                    \
@@ -716,6 +747,7 @@ int launch_project_bf16x3(const uint8_t* X, int64_t rows, int d, const void* Ab3
   args.p_so = p_so;
   args.p_sr = p_sr;
   args.err = d_err;
+  args.wait_ns = g_tc_wait_ns.load();
   const bool enc = codes != nullptr;
 #define DL_TC_CASE(NN)                                                        \
   case NN:                                                                    \
@@ -766,6 +798,7 @@ int launch_project_tf32(const float* X, int64_t rows, int d, const float* Asplit
   args.p_so = p_so;
   args.p_sr = p_sr;
   args.err = d_err;
+  args.wait_ns = g_tc_wait_ns.load();
   const bool enc = codes != nullptr;
 #define DL_TC_CASE(NN)                                                        \
   case NN:                                                                    \
@@ -785,3 +818,7 @@ int launch_project_tf32(const float* X, int64_t rows, int d, const float* Asplit
 }
 
 }  // namespace detlsh
+
+extern "C" uint64_t detlsh_test_set_wait_limit_ns(uint64_t ns) {
+  return detlsh::g_tc_wait_ns.exchange(ns);
+}

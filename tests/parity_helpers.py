@@ -82,3 +82,43 @@ def oracle_queries(ref, Q, k, c, r_min, eps, beta, keep=True):
         res.append(O.c2k_ann(ref, Q[qi], int(k[qi]), float(c[qi]), float(r_min[qi]), eps, beta,
                              keep_candidates=keep))
     return res
+
+
+def mirror_index(idx, X, A, K, L, Nr, max_leaf):
+    """The FP32-mirror oracle index of a GPU index: the GPU's breakpoints and
+    codes, the DE-Trees built from those codes by the oracle (which must equal
+    the GPU's leaf tables)."""
+    n = X.shape[0]
+    E = pkg.detlsh_export(idx, "EDGES").numpy().reshape(L * K, Nr + 1).astype(np.float64)
+    codes = gpu_codes(idx, n, K, L)
+    ref = O.index_from_codes(np.asarray(X), np.asarray(A), E, codes, K, L, Nr, max_leaf)
+    assert_trees_equal(gpu_trees(idx, K, L, n), ref.trees)
+    return ref
+
+
+def fp32_distance_band(d):
+    """Relative bound on the error of an FP32 squared distance of d
+    coordinates (a rounded difference, a rounded square and d rounded sums of
+    non-negative terms: at most (d + 3) units of 2^-24), never below the 1e-5
+    of the distance tolerance. Outside this band an FP32 comparison of the
+    squared distance with an FP32 threshold decides as the FP64 one does."""
+    return max(1e-5, (d + 3) * 2.0 ** -24)
+
+
+def check_topk_up_to_ties(got_ids, got_dist, ref, X64, q64, k, band):
+    """The GPU's top-k over the same candidate set as the oracle's: position
+    by position the same ids, except a swap between candidates whose FP64
+    distances agree within `band`; returned distances within 1e-5 of FP64."""
+    got_ids = np.asarray(got_ids[:k])
+    assert len(set(got_ids[got_ids >= 0].tolist())) == int((got_ids >= 0).sum())
+    cand = set(ref.cand.tolist())
+    for i in range(k):
+        gi, ri = int(got_ids[i]), int(ref.ids[i])
+        if ri < 0:
+            assert gi == -1 and np.isinf(got_dist[i])
+            continue
+        assert gi in cand
+        d_true = math.sqrt(float(((X64[gi] - q64) ** 2).sum()))
+        assert abs(float(got_dist[i]) - d_true) <= 1e-5 * d_true + 1e-30
+        if gi != ri:
+            assert abs(d_true ** 2 - float(ref.dist[i]) ** 2) <= band * float(ref.dist[i]) ** 2, (i, gi, ri)

@@ -37,6 +37,8 @@ def _bf16(t):
     ("tiny", 3_001, 32, 8, 2, 8, 333, 7),
     ("mid", 20_000, 128, 16, 4, 256, 2_000, 64),
     ("serving", 20_000, 128, 16, 4, 256, 2_000, 32),
+    ("precision", 4_000, 960, 16, 4, 256, 400, 64),
+    ("batching", 30_000, 96, 16, 4, 256, 3_000, 64),
 ])
 def test_bf16_build_exact_bit_parity(case):
     name, n, d, K, L, Nr, n_s, max_leaf = case
@@ -57,6 +59,8 @@ def test_bf16_build_exact_bit_parity(case):
 @pytest.mark.parametrize("case", [
     ("tiny", 10_000, 32, 16, 4, 16, 1_000, 256, 60, 10, 0.1),
     ("mid", 20_000, 128, 16, 4, 256, 2_000, 64, 20, 50, 0.1),
+    ("precision", 6_000, 960, 16, 4, 256, 600, 64, 12, 100, 0.1),
+    ("batching", 30_000, 96, 16, 4, 256, 3_000, 256, 16, 100, 0.01),
 ])
 def test_bf16_query_exact_bit_parity(case):
     name, n, d, K, L, Nr, n_s, max_leaf, nq, k, beta = case
@@ -97,16 +101,19 @@ def test_bf16_projection_of_rounded_inputs(name, n, d, n_s):
     idx.free()
 
 
-def test_shortlist_exact_inputs_match_the_oracle():
-    """Integer data is exact in BF16, so the coarse distances are the exact
-    ones and the shortlist path must return the oracle's results."""
-    n, d, K, L, Nr, n_s, max_leaf, nq, k = 20_000, 128, 16, 4, 256, 2_000, 64, 20, 50
-    X, Q = make_workload("mid", n=n, nq=nq, exact=True)
+@pytest.mark.parametrize("name,n,d,n_s,nq,k,shortlist", [("mid", 20_000, 128, 2_000, 20, 50, 512),
+                                                         ("precision", 6_000, 960, 600, 12, 100, 4096)])
+def test_shortlist_exact_inputs_match_the_oracle(name, n, d, n_s, nq, k, shortlist):
+    """Values BF16 holds exactly (integer data; the 1/8 grid of the precision
+    shape) make the coarse distances the exact ones, so the shortlist path
+    must return the oracle's results."""
+    K, L, Nr, max_leaf = 16, 4, 256, 64
+    X, Q = make_workload(name, n=n, nq=nq, exact=True)
     A = gaussian_projection(L, K, d, exact=True)
     ids = sample_ids(n, n_s)
     eps = O.eps_from_lemma3(K, L)
     idx = pkg.detlsh_build(X.to(DEV), A.to(DEV), ids.to(DEV), K, L, Nr, max_leaf, proj_mode=BF16)
-    oid, od, st, _ = pkg.detlsh_query(idx, Q.to(DEV), k, 1.5, 0.0, k_max=k, eps=eps, beta=0.1, shortlist=512)
+    oid, od, st, _ = pkg.detlsh_query(idx, Q.to(DEV), k, 1.5, 0.0, k_max=k, eps=eps, beta=0.1, shortlist=shortlist)
     ref = O.build_index(X.numpy(), A.numpy(), ids.numpy(), K, L, Nr, max_leaf)
     oid, od, st = oid.cpu().numpy(), od.cpu().numpy(), st.cpu().numpy()
     for qi in range(nq):

@@ -10,6 +10,8 @@ over the query batches. The queries run as one 10,000-query call, the way the
 benchmark issues them; the oracle answers only the sampled ones.
 """
 
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -82,4 +84,46 @@ def test_mid_full_size_bit_parity(full, proj_mode):
     for a, b in zip(got, out[:3]):
         assert torch.equal(a, b[sel])
     plan.destroy()
+    idx.free()
+
+
+MIRROR_SAMPLED = (0, 1, 777, 2048, 3333, 3334, 4999, 5000, 6666, 8191, 8192, 9998, 9999)
+
+
+def test_mid_full_size_fp32_mirror_candidate_sets():
+    """The benchmark's own inputs (FP32 points with integer values, N(0,1)
+    hash vectors, the benchmark's sample) and launch configuration (one
+    10,000-query call): the oracle's FP32-mirror form, given the GPU's
+    projected queries, breakpoints and codes, builds the same leaves and gives
+    the same candidate sets, rounds, stop rules, ids and distances for sampled
+    queries spread over the batches. The squared distances of these integer
+    points (below 2^24) are exact in FP32, so the distance test decides as in
+    FP64 and there is no tie band."""
+    from parity_helpers import check_topk_up_to_ties, mirror_index
+    X, Q = make_workload("mid", n=N, nq=NQ)
+    A = gaussian_projection(L, K, D)
+    ids = sample_ids(N, NS)
+    Xd, Qd = X.to(DEV), Q.to(DEV)
+    idx = pkg.detlsh_build(Xd, A.to(DEV), ids.to(DEV), K, L, NR, MAX_LEAF, borrow=True)
+    ref = mirror_index(idx, X.numpy(), A.numpy(), K, L, NR, MAX_LEAF)
+    eps = O.eps_from_lemma3(K, L)
+    kk = torch.full((NQ,), KK, dtype=torch.int32, device=DEV)
+    cc = torch.full((NQ,), C, dtype=torch.float32, device=DEV)
+    rr = torch.zeros(NQ, dtype=torch.float32, device=DEV)
+    qproj = torch.empty(NQ, L * K, dtype=torch.float32, device=DEV)
+    cap = int(math.ceil(BETA * N + KK)) - 1 + idx.info()["largest_leaf"]
+    out = pkg.detlsh_query(idx, Qd, kk, cc, rr, k_max=KK, eps=eps, beta=BETA, cand_cap=cap, qproj=qproj)
+    sel = torch.tensor(MIRROR_SAMPLED, device=DEV)
+    ids_o, dist_o, stats_o = (t[sel].cpu().numpy() for t in out[:3])
+    cand = out[3][sel].cpu().numpy().view(np.uint32)
+    qp = qproj[sel].cpu().numpy()
+    X64 = X.numpy().astype(np.float64)
+    for j, qi in enumerate(MIRROR_SAMPLED):
+        q64 = Q.numpy()[qi].astype(np.float64)
+        r = O.c2k_ann(ref, q64, KK, C, 0.0, eps, BETA, keep_candidates=True, qp32=qp[j])
+        assert (stats_o[j, 0], stats_o[j, 1], stats_o[j, 2], stats_o[j, 3]) == (r.n_cand, r.rounds, r.stop, 0), qi
+        assert np.array_equal(np.sort(cand[j, : stats_o[j, 0]].astype(np.int64)), r.cand), qi
+        assert np.array_equal(ids_o[j], r.ids[:KK]), qi
+        assert np.array_equal(dist_o[j], np.float32(r.dist[:KK])), qi
+        check_topk_up_to_ties(ids_o[j], dist_o[j], r, X64, q64, KK, 1e-5)
     idx.free()

@@ -94,6 +94,10 @@ BUILD_CASES = [
     ("tiny", 37, 32, 2, 2, 2, 2, 1),
     ("mid", 20_000, 128, 16, 4, 256, 2_000, 64),
     ("serving", 20_000, 128, 16, 4, 256, 2_000, 32),
+    # the precision and batching shapes: d = 960 takes the CUDA-core encoder,
+    # d = 96 the TF32 tensor-core one
+    ("precision", 4_000, 960, 16, 4, 256, 400, 64),
+    ("batching", 30_000, 96, 16, 4, 256, 3_000, 64),
 ]
 
 
@@ -246,6 +250,9 @@ QUERY_CASES = [
     ("serving", 3_000, 32, 16, 4, 16, 300, 32, 12, 10, 0.1, 0.0),
     ("serving", 3_000, 512, 16, 4, 16, 300, 32, 12, 10, 0.1, 0.0),
     ("serving", 3_000, 48, 16, 4, 16, 300, 32, 12, 10, 0.1, 0.0),
+    # the precision (d = 960) and batching (d = 96) shapes
+    ("precision", 6_000, 960, 16, 4, 256, 600, 64, 16, 100, 0.1, 0.0),
+    ("batching", 30_000, 96, 16, 4, 256, 3_000, 256, 24, 100, 0.01, 0.0),
 ]
 
 
@@ -314,9 +321,10 @@ def test_query_dedup_by_leaf_position_same_results(case):
 @pytest.mark.parametrize("name,n,d,Nr,n_s,max_leaf,nq,k", [("tiny", 10_000, 32, 16, 1_000, 64, 30, 10),
                                                          ("mid", 20_000, 128, 256, 2_000, 64, 20, 50)])
 def test_det_only_exact_bit_parity(name, n, d, Nr, n_s, max_leaf, nq, k):
-    """DET-ONLY (Sec. 6.1): one DE-Tree over the PAA reduction (segment means,
-    exact here: 1/w with w a power of two) and the same query. Index and
-    results equal the oracle's bit for bit."""
+    """DET-ONLY (Sec. 6.1): one DE-Tree over the PAA reduction and the same
+    query. The library projects with the segment-mean matrix (exact here: 1/w
+    with w a power of two); the oracle computes the segment means from X
+    itself. Index and results equal the oracle's bit for bit."""
     K, L, beta = 16, 1, 0.1
     X, Q = make_workload(name, n=n, nq=nq, exact=True, d=d)
     A = paa_projection(K, d)
@@ -327,7 +335,7 @@ def test_det_only_exact_bit_parity(name, n, d, Nr, n_s, max_leaf, nq, k):
     ks = torch.randint(1, k + 1, (nq,), generator=g, dtype=torch.int32)
     rm = torch.zeros(nq, dtype=torch.float32)
     idx = gpu_build(X, A, ids, K, L, Nr, max_leaf)
-    ref = O.build_index(X.numpy(), A.numpy(), ids.numpy(), K, L, Nr, max_leaf)
+    ref = O.build_index_det_only(X.numpy(), ids.numpy(), K, Nr, max_leaf)
     assert np.array_equal(gpu_codes(idx, n, K, L), ref.codes)
     assert_trees_equal(gpu_trees(idx, K, L, n), ref.trees)
     out_ids, out_dist, stats, _ = pkg.detlsh_query(idx, Q.to(DEV), ks.to(DEV), cs.to(DEV), rm.to(DEV), k_max=k,

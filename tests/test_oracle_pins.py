@@ -277,6 +277,68 @@ def test_query_hand_worked():
         assert (res.n_cand, res.rounds, res.stop) == (case["n_cand"], case["rounds"], case["stop"]), case["why"]
 
 
+def _two_tree_index(g):
+    X = np.array(g["X"], dtype=np.float64)
+    A = np.eye(2)
+    E = np.array(g["edges"], dtype=np.float64)
+    codes = O.encode(O.project(A, X), E)
+    return O.index_from_codes(X, A, E, codes, g["K"], g["L"], g["n_regions"], g["max_size"])
+
+
+def test_query_hand_worked_two_trees():
+    """Alg. 7 with L = 2, worked by hand: the order of the trees within a
+    round, the lower-bound order of the leaves within a tree, the |S| test
+    after every leaf and the duplicate-free count across trees each decide a
+    case (tests/golden/query_hand_two_trees.json)."""
+    g = _load("query_hand_two_trees.json")
+    idx = _two_tree_index(g)
+    assert [t.n_leaves for t in idx.trees] == [4, 4]
+    assert idx.trees[0].ids.tolist() == [2, 4, 0, 1, 3, 5]
+    assert idx.trees[1].ids.tolist() == [0, 5, 2, 3, 1, 4]
+    for case in g["cases"]:
+        res = O.c2k_ann(idx, np.array(g["q"]), case["k"], g["c"], g["r_min"], g["eps"], case["beta"],
+                        keep_candidates=True)
+        assert res.cand.tolist() == case["S"], case["why"]
+        assert res.ids.tolist() == case["ids"], case["why"]
+        assert res.dist.tolist() == [math.sqrt(v) for v in case["dist2"]], case["why"]
+        assert (res.n_cand, res.rounds, res.stop) == (case["n_cand"], case["rounds"], case["stop"]), case["why"]
+
+
+def test_query_tie_band_flag():
+    """The tie band marks a round whose (c r)^2 lies within tie_rel of a
+    candidate's squared distance: in the 1-d hand example ||q,o_3||^2 = 2^-6
+    equals (c r_0)^2 exactly (flagged); with r_min = 1/2 no tested distance
+    is near a threshold (not flagged)."""
+    g = _load("query_hand.json")
+    idx = _hand_index(g)
+    q = np.array([g["q"]])
+    hit = O.c2k_ann(idx, q, 1, 2.0, 0.0625, g["eps"], 1.0, tie_rel=1e-5)
+    assert hit.tie_band and hit.stop == 2
+    assert not O.c2k_ann(idx, q, 1, 2.0, 0.0625, g["eps"], 1.0).tie_band    # off unless asked
+    miss = O.c2k_ann(idx, q, 2, 2.0, 0.5, g["eps"], 1.0, tie_rel=1e-5)
+    assert not miss.tie_band
+
+
+def test_mirror_form_with_own_values_is_the_plain_query():
+    """index_from_codes over the oracle's own breakpoints and codes, queried
+    with the FP32 rounding of the oracle's own projected query, is the plain
+    c2k_ann: the mirror form adds no arithmetic of its own."""
+    X, Q = make_workload("tiny", n=3000, nq=6)
+    X, Q = X.numpy(), Q.numpy()
+    A = gaussian_projection(4, 16, X.shape[1]).numpy()
+    ref = O.build_index(X, A, sample_ids(3000, 300).numpy(), 16, 4, 16, 64)
+    mir = O.index_from_codes(X, A, ref.E, ref.codes, 16, 4, 16, 64)
+    for t_ref, t_mir in zip(ref.trees, mir.trees):
+        assert np.array_equal(t_ref.ids, t_mir.ids) and np.array_equal(t_ref.offset, t_mir.offset)
+    eps = O.eps_from_lemma3(16, 4)
+    for q in Q:
+        a = O.c2k_ann(ref, q, 10, 1.5, 0.0, eps, 0.1, keep_candidates=True)
+        b = O.c2k_ann(mir, q, 10, 1.5, 0.0, eps, 0.1, keep_candidates=True,
+                      qp32=O.project(A, q[None, :])[0].astype(np.float32))
+        assert np.array_equal(a.cand, b.cand) and np.array_equal(a.ids, b.ids)
+        assert (a.n_cand, a.rounds, a.stop) == (b.n_cand, b.rounds, b.stop)
+
+
 def test_query_all_leaves_is_exact_knn():
     # beta*n + k >= n and a radius covering every leaf: S = D, so Alg. 7 returns the exact kNN
     X, Q = make_workload("tiny", n=2000, nq=10)
@@ -316,6 +378,29 @@ def test_det_only_all_leaves_is_exact_knn():
         assert res.n_cand == 2000
         assert res.ids.tolist() == ids.tolist()
         assert np.allclose(res.dist, dist, rtol=0, atol=0)
+
+
+def test_paa_reduce_hand():
+    """DET-ONLY's reduction (Sec. 6.1) on hand-worked points: K=3 over d=7
+    gives segments of w=2 coordinates and leaves the 7th out."""
+    X = np.array([[1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 100.0], [0.0, -2.0, 8.0, 8.0, -1.0, 1.0, 3.0]])
+    assert O.paa_reduce(X, 3).tolist() == [[1.5, 3.5, 5.5], [-1.0, 8.0, 0.0]]
+    assert O.paa_reduce(X[:, :4], 1).tolist() == [[2.5], [3.5]]
+    assert O.paa_reduce(X, 7).tolist() == X.tolist()
+
+
+def test_det_only_index_reduces_x_itself():
+    """The oracle's DET-ONLY index computes segment means from X (not from a
+    projection matrix); with S = D its query returns the exact kNN."""
+    X, Q = make_workload("tiny", n=2000, nq=6)
+    X, Q = X.numpy(), Q.numpy()
+    idx = O.build_index_det_only(X, sample_ids(2000, 200).numpy(), 16, 16, 32)
+    assert idx.L == 1 and idx.reduction == "paa"
+    assert np.array_equal(idx.P, O.paa_reduce(X, 16))
+    for q in Q:
+        res = O.c2k_ann(idx, q, 7, 1.5, 1e6, 3.0, 1.0, keep_candidates=True)
+        ids, dist = O.exact_knn(X, q, 7)
+        assert res.n_cand == 2000 and res.ids.tolist() == ids.tolist()
 
 
 def _range_index(K=8, max_leaf=32):

@@ -16,10 +16,15 @@ shapes instead:
 Queries are fresh draws from the same mixture (same centres, another seed),
 the synthetic counterpart of the paper's held-out queries (Sec. 6.1).
 
-``exact=True`` returns a variant on a dyadic grid (``tiny``: multiples of 1/4)
-so that every FP32 sum and product of the method is exact; ``mid``/``serving``
-are integer-valued already. ``gaussian_projection(exact=True)`` likewise puts
-the N(0,1) draws on a 1/16 grid.
+``exact=True`` returns a variant on a dyadic grid (``tiny``: multiples of 1/4;
+``precision``: multiples of 1/8 clipped to +-63/8; ``batching``: multiples of
+1/256, which keeps |x| <= 1) so that every FP32 sum and product of the method
+is exact with hash vectors from ``gaussian_projection(exact=True)`` (N(0,1)
+draws on a 1/16 grid, at most 7 significant bits): at d = 960 a projection
+is at most 960 * 127 * 63 < 2^24 units of 2^-7 and a squared distance at
+most 960 * 126^2 < 2^24 units of 2^-6; at d = 96 a squared distance between
+points of norm about 1 is at most about 4 * 2^16 units of 2^-16. BF16 holds
+every such value. ``mid``/``serving`` are integer-valued already.
 
 Generation uses ``torch.Generator`` on the requested device; the same seed
 gives different numbers on CPU and CUDA, so a test that compares two sides
@@ -141,6 +146,12 @@ def make_workload(name: str, n: Optional[int] = None, nq: Optional[int] = None,
         if name == "tiny":
             X = (X * 4.0).round_() / 4.0
             Q = (Q * 4.0).round_() / 4.0
+        elif name == "precision":
+            X = (X * 8.0).round_().clamp_(-63, 63) / 8.0
+            Q = (Q * 8.0).round_().clamp_(-63, 63) / 8.0
+        elif name == "batching":
+            X = (X * 256.0).round_() / 256.0
+            Q = (Q * 256.0).round_() / 256.0
         elif name not in ("mid", "serving"):
             raise ValueError(f"no exact-arithmetic variant of {name!r}")
     if w.dtype == "u8":
