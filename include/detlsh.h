@@ -111,7 +111,11 @@ typedef struct {
                                 the memory budget, so that one batch's kernels
                                 may overlap the next one's. Plans run one batch
                                 at a time.                                        */
-  int32_t reserved;
+  int32_t coarse_gather;     /* shortlist mode: 0 computes the coarse distances
+                                leaf by leaf on the tensor cores (each leaf's rows
+                                read once for up to 128 queries that activated
+                                it); 1 gathers every candidate's row on the CUDA
+                                cores                                             */
 } detlsh_tuning;
 
 /* Query parameters shared by a batch (Alg. 7 inputs besides q, k, c, r_min). */

@@ -59,11 +59,12 @@ class Params(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int64), ("walk_ctas_per_sm", ctypes.c_int32),
                 ("dist_rows", ctypes.c_int32), ("dist_ctas_per_sm", ctypes.c_int32),
-                ("shortlist", ctypes.c_int32), ("streams", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("shortlist", ctypes.c_int32), ("streams", ctypes.c_int32), ("coarse_gather", ctypes.c_int32)]
 
     def as_dict(self):
         return {"batch": self.batch, "walk_ctas_per_sm": self.walk_ctas_per_sm, "dist_rows": self.dist_rows,
-                "dist_ctas_per_sm": self.dist_ctas_per_sm, "shortlist": self.shortlist, "streams": self.streams}
+                "dist_ctas_per_sm": self.dist_ctas_per_sm, "shortlist": self.shortlist, "streams": self.streams,
+                "coarse_gather": self.coarse_gather}
 
 
 def _tuning(t) -> Optional[Tuning]:
@@ -71,7 +72,8 @@ def _tuning(t) -> Optional[Tuning]:
         return t
     return Tuning(batch=t.get("batch", 0), walk_ctas_per_sm=t.get("walk_ctas_per_sm", 0),
                   dist_rows=t.get("dist_rows", 0), dist_ctas_per_sm=t.get("dist_ctas_per_sm", 0),
-                  shortlist=t.get("shortlist", 0), streams=t.get("streams", 0))
+                  shortlist=t.get("shortlist", 0), streams=t.get("streams", 0),
+                  coarse_gather=t.get("coarse_gather", 0))
 
 
 class ServerConfig(ctypes.Structure):

@@ -197,7 +197,8 @@ void free_index(detlsh_index* idx) {
   if (idx->owns_x && idx->X) cudaFreeAsync(const_cast<void*>(idx->X), 0);
   void* arrays[] = {idx->A, idx->At, idx->E, idx->Ps, idx->sample, idx->codes, idx->leaf_ids, idx->leaf_pos, idx->leaf_base,
                     idx->leaf_range, idx->leaf_plen, idx->leaf_prefix, idx->leaf_lo, idx->leaf_hi,
-                    idx->leaf_tree, idx->Xb, idx->Ab, idx->d_err, idx->Rtab, idx->Rlo, idx->Rinv, idx->Atf, idx->Ab3};
+                    idx->leaf_tree, idx->Xb, idx->Ab, idx->d_err, idx->Rtab, idx->Rlo, idx->Rinv, idx->Atf, idx->Ab3,
+                    idx->xn2, idx->chunk_base, idx->chunk_leaf};
   for (void* p : arrays)
     if (p) cudaFreeAsync(p, 0);
   cudaStreamSynchronize(0);
@@ -354,6 +355,8 @@ int build_impl(const void* X, int64_t n, int32_t d, int32_t dtype, const float* 
   tm.begin(TR_LEAVES);
   DL_TRY(build_leaves(idx, s));
   tm.end();
+  // BF16 indexes: what the leaf-major coarse distances of the shortlist mode read
+  if (idx->Xb) DL_TRY(build_lm_tables(idx, s));
   DL_TRY(tm.finish());
   DL_CUDA(cudaStreamSynchronize(s));
   return DETLSH_OK;
@@ -762,6 +765,7 @@ int detlsh_autotune(const detlsh_index* idx, const void* Q, int64_t nq, int32_t 
   out->dist_rows = best.dist_rows;
   out->dist_ctas_per_sm = best.dist_ctas_per_sm;
   out->streams = best.streams;
+  out->coarse_gather = best.coarse_gather;
   out->shortlist = pick;
   return DETLSH_OK;
 }

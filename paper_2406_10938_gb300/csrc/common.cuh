@@ -16,6 +16,9 @@ constexpr int kMaxL = 16;
 constexpr int kMaxLK = 256;
 constexpr int kRoundCap = 256;   // rounds of Alg. 7; the last one has infinite radius
 constexpr int kMaxTopK = 1024;
+// points per leaf chunk of the leaf-major coarse distances: a run of at most
+// 32 points that starts in a chunk ends inside the 256-point tile at its start
+constexpr uint32_t kLmChunk = 224;
 
 void set_error(const char* fmt, ...);
 void clear_error();
@@ -177,6 +180,10 @@ struct detlsh_index {
   uint8_t* leaf_lo = nullptr;       // [total][K] lowest code of the leaf box
   uint8_t* leaf_hi = nullptr;       // [total][K] highest code of the leaf box
   uint16_t* leaf_tree = nullptr;    // [total] tree of each leaf
+  float* xn2 = nullptr;             // [n] squared norms of the BF16 rows (BF16 mode)
+  uint32_t* chunk_base = nullptr;   // [total+1] first chunk of each leaf (BF16 mode)
+  uint32_t* chunk_leaf = nullptr;   // [n_chunks] leaf of each chunk
+  int64_t n_chunks = 0;             // leaf chunks of kLmChunk points
   int64_t total_leaves = 0;
   int64_t max_leaf_count = 0;
   int64_t leaf_base_h[detlsh::kMaxL + 1] = {0};
@@ -294,6 +301,33 @@ int launch_project_tc(const void* Xb, int64_t rows, int d, const void* Ab, int L
                       const float* E, const uint8_t* Rtab, const float* Rlo, const float* Rinv, int Nr,
                       uint8_t* codes, float* P, int64_t p_so, int64_t p_sr, int* d_err, cudaStream_t s);
 int check_tc_error(int* d_err, cudaStream_t s);
+// limit of each bounded wait of the tensor-core kernels (ns)
+unsigned long long tc_wait_limit_ns();
+
+// ---- leaf-major coarse distances on the tensor cores (dist_lm.cu)
+// BF16 indexes: squared norms of the BF16 rows, leaf chunk tables
+int build_lm_tables(detlsh_index* idx, cudaStream_t s);
+size_t lm_smem_bytes();
+// one batch's buffers: the walk's records [B][cap], their chunk sort, units
+struct LmBatch {
+  const void* qb16;         // [B][d] BF16 queries
+  int64_t nqg;              // grid bound on the batch size
+  const uint32_t* nqd;      // batch size (device)
+  const uint4* rec;         // [B][cap] records
+  int64_t cap;
+  const uint32_t* meta;
+  int mq_words, mq_nrec;
+  float* qn;                // [B]
+  uint32_t *khist, *kcur, *koff, *ucnt, *uoff;   // [n_chunks(+1)]
+  uint32_t* nunits;         // device word
+  uint4* srec;              // records by chunk
+  uint32_t* sq;             // their queries
+  uint4* units;
+  void* scan_ws;
+  size_t scan_ws_bytes;
+  float* d2;                // [B][cap]
+};
+int enqueue_coarse_lm(const detlsh_index* idx, const LmBatch& b, cudaStream_t s);
 // FP32 inputs on the tensor cores (TF32 split, FP32-faithful): Asplit holds
 // a_big [N][d] then a_small [N][d] (N = L*K rounded up to 16), from split_tf32.
 bool tf32_eligible(int dtype, int d, int LK);
@@ -329,7 +363,10 @@ int select_breakpoints(const float* Ps, int64_t n_s, int LK, int Nr, float* E,
 // ---- leaves (leaves.cu)
 int build_leaves(detlsh_index* idx, cudaStream_t s);
 
-// ---- sorts with caller storage (sort.cu)
+// ---- scans and sorts with caller storage (sort.cu)
+size_t scan_ws_bytes(int64_t n);
+int exclusive_scan_u32_ws(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* d_total, void* ws,
+                          size_t ws_bytes, cudaStream_t s);
 size_t radix_ws_bytes(int64_t n, int bit_lo, int bit_hi);
 int radix_sort_pairs_ws(const uint32_t* keys_in, const uint32_t* vals_in, int64_t n, int bit_lo,
                         int bit_hi, uint32_t* keys_out, uint32_t* vals_out, void* ws, size_t ws_bytes,
@@ -343,6 +380,7 @@ struct QueryTuning {
   int dist_rows = 1024;      // candidate rows per distance work item (multiple of 64)
   int dist_ctas_per_sm = 0;  // persistent distance CTAs per SM, 1..3; 0: 3
   int streams = 0;           // 2: batches alternate between two streams; 0 or 1: one stream
+  int coarse_gather = 0;     // shortlist mode: 1 gathers each candidate's row (no leaf-major tensor cores)
 };
 
 // Sizes and scratch layout (byte offsets into one device block) of a batch.
@@ -351,6 +389,10 @@ struct QueryShape {
   int64_t nsm = 0;   // SMs of the device
   int LK, L, wgrid, dgrid, dist_rows, tkc, k_max, shortlist, rq;
   bool smem_bitmap;
+  bool lm = false;           // coarse distances by leaf on the tensor cores
+  int64_t nk = 0, max_units = 0;
+  size_t o_rec = 0, o_srec = 0, o_sq = 0, o_qn = 0, o_khist = 0, o_kcur = 0, o_koff = 0, o_ucnt = 0, o_uoff = 0,
+         o_units = 0, o_scanws = 0, scanws_bytes = 0;
   size_t wl_total, bk_smem, bp_smem, bytes;
   size_t o_ctr, o_qp, o_qb16, o_qf, o_lb, o_mm, o_lround, o_hist, o_boff, o_list, o_cand, o_d2,
       o_rend, o_thr, o_meta, o_wsnew, o_wsbm, o_wspos, o_items, o_qk, o_qsort, qsort_bytes, o_hcnt, o_hcta;
@@ -359,7 +401,7 @@ struct QueryShape {
 // control words of a batch (uint32, at QueryShape::o_ctr): queries in the
 // batch, walk query counter, distance items queued, argument error flag,
 // distance items taken
-enum { CT_NQ = 0, CT_WORK, CT_QTAIL, CT_BAD, CT_HEAD, CT_WORDS = 64 };
+enum { CT_NQ = 0, CT_WORK, CT_QTAIL, CT_BAD, CT_HEAD, CT_NUNITS, CT_WORDS = 64 };
 
 // the launch shapes of detlsh_query_params::tuning (defaults for zero fields)
 int tuning_from_params(const detlsh_query_params* qp, QueryTuning* tu);

@@ -566,6 +566,8 @@ int gather_rows_bf16(const void* Xb, int d, const int64_t* ids, int64_t m, void*
 
 std::atomic<unsigned long long> g_tc_wait_ns{TC_WAIT_NS};
 
+unsigned long long tc_wait_limit_ns() { return g_tc_wait_ns.load(); }
+
 int check_tc_error(int* d_err, cudaStream_t s) {
   int h = 0;
   DL_CUDA(cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));

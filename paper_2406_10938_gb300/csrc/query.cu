@@ -205,6 +205,7 @@ enum {
   MQ_TEND,        // round in which the walk ended
   MQ_STOP,        // 1: |S| >= T, 3: every leaf active
   MQ_OVERFLOW,    // candidate list overflow (never expected)
+  MQ_NREC,        // leaf-run records the walk wrote (coarse distances by leaf)
   MQ_WORDS = 16
 };
 
@@ -507,6 +508,7 @@ struct WalkArgs {
   uint4* items;               // distance work queue: (query, first row, end row) per item
   uint32_t* qtail;            // items queued, zero at launch
   int dist_rows;              // candidate rows per item
+  uint4* rec;                 // [nqb][cap] leaf-run records, or null (then items are queued)
 };
 
 struct WalkLayout {
@@ -535,7 +537,7 @@ __host__ __device__ inline WalkLayout walk_layout(int L, int64_t smem_bitmap_wor
   return o;
 }
 
-enum { W_S = 0, W_STOP, W_NEED, W_KSTAR, W_ACC, W_TOTNEW, W_QN, W_LEAFA, W_OFFA, W_OVF, W_ONE };
+enum { W_S = 0, W_STOP, W_NEED, W_KSTAR, W_ACC, W_TOTNEW, W_QN, W_LEAFA, W_OFFA, W_OVF, W_ONE, W_NREC };
 
 // Append the new points of bucket leaves list[0..nl) (only leaves whose select
 // key lies in (kmin, kstar] when filtered) to the candidate list, in batches of at most
@@ -545,12 +547,17 @@ enum { W_S = 0, W_STOP, W_NEED, W_KSTAR, W_ACC, W_TOTNEW, W_QN, W_LEAFA, W_OFFA,
 // points of leaf list[j] not yet in S, lbk[j] its lower-bound bits, and
 // misc[W_TOTNEW] their total.
 // POS: the bitmap is indexed by a.leaf_pos (tree-0 leaf positions) instead of point ids.
+// With a.rec, every run of consecutive points of one leaf within a warp's 32
+// lanes that holds new points is also recorded for the leaf-major coarse
+// distances: (leaf, offset of the run's first point in the leaf, list
+// position of its first new point, mask of its new points).
 template <bool POS>
 __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, bool filtered,
                          unsigned long long kstar, const float* lbrow, unsigned char* sm,
                          const WalkLayout& ly, uint32_t* bitmap, uint32_t* cand,
                          bool count_only = false, uint32_t* newcnt = nullptr,
-                         uint32_t* lbk = nullptr, bool has_kmin = false, unsigned long long kmin = 0) {
+                         uint32_t* lbk = nullptr, bool has_kmin = false, unsigned long long kmin = 0,
+                         uint4* rec = nullptr) {
   unsigned long long* misc = reinterpret_cast<unsigned long long*>(sm + ly.misc);
   uint32_t* bpref = reinterpret_cast<uint32_t*>(sm + ly.bpref);
   uint32_t* bstart = reinterpret_cast<uint32_t*>(sm + ly.bstart);
@@ -686,6 +693,36 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
       uint32_t base = 0;   // one reservation per warp for the step's new points
       if (lane == 0 && tot) base = (uint32_t)atomicAdd(&misc[W_QN], (unsigned long long)tot);
       base = __shfl_sync(0xffffffffu, base, 0);
+      if (rec) {
+#pragma unroll
+        for (int u = 0, b2 = 0; u < WILP; b2 += __popc(fm[u]), ++u) {
+          // the valid lanes (f < take_pts) are a prefix of the warp
+          const uint32_t f = f0 + u * WT + threadIdx.x;
+          const bool valid = f < take_pts;
+          const uint32_t j = valid ? (uint32_t)fmap[f] : 0xffffffffu;
+          const uint32_t jp = __shfl_up_sync(0xffffffffu, j, 1);
+          const uint32_t leaders = __ballot_sync(0xffffffffu, valid && (lane == 0 || jp != j));
+          const uint32_t nvalid = __popc(__ballot_sync(0xffffffffu, valid));
+          const uint32_t after = leaders & ~((2u << lane) - 1u);   // leaders above this lane
+          const uint32_t end = after ? (uint32_t)(__ffs(after) - 1) : nvalid;
+          const bool lead = (leaders >> lane) & 1u;
+          uint32_t mask = 0;
+          if (lead) {
+            const uint32_t len = end - lane;
+            mask = (fm[u] >> lane) & (len >= 32 ? 0xffffffffu : ((1u << len) - 1u));
+          }
+          const uint32_t em = __ballot_sync(0xffffffffu, mask != 0u);
+          uint32_t slot = 0;
+          if (lane == 0 && em) slot = (uint32_t)atomicAdd(&misc[W_NREC], (unsigned long long)__popc(em));
+          slot = __shfl_sync(0xffffffffu, slot, 0);
+          const uint32_t rs = slot + __popc(em & lt);
+          if (mask && (int64_t)rs < a.cap) {
+            const uint32_t off = f - bpref[j] + (j == 0 ? offa : 0u);
+            const unsigned long long pos = S0 + base + b2 + __popc(fm[u] & lt);
+            rec[rs] = make_uint4(list[la + j], off, (uint32_t)pos, mask);
+          }
+        }
+      }
 #pragma unroll
       for (int u = 0; u < WILP; ++u) {
         if ((fm[u] >> lane) & 1u) {
@@ -876,6 +913,7 @@ __global__ void __launch_bounds__(WT, 2) k_walk(WalkArgs a) {
     const float* lbrow = a.lb2 + qb * a.total_leaves;
     const uint32_t* list = a.list + qb * a.total_leaves;
     uint32_t* cand = a.cand + qb * a.cap;
+    uint4* rec = a.rec ? a.rec + qb * a.cap : nullptr;
     uint32_t* rend = a.round_end + qb * kRoundCap;
     uint32_t* m = a.meta + qb * MQ_WORDS;
     const unsigned long long T = ((unsigned long long)m[MQ_T_HI] << 32) | m[MQ_T_LO];
@@ -890,6 +928,7 @@ __global__ void __launch_bounds__(WT, 2) k_walk(WalkArgs a) {
       misc[W_S] = 0;
       misc[W_STOP] = 0;
       misc[W_OVF] = 0;
+      misc[W_NREC] = 0;
     }
     __syncthreads();
     int t_end = tcap;
@@ -901,7 +940,8 @@ __global__ void __launch_bounds__(WT, 2) k_walk(WalkArgs a) {
       const bool whole_round = misc[W_S] + rpts < T;
       if (whole_round) {
         const uint32_t nl = s_boff[(t + 1) * L] - s_boff[t * L];
-        if (nl) walk_add<POS>(a, list + s_boff[t * L], nl, false, ~0ull, lbrow, sm, ly, bitmap, cand);
+        if (nl) walk_add<POS>(a, list + s_boff[t * L], nl, false, ~0ull, lbrow, sm, ly, bitmap, cand, false, nullptr,
+                              nullptr, false, 0, rec);
       }
       for (int i = 0; i < L && !whole_round; ++i) {
         const int b = t * L + i;
@@ -911,7 +951,7 @@ __global__ void __launch_bounds__(WT, 2) k_walk(WalkArgs a) {
         const unsigned long long bpts = s_pts[b];   // all of the bucket's points
         bool cut = false;
         if (misc[W_S] + bpts < T) {
-          walk_add<POS>(a, bl, nl, false, ~0ull, lbrow, sm, ly, bitmap, cand);
+          walk_add<POS>(a, bl, nl, false, ~0ull, lbrow, sm, ly, bitmap, cand, false, nullptr, nullptr, false, 0, rec);
         } else {
           // the bucket may hold the cut: its leaves in key order (lower bound,
           // leaf) are taken in chunks of about twice the points still needed
@@ -935,11 +975,13 @@ __global__ void __launch_bounds__(WT, 2) k_walk(WalkArgs a) {
             walk_add<POS>(a, bl, nl, true, kc, lbrow, sm, ly, bitmap, cand, true, newcnt, lbk, has_kmin, kmin);
             if (S0 + misc[W_TOTNEW] >= T) {
               const unsigned long long kstar = select_key(bl, lbk, newcnt, nl, has_kmin, kmin, need, sel, misc);
-              walk_add<POS>(a, bl, nl, true, kstar, lbrow, sm, ly, bitmap, cand, false, nullptr, nullptr, has_kmin, kmin);
+              walk_add<POS>(a, bl, nl, true, kstar, lbrow, sm, ly, bitmap, cand, false, nullptr, nullptr, has_kmin, kmin,
+                            rec);
               cut = true;
               break;
             }
-            walk_add<POS>(a, bl, nl, true, kc, lbrow, sm, ly, bitmap, cand, false, nullptr, nullptr, has_kmin, kmin);
+            walk_add<POS>(a, bl, nl, true, kc, lbrow, sm, ly, bitmap, cand, false, nullptr, nullptr, has_kmin, kmin,
+                          rec);
             if (kc == ~0ull) break;   // the bucket is exhausted without a cut
             has_kmin = true;
             kmin = kc;
@@ -966,9 +1008,11 @@ __global__ void __launch_bounds__(WT, 2) k_walk(WalkArgs a) {
       m[MQ_TEND] = (uint32_t)t_end;
       m[MQ_STOP] = misc[W_STOP] ? (uint32_t)misc[W_STOP] : 3u;
       m[MQ_OVERFLOW] = (uint32_t)misc[W_OVF];
+      m[MQ_NREC] = (uint32_t)misc[W_NREC];
     }
-    // queue the distance work of the listed candidates
-    {
+    // queue the distance work of the listed candidates (unless the leaf-run
+    // records serve the distances)
+    if (!a.rec) {
       __shared__ uint32_t s_ib, s_ni;
       if (threadIdx.x == 0) {
         const int64_t ns = min((int64_t)misc[W_S], a.cap);
@@ -1681,6 +1725,8 @@ int tuning_from_params(const detlsh_query_params* qp, QueryTuning* tu) {
   if (t.dist_rows) tu->dist_rows = t.dist_rows;
   tu->dist_ctas_per_sm = t.dist_ctas_per_sm;
   tu->streams = t.streams;
+  DL_REQUIRE(t.coarse_gather == 0 || t.coarse_gather == 1, "tuning.coarse_gather must be 0 or 1");
+  tu->coarse_gather = t.coarse_gather;
   return DETLSH_OK;
 }
 
@@ -1761,13 +1807,17 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   sh.cap = std::max<int64_t>(
       1, std::min<int64_t>(idx->n, (int64_t)std::min(tmax, 9.0e18) - 1 + idx->max_leaf_count));
   sh.items_per_q = (sh.cap + sh.dist_rows - 1) / sh.dist_rows;
+  // shortlist mode: coarse distances by leaf on the tensor cores (each record
+  // holds at least one new point, so a query writes at most cap of them)
+  sh.lm = shortlist > 0 && idx->chunk_base != nullptr && tu.coarse_gather == 0;
+  sh.nk = sh.lm ? idx->n_chunks : 0;
   // batch size: the tuning's, else bounded by the per-query buffers (at most
   // 12 GiB and a quarter of the free device memory; fewer, larger batches
   // shorten the tails of the per-query kernels)
   const int64_t per_q = sh.TL * 9 + sh.cap * 8 + sh.RL * 16 + kRoundCap * 12 + MQ_WORDS * 4 +
                         sh.LK * 4 + sh.items_per_q * 16 + ((sh.TL + 16383) / 16384) * sh.RL * 4 +
                         (idx->Xb ? (int64_t)idx->d * 2 : 0) + (shortlist > 0 ? (int64_t)idx->d * 4 : 0) +
-                        64;
+                        (sh.lm ? sh.cap * (16 + 16 + 4) + sh.cap / 8 + 4 : 0) + 64;
   int64_t B = tu.batch;
   if (B == 0) {
     size_t mem_free = 0, mem_total = 0;
@@ -1815,6 +1865,21 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   sh.o_qk = take(sizeof(uint32_t) * 4 * B);
   sh.qsort_bytes = radix_ws_bytes(B, 0, 32);
   sh.o_qsort = take(sh.qsort_bytes);
+  if (sh.lm) {
+    sh.max_units = sh.nk + (B * sh.cap) / 128 + 1;
+    sh.o_rec = take(sizeof(uint4) * B * sh.cap);
+    sh.o_srec = take(sizeof(uint4) * B * sh.cap);
+    sh.o_sq = take(sizeof(uint32_t) * B * sh.cap);
+    sh.o_qn = take(sizeof(float) * B);
+    sh.o_khist = take(sizeof(uint32_t) * sh.nk);
+    sh.o_kcur = take(sizeof(uint32_t) * sh.nk);
+    sh.o_koff = take(sizeof(uint32_t) * (sh.nk + 1));
+    sh.o_ucnt = take(sizeof(uint32_t) * sh.nk);
+    sh.o_uoff = take(sizeof(uint32_t) * (sh.nk + 1));
+    sh.o_units = take(sizeof(uint4) * sh.max_units);
+    sh.scanws_bytes = scan_ws_bytes(sh.nk);
+    sh.o_scanws = take(sh.scanws_bytes);
+  }
   sh.bytes = p;
   *out = sh;
   return DETLSH_OK;
@@ -1971,6 +2036,7 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   wa.items = items;
   wa.qtail = ctr + CT_QTAIL;
   wa.dist_rows = sh.dist_rows;
+  wa.rec = sh.lm ? reinterpret_cast<uint4*>(b + sh.o_rec) : nullptr;
   tm.begin(TR_WALK);
   if (idx->leaf_pos)
     k_walk<true><<<(unsigned)std::min<int64_t>(nqg, sh.wgrid), WT, sh.wl_total, s>>>(wa);
@@ -1980,7 +2046,31 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   tm.end();
 
   tm.begin(TR_DIST);
-  if (sh.shortlist > 0)
+  if (sh.lm) {
+    LmBatch lb{};
+    lb.qb16 = b + sh.o_qb16;
+    lb.nqg = nqg;
+    lb.nqd = nqd;
+    lb.rec = reinterpret_cast<const uint4*>(b + sh.o_rec);
+    lb.cap = sh.cap;
+    lb.meta = meta;
+    lb.mq_words = MQ_WORDS;
+    lb.mq_nrec = MQ_NREC;
+    lb.qn = reinterpret_cast<float*>(b + sh.o_qn);
+    lb.khist = reinterpret_cast<uint32_t*>(b + sh.o_khist);
+    lb.kcur = reinterpret_cast<uint32_t*>(b + sh.o_kcur);
+    lb.koff = reinterpret_cast<uint32_t*>(b + sh.o_koff);
+    lb.ucnt = reinterpret_cast<uint32_t*>(b + sh.o_ucnt);
+    lb.uoff = reinterpret_cast<uint32_t*>(b + sh.o_uoff);
+    lb.nunits = ctr + CT_NUNITS;
+    lb.srec = reinterpret_cast<uint4*>(b + sh.o_srec);
+    lb.sq = reinterpret_cast<uint32_t*>(b + sh.o_sq);
+    lb.units = reinterpret_cast<uint4*>(b + sh.o_units);
+    lb.scan_ws = b + sh.o_scanws;
+    lb.scan_ws_bytes = sh.scanws_bytes;
+    lb.d2 = d2b;
+    DL_TRY(enqueue_coarse_lm(idx, lb, s));
+  } else if (sh.shortlist > 0)
     k_dist_bf16<<<sh.dgrid, DT, 0, s>>>(static_cast<const __nv_bfloat16*>(idx->Xb), idx->d, qf, 0, candb,
                                          sh.cap, items, ctr + CT_QTAIL, ctr + CT_HEAD, d2b);
   else if (dist_u8_eligible(idx, Q))

@@ -145,3 +145,69 @@ def test_shortlist_float_inputs_recall_and_exact_distances():
         assert np.allclose(d2[qi], true, rtol=1e-5, atol=1e-6)
     assert np.mean(r2) >= np.mean(r1) - 0.02, (np.mean(r1), np.mean(r2))
     idx.free()
+
+
+@pytest.mark.parametrize("name,n,d,K,L,Nr,n_s,max_leaf,nq,k,beta", [
+    ("tiny", 10_000, 32, 16, 4, 16, 1_000, 256, 40, 10, 0.1),       # d below one 64-coordinate stage
+    ("batching", 30_000, 96, 16, 4, 256, 3_000, 256, 16, 100, 0.01),  # a partial second stage
+    ("mid", 20_000, 128, 16, 4, 256, 2_000, 64, 20, 50, 0.1),
+    ("tiny", 10_000, 32, 4, 4, 16, 1_000, 2_048, 12, 20, 0.5),      # leaves of several 224-point chunks
+    ("precision", 6_000, 960, 16, 4, 256, 600, 64, 8, 100, 0.1),     # fifteen stages
+])
+def test_coarse_by_leaf_on_exact_inputs(name, n, d, K, L, Nr, n_s, max_leaf, nq, k, beta):
+    """The shortlist mode's coarse distances by leaf on the tensor cores
+    (||q||^2 + ||o||^2 - 2 q.o, BF16 operands, FP32 accumulation) are exact
+    when BF16 holds the values and every sum is exact: the results equal the
+    per-candidate gather's and the oracle's bit for bit, and the candidate
+    sets are the oracle's."""
+    X, Q = make_workload(name, n=n, nq=nq, exact=True, d=d)
+    A = gaussian_projection(L, K, d, exact=True)
+    ids = sample_ids(n, n_s)
+    eps = O.eps_from_lemma3(K, L)
+    idx = pkg.detlsh_build(X.to(DEV), A.to(DEV), ids.to(DEV), K, L, Nr, max_leaf, proj_mode=BF16)
+    g = torch.Generator().manual_seed(nq + d)
+    cs = torch.tensor([1.2, 1.5, 2.0])[torch.randint(0, 3, (nq,), generator=g)]
+    ks = torch.randint(1, k + 1, (nq,), generator=g, dtype=torch.int32)
+    rm = torch.zeros(nq)
+    sl = min(4096, max(k, 256))
+    outs = []
+    for gather in (0, 1):
+        outs.append(pkg.detlsh_query(idx, Q.to(DEV), ks.to(DEV), cs.to(DEV), rm.to(DEV), k_max=k, eps=eps,
+                                     beta=beta, shortlist=sl, cand_cap=n, tuning={"coarse_gather": gather}))
+    for a, b in zip(outs[0][:3], outs[1][:3]):
+        assert torch.equal(a, b)
+    oid, od, st, cand = (t.cpu().numpy() for t in outs[0])
+    cand = cand.view(np.uint32)
+    ref = O.build_index(X.numpy(), A.numpy(), ids.numpy(), K, L, Nr, max_leaf)
+    for qi, r in enumerate(oracle_queries(ref, Q.numpy(), ks.numpy(), cs.numpy(), rm.numpy(), eps, beta)):
+        kq = int(ks[qi])
+        assert (st[qi, 0], st[qi, 1], st[qi, 2]) == (r.n_cand, r.rounds, r.stop), qi
+        assert np.array_equal(np.sort(cand[qi, : st[qi, 0]].astype(np.int64)), r.cand), qi
+        assert np.array_equal(oid[qi, :kq], r.ids[:kq]), qi
+        assert np.array_equal(od[qi, :kq], np.float32(r.dist[:kq])), qi
+    if name == "tiny" and K == 4:
+        assert idx.info()["largest_leaf"] > 448     # some leaf spans three chunks
+    idx.free()
+
+
+def test_coarse_by_leaf_float_inputs_agree_with_the_gather():
+    """FP32 inputs: the two coarse formulations round differently, so their
+    shortlists may differ at the margin; the returned distances are exact FP32
+    re-ranks either way and the top-k ids agree for nearly every query."""
+    n, d, K, L, Nr, n_s, nq, k = 20_000, 128, 16, 4, 256, 2_000, 64, 20
+    X, Q = make_workload("precision", n=n, nq=nq, d=d)
+    A = gaussian_projection(L, K, d)
+    ids = sample_ids(n, n_s)
+    idx = pkg.detlsh_build(X.to(DEV), A.to(DEV), ids.to(DEV), K, L, Nr, 128, proj_mode=BF16)
+    a = pkg.detlsh_query(idx, Q.to(DEV), k, 1.5, 0.0, k_max=k, beta=0.1, shortlist=256)
+    b = pkg.detlsh_query(idx, Q.to(DEV), k, 1.5, 0.0, k_max=k, beta=0.1, shortlist=256,
+                         tuning={"coarse_gather": 1})
+    ia, ib = a[0].cpu().numpy(), b[0].cpu().numpy()
+    agree = np.mean([len(set(ia[i]) & set(ib[i])) / k for i in range(nq)])
+    assert agree >= 0.99, agree
+    Xn, Qn = X.numpy().astype(np.float64), Q.numpy().astype(np.float64)
+    da = a[1].cpu().numpy()
+    for qi in range(nq):
+        true = np.sqrt(((Xn[ia[qi]] - Qn[qi]) ** 2).sum(axis=1))
+        assert np.allclose(da[qi], true, rtol=1e-5, atol=1e-6)
+    idx.free()
