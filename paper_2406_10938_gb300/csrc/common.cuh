@@ -16,9 +16,6 @@ constexpr int kMaxL = 16;
 constexpr int kMaxLK = 256;
 constexpr int kRoundCap = 256;   // rounds of Alg. 7; the last one has infinite radius
 constexpr int kMaxTopK = 1024;
-// points per leaf chunk of the leaf-major coarse distances: a run of at most
-// 32 points that starts in a chunk ends inside the 256-point tile at its start
-constexpr uint32_t kLmChunk = 224;
 
 void set_error(const char* fmt, ...);
 void clear_error();
@@ -183,7 +180,8 @@ struct detlsh_index {
   float* xn2 = nullptr;             // [n] squared norms of the BF16 rows (BF16 mode)
   uint32_t* chunk_base = nullptr;   // [total+1] first chunk of each leaf (BF16 mode)
   uint32_t* chunk_leaf = nullptr;   // [n_chunks] leaf of each chunk
-  int64_t n_chunks = 0;             // leaf chunks of kLmChunk points
+  int64_t n_chunks = 0;             // leaf chunks of lm_nmax - 32 points
+  int32_t lm_nmax = 0;              // points per tile of the leaf-major coarse distances (64 or 256)
   int64_t total_leaves = 0;
   int64_t max_leaf_count = 0;
   int64_t leaf_base_h[detlsh::kMaxL + 1] = {0};
@@ -307,7 +305,8 @@ unsigned long long tc_wait_limit_ns();
 // ---- leaf-major coarse distances on the tensor cores (dist_lm.cu)
 // BF16 indexes: squared norms of the BF16 rows, leaf chunk tables
 int build_lm_tables(detlsh_index* idx, cudaStream_t s);
-size_t lm_smem_bytes();
+// sort keys of the records (per leaf chunk, its 32-point windows)
+int64_t lm_sort_keys(int64_t n_chunks);
 // one batch's buffers: the walk's records [B][cap], their chunk sort, units
 struct LmBatch {
   const void* qb16;         // [B][d] BF16 queries
@@ -318,7 +317,8 @@ struct LmBatch {
   const uint32_t* meta;
   int mq_words, mq_nrec;
   float* qn;                // [B]
-  uint32_t *khist, *kcur, *koff, *ucnt, *uoff;   // [n_chunks(+1)]
+  uint32_t *khist, *kcur, *koff;   // [lm_sort_keys(n_chunks)] (+1 for koff)
+  uint32_t *ucnt, *uoff;           // [n_chunks] (+1 for uoff)
   uint32_t* nunits;         // device word
   uint4* srec;              // records by chunk
   uint32_t* sq;             // their queries

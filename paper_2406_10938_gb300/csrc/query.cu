@@ -565,6 +565,7 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   __shared__ uint32_t s_w[WNW];
+  uint32_t& s_nrec = *reinterpret_cast<uint32_t*>(&misc[W_NREC]);   // records of the query so far
 
   uint32_t* s_newc = reinterpret_cast<uint32_t*>(sm + ly.newc);
   if (threadIdx.x == 0) {
@@ -694,8 +695,11 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
       if (lane == 0 && tot) base = (uint32_t)atomicAdd(&misc[W_QN], (unsigned long long)tot);
       base = __shfl_sync(0xffffffffu, base, 0);
       if (rec) {
+        // runs of each of the WILP point groups: masks first, then one slot
+        // reservation per warp for all of them
+        uint32_t rmask[WILP], em[WILP], ntot = 0;
 #pragma unroll
-        for (int u = 0, b2 = 0; u < WILP; b2 += __popc(fm[u]), ++u) {
+        for (int u = 0; u < WILP; ++u) {
           // the valid lanes (f < take_pts) are a prefix of the warp
           const uint32_t f = f0 + u * WT + threadIdx.x;
           const bool valid = f < take_pts;
@@ -705,21 +709,26 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
           const uint32_t nvalid = __popc(__ballot_sync(0xffffffffu, valid));
           const uint32_t after = leaders & ~((2u << lane) - 1u);   // leaders above this lane
           const uint32_t end = after ? (uint32_t)(__ffs(after) - 1) : nvalid;
-          const bool lead = (leaders >> lane) & 1u;
-          uint32_t mask = 0;
-          if (lead) {
+          rmask[u] = 0;
+          if ((leaders >> lane) & 1u) {
             const uint32_t len = end - lane;
-            mask = (fm[u] >> lane) & (len >= 32 ? 0xffffffffu : ((1u << len) - 1u));
+            rmask[u] = (fm[u] >> lane) & (len >= 32 ? 0xffffffffu : ((1u << len) - 1u));
           }
-          const uint32_t em = __ballot_sync(0xffffffffu, mask != 0u);
-          uint32_t slot = 0;
-          if (lane == 0 && em) slot = (uint32_t)atomicAdd(&misc[W_NREC], (unsigned long long)__popc(em));
-          slot = __shfl_sync(0xffffffffu, slot, 0);
-          const uint32_t rs = slot + __popc(em & lt);
-          if (mask && (int64_t)rs < a.cap) {
+          em[u] = __ballot_sync(0xffffffffu, rmask[u] != 0u);
+          ntot += __popc(em[u]);
+        }
+        uint32_t slot = 0;
+        if (lane == 0 && ntot) slot = atomicAdd(&s_nrec, ntot);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+#pragma unroll
+        for (int u = 0, b2 = 0; u < WILP; b2 += __popc(fm[u]), slot += __popc(em[u]), ++u) {
+          const uint32_t rs = slot + __popc(em[u] & lt);
+          if (rmask[u] && (int64_t)rs < a.cap) {
+            const uint32_t f = f0 + u * WT + threadIdx.x;
+            const uint32_t j = fmap[f];
             const uint32_t off = f - bpref[j] + (j == 0 ? offa : 0u);
             const unsigned long long pos = S0 + base + b2 + __popc(fm[u] & lt);
-            rec[rs] = make_uint4(list[la + j], off, (uint32_t)pos, mask);
+            rec[rs] = make_uint4(list[la + j], off, (uint32_t)pos, rmask[u]);
           }
         }
       }
@@ -1871,13 +1880,14 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
     sh.o_srec = take(sizeof(uint4) * B * sh.cap);
     sh.o_sq = take(sizeof(uint32_t) * B * sh.cap);
     sh.o_qn = take(sizeof(float) * B);
-    sh.o_khist = take(sizeof(uint32_t) * sh.nk);
-    sh.o_kcur = take(sizeof(uint32_t) * sh.nk);
-    sh.o_koff = take(sizeof(uint32_t) * (sh.nk + 1));
+    const int64_t nks = lm_sort_keys(sh.nk);
+    sh.o_khist = take(sizeof(uint32_t) * nks);
+    sh.o_kcur = take(sizeof(uint32_t) * nks);
+    sh.o_koff = take(sizeof(uint32_t) * (nks + 1));
     sh.o_ucnt = take(sizeof(uint32_t) * sh.nk);
     sh.o_uoff = take(sizeof(uint32_t) * (sh.nk + 1));
     sh.o_units = take(sizeof(uint4) * sh.max_units);
-    sh.scanws_bytes = scan_ws_bytes(sh.nk);
+    sh.scanws_bytes = scan_ws_bytes(nks);
     sh.o_scanws = take(sh.scanws_bytes);
   }
   sh.bytes = p;
