@@ -371,7 +371,8 @@ void detlsh_plan_destroy(detlsh_plan* plan);
  * DETLSH_PROJ_BF16 and min_agreement in (0, 1], out->shortlist is the
  * smallest shortlist in {64, 128, ..., 4096} (at least k_max) whose top-k
  * holds, averaged over the sample, at least min_agreement of the ids of the
- * exact FP32 top-k, if it is also faster than exact distances; else 0.
+ * exact FP32 top-k, if it is also faster than exact distances (else 0), and
+ * out->coarse_gather is the faster of the two coarse-distance methods.
  * Synchronizes `stream`. Errors as detlsh_query.
  */
 int detlsh_autotune(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dtype,

@@ -750,8 +750,17 @@ int detlsh_autotune(const detlsh_index* idx, const void* Q, int64_t nq, int32_t 
       }
       agree /= (double)nq;
       if (agree >= min_agreement) {
-        float t_sl = 0.f;
+        // the coarse distances by leaf on the tensor cores or by candidate
+        // gather, whichever is faster on this index and sample
+        float t_sl = 0.f, t_alt = 0.f;
         st = time_tuned(x, sl, best, &t_sl);
+        QueryTuning alt = best;
+        alt.coarse_gather = 1 - best.coarse_gather;
+        if (st == DETLSH_OK) st = time_tuned(x, sl, alt, &t_alt);
+        if (st == DETLSH_OK && t_alt < t_sl) {
+          best = alt;
+          t_sl = t_alt;
+        }
         if (st == DETLSH_OK && t_sl < t_exact) pick = sl;
         break;
       }

@@ -181,7 +181,7 @@ struct detlsh_index {
   uint32_t* chunk_base = nullptr;   // [total+1] first chunk of each leaf (BF16 mode)
   uint32_t* chunk_leaf = nullptr;   // [n_chunks] leaf of each chunk
   int64_t n_chunks = 0;             // leaf chunks of lm_nmax - 32 points
-  int32_t lm_nmax = 0;              // points per tile of the leaf-major coarse distances (64 or 256)
+  int32_t lm_nmax = 0;              // points per tile of the leaf-major coarse distances (64 or 128)
   int64_t total_leaves = 0;
   int64_t max_leaf_count = 0;
   int64_t leaf_base_h[detlsh::kMaxL + 1] = {0};

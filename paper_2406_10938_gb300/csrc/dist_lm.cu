@@ -9,7 +9,7 @@
 // of the batch are grouped by leaf chunk (NMAX - 32 points: a run of at most
 // 32 points that starts in a chunk lies inside the NMAX-point tile at the
 // chunk's start) and, inside a chunk, by the 32-point window the run starts
-// in. NMAX is 64 for indexes of small leaves, else 256 (chosen at build).
+// in. NMAX is 64 for indexes of small leaves, else 128 (chosen at build).
 // A persistent kernel then takes (chunk, up to 128 records) units:
 //   last 4     stage each unit's metadata (query rows, point ids, list
 //              positions, masks, norms) into a ring of eight slots, four
@@ -555,8 +555,8 @@ int64_t lm_sort_keys(int64_t n_chunks) { return n_chunks * LM_SUB; }
 int build_lm_tables(detlsh_index* idx, cudaStream_t s) {
   const int64_t TL = idx->total_leaves;
   // 64-point tiles (six stages, eight accumulators) when the leaves are small
-  // on average, else 256-point tiles (three stages, two accumulators)
-  idx->lm_nmax = (idx->n * idx->L) <= 48 * TL ? 64 : 256;
+  // on average, else 128-point tiles (four stages, four accumulators)
+  idx->lm_nmax = (idx->n * idx->L) <= 48 * TL ? 64 : 128;
   const uint32_t chunk = (uint32_t)idx->lm_nmax - 32;
   DL_TRY(index_alloc(&idx->xn2, sizeof(float) * idx->n, s));
   k_rownorm_bf16<<<152 * 8, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(idx->Xb), idx->n, nullptr, idx->d,
@@ -622,7 +622,7 @@ int enqueue_coarse_lm(const detlsh_index* idx, const LmBatch& b, cudaStream_t s)
   a.cap = b.cap;
   a.err = idx->d_err;
   a.wait_ns = tc_wait_limit_ns();
-  return nmax == 64 ? launch_lm<64>(a, s) : launch_lm<256>(a, s);
+  return nmax == 64 ? launch_lm<64>(a, s) : launch_lm<128>(a, s);
 }
 
 }  // namespace detlsh
