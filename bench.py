@@ -920,7 +920,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-queries", type=int, default=8, help="queries of the single-thread oracle baseline")
-    ap.add_argument("--nq", type=int, default=WORKLOAD["nq"], help="queries per step (default: the workload's)")
+    ap.add_argument("--nq", type=int, default=None,
+                    help="queries per step (default: the workload's; applies to the workload run alone)")
     ap.add_argument("--method", default="det-lsh", choices=["det-lsh", "det-only"],
                     help="mid workload: DET-LSH (L Gaussian projections) or DET-ONLY (one tree over PAA)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -946,7 +947,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    WORKLOAD["nq"] = args.nq
+    if args.nq is not None:
+        {"mid": WORKLOAD, "batching": BATCHING, "precision": PRECISION, "serving": SERVING}[args.workload]["nq"] = args.nq
     if args.method == "det-only":
         WORKLOAD["method"] = "det-only"
         WORKLOAD["L"] = 1
