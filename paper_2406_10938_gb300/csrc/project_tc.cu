@@ -573,7 +573,10 @@ int check_tc_error(int* d_err, cudaStream_t s) {
   DL_CUDA(cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   DL_CUDA(cudaStreamSynchronize(s));
   if (h) {
-    set_error("a bounded wait in the tensor-core projection ran out");
+    // reported once: the word is cleared for the index's next call
+    DL_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    DL_CUDA(cudaStreamSynchronize(s));
+    set_error("a bounded wait of a tensor-core kernel ran out");
     return DETLSH_ETIMEOUT;
   }
   return DETLSH_OK;

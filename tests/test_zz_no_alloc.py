@@ -14,6 +14,7 @@ other test has run.
 """
 
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -57,6 +58,9 @@ def test_matches_allocating_entry_point_on_consecutive_calls(pkg):
     outs = [torch.full((Ps.shape[0], Nr + 1), float("nan"), device="cuda:0") for Ps, Nr in ins]
     # first call on the device (looks up the fixed array), then measure
     assert _noalloc(L, ins[0][0], ins[0][1], outs[0]) == 0, L.detlsh_last_error()
+    # tensors of earlier tests held in reference cycles are freed now, not
+    # during the measurement
+    gc.collect()
     torch.cuda.synchronize()
     torch_before = torch.cuda.memory_allocated()
     before = _pool_stats(L, reset=True)
