@@ -116,6 +116,15 @@ typedef struct {
                                 read once for up to 128 queries that activated
                                 it); 1 gathers every candidate's row on the CUDA
                                 cores                                             */
+  int32_t id_bucket_log2;    /* the per-candidate distance gather takes the
+                                batch's candidates grouped by point-id range, all
+                                queries' candidates in ids [0, 2^x) first, then
+                                [2^x, 2^(x+1)), ..., so that the rows read at the
+                                same time lie in a few MB of X and stay in L2
+                                (the points are candidates of many queries of a
+                                batch). 0: x chosen for ranges of about 32 MB of
+                                points; 10..31: that x; -1: walk order (no
+                                grouping). The distances are the same either way */
 } detlsh_tuning;
 
 /* Query parameters shared by a batch (Alg. 7 inputs besides q, k, c, r_min). */

@@ -59,12 +59,13 @@ class Params(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int64), ("walk_ctas_per_sm", ctypes.c_int32),
                 ("dist_rows", ctypes.c_int32), ("dist_ctas_per_sm", ctypes.c_int32),
-                ("shortlist", ctypes.c_int32), ("streams", ctypes.c_int32), ("coarse_gather", ctypes.c_int32)]
+                ("shortlist", ctypes.c_int32), ("streams", ctypes.c_int32), ("coarse_gather", ctypes.c_int32),
+                ("id_bucket_log2", ctypes.c_int32)]
 
     def as_dict(self):
         return {"batch": self.batch, "walk_ctas_per_sm": self.walk_ctas_per_sm, "dist_rows": self.dist_rows,
                 "dist_ctas_per_sm": self.dist_ctas_per_sm, "shortlist": self.shortlist, "streams": self.streams,
-                "coarse_gather": self.coarse_gather}
+                "coarse_gather": self.coarse_gather, "id_bucket_log2": self.id_bucket_log2}
 
 
 def _tuning(t) -> Optional[Tuning]:
@@ -73,7 +74,7 @@ def _tuning(t) -> Optional[Tuning]:
     return Tuning(batch=t.get("batch", 0), walk_ctas_per_sm=t.get("walk_ctas_per_sm", 0),
                   dist_rows=t.get("dist_rows", 0), dist_ctas_per_sm=t.get("dist_ctas_per_sm", 0),
                   shortlist=t.get("shortlist", 0), streams=t.get("streams", 0),
-                  coarse_gather=t.get("coarse_gather", 0))
+                  coarse_gather=t.get("coarse_gather", 0), id_bucket_log2=t.get("id_bucket_log2", 0))
 
 
 class ServerConfig(ctypes.Structure):

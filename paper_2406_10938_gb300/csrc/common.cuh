@@ -381,6 +381,7 @@ struct QueryTuning {
   int dist_ctas_per_sm = 0;  // persistent distance CTAs per SM, 1..3; 0: 3
   int streams = 0;           // 2: batches alternate between two streams; 0 or 1: one stream
   int coarse_gather = 0;     // shortlist mode: 1 gathers each candidate's row (no leaf-major tensor cores)
+  int id_bucket_log2 = 0;    // gather by point-id range of 2^x rows; 0: automatic; -1: in walk order
 };
 
 // Sizes and scratch layout (byte offsets into one device block) of a batch.
@@ -391,6 +392,10 @@ struct QueryShape {
   bool smem_bitmap;
   bool lm = false;           // coarse distances by leaf on the tensor cores
   int64_t nk = 0, max_units = 0;
+  // gather by point-id range: log2 rows per range (0: walk order), ranges
+  int bshift = 0;
+  int64_t nbk = 0;
+  size_t o_pairs = 0, o_bcnt = 0, o_boffq = 0, o_icnt = 0, o_ioff = 0, o_bscan = 0, bscan_bytes = 0;
   size_t o_rec = 0, o_srec = 0, o_sq = 0, o_qn = 0, o_khist = 0, o_kcur = 0, o_koff = 0, o_ucnt = 0, o_uoff = 0,
          o_units = 0, o_scanws = 0, scanws_bytes = 0;
   size_t wl_total, bk_smem, bp_smem, bytes;

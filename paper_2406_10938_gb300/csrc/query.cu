@@ -509,6 +509,7 @@ struct WalkArgs {
   uint32_t* qtail;            // items queued, zero at launch
   int dist_rows;              // candidate rows per item
   uint4* rec;                 // [nqb][cap] leaf-run records, or null (then items are queued)
+  int queue_items;            // 0: the distance work is queued after the walk (by point-id range)
 };
 
 struct WalkLayout {
@@ -1021,7 +1022,7 @@ __global__ void __launch_bounds__(WT, 2) k_walk(WalkArgs a) {
     }
     // queue the distance work of the listed candidates (unless the leaf-run
     // records serve the distances)
-    if (!a.rec) {
+    if (!a.rec && a.queue_items) {
       __shared__ uint32_t s_ib, s_ni;
       if (threadIdx.x == 0) {
         const int64_t ns = min((int64_t)misc[W_S], a.cap);
@@ -1157,12 +1158,14 @@ __device__ __forceinline__ uint32_t next_item(uint32_t* head, int lane) {
   return __shfl_sync(0xffffffffu, it, 0);
 }
 
-template <typename TX>
+// BK: the items address the query's candidates grouped by point-id range,
+// (point id, list position) pairs; the distance goes to the list position.
+template <typename TX, bool BK>
 __global__ void __launch_bounds__(DT, 3)
 k_dist(const TX* __restrict__ X, int d, const TX* __restrict__ Q, int64_t q0,
-       const uint32_t* __restrict__ cand, int64_t cap, const uint4* __restrict__ items,
-       const uint32_t* __restrict__ qtail, uint32_t* __restrict__ head, float* __restrict__ d2out,
-       bool vec4) {
+       const uint32_t* __restrict__ cand, const uint2* __restrict__ pairs, int64_t cap,
+       const uint4* __restrict__ items, const uint32_t* __restrict__ qtail, uint32_t* __restrict__ head,
+       float* __restrict__ d2out, bool vec4) {
   const uint32_t nit = *qtail;
   const int lane = threadIdx.x & 31;
   uint32_t it = next_item(head, lane);
@@ -1173,19 +1176,20 @@ k_dist(const TX* __restrict__ X, int d, const TX* __restrict__ Q, int64_t q0,
     const int64_t r0 = item.y, r1 = item.z;
     const TX* q = Q + (q0 + qb) * (int64_t)d;
     const uint32_t* cl = cand + qb * cap;
+    const uint2* pl = BK ? pairs + qb * cap : nullptr;
     float* out = d2out + qb * cap;
     for (int64_t e0 = r0; e0 < r1; e0 += ILP) {
       uint32_t ids[ILP];
       float acc[ILP];
 #pragma unroll
       for (int u = 0; u < ILP; ++u) {
-        ids[u] = (e0 + u < r1) ? __ldg(cl + e0 + u) : 0xffffffffu;
+        ids[u] = (e0 + u < r1) ? (BK ? __ldg(&pl[e0 + u].x) : __ldg(cl + e0 + u)) : 0xffffffffu;
         acc[u] = 0.f;
       }
       rows_dist2<TX>(X, d, ids, q, vec4, lane, acc);
       const float v = transpose_reduce8(acc, lane);
       const int r = (lane >> 2) & 7;
-      if ((lane & 3) == 0 && e0 + r < r1) out[e0 + r] = v;
+      if ((lane & 3) == 0 && e0 + r < r1) out[BK ? (int64_t)__ldg(&pl[e0 + r].y) : e0 + r] = v;
     }
     it = nx;
   }
@@ -1196,10 +1200,12 @@ k_dist(const TX* __restrict__ X, int d, const TX* __restrict__ Q, int64_t q0,
 // of them (32 rows at d = 128) in flight. The squared distance is
 // sum x^2 - 2 sum x q + sum q^2 in 32-bit integers (dp4a), exact whatever the
 // order of the sums (at most 512 * 255^2 < 2^31), converted to FP32 once.
+template <bool BK>
 __global__ void __launch_bounds__(DT, 3)
 k_dist_u8(const uint8_t* __restrict__ X, int d, const uint8_t* __restrict__ Q, int64_t q0,
-          const uint32_t* __restrict__ cand, int64_t cap, const uint4* __restrict__ items,
-          const uint32_t* __restrict__ qtail, uint32_t* __restrict__ head, float* __restrict__ d2out) {
+          const uint32_t* __restrict__ cand, const uint2* __restrict__ pairs, int64_t cap,
+          const uint4* __restrict__ items, const uint32_t* __restrict__ qtail, uint32_t* __restrict__ head,
+          float* __restrict__ d2out) {
   const uint32_t nit = *qtail;
   const int lane = threadIdx.x & 31;
   const int gs = d >> 4;       // lanes per row
@@ -1216,13 +1222,14 @@ k_dist_u8(const uint8_t* __restrict__ X, int d, const uint8_t* __restrict__ Q, i
                     __dp4a(qv.w, qv.w, 0u));
     for (int off = gs >> 1; off > 0; off >>= 1) qsq += __shfl_xor_sync(0xffffffffu, qsq, off);
     const uint32_t* cl = cand + qb * cap;
+    const uint2* pl = BK ? pairs + qb * cap : nullptr;
     float* out = d2out + qb * cap;
     for (int64_t e0 = r0; e0 < r1; e0 += 8 * rpl) {
       uint32_t ids[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int64_t e = e0 + u * rpl + grp;
-        ids[u] = e < r1 ? __ldg(cl + e) : 0xffffffffu;
+        ids[u] = e < r1 ? (BK ? __ldg(&pl[e].x) : __ldg(cl + e)) : 0xffffffffu;
       }
       uint4 xv[8];
 #pragma unroll
@@ -1246,12 +1253,89 @@ k_dist_u8(const uint8_t* __restrict__ X, int d, const uint8_t* __restrict__ Q, i
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int64_t e = e0 + u * rpl + grp;
-          if (e < r1) out[e] = (float)(part[u] + qsq);
+          if (e < r1) out[BK ? (int64_t)__ldg(&pl[e].y) : e] = (float)(part[u] + qsq);
         }
       }
     }
     it = nx;
   }
+}
+
+// ------------------------------------------------------------------ gather by point-id range
+// The candidates of a batch grouped by point-id range before the gather: a
+// point is a candidate of many queries of a batch (about beta of them), so
+// when every query's candidates in ids [0, R) are taken first, then those in
+// [R, 2R), ..., the rows read at the same time lie in R rows of X, which stay
+// in L2 while all queries read them. The distances are the same; each goes
+// to its list position.
+constexpr int BKT = 256;   // threads of the per-query grouping kernel
+constexpr int kMaxIdBuckets = 1024;
+
+// One CTA per query: its candidates' counts per id range (range-major counts
+// bcnt[b][qb] and in-query offsets boffq[qb][b]), then the (point id, list
+// position) pairs of each range at its offset. Queries at or past the batch
+// size count nothing.
+__global__ void __launch_bounds__(BKT)
+k_cand_buckets(const uint32_t* __restrict__ cand, int64_t cap, const uint32_t* __restrict__ meta,
+               const uint32_t* __restrict__ nqd, int bshift, int nbk, int64_t nqg, uint2* __restrict__ pairs,
+               uint32_t* __restrict__ bcnt, uint32_t* __restrict__ boffq) {
+  __shared__ uint32_t s_cnt[kMaxIdBuckets], s_off[kMaxIdBuckets];
+  __shared__ uint32_t s_w[BKT / 32];
+  const int64_t qb = blockIdx.x;
+  const bool active = qb < (int64_t)*nqd;
+  const int64_t ns = active ? min((int64_t)meta[qb * MQ_WORDS + MQ_NS], cap) : 0;
+  for (int b = threadIdx.x; b < nbk; b += BKT) s_cnt[b] = 0;
+  __syncthreads();
+  const uint32_t* cl = cand + qb * cap;
+  for (int64_t i = threadIdx.x; i < ns; i += BKT) atomicAdd(&s_cnt[__ldg(cl + i) >> bshift], 1u);
+  __syncthreads();
+  // exclusive scan of the counts: each thread a contiguous run of ranges
+  const int per = (nbk + BKT - 1) / BKT;
+  const int b0 = threadIdx.x * per;
+  uint32_t run = 0;
+  for (int b = b0; b < min(nbk, b0 + per); ++b) run += s_cnt[b];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[w] = x;
+  __syncthreads();
+  uint32_t before = x - run;
+  for (int i = 0; i < w; ++i) before += s_w[i];
+  for (int b = b0; b < min(nbk, b0 + per); ++b) {
+    s_off[b] = before;
+    boffq[qb * nbk + b] = before;
+    bcnt[(int64_t)b * nqg + qb] = s_cnt[b];
+    before += s_cnt[b];
+  }
+  __syncthreads();
+  uint2* pl = pairs + qb * cap;
+  for (int64_t i = threadIdx.x; i < ns; i += BKT) {
+    const uint32_t id = __ldg(cl + i);
+    const uint32_t p = atomicAdd(&s_off[id >> bshift], 1u);
+    pl[p] = make_uint2(id, (uint32_t)i);
+  }
+}
+
+// distance work items per (range, query) cell
+__global__ void k_cell_items(const uint32_t* __restrict__ bcnt, int64_t cells, int rows, uint32_t* __restrict__ icnt) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < cells) icnt[c] = (bcnt[c] + rows - 1) / rows;
+}
+
+// the items of each cell at its place in range-major order
+__global__ void k_cell_fill(const uint32_t* __restrict__ bcnt, const uint32_t* __restrict__ ioff,
+                            const uint32_t* __restrict__ boffq, int nbk, int64_t nqg, int rows,
+                            uint4* __restrict__ items) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= (int64_t)nbk * nqg) return;
+  const int64_t b = c / nqg, qb = c - b * nqg;
+  const uint32_t cnt = bcnt[c], r0 = boffq[qb * nbk + b];
+  for (uint32_t t = 0; t * (uint32_t)rows < cnt; ++t)
+    items[ioff[c] + t] = make_uint4((uint32_t)qb, r0 + t * rows, r0 + min(cnt, (t + 1) * (uint32_t)rows), 0u);
 }
 
 // k_dist_u8 applies: uint8 rows and queries 16-byte aligned, d in {16, ..., 512}.
@@ -1324,10 +1408,12 @@ __device__ __forceinline__ float transpose_reduce8_half(const float* acc, int la
   return v;
 }
 
+template <bool BK>
 __global__ void __launch_bounds__(DT, 3)
 k_dist_bf16(const __nv_bfloat16* __restrict__ Xb, int d, const float* __restrict__ Qf, int64_t q0,
-            const uint32_t* __restrict__ cand, int64_t cap, const uint4* __restrict__ items,
-            const uint32_t* __restrict__ qtail, uint32_t* __restrict__ head, float* __restrict__ d2out) {
+            const uint32_t* __restrict__ cand, const uint2* __restrict__ pairs, int64_t cap,
+            const uint4* __restrict__ items, const uint32_t* __restrict__ qtail, uint32_t* __restrict__ head,
+            float* __restrict__ d2out) {
   const uint32_t nit = *qtail;
   const int lane = threadIdx.x & 31, h = lane >> 4;
   uint32_t it = next_item(head, lane);
@@ -1338,6 +1424,7 @@ k_dist_bf16(const __nv_bfloat16* __restrict__ Xb, int d, const float* __restrict
     const int64_t r0 = item.y, r1 = item.z;
     const float* q = Qf + (q0 + qb) * (int64_t)d;
     const uint32_t* cl = cand + qb * cap;
+    const uint2* pl = BK ? pairs + qb * cap : nullptr;
     float* out = d2out + qb * cap;
     // warp step: 2*ILP rows, rows e0 + h*ILP + u of half-warp h
     for (int64_t e0 = r0; e0 < r1; e0 += 2 * ILP) {
@@ -1346,13 +1433,13 @@ k_dist_bf16(const __nv_bfloat16* __restrict__ Xb, int d, const float* __restrict
 #pragma unroll
       for (int u = 0; u < ILP; ++u) {
         const int64_t e = e0 + h * ILP + u;
-        ids[u] = (e < r1) ? __ldg(cl + e) : 0xffffffffu;
+        ids[u] = (e < r1) ? (BK ? __ldg(&pl[e].x) : __ldg(cl + e)) : 0xffffffffu;
         acc[u] = 0.f;
       }
       rows_dist2_bf16(Xb, d, ids, q, lane & 15, acc);
       const float v = transpose_reduce8_half(acc, lane);
       const int64_t e = e0 + (lane >> 1);   // = e0 + h*ILP + ((lane >> 1) & 7)
-      if ((lane & 1) == 0 && e < r1) out[e] = v;
+      if ((lane & 1) == 0 && e < r1) out[BK ? (int64_t)__ldg(&pl[e].y) : e] = v;
     }
     it = nx;
   }
@@ -1736,6 +1823,9 @@ int tuning_from_params(const detlsh_query_params* qp, QueryTuning* tu) {
   tu->streams = t.streams;
   DL_REQUIRE(t.coarse_gather == 0 || t.coarse_gather == 1, "tuning.coarse_gather must be 0 or 1");
   tu->coarse_gather = t.coarse_gather;
+  DL_REQUIRE(t.id_bucket_log2 == 0 || t.id_bucket_log2 == -1 || (t.id_bucket_log2 >= 10 && t.id_bucket_log2 <= 31),
+             "tuning.id_bucket_log2 must be 0, -1 or in [10, 31]");
+  tu->id_bucket_log2 = t.id_bucket_log2;
   return DETLSH_OK;
 }
 
@@ -1815,7 +1905,25 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   const double tmax = std::ceil(beta * (double)idx->n + (double)k_max);
   sh.cap = std::max<int64_t>(
       1, std::min<int64_t>(idx->n, (int64_t)std::min(tmax, 9.0e18) - 1 + idx->max_leaf_count));
-  sh.items_per_q = (sh.cap + sh.dist_rows - 1) / sh.dist_rows;
+  // gather by point-id range: ranges of about 32 MB of rows (the gather's row
+  // bytes; measured best among 2 to 64 MB on the mid workload), at most
+  // kMaxIdBuckets of them, only with more than one
+  if (tu.id_bucket_log2 >= 0) {
+    const int64_t row_bytes =
+        shortlist > 0 ? (int64_t)idx->d * 2 : (int64_t)idx->d * (idx->dtype == DETLSH_U8 ? 1 : 4);
+    int bs = tu.id_bucket_log2;
+    if (bs == 0) {
+      bs = 10;
+      while (bs < 31 && ((int64_t)2 << bs) * row_bytes <= ((int64_t)32 << 20)) ++bs;
+    }
+    while (bs < 31 && ((idx->n - 1) >> bs) + 1 > kMaxIdBuckets) ++bs;
+    const int64_t nbk = ((idx->n - 1) >> bs) + 1;
+    if (nbk > 1) {
+      sh.bshift = bs;
+      sh.nbk = nbk;
+    }
+  }
+  sh.items_per_q = (sh.cap + sh.dist_rows - 1) / sh.dist_rows + sh.nbk;
   // shortlist mode: coarse distances by leaf on the tensor cores (each record
   // holds at least one new point, so a query writes at most cap of them)
   sh.lm = shortlist > 0 && idx->chunk_base != nullptr && tu.coarse_gather == 0;
@@ -1826,7 +1934,8 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   const int64_t per_q = sh.TL * 9 + sh.cap * 8 + sh.RL * 16 + kRoundCap * 12 + MQ_WORDS * 4 +
                         sh.LK * 4 + sh.items_per_q * 16 + ((sh.TL + 16383) / 16384) * sh.RL * 4 +
                         (idx->Xb ? (int64_t)idx->d * 2 : 0) + (shortlist > 0 ? (int64_t)idx->d * 4 : 0) +
-                        (sh.lm ? sh.cap * (16 + 16 + 4) + sh.cap / 8 + 4 : 0) + 64;
+                        (sh.lm ? sh.cap * (16 + 16 + 4) + sh.cap / 8 + 4 : 0) +
+                        (!sh.lm && sh.nbk ? sh.cap * 8 + sh.nbk * 16 : 0) + 64;
   int64_t B = tu.batch;
   if (B == 0) {
     size_t mem_free = 0, mem_total = 0;
@@ -1874,6 +1983,20 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   sh.o_qk = take(sizeof(uint32_t) * 4 * B);
   sh.qsort_bytes = radix_ws_bytes(B, 0, 32);
   sh.o_qsort = take(sh.qsort_bytes);
+  if (sh.lm) {
+    sh.nbk = 0;   // the leaf-major coarse distances take no items
+    sh.bshift = 0;
+  }
+  if (sh.nbk) {
+    const int64_t cells = sh.nbk * B;
+    sh.o_pairs = take(sizeof(uint2) * B * sh.cap);
+    sh.o_bcnt = take(sizeof(uint32_t) * cells);
+    sh.o_boffq = take(sizeof(uint32_t) * cells);
+    sh.o_icnt = take(sizeof(uint32_t) * cells);
+    sh.o_ioff = take(sizeof(uint32_t) * (cells + 1));
+    sh.bscan_bytes = scan_ws_bytes(cells);
+    sh.o_bscan = take(sh.bscan_bytes);
+  }
   if (sh.lm) {
     sh.max_units = sh.nk + (B * sh.cap) / 128 + 1;
     sh.o_rec = take(sizeof(uint4) * B * sh.cap);
@@ -2047,6 +2170,7 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   wa.qtail = ctr + CT_QTAIL;
   wa.dist_rows = sh.dist_rows;
   wa.rec = sh.lm ? reinterpret_cast<uint4*>(b + sh.o_rec) : nullptr;
+  wa.queue_items = sh.nbk ? 0 : 1;
   tm.begin(TR_WALK);
   if (idx->leaf_pos)
     k_walk<true><<<(unsigned)std::min<int64_t>(nqg, sh.wgrid), WT, sh.wl_total, s>>>(wa);
@@ -2056,6 +2180,24 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   tm.end();
 
   tm.begin(TR_DIST);
+  const uint2* pairs = sh.nbk ? reinterpret_cast<const uint2*>(b + sh.o_pairs) : nullptr;
+  if (sh.nbk && nqg > 0) {
+    // the distance work by point-id range: per query its candidates grouped by
+    // range, then the items of every (range, query) cell, range-major
+    uint32_t* bcnt = reinterpret_cast<uint32_t*>(b + sh.o_bcnt);
+    uint32_t* boffq = reinterpret_cast<uint32_t*>(b + sh.o_boffq);
+    uint32_t* icnt = reinterpret_cast<uint32_t*>(b + sh.o_icnt);
+    uint32_t* ioff = reinterpret_cast<uint32_t*>(b + sh.o_ioff);
+    const int64_t cells = sh.nbk * nqg;
+    k_cand_buckets<<<(unsigned)nqg, BKT, 0, s>>>(candb, sh.cap, meta, nqd, sh.bshift, (int)sh.nbk, nqg,
+                                                 reinterpret_cast<uint2*>(b + sh.o_pairs), bcnt, boffq);
+    DL_LAUNCH();
+    k_cell_items<<<ceil_div(cells, 256), 256, 0, s>>>(bcnt, cells, sh.dist_rows, icnt);
+    DL_LAUNCH();
+    DL_TRY(exclusive_scan_u32_ws(icnt, ioff, cells, ctr + CT_QTAIL, b + sh.o_bscan, sh.bscan_bytes, s));
+    k_cell_fill<<<ceil_div(cells, 256), 256, 0, s>>>(bcnt, ioff, boffq, (int)sh.nbk, nqg, sh.dist_rows, items);
+    DL_LAUNCH();
+  }
   if (sh.lm) {
     LmBatch lb{};
     lb.qb16 = b + sh.o_qb16;
@@ -2080,21 +2222,23 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
     lb.scan_ws_bytes = sh.scanws_bytes;
     lb.d2 = d2b;
     DL_TRY(enqueue_coarse_lm(idx, lb, s));
-  } else if (sh.shortlist > 0)
-    k_dist_bf16<<<sh.dgrid, DT, 0, s>>>(static_cast<const __nv_bfloat16*>(idx->Xb), idx->d, qf, 0, candb,
-                                         sh.cap, items, ctr + CT_QTAIL, ctr + CT_HEAD, d2b);
-  else if (dist_u8_eligible(idx, Q))
-    k_dist_u8<<<sh.dgrid, DT, 0, s>>>(static_cast<const uint8_t*>(idx->X), idx->d,
-                                      static_cast<const uint8_t*>(Q), q0, candb, sh.cap, items,
-                                      ctr + CT_QTAIL, ctr + CT_HEAD, d2b);
-  else if (idx->dtype == DETLSH_U8)
-    k_dist<uint8_t><<<sh.dgrid, DT, 0, s>>>(static_cast<const uint8_t*>(idx->X), idx->d,
-                                             static_cast<const uint8_t*>(Q), q0, candb, sh.cap, items,
-                                             ctr + CT_QTAIL, ctr + CT_HEAD, d2b, vec4);
-  else
-    k_dist<float><<<sh.dgrid, DT, 0, s>>>(static_cast<const float*>(idx->X), idx->d,
-                                           static_cast<const float*>(Q), q0, candb, sh.cap, items,
-                                           ctr + CT_QTAIL, ctr + CT_HEAD, d2b, vec4);
+  } else if (sh.shortlist > 0) {
+    (pairs ? k_dist_bf16<true> : k_dist_bf16<false>)<<<sh.dgrid, DT, 0, s>>>(
+        static_cast<const __nv_bfloat16*>(idx->Xb), idx->d, qf, 0, candb, pairs, sh.cap, items, ctr + CT_QTAIL,
+        ctr + CT_HEAD, d2b);
+  } else if (dist_u8_eligible(idx, Q)) {
+    (pairs ? k_dist_u8<true> : k_dist_u8<false>)<<<sh.dgrid, DT, 0, s>>>(
+        static_cast<const uint8_t*>(idx->X), idx->d, static_cast<const uint8_t*>(Q), q0, candb, pairs, sh.cap,
+        items, ctr + CT_QTAIL, ctr + CT_HEAD, d2b);
+  } else if (idx->dtype == DETLSH_U8) {
+    (pairs ? k_dist<uint8_t, true> : k_dist<uint8_t, false>)<<<sh.dgrid, DT, 0, s>>>(
+        static_cast<const uint8_t*>(idx->X), idx->d, static_cast<const uint8_t*>(Q), q0, candb, pairs, sh.cap,
+        items, ctr + CT_QTAIL, ctr + CT_HEAD, d2b, vec4);
+  } else {
+    (pairs ? k_dist<float, true> : k_dist<float, false>)<<<sh.dgrid, DT, 0, s>>>(
+        static_cast<const float*>(idx->X), idx->d, static_cast<const float*>(Q), q0, candb, pairs, sh.cap, items,
+        ctr + CT_QTAIL, ctr + CT_HEAD, d2b, vec4);
+  }
   DL_LAUNCH();
   tm.end();
   trace_add(TR_DIST_LAUNCHES, timed ? 1.0 : 0.0);
