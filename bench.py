@@ -160,6 +160,24 @@ def roofline_obj(kernel, algo_bytes_per_launch, avg_launch_ms, launches, traffic
     return out
 
 
+def tensor_roofline_obj(kernel, flops_per_launch, avg_launch_ms, launches, source=None):
+    """A contraction on the tensor cores against the measured dense BF16 rate
+    (the sustained figure: the kernel runs inside a long step)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, kind = float(json.load(f)["bf16_tflops_sustained"]), "measured (sustained)"
+    except Exception:
+        peak, kind = 1700.0, "fallback (sustained)"
+    achieved = flops_per_launch / (avg_launch_ms / 1000.0) / 1e12
+    out = {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": achieved / peak, "peak_kind": kind, "traffic": None,
+           "algorithmic_flops_per_launch": flops_per_launch, "launches_per_step": launches,
+           "avg_launch_ms": avg_launch_ms}
+    if source:
+        out["source"] = source
+    return out
+
+
 def build_roofline_obj(n, bytes_per_point, build_ms, phases=None):
     peak, peak_kind = _peaks()
     achieved = n * bytes_per_point / (build_ms / 1000.0) / 1e9
@@ -751,10 +769,17 @@ def precision_leg(args, rank, world, local_rank, barrier, steps, warmup):
         g32 = out[1][sel].reshape(-1).double()
         rel = ((g32 - d64).abs() / d64.clamp_min(1e-30))
         n_cand = float(out[2][:, 0].double().sum())
-        kern = "k_dist_bf16" if shortlist else "k_dist"
-        dbytes = (2 * d if shortlist else 4 * d) + 8
-        roof = roofline_obj(kern, n_cand * dbytes / ph["dist_launches"], ph["dist_ms"] / ph["dist_launches"],
-                            ph["dist_launches"], source="CUDA events around the kernel in a traced step")
+        if shortlist:
+            # the coarse distances by leaf on the tensor cores: the algorithmic
+            # work is one d-long dot product (2d flops) per coarse candidate
+            roof = tensor_roofline_obj(
+                "k_dist_lm (BF16 tcgen05, by leaf chunk)", n_cand * 2.0 * d / ph["dist_launches"],
+                ph["dist_ms"] / ph["dist_launches"], ph["dist_launches"],
+                source="CUDA events around the coarse-distance stage (record sort + kernel) in a traced step")
+        else:
+            roof = roofline_obj("k_dist", n_cand * (4 * d + 8) / ph["dist_launches"],
+                                ph["dist_ms"] / ph["dist_launches"], ph["dist_launches"],
+                                source="CUDA events around the kernel in a traced step")
         bpp = build_bytes_per_point(d, 2 if proj_mode else 4, w["K"], w["L"])
         return {"qps": job_throughput(nq, world, ms / 1000.0), "ms_per_step": ms, "recall_at_100": rec,
                 "dist_rel_err_max": float(rel.max()), "dist_rel_err_mean": float(rel.mean()),

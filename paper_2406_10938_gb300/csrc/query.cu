@@ -1089,12 +1089,16 @@ __device__ __forceinline__ void rows_dist2(const TX* __restrict__ X, int d,
   using V = Vec4Of<TX>;
   if (vec4) {
     const int d4 = d >> 2;
+    // a missing row (id ~0) reads row 0 and its sum is not used: the loads
+    // need no branch
+    const TX* xr[ILP];
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) xr[u] = X + (int64_t)(ids[u] != 0xffffffffu ? ids[u] : 0u) * d;
     for (int i = lane; i < d4; i += 32) {
       const typename V::T qv = V::ld(q, i);
       typename V::T xv[ILP];
 #pragma unroll
-      for (int u = 0; u < ILP; ++u)
-        xv[u] = (ids[u] != 0xffffffffu) ? V::ld(X + (int64_t)ids[u] * d, i) : qv;
+      for (int u = 0; u < ILP; ++u) xv[u] = V::ld(xr[u], i);
       const float4 qf = V::f(qv);
 #pragma unroll
       for (int u = 0; u < ILP; ++u) {
