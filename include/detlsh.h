@@ -123,8 +123,11 @@ typedef struct {
                                 same time lie in a few MB of X and stay in L2
                                 (the points are candidates of many queries of a
                                 batch). 0: x chosen for ranges of about 32 MB of
-                                points; 10..31: that x; -1: walk order (no
-                                grouping). The distances are the same either way */
+                                points, and the walk order kept where a point is
+                                expected among fewer than 16 queries' candidates
+                                (beta times the batch size); 10..31: that x;
+                                -1: walk order (no grouping). The distances are
+                                the same either way                               */
 } detlsh_tuning;
 
 /* Query parameters shared by a batch (Alg. 7 inputs besides q, k, c, r_min). */

@@ -1950,6 +1950,15 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   }
   B = std::max<int64_t>(1, std::min<int64_t>(B, std::max<int64_t>(nq, 1)));
   sh.B = B;
+  // the grouping pays when a row is a candidate of many queries of a batch
+  // (about beta*B of them); with few (small batches, small beta: the serving
+  // shapes) its own passes cost more than the reuse saves, so the automatic
+  // setting keeps the walk order below beta*B = 16
+  if (sh.nbk && tu.id_bucket_log2 == 0 && beta * (double)B < 16.0) {
+    sh.nbk = 0;
+    sh.bshift = 0;
+    sh.items_per_q = (sh.cap + sh.dist_rows - 1) / sh.dist_rows;
+  }
   sh.wgrid = (int)std::min<int64_t>(B, (int64_t)nsm * walk_per_sm);
   int64_t max_tree_leaves = 1;
   for (int t = 0; t < sh.L; ++t)
