@@ -100,7 +100,8 @@ typedef struct {
   int32_t walk_ctas_per_sm;  /* bucket-walk CTAs per SM, 1..4 (0: as many as fit)  */
   int32_t dist_rows;         /* candidate rows per distance work item, a multiple
                                 of 64 in [64, 8192] (0: 1024)                     */
-  int32_t dist_ctas_per_sm;  /* persistent distance CTAs per SM, 1..3 (0: 3)       */
+  int32_t dist_ctas_per_sm;  /* persistent distance CTAs per SM, 1..4 (0: 4; 3 for
+                                the BF16 gather of the shortlist mode)            */
   int32_t shortlist;         /* detlsh_autotune's pick for
                                 detlsh_query_params.shortlist; the query ignores
                                 this field                                        */

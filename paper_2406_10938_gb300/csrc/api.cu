@@ -697,7 +697,7 @@ int detlsh_autotune(const detlsh_index* idx, const void* Q, int64_t nq, int32_t 
     t.dist_rows = rows;
     attempt(t);
   }
-  for (int dc3 : {1, 2, 3}) {
+  for (int dc3 : {1, 2, 3, 4}) {
     QueryTuning t = best;
     t.dist_ctas_per_sm = dc3;
     attempt(t);

@@ -378,7 +378,7 @@ struct QueryTuning {
   int64_t batch = 0;         // queries per batch; 0: sized from free device memory
   int walk_ctas_per_sm = 0;  // walk CTAs per SM, 1..3; 0: as many as fit
   int dist_rows = 1024;      // candidate rows per distance work item (multiple of 64)
-  int dist_ctas_per_sm = 0;  // persistent distance CTAs per SM, 1..3; 0: 3
+  int dist_ctas_per_sm = 0;  // persistent distance CTAs per SM, 1..4; 0: 4 (3 for the BF16 gather)
   int streams = 0;           // 2: batches alternate between two streams; 0 or 1: one stream
   int coarse_gather = 0;     // shortlist mode: 1 gathers each candidate's row (no leaf-major tensor cores)
   int id_bucket_log2 = 0;    // gather by point-id range of 2^x rows; 0: automatic; -1: in walk order

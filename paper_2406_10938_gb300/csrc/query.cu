@@ -1165,7 +1165,7 @@ __device__ __forceinline__ uint32_t next_item(uint32_t* head, int lane) {
 // BK: the items address the query's candidates grouped by point-id range,
 // (point id, list position) pairs; the distance goes to the list position.
 template <typename TX, bool BK>
-__global__ void __launch_bounds__(DT, 3)
+__global__ void __launch_bounds__(DT, 4)
 k_dist(const TX* __restrict__ X, int d, const TX* __restrict__ Q, int64_t q0,
        const uint32_t* __restrict__ cand, const uint2* __restrict__ pairs, int64_t cap,
        const uint4* __restrict__ items, const uint32_t* __restrict__ qtail, uint32_t* __restrict__ head,
@@ -1205,7 +1205,7 @@ k_dist(const TX* __restrict__ X, int d, const TX* __restrict__ Q, int64_t q0,
 // sum x^2 - 2 sum x q + sum q^2 in 32-bit integers (dp4a), exact whatever the
 // order of the sums (at most 512 * 255^2 < 2^31), converted to FP32 once.
 template <bool BK>
-__global__ void __launch_bounds__(DT, 3)
+__global__ void __launch_bounds__(DT, 4)
 k_dist_u8(const uint8_t* __restrict__ X, int d, const uint8_t* __restrict__ Q, int64_t q0,
           const uint32_t* __restrict__ cand, const uint2* __restrict__ pairs, int64_t cap,
           const uint4* __restrict__ items, const uint32_t* __restrict__ qtail, uint32_t* __restrict__ head,
@@ -1846,8 +1846,8 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
     return DETLSH_EINVAL;
   }
   if (tu.walk_ctas_per_sm < 0 || tu.walk_ctas_per_sm > 4 || tu.dist_ctas_per_sm < 0 ||
-      tu.dist_ctas_per_sm > 3 || tu.batch < 0 || tu.streams < 0 || tu.streams > 2) {
-    set_error("walk_ctas_per_sm must be in [0, 4], dist_ctas_per_sm in [0, 3], streams in [0, 2], batch >= 0");
+      tu.dist_ctas_per_sm > 4 || tu.batch < 0 || tu.streams < 0 || tu.streams > 2) {
+    set_error("walk_ctas_per_sm must be in [0, 4], dist_ctas_per_sm in [0, 4], streams in [0, 2], batch >= 0");
     return DETLSH_EINVAL;
   }
   sh.L = idx->L;
@@ -1883,7 +1883,8 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   DL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&walk_per_sm, k_walk<false>, WT, wl.total));
   walk_per_sm = std::max(walk_per_sm, 1);
   if (tu.walk_ctas_per_sm > 0) walk_per_sm = std::min(walk_per_sm, tu.walk_ctas_per_sm);
-  sh.dgrid = nsm * (tu.dist_ctas_per_sm ? tu.dist_ctas_per_sm : 3);
+  // the FP32 and uint8 gathers fit four CTAs per SM, the BF16 one three
+  sh.dgrid = nsm * (tu.dist_ctas_per_sm ? tu.dist_ctas_per_sm : (shortlist > 0 ? 3 : 4));
   sh.nsm = nsm;
   // split bucketing: per-CTA histograms over (round, tree)
   sh.rq = 1;

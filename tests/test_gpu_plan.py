@@ -115,6 +115,7 @@ def test_plan_flags_bad_device_argument_and_recovers():
     {"batch": 7, "walk_ctas_per_sm": 2, "dist_rows": 128},
     {"batch": 9, "streams": 2},
     {"batch": 9, "streams": 1, "dist_ctas_per_sm": 3},
+    {"dist_ctas_per_sm": 4, "id_bucket_log2": 12},
 ])
 def test_tuning_does_not_change_results(tuning):
     X, Q, A, ids, ks, cs, idx = _case("mid", n=20_000, d=128, Nr=256, n_s=2_000, max_leaf=64, nq=40, k=50)
@@ -130,7 +131,7 @@ def test_tuning_does_not_change_results(tuning):
 
 def test_tuning_rejects_bad_shapes():
     X, Q, A, ids, ks, cs, idx = _case(nq=4)
-    for bad in ({"dist_rows": 100}, {"dist_ctas_per_sm": 4}, {"walk_ctas_per_sm": 9}, {"batch": -1},
+    for bad in ({"dist_rows": 100}, {"dist_ctas_per_sm": 5}, {"walk_ctas_per_sm": 9}, {"batch": -1},
                 {"streams": 3}):
         with pytest.raises(pkg.DetlshError):
             pkg.detlsh_query(idx, Q.to(DEV), ks.to(DEV), cs.to(DEV), 0.0, k_max=10, tuning=bad)
@@ -142,7 +143,7 @@ def test_autotune_fp32_index():
     t = pkg.detlsh_autotune(idx, Q.to(DEV), ks.to(DEV), cs.to(DEV), 0.0, k_max=50, beta=0.1, min_agreement=0.99)
     assert t["walk_ctas_per_sm"] in (0, 1, 2, 3, 4)
     assert t["dist_rows"] % 64 == 0 and 64 <= t["dist_rows"] <= 8192
-    assert t["dist_ctas_per_sm"] in (0, 1, 2, 3)
+    assert t["dist_ctas_per_sm"] in (0, 1, 2, 3, 4)
     assert t["streams"] in (0, 1, 2)
     assert t["batch"] in (0, 1024, 2048, 4096, 8192, 16384)
     assert t["shortlist"] == 0                         # no BF16 copy to re-rank from
