@@ -386,7 +386,7 @@ struct QueryTuning {
 
 // Sizes and scratch layout (byte offsets into one device block) of a batch.
 struct QueryShape {
-  int64_t B, cap, TL, RL, words, max_tree_leaves, items_per_q, bsplit;
+  int64_t B, cap, TL, RL, words, max_tree_leaves, items_per_q, nblk;
   int64_t nsm = 0;   // SMs of the device
   int LK, L, wgrid, dgrid, dist_rows, tkc, k_max, shortlist, rq;
   bool smem_bitmap;
@@ -398,9 +398,9 @@ struct QueryShape {
   size_t o_pairs = 0, o_bcnt = 0, o_boffq = 0, o_icnt = 0, o_ioff = 0, o_bscan = 0, bscan_bytes = 0;
   size_t o_rec = 0, o_srec = 0, o_sq = 0, o_qn = 0, o_khist = 0, o_kcur = 0, o_koff = 0, o_ucnt = 0, o_uoff = 0,
          o_units = 0, o_scanws = 0, scanws_bytes = 0;
-  size_t wl_total, bk_smem, bp_smem, bytes;
+  size_t wl_total, bk_smem, bytes;
   size_t o_ctr, o_qp, o_qb16, o_qf, o_lb, o_mm, o_lround, o_hist, o_boff, o_list, o_cand, o_d2,
-      o_rend, o_thr, o_meta, o_wsnew, o_wsbm, o_wspos, o_items, o_qk, o_qsort, qsort_bytes, o_hcnt, o_hcta;
+      o_rend, o_thr, o_meta, o_wsnew, o_wsbm, o_wspos, o_items, o_qk, o_qsort, qsort_bytes, o_blkmin, o_blist;
 };
 
 // control words of a batch (uint32, at QueryShape::o_ctr): queries in the

@@ -5,13 +5,16 @@
 //               (query, leaf) pair. One thread owns one leaf and keeps its box
 //               edges in registers while it loops over a chunk of queries whose
 //               projections sit in shared memory; it also folds each query's
-//               smallest positive and largest bound into two per-query words.
+//               smallest positive and largest bound into two per-query words,
+//               and records the smallest bound of every block of 32 leaves.
 // k_thresh    -- per query, the FP64 round table r_0, c*r_0, ... (Alg. 7).
-// k_round_hist, k_bucket_plan, k_bucket_scatter
-//             -- each leaf gets the first round t whose projected threshold
-//               (eps*r_t)^2 covers its lower bound; leaves are bucketed by
-//               (round, tree), up to the first round in which some tree alone
-//               holds beta*n+k points.
+// k_round_expand
+//             -- one CTA per query: each leaf gets the first round t whose
+//               projected threshold (eps*r_t)^2 covers its lower bound, and the
+//               leaves of the rounds up to the first one in which some tree
+//               alone holds beta*n+k points go to (round, tree) bucket lists;
+//               leaf blocks are expanded in the order of their smallest bound's
+//               round and only until that round is known.
 // k_walk      -- one CTA per query: the buckets in Alg. 7's order. A bucket
 //               that cannot bring |S| to beta*n+k is taken whole (order inside
 //               it does not change S); the one that can is cut at the first
@@ -80,7 +83,8 @@ __global__ void __launch_bounds__(LB_THREADS)
 k_leaf_lb(const float* __restrict__ qp, const uint32_t* __restrict__ nqd, int LK, const float* __restrict__ E, int Nr,
           int K, const uint8_t* __restrict__ leaf_lo, const uint8_t* __restrict__ leaf_hi,
           const uint16_t* __restrict__ leaf_tree, int64_t total_leaves, float* __restrict__ lb2,
-          uint32_t* __restrict__ minpos, uint32_t* __restrict__ maxlb) {
+          uint32_t* __restrict__ minpos, uint32_t* __restrict__ maxlb, uint32_t* __restrict__ blkmin,
+          int64_t nblk) {
   // q' rows of the CTA's queries, LKP = L*K rounded up to even, + 2 floats
   // apart (every row starts 8-byte aligned)
   extern __shared__ __align__(16) float s_qrows[];
@@ -155,6 +159,9 @@ k_leaf_lb(const float* __restrict__ qp, const uint32_t* __restrict__ nqd, int LK
     // non-negative floats order like their bit patterns
     uint32_t mn = (valid && acc > 0.f) ? __float_as_uint(acc) : 0xffffffffu;
     uint32_t mx = valid ? __float_as_uint(acc) : 0u;
+    // the smallest bound of the warp's 32 leaves (a lower-bound block)
+    const uint32_t mb = __reduce_min_sync(0xffffffffu, valid ? __float_as_uint(acc) : 0x7f800000u);
+    if ((threadIdx.x & 31) == 0 && (leaf >> 5) < nblk) blkmin[(qb0 + q) * nblk + (leaf >> 5)] = mb;
     mn = __reduce_min_sync(0xffffffffu, mn);
     mx = __reduce_max_sync(0xffffffffu, mx);
     if ((threadIdx.x & 31) == 0) {
@@ -254,187 +261,169 @@ __global__ void k_thresh(const uint32_t* __restrict__ minpos, const uint32_t* __
   m[MQ_TLAST] = 0;
 }
 
-// ------------------------------------------------------------------ buckets
-constexpr int BT = 256;
+// ------------------------------------------------------------------ rounds and buckets
+// Every leaf joins in the first round t whose projected threshold (eps*r_t)^2
+// covers its lower bound; the walk needs, per (round, tree), the leaves and
+// points of the rounds up to the first one in which some tree alone holds
+// T = beta*n + k points (tcap), and the leaves of those rounds in bucket lists.
+// Leaves of later rounds are never needed. k_leaf_lb records the smallest
+// lower bound of every block of 32 consecutive leaves; a leaf's round is at
+// least its block's, so after the blocks of rounds 0..t have been expanded
+// (their leaves' rounds computed exactly) the per-(round, tree) counts of
+// rounds 0..t are complete. One CTA per query expands the blocks round by
+// round and stops at tcap: only the blocks whose smallest bound is covered by
+// the tcap threshold are read leaf by leaf.
+constexpr int RX = 512;                 // threads of the per-query round kernel
+constexpr int kLbBlock = 32;            // leaves per lower-bound block (one warp of k_leaf_lb)
 
-// ------------------------------------------------------------------ buckets, split
-// Every leaf gets the first round t with (eps*r_t)^2 >= its lower bound; the
-// last reachable round is the first one in which some tree alone holds T
-// points; the leaves of rounds up to it go to their (round, tree) bucket
-// lists. Several CTAs per query, each over a contiguous range of the leaves:
-// (1) every leaf's
-// round, counted per (round, tree) in
-// shared memory and added to the query's histograms (one global atomic per
-// bucket and CTA); (2) per query, the last reachable round and the bucket
-// offsets; (3) each CTA counts its leaves per bucket, reserves their places
-// with one global atomic per bucket, and scatters them (order inside a bucket
-// is free).
-
-__global__ void __launch_bounds__(BT)
-k_round_hist(const float* __restrict__ lb2, int64_t total_leaves, int64_t lpc, const float* __restrict__ thrP,
-             const uint16_t* __restrict__ leaf_tree, const uint32_t* __restrict__ leaf_range, int L,
-             const uint32_t* __restrict__ nqd, uint8_t* __restrict__ lround, uint32_t* __restrict__ hcnt,
-             uint32_t* __restrict__ hpts, uint32_t* __restrict__ hcta, uint32_t* __restrict__ meta) {
-  extern __shared__ __align__(16) unsigned char smr[];
-  const int RL = kRoundCap * L;
-  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smr);   // [RL]
-  uint32_t* s_pts = s_cnt + RL;                          // [RL]
-  float* s_thr = reinterpret_cast<float*>(s_pts + RL);  // [kRoundCap]
-  __shared__ uint32_t s_tl;
-  const int64_t qb = blockIdx.y;
-  if (qb >= (int64_t)*nqd) return;
-  const int Ru = (int)meta[qb * MQ_WORDS + MQ_RU];
-  const int lane = threadIdx.x & 31;
-  const uint32_t lt = (1u << lane) - 1u;
-  for (int i = threadIdx.x; i < Ru * L; i += BT) {
-    s_cnt[i] = 0;
-    s_pts[i] = 0;
-  }
-  for (int i = threadIdx.x; i < Ru; i += BT) s_thr[i] = thrP[qb * kRoundCap + i];
-  if (threadIdx.x == 0) s_tl = 0;
-  __syncthreads();
-  const int64_t la = (int64_t)blockIdx.x * lpc;
-  const int64_t lb_end = min(total_leaves, la + lpc);
-  const float* lbrow = lb2 + qb * total_leaves;
-  uint8_t* lr = lround + qb * total_leaves;
-  constexpr int BU = 4;
-  uint32_t tl = 0;
-  for (int64_t l0 = la + threadIdx.x; l0 < la + (lb_end - la + BT * BU - 1) / (BT * BU) * (BT * BU); l0 += BT * BU) {
-    float lbv[BU];
-    uint32_t tr[BU], pc[BU];
-#pragma unroll
-    for (int u = 0; u < BU; ++u) {
-      const int64_t l = l0 + (int64_t)u * BT;
-      if (l < lb_end) {
-        lbv[u] = lbrow[l];
-        tr[u] = leaf_tree[l];
-        pc[u] = leaf_range[2 * l + 1];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < BU; ++u) {
-      const int64_t l = l0 + (int64_t)u * BT;
-      const bool valid = l < lb_end;
-      uint32_t key = 0xffffffffu, pts = 0;
-      if (valid) {
-        const uint32_t t = (uint32_t)lower_bound_f(s_thr, Ru, lbv[u]);
-        lr[l] = (uint8_t)t;
-        key = t * (uint32_t)L + tr[u];
-        pts = pc[u];
-        tl = max(tl, t);
-      }
-      const uint32_t peers = __match_any_sync(0xffffffffu, key);
-      const uint32_t sum = __reduce_add_sync(peers, pts);
-      if (valid && (peers & lt) == 0) {
-        atomicAdd(&s_cnt[key], (uint32_t)__popc(peers));
-        atomicAdd(&s_pts[key], sum);
-      }
-    }
-  }
-  tl = __reduce_max_sync(0xffffffffu, tl);
-  if (lane == 0) atomicMax(&s_tl, tl);
-  __syncthreads();
-  uint32_t* hc = hcta + (qb * gridDim.x + blockIdx.x) * RL;   // this CTA's counts per bucket
-  for (int i = threadIdx.x; i < Ru * L; i += BT) {
-    const uint32_t c = s_cnt[i];
-    hc[i] = c;
-    if (c) {
-      atomicAdd(&hcnt[qb * RL + i], c);
-      atomicAdd(&hpts[qb * RL + i], s_pts[i]);
-    }
-  }
-  if (threadIdx.x == 0) atomicMax(&meta[qb * MQ_WORDS + MQ_TLAST], s_tl);
+size_t round_smem_bytes(int L) {
+  return sizeof(uint32_t) * (3 * (size_t)kRoundCap + 2 + 4 * (size_t)kRoundCap * L + 1);
 }
 
-// Per query: the last reachable round (the first one in which some tree alone
-// holds T points), bucket offsets, and the count array zeroed into cursors.
-__global__ void __launch_bounds__(BT)
-k_bucket_plan(int L, int nsplit, const uint32_t* __restrict__ nqd, uint32_t* __restrict__ hcnt,
-              const uint32_t* __restrict__ hpts, uint32_t* __restrict__ hcta, uint32_t* __restrict__ boff,
-              uint32_t* __restrict__ meta) {
-  extern __shared__ __align__(16) unsigned char smp[];
+// warp-aggregated shared-memory adds of (1, w) at key (~0: nothing)
+__device__ __forceinline__ void add_key(uint32_t* cnt, uint32_t* wsum, uint32_t key, uint32_t w, int lane) {
+  const uint32_t peers = __match_any_sync(0xffffffffu, key);
+  const uint32_t sum = __reduce_add_sync(peers, w);
+  if (key != 0xffffffffu && (peers & ((1u << lane) - 1u)) == 0) {
+    atomicAdd(&cnt[key], (uint32_t)__popc(peers));
+    if (wsum) atomicAdd(&wsum[key], sum);
+  }
+}
+
+__global__ void __launch_bounds__(RX)
+k_round_expand(const float* __restrict__ lb2, const uint32_t* __restrict__ blkmin, int64_t TL, int64_t nblk,
+               const float* __restrict__ thrP, const uint16_t* __restrict__ leaf_tree,
+               const uint32_t* __restrict__ leaf_range, int L, const uint32_t* __restrict__ nqd,
+               uint8_t* __restrict__ lround, uint32_t* __restrict__ blist, uint32_t* __restrict__ hpts,
+               uint32_t* __restrict__ boff, uint32_t* __restrict__ list, uint32_t* __restrict__ meta) {
+  extern __shared__ __align__(16) uint32_t smx[];
   const int RL = kRoundCap * L;
-  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smp);   // [RL]
-  uint32_t* s_pts = s_cnt + RL;                          // [RL]
-  __shared__ int s_tcap;
+  float* s_thr = reinterpret_cast<float*>(smx);   // [kRoundCap]
+  uint32_t* s_bcnt = smx + kRoundCap;             // [kRoundCap] blocks per block round
+  uint32_t* s_boffb = s_bcnt + kRoundCap;         // [kRoundCap + 1] their offsets, then cursors
+  uint32_t* s_cnt = s_boffb + kRoundCap + 2;      // [RL] leaves per (round, tree)
+  uint32_t* s_pts = s_cnt + RL;                   // [RL] points per (round, tree)
+  uint32_t* s_off = s_pts + RL;                   // [RL + 1] bucket offsets
+  uint32_t* s_cur = s_off + RL + 1;               // [RL] bucket cursors
+  __shared__ unsigned long long s_cum[kMaxL];
+  __shared__ int s_tcap, s_stop;
   const int64_t qb = blockIdx.x;
   if (qb >= (int64_t)*nqd) return;
+  const int tid = threadIdx.x, lane = tid & 31;
   uint32_t* m = meta + qb * MQ_WORDS;
-  const int tlast = (int)m[MQ_TLAST];
-  const int nb = (tlast + 1) * L;
-  for (int i = threadIdx.x; i < nb; i += BT) {
-    s_cnt[i] = hcnt[qb * RL + i];
-    s_pts[i] = hpts[qb * RL + i];
+  const int Ru = (int)m[MQ_RU];
+  const unsigned long long T = ((unsigned long long)m[MQ_T_HI] << 32) | m[MQ_T_LO];
+  for (int i = tid; i < Ru; i += RX) s_thr[i] = thrP[qb * kRoundCap + i];
+  for (int i = tid; i < kRoundCap; i += RX) s_bcnt[i] = 0;
+  for (int i = tid; i < Ru * L; i += RX) {
+    s_cnt[i] = 0;
+    s_pts[i] = 0;
+    s_cur[i] = 0;
+  }
+  if (tid < kMaxL) s_cum[tid] = 0;
+  if (tid == 0) {
+    s_tcap = Ru - 1;   // the last round holds every remaining leaf
+    s_stop = 0;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned long long T = ((unsigned long long)m[MQ_T_HI] << 32) | m[MQ_T_LO];
-    int tcap = tlast;
-    unsigned long long cum[kMaxL];
-    for (int i = 0; i < L; ++i) cum[i] = 0;
-    for (int t = 0; t <= tlast && tcap == tlast; ++t) {
-      for (int i = 0; i < L; ++i) {
-        cum[i] += s_pts[t * L + i];
-        if (cum[i] >= T) tcap = t;
-      }
-    }
-    m[MQ_TCAP] = (uint32_t)tcap;
-    s_tcap = tcap;
-    uint32_t* bo = boff + qb * (RL + 1);
+  // blocks by the round of their smallest lower bound
+  const uint32_t* bm = blkmin + qb * nblk;
+  const int64_t nb_iter = (nblk + RX - 1) / RX * RX;
+  for (int64_t bk = tid; bk < nb_iter; bk += RX) {
+    const uint32_t rb = bk < nblk ? (uint32_t)lower_bound_f(s_thr, Ru, __uint_as_float(bm[bk])) : 0xffffffffu;
+    add_key(s_bcnt, nullptr, rb, 0u, lane);
+  }
+  __syncthreads();
+  if (tid == 0) {
     uint32_t run = 0;
-    for (int b = 0; b < (tcap + 1) * L; ++b) {
-      bo[b] = run;
-      run += s_cnt[b];
+    for (int t = 0; t < Ru; ++t) {
+      s_boffb[t] = run;
+      run += s_bcnt[t];
     }
-    bo[(tcap + 1) * L] = run;
+    s_boffb[Ru] = run;
   }
   __syncthreads();
-  // where each CTA's leaves of a bucket start: the bucket's offset plus the
-  // counts of the CTAs before it
-  const uint32_t* bo = boff + qb * (RL + 1);
-  uint32_t* hc = hcta + qb * (int64_t)nsplit * RL;
-  for (int i = threadIdx.x; i < (s_tcap + 1) * L; i += BT) {
-    uint32_t run = bo[i];
-    for (int c = 0; c < nsplit; ++c) {
-      const uint32_t v = hc[(int64_t)c * RL + i];
-      hc[(int64_t)c * RL + i] = run;
-      run += v;
-    }
+  uint32_t* bl = blist + qb * nblk;
+  for (int64_t bk = tid; bk < nb_iter; bk += RX) {
+    const uint32_t rb = bk < nblk ? (uint32_t)lower_bound_f(s_thr, Ru, __uint_as_float(bm[bk])) : 0xffffffffu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, rb);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (rb != 0xffffffffu && lane == leader) base = atomicAdd(&s_boffb[rb], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (rb != 0xffffffffu) bl[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)bk;
   }
-}
-
-__global__ void __launch_bounds__(BT)
-k_bucket_scatter(int64_t total_leaves, int64_t lpc, const uint16_t* __restrict__ leaf_tree, int L,
-                 const uint32_t* __restrict__ nqd, const uint8_t* __restrict__ lround,
-                 const uint32_t* __restrict__ hcta, const uint32_t* __restrict__ meta, uint32_t* __restrict__ list) {
-  extern __shared__ __align__(16) unsigned char sms[];
-  const int RL = kRoundCap * L;
-  uint32_t* s_next = reinterpret_cast<uint32_t*>(sms);   // [RL]: this CTA's next place per bucket
-  const int64_t qb = blockIdx.y;
-  if (qb >= (int64_t)*nqd) return;
-  const uint32_t tcap = meta[qb * MQ_WORDS + MQ_TCAP];
-  const int nb = ((int)tcap + 1) * L;
-  const int lane = threadIdx.x & 31;
-  const uint32_t lt = (1u << lane) - 1u;
-  const uint32_t* hc = hcta + (qb * gridDim.x + blockIdx.x) * RL;
-  for (int i = threadIdx.x; i < nb; i += BT) s_next[i] = hc[i];
   __syncthreads();
-  const int64_t la = (int64_t)blockIdx.x * lpc;
-  const int64_t lb_end = min(total_leaves, la + lpc);
-  const uint8_t* lr = lround + qb * total_leaves;
-  uint32_t* ql = list + qb * total_leaves;
-  for (int64_t l = la + threadIdx.x; l < la + (lb_end - la + BT - 1) / BT * BT; l += BT) {
+  // s_boffb[t] now holds the end of round t's blocks; its start is the end of t-1
+  const float* lbrow = lb2 + qb * TL;
+  uint8_t* lr = lround + qb * TL;
+  for (int t = 0; t < Ru; ++t) {
+    const uint32_t b0 = t > 0 ? s_boffb[t - 1] : 0u, b1 = s_boffb[t];
+    const uint32_t items = (b1 - b0) * kLbBlock;
+    const uint32_t it_iter = (items + RX - 1) / RX * RX;
+    for (uint32_t it = tid; it < it_iter; it += RX) {
+      uint32_t key = 0xffffffffu, pts = 0;
+      if (it < items) {
+        const int64_t leaf = (int64_t)bl[b0 + it / kLbBlock] * kLbBlock + it % kLbBlock;
+        if (leaf < TL) {
+          const uint32_t r = (uint32_t)lower_bound_f(s_thr, Ru, lbrow[leaf]);
+          lr[leaf] = (uint8_t)r;
+          key = r * (uint32_t)L + leaf_tree[leaf];
+          pts = leaf_range[2 * leaf + 1];
+        }
+      }
+      add_key(s_cnt, s_pts, key, pts, lane);
+    }
+    __syncthreads();
+    // rounds 0..t are complete: does some tree alone hold T points?
+    if (tid == 0) {
+      for (int i = 0; i < L; ++i) {
+        s_cum[i] += s_pts[t * L + i];
+        if (s_cum[i] >= T) s_stop = 1;
+      }
+      if (s_stop) s_tcap = t;
+    }
+    __syncthreads();
+    if (s_stop) break;
+  }
+  const int tcap = s_tcap;
+  const int nbk = (tcap + 1) * L;
+  if (tid == 0) {
+    uint32_t run = 0;
+    for (int i = 0; i < nbk; ++i) {
+      s_off[i] = run;
+      run += s_cnt[i];
+    }
+    s_off[nbk] = run;
+    m[MQ_TCAP] = (uint32_t)tcap;
+    m[MQ_TLAST] = (uint32_t)(Ru - 1);
+  }
+  __syncthreads();
+  uint32_t* bo = boff + qb * (kRoundCap * L + 1);
+  uint32_t* hp = hpts + qb * kRoundCap * L;
+  for (int i = tid; i <= nbk; i += RX) bo[i] = s_off[i];
+  for (int i = tid; i < nbk; i += RX) hp[i] = s_pts[i];
+  // the leaves of rounds up to tcap into their bucket lists (they lie in the
+  // blocks of rounds up to tcap, all expanded)
+  uint32_t* ql = list + qb * TL;
+  const uint32_t items = s_boffb[tcap] * kLbBlock;
+  const uint32_t it_iter = (items + RX - 1) / RX * RX;
+  for (uint32_t it = tid; it < it_iter; it += RX) {
     uint32_t key = 0xffffffffu;
-    if (l < lb_end) {
-      const uint32_t t = lr[l];
-      if (t <= tcap) key = t * (uint32_t)L + leaf_tree[l];
+    int64_t leaf = 0;
+    if (it < items) {
+      leaf = (int64_t)bl[it / kLbBlock] * kLbBlock + it % kLbBlock;
+      if (leaf < TL) {
+        const uint32_t r = lr[leaf];
+        if ((int)r <= tcap) key = r * (uint32_t)L + leaf_tree[leaf];
+      }
     }
     const uint32_t peers = __match_any_sync(0xffffffffu, key);
     const int leader = __ffs(peers) - 1;
     uint32_t base = 0;
-    if (key != 0xffffffffu && lane == leader) base = atomicAdd(&s_next[key], (uint32_t)__popc(peers));
+    if (key != 0xffffffffu && lane == leader) base = s_off[key] + atomicAdd(&s_cur[key], (uint32_t)__popc(peers));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (key != 0xffffffffu) ql[base + __popc(peers & lt)] = (uint32_t)l;
+    if (key != 0xffffffffu) ql[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)leaf;
   }
 }
 
@@ -1888,15 +1877,10 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   sh.nsm = nsm;
   // split bucketing: per-CTA histograms over (round, tree)
   sh.rq = 1;
-  sh.bk_smem = sizeof(uint32_t) * 2 * sh.RL + sizeof(float) * kRoundCap;
-  sh.bp_smem = sizeof(uint32_t) * 2 * sh.RL;
+  sh.nblk = (sh.TL + kLbBlock - 1) / kLbBlock;
+  sh.bk_smem = round_smem_bytes(sh.L);
   if (sh.bk_smem > 48 * 1024)
-    DL_CUDA(cudaFuncSetAttribute(k_round_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.bk_smem));
-  if (sh.bp_smem > 48 * 1024)
-    DL_CUDA(cudaFuncSetAttribute(k_bucket_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.bp_smem));
-  if (sh.RL * sizeof(uint32_t) > 48 * 1024)
-    DL_CUDA(cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sh.RL * sizeof(uint32_t))));
+    DL_CUDA(cudaFuncSetAttribute(k_round_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.bk_smem));
   DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 4096, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
   DL_CUDA(cudaFuncSetAttribute(k_finalize<uint8_t, 4096, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768));
   DL_CUDA(cudaFuncSetAttribute(k_finalize<float, 8192, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
@@ -1937,7 +1921,7 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   // 12 GiB and a quarter of the free device memory; fewer, larger batches
   // shorten the tails of the per-query kernels)
   const int64_t per_q = sh.TL * 9 + sh.cap * 8 + sh.RL * 16 + kRoundCap * 12 + MQ_WORDS * 4 +
-                        sh.LK * 4 + sh.items_per_q * 16 + ((sh.TL + 16383) / 16384) * sh.RL * 4 +
+                        sh.LK * 4 + sh.items_per_q * 16 + sh.nblk * 8 +
                         (idx->Xb ? (int64_t)idx->d * 2 : 0) + (shortlist > 0 ? (int64_t)idx->d * 4 : 0) +
                         (sh.lm ? sh.cap * (16 + 16 + 4) + sh.cap / 8 + 4 : 0) +
                         (!sh.lm && sh.nbk ? sh.cap * 8 + sh.nbk * 16 : 0) + 64;
@@ -1980,9 +1964,8 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
   sh.o_mm = take(sizeof(uint32_t) * 2 * B);
   sh.o_lround = take((size_t)B * sh.TL);
   sh.o_hist = take(sizeof(uint32_t) * B * sh.RL);
-  sh.o_hcnt = take(sizeof(uint32_t) * B * sh.RL);
-  sh.bsplit = (sh.TL + 16383) / 16384;
-  sh.o_hcta = take(sizeof(uint32_t) * B * sh.bsplit * sh.RL);
+  sh.o_blkmin = take(sizeof(uint32_t) * B * sh.nblk);
+  sh.o_blist = take(sizeof(uint32_t) * B * sh.nblk);
   sh.o_boff = take(sizeof(uint32_t) * B * (sh.RL + 1));
   sh.o_list = take(sizeof(uint32_t) * B * sh.TL);
   sh.o_cand = take(sizeof(uint32_t) * B * sh.cap);
@@ -2125,8 +2108,9 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
 
   dim3 g1(ceil_div(TL, LB_THREADS), ceil_div(nqg, LB_QCH));
   tm.begin(TR_LB);
+  uint32_t* blkmin = reinterpret_cast<uint32_t*>(b + sh.o_blkmin);
   k_leaf_lb<<<g1, LB_THREADS, lb_smem_bytes(LK), s>>>(qp, nqd, LK, idx->E, idx->Nr, idx->K, idx->leaf_lo, idx->leaf_hi,
-                                      idx->leaf_tree, TL, lb, d_min, d_max);
+                                      idx->leaf_tree, TL, lb, d_min, d_max, blkmin, sh.nblk);
   DL_LAUNCH();
   tm.end();
   trace_add(TR_LB_LAUNCHES, timed ? 1.0 : 0.0);
@@ -2135,24 +2119,10 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   k_thresh<<<ceil_div(nqg, 128), 128, 0, s>>>(d_min, d_max, q0, nqd, k, c, r_min, eps, beta, idx->n,
                                               thrP, thrC, meta);
   DL_LAUNCH();
-  {
-    uint32_t* hcnt = reinterpret_cast<uint32_t*>(b + sh.o_hcnt);
-    DL_CUDA(cudaMemsetAsync(hcnt, 0, sizeof(uint32_t) * nqg * sh.RL, s));
-    DL_CUDA(cudaMemsetAsync(h_pts, 0, sizeof(uint32_t) * nqg * sh.RL, s));
-    // 16,384 leaves per CTA (measured best on the mid and batching workloads;
-    // a small serving batch still gets TL/16,384 CTAs per query)
-    const int64_t lpc = 16384;
-    const dim3 gb((unsigned)sh.bsplit, (unsigned)nqg);
-    uint32_t* hcta = reinterpret_cast<uint32_t*>(b + sh.o_hcta);
-    k_round_hist<<<gb, BT, sh.bk_smem, s>>>(lb, TL, lpc, thrP, idx->leaf_tree, idx->leaf_range, L, nqd, lround, hcnt,
-                                           h_pts, hcta, meta);
-    DL_LAUNCH();
-    k_bucket_plan<<<(unsigned)nqg, BT, sh.bp_smem, s>>>(L, (int)sh.bsplit, nqd, hcnt, h_pts, hcta, boff, meta);
-    DL_LAUNCH();
-    k_bucket_scatter<<<gb, BT, sizeof(uint32_t) * sh.RL, s>>>(TL, lpc, idx->leaf_tree, L, nqd, lround, hcta, meta,
-                                                               list);
-    DL_LAUNCH();
-  }
+  k_round_expand<<<(unsigned)nqg, RX, sh.bk_smem, s>>>(lb, blkmin, TL, sh.nblk, thrP, idx->leaf_tree, idx->leaf_range,
+                                                      L, nqd, lround, reinterpret_cast<uint32_t*>(b + sh.o_blist),
+                                                      h_pts, boff, list, meta);
+  DL_LAUNCH();
   tm.end();
 
   WalkArgs wa{};
