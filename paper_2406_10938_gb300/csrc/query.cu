@@ -1171,18 +1171,38 @@ k_dist(const TX* __restrict__ X, int d, const TX* __restrict__ Q, int64_t q0,
     const uint32_t* cl = cand + qb * cap;
     const uint2* pl = BK ? pairs + qb * cap : nullptr;
     float* out = d2out + qb * cap;
-    for (int64_t e0 = r0; e0 < r1; e0 += ILP) {
-      uint32_t ids[ILP];
-      float acc[ILP];
+    if (BK) {
+      // lanes 0..7 load the step's eight (point id, list position) pairs and
+      // the warp shares them by shuffles
+      for (uint32_t e0 = (uint32_t)r0; e0 < (uint32_t)r1; e0 += ILP) {
+        const uint32_t e = e0 + (uint32_t)(lane & 7);
+        const uint2 P = (lane < 8 && e < (uint32_t)r1) ? __ldg(pl + e) : make_uint2(0xffffffffu, 0xffffffffu);
+        uint32_t ids[ILP];
+        float acc[ILP];
 #pragma unroll
-      for (int u = 0; u < ILP; ++u) {
-        ids[u] = (e0 + u < r1) ? (BK ? __ldg(&pl[e0 + u].x) : __ldg(cl + e0 + u)) : 0xffffffffu;
-        acc[u] = 0.f;
+        for (int u = 0; u < ILP; ++u) {
+          ids[u] = __shfl_sync(0xffffffffu, P.x, u);
+          acc[u] = 0.f;
+        }
+        rows_dist2<TX>(X, d, ids, q, vec4, lane, acc);
+        const float v = transpose_reduce8(acc, lane);
+        const uint32_t pos = __shfl_sync(0xffffffffu, P.y, (lane >> 2) & 7);
+        if ((lane & 3) == 0 && pos != 0xffffffffu) out[pos] = v;
       }
-      rows_dist2<TX>(X, d, ids, q, vec4, lane, acc);
-      const float v = transpose_reduce8(acc, lane);
-      const int r = (lane >> 2) & 7;
-      if ((lane & 3) == 0 && e0 + r < r1) out[BK ? (int64_t)__ldg(&pl[e0 + r].y) : e0 + r] = v;
+    } else {
+      for (int64_t e0 = r0; e0 < r1; e0 += ILP) {
+        uint32_t ids[ILP];
+        float acc[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+          ids[u] = (e0 + u < r1) ? __ldg(cl + e0 + u) : 0xffffffffu;
+          acc[u] = 0.f;
+        }
+        rows_dist2<TX>(X, d, ids, q, vec4, lane, acc);
+        const float v = transpose_reduce8(acc, lane);
+        const int r = (lane >> 2) & 7;
+        if ((lane & 3) == 0 && e0 + r < r1) out[e0 + r] = v;
+      }
     }
     it = nx;
   }
