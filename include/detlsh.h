@@ -535,6 +535,19 @@ int detlsh_memory_stats(int32_t reset_peak, int64_t* out, int32_t len);
  */
 uint64_t detlsh_test_set_wait_limit_ns(uint64_t ns);
 
+/*
+ * detlsh_check_status -- the checked build's record (no counterpart in the
+ * paper). A library compiled with DETLSH_CHECKED checks the data-dependent
+ * indices of its query kernels on the device (candidate positions, point
+ * ids, bucket and list places, work items); a failed check skips the access
+ * and is recorded. Synchronizes the current device, then writes out[0] the
+ * number of failed checks since the previous call, out[1] the site of the
+ * first one, out[2..3] its index (low, high 32 bits), and clears the record.
+ * Returns 1 for a checked build (entries written: min(len, 4)), 0 for the
+ * normal build (nothing written), DETLSH_ECUDA if the record cannot be read.
+ */
+int detlsh_check_status(uint32_t* out, int32_t len);
+
 /* detlsh_strerror -- static text for a detlsh_status value. */
 const char* detlsh_strerror(int status);
 

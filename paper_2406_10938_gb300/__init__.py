@@ -14,6 +14,7 @@ from .binding import (  # noqa: F401
     detlsh_plan_query,
     detlsh_plan_status,
     detlsh_build,
+    detlsh_check_status,
     detlsh_draw_hashes,
     detlsh_draw_sample,
     detlsh_memory_stats,

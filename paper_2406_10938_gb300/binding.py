@@ -36,7 +36,7 @@ SYMBOLS = ("detlsh_build", "detlsh_query", "detlsh_free", "detlsh_export_size", 
            "detlsh_plan_destroy", "detlsh_autotune", "detlsh_server_create", "detlsh_server_submit",
            "detlsh_server_poll", "detlsh_server_replay", "detlsh_server_stats", "detlsh_server_destroy",
            "detlsh_rc_ann", "detlsh_insert", "detlsh_memory_stats", "detlsh_draw_hashes",
-           "detlsh_draw_sample", "detlsh_test_set_wait_limit_ns")
+           "detlsh_draw_sample", "detlsh_test_set_wait_limit_ns", "detlsh_check_status")
 PENDING, EADMIT = 1, -5
 PLAN_GRAPH = 1
 TRACE_KEYS = ("sample_proj_ms", "breakpoints_ms", "encode_ms", "leaves_ms", "query_proj_ms", "lb_ms",
@@ -96,11 +96,16 @@ _lib = None
 
 
 def lib(path: Optional[str] = None):
-    """Load libdetlsh.so (raises if it is missing)."""
+    """Load libdetlsh.so (raises if it is missing). With DETLSH_CHECKED=1 in the
+    environment the checked build (device index checks) is built if needed and
+    loaded instead."""
     global _lib
     if _lib is not None and path is None:
         return _lib
     p = path or LIB
+    if path is None and os.environ.get("DETLSH_CHECKED") == "1":
+        from .build_lib import build as _build
+        p = _build(checked=True)
     if not os.path.exists(p):
         raise RuntimeError(f"{p} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
     L = ctypes.CDLL(p)
@@ -137,6 +142,8 @@ def lib(path: Optional[str] = None):
     L.detlsh_trace_get.restype = ctypes.c_int
     L.detlsh_launch_count.argtypes = []
     L.detlsh_launch_count.restype = i64
+    L.detlsh_check_status.argtypes = [ctypes.POINTER(ctypes.c_uint32), i32]
+    L.detlsh_check_status.restype = ctypes.c_int
     L.detlsh_rc_ann.argtypes = [vp, vp, i64, i32, vp, vp, dbl, dbl, vp, vp, vp, vp]
     L.detlsh_rc_ann.restype = ctypes.c_int
     L.detlsh_insert.argtypes = [vp, vp, i64, i32, i32, vp]
@@ -590,3 +597,15 @@ def detlsh_trace_get() -> dict:
 
 def detlsh_launch_count() -> int:
     return int(lib().detlsh_launch_count())
+
+
+def detlsh_check_status():
+    """None for the normal build; for the checked build (failed checks since
+    the last call, site of the first, its index), the record then cleared."""
+    out = (ctypes.c_uint32 * 4)()
+    r = lib().detlsh_check_status(out, 4)
+    if r < 0:
+        _check(r, "detlsh_check_status")
+    if r == 0:
+        return None
+    return int(out[0]), int(out[1]), int(out[2]) | (int(out[3]) << 32)

@@ -421,6 +421,22 @@ int time_tuned(const TuneCtx& x, int shortlist, const QueryTuning& tu, float* ms
 
 }  // namespace detlsh
 
+#ifdef DETLSH_CHECKED
+namespace detlsh {
+namespace {
+constexpr int kMaxCheckReaders = 32;
+int (*g_check_readers[kMaxCheckReaders])(unsigned int*) = {};
+int g_n_check_readers = 0;
+}  // namespace
+// called during the library's static initialisation, one reader per
+// translation unit
+int register_check_reader(int (*read)(unsigned int* words)) {
+  if (g_n_check_readers < kMaxCheckReaders) g_check_readers[g_n_check_readers++] = read;
+  return g_n_check_readers;
+}
+}  // namespace detlsh
+#endif
+
 extern "C" {
 
 const char* detlsh_strerror(int status) {
@@ -479,6 +495,30 @@ int detlsh_memory_stats(int32_t reset_peak, int64_t* out, int32_t len) {
 
 int64_t detlsh_launch_count(void) {
   return (int64_t)__atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+}
+
+
+int detlsh_check_status(uint32_t* out, int32_t len) {
+#ifdef DETLSH_CHECKED
+  if (cudaDeviceSynchronize() != cudaSuccess) return DETLSH_ECUDA;
+  uint32_t tot[4] = {0u, 0u, 0u, 0u};
+  for (int i = 0; i < g_n_check_readers; ++i) {
+    unsigned int w[4];
+    if (g_check_readers[i](w) != 0) return DETLSH_ECUDA;
+    if (w[0] && !tot[0]) {
+      tot[1] = w[1];
+      tot[2] = w[2];
+      tot[3] = w[3];
+    }
+    tot[0] += w[0];
+  }
+  for (int i = 0; i < std::min<int>(len, 4); ++i) out[i] = tot[i];
+  return 1;
+#else
+  (void)out;
+  (void)len;
+  return 0;
+#endif
 }
 
 double detlsh_eps_lemma3(int32_t K, int32_t L) {

@@ -17,6 +17,35 @@ constexpr int kMaxLK = 256;
 constexpr int kRoundCap = 256;   // rounds of Alg. 7; the last one has infinite radius
 constexpr int kMaxTopK = 1024;
 
+// ---- the checked build (compiled with DETLSH_CHECKED): data-dependent indices
+// of the query kernels are checked on the device; a failed check skips the
+// access and records (failures, first site, first index) in a status word of
+// its translation unit, which detlsh_check_status collects. In the normal
+// build DL_CHECK is true and the checks vanish.
+#ifdef DETLSH_CHECKED
+static __device__ unsigned int g_dl_check[4];
+__device__ __forceinline__ bool dl_check(bool ok, unsigned site, unsigned long long index) {
+  if (!ok && atomicAdd(&g_dl_check[0], 1u) == 0u) {
+    g_dl_check[1] = site;
+    g_dl_check[2] = (unsigned)index;
+    g_dl_check[3] = (unsigned)(index >> 32);
+  }
+  return ok;
+}
+int register_check_reader(int (*read)(unsigned int* words));
+// this translation unit's status word: copied out, then cleared
+static int read_check_words(unsigned int* w) {
+  if (cudaMemcpyFromSymbol(w, g_dl_check, sizeof(unsigned int) * 4) != cudaSuccess) return -1;
+  const unsigned int zero[4] = {0u, 0u, 0u, 0u};
+  if (cudaMemcpyToSymbol(g_dl_check, zero, sizeof(zero)) != cudaSuccess) return -1;
+  return 0;
+}
+static const int g_dl_check_registered = register_check_reader(&read_check_words);
+#define DL_CHECK(cond, site, index) (::detlsh::dl_check((cond), (site), (unsigned long long)(index)))
+#else
+#define DL_CHECK(cond, site, index) true
+#endif
+
 void set_error(const char* fmt, ...);
 void clear_error();
 void count_launch();

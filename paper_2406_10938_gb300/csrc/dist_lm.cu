@@ -268,6 +268,7 @@ __global__ void __launch_bounds__(LmShape<NMAX>::THREADS, 1) k_dist_lm(LmArgs a)
       for (int i = 0; i < NMAX / 32; ++i) {
         const uint32_t j = lane + 32 * i;
         id[i] = j < N ? lids[j] : 0u;
+        if (!DL_CHECK(id[i] < a.n, 50, id[i])) id[i] = 0u;
       }
 #pragma unroll
       for (int i = 0; i < LM_M / 32; ++i) {

@@ -114,6 +114,7 @@ k_leaf_lb(const float* __restrict__ qp, const uint32_t* __restrict__ nqd, int LK
     if (valid && j < K) {
       const int r = tree * K + j;
       const int lo = leaf_lo[leaf * K + j], hi = leaf_hi[leaf * K + j];
+      (void)DL_CHECK(lo <= hi && hi < Nr, 60, leaf);
       if (lo > 0) el[j] = __ldg(E + (int64_t)r * (Nr + 1) + lo);
       if (hi < Nr - 1) eh[j] = __ldg(E + (int64_t)r * (Nr + 1) + hi + 1);
     }
@@ -351,7 +352,8 @@ k_round_expand(const float* __restrict__ lb2, const uint32_t* __restrict__ blkmi
     uint32_t base = 0;
     if (rb != 0xffffffffu && lane == leader) base = atomicAdd(&s_boffb[rb], (uint32_t)__popc(peers));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (rb != 0xffffffffu) bl[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)bk;
+    const uint32_t bp = base + __popc(peers & ((1u << lane) - 1u));
+    if (rb != 0xffffffffu && DL_CHECK(bp < nblk, 30, bp)) bl[bp] = (uint32_t)bk;
   }
   __syncthreads();
   // s_boffb[t] now holds the end of round t's blocks; its start is the end of t-1
@@ -370,6 +372,7 @@ k_round_expand(const float* __restrict__ lb2, const uint32_t* __restrict__ blkmi
           lr[leaf] = (uint8_t)r;
           key = r * (uint32_t)L + leaf_tree[leaf];
           pts = leaf_range[2 * leaf + 1];
+          if (!DL_CHECK(key < (uint32_t)(Ru * L), 31, key)) key = 0xffffffffu;
         }
       }
       add_key(s_cnt, s_pts, key, pts, lane);
@@ -423,7 +426,8 @@ k_round_expand(const float* __restrict__ lb2, const uint32_t* __restrict__ blkmi
     uint32_t base = 0;
     if (key != 0xffffffffu && lane == leader) base = s_off[key] + atomicAdd(&s_cur[key], (uint32_t)__popc(peers));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (key != 0xffffffffu) ql[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)leaf;
+    const uint32_t lp = base + __popc(peers & ((1u << lane) - 1u));
+    if (key != 0xffffffffu && DL_CHECK(lp < TL, 32, lp)) ql[lp] = (uint32_t)leaf;
   }
 }
 
@@ -578,7 +582,7 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const uint32_t j = 2 * threadIdx.x + h;
-      if (j < nb) {
+      if (j < nb && DL_CHECK(list[la + j] < a.total_leaves, 1, list[la + j])) {
         const uint32_t leaf = list[la + j];
         const uint32_t st = a.leaf_range[2 * (int64_t)leaf];
         uint32_t cnt = a.leaf_range[2 * (int64_t)leaf + 1];
@@ -640,7 +644,8 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
         const uint32_t f = f0 + u * WT + threadIdx.x;
         ids[u] = 0xffffffffu;
         bp[u] = 0xffffffffu;
-        if (f < take_pts) {
+        if (f < take_pts && DL_CHECK(bstart[fmap[f]] + (f - bpref[fmap[f]]) < (int64_t)a.L * a.n, 2,
+                                     bstart[fmap[f]] + (f - bpref[fmap[f]]))) {
           const uint32_t j = fmap[f];
           const int64_t e = bstart[j] + (f - bpref[j]);
           if (POS) {
@@ -655,7 +660,10 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
       if (count_only) {
         uint32_t word[WILP];
 #pragma unroll
-        for (int u = 0; u < WILP; ++u) word[u] = bp[u] != 0xffffffffu ? bitmap[bp[u] >> 5] : 0xffffffffu;
+        for (int u = 0; u < WILP; ++u)
+          word[u] = (bp[u] != 0xffffffffu && DL_CHECK((int64_t)(bp[u] >> 5) < a.bitmap_words, 3, bp[u]))
+                        ? bitmap[bp[u] >> 5]
+                        : 0xffffffffu;
 #pragma unroll
         for (int u = 0; u < WILP; ++u) {
           const uint32_t f = f0 + u * WT + threadIdx.x;
@@ -673,7 +681,9 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
       uint32_t old[WILP];
 #pragma unroll
       for (int u = 0; u < WILP; ++u)
-        old[u] = bp[u] != 0xffffffffu ? atomicOr(bitmap + (bp[u] >> 5), 1u << (bp[u] & 31)) : 0xffffffffu;
+        old[u] = (bp[u] != 0xffffffffu && DL_CHECK((int64_t)(bp[u] >> 5) < a.bitmap_words, 3, bp[u]))
+                     ? atomicOr(bitmap + (bp[u] >> 5), 1u << (bp[u] & 31))
+                     : 0xffffffffu;
       uint32_t fm[WILP], tot = 0;
 #pragma unroll
       for (int u = 0; u < WILP; ++u) {
@@ -1155,7 +1165,7 @@ __device__ __forceinline__ uint32_t next_item(uint32_t* head, int lane) {
 // (point id, list position) pairs; the distance goes to the list position.
 template <typename TX, bool BK>
 __global__ void __launch_bounds__(DT, 4)
-k_dist(const TX* __restrict__ X, int d, const TX* __restrict__ Q, int64_t q0,
+k_dist(const TX* __restrict__ X, int d, int64_t n, const TX* __restrict__ Q, int64_t q0,
        const uint32_t* __restrict__ cand, const uint2* __restrict__ pairs, int64_t cap,
        const uint4* __restrict__ items, const uint32_t* __restrict__ qtail, uint32_t* __restrict__ head,
        float* __restrict__ d2out, bool vec4) {
@@ -1182,12 +1192,13 @@ k_dist(const TX* __restrict__ X, int d, const TX* __restrict__ Q, int64_t q0,
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
           ids[u] = __shfl_sync(0xffffffffu, P.x, u);
+          if (ids[u] != 0xffffffffu && !DL_CHECK(ids[u] < n, 10, ids[u])) ids[u] = 0xffffffffu;
           acc[u] = 0.f;
         }
         rows_dist2<TX>(X, d, ids, q, vec4, lane, acc);
         const float v = transpose_reduce8(acc, lane);
         const uint32_t pos = __shfl_sync(0xffffffffu, P.y, (lane >> 2) & 7);
-        if ((lane & 3) == 0 && pos != 0xffffffffu) out[pos] = v;
+        if ((lane & 3) == 0 && pos != 0xffffffffu && DL_CHECK(pos < cap, 11, pos)) out[pos] = v;
       }
     } else {
       for (int64_t e0 = r0; e0 < r1; e0 += ILP) {
@@ -1196,6 +1207,7 @@ k_dist(const TX* __restrict__ X, int d, const TX* __restrict__ Q, int64_t q0,
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
           ids[u] = (e0 + u < r1) ? __ldg(cl + e0 + u) : 0xffffffffu;
+          if (ids[u] != 0xffffffffu && !DL_CHECK(ids[u] < n, 10, ids[u])) ids[u] = 0xffffffffu;
           acc[u] = 0.f;
         }
         rows_dist2<TX>(X, d, ids, q, vec4, lane, acc);
@@ -1215,7 +1227,7 @@ k_dist(const TX* __restrict__ X, int d, const TX* __restrict__ Q, int64_t q0,
 // order of the sums (at most 512 * 255^2 < 2^31), converted to FP32 once.
 template <bool BK>
 __global__ void __launch_bounds__(DT, 4)
-k_dist_u8(const uint8_t* __restrict__ X, int d, const uint8_t* __restrict__ Q, int64_t q0,
+k_dist_u8(const uint8_t* __restrict__ X, int d, int64_t n, const uint8_t* __restrict__ Q, int64_t q0,
           const uint32_t* __restrict__ cand, const uint2* __restrict__ pairs, int64_t cap,
           const uint4* __restrict__ items, const uint32_t* __restrict__ qtail, uint32_t* __restrict__ head,
           float* __restrict__ d2out) {
@@ -1243,6 +1255,7 @@ k_dist_u8(const uint8_t* __restrict__ X, int d, const uint8_t* __restrict__ Q, i
       for (int u = 0; u < 8; ++u) {
         const int64_t e = e0 + u * rpl + grp;
         ids[u] = e < r1 ? (BK ? __ldg(&pl[e].x) : __ldg(cl + e)) : 0xffffffffu;
+        if (ids[u] != 0xffffffffu && !DL_CHECK(ids[u] < n, 12, ids[u])) ids[u] = 0xffffffffu;
       }
       uint4 xv[8];
 #pragma unroll
@@ -1300,7 +1313,10 @@ k_cand_buckets(const uint32_t* __restrict__ cand, int64_t cap, const uint32_t* _
   for (int b = threadIdx.x; b < nbk; b += BKT) s_cnt[b] = 0;
   __syncthreads();
   const uint32_t* cl = cand + qb * cap;
-  for (int64_t i = threadIdx.x; i < ns; i += BKT) atomicAdd(&s_cnt[__ldg(cl + i) >> bshift], 1u);
+  for (int64_t i = threadIdx.x; i < ns; i += BKT) {
+    const uint32_t bk = __ldg(cl + i) >> bshift;
+    if (DL_CHECK(bk < (uint32_t)nbk, 20, bk)) atomicAdd(&s_cnt[bk], 1u);
+  }
   __syncthreads();
   // exclusive scan of the counts: each thread a contiguous run of ranges
   const int per = (nbk + BKT - 1) / BKT;
@@ -1328,8 +1344,9 @@ k_cand_buckets(const uint32_t* __restrict__ cand, int64_t cap, const uint32_t* _
   uint2* pl = pairs + qb * cap;
   for (int64_t i = threadIdx.x; i < ns; i += BKT) {
     const uint32_t id = __ldg(cl + i);
+    if (!DL_CHECK((id >> bshift) < (uint32_t)nbk, 20, id)) continue;
     const uint32_t p = atomicAdd(&s_off[id >> bshift], 1u);
-    pl[p] = make_uint2(id, (uint32_t)i);
+    if (DL_CHECK(p < cap, 21, p)) pl[p] = make_uint2(id, (uint32_t)i);
   }
 }
 
@@ -1423,7 +1440,7 @@ __device__ __forceinline__ float transpose_reduce8_half(const float* acc, int la
 
 template <bool BK>
 __global__ void __launch_bounds__(DT, 3)
-k_dist_bf16(const __nv_bfloat16* __restrict__ Xb, int d, const float* __restrict__ Qf, int64_t q0,
+k_dist_bf16(const __nv_bfloat16* __restrict__ Xb, int d, int64_t n, const float* __restrict__ Qf, int64_t q0,
             const uint32_t* __restrict__ cand, const uint2* __restrict__ pairs, int64_t cap,
             const uint4* __restrict__ items, const uint32_t* __restrict__ qtail, uint32_t* __restrict__ head,
             float* __restrict__ d2out) {
@@ -1447,6 +1464,7 @@ k_dist_bf16(const __nv_bfloat16* __restrict__ Xb, int d, const float* __restrict
       for (int u = 0; u < ILP; ++u) {
         const int64_t e = e0 + h * ILP + u;
         ids[u] = (e < r1) ? (BK ? __ldg(&pl[e].x) : __ldg(cl + e)) : 0xffffffffu;
+        if (ids[u] != 0xffffffffu && !DL_CHECK(ids[u] < n, 13, ids[u])) ids[u] = 0xffffffffu;
         acc[u] = 0.f;
       }
       rows_dist2_bf16(Xb, d, ids, q, lane & 15, acc);
@@ -1629,7 +1647,11 @@ __global__ void __launch_bounds__(NT) k_finalize(FinalArgs a) {
   const int64_t qb = blockIdx.x;
   const int64_t qg = a.q0 + qb;
   const uint32_t* m = a.meta + qb * MQ_WORDS;
-  const uint32_t nS = m[MQ_NS], t_end = m[MQ_TEND], stopT = m[MQ_STOP];
+  // (the list never holds more than cap entries; an overflow is reported in the stats)
+  const uint32_t nS0 = m[MQ_NS];
+  const uint32_t nS = (uint32_t)min((int64_t)nS0, a.cap);
+  (void)DL_CHECK((int64_t)nS0 <= a.cap, 40, nS0);
+  const uint32_t t_end = m[MQ_TEND], stopT = m[MQ_STOP];
   const int Ru = (int)m[MQ_RU];
   const int kq = a.k[qg];
   const int keep = a.shortlist > 0 ? max(a.shortlist, kq) : kq;   // entries the buffer keeps
@@ -2228,19 +2250,19 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
     DL_TRY(enqueue_coarse_lm(idx, lb, s));
   } else if (sh.shortlist > 0) {
     (pairs ? k_dist_bf16<true> : k_dist_bf16<false>)<<<sh.dgrid, DT, 0, s>>>(
-        static_cast<const __nv_bfloat16*>(idx->Xb), idx->d, qf, 0, candb, pairs, sh.cap, items, ctr + CT_QTAIL,
+        static_cast<const __nv_bfloat16*>(idx->Xb), idx->d, idx->n, qf, 0, candb, pairs, sh.cap, items, ctr + CT_QTAIL,
         ctr + CT_HEAD, d2b);
   } else if (dist_u8_eligible(idx, Q)) {
     (pairs ? k_dist_u8<true> : k_dist_u8<false>)<<<sh.dgrid, DT, 0, s>>>(
-        static_cast<const uint8_t*>(idx->X), idx->d, static_cast<const uint8_t*>(Q), q0, candb, pairs, sh.cap,
+        static_cast<const uint8_t*>(idx->X), idx->d, idx->n, static_cast<const uint8_t*>(Q), q0, candb, pairs, sh.cap,
         items, ctr + CT_QTAIL, ctr + CT_HEAD, d2b);
   } else if (idx->dtype == DETLSH_U8) {
     (pairs ? k_dist<uint8_t, true> : k_dist<uint8_t, false>)<<<sh.dgrid, DT, 0, s>>>(
-        static_cast<const uint8_t*>(idx->X), idx->d, static_cast<const uint8_t*>(Q), q0, candb, pairs, sh.cap,
+        static_cast<const uint8_t*>(idx->X), idx->d, idx->n, static_cast<const uint8_t*>(Q), q0, candb, pairs, sh.cap,
         items, ctr + CT_QTAIL, ctr + CT_HEAD, d2b, vec4);
   } else {
     (pairs ? k_dist<float, true> : k_dist<float, false>)<<<sh.dgrid, DT, 0, s>>>(
-        static_cast<const float*>(idx->X), idx->d, static_cast<const float*>(Q), q0, candb, pairs, sh.cap, items,
+        static_cast<const float*>(idx->X), idx->d, idx->n, static_cast<const float*>(Q), q0, candb, pairs, sh.cap, items,
         ctr + CT_QTAIL, ctr + CT_HEAD, d2b, vec4);
   }
   DL_LAUNCH();

@@ -36,6 +36,15 @@ def test_every_declared_symbol_is_exported(L):
         assert hasattr(L, name), name
 
 
+def test_normal_build_reports_no_device_checks(L):
+    # the index checks exist only in the DETLSH_CHECKED build; the normal
+    # library says so without touching a GPU
+    import ctypes
+    out = (ctypes.c_uint32 * 4)(7, 7, 7, 7)
+    assert L.detlsh_check_status(out, 4) == 0
+    assert list(out) == [7, 7, 7, 7]
+
+
 def test_eps_solver_matches_scipy(L):
     from scipy.stats import chi2
     for K in (1, 2, 8, 16, 31, 32):
