@@ -69,7 +69,12 @@ cudaMemPool_t scratch_pool() {
     props.location.id = dev;
     cudaMemPool_t pool = nullptr;
     if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
-      uint64_t keep = (uint64_t)16 << 30;
+      // freed memory up to a quarter of the device (at least 16 GiB) stays
+      // mapped, so repeated builds and queries do not remap it (a build of
+      // 1e8 points allocates about 16 GB of index and sort scratch)
+      size_t fr = 0, total = 0;
+      cudaMemGetInfo(&fr, &total);
+      uint64_t keep = std::max<uint64_t>((uint64_t)16 << 30, (uint64_t)total / 4);
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
       pools[dev] = pool;
     } else {
