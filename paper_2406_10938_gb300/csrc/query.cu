@@ -891,7 +891,7 @@ __device__ unsigned long long select_key(const uint32_t* bl, const uint32_t* lbk
 
 // One CTA per query (persistent over the batch): the buckets in Alg. 7 order.
 template <bool POS>
-__global__ void __launch_bounds__(WT, 2) k_walk(WalkArgs a) {
+__global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
   const WalkLayout ly = walk_layout(a.L, a.smem_bitmap ? a.bitmap_words : 0);
   uint32_t* s_boff = reinterpret_cast<uint32_t*>(sm + ly.boff);
