@@ -191,17 +191,6 @@ __device__ __forceinline__ int lower_bound_f(const float* a, int n, float v) {
   return lo;
 }
 
-// index of the first element > v in a non-decreasing array (n if none)
-__device__ __forceinline__ int upper_bound_u(const uint32_t* a, int n, uint32_t v) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (a[mid] <= v) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
 // per-query words of the pipeline (uint32)
 enum {
   MQ_RU = 0,      // rounds in the threshold table
@@ -1671,6 +1660,11 @@ __global__ void __launch_bounds__(NT) k_finalize(FinalArgs a) {
   // u = first round whose exact threshold (c*r_u)^2 covers its distance
   constexpr int FU = 4;   // candidates per thread in flight
   const uint32_t iters = (nS + NT * FU - 1) / (NT * FU) * (NT * FU);
+  // only a distance within the last tested round's threshold counts (most
+  // candidates are farther); a thread's positions only grow, so the round
+  // of its current position is kept and advanced
+  const float thr_last = nr > 0 ? s_thr[nr - 1] : -INFINITY;
+  int rcur = 0;
   for (uint32_t p0 = threadIdx.x; p0 < iters; p0 += NT * FU) {
     float dv[FU];
 #pragma unroll
@@ -1682,13 +1676,15 @@ __global__ void __launch_bounds__(NT) k_finalize(FinalArgs a) {
     for (int u = 0; u < FU; ++u) {
       const uint32_t p = p0 + u * NT;
       uint32_t key = 0xffffffffu;
-      if (p < nS) {
-        const int r = upper_bound_u(s_rend, nr, p);
-        const int x = max(r, lower_bound_f(s_thr, Ru, dv[u]));
+      if (p < nS && dv[u] <= thr_last) {
+        while (rcur < nr && s_rend[rcur] <= p) ++rcur;   // the round p was inserted in
+        const int x = rcur + lower_bound_f(s_thr + rcur, nr - rcur, dv[u]);
         if (x < nr) key = (uint32_t)x;
       }
-      const uint32_t peers = __match_any_sync(0xffffffffu, key);
-      if (key != 0xffffffffu && (peers & lt) == 0) atomicAdd(&s_hist[key], (uint32_t)__popc(peers));
+      if (__any_sync(0xffffffffu, key != 0xffffffffu)) {
+        const uint32_t peers = __match_any_sync(0xffffffffu, key);
+        if (key != 0xffffffffu && (peers & lt) == 0) atomicAdd(&s_hist[key], (uint32_t)__popc(peers));
+      }
     }
   }
   __syncthreads();
