@@ -1088,14 +1088,18 @@ __device__ __forceinline__ void rows_dist2(const TX* __restrict__ X, int d,
 #pragma unroll
       for (int u = 0; u < ILP; ++u) xv[u] = V::ld(xr[u], i);
       const float4 qf = V::f(qv);
+      // (x - q) of two coordinates per packed FP32 subtraction (each rounded
+      // as a scalar one), then the squares added in coordinate order by fused
+      // multiply-adds
+      const unsigned long long qxy = pack2(qf.x, qf.y), qzw = pack2(qf.z, qf.w);
 #pragma unroll
       for (int u = 0; u < ILP; ++u) {
         const float4 xf = V::f(xv[u]);
-        const float d0 = xf.x - qf.x, d1 = xf.y - qf.y, d2 = xf.z - qf.z, d3 = xf.w - qf.w;
-        acc[u] = fmaf(d0, d0, acc[u]);
-        acc[u] = fmaf(d1, d1, acc[u]);
-        acc[u] = fmaf(d2, d2, acc[u]);
-        acc[u] = fmaf(d3, d3, acc[u]);
+        const unsigned long long dxy = sub2(pack2(xf.x, xf.y), qxy), dzw = sub2(pack2(xf.z, xf.w), qzw);
+        acc[u] = fmaf(lo2(dxy), lo2(dxy), acc[u]);
+        acc[u] = fmaf(hi2(dxy), hi2(dxy), acc[u]);
+        acc[u] = fmaf(lo2(dzw), lo2(dzw), acc[u]);
+        acc[u] = fmaf(hi2(dzw), hi2(dzw), acc[u]);
       }
     }
   } else {
@@ -1727,12 +1731,20 @@ __global__ void __launch_bounds__(NT) k_finalize(FinalArgs a) {
     }
     const unsigned long long tau = s_tau;
     const uint32_t c1 = min(nsf, c0 + (uint32_t)chunk);
+    const uint32_t tau_hi = (uint32_t)(tau >> 32);
     for (uint32_t p0 = c0 + threadIdx.x; p0 < c1; p0 += NT * FU) {
+      uint32_t db[FU];
+#pragma unroll
+      for (int u = 0; u < FU; ++u) {
+        const uint32_t p = p0 + u * NT;
+        db[u] = p < c1 ? __float_as_uint(dl[p]) : 0xffffffffu;
+      }
+      // the id is read only where the distance alone does not decide
       unsigned long long kv[FU];
 #pragma unroll
       for (int u = 0; u < FU; ++u) {
         const uint32_t p = p0 + u * NT;
-        kv[u] = p < c1 ? (((unsigned long long)__float_as_uint(dl[p]) << 32) | cl[p]) : ~0ull;
+        kv[u] = (p < c1 && db[u] <= tau_hi) ? (((unsigned long long)db[u] << 32) | cl[p]) : ~0ull;
       }
 #pragma unroll
       for (int u = 0; u < FU; ++u) {
