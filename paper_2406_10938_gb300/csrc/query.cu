@@ -1070,12 +1070,44 @@ struct Vec4Of<uint8_t> {
 // Partial squared distances of ILP rows (ids[u] == ~0u: no row) to q; each
 // lane covers a strided slice of the d coordinates, all rows' loads of a
 // slice are issued before their arithmetic.
-template <typename TX>
+// TWO_SLICES: the distance kernels' path for d <= 256 (at most two slices per
+// lane, addresses formed once per row); the top-k's shortlist re-rank keeps
+// the plain loop, which needs fewer registers. Both give the same sums.
+template <typename TX, bool TWO_SLICES = true>
 __device__ __forceinline__ void rows_dist2(const TX* __restrict__ X, int d,
                                            const uint32_t* ids, const TX* __restrict__ q,
                                            bool vec4, int lane, float* acc) {
   using V = Vec4Of<TX>;
-  if (vec4) {
+  if (TWO_SLICES && vec4 && d <= 256) {
+    // at most two 4-coordinate slices per lane (lane and lane + 32): the
+    // lane's offset is folded into each row's address once and the second
+    // slice is a constant offset from it. A missing row (id ~0) reads row 0
+    // and its sum is not used, so the loads need no branch
+    const int d4 = d >> 2;
+    const TX* xr[ILP];
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) xr[u] = X + 4 * lane + (int64_t)(ids[u] != 0xffffffffu ? ids[u] : 0u) * d;
+    const TX* ql = q + 4 * lane;
+#pragma unroll
+    for (int sl = 0; sl < 2; ++sl) {
+      if (lane + 32 * sl >= d4) break;
+      const typename V::T qv = V::ld(ql, 32 * sl);
+      typename V::T xv[ILP];
+#pragma unroll
+      for (int u = 0; u < ILP; ++u) xv[u] = V::ld(xr[u], 32 * sl);
+      const float4 qf = V::f(qv);
+      const unsigned long long qxy = pack2(qf.x, qf.y), qzw = pack2(qf.z, qf.w);
+#pragma unroll
+      for (int u = 0; u < ILP; ++u) {
+        const float4 xf = V::f(xv[u]);
+        const unsigned long long dxy = sub2(pack2(xf.x, xf.y), qxy), dzw = sub2(pack2(xf.z, xf.w), qzw);
+        acc[u] = fmaf(lo2(dxy), lo2(dxy), acc[u]);
+        acc[u] = fmaf(hi2(dxy), hi2(dxy), acc[u]);
+        acc[u] = fmaf(lo2(dzw), lo2(dzw), acc[u]);
+        acc[u] = fmaf(hi2(dzw), hi2(dzw), acc[u]);
+      }
+    }
+  } else if (vec4) {
     const int d4 = d >> 2;
     // a missing row (id ~0) reads row 0 and its sum is not used: the loads
     // need no branch
@@ -1776,7 +1808,7 @@ __global__ void __launch_bounds__(NT) k_finalize(FinalArgs a) {
         ids[u] = (e0 + u < have) ? (uint32_t)(tk[e0 + u] & 0xffffffffull) : 0xffffffffu;
         acc[u] = 0.f;
       }
-      rows_dist2<TX>(X, a.d, ids, q, a.vec4, lane, acc);
+      rows_dist2<TX, false>(X, a.d, ids, q, a.vec4, lane, acc);
       const float v = transpose_reduce8(acc, lane);
       const int r = (lane >> 2) & 7;
       __syncwarp();
