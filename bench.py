@@ -148,6 +148,13 @@ def _ncu_traffic_per_unit(kernel, workload="mid"):
     return None
 
 
+def gather_kernel(d, shortlist):
+    """The distance kernel the library launches for FP32 rows of d coordinates."""
+    if shortlist:
+        return "k_dist_bf16"
+    return "k_dist_g8" if d % 4 == 0 and d <= 128 else "k_dist"
+
+
 def roofline_obj(kernel, algo_bytes_per_launch, avg_launch_ms, launches, traffic=None, source=None):
     peak, peak_kind = _peaks()
     achieved = algo_bytes_per_launch / (avg_launch_ms / 1000.0) / 1e9
@@ -447,7 +454,7 @@ def mid_leg(args, rank, world, local_rank, barrier):
     total_leaves = info["total_leaves"]
     enc_bytes = w["n"] * (w["d"] * (2 if proj_mode else s_in) + w["K"] * w["L"])
     cand = {
-        ("k_dist_bf16" if args.shortlist else "k_dist"): (
+        gather_kernel(w["d"], args.shortlist): (
             n_cand * (w["d"] * (2 if args.shortlist else s_in) + 4 + 4), ph["dist_ms"], ph["dist_launches"]),
         "k_walk": (nq * total_leaves * 4.0 + n_cand * 8, ph["walk_ms"], ph["dist_launches"]),
         "k_finalize": (n_cand * 8.0, ph["finalize_ms"], ph["dist_launches"]),
@@ -458,7 +465,7 @@ def mid_leg(args, rank, world, local_rank, barrier):
     dom = max(cand, key=lambda k_: cand[k_][1])
     b, ms, nl = cand[dom]
     per_unit = _ncu_traffic_per_unit(dom.split("<")[0])
-    traffic = per_unit * (n_cand / nl) if (per_unit is not None and dom == "k_dist") else None
+    traffic = per_unit * (n_cand / nl) if (per_unit is not None and dom in ("k_dist", "k_dist_g8")) else None
     roofline = roofline_obj(dom, b / nl, ms / nl, nl, traffic=traffic,
                             source="CUDA events around the kernel on the query's stream, timed steps")
     bpp = build_bytes_per_point(w["d"], s_in, w["K"], w["L"])
@@ -476,7 +483,9 @@ def mid_leg(args, rank, world, local_rank, barrier):
     if proj_mode == 0 and not args.no_mixed:
         pkg.detlsh_trace_enable(False)
         idx_m = pkg.detlsh_build(X, A, ids, w["K"], w["L"], w["n_regions"], w["max_leaf"], borrow=True, proj_mode=1)
-        ns = min(nq, 2000)
+        # as many held-out queries as the scored step: the tuned batch size
+        # and stream count are chosen for this query count
+        ns = nq
         _, Q_tune = make_workload(w["name"], n=1, nq=ns, seed_query=1000 + rank, device=dev)
         tune = pkg.detlsh_autotune(idx_m, Q_tune, kk[:ns], cc[:ns], rr[:ns], k_max=w["k"], eps=eps,
                                    beta=w["beta"], min_agreement=0.995)
@@ -652,7 +661,7 @@ def batching_leg(args, rank, world, local_rank, barrier, steps, warmup):
     recall = sum(r for _, r in rec) / len(rec)
 
     dbytes = w["d"] * (2 if args.shortlist else 4) + 8
-    cand = {("k_dist_bf16" if args.shortlist else "k_dist"): (n_cand * dbytes, ph["dist_ms"], ph["dist_launches"]),
+    cand = {gather_kernel(w["d"], args.shortlist): (n_cand * dbytes, ph["dist_ms"], ph["dist_launches"]),
             "k_walk": (nq * info["total_leaves"] * 4.0 + n_cand * 8, ph["walk_ms"], ph["dist_launches"]),
             "k_leaf_lb": (nq * info["total_leaves"] * 4.0, ph["lb_ms"], ph["lb_launches"])}
     dom = max(cand, key=lambda k_: cand[k_][1])

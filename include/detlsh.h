@@ -504,7 +504,9 @@ double detlsh_eps_lemma3(int32_t K, int32_t L);
  *   [5] leaf lower bounds, [6] candidate distances, [7] number of distance
  *   launches, [8] number of lower-bound launches, [9] whole build, [10] whole
  *   query, [11] bucket walks, [12] stop test and top-k, [13] round table,
- *   leaf rounds and bucket lists.
+ *   leaf rounds and bucket lists, [14]-[16] the leaf build's root sort,
+ *   gathers and level passes, [17] its number of level iterations, [18] the
+ *   grouping of candidates by point-id range before the distances.
  *   Returns the number of entries written (<= len).
  * detlsh_launch_count -- kernels this library has launched in the process.
  */

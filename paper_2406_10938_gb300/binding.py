@@ -41,7 +41,7 @@ PENDING, EADMIT = 1, -5
 PLAN_GRAPH = 1
 TRACE_KEYS = ("sample_proj_ms", "breakpoints_ms", "encode_ms", "leaves_ms", "query_proj_ms", "lb_ms",
               "dist_ms", "dist_launches", "lb_launches", "build_ms", "query_ms", "walk_ms", "finalize_ms",
-              "bucket_ms", "leaf_root_ms", "leaf_gather_ms", "leaf_levels_ms", "leaf_iterations")
+              "bucket_ms", "leaf_root_ms", "leaf_gather_ms", "leaf_levels_ms", "leaf_iterations", "group_ms")
 
 
 class DetlshError(RuntimeError):

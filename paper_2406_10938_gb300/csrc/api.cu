@@ -648,6 +648,7 @@ int detlsh_query(const detlsh_index* idx, const void* Q, int64_t nq, int32_t dty
   }
   trace_reset(TR_QUERY_PROJ, TR_LB_LAUNCHES);
   trace_reset(TR_QUERY_TOTAL, TR_BUCKET);
+  trace_reset(TR_GROUP, TR_GROUP);
   PhaseTimer total(s);
   total.begin(TR_QUERY_TOTAL);
   Out oi, od, os, oc, oq;

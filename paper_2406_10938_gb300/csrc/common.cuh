@@ -56,7 +56,7 @@ int require_device_ptr(const void* p, const char* name);
 enum TracePhase {
   TR_SAMPLE_PROJ = 0, TR_BREAKPOINTS, TR_ENCODE, TR_LEAVES, TR_QUERY_PROJ, TR_LB, TR_DIST,
   TR_DIST_LAUNCHES, TR_LB_LAUNCHES, TR_BUILD_TOTAL, TR_QUERY_TOTAL, TR_WALK, TR_FINALIZE, TR_BUCKET,
-  TR_LEAF_ROOT, TR_LEAF_GATHER, TR_LEAF_LEVELS, TR_LEAF_ITERS, TR_COUNT
+  TR_LEAF_ROOT, TR_LEAF_GATHER, TR_LEAF_LEVELS, TR_LEAF_ITERS, TR_GROUP, TR_COUNT
 };
 bool trace_on();
 void trace_reset(int first, int last);

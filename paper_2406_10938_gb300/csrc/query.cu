@@ -67,6 +67,12 @@ __device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigne
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
 __device__ __forceinline__ float max3f(float a, float b, float c) {
   float d;
   asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
@@ -78,7 +84,9 @@ __device__ __forceinline__ float hi2(unsigned long long v) { return __uint_as_fl
 // Leaf lower bound: sum over j = 0..K-1, in that order, of
 // max(e_lo - x, x - e_hi, 0)^2 in FP32 (no contraction). Dimensions are taken
 // in pairs with packed FP32x2 subtractions and products; the sum keeps the
-// scalar order.
+// scalar order. KT > 0: K == KT, known at compile time (an even KT makes every
+// tree's q' slice 8-byte aligned and drops the per-dimension tests).
+template <int KT>
 __global__ void __launch_bounds__(LB_THREADS)
 k_leaf_lb(const float* __restrict__ qp, const uint32_t* __restrict__ nqd, int LK, const float* __restrict__ E, int Nr,
           int K, const uint8_t* __restrict__ leaf_lo, const uint8_t* __restrict__ leaf_hi,
@@ -90,6 +98,7 @@ k_leaf_lb(const float* __restrict__ qp, const uint32_t* __restrict__ nqd, int LK
   extern __shared__ __align__(16) float s_qrows[];
   const int LKP = (LK + 1) / 2 * 2 + 2;
   __shared__ uint32_t s_min[LB_QCH], s_max[LB_QCH];
+  if (KT > 0) K = KT;
   const int64_t leaf = (int64_t)blockIdx.x * LB_THREADS + threadIdx.x;
   const int64_t qb0 = (int64_t)blockIdx.y * LB_QCH;
   const int64_t nqb = *nqd;
@@ -126,8 +135,11 @@ k_leaf_lb(const float* __restrict__ qp, const uint32_t* __restrict__ nqd, int LK
     eh2[j] = pack2(eh[2 * j], eh[2 * j + 1]);
   }
   const int rbase = tree * K;
-  const bool paired = (rbase % 2) == 0;   // q' rows at an even base are 8-byte aligned
-  for (int q = 0; q < nqc; ++q) {
+  // q' rows at an even base are 8-byte aligned
+  const bool paired = (KT > 0 && KT % 2 == 0) || (rbase % 2) == 0;
+  float* lbp = lb2 + qb0 * total_leaves + leaf;
+  uint32_t* bmp = blkmin + qb0 * nblk + (leaf >> 5);
+  for (int q = 0; q < nqc; ++q, lbp += total_leaves, bmp += nblk) {
     float acc = 0.f;
     if (paired) {
       const float* xq = s_qrows + q * LKP + rbase;
@@ -156,15 +168,17 @@ k_leaf_lb(const float* __restrict__ qp, const uint32_t* __restrict__ nqd, int LK
         }
       }
     }
-    if (valid) lb2[(qb0 + q) * total_leaves + leaf] = acc;
+    if (valid) *lbp = acc;
     // non-negative floats order like their bit patterns
-    uint32_t mn = (valid && acc > 0.f) ? __float_as_uint(acc) : 0xffffffffu;
-    uint32_t mx = valid ? __float_as_uint(acc) : 0u;
     // the smallest bound of the warp's 32 leaves (a lower-bound block)
     const uint32_t mb = __reduce_min_sync(0xffffffffu, valid ? __float_as_uint(acc) : 0x7f800000u);
-    if ((threadIdx.x & 31) == 0 && (leaf >> 5) < nblk) blkmin[(qb0 + q) * nblk + (leaf >> 5)] = mb;
-    mn = __reduce_min_sync(0xffffffffu, mn);
-    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0 && (leaf >> 5) < nblk) *bmp = mb;
+    // the smallest positive bound: the block's when that is positive and
+    // finite (then every valid bound is positive), else a second reduction
+    uint32_t mn = mb;
+    if (mb == 0u || mb >= 0x7f800000u)
+      mn = __reduce_min_sync(0xffffffffu, (valid && acc > 0.f) ? __float_as_uint(acc) : 0xffffffffu);
+    const uint32_t mx = __reduce_max_sync(0xffffffffu, valid ? __float_as_uint(acc) : 0u);
     if ((threadIdx.x & 31) == 0) {
       atomicMin(&s_min[q], mn);
       atomicMax(&s_max[q], mx);
@@ -1245,6 +1259,120 @@ k_dist(const TX* __restrict__ X, int d, int64_t n, const TX* __restrict__ Q, int
   }
 }
 
+// FP32 rows with d <= 128, d a multiple of 4 and 16-byte aligned rows: eight
+// lanes per row, lane s of a group holding the 4-coordinate slices s, s + 8,
+// s + 16, s + 24 (S of them) of the row and, in registers for the whole item,
+// of q. A warp step takes eight rows, two per 8-lane group; every lane loads
+// its own rows' ids (eight lanes share an address), so the only shuffles left
+// are the three of the 8-lane reduction — with 32 lanes per row the id
+// broadcasts and the 32-lane reduction took more L1 data-pipe cycles than the
+// row loads' own wavefronts. Per lane and row the squares of even and odd
+// coordinates are accumulated by packed FP32 fused multiply-adds in
+// coordinate order, added, and the eight lanes' partials summed by a
+// butterfly (xor 4, 2, 1): the same order for every row, so a row's distance
+// does not depend on where in a step or which item it is taken.
+struct G8Lane {
+  int sub, g;
+  bool hi;
+};
+
+// the lane's slices of q as packed pairs (zeros past d)
+template <int S>
+__device__ __forceinline__ void g8_load_q(const float* q, const bool* has, const G8Lane& gl,
+                                          unsigned long long (&qv)[S][2]) {
+  const float4* ql = reinterpret_cast<const float4*>(q) + gl.sub;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const float4 f = has[s] ? __ldg(ql + 8 * s) : make_float4(0.f, 0.f, 0.f, 0.f);
+    qv[s][0] = pack2(f.x, f.y);
+    qv[s][1] = pack2(f.z, f.w);
+  }
+}
+
+// the distances of one query's candidates [r0, r1): list entries cl[e] (BK:
+// pairs pl[e] = (point id, list position)), each written to out[position]
+template <int S, bool BK>
+__device__ __forceinline__ void g8_rows(const float* __restrict__ X, int d, int64_t n,
+                                        const uint32_t* __restrict__ cl, const uint2* __restrict__ pl,
+                                        uint32_t r0, uint32_t r1, int64_t cap, const bool* has, const G8Lane& gl,
+                                        const unsigned long long (&qv)[S][2], float* __restrict__ out) {
+  for (uint32_t e0 = r0; e0 < r1; e0 += 8) {
+    uint32_t id[2], pos[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const uint32_t e = e0 + 2 * gl.g + u;
+      id[u] = 0xffffffffu;
+      pos[u] = 0xffffffffu;
+      if (e < r1) {
+        if (BK) {
+          const uint2 P = __ldg(pl + e);
+          id[u] = P.x;
+          pos[u] = P.y;
+        } else {
+          id[u] = __ldg(cl + e);
+          pos[u] = e;
+        }
+      }
+      if (id[u] != 0xffffffffu && !DL_CHECK(id[u] < n, 10, id[u])) id[u] = 0xffffffffu;
+    }
+    // a missing row (id ~0) reads row 0 and its sum is not stored
+    const float4* xr[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      xr[u] = reinterpret_cast<const float4*>(X + (int64_t)(id[u] != 0xffffffffu ? id[u] : 0u) * d) + gl.sub;
+    float4 xv[2][S];
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int u = 0; u < 2; ++u) xv[u][s] = has[s] ? __ldg(xr[u] + 8 * s) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float acc[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      unsigned long long a2 = 0ull;   // (even, odd) coordinate sums, both +0
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const unsigned long long dxy = sub2(pack2(xv[u][s].x, xv[u][s].y), qv[s][0]);
+        const unsigned long long dzw = sub2(pack2(xv[u][s].z, xv[u][s].w), qv[s][1]);
+        a2 = fma2(dxy, dxy, a2);
+        a2 = fma2(dzw, dzw, a2);
+      }
+      acc[u] = lo2(a2) + hi2(a2);
+    }
+    // 8-lane butterfly: after the xor-4 exchange a lane keeps row `hi`
+    float v = (gl.hi ? acc[1] : acc[0]) + __shfl_xor_sync(0xffffffffu, gl.hi ? acc[0] : acc[1], 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    const uint32_t p = gl.hi ? pos[1] : pos[0];
+    if ((gl.sub & 3) == 0 && p != 0xffffffffu && DL_CHECK(p < cap, 11, p)) out[p] = v;
+  }
+}
+
+// persistent over the work queue, as k_dist
+template <int S, bool BK>
+__global__ void __launch_bounds__(DT, 4)
+k_dist_g8(const float* __restrict__ X, int d, int64_t n, const float* __restrict__ Q, int64_t q0,
+          const uint32_t* __restrict__ cand, const uint2* __restrict__ pairs, int64_t cap,
+          const uint4* __restrict__ items, const uint32_t* __restrict__ qtail, uint32_t* __restrict__ head,
+          float* __restrict__ d2out) {
+  const uint32_t nit = *qtail;
+  const int lane = threadIdx.x & 31;
+  const G8Lane gl{lane & 7, lane >> 3, (lane & 4) != 0};
+  bool has[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) has[s] = 8 * s + gl.sub < (d >> 2);
+  uint32_t it = next_item(head, lane);
+  while (it < nit) {
+    const uint4 item = items[it];
+    const uint32_t nx = next_item(head, lane);
+    const int64_t qb = item.x;
+    unsigned long long qv[S][2];
+    g8_load_q<S>(Q + (q0 + qb) * (int64_t)d, has, gl, qv);
+    g8_rows<S, BK>(X, d, n, cand + qb * cap, BK ? pairs + qb * cap : nullptr, item.y, item.z, cap, has, gl, qv,
+                   d2out + qb * cap);
+    it = nx;
+  }
+}
+
 // uint8 rows, d a power of two from 16 to 512: d/16 lanes per row, 16 bytes a
 // lane, so one load instruction covers 32/(d/16) rows and a warp keeps eight
 // of them (32 rows at d = 128) in flight. The squared distance is
@@ -1947,7 +2075,8 @@ int query_shape(const detlsh_index* idx, int64_t nq, int k_max, double beta, int
     return DETLSH_EINVAL;
   }
   sh.wl_total = wl.total;
-  DL_CUDA(cudaFuncSetAttribute(k_leaf_lb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lb_smem_bytes(sh.LK)));
+  DL_CUDA(cudaFuncSetAttribute(k_leaf_lb<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lb_smem_bytes(sh.LK)));
+  DL_CUDA(cudaFuncSetAttribute(k_leaf_lb<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lb_smem_bytes(sh.LK)));
   DL_CUDA(cudaFuncSetAttribute(k_walk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wl.total));
   DL_CUDA(cudaFuncSetAttribute(k_walk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wl.total));
   int walk_per_sm = 0;
@@ -2194,7 +2323,7 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   dim3 g1(ceil_div(TL, LB_THREADS), ceil_div(nqg, LB_QCH));
   tm.begin(TR_LB);
   uint32_t* blkmin = reinterpret_cast<uint32_t*>(b + sh.o_blkmin);
-  k_leaf_lb<<<g1, LB_THREADS, lb_smem_bytes(LK), s>>>(qp, nqd, LK, idx->E, idx->Nr, idx->K, idx->leaf_lo, idx->leaf_hi,
+  (idx->K == 16 ? k_leaf_lb<16> : k_leaf_lb<0>)<<<g1, LB_THREADS, lb_smem_bytes(LK), s>>>(qp, nqd, LK, idx->E, idx->Nr, idx->K, idx->leaf_lo, idx->leaf_hi,
                                       idx->leaf_tree, TL, lb, d_min, d_max, blkmin, sh.nblk);
   DL_LAUNCH();
   tm.end();
@@ -2248,7 +2377,7 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
   DL_LAUNCH();
   tm.end();
 
-  tm.begin(TR_DIST);
+  tm.begin(TR_GROUP);
   const uint2* pairs = sh.nbk ? reinterpret_cast<const uint2*>(b + sh.o_pairs) : nullptr;
   if (sh.nbk && nqg > 0) {
     // the distance work by point-id range: per query its candidates grouped by
@@ -2267,6 +2396,8 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
     k_cell_fill<<<ceil_div(cells, 256), 256, 0, s>>>(bcnt, ioff, boffq, (int)sh.nbk, nqg, sh.dist_rows, items);
     DL_LAUNCH();
   }
+  tm.end();
+  tm.begin(TR_DIST);
   if (sh.lm) {
     LmBatch lb{};
     lb.qb16 = b + sh.o_qb16;
@@ -2303,6 +2434,16 @@ int enqueue_batch(const detlsh_index* idx, const QueryShape& sh, void* base, con
     (pairs ? k_dist<uint8_t, true> : k_dist<uint8_t, false>)<<<sh.dgrid, DT, 0, s>>>(
         static_cast<const uint8_t*>(idx->X), idx->d, idx->n, static_cast<const uint8_t*>(Q), q0, candb, pairs, sh.cap,
         items, ctr + CT_QTAIL, ctr + CT_HEAD, d2b, vec4);
+  } else if (vec4 && idx->d <= 128) {
+    auto kern = pairs ? k_dist_g8<4, true> : k_dist_g8<4, false>;
+    switch ((idx->d / 4 + 7) / 8) {
+      case 1: kern = pairs ? k_dist_g8<1, true> : k_dist_g8<1, false>; break;
+      case 2: kern = pairs ? k_dist_g8<2, true> : k_dist_g8<2, false>; break;
+      case 3: kern = pairs ? k_dist_g8<3, true> : k_dist_g8<3, false>; break;
+      default: break;
+    }
+    kern<<<sh.dgrid, DT, 0, s>>>(static_cast<const float*>(idx->X), idx->d, idx->n, static_cast<const float*>(Q), q0,
+                                 candb, pairs, sh.cap, items, ctr + CT_QTAIL, ctr + CT_HEAD, d2b);
   } else {
     (pairs ? k_dist<float, true> : k_dist<float, false>)<<<sh.dgrid, DT, 0, s>>>(
         static_cast<const float*>(idx->X), idx->d, idx->n, static_cast<const float*>(Q), q0, candb, pairs, sh.cap, items,
