@@ -534,7 +534,8 @@ __host__ __device__ inline WalkLayout walk_layout(int L, int64_t smem_bitmap_wor
   return o;
 }
 
-enum { W_S = 0, W_STOP, W_NEED, W_KSTAR, W_ACC, W_TOTNEW, W_QN, W_LEAFA, W_OFFA, W_OVF, W_ONE, W_NREC };
+enum { W_S = 0, W_STOP, W_NEED, W_KSTAR, W_ACC, W_TOTNEW, W_QN, W_LEAFA, W_OFFA, W_OVF, W_ONE, W_NREC, W_LASTEX,
+       W_LASTNEW };
 
 // Append the new points of bucket leaves list[0..nl) (only leaves whose select
 // key lies in (kmin, kstar] when filtered) to the candidate list, in batches of at most
@@ -569,6 +570,8 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
     misc[W_LEAFA] = 0;
     misc[W_OFFA] = 0;
     misc[W_TOTNEW] = 0;
+    misc[W_LASTEX] = 0;
+    misc[W_LASTNEW] = 0;
   }
   if (count_only)
     for (uint32_t j = threadIdx.x; j < nl; j += WT) newcnt[j] = 0;
@@ -756,6 +759,10 @@ __device__ void walk_add(const WalkArgs& a, const uint32_t* list, uint32_t nl, b
     }
     if (threadIdx.x == 0) {
       if (!count_only) misc[W_S] += misc[W_QN];
+      // points this call examined and found new (the walk's estimate of the
+      // new share of the next points it will examine)
+      misc[W_LASTEX] += take_pts;
+      misc[W_LASTNEW] = count_only ? misc[W_TOTNEW] : misc[W_LASTNEW] + misc[W_QN];
       if (take_leaves == 0) {
         const uint32_t first_total = bpref[1] + offa;  // points of leaf la (after filter)
         const uint32_t newoff = offa + take_pts;
@@ -966,11 +973,16 @@ __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
           walk_add<POS>(a, bl, nl, false, ~0ull, lbrow, sm, ly, bitmap, cand, false, nullptr, nullptr, false, 0, rec);
         } else {
           // the bucket may hold the cut: its leaves in key order (lower bound,
-          // leaf) are taken in chunks of about twice the points still needed
-          // (a select on the leaves' sizes); the new points of a chunk are
-          // counted (bitmap read only) and the chunk is added whole, or, if it
-          // holds the cut, up to the leaf where |S| reaches T (a select on the
-          // new counts). Only the chunks up to the cut are examined.
+          // leaf) are taken in chunks (a select on the leaves' sizes) of the
+          // points still needed over the new share of the points examined last
+          // (the previous bucket, or the previous chunk), with a quarter more —
+          // twice the need when there is no such share; the new points of a
+          // chunk are counted (bitmap read only) and the chunk is added whole,
+          // or, if it holds the cut, up to the leaf where |S| reaches T (a
+          // select on the new counts). Only the chunks up to the cut are
+          // examined. A leaf's new count does not depend on the other leaves
+          // of its bucket (one tree holds a point once), so the cut leaf and S
+          // do not depend on the chunk sizes.
           for (uint32_t j = threadIdx.x; j < nl; j += WT) {
             const uint32_t leaf = bl[j];
             lbk[j] = __float_as_uint(lbrow[leaf]);
@@ -982,8 +994,12 @@ __global__ void __launch_bounds__(WT, 3) k_walk(WalkArgs a) {
           while (true) {
             const unsigned long long S0 = misc[W_S];
             const unsigned long long need = T - S0;
-            const unsigned long long kc =
-                select_key(bl, lbk, tcnt, nl, has_kmin, kmin, 2 * need, sel, misc);
+            const unsigned long long ex = misc[W_LASTEX], nw = misc[W_LASTNEW];
+            unsigned long long target = 2 * need;
+            if (ex > 0 && nw > 0)
+              target = (unsigned long long)((double)need * fmin(8.0, fmax(1.0, 1.25 * (double)ex / (double)nw)));
+            __syncthreads();   // every thread has read the last call's counts
+            const unsigned long long kc = select_key(bl, lbk, tcnt, nl, has_kmin, kmin, target, sel, misc);
             walk_add<POS>(a, bl, nl, true, kc, lbrow, sm, ly, bitmap, cand, true, newcnt, lbk, has_kmin, kmin);
             if (S0 + misc[W_TOTNEW] >= T) {
               const unsigned long long kstar = select_key(bl, lbk, newcnt, nl, has_kmin, kmin, need, sel, misc);
