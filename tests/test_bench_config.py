@@ -28,3 +28,31 @@ def test_det_only_uses_one_tree_over_paa():
     seg = w["d"] // w["K"]
     assert torch.allclose(A.sum(1), torch.ones(w["K"]))
     assert (A[0, :seg] == 1.0 / seg).all() and (A[0, seg:] == 0).all()
+
+
+def test_gather_kernel_names_follow_the_library_dispatch():
+    # FP32 rows of at most 128 coordinates (a multiple of 4) take the
+    # eight-lanes-per-row gather, other widths the general one, a shortlist
+    # the BF16 coarse gather
+    assert bench.gather_kernel(128, 0) == "k_dist_g8"
+    assert bench.gather_kernel(96, 0) == "k_dist_g8"
+    assert bench.gather_kernel(4, 0) == "k_dist_g8"
+    assert bench.gather_kernel(132, 0) == "k_dist"
+    assert bench.gather_kernel(960, 0) == "k_dist"
+    assert bench.gather_kernel(126, 0) == "k_dist"
+    assert bench.gather_kernel(128, 64) == "k_dist_bf16"
+
+
+def test_ncu_traffic_is_used_only_for_the_captured_source(tmp_path, monkeypatch):
+    import hashlib
+    src = tmp_path / "kernel.cu"
+    src.write_text("__global__ void k() {}\n")
+    sha = hashlib.sha1(src.read_bytes()).hexdigest()
+    (tmp_path / "profiles").mkdir()
+    prof = tmp_path / "profiles" / "k_x_mid.md"
+    prof.write_text(f"# k_x\n\ntraffic_bytes_per_unit: 66.0 candidate kernel.cu {sha}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._ncu_traffic_per_unit("k_x") == 66.0
+    src.write_text("__global__ void k() { /* changed */ }\n")
+    assert bench._ncu_traffic_per_unit("k_x") is None
+    assert bench._ncu_traffic_per_unit("k_missing") is None
