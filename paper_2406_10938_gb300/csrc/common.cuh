@@ -405,7 +405,7 @@ int radix_sort_pairs_ws(const uint32_t* keys_in, const uint32_t* vals_in, int64_
 // Launch shapes of the query pipeline (results do not depend on them).
 struct QueryTuning {
   int64_t batch = 0;         // queries per batch; 0: sized from free device memory
-  int walk_ctas_per_sm = 0;  // walk CTAs per SM, 1..3; 0: as many as fit
+  int walk_ctas_per_sm = 0;  // walk CTAs per SM, 1..4; 0: as many as fit
   int dist_rows = 1024;      // candidate rows per distance work item (multiple of 64)
   int dist_ctas_per_sm = 0;  // persistent distance CTAs per SM, 1..4; 0: 4 (3 for the BF16 gather)
   int streams = 0;           // 2: batches alternate between two streams; 0 or 1: one stream
